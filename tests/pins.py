@@ -1,0 +1,173 @@
+"""Checks that pin the O1 oracle to facts outside itself.
+
+Each function returns an error figure (0 when the fact holds exactly); the pin
+tests assert them small, and the mutation tests assert that a planted mistake
+in the oracle makes at least one of them large.  None of them re-types the
+oracle's tail-integral formula.
+"""
+import numpy as np
+
+import oracle
+from oracle import brute, edge_form, sparse_fft
+from synth import make_clip, clip_from_rings, rect_ring, RECT_ONLY
+
+TWO_PI = 2.0 * np.pi
+
+
+def _gl_integral(freq, a, b, T, nodes=64):
+    """integral_a^b exp(-j 2 pi f t / T) dt by Gauss-Legendre (signed interval)."""
+    t, w = np.polynomial.legendre.leggauss(nodes)
+    mid, half = 0.5 * (a + b), 0.5 * (b - a)
+    pts = mid + half * t
+    freq = np.asarray(freq, dtype=np.float64)
+    return half * np.sum(w[None, :] * np.exp(-1j * TWO_PI * freq[:, None] * pts[None, :] / T), axis=1)
+
+
+def pin_area(clip, K=2):
+    """F(0,0) equals the polygon area from the shoelace formula on the rings (Step 1)."""
+    area = 0
+    for m in range(clip.n_polys):
+        rx, ry = clip.ring(m)
+        area += -int(np.sum(rx * np.roll(ry, -1) - np.roll(rx, -1) * ry)) // 2
+    F = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    e1 = abs(oracle.area_exact(clip.x, clip.y, clip.s, clip.T) - area)
+    e2 = abs(F[K, K] - area) / max(area, 1)
+    return max(e1, e2)
+
+
+def pin_rectangle(T, x1, y1, x2, y2, K):
+    """A rectangle's block is the outer product of two box transforms,
+    (b - a) e^{-j pi f (a + b) / T} sinc(f (b - a) / T)."""
+    c = clip_from_rings(T, [rect_ring(x1, y1, x2, y2)])
+    F = oracle.block(c.x, c.y, c.s, T, K)
+    f = np.arange(-K, K + 1)
+
+    def box(a, b):
+        return (b - a) * np.exp(-1j * np.pi * f * (a + b) / T) * np.sinc(f * (b - a) / T)
+
+    ref = np.outer(box(x1, x2), box(y1, y2))
+    return np.max(np.abs(F - ref)) / ((x2 - x1) * (y2 - y1))
+
+
+def pin_single_quadrant(T, xv, yv, K):
+    """One signed corner alone is the quadrant [x, T) x [y, T): compare with the
+    sum of quadrature-integrated unit cells of that quadrant."""
+    F = oracle.block(np.array([xv]), np.array([yv]), np.array([1], dtype=np.int8), T, K)
+    f = np.arange(-K, K + 1)
+    C = brute.cell_integrals(f, T)
+    ref = np.outer(C[:, xv:].sum(axis=1), C[:, yv:].sum(axis=1))
+    return np.max(np.abs(F - ref)) / ((T - xv) * (T - yv))
+
+
+def pin_brute(clip, K):
+    """O1 equals the unit-cell brute force (no signed corners, no closed form)."""
+    F1 = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    F3 = brute.block(clip.x, clip.y, clip.poly_offsets, clip.T, K)
+    return np.max(np.abs(F1 - F3)) / max(abs(F3[K, K]), 1)
+
+
+def pin_edge_form(clip, K):
+    F1 = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    F2 = edge_form.block(clip.x, clip.y, clip.poly_offsets, clip.T, K)
+    return np.max(np.abs(F1 - F2)) / max(abs(F2[K, K]), 1)
+
+
+def pin_sparse_fft(clip, K):
+    F1 = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    F4 = sparse_fft.block(clip.x, clip.y, clip.poly_offsets, clip.T, K)
+    return np.max(np.abs(F1 - F4)) / max(abs(F4[K, K]), 1)
+
+
+def pin_hermitian(clip, K):
+    """f is real, so F(-k,-l) = conj F(k,l)."""
+    F = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    return np.max(np.abs(F[::-1, ::-1] - np.conj(F))) / max(abs(F[K, K]), 1)
+
+
+def pin_merge(T, K):
+    """Two rectangles sharing a side add up to the merged rectangle (Eq. signal_model:
+    the half-open cells make them disjoint)."""
+    a = clip_from_rings(T, [rect_ring(3, 5, 11, 14)])
+    b = clip_from_rings(T, [rect_ring(11, 5, 20, 14)])
+    u = clip_from_rings(T, [rect_ring(3, 5, 20, 14)])
+    Fa = oracle.block(a.x, a.y, a.s, T, K)
+    Fb = oracle.block(b.x, b.y, b.s, T, K)
+    Fu = oracle.block(u.x, u.y, u.s, T, K)
+    return np.max(np.abs(Fa + Fb - Fu)) / (17 * 9)
+
+
+def pin_translation(clip, dx, dy, K):
+    """Shifting the clip by (dx, dy) multiplies F(k,l) by e^{-j 2 pi (k dx + l dy) / T}."""
+    T = clip.T
+    F = oracle.block(clip.x, clip.y, clip.s, T, K)
+    Fs = oracle.block(clip.x + dx, clip.y + dy, clip.s, T, K)
+    f = np.arange(-K, K + 1)
+    ramp = np.exp(-1j * TWO_PI * (f[:, None] * dx + f[None, :] * dy) / T)
+    return np.max(np.abs(Fs - ramp * F)) / max(abs(F[K, K]), 1)
+
+
+def _loss_at(xr, yr, s, T, K, Ft):
+    F = oracle.block_entries(xr, yr, s, T, oracle.freqs(K), oracle.freqs(K))
+    return oracle.pupil_loss(F, Ft, K)[0]
+
+
+def pin_vertex_gradient_fd(clip, target, K, vertices, h=1e-4):
+    """Analytic per-vertex gradient vs central differences of the loss, the vertex
+    moved alone (F = sum_v s_v X(x_v) X(y_v) is smooth in each coordinate)."""
+    T = clip.T
+    Ft = oracle.block(target.x, target.y, target.s, T, K)
+    F = oracle.block(clip.x, clip.y, clip.s, T, K)
+    _, G = oracle.pupil_loss(F, Ft, K)
+    gx, gy = oracle.vertex_gradient(clip.x, clip.y, clip.s, T, K, G)
+    xr = clip.x.astype(np.float64)
+    yr = clip.y.astype(np.float64)
+    err, scale = 0.0, 0.0
+    for v in vertices:
+        for g, arr, other in ((gx, xr, yr), (gy, yr, xr)):
+            keep = arr[v]
+            arr[v] = keep + h
+            lp = _loss_at(xr, yr, clip.s, T, K, Ft)
+            arr[v] = keep - h
+            lm = _loss_at(xr, yr, clip.s, T, K, Ft)
+            arr[v] = keep
+            fd = (lp - lm) / (2 * h)
+            err = max(err, abs(fd - g[v]))
+            scale = max(scale, abs(fd))
+    return err / max(scale, 1e-300)
+
+
+def pin_edge_gradient_boundary(clip, target, K):
+    """dL/d(edge position) from the boundary integral of the moving edge.
+
+    With y up and clockwise rings the interior lies right of the travel
+    direction, so dF/da = -integral_{y_s}^{y_e} e^{-j w (k a + l y)} dy for a
+    vertical edge at x = a, and dF/db = +integral_{x_s}^{x_e} e^{-j w (k x + l b)} dx
+    for a horizontal edge at y = b (signed intervals, quadrature)."""
+    T = clip.T
+    f = oracle.freqs(K)
+    Ft = oracle.block(target.x, target.y, target.s, T, K)
+    F = oracle.block(clip.x, clip.y, clip.s, T, K)
+    _, G = oracle.pupil_loss(F, Ft, K)
+    gx, gy = oracle.vertex_gradient(clip.x, clip.y, clip.s, T, K, G)
+    gE = oracle.edge_gradient(gx, gy, clip.ev0, clip.ev1, clip.eaxis)
+    ref = np.zeros_like(gE)
+    for e in range(clip.ev0.shape[0]):
+        a, b = clip.ev0[e], clip.ev1[e]
+        if clip.eaxis[e] == 0:
+            pos = float(clip.x[a])
+            Iy = _gl_integral(f, float(clip.y[a]), float(clip.y[b]), T)
+            dF = -np.outer(np.exp(-1j * TWO_PI * f * pos / T), Iy)
+        else:
+            pos = float(clip.y[a])
+            Ix = _gl_integral(f, float(clip.x[a]), float(clip.x[b]), T)
+            dF = np.outer(Ix, np.exp(-1j * TWO_PI * f * pos / T))
+        ref[e] = np.real(np.sum(np.conj(G) * dF))
+    return np.max(np.abs(gE - ref)) / max(np.max(np.abs(ref)), 1e-300)
+
+
+def tiny_clips():
+    """Small clips for the brute-force pins (T <= 32)."""
+    return [make_clip(16, 2, 11, smin=3, smax=6, wmin=1, margin=1),
+            make_clip(24, 4, 12, smin=3, smax=9, wmin=1, margin=1),
+            make_clip(32, 4, 13, smin=4, smax=14, wmin=1, margin=1),
+            make_clip(32, 9, 14, smin=3, smax=8, wmin=1, margin=1, mix=RECT_ONLY)]
