@@ -1,0 +1,163 @@
+/*
+ * fcfs.h -- C ABI of the GB300 (sm_103a) continuous Fourier-series library for
+ * Manhattan clips (fast continuous Fourier series, FCFS).
+ *
+ * The transform.  A clip is the period [0,T) x [0,T) holding disjoint simple
+ * rectilinear lattice polygons (Sec. II-A.2, Eq. polydef_R); its image is the sum
+ * of their indicators (Sec. III-A, Eq. signal_model).  The library returns the
+ * unnormalised continuous Fourier-series block
+ *
+ *     F(k,l) = integral over the image of exp(-j 2 pi (k x + l y) / T) dx dy,
+ *     |k|, |l| <= K,
+ *
+ * i.e. the paper's coefficients of Eq. fourier_basis times T, so F(0,0) is the
+ * area.  Each polygon enters as its signed corners (x_v, y_v, s_v): by
+ * Prop. rect_union and Lemma polyip with the tail primitive, the polygon is the
+ * signed sum of upper-right quadrants [x_v,T) x [y_v,T), s_v = -1 at the start
+ * and +1 at the end of every horizontal edge of a clockwise ring (y up),
+ * equivalently the 2-D finite difference of the occupancy at the corner.  Then
+ *
+ *     F = X diag(s) Y^T,   X[k,v] = integral_{x_v}^T exp(-j 2 pi k t / T) dt,
+ *
+ * evaluated on the GPU in the reduced closed forms of Prop. CFT: F(0,0) is the
+ * exact integer area (Eq. Fdc), F(k,0) and F(0,l) are weighted 1-D sums
+ * (Eqs. Fk0, F0l), and F(k,l), k,l != 0, is -T^2/(4 pi^2 k l) times the 2-D DFT
+ * of the sparse +-1 corner image at (k mod T, l mod T) (Eq. Fkl, Step 4).
+ *
+ * Common conventions.
+ *  - Every array pointer is a DEVICE pointer owned by the caller.  The library
+ *    allocates nothing on the device; scratch memory is the caller's workspace.
+ *  - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is the
+ *    legacy default stream).  Calls return once the work is enqueued.
+ *  - Vertex arrays are structure-of-arrays: int32 x[V], int32 y[V], int8 s[V],
+ *    16-byte aligned (torch allocations are), vertices of a polygon contiguous.
+ *  - T is a power of two, 4 <= T <= 65536; coordinates satisfy 0 <= x,y <= T;
+ *    s is +1 or -1; the signed set must be balanced (every vertical and every
+ *    horizontal line carries signs summing to zero), as it is for any union of
+ *    polygons.  1 <= K <= 4096.
+ *  - F_out is complex64 interleaved (re, im), (2K+1) x (2K+1) row-major,
+ *    F_out[(k+K)*(2K+1) + (l+K)] = F(k,l).
+ *  - Host-detectable errors are returned at once and nothing is enqueued.
+ *    Errors found on the device (bad vertex data with FCFS_FLAG_VALIDATE, a
+ *    bounded wait that gave up) are written to a status word in the workspace,
+ *    read with fcfs_get_status().  No kernel traps.
+ *  - Results are deterministic: reductions run in a fixed order.
+ */
+#ifndef FCFS_H
+#define FCFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FCFS_OK = 0,
+    FCFS_EINVAL = 1,         /* bad scalar argument, NULL or misaligned pointer */
+    FCFS_EINVAL_DATA = 2,    /* device validation rejected the vertex data */
+    FCFS_EWORKSPACE = 3,     /* workspace NULL, misaligned (256 B) or too small */
+    FCFS_ECUDA = 4,          /* a CUDA runtime or driver call failed */
+    FCFS_ETIMEOUT = 5,       /* a bounded device-side wait gave up */
+    FCFS_EUNSUPPORTED = 6    /* size or precision outside the implemented range */
+} fcfs_status;
+
+typedef enum {
+    FCFS_PREC_FP32 = 0,      /* CUDA-core FP32 FMAs, FP32 sincos table */
+    FCFS_PREC_SPLIT_F16 = 1  /* tcgen05 tensor cores, hi+lo FP16 operands, FP32 accumulate */
+} fcfs_precision;
+
+enum {
+    FCFS_FLAG_VALIDATE = 1   /* check ranges, signs and balance on the device */
+};
+
+/* Library version, major*10000 + minor*100 + patch. */
+int fcfs_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char* fcfs_status_string(fcfs_status st);
+
+/* Number of kernels this process has enqueued through the library so far
+ * (host-side counter; lets a caller count launches inside a timed region). */
+uint64_t fcfs_launch_count(void);
+
+/*
+ * Forward block of one clip (Prop. CFT, Alg. 2).
+ *   x, y, s    : V signed corners (device), see conventions.
+ *   V          : number of corners, 0 <= V < 2^31.  V = 0 gives F = 0.
+ *   T, K       : period and cut-off.
+ *   prec       : fcfs_precision.
+ *   flags      : 0 or FCFS_FLAG_VALIDATE.
+ *   F_out      : (2K+1)^2 complex64 (device), written completely.
+ *   area_out   : one int64 (device), the exact area F(0,0).
+ *   workspace  : device scratch, 256-byte aligned, >= fcfs_workspace_size(...)
+ *                bytes; its first bytes hold the status word of this call.
+ * Returns FCFS_OK once enqueued.
+ */
+size_t fcfs_workspace_size(int64_t V, int32_t T, int32_t K, int32_t prec);
+fcfs_status fcfs_forward(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V,
+                         int32_t T, int32_t K, int32_t prec, uint32_t flags,
+                         float* F_out, int64_t* area_out,
+                         void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Adjoint: derivatives of a real loss L with respect to every corner
+ * coordinate, given the cotangent dF = dL/dRe F + j dL/dIm F over the block
+ * (complex64, same layout as F_out).  Differentiating Lemma polyip with the
+ * tail primitive, dX[k,v]/dx_v = -exp(-j 2 pi k x_v / T), so
+ *   gx[v] = -s_v Re sum_{k,l} conj(dF(k,l)) exp(-j 2 pi k x_v/T) X[l](y_v),
+ *   gy[v] = -s_v Re sum_{k,l} conj(dF(k,l)) X[k](x_v) exp(-j 2 pi l y_v/T),
+ * with the full tail integrals (per corner their constant parts do not cancel).
+ *   gx, gy     : V floats each (device), written completely.
+ * Workspace as for fcfs_forward, sized by fcfs_adjoint_workspace_size().
+ */
+size_t fcfs_adjoint_workspace_size(int64_t V, int32_t T, int32_t K, int32_t prec);
+fcfs_status fcfs_adjoint(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V,
+                         int32_t T, int32_t K, int32_t prec, const float* dF,
+                         float* gx, float* gy,
+                         void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Chain corner derivatives to edge positions: a vertical edge (axis 0) sits at
+ * x and moves the x of both its corners, a horizontal edge (axis 1) sits at y:
+ *   gE[e] = g_axis[ev0[e]] + g_axis[ev1[e]],  g_0 = gx, g_1 = gy.
+ *   ev0, ev1   : E corner indices (device, int32, each < V).
+ *   eaxis      : E axis codes (device, int8, 0 or 1).
+ *   gE         : E floats (device).
+ * Needs no workspace; indices are trusted (callers pass the rings' edges).
+ */
+fcfs_status fcfs_edge_chain(const float* gx, const float* gy, const int32_t* ev0,
+                            const int32_t* ev1, const int8_t* eaxis, int64_t E,
+                            float* gE, void* stream);
+
+/*
+ * Batch of clips sharing T and K (tiles of a layout are independent, Sec. III-A):
+ * clip c owns corners [offsets[c], offsets[c+1]) of the concatenated arrays.
+ *   offsets    : n_clips + 1 int64 (device), offsets[0] = 0,
+ *                offsets[n_clips] = V_total, non-decreasing.
+ *   F_out      : n_clips * (2K+1)^2 complex64 (device), clip-major.
+ *   area_out   : n_clips int64 (device).
+ * One persistent kernel walks a device-built work list of (clip, tile, vertex
+ * range) units, so the call is capturable in a CUDA graph (no host sync).
+ * Workspace sized by fcfs_batch_workspace_size(V_total, n_clips, ...).
+ */
+size_t fcfs_batch_workspace_size(int64_t V_total, int32_t n_clips, int32_t T, int32_t K,
+                                 int32_t prec);
+fcfs_status fcfs_batch(const int32_t* x, const int32_t* y, const int8_t* s,
+                       const int64_t* offsets, int32_t n_clips, int64_t V_total,
+                       int32_t T, int32_t K, int32_t prec, uint32_t flags,
+                       float* F_out, int64_t* area_out,
+                       void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Synchronise `stream` and return the device status word of the last call that
+ * used `workspace` (FCFS_OK, FCFS_EINVAL_DATA or FCFS_ETIMEOUT).
+ */
+fcfs_status fcfs_get_status(const void* workspace, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCFS_H */

@@ -1,0 +1,229 @@
+// C ABI of the FCFS library: argument checks, the launch plan (tiles, vertex
+// splits, workspace layout) and the kernel sequence of each entry point.
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include <cudaTypedefs.h>
+
+#include "fcfs_common.cuh"
+
+namespace fcfs {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+size_t tc_smem_for(int bn, int T, int full);
+
+static int ceil_log2(long long v) {
+  int r = 0;
+  while ((1LL << r) < v) ++r;
+  return r;
+}
+
+static int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 148;
+  return n;
+}
+
+// Number of vertex splits: the smallest count whose CTAs fill the machine's
+// waves to >= 90% while every split keeps >= min_chunks chunks; otherwise the
+// best wave efficiency found.
+static int choose_splits(long long tiles, long long nchunks, long long slots, long long min_chunks) {
+  if (nchunks <= 0) return 0;
+  long long smax = std::max(1LL, nchunks / std::max(1LL, min_chunks));
+  smax = std::min(smax, 4096LL);
+  long long best = 1;
+  double best_eff = -1.0;
+  for (long long s = 1; s <= smax; ++s) {
+    long long ctas = tiles * s;
+    long long waves = (ctas + slots - 1) / slots;
+    double eff = (double)ctas / (double)(waves * slots);
+    if (eff >= 0.9) return (int)s;
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = s;
+    }
+  }
+  return (int)best;
+}
+
+static int g_split_override = 0;   // testing/autotuning hook, 0 = automatic
+
+fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
+  memset(&pl, 0, sizeof(pl));
+  if (T < 4 || T > 65536 || (T & (T - 1)) != 0) return FCFS_EUNSUPPORTED;
+  if (K < 1 || K > 4096) return FCFS_EUNSUPPORTED;
+  if (V < 0 || V >= (1LL << 31)) return FCFS_EINVAL;
+  if (prec != FCFS_PREC_FP32 && prec != FCFS_PREC_SPLIT_F16) return FCFS_EINVAL;
+  pl.V = V;
+  pl.T = T;
+  pl.K = K;
+  pl.prec = prec;
+  pl.logT = ceil_log2(T);
+  pl.full = T <= kFullTableMaxT ? 1 : 0;
+  pl.fixq = min(30, 62 - ceil_log2(std::max<long long>(V, 1)) - pl.logT);
+  pl.M2 = 2 * K;
+  const bool tc = prec == FCFS_PREC_SPLIT_F16;
+  if (tc) {
+    pl.bm = 128;
+    pl.bn = (pl.full && pl.M2 > 128) ? 256 : 128;
+    pl.chunk = 64;
+  } else {
+    pl.bm = pl.bn = 128;
+    pl.chunk = 32;
+  }
+  pl.tiles_m = (pl.M2 + pl.bm - 1) / pl.bm;
+  pl.tiles_n = (pl.M2 + pl.bn - 1) / pl.bn;
+  const long long nchunks = (V + pl.chunk - 1) / pl.chunk;
+  const long long slots = (long long)sm_count() * (tc ? 1 : 2);
+  int s = g_split_override > 0 ? (int)std::min<long long>(g_split_override, nchunks)
+                               : choose_splits((long long)pl.tiles_m * pl.tiles_n, nchunks, slots, 4);
+  if (s > 0) {
+    const long long per = (nchunks + s - 1) / s;
+    pl.split_len = per * pl.chunk;
+    pl.splits = (int)((V + pl.split_len - 1) / pl.split_len);
+  }
+  size_t o = 0;
+  pl.off_status = o;
+  o = align_up(o + sizeof(Status), kWsAlign);
+  pl.off_tab_tc = o;
+  if (tc) o = align_up(o + tab_tc_bytes(T, pl.full), kWsAlign);
+  pl.off_tab_f32 = o;
+  if (!tc) o = align_up(o + tab_f32_bytes(T, pl.full), kWsAlign);
+  pl.off_tab_fix = o;
+  o = align_up(o + tab_fix_bytes(T, pl.full), kWsAlign);
+  pl.off_axis = o;
+  o = align_up(o + axis_bytes(K), kWsAlign);
+  pl.off_hist = o;
+  o = align_up(o + (size_t)2 * (T + 1) * sizeof(int), kWsAlign);
+  pl.off_part = o;
+  o = align_up(o + (size_t)pl.splits * pl.M2 * pl.M2 * sizeof(float), kWsAlign);
+  pl.total = o;
+  return FCFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tensor maps for the 1-D TMA vertex loads
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+static bool encode_1d(CUtensorMap* map, const void* base, CUtensorMapDataType dt, uint64_t n) {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!g_encode) return false;
+  cuuint64_t dims[1] = {n};
+  cuuint64_t strides[1] = {0};
+  cuuint32_t box[1] = {80};
+  cuuint32_t estr[1] = {1};
+  CUresult r = g_encode(map, dt, 1, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool make_vertex_maps(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, VertexMaps& mp) {
+  return encode_1d(&mp.x, x, CU_TENSOR_MAP_DATA_TYPE_INT32, (uint64_t)V) &&
+         encode_1d(&mp.y, y, CU_TENSOR_MAP_DATA_TYPE_INT32, (uint64_t)V) &&
+         encode_1d(&mp.s, s, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)V);
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+fcfs_status check_ws(const Plan& pl, void* ws, size_t ws_bytes) {
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) % kWsAlign) != 0 || ws_bytes < pl.total) return FCFS_EWORKSPACE;
+  return FCFS_OK;
+}
+
+#define FCFS_CU(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) {                            \
+      if (getenv("FCFS_LOG"))                           \
+        fprintf(stderr, "fcfs: %s: %s\n", #call, cudaGetErrorString(e_)); \
+      return FCFS_ECUDA;                                \
+    }                                                   \
+  } while (0)
+
+fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, int32_t T, int32_t K,
+                         int32_t prec, uint32_t flags, float* F, int64_t* area, void* ws, size_t ws_bytes,
+                         cudaStream_t st) {
+  if (!F || !area) return FCFS_EINVAL;
+  if (V > 0 && (!x || !y || !s || !aligned16(x) || !aligned16(y) || !aligned16(s))) return FCFS_EINVAL;
+  if (flags & ~(uint32_t)FCFS_FLAG_VALIDATE) return FCFS_EINVAL;
+  Plan pl;
+  fcfs_status r = make_plan(V, T, K, prec, pl);
+  if (r != FCFS_OK) return r;
+  if ((r = check_ws(pl, ws, ws_bytes)) != FCFS_OK) return r;
+  const bool validate = (flags & FCFS_FLAG_VALIDATE) != 0;
+  VertexMaps mp;
+  if (prec == FCFS_PREC_SPLIT_F16 && V > 0 && !make_vertex_maps(x, y, s, V, mp)) return FCFS_ECUDA;
+  FCFS_CU(launch_prep(pl, ws, validate, st));
+  FCFS_CU(launch_axis(pl, x, y, s, ws, validate, st));
+  if (prec == FCFS_PREC_SPLIT_F16)
+    FCFS_CU(launch_gemm_tc(pl, mp, ws, st));
+  else
+    FCFS_CU(launch_gemm_simt(pl, x, y, s, ws, st));
+  FCFS_CU(launch_reduce(pl, ws, F, area, validate, st));
+  return FCFS_OK;
+}
+
+}  // namespace fcfs
+
+using namespace fcfs;
+
+extern "C" {
+
+int fcfs_version(void) { return 100; }
+
+const char* fcfs_status_string(fcfs_status st) {
+  switch (st) {
+    case FCFS_OK: return "ok";
+    case FCFS_EINVAL: return "invalid argument";
+    case FCFS_EINVAL_DATA: return "invalid vertex data";
+    case FCFS_EWORKSPACE: return "workspace missing, misaligned or too small";
+    case FCFS_ECUDA: return "CUDA error";
+    case FCFS_ETIMEOUT: return "device wait timed out";
+    case FCFS_EUNSUPPORTED: return "unsupported size or precision";
+  }
+  return "unknown status";
+}
+
+uint64_t fcfs_launch_count(void) { return g_launches.load(); }
+
+size_t fcfs_workspace_size(int64_t V, int32_t T, int32_t K, int32_t prec) {
+  Plan pl;
+  if (make_plan(V, T, K, prec, pl) != FCFS_OK) return 0;
+  return pl.total;
+}
+
+fcfs_status fcfs_forward(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, int32_t T, int32_t K,
+                         int32_t prec, uint32_t flags, float* F_out, int64_t* area_out, void* workspace,
+                         size_t ws_bytes, void* stream) {
+  return forward_impl(x, y, s, V, T, K, prec, flags, F_out, area_out, workspace, ws_bytes,
+                      static_cast<cudaStream_t>(stream));
+}
+
+fcfs_status fcfs_get_status(const void* workspace, void* stream) {
+  if (!workspace) return FCFS_EWORKSPACE;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return FCFS_ECUDA;
+  Status h{0, 0};
+  if (cudaMemcpy(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return FCFS_ECUDA;
+  return static_cast<fcfs_status>(h.code);
+}
+
+// Test hook: force the number of vertex splits (0 restores the automatic choice).
+void fcfs_debug_set_splits(int32_t s) { g_split_override = s; }
+
+}  // extern "C"

@@ -1,0 +1,238 @@
+// Shared definitions of the FCFS CUDA library: status codes, the workspace
+// plan, sincos table access and the inline-PTX wrappers (mbarrier, TMA bulk
+// copies, tcgen05/TMEM) used by the sm_103a kernels.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fcfs.h"
+
+namespace fcfs {
+
+// ---------------------------------------------------------------------------
+// Workspace plan (host and device agree on every offset)
+// ---------------------------------------------------------------------------
+constexpr int kFullTableMaxT = 8192;   // full-period tables up to this T, quarter-wave above
+constexpr int kWsAlign = 256;
+
+struct Plan {
+  int64_t V;
+  int32_t T, K, prec;
+  int32_t logT;
+  int32_t full;        // 1: full-period tables, 0: quarter-wave tables
+  int32_t fixq;        // fixed-point scale 2^fixq of the axis-line table
+  int32_t M2;          // 2K: rows (and columns) of the quarter-plane product
+  int32_t bm, bn;      // GEMM tile
+  int32_t tiles_m, tiles_n;
+  int32_t splits;      // vertex splits (split-K)
+  int32_t chunk;       // vertices per pipeline chunk
+  int64_t split_len;   // vertices per split, a multiple of chunk
+  size_t off_status, off_tab_tc, off_tab_f32, off_tab_fix, off_axis, off_hist, off_part, total;
+};
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Table sizes in bytes
+__host__ __device__ inline size_t tab_tc_bytes(int T, int full) {
+  return full ? (size_t)T * 8 : align_up((size_t)(T / 4 + 1) * 4, 16);
+}
+__host__ __device__ inline size_t tab_f32_bytes(int T, int full) {
+  return full ? (size_t)T * 8 : align_up((size_t)(T / 4 + 1) * 4, 16);
+}
+__host__ __device__ inline size_t tab_fix_bytes(int T, int full) {
+  return full ? (size_t)T * 8 : align_up((size_t)(T / 4 + 1) * 4, 16);
+}
+
+// Axis accumulators: int64 acc[4][K] then the int64 area
+//   acc[0][k-1] = sum s y cos(2 pi k x / T) 2^q     acc[1] = sum s y sin(...) 2^q
+//   acc[2][l-1] = sum s x cos(2 pi l y / T) 2^q     acc[3] = sum s x sin(...) 2^q
+__host__ __device__ inline size_t axis_bytes(int K) { return align_up((size_t)(4 * K + 1) * 8, 256); }
+
+// Device status word (first 4 bytes of the workspace)
+struct Status {
+  unsigned int code;
+  unsigned int detail;
+};
+
+__device__ inline void set_status(Status* st, unsigned int code, unsigned int detail) {
+  if (atomicCAS(&st->code, 0u, code) == 0u) st->detail = detail;
+}
+
+// ---------------------------------------------------------------------------
+// Inline PTX: shared memory, mbarrier, TMA, tcgen05
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after ~kWaitCycles SM cycles (about a second), records
+// FCFS_ETIMEOUT with the call site and returns false.
+constexpr long long kWaitCycles = 2000000000LL;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, Status* st, unsigned site) {
+  if (mbar_try_wait(bar, parity)) return true;
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) {
+      set_status(st, FCFS_ETIMEOUT, site);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 1-D tiled TMA load of `box` elements starting at element `coord`.
+__device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* map, int32_t coord, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2}], [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(coord), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Plain bulk copy global -> shared (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// tcgen05 / TMEM
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16, one CTA.
+__device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on `bar` once every tcgen05 op issued so far by this thread has completed.
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 32 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (sm_100 family): K-major operand, 128-byte
+// swizzle, 8-row core-matrix groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);         // start address
+  d |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                           // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                           // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: A = B = FP16, D = FP32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ---------------------------------------------------------------------------
+// Sincos tables.  Phase index p = (k * a) mod T is exact in integers; a table
+// entry holds cos and sin of 2 pi p / T.  Full tables have T entries; quarter-
+// wave tables hold cos(2 pi r / T) for r in [0, T/4] and rebuild both values by
+// the quadrant symmetries.
+// ---------------------------------------------------------------------------
+struct Quad {
+  uint32_t i1, i2;   // table indices of |cos| and |sin|
+  uint32_t cneg, sneg;
+};
+__device__ __forceinline__ Quad quad_split(uint32_t p, uint32_t logQ) {
+  const uint32_t Q = 1u << logQ;
+  const uint32_t q = p >> logQ, r = p & (Q - 1u);
+  Quad o;
+  const bool odd = q & 1u;
+  o.i1 = odd ? Q - r : r;
+  o.i2 = odd ? r : Q - r;
+  o.cneg = ((q + 1u) >> 1) & 1u;   // cos < 0 in quadrants 1, 2
+  o.sneg = q >> 1;                  // sin < 0 in quadrants 2, 3
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch wrappers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+struct VertexMaps {
+  CUtensorMap x, y, s;
+};
+
+cudaError_t launch_prep(const Plan& pl, void* ws, bool validate, cudaStream_t st);
+cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, const int8_t* s, void* ws,
+                        bool validate, cudaStream_t st);
+cudaError_t launch_reduce(const Plan& pl, void* ws, float* F, int64_t* area, bool validate, cudaStream_t st);
+cudaError_t launch_gemm_simt(const Plan& pl, const int32_t* x, const int32_t* y, const int8_t* s, void* ws,
+                             cudaStream_t st);
+cudaError_t launch_gemm_tc(const Plan& pl, const VertexMaps& maps, void* ws, cudaStream_t st);
+void count_launch(int n);
+
+}  // namespace fcfs

@@ -1,0 +1,299 @@
+// Table fill, exact area and axis lines, and the FP64 split-K reduction with
+// the quarter-plane butterfly and the Prop. CFT scale factors.
+#include <math_constants.h>
+
+#include "fcfs_common.cuh"
+
+namespace fcfs {
+
+// ---------------------------------------------------------------------------
+// Prep: zero the status word and the integer accumulators, build the tables.
+//
+// Base values are C[r] = cos(2 pi r / T), r in [0, T/4], from the FP64 cospi
+// (correctly reduced because 2r/T is exact for a power-of-two T).  Every other
+// entry is an exact sign/swap of a base value, so the tables keep the symmetries
+// cos(th + pi) = -cos(th) etc. bit for bit.
+//  - TC table (tensor path): FP16 hi = rn(c), lo = rn(c - hi) for cos and sin.
+//    Full: uint2 {cos_hi | sin_hi << 16, cos_lo | sin_lo << 16} per phase.
+//    Quarter: uint32 {hi | lo << 16} of C[r].
+//  - F32 table (plain path): float2 {cos, sin} (full) or float C[r] (quarter).
+//  - Fixed table (axis lines): int32 round(c * 2^q), int2 (full) or int (quarter).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double base_cos(int r, int T) { return cospi(2.0 * (double)r / (double)T); }
+
+__device__ __forceinline__ uint32_t hilo_bits(double c) {
+  __half h = __double2half(c);
+  __half l = __double2half(c - (double)__half2float(h));
+  return (uint32_t)__half_as_ushort(h) | ((uint32_t)__half_as_ushort(l) << 16);
+}
+
+__global__ void prep_kernel(Plan pl, uint8_t* ws, int validate) {
+  const int T = pl.T;
+  const int logQ = pl.logT - 2;
+  const int Q = T / 4;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  if (gid == 0) {
+    Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
+    st->code = 0;
+    st->detail = 0;
+  }
+  long long* acc = reinterpret_cast<long long*>(ws + pl.off_axis);
+  for (long long i = gid; i < 4LL * pl.K + 1; i += gsz) acc[i] = 0;
+  if (validate) {
+    int* hist = reinterpret_cast<int*>(ws + pl.off_hist);
+    for (long long i = gid; i < 2LL * (T + 1); i += gsz) hist[i] = 0;
+  }
+  const double scale = ldexp(1.0, pl.fixq);
+  const bool tc = pl.prec == FCFS_PREC_SPLIT_F16;
+  if (pl.full) {
+    for (long long p = gid; p < T; p += gsz) {
+      Quad qd = quad_split((uint32_t)p, (uint32_t)logQ);
+      double c = base_cos((int)qd.i1, T), s = base_cos((int)qd.i2, T);
+      if (qd.cneg) c = -c;
+      if (qd.sneg) s = -s;
+      if (tc) {
+        uint32_t hc = hilo_bits(c), hs = hilo_bits(s);
+        reinterpret_cast<uint2*>(ws + pl.off_tab_tc)[p] =
+            make_uint2((hc & 0xFFFFu) | (hs << 16), (hc >> 16) | (hs & 0xFFFF0000u));
+      } else {
+        reinterpret_cast<float2*>(ws + pl.off_tab_f32)[p] = make_float2((float)c, (float)s);
+      }
+      reinterpret_cast<int2*>(ws + pl.off_tab_fix)[p] =
+          make_int2((int)llrint(c * scale), (int)llrint(s * scale));
+    }
+  } else {
+    for (long long r = gid; r <= Q; r += gsz) {
+      double c = base_cos((int)r, T);
+      if (tc)
+        reinterpret_cast<uint32_t*>(ws + pl.off_tab_tc)[r] = hilo_bits(c);
+      else
+        reinterpret_cast<float*>(ws + pl.off_tab_f32)[r] = (float)c;
+      reinterpret_cast<int*>(ws + pl.off_tab_fix)[r] = (int)llrint(c * scale);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Area and axis lines, exact in 64-bit integers (Eqs. Fdc, Fk0, F0l; Steps 1-3).
+//
+//   area        = sum_v s_v x_v y_v                      (int64, exact)
+//   Sx(k)       = sum_v s_v y_v exp(-j 2 pi k x_v / T)   (F(k,0) = j T/(2 pi k) Sx(k))
+//   Sy(l)       = sum_v s_v x_v exp(-j 2 pi l y_v / T)   (F(0,l) = j T/(2 pi l) Sy(l))
+//
+// The twiddles are fixed-point integers round(cos * 2^q); products and sums
+// are exact int64, so the only error is the 2^-(q+1) rounding of each twiddle.
+// q is chosen on the host so that V * T * 2^q < 2^62: the final sums then fit,
+// and modular int64 addition makes the order of the partial sums irrelevant
+// (the result is bit-identical run to run).  Balance is not assumed.
+// Block: 256 threads = 256 consecutive k; blockIdx.x picks a vertex range.
+// ---------------------------------------------------------------------------
+constexpr int kAxisThreads = 256;
+constexpr int kAxisStage = 256;
+
+template <bool FULL>
+__device__ __forceinline__ int2 fix_lookup(const void* tab, uint32_t p, uint32_t logQ) {
+  if (FULL) return reinterpret_cast<const int2*>(tab)[p];
+  const int* t = reinterpret_cast<const int*>(tab);
+  Quad qd = quad_split(p, logQ);
+  int c = t[qd.i1], s = t[qd.i2];
+  return make_int2(qd.cneg ? -c : c, qd.sneg ? -s : s);
+}
+
+template <bool FULL>
+__global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32_t* __restrict__ x,
+                                                          const int32_t* __restrict__ y,
+                                                          const int8_t* __restrict__ s, uint8_t* ws, int vper,
+                                                          int validate) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  const size_t tb = tab_fix_bytes(pl.T, FULL);
+  int* sx = reinterpret_cast<int*>(sm + tb);
+  int* sy = sx + kAxisStage;
+  int* ssg = sy + kAxisStage;
+  {
+    const int4* src = reinterpret_cast<const int4*>(ws + pl.off_tab_fix);
+    int4* dst = reinterpret_cast<int4*>(sm);
+    for (int i = threadIdx.x; i < (int)(tb / 16); i += blockDim.x) dst[i] = src[i];
+  }
+  const int T = pl.T;
+  const uint32_t mask = (uint32_t)T - 1u;
+  const uint32_t logQ = (uint32_t)pl.logT - 2u;
+  const int k = blockIdx.y * kAxisThreads + threadIdx.x + 1;
+  const long long v0 = (long long)blockIdx.x * vper;
+  const long long v1 = min((long long)pl.V, v0 + vper);
+  long long a0 = 0, a1 = 0, a2 = 0, a3 = 0, area = 0;
+  Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
+  int* hist = reinterpret_cast<int*>(ws + pl.off_hist);
+  for (long long b = v0; b < v1; b += kAxisStage) {
+    const int n = (int)min((long long)kAxisStage, v1 - b);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int xv = x[b + i], yv = y[b + i], sv = s[b + i];
+      sx[i] = xv;
+      sy[i] = yv;
+      ssg[i] = sv;
+      if (blockIdx.y == 0) {
+        area += (long long)sv * xv * (long long)yv;
+        if (validate) {
+          const bool ok = xv >= 0 && xv <= T && yv >= 0 && yv <= T && (sv == 1 || sv == -1);
+          if (!ok) {
+            set_status(st, FCFS_EINVAL_DATA, (unsigned)(b + i));
+          } else {
+            atomicAdd(&hist[xv], sv);
+            atomicAdd(&hist[T + 1 + yv], sv);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (k <= pl.K) {
+#pragma unroll 4
+      for (int i = 0; i < n; ++i) {
+        const int xv = sx[i], yv = sy[i], sv = ssg[i];
+        const int2 tx = fix_lookup<FULL>(sm, ((uint32_t)k * (uint32_t)xv) & mask, logQ);
+        const int2 ty = fix_lookup<FULL>(sm, ((uint32_t)k * (uint32_t)yv) & mask, logQ);
+        const int wy = sv * yv, wx = sv * xv;
+        a0 += (long long)tx.x * wy;
+        a1 += (long long)tx.y * wy;
+        a2 += (long long)ty.x * wx;
+        a3 += (long long)ty.y * wx;
+      }
+    }
+  }
+  long long* acc = reinterpret_cast<long long*>(ws + pl.off_axis);
+  if (k <= pl.K) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[k - 1]), (unsigned long long)a0);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[pl.K + k - 1]), (unsigned long long)a1);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[2 * pl.K + k - 1]), (unsigned long long)a2);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[3 * pl.K + k - 1]), (unsigned long long)a3);
+  }
+  if (blockIdx.y == 0) {
+    for (int o = 16; o > 0; o >>= 1) area += __shfl_xor_sync(0xffffffffu, area, o);
+    if ((threadIdx.x & 31) == 0 && area != 0)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&acc[4 * pl.K]), (unsigned long long)area);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reduce + epilogue.  One thread per (k, l) in [0, K]^2.
+//  - (0,0): the exact area (and F(0,0) = its nearest float).
+//  - (k,0), (0,l): axis lines from the integer sums, F(k,0) = (T / 2 pi k)(S + jC)
+//    where sum s y exp(-j w k x) = C - jS; F(-k,0) = conj F(k,0).
+//  - k,l >= 1: FP64 sum over splits, in split order, of the FP32 quarter-plane
+//    partials CC, CS, SC, SS (rows 2(k-1)+{cos,sin}, columns 2(l-1)+{cos,sin});
+//    G(k,l) = CC - SS - j(SC + CS), G(k,-l) = CC + SS - j(SC - CS);
+//    F(k,l) = -T^2/(4 pi^2 k l) G(k,l), F(k,-l) = +T^2/(4 pi^2 k l) G(k,-l) (Eq. Fkl);
+//    F(-k,-l) = conj F(k,l), F(-k,l) = conj F(k,-l) (real image).
+// ---------------------------------------------------------------------------
+__global__ void reduce_kernel(Plan pl, const uint8_t* ws, float2* __restrict__ F, long long* __restrict__ area_out,
+                              int validate) {
+  const int K = pl.K;
+  const long long n1 = (long long)K + 1;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long W = 2LL * K + 1;
+  if (validate && blockIdx.x == 0) {
+    const int* hist = reinterpret_cast<const int*>(ws + pl.off_hist);
+    Status* st = reinterpret_cast<Status*>(const_cast<uint8_t*>(ws) + pl.off_status);
+    for (int i = threadIdx.x; i < 2 * (pl.T + 1); i += blockDim.x)
+      if (hist[i] != 0) set_status(st, FCFS_EINVAL_DATA, 0x80000000u | (unsigned)i);
+  }
+  if (idx >= n1 * n1) return;
+  const int k = (int)(idx / n1), l = (int)(idx % n1);
+  const double T = (double)pl.T;
+  const long long* acc = reinterpret_cast<const long long*>(ws + pl.off_axis);
+  const double inv = ldexp(1.0, -pl.fixq);
+  if (k == 0 && l == 0) {
+    const long long a = acc[4 * K];
+    area_out[0] = a;
+    F[K * W + K] = make_float2((float)a, 0.f);
+    return;
+  }
+  if (l == 0 || k == 0) {
+    const int f = k + l;   // the nonzero one
+    const int base = (l == 0) ? 0 : 2 * K;
+    const double C = (double)acc[base + f - 1] * inv;
+    const double S = (double)acc[base + K + f - 1] * inv;
+    const double g = T / (2.0 * CUDART_PI * f);
+    const float re = (float)(g * S), im = (float)(g * C);
+    if (l == 0) {
+      F[(K + k) * W + K] = make_float2(re, im);
+      F[(K - k) * W + K] = make_float2(re, -im);
+    } else {
+      F[K * W + K + l] = make_float2(re, im);
+      F[K * W + K - l] = make_float2(re, -im);
+    }
+    return;
+  }
+  const int M2 = pl.M2;
+  const size_t plane = (size_t)M2 * M2;
+  const float* P = reinterpret_cast<const float*>(ws + pl.off_part);
+  const size_t o0 = (size_t)(2 * (k - 1)) * M2 + 2 * (l - 1);
+  double cc = 0, cs = 0, sc = 0, ss = 0;
+  for (int sp = 0; sp < pl.splits; ++sp) {
+    const float2 r0 = *reinterpret_cast<const float2*>(P + sp * plane + o0);
+    const float2 r1 = *reinterpret_cast<const float2*>(P + sp * plane + o0 + M2);
+    cc += r0.x;
+    cs += r0.y;
+    sc += r1.x;
+    ss += r1.y;
+  }
+  const double a = T * T / (4.0 * CUDART_PI * CUDART_PI * (double)k * (double)l);
+  // F(k,l) = -a G(k,l)
+  const double pr = -a * (cc - ss), pi = a * (sc + cs);
+  // F(k,-l) = +a G(k,-l)
+  const double mr = a * (cc + ss), mi = -a * (sc - cs);
+  F[(K + k) * W + (K + l)] = make_float2((float)pr, (float)pi);
+  F[(K - k) * W + (K - l)] = make_float2((float)pr, (float)-pi);
+  F[(K + k) * W + (K - l)] = make_float2((float)mr, (float)mi);
+  F[(K - k) * W + (K + l)] = make_float2((float)mr, (float)-mi);
+}
+
+// ---------------------------------------------------------------------------
+// Host launch wrappers
+// ---------------------------------------------------------------------------
+cudaError_t launch_prep(const Plan& pl, void* ws, bool validate, cudaStream_t st) {
+  long long work = pl.full ? pl.T : pl.T / 4 + 1;
+  work = max(work, 4LL * pl.K + 1);
+  if (validate) work = max(work, 2LL * (pl.T + 1));
+  int blocks = (int)min((work + 255) / 256, 1024LL);
+  prep_kernel<<<blocks, 256, 0, st>>>(pl, static_cast<uint8_t*>(ws), validate ? 1 : 0);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, const int8_t* s, void* ws,
+                        bool validate, cudaStream_t st) {
+  if (pl.V == 0) return cudaSuccess;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int kblocks = (pl.K + kAxisThreads - 1) / kAxisThreads;
+  const long long target = max(1LL, (long long)(2 * sms) / kblocks);
+  long long vper = (pl.V + target - 1) / target;
+  vper = max(64LL, (vper + 63) / 64 * 64);
+  const int vblocks = (int)((pl.V + vper - 1) / vper);
+  const size_t smem = tab_fix_bytes(pl.T, pl.full) + 3 * kAxisStage * sizeof(int);
+  dim3 grid(vblocks, kblocks);
+  if (pl.full) {
+    cudaFuncSetAttribute(axis_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    axis_kernel<true><<<grid, kAxisThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws), (int)vper,
+                                                        validate ? 1 : 0);
+  } else {
+    cudaFuncSetAttribute(axis_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    axis_kernel<false><<<grid, kAxisThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws), (int)vper,
+                                                         validate ? 1 : 0);
+  }
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const Plan& pl, void* ws, float* F, int64_t* area, bool validate, cudaStream_t st) {
+  const long long n = (long long)(pl.K + 1) * (pl.K + 1);
+  const int blocks = (int)((n + 255) / 256);
+  reduce_kernel<<<blocks, 256, 0, st>>>(pl, static_cast<const uint8_t*>(ws), reinterpret_cast<float2*>(F),
+                                        reinterpret_cast<long long*>(area), validate ? 1 : 0);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace fcfs

@@ -1,0 +1,134 @@
+"""Torch-facing binding of the FCFS library.
+
+Every function marshals device tensors into the C ABI of include/fcfs.h; the
+arithmetic runs in the library's CUDA kernels.  PyTorch provides the device
+memory (outputs and workspaces) and the current stream.
+"""
+import torch
+
+from . import _lib
+from ._lib import FCFSError, PREC, FLAG_VALIDATE
+
+__all__ = ["forward", "adjoint", "edge_chain", "batch", "workspace_size", "get_status",
+           "launch_count", "FCFSError"]
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _check_vertices(x, y, s):
+    for name, t, dt in (("x", x, torch.int32), ("y", y, torch.int32), ("s", s, torch.int8)):
+        if not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if t.dtype != dt:
+            raise ValueError("%s must be %s" % (name, dt))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    if not (x.shape == y.shape == s.shape) or x.dim() != 1:
+        raise ValueError("x, y, s must be 1-D of equal length")
+
+
+def _prec(prec):
+    return PREC[prec] if isinstance(prec, str) else int(prec)
+
+
+def workspace_size(V, T, K, prec="split_f16"):
+    return int(_lib.load().fcfs_workspace_size(int(V), int(T), int(K), _prec(prec)))
+
+
+def alloc_workspace(nbytes, device):
+    # torch allocations are 512-byte aligned; the library asks for 256
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def forward(x, y, s, T, K, prec="split_f16", validate=False, out=None, area_out=None, workspace=None,
+            stream=None):
+    """F(k, l), |k|,|l| <= K, of one clip: complex64 (2K+1, 2K+1) and the int64 area."""
+    _check_vertices(x, y, s)
+    lib = _lib.load()
+    dev = x.device
+    W = 2 * int(K) + 1
+    if out is None:
+        out = torch.empty((W, W), dtype=torch.complex64, device=dev)
+    if area_out is None:
+        area_out = torch.empty((1,), dtype=torch.int64, device=dev)
+    need = workspace_size(x.numel(), T, K, prec)
+    if workspace is None:
+        workspace = alloc_workspace(need, dev)
+    code = lib.fcfs_forward(_ptr(x), _ptr(y), _ptr(s), x.numel(), int(T), int(K), _prec(prec),
+                            FLAG_VALIDATE if validate else 0, _ptr(out), _ptr(area_out),
+                            _ptr(workspace), workspace.numel(), _stream(stream))
+    _lib.check("fcfs_forward", code)
+    return out, area_out
+
+
+def adjoint(x, y, s, T, K, dF, prec="fp32", gx=None, gy=None, workspace=None, stream=None):
+    """Corner derivatives (gx, gy) of a real loss with cotangent dF (complex64 block)."""
+    _check_vertices(x, y, s)
+    if dF.dtype != torch.complex64 or not dF.is_contiguous() or dF.shape != (2 * K + 1, 2 * K + 1):
+        raise ValueError("dF must be a contiguous complex64 (2K+1, 2K+1) tensor")
+    lib = _lib.load()
+    dev = x.device
+    V = x.numel()
+    gx = torch.empty(V, dtype=torch.float32, device=dev) if gx is None else gx
+    gy = torch.empty(V, dtype=torch.float32, device=dev) if gy is None else gy
+    need = int(lib.fcfs_adjoint_workspace_size(V, int(T), int(K), _prec(prec)))
+    if workspace is None:
+        workspace = alloc_workspace(need, dev)
+    code = lib.fcfs_adjoint(_ptr(x), _ptr(y), _ptr(s), V, int(T), int(K), _prec(prec), _ptr(dF),
+                            _ptr(gx), _ptr(gy), _ptr(workspace), workspace.numel(), _stream(stream))
+    _lib.check("fcfs_adjoint", code)
+    return gx, gy
+
+
+def edge_chain(gx, gy, ev0, ev1, eaxis, out=None, stream=None):
+    """Per-edge derivative: a vertical edge moves both corners in x, a horizontal one in y."""
+    lib = _lib.load()
+    E = ev0.numel()
+    out = torch.empty(E, dtype=torch.float32, device=gx.device) if out is None else out
+    code = lib.fcfs_edge_chain(_ptr(gx), _ptr(gy), _ptr(ev0), _ptr(ev1), _ptr(eaxis), E, _ptr(out),
+                               _stream(stream))
+    _lib.check("fcfs_edge_chain", code)
+    return out
+
+
+def batch(x, y, s, offsets, T, K, prec="split_f16", validate=False, out=None, area_out=None,
+          workspace=None, stream=None):
+    """Blocks of n clips (offsets: int64 CUDA tensor [n+1]): (n, 2K+1, 2K+1) and (n,)."""
+    _check_vertices(x, y, s)
+    lib = _lib.load()
+    dev = x.device
+    n = offsets.numel() - 1
+    W = 2 * int(K) + 1
+    out = torch.empty((n, W, W), dtype=torch.complex64, device=dev) if out is None else out
+    area_out = torch.empty((n,), dtype=torch.int64, device=dev) if area_out is None else area_out
+    need = int(lib.fcfs_batch_workspace_size(x.numel(), n, int(T), int(K), _prec(prec)))
+    if workspace is None:
+        workspace = alloc_workspace(need, dev)
+    code = lib.fcfs_batch(_ptr(x), _ptr(y), _ptr(s), _ptr(offsets), n, x.numel(), int(T), int(K),
+                          _prec(prec), FLAG_VALIDATE if validate else 0, _ptr(out), _ptr(area_out),
+                          _ptr(workspace), workspace.numel(), _stream(stream))
+    _lib.check("fcfs_batch", code)
+    return out, area_out
+
+
+def get_status(workspace, stream=None):
+    """Synchronise and return the device status name of the last call on ``workspace``."""
+    code = _lib.load().fcfs_get_status(_ptr(workspace), _stream(stream))
+    return _lib.STATUS.get(code, str(code))
+
+
+def launch_count():
+    return int(_lib.load().fcfs_launch_count())
+
+
+def set_splits(n):
+    """Force the number of vertex splits (0: automatic); a test hook."""
+    _lib.load().fcfs_debug_set_splits(int(n))
