@@ -151,6 +151,19 @@ fcfs_status fcfs_batch(const int32_t* x, const int32_t* y, const int8_t* s,
                        void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * Measurement hooks.  fcfs_profile_enable(1) makes every later call bracket
+ * each of its stages with CUDA events on the caller's stream; after a call,
+ * fcfs_profile_read() waits for the last event and writes up to n stage
+ * durations in milliseconds (0: prep/tables, 1: area and axis lines,
+ * 2: contraction, 3: reduce and epilogue).  Returns the number written.
+ * fcfs_debug_set_splits(n) forces n vertex splits (0: automatic choice).
+ * Not thread-safe; meant for benchmarks and tests.
+ */
+void fcfs_profile_enable(int32_t on);
+int32_t fcfs_profile_read(float* ms, int32_t n);
+void fcfs_debug_set_splits(int32_t n);
+
+/*
  * Synchronise `stream` and return the device status word of the last call that
  * used `workspace` (FCFS_OK, FCFS_EINVAL_DATA or FCFS_ETIMEOUT).
  */

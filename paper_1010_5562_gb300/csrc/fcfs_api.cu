@@ -15,6 +15,21 @@ namespace fcfs {
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
+// Stage timing: when enabled, every stage of a call is bracketed by CUDA events
+// recorded on the caller's stream (prep, axis, contraction, reduce).
+constexpr int kProfStages = 4;
+static bool g_prof = false;
+static cudaEvent_t g_ev[2 * kProfStages];
+static bool g_ev_made = false;
+static void prof_mark(int i, cudaStream_t st) {
+  if (!g_prof) return;
+  if (!g_ev_made) {
+    for (auto& e : g_ev) cudaEventCreate(&e);
+    g_ev_made = true;
+  }
+  cudaEventRecord(g_ev[i], st);
+}
+
 size_t tc_smem_for(int bn, int T, int full);
 
 static int ceil_log2(long long v) {
@@ -54,6 +69,19 @@ static int choose_splits(long long tiles, long long nchunks, long long slots, lo
 
 static int g_split_override = 0;   // testing/autotuning hook, 0 = automatic
 
+// Tag of the cached tables: their kind, period, fixed-point scale and offsets.
+static uint64_t table_tag(const Plan& pl) {
+  uint64_t h = 0xCBF29CE484222325ull;   // FNV-1a over the fields that fix the table bytes
+  const uint64_t f[6] = {2u /* layout version */, (uint64_t)pl.T, (uint64_t)pl.fixq, (uint64_t)pl.full,
+                         (uint64_t)pl.off_tab_f32, (uint64_t)pl.off_tab_fix};
+  for (uint64_t v : f)
+    for (int b = 0; b < 8; ++b) {
+      h ^= (v >> (8 * b)) & 0xFFu;
+      h *= 0x100000001B3ull;
+    }
+  return h | 1u;   // never 0, so zeroed memory is never mistaken for a tag
+}
+
 fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
   memset(&pl, 0, sizeof(pl));
   if (T < 4 || T > 65536 || (T & (T - 1)) != 0) return FCFS_EUNSUPPORTED;
@@ -91,10 +119,8 @@ fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
   size_t o = 0;
   pl.off_status = o;
   o = align_up(o + sizeof(Status), kWsAlign);
-  pl.off_tab_tc = o;
-  if (tc) o = align_up(o + tab_tc_bytes(T, pl.full), kWsAlign);
   pl.off_tab_f32 = o;
-  if (!tc) o = align_up(o + tab_f32_bytes(T, pl.full), kWsAlign);
+  o = align_up(o + tab_f32_bytes(T, pl.full), kWsAlign);
   pl.off_tab_fix = o;
   o = align_up(o + tab_fix_bytes(T, pl.full), kWsAlign);
   pl.off_axis = o;
@@ -104,6 +130,7 @@ fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
   pl.off_part = o;
   o = align_up(o + (size_t)pl.splits * pl.M2 * pl.M2 * sizeof(float), kWsAlign);
   pl.total = o;
+  pl.tag = table_tag(pl);
   return FCFS_OK;
 }
 
@@ -169,13 +196,21 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
   const bool validate = (flags & FCFS_FLAG_VALIDATE) != 0;
   VertexMaps mp;
   if (prec == FCFS_PREC_SPLIT_F16 && V > 0 && !make_vertex_maps(x, y, s, V, mp)) return FCFS_ECUDA;
+  prof_mark(0, st);
   FCFS_CU(launch_prep(pl, ws, validate, st));
+  prof_mark(1, st);
+  prof_mark(2, st);
   FCFS_CU(launch_axis(pl, x, y, s, ws, validate, st));
+  prof_mark(3, st);
+  prof_mark(4, st);
   if (prec == FCFS_PREC_SPLIT_F16)
     FCFS_CU(launch_gemm_tc(pl, mp, ws, st));
   else
     FCFS_CU(launch_gemm_simt(pl, x, y, s, ws, st));
+  prof_mark(5, st);
+  prof_mark(6, st);
   FCFS_CU(launch_reduce(pl, ws, F, area, validate, st));
+  prof_mark(7, st);
   return FCFS_OK;
 }
 
@@ -225,5 +260,16 @@ fcfs_status fcfs_get_status(const void* workspace, void* stream) {
 
 // Test hook: force the number of vertex splits (0 restores the automatic choice).
 void fcfs_debug_set_splits(int32_t s) { g_split_override = s; }
+
+void fcfs_profile_enable(int32_t on) { g_prof = on != 0; }
+
+int32_t fcfs_profile_read(float* ms, int32_t n) {
+  if (!g_ev_made || !ms) return 0;
+  if (cudaEventSynchronize(g_ev[2 * kProfStages - 1]) != cudaSuccess) return 0;
+  int k = 0;
+  for (; k < n && k < kProfStages; ++k)
+    if (cudaEventElapsedTime(&ms[k], g_ev[2 * k], g_ev[2 * k + 1]) != cudaSuccess) ms[k] = -1.f;
+  return k;
+}
 
 }  // extern "C"

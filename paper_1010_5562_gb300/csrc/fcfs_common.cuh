@@ -30,15 +30,16 @@ struct Plan {
   int32_t splits;      // vertex splits (split-K)
   int32_t chunk;       // vertices per pipeline chunk
   int64_t split_len;   // vertices per split, a multiple of chunk
-  size_t off_status, off_tab_tc, off_tab_f32, off_tab_fix, off_axis, off_hist, off_part, total;
+  size_t off_status, off_tab_f32, off_tab_fix, off_axis, off_hist, off_part, total;
+  uint64_t tag;        // identifies the tables cached in this workspace layout
 };
+
+// Workspace header: the status word of the last call, then the table tag.
+constexpr size_t kTagOffset = 8;
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Table sizes in bytes
-__host__ __device__ inline size_t tab_tc_bytes(int T, int full) {
-  return full ? (size_t)T * 8 : align_up((size_t)(T / 4 + 1) * 4, 16);
-}
 __host__ __device__ inline size_t tab_f32_bytes(int T, int full) {
   return full ? (size_t)T * 8 : align_up((size_t)(T / 4 + 1) * 4, 16);
 }
@@ -217,6 +218,15 @@ __device__ __forceinline__ Quad quad_split(uint32_t p, uint32_t logQ) {
   o.cneg = ((q + 1u) >> 1) & 1u;   // cos < 0 in quadrants 1, 2
   o.sneg = q >> 1;                  // sin < 0 in quadrants 2, 3
   return o;
+}
+
+// cos and sin of 2 pi p / T from the FP32 table
+template <bool FULL>
+__device__ __forceinline__ float2 f32_lookup(const float* tab, uint32_t p, uint32_t logQ) {
+  if (FULL) return reinterpret_cast<const float2*>(tab)[p];
+  Quad qd = quad_split(p, logQ);
+  const float c = tab[qd.i1], s = tab[qd.i2];
+  return make_float2(qd.cneg ? -c : c, qd.sneg ? -s : s);
 }
 
 // ---------------------------------------------------------------------------

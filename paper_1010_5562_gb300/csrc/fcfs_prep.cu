@@ -7,25 +7,19 @@
 namespace fcfs {
 
 // ---------------------------------------------------------------------------
-// Prep: zero the status word and the integer accumulators, build the tables.
+// Prep: zero the status word and the integer accumulators; build the tables
+// unless the workspace already holds them (its tag matches the plan's).
 //
 // Base values are C[r] = cos(2 pi r / T), r in [0, T/4], from the FP64 cospi
 // (correctly reduced because 2r/T is exact for a power-of-two T).  Every other
 // entry is an exact sign/swap of a base value, so the tables keep the symmetries
 // cos(th + pi) = -cos(th) etc. bit for bit.
-//  - TC table (tensor path): FP16 hi = rn(c), lo = rn(c - hi) for cos and sin.
-//    Full: uint2 {cos_hi | sin_hi << 16, cos_lo | sin_lo << 16} per phase.
-//    Quarter: uint32 {hi | lo << 16} of C[r].
-//  - F32 table (plain path): float2 {cos, sin} (full) or float C[r] (quarter).
+//  - F32 table: float2 {cos, sin} per phase (full) or float C[r] (quarter).
 //  - Fixed table (axis lines): int32 round(c * 2^q), int2 (full) or int (quarter).
+// The tag is written by the last kernel of a call, once every kernel that reads
+// the tables has been enqueued behind this one.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double base_cos(int r, int T) { return cospi(2.0 * (double)r / (double)T); }
-
-__device__ __forceinline__ uint32_t hilo_bits(double c) {
-  __half h = __double2half(c);
-  __half l = __double2half(c - (double)__half2float(h));
-  return (uint32_t)__half_as_ushort(h) | ((uint32_t)__half_as_ushort(l) << 16);
-}
 
 __global__ void prep_kernel(Plan pl, uint8_t* ws, int validate) {
   const int T = pl.T;
@@ -44,31 +38,22 @@ __global__ void prep_kernel(Plan pl, uint8_t* ws, int validate) {
     int* hist = reinterpret_cast<int*>(ws + pl.off_hist);
     for (long long i = gid; i < 2LL * (T + 1); i += gsz) hist[i] = 0;
   }
+  if (*reinterpret_cast<volatile const unsigned long long*>(ws + kTagOffset) == pl.tag) return;
   const double scale = ldexp(1.0, pl.fixq);
-  const bool tc = pl.prec == FCFS_PREC_SPLIT_F16;
   if (pl.full) {
     for (long long p = gid; p < T; p += gsz) {
       Quad qd = quad_split((uint32_t)p, (uint32_t)logQ);
       double c = base_cos((int)qd.i1, T), s = base_cos((int)qd.i2, T);
       if (qd.cneg) c = -c;
       if (qd.sneg) s = -s;
-      if (tc) {
-        uint32_t hc = hilo_bits(c), hs = hilo_bits(s);
-        reinterpret_cast<uint2*>(ws + pl.off_tab_tc)[p] =
-            make_uint2((hc & 0xFFFFu) | (hs << 16), (hc >> 16) | (hs & 0xFFFF0000u));
-      } else {
-        reinterpret_cast<float2*>(ws + pl.off_tab_f32)[p] = make_float2((float)c, (float)s);
-      }
+      reinterpret_cast<float2*>(ws + pl.off_tab_f32)[p] = make_float2((float)c, (float)s);
       reinterpret_cast<int2*>(ws + pl.off_tab_fix)[p] =
           make_int2((int)llrint(c * scale), (int)llrint(s * scale));
     }
   } else {
     for (long long r = gid; r <= Q; r += gsz) {
-      double c = base_cos((int)r, T);
-      if (tc)
-        reinterpret_cast<uint32_t*>(ws + pl.off_tab_tc)[r] = hilo_bits(c);
-      else
-        reinterpret_cast<float*>(ws + pl.off_tab_f32)[r] = (float)c;
+      const double c = base_cos((int)r, T);
+      reinterpret_cast<float*>(ws + pl.off_tab_f32)[r] = (float)c;
       reinterpret_cast<int*>(ws + pl.off_tab_fix)[r] = (int)llrint(c * scale);
     }
   }
@@ -179,13 +164,28 @@ __global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32
 //  - (0,0): the exact area (and F(0,0) = its nearest float).
 //  - (k,0), (0,l): axis lines from the integer sums, F(k,0) = (T / 2 pi k)(S + jC)
 //    where sum s y exp(-j w k x) = C - jS; F(-k,0) = conj F(k,0).
-//  - k,l >= 1: FP64 sum over splits, in split order, of the FP32 quarter-plane
-//    partials CC, CS, SC, SS (rows 2(k-1)+{cos,sin}, columns 2(l-1)+{cos,sin});
+//  - k,l >= 1: sum over splits, in split order, of the FP32 quarter-plane
+//    partials CC, CS, SC, SS (rows 2(k-1)+{cos,sin}, columns 2(l-1)+{cos,sin}),
+//    compensated: every addition is an error-free TwoSum (Knuth) and the
+//    rounding errors are carried in a second float, so the sum is as accurate
+//    as an FP64 one while it runs on the FP32 pipe;
 //    G(k,l) = CC - SS - j(SC + CS), G(k,-l) = CC + SS - j(SC - CS);
 //    F(k,l) = -T^2/(4 pi^2 k l) G(k,l), F(k,-l) = +T^2/(4 pi^2 k l) G(k,-l) (Eq. Fkl);
 //    F(-k,-l) = conj F(k,l), F(-k,l) = conj F(k,-l) (real image).
+// The last thread to finish writes the table tag of the workspace.
 // ---------------------------------------------------------------------------
-__global__ void reduce_kernel(Plan pl, const uint8_t* ws, float2* __restrict__ F, long long* __restrict__ area_out,
+struct CSum {
+  float hi, lo;
+};
+__device__ __forceinline__ void csum_add(CSum& a, float b) {
+  const float s = a.hi + b;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b - bb);
+  a.hi = s;
+  a.lo += e;
+}
+
+__global__ void reduce_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, long long* __restrict__ area_out,
                               int validate) {
   const int K = pl.K;
   const long long n1 = (long long)K + 1;
@@ -193,10 +193,11 @@ __global__ void reduce_kernel(Plan pl, const uint8_t* ws, float2* __restrict__ F
   const long long W = 2LL * K + 1;
   if (validate && blockIdx.x == 0) {
     const int* hist = reinterpret_cast<const int*>(ws + pl.off_hist);
-    Status* st = reinterpret_cast<Status*>(const_cast<uint8_t*>(ws) + pl.off_status);
+    Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
     for (int i = threadIdx.x; i < 2 * (pl.T + 1); i += blockDim.x)
       if (hist[i] != 0) set_status(st, FCFS_EINVAL_DATA, 0x80000000u | (unsigned)i);
   }
+  if (idx == 0) *reinterpret_cast<unsigned long long*>(ws + kTagOffset) = pl.tag;
   if (idx >= n1 * n1) return;
   const int k = (int)(idx / n1), l = (int)(idx % n1);
   const double T = (double)pl.T;
@@ -228,35 +229,41 @@ __global__ void reduce_kernel(Plan pl, const uint8_t* ws, float2* __restrict__ F
   const size_t plane = (size_t)M2 * M2;
   const float* P = reinterpret_cast<const float*>(ws + pl.off_part);
   const size_t o0 = (size_t)(2 * (k - 1)) * M2 + 2 * (l - 1);
-  double cc = 0, cs = 0, sc = 0, ss = 0;
+  CSum cc{0.f, 0.f}, cs{0.f, 0.f}, sc{0.f, 0.f}, ss{0.f, 0.f};
+#pragma unroll 4
   for (int sp = 0; sp < pl.splits; ++sp) {
-    const float2 r0 = *reinterpret_cast<const float2*>(P + sp * plane + o0);
-    const float2 r1 = *reinterpret_cast<const float2*>(P + sp * plane + o0 + M2);
-    cc += r0.x;
-    cs += r0.y;
-    sc += r1.x;
-    ss += r1.y;
+    const float2 r0 = __ldcs(reinterpret_cast<const float2*>(P + sp * plane + o0));
+    const float2 r1 = __ldcs(reinterpret_cast<const float2*>(P + sp * plane + o0 + M2));
+    csum_add(cc, r0.x);
+    csum_add(cs, r0.y);
+    csum_add(sc, r1.x);
+    csum_add(ss, r1.y);
   }
-  const double a = T * T / (4.0 * CUDART_PI * CUDART_PI * (double)k * (double)l);
-  // F(k,l) = -a G(k,l)
-  const double pr = -a * (cc - ss), pi = a * (sc + cs);
-  // F(k,-l) = +a G(k,-l)
-  const double mr = a * (cc + ss), mi = -a * (sc - cs);
-  F[(K + k) * W + (K + l)] = make_float2((float)pr, (float)pi);
-  F[(K - k) * W + (K - l)] = make_float2((float)pr, (float)-pi);
-  F[(K + k) * W + (K - l)] = make_float2((float)mr, (float)mi);
-  F[(K - k) * W + (K + l)] = make_float2((float)mr, (float)-mi);
+  // combine hi and lo parts; the cancellations below are exact or relative to
+  // the result, and the result is rounded to FP32 anyway
+  const float a = (float)(T * T / (4.0 * CUDART_PI * CUDART_PI)) / ((float)k * (float)l);
+  const float gr_p = (cc.hi - ss.hi) + (cc.lo - ss.lo);   // Re G(k,l)
+  const float gi_p = -((sc.hi + cs.hi) + (sc.lo + cs.lo)); // Im G(k,l)
+  const float gr_m = (cc.hi + ss.hi) + (cc.lo + ss.lo);   // Re G(k,-l)
+  const float gi_m = -((sc.hi - cs.hi) + (sc.lo - cs.lo)); // Im G(k,-l)
+  const float pr = -a * gr_p, pi = -a * gi_p;   // F(k,l)  = -a G(k,l)
+  const float mr = a * gr_m, mi = a * gi_m;     // F(k,-l) = +a G(k,-l)
+  F[(K + k) * W + (K + l)] = make_float2(pr, pi);
+  F[(K - k) * W + (K - l)] = make_float2(pr, -pi);
+  F[(K + k) * W + (K - l)] = make_float2(mr, mi);
+  F[(K - k) * W + (K + l)] = make_float2(mr, -mi);
 }
 
 // ---------------------------------------------------------------------------
 // Host launch wrappers
 // ---------------------------------------------------------------------------
 cudaError_t launch_prep(const Plan& pl, void* ws, bool validate, cudaStream_t st) {
+  // one thread per table entry on a cold workspace (the FP64 cospi is the cost)
   long long work = pl.full ? pl.T : pl.T / 4 + 1;
   work = max(work, 4LL * pl.K + 1);
   if (validate) work = max(work, 2LL * (pl.T + 1));
-  int blocks = (int)min((work + 255) / 256, 1024LL);
-  prep_kernel<<<blocks, 256, 0, st>>>(pl, static_cast<uint8_t*>(ws), validate ? 1 : 0);
+  int blocks = (int)min((work + 63) / 64, 2048LL);
+  prep_kernel<<<blocks, 64, 0, st>>>(pl, static_cast<uint8_t*>(ws), validate ? 1 : 0);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -290,7 +297,7 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
 cudaError_t launch_reduce(const Plan& pl, void* ws, float* F, int64_t* area, bool validate, cudaStream_t st) {
   const long long n = (long long)(pl.K + 1) * (pl.K + 1);
   const int blocks = (int)((n + 255) / 256);
-  reduce_kernel<<<blocks, 256, 0, st>>>(pl, static_cast<const uint8_t*>(ws), reinterpret_cast<float2*>(F),
+  reduce_kernel<<<blocks, 256, 0, st>>>(pl, static_cast<uint8_t*>(ws), reinterpret_cast<float2*>(F),
                                         reinterpret_cast<long long*>(area), validate ? 1 : 0);
   count_launch(1);
   return cudaGetLastError();

@@ -19,14 +19,6 @@ constexpr int kSChunk = 32;    // vertices per chunk
 constexpr int kSThreads = 256;
 
 template <bool FULL>
-__device__ __forceinline__ float2 f32_lookup(const float* tab, uint32_t p, uint32_t logQ) {
-  if (FULL) return reinterpret_cast<const float2*>(tab)[p];
-  Quad qd = quad_split(p, logQ);
-  float c = tab[qd.i1], s = tab[qd.i2];
-  return make_float2(qd.cneg ? -c : c, qd.sneg ? -s : s);
-}
-
-template <bool FULL>
 __global__ void __launch_bounds__(kSThreads, 2) gemm_simt_kernel(Plan pl, const int32_t* __restrict__ x,
                                                                 const int32_t* __restrict__ y,
                                                                 const int8_t* __restrict__ s, uint8_t* ws) {

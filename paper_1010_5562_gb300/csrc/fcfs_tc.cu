@@ -2,19 +2,25 @@
 // the accumulator in TMEM and both operands generated on chip.
 //
 //   P[m, n] = sum_v A[m, v] B[n, v]  (see fcfs_simt.cu for A, B and the rows),
-//   A = A_hi + A_lo, B = B_hi + B_lo (FP16, hi = rn(c), lo = rn(c - hi)),
+//   A = A_hi + A_lo, B = B_hi + B_lo (FP16, hi = rn(a), lo = rn(a - hi)),
 //   P ~= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T, accumulated in FP32 in TMEM.
 //
-// The dropped A_lo B_lo^T term is below 2^-22 of a term.  The corner sign s_v
-// is folded into the phase (s = -1 adds T/2), so generating A costs the same
-// as generating B.  CTA roles (192 threads):
-//   warps 0-3   generate the A and B tiles of a 64-vertex chunk into shared
-//               memory in the K-major 128-byte-swizzled layout, then drain TMEM
-//               in the epilogue;
-//   warp 4      allocates TMEM; lane 0 issues the tcgen05.mma (3 split
-//               products x 4 k-steps per chunk) and the commits;
-//   warp 5      lane 0 streams the vertex chunks (x, y, s) with 1-D TMA and
-//               bulk-copies the sincos table once.
+// The dropped A_lo B_lo^T term is below 2^-22 of a term.  Operand generation:
+// each generator thread owns 8 vertices and a run of 8 consecutive
+// frequencies f0..f0+7.  It reads cos/sin(2 pi f0 a / T) (the anchor) and
+// cos/sin(2 pi a / T) (the step) from the FP32 table at exact integer phase
+// indices and produces the run by angle addition, one complex FP32 multiply
+// per frequency; every value is therefore a deterministic function of
+// (frequency, coordinate), so the two corners of an edge still get identical
+// (or exactly opposite) operands.  The corner sign s_v is folded into the
+// anchor phase (s = -1 adds T/2).  CTA roles:
+//   generator warps  write the hi and lo tiles of a 64-vertex chunk into shared
+//                    memory (K-major, 128-byte swizzle); warps 0-3 then drain
+//                    TMEM in the epilogue;
+//   MMA warp         allocates TMEM; lane 0 issues the tcgen05.mma (3 split
+//                    products x 4 k-steps per chunk) and the commits;
+//   TMA warp         lane 0 streams the vertex chunks (x, y, s) with 1-D TMA
+//                    and bulk-copies the sincos table once.
 // Every mbarrier wait is bounded: on time-out the status word gets
 // FCFS_ETIMEOUT and the CTA drains and exits normally.
 #include "fcfs_common.cuh"
@@ -23,9 +29,7 @@ namespace fcfs {
 
 constexpr int kBM = 128;         // tile rows (64 k values x {cos, sin})
 constexpr int kCh = 64;          // vertices per chunk = one 128-byte swizzle row of FP16
-constexpr int kGenWarps = 4;
-constexpr int kGenThreads = kGenWarps * 32;
-constexpr int kTcThreads = kGenThreads + 64;
+constexpr int kRun = 8;          // consecutive frequencies generated by one thread
 constexpr int kVStages = 2;
 constexpr int kBox = 80;         // TMA box: chunk plus up to 15 elements of alignment slack
 constexpr int kVStageBytes = 896;  // x @0 (320 B), y @384 (320 B), s @768 (80 B)
@@ -37,22 +41,17 @@ struct TcLayout {
   static constexpr int kBTile = BN * 128;
   static constexpr int kStage = 2 * kATile + 2 * kBTile;
   static constexpr int kOps = STAGES * kStage;
+  // one generator thread per (vertex octet, run of kRun row pairs)
+  static constexpr int kRunsA = kBM / 2 / kRun;
+  static constexpr int kGenThreads = (kBM / 2 + BN / 2) / kRun * 8;
+  static constexpr int kGenWarps = kGenThreads / 32;
+  static constexpr int kThreads = kGenThreads + 64;
 };
 
 template <int BN, int STAGES>
 size_t tc_smem_bytes(int T, int full) {
-  return 1024 + TcLayout<BN, STAGES>::kOps + align_up(tab_tc_bytes(T, full), 128) + kVStages * kVStageBytes + 256;
-}
-
-// (cos_hi | sin_hi << 16, cos_lo | sin_lo << 16) of phase p
-template <bool FULL>
-__device__ __forceinline__ uint2 tc_lookup(const uint8_t* tab, uint32_t p, uint32_t logQ) {
-  if (FULL) return reinterpret_cast<const uint2*>(tab)[p];
-  const uint32_t* t = reinterpret_cast<const uint32_t*>(tab);
-  Quad qd = quad_split(p, logQ);
-  const uint32_t c = t[qd.i1], s = t[qd.i2];
-  const uint32_t sg = (qd.cneg ? 0x8000u : 0u) | (qd.sneg ? 0x80000000u : 0u);
-  return make_uint2(__byte_perm(c, s, 0x5410) ^ sg, __byte_perm(c, s, 0x7632) ^ sg);
+  return 1024 + TcLayout<BN, STAGES>::kOps + align_up(tab_f32_bytes(T, full), 128) + kVStages * kVStageBytes +
+         256;
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
@@ -65,50 +64,34 @@ __device__ __forceinline__ uint32_t sw128(int r, int c) {
   return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
 }
 
-// Generate the rows of one row pair (cos row 2i, sin row 2i+1) for this
-// thread's 8 vertices and store hi and lo.  `mul` is k (or l), `xin` the
-// coordinates, `add` the phase offsets (T/2 for s = -1 on A, 0 on B).
-template <bool FULL, bool MASKED>
-__device__ __forceinline__ void gen_pair(const uint8_t* tab, uint32_t logQ, uint32_t mask, uint32_t mul,
-                                         const uint32_t (&xin)[8], const uint32_t (&add)[8],
-                                         const uint32_t (&vmask)[4], uint32_t hi_base, uint32_t lo_base,
-                                         int i, int oct) {
-  uint2 e[8];
-#pragma unroll
-  for (int t = 0; t < 8; ++t) e[t] = tc_lookup<FULL>(tab, (mul * xin[t] + add[t]) & mask, logQ);
-  uint32_t ch[4], sh[4], cl[4], sl[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    ch[j] = __byte_perm(e[2 * j].x, e[2 * j + 1].x, 0x5410);
-    sh[j] = __byte_perm(e[2 * j].x, e[2 * j + 1].x, 0x7632);
-    cl[j] = __byte_perm(e[2 * j].y, e[2 * j + 1].y, 0x5410);
-    sl[j] = __byte_perm(e[2 * j].y, e[2 * j + 1].y, 0x7632);
-    if (MASKED) {
-      ch[j] &= vmask[j];
-      sh[j] &= vmask[j];
-      cl[j] &= vmask[j];
-      sl[j] &= vmask[j];
-    }
-  }
-  const int r0 = 2 * i, r1 = 2 * i + 1;
-  st_shared_v4(hi_base + sw128(r0, oct), ch[0], ch[1], ch[2], ch[3]);
-  st_shared_v4(hi_base + sw128(r1, oct), sh[0], sh[1], sh[2], sh[3]);
-  st_shared_v4(lo_base + sw128(r0, oct), cl[0], cl[1], cl[2], cl[3]);
-  st_shared_v4(lo_base + sw128(r1, oct), sl[0], sl[1], sl[2], sl[3]);
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) {
+  uint32_t u;
+  memcpy(&u, &h, 4);
+  return u;
+}
+
+// hi = rn_fp16(v), lo = rn_fp16(v - hi) for two neighbouring vertices (v0 in the low half)
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(v0, v1);
+  const float2 hf = __half22float2(h);
+  hi = h2_bits(h);
+  lo = h2_bits(__floats2half2_rn(v0 - hf.x, v1 - hf.y));
 }
 
 template <int BN, int STAGES, bool FULL>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
                    const __grid_constant__ CUtensorMap tms, Plan pl, uint8_t* ws) {
   using L = TcLayout<BN, STAGES>;
+  constexpr int GT = L::kGenThreads;
+  constexpr int GW = L::kGenWarps;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-  const size_t tb = tab_tc_bytes(pl.T, FULL);
+  const size_t tb = tab_f32_bytes(pl.T, FULL);
   uint8_t* ops = sm;
-  uint8_t* tab = sm + L::kOps;
-  uint8_t* vst = tab + align_up(tb, 128);   // TMA destinations: 128-byte aligned
+  float* tab = reinterpret_cast<float*>(sm + L::kOps);
+  uint8_t* vst = sm + L::kOps + align_up(tb, 128);   // TMA destinations: 128-byte aligned
   uint64_t* bars = reinterpret_cast<uint64_t*>(vst + kVStages * kVStageBytes);
   uint64_t* ofull = bars;
   uint64_t* oempty = ofull + STAGES;
@@ -128,20 +111,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const long long v1 = min((long long)pl.V, v0 + pl.split_len);
   const int nch = (int)((v1 - v0 + kCh - 1) / kCh);
 
-  if (tid == kGenThreads + 32) {
+  if (tid == GT + 32) {
     for (int i = 0; i < STAGES; ++i) {
-      mbar_init(&ofull[i], kGenThreads);
+      mbar_init(&ofull[i], GT);
       mbar_init(&oempty[i], 1);
     }
     for (int i = 0; i < kVStages; ++i) {
       mbar_init(&vfull[i], 1);
-      mbar_init(&vempty[i], kGenThreads);
+      mbar_init(&vempty[i], GT);
     }
     mbar_init(accfull, 1);
     mbar_init(tabbar, 1);
     fence_mbar_init();
   }
-  if (warp == kGenWarps) {
+  if (warp == GW) {
     tmem_alloc(tmem_slot, BN);
     tmem_relinquish();
   }
@@ -150,11 +133,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == kGenWarps + 1) {
+  if (warp == GW + 1) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       mbar_arrive_expect_tx(tabbar, (uint32_t)tb);
-      bulk_load(tab, ws + pl.off_tab_tc, (uint32_t)tb, tabbar);
+      bulk_load(tab, ws + pl.off_tab_f32, (uint32_t)tb, tabbar);
       int j = 0;
       for (; j < nch; ++j) {
         const int vs = j % kVStages;
@@ -173,7 +156,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         mbar_wait(&vfull[q % kVStages], (uint32_t)(q / kVStages) & 1u, st, 2);
       mbar_wait(tabbar, 0, st, 3);
     }
-  } else if (warp == kGenWarps) {
+  } else if (warp == GW) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_f16_f32(kBM, BN);
@@ -202,14 +185,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else {
     // ---------------- generators ----------------
-    const int oct = tid & 7;     // vertex octet of the chunk
-    const int rp = tid >> 3;     // first row pair (0..15)
+    // unit = (vertex octet, run of kRun row pairs); runs [0, kRunsA) are A's
+    // (warp-uniform: 4 runs per warp), the others B's
+    const int oct = tid & 7;
+    const int run = tid >> 3;
+    const bool isA = run < L::kRunsA;
+    const int i0 = kRun * (isA ? run : run - L::kRunsA);       // first row pair in the tile
+    const uint32_t f0 = isA ? (uint32_t)(tm * (kBM / 2) + 1 + i0) : (uint32_t)(tn * (BN / 2) + 1 + i0);
     const uint32_t mask = (uint32_t)pl.T - 1u;
     const uint32_t half = (uint32_t)pl.T >> 1;
     const uint32_t logQ = (uint32_t)pl.logT - 2u;
-    const uint32_t kA = (uint32_t)(tm * (kBM / 2) + 1);
-    const uint32_t lB = (uint32_t)(tn * (BN / 2) + 1);
     const uint32_t ops_a = smem_u32(ops);
+    const int coord_off = isA ? 0 : 384;
     bool ok = mbar_wait(tabbar, 0, st, 5);
     for (int j = 0; ok && j < nch; ++j) {
       const int vs = j % kVStages;
@@ -220,94 +207,115 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const long long cs = v0 + (long long)j * kCh;
       const int off = (int)(cs & 15LL);
       const uint8_t* d = vst + vs * kVStageBytes;
-      const int32_t* xs = reinterpret_cast<const int32_t*>(d);
-      const int32_t* ys = reinterpret_cast<const int32_t*>(d + 384);
+      const int32_t* co = reinterpret_cast<const int32_t*>(d + coord_off);
       const int8_t* ss = reinterpret_cast<const int8_t*>(d + 768);
-      uint32_t xa[8], ya[8], addA[8], zero[8], vmask[4];
+      uint32_t a[8], add[8], vmask[4];
       bool full = true;
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int idx = off + oct * 8 + t;
-        xa[t] = (uint32_t)xs[idx];
-        ya[t] = (uint32_t)ys[idx];
-        addA[t] = ss[idx] < 0 ? half : 0u;
-        zero[t] = 0u;
+        a[t] = (uint32_t)co[idx];
+        add[t] = (isA && ss[idx] < 0) ? half : 0u;
         full = full && (cs + oct * 8 + t < v1);
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const bool a = cs + oct * 8 + 2 * q < v1, b = cs + oct * 8 + 2 * q + 1 < v1;
-        vmask[q] = (a ? 0xFFFFu : 0u) | (b ? 0xFFFF0000u : 0u);
+        const bool lo_ok = cs + oct * 8 + 2 * q < v1, hi_ok = cs + oct * 8 + 2 * q + 1 < v1;
+        vmask[q] = (lo_ok ? 0xFFFFu : 0u) | (hi_ok ? 0xFFFF0000u : 0u);
       }
+      const bool masked = isA && !full;
       // The next TMA write into this stage is an async-proxy write; the
       // mbarrier release alone does not order it after these generic-proxy
       // loads, which may still be in flight.  The proxy fence does.
       fence_proxy_async_smem();
       mbar_arrive(&vempty[vs]);
-      if (!mbar_wait(&oempty[stg], ph ^ 1u, st, 7)) break;
-      const uint32_t ahi = ops_a + stg * L::kStage;
-      const uint32_t alo = ahi + L::kATile;
-      const uint32_t bhi = alo + L::kATile;
-      const uint32_t blo = bhi + L::kBTile;
-      if (full) {
-#pragma unroll 1
-        for (int t = 0; t < kBM / 2 / 16; ++t) {
-          const int i = rp + 16 * t;
-          gen_pair<FULL, false>(tab, logQ, mask, kA + i, xa, addA, vmask, ahi, alo, i, oct);
-        }
-      } else {
-#pragma unroll 1
-        for (int t = 0; t < kBM / 2 / 16; ++t) {
-          const int i = rp + 16 * t;
-          gen_pair<FULL, true>(tab, logQ, mask, kA + i, xa, addA, vmask, ahi, alo, i, oct);
-        }
+      // anchors and steps from the table, before waiting for the stage
+      float c[8], sn[8], wc[8], wsn[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const float2 an = f32_lookup<FULL>(tab, (f0 * a[t] + add[t]) & mask, logQ);
+        const float2 w = f32_lookup<FULL>(tab, a[t] & mask, logQ);
+        c[t] = an.x;
+        sn[t] = an.y;
+        wc[t] = w.x;
+        wsn[t] = w.y;
       }
+      if (!mbar_wait(&oempty[stg], ph ^ 1u, st, 7)) break;
+      const uint32_t base = ops_a + stg * L::kStage + (isA ? 0u : 2u * L::kATile);
+      const uint32_t hi_base = base;
+      const uint32_t lo_base = base + (isA ? L::kATile : L::kBTile);
 #pragma unroll 1
-      for (int t = 0; t < BN / 2 / 16; ++t) {
-        const int i = rp + 16 * t;
-        gen_pair<FULL, false>(tab, logQ, mask, lB + i, ya, zero, vmask, bhi, blo, i, oct);
+      for (int r = 0; r < kRun; ++r) {
+        if (r) {
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const float nc = fmaf(c[t], wc[t], -(sn[t] * wsn[t]));
+            const float ns = fmaf(sn[t], wc[t], c[t] * wsn[t]);
+            c[t] = nc;
+            sn[t] = ns;
+          }
+        }
+        uint32_t ch[4], cl[4], sh[4], sl[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          split2(c[2 * q], c[2 * q + 1], ch[q], cl[q]);
+          split2(sn[2 * q], sn[2 * q + 1], sh[q], sl[q]);
+          if (masked) {
+            ch[q] &= vmask[q];
+            cl[q] &= vmask[q];
+            sh[q] &= vmask[q];
+            sl[q] &= vmask[q];
+          }
+        }
+        const int row = 2 * (i0 + r);
+        st_shared_v4(hi_base + sw128(row, oct), ch[0], ch[1], ch[2], ch[3]);
+        st_shared_v4(hi_base + sw128(row + 1, oct), sh[0], sh[1], sh[2], sh[3]);
+        st_shared_v4(lo_base + sw128(row, oct), cl[0], cl[1], cl[2], cl[3]);
+        st_shared_v4(lo_base + sw128(row + 1, oct), sl[0], sl[1], sl[2], sl[3]);
       }
       fence_proxy_async_smem();
       mbar_arrive(&ofull[stg]);
     }
-    // ---------------- epilogue: TMEM -> FP32 partials ----------------
-    const bool acc_ok = mbar_wait(accfull, 0, st, 8);
-    __syncwarp();   // tcgen05.ld is warp-collective: reconverge after the per-octet branches
-    tc_fence_after();
-    const int M2 = pl.M2;
-    float* P = reinterpret_cast<float*>(ws + pl.off_part) + (size_t)split * M2 * M2;
-    const int row = warp * 32 + lane;
-    const int m = tm * kBM + row;
-    if (acc_ok && nch > 0) {
+    // ---------------- epilogue: TMEM -> FP32 partials (warps 0-3) ----------------
+    if (warp < 4) {
+      const bool acc_ok = mbar_wait(accfull, 0, st, 8);
+      __syncwarp();   // tcgen05.ld is warp-collective: reconverge after the per-thread branches
+      tc_fence_after();
+      const int M2 = pl.M2;
+      float* P = reinterpret_cast<float*>(ws + pl.off_part) + (size_t)split * M2 * M2;
+      const int row = warp * 32 + lane;
+      const int m = tm * kBM + row;
+      if (acc_ok && nch > 0) {
 #pragma unroll 1
-      for (int cb = 0; cb < BN / 32; ++cb) {
-        const int n0 = tn * BN + cb * 32;
-        if (n0 >= M2) break;   // warp-uniform
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), r);
-        tmem_wait_ld();
-        if (m < M2) {
-          float* dst = P + (size_t)m * M2 + n0;
-          if (n0 + 32 <= M2 && (M2 & 3) == 0) {
+        for (int cb = 0; cb < BN / 32; ++cb) {
+          const int n0 = tn * BN + cb * 32;
+          if (n0 >= M2) break;   // warp-uniform
+          uint32_t r[32];
+          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), r);
+          tmem_wait_ld();
+          if (m < M2) {
+            float* dst = P + (size_t)m * M2 + n0;
+            if (n0 + 32 <= M2 && (M2 & 3) == 0) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-              reinterpret_cast<float4*>(dst)[q] =
-                  make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                              __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
-          } else {
-            for (int q = 0; q < 32; ++q)
-              if (n0 + q < M2) dst[q] = __uint_as_float(r[q]);
+              for (int q = 0; q < 8; ++q)
+                reinterpret_cast<float4*>(dst)[q] =
+                    make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+            } else {
+              for (int q = 0; q < 32; ++q)
+                if (n0 + q < M2) dst[q] = __uint_as_float(r[q]);
+            }
           }
         }
+      } else if (m < M2) {
+        for (int n = tn * BN; n < min(M2, tn * BN + BN); ++n) P[(size_t)m * M2 + n] = 0.f;
       }
-    } else if (m < M2) {
-      for (int n = tn * BN; n < min(M2, tn * BN + BN); ++n) P[(size_t)m * M2 + n] = 0.f;
     }
   }
 
   tc_fence_before();
   __syncthreads();
-  if (warp == kGenWarps) {
+  if (warp == GW) {
     __syncwarp();   // lane 0 ran the MMA loop alone; dealloc is warp-collective
     tc_fence_after();
     tmem_dealloc(tmem, BN);
@@ -324,7 +332,7 @@ static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cud
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(pl.tiles_m * pl.tiles_n, pl.splits);
-  kern<<<grid, kTcThreads, smem, st>>>(mp.x, mp.y, mp.s, pl, static_cast<uint8_t*>(ws));
+  kern<<<grid, TcLayout<BN, STAGES>::kThreads, smem, st>>>(mp.x, mp.y, mp.s, pl, static_cast<uint8_t*>(ws));
   count_launch(1);
   return cudaGetLastError();
 }

@@ -132,3 +132,16 @@ def launch_count():
 def set_splits(n):
     """Force the number of vertex splits (0: automatic); a test hook."""
     _lib.load().fcfs_debug_set_splits(int(n))
+
+
+def profile_enable(on=True):
+    """Bracket every stage of later calls with CUDA events (see profile_read)."""
+    _lib.load().fcfs_profile_enable(1 if on else 0)
+
+
+def profile_read():
+    """Durations in ms of the last call's stages: prep, axis, contraction, reduce."""
+    import ctypes as C
+    buf = (C.c_float * 4)()
+    n = _lib.load().fcfs_profile_read(buf, 4)
+    return [float(buf[i]) for i in range(n)]
