@@ -1,5 +1,5 @@
-// Table fill, exact area and axis lines, and the FP64 split-K reduction with
-// the quarter-plane butterfly and the Prop. CFT scale factors.
+// Table fill, exact area and axis lines, and the compensated split-K reduction
+// with the quarter-plane butterfly and the Prop. CFT scale factors.
 #include <math_constants.h>
 
 #include "fcfs_common.cuh"
@@ -71,7 +71,13 @@ __global__ void prep_kernel(Plan pl, uint8_t* ws, int validate) {
 // q is chosen on the host so that V * T * 2^q < 2^62: the final sums then fit,
 // and modular int64 addition makes the order of the partial sums irrelevant
 // (the result is bit-identical run to run).  Balance is not assumed.
+//
 // Block: 256 threads = 256 consecutive k; blockIdx.x picks a vertex range.
+// The 32 lanes of a warp read the table at phases k a mod T for consecutive k,
+// i.e. at stride a.  With a = 2^e u (u odd) that stride hits the same banks
+// 2^e times over, so full-period tables are expanded in shared memory into
+// decimated levels: level e holds the entries at multiples of 2^e and is read
+// at (k u) mod (T / 2^e), a unit stride in k, which is conflict-free.
 // ---------------------------------------------------------------------------
 constexpr int kAxisThreads = 256;
 constexpr int kAxisStage = 256;
@@ -85,59 +91,101 @@ __device__ __forceinline__ int2 fix_lookup(const void* tab, uint32_t p, uint32_t
   return make_int2(qd.cneg ? -c : c, qd.sneg ? -s : s);
 }
 
+// level of coordinate a in the decimated full-period table: (first entry, odd factor, index mask)
+__device__ __forceinline__ int3 decimate(int a, int T, int logT) {
+  const uint32_t am = (uint32_t)a & (uint32_t)(T - 1);
+  if (am == 0) return make_int3(0, 0, 0);           // phase 0 for every k
+  const int e = __ffs(am) - 1;
+  const int size = T >> e;
+  return make_int3(2 * T - 2 * size, (int)(am >> e), size - 1);
+}
+
+size_t axis_smem_bytes(int T, int full) {
+  return (full ? (size_t)2 * T * 8 : tab_fix_bytes(T, 0)) + 8 * kAxisStage * sizeof(int);
+}
+
 template <bool FULL>
 __global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32_t* __restrict__ x,
                                                           const int32_t* __restrict__ y,
                                                           const int8_t* __restrict__ s, uint8_t* ws, int vper,
                                                           int validate) {
-  extern __shared__ __align__(16) uint8_t sm[];
-  const size_t tb = tab_fix_bytes(pl.T, FULL);
-  int* sx = reinterpret_cast<int*>(sm + tb);
-  int* sy = sx + kAxisStage;
-  int* ssg = sy + kAxisStage;
-  {
-    const int4* src = reinterpret_cast<const int4*>(ws + pl.off_tab_fix);
-    int4* dst = reinterpret_cast<int4*>(sm);
-    for (int i = threadIdx.x; i < (int)(tb / 16); i += blockDim.x) dst[i] = src[i];
-  }
+  extern __shared__ __align__(128) uint8_t sm[];
   const int T = pl.T;
+  const size_t tb = tab_fix_bytes(T, FULL);
+  const size_t tall = FULL ? (size_t)2 * T * 8 : tb;
+  int* sv = reinterpret_cast<int*>(sm + tall);   // per staged vertex: 8 ints
+  __shared__ uint64_t tbar;
+  Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
+  if (threadIdx.x == 0) {
+    mbar_init(&tbar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&tbar, (uint32_t)tb);
+    bulk_load(sm, ws + pl.off_tab_fix, (uint32_t)tb, &tbar);
+  }
+  __syncthreads();   // barrier initialised before anyone waits on it
+  mbar_wait(&tbar, 0, st, 20);
+  if (FULL) {
+    // decimated levels e = 1 .. logT-1 from level 0
+    int2* t2 = reinterpret_cast<int2*>(sm);
+    for (int e = 1; e < pl.logT; ++e) {
+      const int size = T >> e, off = 2 * T - 2 * size;
+      for (int m = threadIdx.x; m < size; m += blockDim.x) t2[off + m] = t2[m << e];
+    }
+    __syncthreads();
+  }
   const uint32_t mask = (uint32_t)T - 1u;
   const uint32_t logQ = (uint32_t)pl.logT - 2u;
   const int k = blockIdx.y * kAxisThreads + threadIdx.x + 1;
   const long long v0 = (long long)blockIdx.x * vper;
   const long long v1 = min((long long)pl.V, v0 + vper);
   long long a0 = 0, a1 = 0, a2 = 0, a3 = 0, area = 0;
-  Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
   int* hist = reinterpret_cast<int*>(ws + pl.off_hist);
   for (long long b = v0; b < v1; b += kAxisStage) {
     const int n = (int)min((long long)kAxisStage, v1 - b);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int xv = x[b + i], yv = y[b + i], sv = s[b + i];
-      sx[i] = xv;
-      sy[i] = yv;
-      ssg[i] = sv;
+      const int xv = x[b + i], yv = y[b + i], sgn = s[b + i];
+      int* e = sv + 8 * i;
+      if (FULL) {
+        const int3 dx = decimate(xv, T, pl.logT), dy = decimate(yv, T, pl.logT);
+        e[0] = dx.x; e[1] = dx.y; e[2] = dx.z; e[3] = sgn * yv;
+        e[4] = dy.x; e[5] = dy.y; e[6] = dy.z; e[7] = sgn * xv;
+      } else {
+        e[0] = xv; e[1] = sgn * yv; e[4] = yv; e[5] = sgn * xv;
+      }
       if (blockIdx.y == 0) {
-        area += (long long)sv * xv * (long long)yv;
+        area += (long long)sgn * xv * (long long)yv;
         if (validate) {
-          const bool ok = xv >= 0 && xv <= T && yv >= 0 && yv <= T && (sv == 1 || sv == -1);
+          const bool ok = xv >= 0 && xv <= T && yv >= 0 && yv <= T && (sgn == 1 || sgn == -1);
           if (!ok) {
             set_status(st, FCFS_EINVAL_DATA, (unsigned)(b + i));
           } else {
-            atomicAdd(&hist[xv], sv);
-            atomicAdd(&hist[T + 1 + yv], sv);
+            atomicAdd(&hist[xv], sgn);
+            atomicAdd(&hist[T + 1 + yv], sgn);
           }
         }
       }
     }
     __syncthreads();
     if (k <= pl.K) {
+      const int2* t2 = reinterpret_cast<const int2*>(sm);
 #pragma unroll 4
       for (int i = 0; i < n; ++i) {
-        const int xv = sx[i], yv = sy[i], sv = ssg[i];
-        const int2 tx = fix_lookup<FULL>(sm, ((uint32_t)k * (uint32_t)xv) & mask, logQ);
-        const int2 ty = fix_lookup<FULL>(sm, ((uint32_t)k * (uint32_t)yv) & mask, logQ);
-        const int wy = sv * yv, wx = sv * xv;
+        const int4 ex = reinterpret_cast<const int4*>(sv + 8 * i)[0];
+        const int4 ey = reinterpret_cast<const int4*>(sv + 8 * i)[1];
+        int2 tx, ty;
+        int wy, wx;
+        if (FULL) {
+          tx = t2[ex.x + (int)(((uint32_t)k * (uint32_t)ex.y) & (uint32_t)ex.z)];
+          ty = t2[ey.x + (int)(((uint32_t)k * (uint32_t)ey.y) & (uint32_t)ey.z)];
+          wy = ex.w;
+          wx = ey.w;
+        } else {
+          tx = fix_lookup<false>(sm, ((uint32_t)k * (uint32_t)ex.x) & mask, logQ);
+          ty = fix_lookup<false>(sm, ((uint32_t)k * (uint32_t)ey.x) & mask, logQ);
+          wy = ex.y;
+          wx = ey.y;
+        }
         a0 += (long long)tx.x * wy;
         a1 += (long long)tx.y * wy;
         a2 += (long long)ty.x * wx;
@@ -230,14 +278,26 @@ __global__ void reduce_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, long
   const float* P = reinterpret_cast<const float*>(ws + pl.off_part);
   const size_t o0 = (size_t)(2 * (k - 1)) * M2 + 2 * (l - 1);
   CSum cc{0.f, 0.f}, cs{0.f, 0.f}, sc{0.f, 0.f}, ss{0.f, 0.f};
-#pragma unroll 4
-  for (int sp = 0; sp < pl.splits; ++sp) {
-    const float2 r0 = __ldcs(reinterpret_cast<const float2*>(P + sp * plane + o0));
-    const float2 r1 = __ldcs(reinterpret_cast<const float2*>(P + sp * plane + o0 + M2));
-    csum_add(cc, r0.x);
-    csum_add(cs, r0.y);
-    csum_add(sc, r1.x);
-    csum_add(ss, r1.y);
+  // issue a whole batch of split loads before the dependent sums (latency bound otherwise)
+  constexpr int kBatch = 8;
+  for (int sp0 = 0; sp0 < pl.splits; sp0 += kBatch) {
+    float2 r0[kBatch], r1[kBatch];
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      if (sp0 + b < pl.splits) {
+        r0[b] = __ldcs(reinterpret_cast<const float2*>(P + (size_t)(sp0 + b) * plane + o0));
+        r1[b] = __ldcs(reinterpret_cast<const float2*>(P + (size_t)(sp0 + b) * plane + o0 + M2));
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      if (sp0 + b < pl.splits) {
+        csum_add(cc, r0[b].x);
+        csum_add(cs, r0[b].y);
+        csum_add(sc, r1[b].x);
+        csum_add(ss, r1[b].y);
+      }
+    }
   }
   // combine hi and lo parts; the cancellations below are exact or relative to
   // the result, and the result is rounded to FP32 anyway
@@ -263,6 +323,9 @@ cudaError_t launch_prep(const Plan& pl, void* ws, bool validate, cudaStream_t st
   work = max(work, 4LL * pl.K + 1);
   if (validate) work = max(work, 2LL * (pl.T + 1));
   int blocks = (int)min((work + 63) / 64, 2048LL);
+  // every kernel of a call asks for the largest shared-memory carveout, so the
+  // SMs never repartition L1/shared memory between the kernels of a call
+  cudaFuncSetAttribute(prep_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   prep_kernel<<<blocks, 64, 0, st>>>(pl, static_cast<uint8_t*>(ws), validate ? 1 : 0);
   count_launch(1);
   return cudaGetLastError();
@@ -275,18 +338,20 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int kblocks = (pl.K + kAxisThreads - 1) / kAxisThreads;
-  const long long target = max(1LL, (long long)(2 * sms) / kblocks);
-  long long vper = (pl.V + target - 1) / target;
-  vper = max(64LL, (vper + 63) / 64 * 64);
+  // equal vertex ranges, one block per SM and k-block
+  const long long target = max(1LL, (long long)sms / kblocks);
+  long long vper = max(8LL, (pl.V + target - 1) / target);
   const int vblocks = (int)((pl.V + vper - 1) / vper);
-  const size_t smem = tab_fix_bytes(pl.T, pl.full) + 3 * kAxisStage * sizeof(int);
+  const size_t smem = axis_smem_bytes(pl.T, pl.full);
   dim3 grid(vblocks, kblocks);
   if (pl.full) {
     cudaFuncSetAttribute(axis_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(axis_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     axis_kernel<true><<<grid, kAxisThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws), (int)vper,
                                                         validate ? 1 : 0);
   } else {
     cudaFuncSetAttribute(axis_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(axis_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     axis_kernel<false><<<grid, kAxisThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws), (int)vper,
                                                          validate ? 1 : 0);
   }
@@ -297,6 +362,7 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
 cudaError_t launch_reduce(const Plan& pl, void* ws, float* F, int64_t* area, bool validate, cudaStream_t st) {
   const long long n = (long long)(pl.K + 1) * (pl.K + 1);
   const int blocks = (int)((n + 255) / 256);
+  cudaFuncSetAttribute(reduce_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   reduce_kernel<<<blocks, 256, 0, st>>>(pl, static_cast<uint8_t*>(ws), reinterpret_cast<float2*>(F),
                                         reinterpret_cast<long long*>(area), validate ? 1 : 0);
   count_launch(1);

@@ -22,7 +22,7 @@ template <bool FULL>
 __global__ void __launch_bounds__(kSThreads, 2) gemm_simt_kernel(Plan pl, const int32_t* __restrict__ x,
                                                                 const int32_t* __restrict__ y,
                                                                 const int8_t* __restrict__ s, uint8_t* ws) {
-  extern __shared__ __align__(16) uint8_t sm[];
+  extern __shared__ __align__(128) uint8_t sm[];
   const size_t tb = tab_f32_bytes(pl.T, FULL);
   float* tab = reinterpret_cast<float*>(sm);
   float* As = reinterpret_cast<float*>(sm + tb);           // [kSChunk][kSB]
@@ -32,11 +32,16 @@ __global__ void __launch_bounds__(kSThreads, 2) gemm_simt_kernel(Plan pl, const 
   float* vs = reinterpret_cast<float*>(vy + kSChunk);
 
   const int tid = threadIdx.x;
-  {
-    const float4* src = reinterpret_cast<const float4*>(ws + pl.off_tab_f32);
-    float4* dst = reinterpret_cast<float4*>(tab);
-    for (int i = tid; i < (int)(tb / 16); i += kSThreads) dst[i] = src[i];
+  __shared__ uint64_t tbar;
+  Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
+  if (tid == 0) {   // the table arrives by one bulk copy
+    mbar_init(&tbar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&tbar, (uint32_t)tb);
+    bulk_load(tab, ws + pl.off_tab_f32, (uint32_t)tb, &tbar);
   }
+  __syncthreads();
+  mbar_wait(&tbar, 0, st, 21);
   const int tile = blockIdx.x, split = blockIdx.y;
   const int tm = tile / pl.tiles_n, tn = tile % pl.tiles_n;
   const int kbase = tm * (kSB / 2) + 1;    // first k of the tile's rows
@@ -122,9 +127,11 @@ cudaError_t launch_gemm_simt(const Plan& pl, const int32_t* x, const int32_t* y,
   dim3 grid(pl.tiles_m * pl.tiles_n, pl.splits);
   if (pl.full) {
     cudaFuncSetAttribute(gemm_simt_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(gemm_simt_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     gemm_simt_kernel<true><<<grid, kSThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws));
   } else {
     cudaFuncSetAttribute(gemm_simt_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(gemm_simt_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     gemm_simt_kernel<false><<<grid, kSThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws));
   }
   count_launch(1);

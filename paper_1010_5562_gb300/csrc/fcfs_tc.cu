@@ -41,9 +41,12 @@ struct TcLayout {
   static constexpr int kBTile = BN * 128;
   static constexpr int kStage = 2 * kATile + 2 * kBTile;
   static constexpr int kOps = STAGES * kStage;
-  // one generator thread per (vertex octet, run of kRun row pairs)
+  // one generator thread per (vertex octet, run of kRun row pairs); two groups
+  // of such threads take alternate chunks
+  static constexpr int kGroups = 2;
   static constexpr int kRunsA = kBM / 2 / kRun;
-  static constexpr int kGenThreads = (kBM / 2 + BN / 2) / kRun * 8;
+  static constexpr int kGroupThreads = (kBM / 2 + BN / 2) / kRun * 8;
+  static constexpr int kGenThreads = kGroups * kGroupThreads;
   static constexpr int kGenWarps = kGenThreads / 32;
   static constexpr int kThreads = kGenThreads + 64;
 };
@@ -113,12 +116,12 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
 
   if (tid == GT + 32) {
     for (int i = 0; i < STAGES; ++i) {
-      mbar_init(&ofull[i], GT);
+      mbar_init(&ofull[i], L::kGroupThreads);   // one group fills a chunk
       mbar_init(&oempty[i], 1);
     }
     for (int i = 0; i < kVStages; ++i) {
       mbar_init(&vfull[i], 1);
-      mbar_init(&vempty[i], GT);
+      mbar_init(&vempty[i], L::kGroupThreads);
     }
     mbar_init(accfull, 1);
     mbar_init(tabbar, 1);
@@ -185,10 +188,13 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     }
   } else {
     // ---------------- generators ----------------
-    // unit = (vertex octet, run of kRun row pairs); runs [0, kRunsA) are A's
+    // group g takes chunks j = g, g + kGroups, ...; within a group, unit =
+    // (vertex octet, run of kRun row pairs); runs [0, kRunsA) are A's
     // (warp-uniform: 4 runs per warp), the others B's
-    const int oct = tid & 7;
-    const int run = tid >> 3;
+    const int group = tid / L::kGroupThreads;
+    const int gtid = tid % L::kGroupThreads;
+    const int oct = gtid & 7;
+    const int run = gtid >> 3;
     const bool isA = run < L::kRunsA;
     const int i0 = kRun * (isA ? run : run - L::kRunsA);       // first row pair in the tile
     const uint32_t f0 = isA ? (uint32_t)(tm * (kBM / 2) + 1 + i0) : (uint32_t)(tn * (BN / 2) + 1 + i0);
@@ -197,8 +203,13 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     const uint32_t logQ = (uint32_t)pl.logT - 2u;
     const uint32_t ops_a = smem_u32(ops);
     const int coord_off = isA ? 0 : 384;
+    // swizzled byte offset of this thread's 16-byte chunk in row r: (oct ^ (r & 7)) << 4;
+    // rows 2(i0 + r) have r & 7 = 2r & 7 because i0 is a multiple of 8
+    uint32_t xo[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) xo[c] = (uint32_t)((oct ^ c) << 4);
     bool ok = mbar_wait(tabbar, 0, st, 5);
-    for (int j = 0; ok && j < nch; ++j) {
+    for (int j = group; ok && j < nch; j += L::kGroups) {
       const int vs = j % kVStages;
       const uint32_t vph = (uint32_t)(j / kVStages) & 1u;
       const int stg = j % STAGES;
@@ -210,20 +221,19 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
       const int32_t* co = reinterpret_cast<const int32_t*>(d + coord_off);
       const int8_t* ss = reinterpret_cast<const int8_t*>(d + 768);
       uint32_t a[8], add[8], vmask[4];
-      bool full = true;
+      const long long first = cs + oct * 8;
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int idx = off + oct * 8 + t;
         a[t] = (uint32_t)co[idx];
         add[t] = (isA && ss[idx] < 0) ? half : 0u;
-        full = full && (cs + oct * 8 + t < v1);
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const bool lo_ok = cs + oct * 8 + 2 * q < v1, hi_ok = cs + oct * 8 + 2 * q + 1 < v1;
+        const bool lo_ok = first + 2 * q < v1, hi_ok = first + 2 * q + 1 < v1;
         vmask[q] = (lo_ok ? 0xFFFFu : 0u) | (hi_ok ? 0xFFFF0000u : 0u);
       }
-      const bool masked = isA && !full;
+      const bool masked = isA && (first + 8 > v1);
       // The next TMA write into this stage is an async-proxy write; the
       // mbarrier release alone does not order it after these generic-proxy
       // loads, which may still be in flight.  The proxy fence does.
@@ -241,10 +251,9 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
         wsn[t] = w.y;
       }
       if (!mbar_wait(&oempty[stg], ph ^ 1u, st, 7)) break;
-      const uint32_t base = ops_a + stg * L::kStage + (isA ? 0u : 2u * L::kATile);
-      const uint32_t hi_base = base;
-      const uint32_t lo_base = base + (isA ? L::kATile : L::kBTile);
-#pragma unroll 1
+      const uint32_t tile_hi = ops_a + stg * L::kStage + (isA ? 0u : 2u * L::kATile) + 256u * (uint32_t)i0;
+      const uint32_t lo_delta = isA ? (uint32_t)L::kATile : (uint32_t)L::kBTile;
+#pragma unroll
       for (int r = 0; r < kRun; ++r) {
         if (r) {
 #pragma unroll
@@ -260,18 +269,23 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
         for (int q = 0; q < 4; ++q) {
           split2(c[2 * q], c[2 * q + 1], ch[q], cl[q]);
           split2(sn[2 * q], sn[2 * q + 1], sh[q], sl[q]);
-          if (masked) {
+        }
+        if (masked) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
             ch[q] &= vmask[q];
             cl[q] &= vmask[q];
             sh[q] &= vmask[q];
             sl[q] &= vmask[q];
           }
         }
-        const int row = 2 * (i0 + r);
-        st_shared_v4(hi_base + sw128(row, oct), ch[0], ch[1], ch[2], ch[3]);
-        st_shared_v4(hi_base + sw128(row + 1, oct), sh[0], sh[1], sh[2], sh[3]);
-        st_shared_v4(lo_base + sw128(row, oct), cl[0], cl[1], cl[2], cl[3]);
-        st_shared_v4(lo_base + sw128(row + 1, oct), sl[0], sl[1], sl[2], sl[3]);
+        // cos row 2(i0 + r) and sin row 2(i0 + r) + 1 of the hi and lo tiles
+        const uint32_t rc = tile_hi + 256u * r + xo[(2 * r) & 7];
+        const uint32_t rs = tile_hi + 256u * r + 128u + xo[(2 * r + 1) & 7];
+        st_shared_v4(rc, ch[0], ch[1], ch[2], ch[3]);
+        st_shared_v4(rs, sh[0], sh[1], sh[2], sh[3]);
+        st_shared_v4(rc + lo_delta, cl[0], cl[1], cl[2], cl[3]);
+        st_shared_v4(rs + lo_delta, sl[0], sl[1], sl[2], sl[3]);
       }
       fence_proxy_async_smem();
       mbar_arrive(&ofull[stg]);
@@ -331,6 +345,7 @@ static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cud
   auto kern = gemm_tc_kernel<BN, STAGES, FULL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   dim3 grid(pl.tiles_m * pl.tiles_n, pl.splits);
   kern<<<grid, TcLayout<BN, STAGES>::kThreads, smem, st>>>(mp.x, mp.y, mp.s, pl, static_cast<uint8_t*>(ws));
   count_launch(1);
