@@ -151,6 +151,31 @@ fcfs_status fcfs_batch(const int32_t* x, const int32_t* y, const int8_t* s,
                        void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * Forward block for callers that cannot allocate device memory (no counterpart
+ * in the paper; it exists for such callers).  Some code cannot call cudaMalloc
+ * where it needs the transform: a plugin whose host framework owns all device
+ * memory, a real-time loop where an allocation would stall the device, a
+ * memory-pool callback that must not re-enter the allocator.  This entry point
+ * takes the same inputs and outputs as fcfs_forward but no workspace: its
+ * scratch is a fixed array of FCFS_NOALLOC_SCRATCH_BYTES compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  Nothing is allocated per call, by the caller or by the library.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the array and it keeps the last call's contents (cached
+ *    sincos tables; each call zeroes its accumulators itself).  Calls that
+ *    overlap on the GPU (other streams, unordered host threads) race: issue
+ *    them one after another.
+ *  - A clip whose workspace exceeds the array runs with fewer vertex splits;
+ *    if even one split does not fit (about K > 1400), FCFS_EUNSUPPORTED.
+ *  - flags must be 0 (no device validation); device-side status is not exposed.
+ */
+#define FCFS_NOALLOC_SCRATCH_BYTES (32u << 20)
+fcfs_status fcfs_forward_noalloc(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V,
+                                 int32_t T, int32_t K, int32_t prec, uint32_t flags,
+                                 float* F_out, int64_t* area_out, void* stream);
+
+/*
  * Measurement hooks.  fcfs_profile_enable(1) makes every later call bracket
  * each of its stages with CUDA events on the caller's stream; after a call,
  * fcfs_profile_read() waits for the last event and writes up to n stage
