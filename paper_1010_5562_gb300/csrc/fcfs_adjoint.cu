@@ -1,9 +1,294 @@
 // Adjoint of the block transform and edge chaining.
+//
+// For a real loss with cotangent G = dL/dRe F + j dL/dIm F and D = conj(G),
+// differentiating F(k,l) = sum_v s_v X_k(x_v) X_l(y_v) (Lemma polyip with the
+// tail primitive, dX_k(a)/da = -exp(-j 2 pi k a / T)) gives
+//   gx_v = -s_v Re sum_k E_k(x_v) U_k(y_v),  U_k(y) = sum_l D(k,l) X_l(y),
+// E_k(a) = exp(-j 2 pi k a / T).  With X_l(y) = a_l (1 - E_l(y)), a_l = jT/(2 pi l),
+// and X_0(y) = T - y:
+//   U_k(y) = C_k - D(k,0) y - sum_{l>0} [Hp(k,l) cos(2 pi l y/T) + Hm(k,l) sin(2 pi l y/T)],
+//   H(k,l) = D(k,l) a_l,  Hp = H(k,l) + H(k,-l),  Hm = -j (H(k,l) - H(k,-l)),
+//   C_k = sum_{l != 0} H(k,l) + T D(k,0).
+// Folding +-k (cos even, sin odd) turns Re sum_k E_k(x) Z_k into sum_rows A'[row] Z'[row]
+// with A' = (1, cos(2 pi k x/T), sin(2 pi k x/T))_k and Z'[0] = Re Z_0,
+// Z'[(k,c)] = Re Z_k + Re Z_-k, Z'[(k,s)] = Im Z_k - Im Z_-k.  Hence
+//   gx_v = -s_v sum_rows A'[row, v] (M' B')[row, v],
+// a contraction of the real (2K+1) x (2K+2) coefficient matrix M' with the
+// generated operand B' = (cos, sin of 2 pi l y_v / T for l = 1..K, 1, y_v) and a
+// fused column dot with A'.  The full tail integrals are kept (their constant
+// parts do not cancel per corner).  gy is the same with x and y swapped and D
+// transposed.
 #include <algorithm>
+
+#include <math_constants.h>
 
 #include "fcfs_common.cuh"
 
 namespace fcfs {
+
+fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl);
+fcfs_status check_ws(const Plan& pl, void* ws, size_t ws_bytes);
+
+// Workspace of an adjoint call: the forward plan's header and tables, then the
+// two transposed coefficient matrices Mt[col][row] (rows padded to kAdjRowsPad)
+// and the per-row-tile partial gradients.
+struct AdjPlan {
+  Plan p;
+  int rows, cols, rows_pad, R, row_tiles;
+  size_t off_m, off_part, total;
+};
+constexpr int kAdjThreads = 128;
+constexpr size_t kAdjSmemBudget = 200 * 1024;
+
+static fcfs_status make_adj_plan(int64_t V, int32_t T, int32_t K, AdjPlan& ap) {
+  fcfs_status r = make_plan(V, T, K, FCFS_PREC_FP32, ap.p);
+  if (r != FCFS_OK) return r;
+  ap.rows = 2 * K + 1;
+  ap.cols = 2 * K + 2;
+  const size_t tab = align_up(tab_f32_bytes(T, ap.p.full), 128);
+  ap.R = 0;
+  for (int R : {64, 32, 16, 8})
+    if (!ap.R && tab + (size_t)ap.cols * R * sizeof(float) <= kAdjSmemBudget) ap.R = R;
+  if (!ap.R) return FCFS_EUNSUPPORTED;
+  ap.row_tiles = (ap.rows + ap.R - 1) / ap.R;
+  ap.rows_pad = ap.row_tiles * ap.R;
+  size_t o = ap.p.off_part;   // the forward's split partials are not needed here
+  ap.off_m = o;
+  o = align_up(o + (size_t)2 * ap.cols * ap.rows_pad * sizeof(float), kWsAlign);
+  ap.off_part = o;
+  o = align_up(o + (size_t)2 * ap.row_tiles * V * sizeof(float), kWsAlign);
+  ap.total = o;
+  ap.p.total = o;
+  return FCFS_OK;
+}
+
+// Coefficient matrices.  Block (row, matrix): matrix 0 serves gx (D), matrix 1
+// serves gy (D transposed).  FP64 for the folding, stored as FP32.
+__global__ void adj_coef_kernel(AdjPlan ap, const float2* __restrict__ dF, uint8_t* ws) {
+  const int K = ap.p.K, W = 2 * K + 1;
+  const int row = blockIdx.x, mat = blockIdx.y;
+  const double T = (double)ap.p.T;
+  float* Mt = reinterpret_cast<float*>(ws + ap.off_m) + (size_t)mat * ap.cols * ap.rows_pad;
+  const int k = (row + 1) / 2;
+  const int kind = row == 0 ? 0 : (row & 1 ? 1 : 2);   // 0: k = 0, 1: cos row, 2: sin row
+  // D(k,l) of this matrix
+  auto D = [&](int kk, int ll) -> double2 {
+    const float2 g = mat == 0 ? dF[(size_t)(kk + K) * W + (ll + K)] : dF[(size_t)(ll + K) * W + (kk + K)];
+    return make_double2((double)g.x, -(double)g.y);
+  };
+  // H(kk, l) = D(kk, l) * j T / (2 pi l)
+  auto H = [&](int kk, int ll) -> double2 {
+    const double2 d = D(kk, ll);
+    const double a = T / (2.0 * CUDART_PI * (double)ll);
+    return make_double2(-d.y * a, d.x * a);
+  };
+  auto fold = [&](double2 zk, double2 zmk) -> double {
+    return kind == 0 ? zk.x : (kind == 1 ? zk.x + zmk.x : zk.y - zmk.y);
+  };
+  __shared__ double red[2][2][kAdjThreads];   // partial sums of C_k and C_-k
+  double2 ck = make_double2(0, 0), cmk = make_double2(0, 0);
+  for (int l = 1 + threadIdx.x; l <= K; l += blockDim.x) {
+    const double2 hk = H(k, l), hkm = H(k, -l), hmk = H(-k, l), hmkm = H(-k, -l);
+    ck.x += hk.x + hkm.x;
+    ck.y += hk.y + hkm.y;
+    cmk.x += hmk.x + hmkm.x;
+    cmk.y += hmk.y + hmkm.y;
+    // Hp = H(k,l) + H(k,-l), Hm = -j (H(k,l) - H(k,-l)); same for -k
+    const double2 hp_k = make_double2(hk.x + hkm.x, hk.y + hkm.y);
+    const double2 hm_k = make_double2(hk.y - hkm.y, -(hk.x - hkm.x));
+    const double2 hp_mk = make_double2(hmk.x + hmkm.x, hmk.y + hmkm.y);
+    const double2 hm_mk = make_double2(hmk.y - hmkm.y, -(hmk.x - hmkm.x));
+    Mt[(size_t)(2 * (l - 1)) * ap.rows_pad + row] = (float)(-fold(hp_k, hp_mk));
+    Mt[(size_t)(2 * (l - 1) + 1) * ap.rows_pad + row] = (float)(-fold(hm_k, hm_mk));
+  }
+  red[0][0][threadIdx.x] = ck.x;
+  red[0][1][threadIdx.x] = ck.y;
+  red[1][0][threadIdx.x] = cmk.x;
+  red[1][1][threadIdx.x] = cmk.y;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s4[4] = {0, 0, 0, 0};
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      s4[0] += red[0][0][t];
+      s4[1] += red[0][1][t];
+      s4[2] += red[1][0][t];
+      s4[3] += red[1][1][t];
+    }
+    const double2 dk0 = D(k, 0), dmk0 = D(-k, 0);
+    const double2 Ck = make_double2(s4[0] + T * dk0.x, s4[1] + T * dk0.y);
+    const double2 Cmk = make_double2(s4[2] + T * dmk0.x, s4[3] + T * dmk0.y);
+    Mt[(size_t)(2 * K) * ap.rows_pad + row] = (float)fold(Ck, Cmk);
+    Mt[(size_t)(2 * K + 1) * ap.rows_pad + row] = (float)(-fold(dk0, dmk0));
+  }
+  // padding rows of the last tile
+  if (row == 0)
+    for (int i = threadIdx.x; i < ap.cols * (ap.rows_pad - ap.rows); i += blockDim.x) {
+      const int c = i / (ap.rows_pad - ap.rows), rr = ap.rows + i % (ap.rows_pad - ap.rows);
+      Mt[(size_t)c * ap.rows_pad + rr] = 0.f;
+    }
+}
+
+// Contraction with fused column dot.  Block (row tile, vertex range, matrix);
+// each thread takes one corner at a time and accumulates R rows in registers.
+template <int R, bool FULL>
+__global__ void __launch_bounds__(kAdjThreads) adj_gemm_kernel(AdjPlan ap, const int32_t* __restrict__ x,
+                                                             const int32_t* __restrict__ y, uint8_t* ws,
+                                                             int vper) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  const Plan& pl = ap.p;
+  const size_t tb = tab_f32_bytes(pl.T, FULL);
+  float* tab = reinterpret_cast<float*>(sm);
+  float* Ms = reinterpret_cast<float*>(sm + align_up(tb, 128));   // [cols][R]
+  const int tile = blockIdx.x, mat = blockIdx.z;
+  const float* Mt = reinterpret_cast<const float*>(ws + ap.off_m) + (size_t)mat * ap.cols * ap.rows_pad;
+  __shared__ uint64_t tbar;
+  Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
+  if (threadIdx.x == 0) {
+    mbar_init(&tbar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&tbar, (uint32_t)tb);
+    bulk_load(tab, ws + pl.off_tab_f32, (uint32_t)tb, &tbar);
+  }
+  for (int i = threadIdx.x; i < ap.cols * R; i += blockDim.x) {
+    const int c = i / R, r = i % R;
+    Ms[i] = Mt[(size_t)c * ap.rows_pad + tile * R + r];
+  }
+  __syncthreads();
+  mbar_wait(&tbar, 0, st, 30);
+  const int K = pl.K;
+  const uint32_t mask = (uint32_t)pl.T - 1u;
+  const uint32_t logQ = (uint32_t)pl.logT - 2u;
+  const int32_t* ca = mat == 0 ? x : y;   // coordinate of the epilogue operand A'
+  const int32_t* cb = mat == 0 ? y : x;   // coordinate of the contraction operand B'
+  float* part = reinterpret_cast<float*>(ws + ap.off_part) + ((size_t)mat * ap.row_tiles + tile) * pl.V;
+  const long long v0 = (long long)blockIdx.y * vper;
+  const long long v1 = min((long long)pl.V, v0 + vper);
+  for (long long v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+    const int a = ca[v], b = cb[v];
+    float acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0.f;
+    for (int l = 1; l <= K; ++l) {
+      const float2 e = f32_lookup<FULL>(tab, ((uint32_t)l * (uint32_t)b) & mask, logQ);
+      const float4* mc = reinterpret_cast<const float4*>(Ms + (size_t)(2 * (l - 1)) * R);
+      const float4* ms = reinterpret_cast<const float4*>(Ms + (size_t)(2 * (l - 1) + 1) * R);
+#pragma unroll
+      for (int q = 0; q < R / 4; ++q) {
+        const float4 c4 = mc[q], s4 = ms[q];
+        acc[4 * q] = fmaf(c4.x, e.x, fmaf(s4.x, e.y, acc[4 * q]));
+        acc[4 * q + 1] = fmaf(c4.y, e.x, fmaf(s4.y, e.y, acc[4 * q + 1]));
+        acc[4 * q + 2] = fmaf(c4.z, e.x, fmaf(s4.z, e.y, acc[4 * q + 2]));
+        acc[4 * q + 3] = fmaf(c4.w, e.x, fmaf(s4.w, e.y, acc[4 * q + 3]));
+      }
+    }
+    {
+      const float fb = (float)b;
+      const float4* m1 = reinterpret_cast<const float4*>(Ms + (size_t)(2 * K) * R);
+      const float4* mb = reinterpret_cast<const float4*>(Ms + (size_t)(2 * K + 1) * R);
+#pragma unroll
+      for (int q = 0; q < R / 4; ++q) {
+        const float4 c4 = m1[q], b4 = mb[q];
+        acc[4 * q] += fmaf(b4.x, fb, c4.x);
+        acc[4 * q + 1] += fmaf(b4.y, fb, c4.y);
+        acc[4 * q + 2] += fmaf(b4.z, fb, c4.z);
+        acc[4 * q + 3] += fmaf(b4.w, fb, c4.w);
+      }
+    }
+    // column dot with A' = (1 | cos, sin of 2 pi k a / T) over this tile's rows
+    float out = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int row = tile * R + r;
+      if (row >= ap.rows) break;
+      float av;
+      if (row == 0) {
+        av = 1.f;
+      } else {
+        const int k = (row + 1) >> 1;
+        const float2 e = f32_lookup<FULL>(tab, ((uint32_t)k * (uint32_t)a) & mask, logQ);
+        av = (row & 1) ? e.x : e.y;
+      }
+      out = fmaf(av, acc[r], out);
+    }
+    part[v] = out;
+  }
+}
+
+// gx_v = -s_v sum_tiles part[0][tile][v], gy likewise (compensated, tile order).
+__global__ void adj_finalize_kernel(AdjPlan ap, const int8_t* __restrict__ s, uint8_t* ws,
+                                    float* __restrict__ gx, float* __restrict__ gy) {
+  const long long V = ap.p.V;
+  // last kernel of the call: the tables built by this call's prep are now valid
+  if (blockIdx.x == 0 && threadIdx.x == 0) *reinterpret_cast<unsigned long long*>(ws + kTagOffset) = ap.p.tag;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    const float* part = reinterpret_cast<const float*>(ws + ap.off_part);
+    float out[2];
+    for (int m = 0; m < 2; ++m) {
+      float hi = 0.f, lo = 0.f;
+      for (int t = 0; t < ap.row_tiles; ++t) {
+        const float b = part[((size_t)m * ap.row_tiles + t) * V + v];
+        const float sum = hi + b, bb = sum - hi;
+        lo += (hi - (sum - bb)) + (b - bb);
+        hi = sum;
+      }
+      out[m] = -(float)s[v] * (hi + lo);
+    }
+    gx[v] = out[0];
+    gy[v] = out[1];
+  }
+}
+
+template <int R, bool FULL>
+static cudaError_t launch_adj_gemm(const AdjPlan& ap, const int32_t* x, const int32_t* y, void* ws, cudaStream_t st) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long target = std::max(1LL, (long long)(2 * sms) / (2LL * ap.row_tiles));
+  const long long vper = std::max(128LL, (ap.p.V + target - 1) / target);
+  const int vb = (int)((ap.p.V + vper - 1) / vper);
+  const size_t smem = align_up(tab_f32_bytes(ap.p.T, FULL), 128) + (size_t)ap.cols * R * sizeof(float);
+  auto kern = adj_gemm_kernel<R, FULL>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  kern<<<dim3(ap.row_tiles, vb, 2), kAdjThreads, smem, st>>>(ap, x, y, static_cast<uint8_t*>(ws), (int)vper);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <bool FULL>
+static cudaError_t launch_adj_gemm_r(const AdjPlan& ap, const int32_t* x, const int32_t* y, void* ws,
+                                     cudaStream_t st) {
+  switch (ap.R) {
+    case 64: return launch_adj_gemm<64, FULL>(ap, x, y, ws, st);
+    case 32: return launch_adj_gemm<32, FULL>(ap, x, y, ws, st);
+    case 16: return launch_adj_gemm<16, FULL>(ap, x, y, ws, st);
+    default: return launch_adj_gemm<8, FULL>(ap, x, y, ws, st);
+  }
+}
+
+static fcfs_status adjoint_impl(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, int32_t T, int32_t K,
+                                int32_t prec, const float* dF, float* gx, float* gy, void* ws, size_t ws_bytes,
+                                cudaStream_t st) {
+  if (prec != FCFS_PREC_FP32 && prec != FCFS_PREC_SPLIT_F16) return FCFS_EINVAL;
+  if (!dF || (V > 0 && (!x || !y || !s || !gx || !gy))) return FCFS_EINVAL;
+  AdjPlan ap;
+  fcfs_status r = make_adj_plan(V, T, K, ap);
+  if (r != FCFS_OK) return r;
+  if ((r = check_ws(ap.p, ws, ws_bytes)) != FCFS_OK) return r;
+  if (V == 0) return FCFS_OK;
+  if (launch_prep(ap.p, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
+  adj_coef_kernel<<<dim3(ap.rows, 2), kAdjThreads, 0, st>>>(ap, reinterpret_cast<const float2*>(dF),
+                                                            static_cast<uint8_t*>(ws));
+  count_launch(1);
+  if (cudaGetLastError() != cudaSuccess) return FCFS_ECUDA;
+  const cudaError_t e = ap.p.full ? launch_adj_gemm_r<true>(ap, x, y, ws, st) : launch_adj_gemm_r<false>(ap, x, y, ws, st);
+  if (e != cudaSuccess) return FCFS_ECUDA;
+  const int blocks = (int)std::min<long long>((V + 255) / 256, 4096);
+  adj_finalize_kernel<<<blocks, 256, 0, st>>>(ap, s, static_cast<uint8_t*>(ws), gx, gy);
+  count_launch(1);
+  if (cudaGetLastError() != cudaSuccess) return FCFS_ECUDA;
+  return FCFS_OK;
+}
 
 // gE[e] = g_axis[ev0[e]] + g_axis[ev1[e]]: an edge moves both of its corners.
 __global__ void edge_chain_kernel(const float* __restrict__ gx, const float* __restrict__ gy,
@@ -32,11 +317,17 @@ fcfs_status fcfs_edge_chain(const float* gx, const float* gy, const int32_t* ev0
   return cudaGetLastError() == cudaSuccess ? FCFS_OK : FCFS_ECUDA;
 }
 
-size_t fcfs_adjoint_workspace_size(int64_t, int32_t, int32_t, int32_t) { return 0; }
+size_t fcfs_adjoint_workspace_size(int64_t V, int32_t T, int32_t K, int32_t prec) {
+  (void)prec;
+  AdjPlan ap;
+  if (make_adj_plan(V, T, K, ap) != FCFS_OK) return 0;
+  return ap.total;
+}
 
-fcfs_status fcfs_adjoint(const int32_t*, const int32_t*, const int8_t*, int64_t, int32_t, int32_t, int32_t,
-                         const float*, float*, float*, void*, size_t, void*) {
-  return FCFS_EUNSUPPORTED;
+fcfs_status fcfs_adjoint(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, int32_t T, int32_t K,
+                         int32_t prec, const float* dF, float* gx, float* gy, void* workspace, size_t ws_bytes,
+                         void* stream) {
+  return adjoint_impl(x, y, s, V, T, K, prec, dF, gx, gy, workspace, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 
 size_t fcfs_batch_workspace_size(int64_t, int32_t, int32_t, int32_t, int32_t) { return 0; }

@@ -145,3 +145,47 @@ def profile_read():
     buf = (C.c_float * 4)()
     n = _lib.load().fcfs_profile_read(buf, 4)
     return [float(buf[i]) for i in range(n)]
+
+
+def vertices_from_edges(pos, ev0, ev1, eaxis, V):
+    """Integer corner coordinates from edge positions: a vertical edge (axis 0)
+    gives the x of both its corners, a horizontal edge (axis 1) their y."""
+    p = torch.round(pos).to(torch.int32)
+    vert = eaxis == 0
+    x = torch.empty(V, dtype=torch.int32, device=pos.device)
+    y = torch.empty(V, dtype=torch.int32, device=pos.device)
+    for ends in (ev0, ev1):
+        x[ends[vert].long()] = p[vert]
+        y[ends[~vert].long()] = p[~vert]
+    return x, y
+
+
+class BlockFunction(torch.autograd.Function):
+    """F(k,l) of a clip as a differentiable function of its edge positions.
+
+    forward(pos, ev0, ev1, eaxis, s, T, K, prec) -> complex64 (2K+1, 2K+1).
+    `pos` holds lattice-valued edge positions (float); the block is evaluated at
+    those integer positions and the gradient is the exact derivative of the
+    continuous transform with respect to each edge position (both corners of an
+    edge move together), computed by the adjoint kernels and edge chaining.
+    """
+
+    @staticmethod
+    def forward(ctx, pos, ev0, ev1, eaxis, s, T, K, prec="fp32"):
+        x, y = vertices_from_edges(pos, ev0, ev1, eaxis, s.numel())
+        F, _ = forward(x, y, s, T, K, prec=prec)
+        ctx.save_for_backward(x, y, s, ev0, ev1, eaxis)
+        ctx.T, ctx.K, ctx.prec = int(T), int(K), prec
+        return F
+
+    @staticmethod
+    def backward(ctx, gF):
+        x, y, s, ev0, ev1, eaxis = ctx.saved_tensors
+        gx, gy = adjoint(x, y, s, ctx.T, ctx.K, gF.contiguous(), prec=ctx.prec)
+        gE = edge_chain(gx, gy, ev0, ev1, eaxis)
+        return gE, None, None, None, None, None, None, None
+
+
+def block(pos, ev0, ev1, eaxis, s, T, K, prec="fp32"):
+    """Differentiable block of a clip from its edge positions (see BlockFunction)."""
+    return BlockFunction.apply(pos, ev0, ev1, eaxis, s, T, K, prec)

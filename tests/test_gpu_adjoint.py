@@ -1,0 +1,120 @@
+"""Adjoint (corner and edge derivatives) on the GPU against the FP64 oracle.
+
+Error measure: max_v |g_gpu - g_oracle| / max_v |g_oracle| over all corners (and
+over all edges for the chained derivative).  The FP32 adjoint sums (2K+2)-term
+FP32 dot products per row and a compensated sum over row tiles; the bound 1e-5
+leaves a factor of ~10 over the measured error.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import config_clip, config4_target, make_clip
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def fc():
+    from paper_1010_5562_gb300 import build as B
+    B.build()
+    from paper_1010_5562_gb300 import fcfs
+    assert torch.cuda.is_available()
+    return fcfs
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_grad(fc, clip, K, G):
+    x, y, s = dev(clip.x), dev(clip.y), dev(clip.s)
+    dF = torch.from_numpy(G.astype(np.complex64)).cuda()
+    gx, gy = fc.adjoint(x, y, s, clip.T, K, dF)
+    torch.cuda.synchronize()
+    return gx.cpu().numpy().astype(np.float64), gy.cpu().numpy().astype(np.float64)
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("K", [1, 7, 40, 64, 100])
+def test_random_cotangent(fc, K):
+    clip = make_clip(512, 30, 700 + K, smin=6, smax=40)
+    rng = np.random.default_rng(K)
+    W = 2 * K + 1
+    G = rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))
+    gx, gy = gpu_grad(fc, clip, K, G)
+    rx, ry = oracle.vertex_gradient(clip.x, clip.y, clip.s, clip.T, K, G)
+    assert rel(gx, rx) < TOL and rel(gy, ry) < TOL, (rel(gx, rx), rel(gy, ry))
+
+
+def test_config4_pupil_loss_gradient(fc):
+    """Workload 4: T=2048, ~31.7k corners, K=128, L = sum over k^2+l^2 <= K^2 of
+    |F - F_target|^2 with the target's edges jittered by U{-2..2}."""
+    clip, K = config_clip(4)
+    tgt, _ = config4_target(clip)
+    T = clip.T
+    F = oracle.block(clip.x, clip.y, clip.s, T, K)
+    Ft = oracle.block(tgt.x, tgt.y, tgt.s, T, K)
+    _, G = oracle.pupil_loss(F, Ft, K)
+    gx, gy = gpu_grad(fc, clip, K, G)
+    rx, ry = oracle.vertex_gradient(clip.x, clip.y, clip.s, T, K, G)
+    assert rel(gx, rx) < TOL and rel(gy, ry) < TOL, (rel(gx, rx), rel(gy, ry))
+    # chained to edge positions on the GPU
+    gE = fc.edge_chain(dev(gx.astype(np.float32)), dev(gy.astype(np.float32)), dev(clip.ev0), dev(clip.ev1),
+                       dev(clip.eaxis))
+    rE = oracle.edge_gradient(rx, ry, clip.ev0, clip.ev1, clip.eaxis)
+    assert rel(gE.cpu().numpy().astype(np.float64), rE) < TOL
+
+
+def test_autograd_edge_gradient_and_finite_differences(fc):
+    """Edge gradients through torch.autograd match the oracle, and a +-1 move of
+    an edge changes the GPU loss by the predicted amount."""
+    clip, K = config_clip(4, scale=0.05)
+    tgt, _ = config4_target(clip)
+    T = clip.T
+    ev0, ev1, eaxis, s = dev(clip.ev0), dev(clip.ev1), dev(clip.eaxis), dev(clip.s)
+    mask = torch.from_numpy(oracle.pupil_mask(K)).cuda()
+    Ft, _ = fc.forward(dev(tgt.x), dev(tgt.y), s, T, K, prec="fp32")
+    pos = torch.from_numpy(clip.edge_positions().astype(np.float32)).cuda().requires_grad_(True)
+    F = fc.block(pos, ev0, ev1, eaxis, s, T, K)
+    L = ((F - Ft).abs() ** 2 * mask).sum()
+    L.backward()
+    gE = pos.grad.cpu().numpy().astype(np.float64)
+    Fo = oracle.block(clip.x, clip.y, clip.s, T, K)
+    Fto = oracle.block(tgt.x, tgt.y, tgt.s, T, K)
+    _, G = oracle.pupil_loss(Fo, Fto, K)
+    rx, ry = oracle.vertex_gradient(clip.x, clip.y, clip.s, T, K, G)
+    rE = oracle.edge_gradient(rx, ry, clip.ev0, clip.ev1, clip.eaxis)
+    assert rel(gE, rE) < 1e-4     # includes the FP32 forward error of F in the cotangent
+
+    def loss_at(p):
+        with torch.no_grad():
+            Fp = fc.block(p, ev0, ev1, eaxis, s, T, K)
+            return float(((Fp - Ft).abs().double() ** 2 * mask).sum())
+
+    base = pos.detach().clone()
+    worst = 0.0
+    for e in range(0, clip.ev0.shape[0], max(1, clip.ev0.shape[0] // 12)):
+        pp, pm = base.clone(), base.clone()
+        pp[e] += 1.0
+        pm[e] -= 1.0
+        fd = (loss_at(pp) - loss_at(pm)) / 2.0
+        worst = max(worst, abs(fd - gE[e]) / np.max(np.abs(gE)))
+    # a unit central difference of a smooth function of the edge position;
+    # its truncation error (third derivative) bounds the agreement
+    assert worst < 2e-2, worst
+
+
+def test_edge_chain_empty_and_direct(fc):
+    gx = torch.tensor([1.0, 2.0, 3.0, 4.0], device="cuda")
+    gy = torch.tensor([10.0, 20.0, 30.0, 40.0], device="cuda")
+    ev0 = torch.tensor([0, 1, 2, 3], dtype=torch.int32, device="cuda")
+    ev1 = torch.tensor([1, 2, 3, 0], dtype=torch.int32, device="cuda")
+    ax = torch.tensor([1, 0, 1, 0], dtype=torch.int8, device="cuda")
+    gE = fc.edge_chain(gx, gy, ev0, ev1, ax).cpu().tolist()
+    assert gE == [30.0, 5.0, 70.0, 5.0]
