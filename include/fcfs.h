@@ -138,8 +138,9 @@ fcfs_status fcfs_edge_chain(const float* gx, const float* gy, const int32_t* ev0
  *                offsets[n_clips] = V_total, non-decreasing.
  *   F_out      : n_clips * (2K+1)^2 complex64 (device), clip-major.
  *   area_out   : n_clips int64 (device).
- * One persistent kernel walks a device-built work list of (clip, tile, vertex
- * range) units, so the call is capturable in a CUDA graph (no host sync).
+ * A device-built list of (clip, output tile, vertex range) units is covered
+ * by one launch of the contraction kernel, so the call needs no host
+ * synchronisation and can be captured in a CUDA graph.  flags must be 0.
  * Workspace sized by fcfs_batch_workspace_size(V_total, n_clips, ...).
  */
 size_t fcfs_batch_workspace_size(int64_t V_total, int32_t n_clips, int32_t T, int32_t K,
@@ -176,7 +177,7 @@ fcfs_status fcfs_forward_noalloc(const int32_t* x, const int32_t* y, const int8_
                                  float* F_out, int64_t* area_out, void* stream);
 
 /*
- * Measurement hooks.  fcfs_profile_enable(1) makes every later call bracket
+ * Measurement and tuning hooks.  fcfs_profile_enable(1) makes every later call bracket
  * each of its stages with CUDA events on the caller's stream; after a call,
  * fcfs_profile_read() waits for the last event and writes up to n stage
  * durations in milliseconds (0: prep/tables, 1: area and axis lines,
@@ -187,6 +188,11 @@ fcfs_status fcfs_forward_noalloc(const int32_t* x, const int32_t* y, const int8_
 void fcfs_profile_enable(int32_t on);
 int32_t fcfs_profile_read(float* ms, int32_t n);
 void fcfs_debug_set_splits(int32_t n);
+
+/* Vertex-split granularity of fcfs_batch: n pipeline chunks (64 corners on the
+ * tensor path, 32 on the FP32 path) per unit; 0 restores the default of 4096
+ * corners.  Process-wide; the autotuner sets it per workload. */
+void fcfs_set_batch_unit_chunks(int32_t n);
 
 /*
  * Synchronise `stream` and return the device status word of the last call that

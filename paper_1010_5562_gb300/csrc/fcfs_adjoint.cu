@@ -330,11 +330,5 @@ fcfs_status fcfs_adjoint(const int32_t* x, const int32_t* y, const int8_t* s, in
   return adjoint_impl(x, y, s, V, T, K, prec, dF, gx, gy, workspace, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 
-size_t fcfs_batch_workspace_size(int64_t, int32_t, int32_t, int32_t, int32_t) { return 0; }
-
-fcfs_status fcfs_batch(const int32_t*, const int32_t*, const int8_t*, const int64_t*, int32_t, int64_t, int32_t,
-                       int32_t, int32_t, uint32_t, float*, int64_t*, void*, size_t, void*) {
-  return FCFS_EUNSUPPORTED;
-}
 
 }  // extern "C"

@@ -1,0 +1,126 @@
+// Batch of clips sharing T and K in one pass of the forward kernels.
+//
+// Tiles of a layout are independent (Sec. III-A), so a batch is a list of
+// units (clip, output tile, vertex split): clip c of V_c corners contributes
+// tiles * ceil(V_c / U) units of at most U corners.  The list is built on the
+// device from the device offsets (one block scans the per-clip unit counts),
+// so the call needs no host synchronisation and can be captured in a CUDA
+// graph.  One launch of the contraction kernel covers every unit (its grid is
+// the host-side bound on the unit count; blocks past the actual count exit at
+// once), the axis kernel keeps per-clip integer sums, and the reduce kernel
+// sums each clip's splits.  U is tunable (fcfs_set_batch_unit_chunks).
+#include <algorithm>
+
+#include "fcfs_common.cuh"
+
+namespace fcfs {
+
+fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl);
+fcfs_status check_ws(const Plan& pl, void* ws, size_t ws_bytes);
+bool make_vertex_maps(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, VertexMaps& mp);
+
+static int g_unit_chunks = 0;   // 0: default (4096 corners per unit)
+
+static fcfs_status make_batch_plan(int64_t V, int32_t n, int32_t T, int32_t K, int32_t prec, const int64_t* offsets,
+                                   Plan& pl) {
+  if (n < 1) return FCFS_EINVAL;
+  fcfs_status r = make_plan(V, T, K, prec, pl);
+  if (r != FCFS_OK) return r;
+  pl.batch = 1;
+  pl.n_clips = n;
+  pl.offsets = offsets;
+  const int chunks = g_unit_chunks > 0 ? g_unit_chunks : 4096 / pl.chunk;
+  pl.unit_vertices = (int64_t)chunks * pl.chunk;
+  const long long tiles = (long long)pl.tiles_m * pl.tiles_n;
+  const long long units_max = tiles * ((V + pl.unit_vertices - 1) / pl.unit_vertices + n);
+  if (units_max >= (1LL << 31)) return FCFS_EUNSUPPORTED;
+  pl.splits = (int)units_max;   // grid of the contraction kernel
+  size_t o = pl.off_axis;       // tables stay where the single-clip plan put them
+  o = align_up(o + (size_t)n * (4 * K + 1) * sizeof(long long), kWsAlign);
+  pl.off_hist = o;
+  pl.off_units = o;
+  o = align_up(o + (size_t)(n + 1) * sizeof(int), kWsAlign);
+  pl.off_part = o;
+  o = align_up(o + (size_t)units_max * pl.bm * pl.bn * sizeof(float), kWsAlign);
+  pl.total = o;
+  return FCFS_OK;
+}
+
+// unit_start[c] = sum over clips c' < c of tiles * ceil(V_c' / U); unit_start[n] = total
+__global__ void __launch_bounds__(1024) batch_units_kernel(Plan pl, uint8_t* ws) {
+  int* ustart = reinterpret_cast<int*>(ws + pl.off_units);
+  const int n = pl.n_clips, tiles = pl.tiles_m * pl.tiles_n;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int c0 = min(n, (int)threadIdx.x * per), c1 = min(n, c0 + per);
+  auto units = [&](int c) {
+    const long long vc = pl.offsets[c + 1] - pl.offsets[c];
+    return tiles * (int)((vc + pl.unit_vertices - 1) / pl.unit_vertices);
+  };
+  int local = 0;
+  for (int c = c0; c < c1; ++c) local += units(c);
+  __shared__ int scan[1024];
+  scan[threadIdx.x] = local;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {   // inclusive scan
+    const int v = threadIdx.x >= (unsigned)off ? scan[threadIdx.x - off] : 0;
+    __syncthreads();
+    scan[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = scan[threadIdx.x] - local;
+  for (int c = c0; c < c1; ++c) {
+    ustart[c] = run;
+    run += units(c);
+  }
+  if (threadIdx.x == blockDim.x - 1) ustart[n] = scan[threadIdx.x];
+}
+
+static fcfs_status batch_impl(const int32_t* x, const int32_t* y, const int8_t* s, const int64_t* offsets,
+                              int32_t n, int64_t V, int32_t T, int32_t K, int32_t prec, uint32_t flags, float* F,
+                              int64_t* area, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (!F || !area || !offsets || n < 1) return FCFS_EINVAL;
+  if (flags != 0) return FCFS_EUNSUPPORTED;   // device validation is offered for single clips
+  const auto aligned16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (V > 0 && (!x || !y || !s || !aligned16(x) || !aligned16(y) || !aligned16(s))) return FCFS_EINVAL;
+  Plan pl;
+  fcfs_status r = make_batch_plan(V, n, T, K, prec, offsets, pl);
+  if (r != FCFS_OK) return r;
+  if ((r = check_ws(pl, ws, ws_bytes)) != FCFS_OK) return r;
+  VertexMaps mp;
+  if (prec == FCFS_PREC_SPLIT_F16 && V > 0 && !make_vertex_maps(x, y, s, V, mp)) return FCFS_ECUDA;
+  if (launch_prep(pl, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
+  batch_units_kernel<<<1, 1024, 0, st>>>(pl, static_cast<uint8_t*>(ws));
+  count_launch(1);
+  if (cudaGetLastError() != cudaSuccess) return FCFS_ECUDA;
+  if (launch_axis(pl, x, y, s, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
+  if (V > 0) {
+    const cudaError_t e = prec == FCFS_PREC_SPLIT_F16 ? launch_gemm_tc(pl, mp, ws, st)
+                                                       : launch_gemm_simt(pl, x, y, s, ws, st);
+    if (e != cudaSuccess) return FCFS_ECUDA;
+  }
+  if (launch_reduce(pl, ws, F, area, false, st) != cudaSuccess) return FCFS_ECUDA;
+  return FCFS_OK;
+}
+
+}  // namespace fcfs
+
+using namespace fcfs;
+
+extern "C" {
+
+size_t fcfs_batch_workspace_size(int64_t V_total, int32_t n_clips, int32_t T, int32_t K, int32_t prec) {
+  Plan pl;
+  if (make_batch_plan(V_total, n_clips, T, K, prec, nullptr, pl) != FCFS_OK) return 0;
+  return pl.total;
+}
+
+fcfs_status fcfs_batch(const int32_t* x, const int32_t* y, const int8_t* s, const int64_t* offsets, int32_t n_clips,
+                       int64_t V_total, int32_t T, int32_t K, int32_t prec, uint32_t flags, float* F_out,
+                       int64_t* area_out, void* workspace, size_t ws_bytes, void* stream) {
+  return batch_impl(x, y, s, offsets, n_clips, V_total, T, K, prec, flags, F_out, area_out, workspace, ws_bytes,
+                    static_cast<cudaStream_t>(stream));
+}
+
+void fcfs_set_batch_unit_chunks(int32_t n) { g_unit_chunks = n > 0 ? n : 0; }
+
+}  // extern "C"

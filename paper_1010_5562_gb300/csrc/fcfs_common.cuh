@@ -32,7 +32,62 @@ struct Plan {
   int64_t split_len;   // vertices per split, a multiple of chunk
   size_t off_status, off_tab_f32, off_tab_fix, off_axis, off_hist, off_part, total;
   uint64_t tag;        // identifies the tables cached in this workspace layout
+  // batch mode (several clips): the contraction kernels walk units
+  // (clip, tile, vertex split) instead of (tile, split)
+  int32_t batch;               // 0: one clip; 1: batch
+  int32_t n_clips;
+  int64_t unit_vertices;       // vertices per unit (a multiple of chunk)
+  const int64_t* offsets;      // device, n_clips + 1
+  size_t off_units;            // int32 unit_start[n_clips + 1] in the workspace
 };
+
+// Work of one CTA of a contraction kernel: output tile, vertex range, and
+// where its FP32 partial tile goes (base and row stride).
+struct Unit {
+  int tm, tn;
+  long long v0, v1;
+  float* P;
+  int ld;
+  bool live;
+};
+
+// Single clip: blockIdx = (tile, split); batch: blockIdx.x = unit index.
+__device__ inline Unit unit_of_block(const Plan& pl, uint8_t* ws, int bm, int bn) {
+  Unit u;
+  float* part = reinterpret_cast<float*>(ws + pl.off_part);
+  if (!pl.batch) {
+    const int tile = blockIdx.x, split = blockIdx.y;
+    u.tm = tile / pl.tiles_n;
+    u.tn = tile % pl.tiles_n;
+    u.v0 = (long long)split * pl.split_len;
+    u.v1 = min((long long)pl.V, u.v0 + pl.split_len);
+    u.ld = pl.M2;
+    u.P = part + (size_t)split * pl.M2 * pl.M2 + (size_t)u.tm * bm * pl.M2 + (size_t)u.tn * bn;
+    u.live = true;
+    return u;
+  }
+  const int* ustart = reinterpret_cast<const int*>(ws + pl.off_units);
+  const int uid = blockIdx.x;
+  u.live = uid < ustart[pl.n_clips];
+  if (!u.live) return u;
+  int lo = 0, hi = pl.n_clips;   // last clip c with ustart[c] <= uid
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (ustart[mid] <= uid) lo = mid; else hi = mid;
+  }
+  const int c = lo;
+  const long long cv0 = pl.offsets[c], cv1 = pl.offsets[c + 1];
+  const int S = (int)((cv1 - cv0 + pl.unit_vertices - 1) / pl.unit_vertices);
+  const int r = uid - ustart[c];
+  const int tile = r / S, sp = r % S;
+  u.tm = tile / pl.tiles_n;
+  u.tn = tile % pl.tiles_n;
+  u.v0 = cv0 + (long long)sp * pl.unit_vertices;
+  u.v1 = min(cv1, u.v0 + pl.unit_vertices);
+  u.ld = bn;
+  u.P = part + (size_t)uid * bm * bn;
+  return u;
+}
 
 // Workspace header: the status word of the last call, then the table tag.
 constexpr size_t kTagOffset = 8;

@@ -33,7 +33,8 @@ __global__ void prep_kernel(Plan pl, uint8_t* ws, int validate) {
     st->detail = 0;
   }
   long long* acc = reinterpret_cast<long long*>(ws + pl.off_axis);
-  for (long long i = gid; i < 4LL * pl.K + 1; i += gsz) acc[i] = 0;
+  const long long nacc = (4LL * pl.K + 1) * (pl.batch ? pl.n_clips : 1);
+  for (long long i = gid; i < nacc; i += gsz) acc[i] = 0;
   if (validate) {
     int* hist = reinterpret_cast<int*>(ws + pl.off_hist);
     for (long long i = gid; i < 2LL * (T + 1); i += gsz) hist[i] = 0;
@@ -101,7 +102,8 @@ __device__ __forceinline__ int3 decimate(int a, int T, int logT) {
 }
 
 size_t axis_smem_bytes(int T, int full) {
-  return (full ? (size_t)2 * T * 8 : tab_fix_bytes(T, 0)) + 8 * kAxisStage * sizeof(int);
+  return (full ? (size_t)2 * T * 8 : tab_fix_bytes(T, 0)) + 9 * kAxisStage * sizeof(int) +
+         kAxisStage * sizeof(long long);
 }
 
 template <bool FULL>
@@ -114,6 +116,8 @@ __global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32
   const size_t tb = tab_fix_bytes(T, FULL);
   const size_t tall = FULL ? (size_t)2 * T * 8 : tb;
   int* sv = reinterpret_cast<int*>(sm + tall);   // per staged vertex: 8 ints
+  int* sclip = sv + 8 * kAxisStage;              // per staged vertex: clip index
+  long long* sarea = reinterpret_cast<long long*>(sclip + kAxisStage);   // s x y
   __shared__ uint64_t tbar;
   Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
   if (threadIdx.x == 0) {
@@ -140,12 +144,38 @@ __global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32
   const long long v1 = min((long long)pl.V, v0 + vper);
   long long a0 = 0, a1 = 0, a2 = 0, a3 = 0, area = 0;
   int* hist = reinterpret_cast<int*>(ws + pl.off_hist);
+  long long* acc = reinterpret_cast<long long*>(ws + pl.off_axis);
+  const int A = 4 * pl.K + 1;   // accumulators per clip
+  int cur = -1;                 // clip of the running sums
+  auto flush = [&](int c) {
+    long long* ac = acc + (size_t)c * A;
+    if (k <= pl.K) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&ac[k - 1]), (unsigned long long)a0);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&ac[pl.K + k - 1]), (unsigned long long)a1);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&ac[2 * pl.K + k - 1]), (unsigned long long)a2);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&ac[3 * pl.K + k - 1]), (unsigned long long)a3);
+    }
+    if (blockIdx.y == 0 && threadIdx.x == 0 && area != 0)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&ac[4 * pl.K]), (unsigned long long)area);
+    a0 = a1 = a2 = a3 = area = 0;
+  };
   for (long long b = v0; b < v1; b += kAxisStage) {
     const int n = (int)min((long long)kAxisStage, v1 - b);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const int xv = x[b + i], yv = y[b + i], sgn = s[b + i];
       int* e = sv + 8 * i;
+      int c = 0;
+      if (pl.batch) {   // last clip whose first vertex is <= b + i
+        int lo = 0, hi = pl.n_clips;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (pl.offsets[mid] <= b + i) lo = mid; else hi = mid;
+        }
+        c = lo;
+      }
+      sclip[i] = c;
+      sarea[i] = (long long)sgn * xv * (long long)yv;
       if (FULL) {
         const int3 dx = decimate(xv, T, pl.logT), dy = decimate(yv, T, pl.logT);
         e[0] = dx.x; e[1] = dx.y; e[2] = dx.z; e[3] = sgn * yv;
@@ -154,7 +184,6 @@ __global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32
         e[0] = xv; e[1] = sgn * yv; e[4] = yv; e[5] = sgn * xv;
       }
       if (blockIdx.y == 0) {
-        area += (long long)sgn * xv * (long long)yv;
         if (validate) {
           const bool ok = xv >= 0 && xv <= T && yv >= 0 && yv <= T && (sgn == 1 || sgn == -1);
           if (!ok) {
@@ -167,10 +196,16 @@ __global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32
       }
     }
     __syncthreads();
-    if (k <= pl.K) {
+    {
       const int2* t2 = reinterpret_cast<const int2*>(sm);
+      const bool act = k <= pl.K;
 #pragma unroll 4
       for (int i = 0; i < n; ++i) {
+        if (sclip[i] != cur) {   // block-uniform: the clips of the staged vertices
+          if (cur >= 0) flush(cur);
+          cur = sclip[i];
+        }
+        if (!act) continue;
         const int4 ex = reinterpret_cast<const int4*>(sv + 8 * i)[0];
         const int4 ey = reinterpret_cast<const int4*>(sv + 8 * i)[1];
         int2 tx, ty;
@@ -190,21 +225,12 @@ __global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32
         a1 += (long long)tx.y * wy;
         a2 += (long long)ty.x * wx;
         a3 += (long long)ty.y * wx;
+        // the area sum_v s x y rides on thread 0 of the first k-block
+        if (threadIdx.x == 0 && blockIdx.y == 0) area += sarea[i];
       }
     }
   }
-  long long* acc = reinterpret_cast<long long*>(ws + pl.off_axis);
-  if (k <= pl.K) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[k - 1]), (unsigned long long)a0);
-    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[pl.K + k - 1]), (unsigned long long)a1);
-    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[2 * pl.K + k - 1]), (unsigned long long)a2);
-    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[3 * pl.K + k - 1]), (unsigned long long)a3);
-  }
-  if (blockIdx.y == 0) {
-    for (int o = 16; o > 0; o >>= 1) area += __shfl_xor_sync(0xffffffffu, area, o);
-    if ((threadIdx.x & 31) == 0 && area != 0)
-      atomicAdd(reinterpret_cast<unsigned long long*>(&acc[4 * pl.K]), (unsigned long long)area);
-  }
+  if (cur >= 0) flush(cur);
 }
 
 // ---------------------------------------------------------------------------
@@ -245,11 +271,14 @@ __global__ void reduce_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, long
     for (int i = threadIdx.x; i < 2 * (pl.T + 1); i += blockDim.x)
       if (hist[i] != 0) set_status(st, FCFS_EINVAL_DATA, 0x80000000u | (unsigned)i);
   }
-  if (idx == 0) *reinterpret_cast<unsigned long long*>(ws + kTagOffset) = pl.tag;
+  if (idx == 0 && blockIdx.y == 0) *reinterpret_cast<unsigned long long*>(ws + kTagOffset) = pl.tag;
   if (idx >= n1 * n1) return;
+  const int clip = blockIdx.y;   // 0 for a single clip
+  F += (size_t)clip * W * W;
+  area_out += clip;
   const int k = (int)(idx / n1), l = (int)(idx % n1);
   const double T = (double)pl.T;
-  const long long* acc = reinterpret_cast<const long long*>(ws + pl.off_axis);
+  const long long* acc = reinterpret_cast<const long long*>(ws + pl.off_axis) + (size_t)clip * (4 * K + 1);
   const double inv = ldexp(1.0, -pl.fixq);
   if (k == 0 && l == 0) {
     const long long a = acc[4 * K];
@@ -274,24 +303,42 @@ __global__ void reduce_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, long
     return;
   }
   const int M2 = pl.M2;
-  const size_t plane = (size_t)M2 * M2;
   const float* P = reinterpret_cast<const float*>(ws + pl.off_part);
-  const size_t o0 = (size_t)(2 * (k - 1)) * M2 + 2 * (l - 1);
+  // where split sp of entry (k, l) lives: single clip, P[sp][m][n]; batch,
+  // the unit's own bm x bn tile
+  const int m = 2 * (k - 1), n = 2 * (l - 1);
+  size_t base, stride, ld;
+  int S;
+  if (!pl.batch) {
+    S = pl.splits;
+    base = (size_t)m * M2 + n;
+    stride = (size_t)M2 * M2;
+    ld = M2;
+  } else {
+    const int* ustart = reinterpret_cast<const int*>(ws + pl.off_units);
+    const long long vc = pl.offsets[clip + 1] - pl.offsets[clip];
+    S = (int)((vc + pl.unit_vertices - 1) / pl.unit_vertices);
+    const int tm = m / pl.bm, tn = n / pl.bn;
+    const size_t u0 = (size_t)ustart[clip] + (size_t)(tm * pl.tiles_n + tn) * S;
+    base = u0 * pl.bm * pl.bn + (size_t)(m - tm * pl.bm) * pl.bn + (n - tn * pl.bn);
+    stride = (size_t)pl.bm * pl.bn;
+    ld = pl.bn;
+  }
   CSum cc{0.f, 0.f}, cs{0.f, 0.f}, sc{0.f, 0.f}, ss{0.f, 0.f};
   // issue a whole batch of split loads before the dependent sums (latency bound otherwise)
   constexpr int kBatch = 8;
-  for (int sp0 = 0; sp0 < pl.splits; sp0 += kBatch) {
+  for (int sp0 = 0; sp0 < S; sp0 += kBatch) {
     float2 r0[kBatch], r1[kBatch];
 #pragma unroll
     for (int b = 0; b < kBatch; ++b) {
-      if (sp0 + b < pl.splits) {
-        r0[b] = __ldcs(reinterpret_cast<const float2*>(P + (size_t)(sp0 + b) * plane + o0));
-        r1[b] = __ldcs(reinterpret_cast<const float2*>(P + (size_t)(sp0 + b) * plane + o0 + M2));
+      if (sp0 + b < S) {
+        r0[b] = __ldcs(reinterpret_cast<const float2*>(P + base + (size_t)(sp0 + b) * stride));
+        r1[b] = __ldcs(reinterpret_cast<const float2*>(P + base + (size_t)(sp0 + b) * stride + ld));
       }
     }
 #pragma unroll
     for (int b = 0; b < kBatch; ++b) {
-      if (sp0 + b < pl.splits) {
+      if (sp0 + b < S) {
         csum_add(cc, r0[b].x);
         csum_add(cs, r0[b].y);
         csum_add(sc, r1[b].x);
@@ -320,7 +367,7 @@ __global__ void reduce_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, long
 cudaError_t launch_prep(const Plan& pl, void* ws, bool validate, cudaStream_t st) {
   // one thread per table entry on a cold workspace (the FP64 cospi is the cost)
   long long work = pl.full ? pl.T : pl.T / 4 + 1;
-  work = max(work, 4LL * pl.K + 1);
+  work = max(work, (4LL * pl.K + 1) * (pl.batch ? pl.n_clips : 1));
   if (validate) work = max(work, 2LL * (pl.T + 1));
   int blocks = (int)min((work + 63) / 64, 2048LL);
   // every kernel of a call asks for the largest shared-memory carveout, so the
@@ -361,7 +408,7 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
 
 cudaError_t launch_reduce(const Plan& pl, void* ws, float* F, int64_t* area, bool validate, cudaStream_t st) {
   const long long n = (long long)(pl.K + 1) * (pl.K + 1);
-  const int blocks = (int)((n + 255) / 256);
+  const dim3 blocks((unsigned)((n + 255) / 256), pl.batch ? pl.n_clips : 1);
   cudaFuncSetAttribute(reduce_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   reduce_kernel<<<blocks, 256, 0, st>>>(pl, static_cast<uint8_t*>(ws), reinterpret_cast<float2*>(F),
                                         reinterpret_cast<long long*>(area), validate ? 1 : 0);

@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(kSThreads, 2) gemm_simt_kernel(Plan pl, const 
 
   const int tid = threadIdx.x;
   __shared__ uint64_t tbar;
+  if (pl.batch && blockIdx.x >= reinterpret_cast<const int*>(ws + pl.off_units)[pl.n_clips]) return;
   Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
   if (tid == 0) {   // the table arrives by one bulk copy
     mbar_init(&tbar, 1);
@@ -42,12 +43,12 @@ __global__ void __launch_bounds__(kSThreads, 2) gemm_simt_kernel(Plan pl, const 
   }
   __syncthreads();
   mbar_wait(&tbar, 0, st, 21);
-  const int tile = blockIdx.x, split = blockIdx.y;
-  const int tm = tile / pl.tiles_n, tn = tile % pl.tiles_n;
+  const Unit U = unit_of_block(pl, ws, kSB, kSB);
+  if (!U.live) return;
+  const int tm = U.tm, tn = U.tn;
   const int kbase = tm * (kSB / 2) + 1;    // first k of the tile's rows
   const int lbase = tn * (kSB / 2) + 1;
-  const long long v0 = (long long)split * pl.split_len;
-  const long long v1 = min((long long)pl.V, v0 + pl.split_len);
+  const long long v0 = U.v0, v1 = U.v1;
   const uint32_t mask = (uint32_t)pl.T - 1u;
   const uint32_t logQ = (uint32_t)pl.logT - 2u;
 
@@ -99,16 +100,17 @@ __global__ void __launch_bounds__(kSThreads, 2) gemm_simt_kernel(Plan pl, const 
   }
 
   // epilogue: rows ty*4 + r (r < 4) and 64 + ty*4 + r - 4; columns likewise with tx
-  float* P = reinterpret_cast<float*>(ws + pl.off_part) + (size_t)split * pl.M2 * pl.M2;
   const int M2 = pl.M2;
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
-    const int m = tm * kSB + (r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4);
+    const int mr = r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4;
+    const int m = tm * kSB + mr;
     if (m >= M2) continue;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int n = tn * kSB + h * 64 + tx * 4;
-      float* dst = P + (size_t)m * M2 + n;
+      const int nr = h * 64 + tx * 4;
+      const int n = tn * kSB + nr;
+      float* dst = U.P + (size_t)mr * U.ld + nr;
       if (n + 3 < M2 && (M2 & 3) == 0) {
         *reinterpret_cast<float4*>(dst) =
             make_float4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
@@ -124,7 +126,7 @@ cudaError_t launch_gemm_simt(const Plan& pl, const int32_t* x, const int32_t* y,
                              cudaStream_t st) {
   if (pl.splits == 0) return cudaSuccess;
   const size_t smem = tab_f32_bytes(pl.T, pl.full) + 2 * kSChunk * kSB * sizeof(float) + 3 * kSChunk * 4;
-  dim3 grid(pl.tiles_m * pl.tiles_n, pl.splits);
+  dim3 grid = pl.batch ? dim3(pl.splits, 1) : dim3(pl.tiles_m * pl.tiles_n, pl.splits);
   if (pl.full) {
     cudaFuncSetAttribute(gemm_simt_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(gemm_simt_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

@@ -108,10 +108,10 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
 
-  const int tile = blockIdx.x, split = blockIdx.y;
-  const int tm = tile / pl.tiles_n, tn = tile % pl.tiles_n;
-  const long long v0 = (long long)split * pl.split_len;
-  const long long v1 = min((long long)pl.V, v0 + pl.split_len);
+  const Unit U = unit_of_block(pl, ws, kBM, BN);
+  if (!U.live) return;   // unit slots beyond the batch's count: nothing allocated yet
+  const int tm = U.tm, tn = U.tn;
+  const long long v0 = U.v0, v1 = U.v1;
   const int nch = (int)((v1 - v0 + kCh - 1) / kCh);
 
   if (tid == GT + 32) {
@@ -296,7 +296,6 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
       __syncwarp();   // tcgen05.ld is warp-collective: reconverge after the per-thread branches
       tc_fence_after();
       const int M2 = pl.M2;
-      float* P = reinterpret_cast<float*>(ws + pl.off_part) + (size_t)split * M2 * M2;
       const int row = warp * 32 + lane;
       const int m = tm * kBM + row;
       if (acc_ok && nch > 0) {
@@ -308,7 +307,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
           tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), r);
           tmem_wait_ld();
           if (m < M2) {
-            float* dst = P + (size_t)m * M2 + n0;
+            float* dst = U.P + (size_t)row * U.ld + cb * 32;
             if (n0 + 32 <= M2 && (M2 & 3) == 0) {
 #pragma unroll
               for (int q = 0; q < 8; ++q)
@@ -322,7 +321,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
           }
         }
       } else if (m < M2) {
-        for (int n = tn * BN; n < min(M2, tn * BN + BN); ++n) P[(size_t)m * M2 + n] = 0.f;
+        for (int n = tn * BN; n < min(M2, tn * BN + BN); ++n) U.P[(size_t)row * U.ld + (n - tn * BN)] = 0.f;
       }
     }
   }
@@ -346,7 +345,7 @@ static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cud
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  dim3 grid(pl.tiles_m * pl.tiles_n, pl.splits);
+  dim3 grid = pl.batch ? dim3(pl.splits, 1) : dim3(pl.tiles_m * pl.tiles_n, pl.splits);
   kern<<<grid, TcLayout<BN, STAGES>::kThreads, smem, st>>>(mp.x, mp.y, mp.s, pl, static_cast<uint8_t*>(ws));
   count_launch(1);
   return cudaGetLastError();

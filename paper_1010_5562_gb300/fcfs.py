@@ -134,6 +134,11 @@ def set_splits(n):
     _lib.load().fcfs_debug_set_splits(int(n))
 
 
+def set_batch_unit_chunks(n):
+    """Vertex-split granularity of batch(): n pipeline chunks per unit (0: default)."""
+    _lib.load().fcfs_set_batch_unit_chunks(int(n))
+
+
 def profile_enable(on=True):
     """Bracket every stage of later calls with CUDA events (see profile_read)."""
     _lib.load().fcfs_profile_enable(1 if on else 0)

@@ -1,0 +1,111 @@
+"""Batch of clips on the GPU against the FP64 oracle, clip by clip.
+
+Same error measure and bounds as the single-clip forward (max |dF| / area per
+clip: 1e-6 plain FP32, 1e-5 split FP16; exact areas).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import make_clip, concat_clips, batch_clips, clip_from_rings, rect_ring
+
+pytestmark = pytest.mark.gpu
+TOL = {"fp32": 1e-6, "split_f16": 1e-5}
+PRECS = ["fp32", "split_f16"]
+
+
+@pytest.fixture(scope="module")
+def fc():
+    from paper_1010_5562_gb300 import build as B
+    B.build()
+    from paper_1010_5562_gb300 import fcfs
+    assert torch.cuda.is_available()
+    fcfs.set_batch_unit_chunks(0)
+    return fcfs
+
+
+def run_batch(fc, clips, K, prec):
+    x, y, s, off = concat_clips(clips)
+    d = [torch.from_numpy(a).cuda() for a in (x, y, s, off)]
+    F, area = fc.batch(d[0], d[1], d[2], d[3], clips[0].T, K, prec=prec)
+    torch.cuda.synchronize()
+    return F.cpu().numpy().astype(np.complex128), area.cpu().numpy()
+
+
+def check_clip(F, area, clip, K, prec):
+    A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+    assert int(area) == A
+    Fo = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    err = np.max(np.abs(F - Fo)) / max(A, 1)
+    assert err <= TOL[prec], err
+
+
+def small_batch():
+    empty = clip_from_rings(512, [rect_ring(1, 1, 2, 2)])
+    empty.x, empty.y, empty.s = empty.x[:0], empty.y[:0], empty.s[:0]
+    return [make_clip(512, n, 800 + n, smin=6, smax=40) for n in (3, 40, 1, 90, 17)] + \
+           [empty, make_clip(512, 60, 999, smin=6, smax=40)]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("chunks", [0, 1, 3])
+def test_small_batch_against_oracle(fc, prec, chunks):
+    clips = small_batch()
+    fc.set_batch_unit_chunks(chunks)
+    try:
+        F, area = run_batch(fc, clips, 40, prec)
+    finally:
+        fc.set_batch_unit_chunks(0)
+    for c, clip in enumerate(clips):
+        if clip.V == 0:
+            assert area[c] == 0 and not np.any(F[c])
+        else:
+            check_clip(F[c], area[c], clip, 40, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_matches_single_clip_calls(fc, prec):
+    clips = small_batch()[:5]
+    F, _ = run_batch(fc, clips, 40, prec)
+    for c, clip in enumerate(clips):
+        x, y, s = (torch.from_numpy(a).cuda() for a in (clip.x, clip.y, clip.s))
+        Fs, _ = fc.forward(x, y, s, clip.T, 40, prec=prec)
+        A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+        assert np.max(np.abs(F[c] - Fs.cpu().numpy())) / A <= 2 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_config3_full_batch(fc, prec):
+    """512 clips, T=2048, V_c log-uniform in [1e3, 1e5], K=128; a spread of clips
+    is checked against the oracle, every area exactly."""
+    clips, K = batch_clips()
+    F, area = run_batch(fc, clips, K, prec)
+    for c, clip in enumerate(clips):
+        assert int(area[c]) == oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+    order = np.argsort([cl.V for cl in clips])
+    for c in order[[0, 1, 128, 256, 384, 510, 511]]:
+        check_clip(F[c], area[c], clips[c], K, prec)
+
+
+def test_batch_in_cuda_graph(fc):
+    clips = small_batch()
+    x, y, s, off = (torch.from_numpy(a).cuda() for a in concat_clips(clips))
+    K, T = 40, clips[0].T
+    W = 2 * K + 1
+    F = torch.empty((len(clips), W, W), dtype=torch.complex64, device="cuda")
+    area = torch.empty((len(clips),), dtype=torch.int64, device="cuda")
+    ws = torch.empty(fc._lib.load().fcfs_batch_workspace_size(x.numel(), len(clips), T, K, 1),
+                     dtype=torch.uint8, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        fc.batch(x, y, s, off, T, K, out=F, area_out=area, workspace=ws, stream=st)   # warm-up
+    torch.cuda.synchronize()
+    ref = F.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        fc.batch(x, y, s, off, T, K, out=F, area_out=area, workspace=ws, stream=st)
+    F.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(F, ref)
