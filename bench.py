@@ -4,7 +4,7 @@
 Step: one forward block F(k,l), |k|,|l| <= 256, of the synthetic Manhattan clip
 T=4096 with 2000 polygons (~12.6k signed corners), through the C ABI on the
 split-FP16 tensor-core path: tables, exact area and axis lines, tcgen05
-contraction, FP64 split-K reduction and epilogue (four kernels).
+contraction, compensated split-K reduction and epilogue (four kernels).
 Metric: vertex-coefficient terms per second, V * (2K+1)^2 per step.
 
 Default run: N=1, warm-up 50, 5000 timed steps.  The clip's inputs are far
@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the adjoint, batch and large-clip measurements")
     return ap.parse_args()
 
 
@@ -358,13 +360,15 @@ def run_ours(args):
     e2e = {"value": world * n_terms / (statistics.mean(mse) * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": int(V * (4 + 4 + 1)), "d2h_bytes_per_step": int(W * W * 8 + 8)}
 
+    extras = {} if (world > 1 or args.no_extras) else run_extras(fcfs, dev, flush, stream, args)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16",
         "data": "synthetic (seeded Manhattan clip; stands in for the paper's proprietary 22 nm layout)",
         "config": {"workload": WORKLOAD, "precision": "split_f16 (hi+lo FP16 operands, FP32 accumulate, "
-                   "FP64 split-K sum)", "T": T, "K": K, "V": V,
+                   "TwoSum-compensated split-K sum)", "T": T, "K": K, "V": V,
                    "l2": "flushed before every timed step (256 MiB write, outside the events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline,
@@ -373,6 +377,9 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    for k in ("adjoint", "batch", "large"):
+        if k in extras:
+            line[k] = extras[k]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import numpy as np
         cb, Fo, A = cpu_baseline(clip, K, args.cpu_seconds)
@@ -386,11 +393,149 @@ def run_ours(args):
             errs[name] = float(np.max(np.abs(Fg - Fo)) / A)
         line["accuracy"] = {"max_abs_err_over_area": errs, "area_exact": int(area.item()) == A,
                             "reference": "FP64 oracle (direct signed-quadrant vertex sum)"}
+        if extras:
+            extras_accuracy(line, extras)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+# the other workloads: adjoint, batch, large clip (reported beside the step)
+# ---------------------------------------------------------------------------
+def _timed_ms(torch, fn, n, flush, stream):
+    fn()
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(n):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        out.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in out)
+
+
+def run_extras(fcfs, dev, flush, stream, args):
+    import numpy as np
+    import torch
+    from synth import config_clip, config4_target, batch_clips, concat_clips
+    from paper_1010_5562_gb300 import autotune
+    out = {}
+
+    # adjoint: workload 4, pupil loss, FP32
+    clip, K = config_clip(4)
+    tgt, _ = config4_target(clip)
+    T, W = clip.T, 2 * K + 1
+    x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))
+    F, _ = fcfs.forward(x, y, s, T, K, prec="fp32")
+    Ft, _ = fcfs.forward(*(torch.from_numpy(a).to(dev) for a in (tgt.x, tgt.y, tgt.s)), T, K, prec="fp32")
+    f = torch.arange(-K, K + 1, device=dev)
+    mask = ((f[:, None] ** 2 + f[None, :] ** 2) <= K * K)
+    G = (2.0 * (F - Ft) * mask).contiguous()
+    gx = torch.empty(clip.V, dtype=torch.float32, device=dev)
+    gy = torch.empty_like(gx)
+    wsa = torch.empty(fcfs._lib.load().fcfs_adjoint_workspace_size(clip.V, T, K, 0), dtype=torch.uint8, device=dev)
+    ms = _timed_ms(torch, lambda: fcfs.adjoint(x, y, s, T, K, G, gx=gx, gy=gy, workspace=wsa, stream=stream),
+                   20, flush, stream)
+    out["adjoint"] = {"workload": "clip T=2048, 5000 polygons, V=%d, K=128, pupil-disc loss vs edges "
+                                  "jittered +-2; corner derivatives, FP32" % clip.V,
+                      "value": clip.V * W * W / (ms * 1e-3), "unit": UNIT, "ms": ms,
+                      "_check": (clip, tgt, K, G.cpu().numpy(), gx.cpu().numpy(), gy.cpu().numpy())}
+
+    # batch: workload 3, one launch replayed from a CUDA graph vs one call per clip
+    clips, K = batch_clips()
+    T, W = clips[0].T, 2 * K + 1
+    bx, by, bs, boff = (torch.from_numpy(a).to(dev) for a in concat_clips(clips))
+    n = len(clips)
+    terms_b = float(sum(c.V for c in clips)) * W * W
+    uc = autotune.tune_batch(bx, by, bs, boff, T, K, prec="split_f16")
+    fcfs.set_batch_unit_chunks(uc)
+    Fb = torch.empty((n, W, W), dtype=torch.complex64, device=dev)
+    Ab = torch.empty(n, dtype=torch.int64, device=dev)
+    wsb = torch.empty(fcfs._lib.load().fcfs_batch_workspace_size(bx.numel(), n, T, K, 1), dtype=torch.uint8,
+                      device=dev)
+    cap = torch.cuda.Stream(dev)   # graphs are captured on a side stream
+    with torch.cuda.stream(cap):
+        fcfs.batch(bx, by, bs, boff, T, K, out=Fb, area_out=Ab, workspace=wsb, stream=cap)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cap):
+        fcfs.batch(bx, by, bs, boff, T, K, out=Fb, area_out=Ab, workspace=wsb, stream=cap)
+    ms_b = _timed_ms(torch, g.replay, 5, flush, stream)
+    fcfs.set_batch_unit_chunks(0)
+    per = [tuple(torch.from_numpy(a).to(dev) for a in (c.x, c.y, c.s)) for c in clips]
+    wsc = torch.empty(max(fcfs.workspace_size(c.V, T, K) for c in clips), dtype=torch.uint8, device=dev)
+    Fc = torch.empty((W, W), dtype=torch.complex64, device=dev)
+    Ac = torch.empty(1, dtype=torch.int64, device=dev)
+
+    def per_clip():
+        for (cx, cy, cs) in per:
+            fcfs.forward(cx, cy, cs, T, K, out=Fc, area_out=Ac, workspace=wsc, stream=stream)
+
+    ms_c = _timed_ms(torch, per_clip, 3, flush, stream)
+    out["batch"] = {"workload": "512 clips, T=2048, V_c log-uniform 1e3..1e5 (sum %d), K=128, split_f16"
+                                % bx.numel(),
+                    "value": terms_b / (ms_b * 1e-3), "unit": UNIT, "ms": ms_b,
+                    "per_clip_calls_value": terms_b / (ms_c * 1e-3), "per_clip_calls_ms": ms_c,
+                    "unit_chunks": uc, "launch": "one fcfs_batch call replayed from a CUDA graph",
+                    "_check": (clips, K, Fb, Ab)}
+
+    # large clip: workload 5, both precisions
+    clip5, K5 = config_clip(5)
+    W5 = 2 * K5 + 1
+    x5, y5, s5 = (torch.from_numpy(a).to(dev) for a in (clip5.x, clip5.y, clip5.s))
+    big = {}
+    for prec in ("split_f16", "fp32"):
+        F5 = torch.empty((W5, W5), dtype=torch.complex64, device=dev)
+        A5 = torch.empty(1, dtype=torch.int64, device=dev)
+        ws5 = torch.empty(fcfs.workspace_size(clip5.V, clip5.T, K5, prec), dtype=torch.uint8, device=dev)
+        ms5 = _timed_ms(torch, lambda: fcfs.forward(x5, y5, s5, clip5.T, K5, prec=prec, out=F5, area_out=A5,
+                                                    workspace=ws5, stream=stream), 3, flush, stream)
+        big[prec] = {"value": clip5.V * W5 * W5 / (ms5 * 1e-3), "ms": ms5, "_F": F5, "_A": A5}
+    out["large"] = {"workload": "clip T=65536, 150000 polygons, V=%d, K=1024 (2049x2049)" % clip5.V,
+                    "unit": UNIT, "split_f16": big["split_f16"], "fp32": big["fp32"], "_check": (clip5, K5)}
+    return out
+
+
+def extras_accuracy(line, extras):
+    """Errors of the extra workloads against the oracle (CPU leg); strips the
+    bookkeeping fields from the reported objects."""
+    import numpy as np
+    import oracle
+    if "adjoint" in extras:
+        clip, tgt, K, G, gx, gy = extras["adjoint"].pop("_check")
+        rx, ry = oracle.vertex_gradient(clip.x, clip.y, clip.s, clip.T, K, G.astype(np.complex128))
+        rel = max(float(np.max(np.abs(gx - rx)) / np.max(np.abs(rx))),
+                  float(np.max(np.abs(gy - ry)) / np.max(np.abs(ry))))
+        line["adjoint"]["max_rel_err"] = rel
+    if "batch" in extras:
+        clips, K, Fb, Ab = extras["batch"].pop("_check")
+        Fb = Fb.cpu().numpy()
+        Ab = Ab.cpu().numpy()
+        order = np.argsort([c.V for c in clips])
+        worst = 0.0
+        for c in order[[0, 255, 511]]:
+            A = oracle.area_exact(clips[c].x, clips[c].y, clips[c].s, clips[c].T)
+            Fo = oracle.block(clips[c].x, clips[c].y, clips[c].s, clips[c].T, K)
+            worst = max(worst, float(np.max(np.abs(Fb[c] - Fo)) / A))
+        line["batch"]["max_abs_err_over_area_sampled"] = worst
+        line["batch"]["areas_exact"] = bool(all(int(Ab[c]) == oracle.area_exact(cl.x, cl.y, cl.s, cl.T)
+                                                for c, cl in enumerate(clips)))
+    if "large" in extras:
+        clip5, K5 = extras["large"].pop("_check")
+        A = oracle.area_exact(clip5.x, clip5.y, clip5.s, clip5.T)
+        pick = np.unique(np.array([0, 1, -1, 2, -2, 7, -13, 100, -333, 512, K5, -K5, K5 - 1]))
+        Fo = oracle.block_entries(clip5.x, clip5.y, clip5.s, clip5.T, pick, pick)
+        for prec in ("split_f16", "fp32"):
+            d = line["large"][prec]
+            F5 = d.pop("_F").cpu().numpy()[np.ix_(pick + K5, pick + K5)]
+            d["max_abs_err_over_area_sampled"] = float(np.max(np.abs(F5 - Fo)) / A)
+            d["area_exact"] = int(d.pop("_A").item()) == A
 
 
 def main():

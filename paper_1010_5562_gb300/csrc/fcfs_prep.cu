@@ -106,7 +106,7 @@ size_t axis_smem_bytes(int T, int full) {
          kAxisStage * sizeof(long long);
 }
 
-template <bool FULL>
+template <bool FULL, bool BATCH>
 __global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32_t* __restrict__ x,
                                                           const int32_t* __restrict__ y,
                                                           const int8_t* __restrict__ s, uint8_t* ws, int vper,
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32
       const int xv = x[b + i], yv = y[b + i], sgn = s[b + i];
       int* e = sv + 8 * i;
       int c = 0;
-      if (pl.batch) {   // last clip whose first vertex is <= b + i
+      if (BATCH) {   // last clip whose first vertex is <= b + i
         int lo = 0, hi = pl.n_clips;
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
@@ -174,8 +174,12 @@ __global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32
         }
         c = lo;
       }
-      sclip[i] = c;
-      sarea[i] = (long long)sgn * xv * (long long)yv;
+      if (BATCH) {
+        sclip[i] = c;
+        sarea[i] = (long long)sgn * xv * (long long)yv;
+      } else if (blockIdx.y == 0) {
+        area += (long long)sgn * xv * (long long)yv;
+      }
       if (FULL) {
         const int3 dx = decimate(xv, T, pl.logT), dy = decimate(yv, T, pl.logT);
         e[0] = dx.x; e[1] = dx.y; e[2] = dx.z; e[3] = sgn * yv;
@@ -200,8 +204,9 @@ __global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32
       const int2* t2 = reinterpret_cast<const int2*>(sm);
       const bool act = k <= pl.K;
 #pragma unroll 4
+      if (!BATCH) cur = 0;
       for (int i = 0; i < n; ++i) {
-        if (sclip[i] != cur) {   // block-uniform: the clips of the staged vertices
+        if (BATCH && sclip[i] != cur) {   // block-uniform: the clips of the staged vertices
           if (cur >= 0) flush(cur);
           cur = sclip[i];
         }
@@ -225,10 +230,20 @@ __global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32
         a1 += (long long)tx.y * wy;
         a2 += (long long)ty.x * wx;
         a3 += (long long)ty.y * wx;
-        // the area sum_v s x y rides on thread 0 of the first k-block
-        if (threadIdx.x == 0 && blockIdx.y == 0) area += sarea[i];
+        // batch: the area sum_v s x y rides on thread 0 of the first k-block
+        if (BATCH && threadIdx.x == 0 && blockIdx.y == 0) area += sarea[i];
       }
     }
+  }
+  if (!BATCH && blockIdx.y == 0) {   // single clip: the staging threads hold the area
+    for (int o = 16; o > 0; o >>= 1) area += __shfl_xor_sync(0xffffffffu, area, o);
+    if ((threadIdx.x & 31) != 0) area = 0;
+    __shared__ long long warea[kAxisThreads / 32];
+    if ((threadIdx.x & 31) == 0) warea[threadIdx.x >> 5] = area;
+    __syncthreads();
+    area = 0;
+    if (threadIdx.x == 0)
+      for (int w = 0; w < kAxisThreads / 32; ++w) area += warea[w];
   }
   if (cur >= 0) flush(cur);
 }
@@ -391,17 +406,11 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
   const int vblocks = (int)((pl.V + vper - 1) / vper);
   const size_t smem = axis_smem_bytes(pl.T, pl.full);
   dim3 grid(vblocks, kblocks);
-  if (pl.full) {
-    cudaFuncSetAttribute(axis_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(axis_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    axis_kernel<true><<<grid, kAxisThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws), (int)vper,
-                                                        validate ? 1 : 0);
-  } else {
-    cudaFuncSetAttribute(axis_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(axis_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    axis_kernel<false><<<grid, kAxisThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws), (int)vper,
-                                                         validate ? 1 : 0);
-  }
+  auto kern = pl.full ? (pl.batch ? axis_kernel<true, true> : axis_kernel<true, false>)
+                      : (pl.batch ? axis_kernel<false, true> : axis_kernel<false, false>);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  kern<<<grid, kAxisThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws), (int)vper, validate ? 1 : 0);
   count_launch(1);
   return cudaGetLastError();
 }

@@ -18,7 +18,9 @@
 //                    memory (K-major, 128-byte swizzle); warps 0-3 then drain
 //                    TMEM in the epilogue;
 //   MMA warp         allocates TMEM; lane 0 issues the tcgen05.mma (3 split
-//                    products x 4 k-steps per chunk) and the commits;
+//                    products x 4 k-steps per chunk; hi*hi into one FP32
+//                    accumulator, the two correction products into a second)
+//                    and the commits;
 //   TMA warp         lane 0 streams the vertex chunks (x, y, s) with 1-D TMA
 //                    and bulk-copies the sincos table once.
 // Every mbarrier wait is bounded: on time-out the status word gets
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     fence_mbar_init();
   }
   if (warp == GW) {
-    tmem_alloc(tmem_slot, BN);
+    tmem_alloc(tmem_slot, 2 * BN);   // D1 (hi*hi) and D2 (hi*lo + lo*hi)
     tmem_relinquish();
   }
   tc_fence_before();
@@ -178,9 +180,12 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
           const uint32_t o = ks * 32;   // 16 FP16 = 32 bytes along K inside the swizzle row
           const uint64_t dah = sdesc_sw128(ahi + o), dal = sdesc_sw128(alo + o);
           const uint64_t dbh = sdesc_sw128(bhi + o), dbl = sdesc_sw128(blo + o);
+          // the large hi*hi products and the small correction products go to
+          // separate accumulators: each rounded add into D1 carries one 16-vertex
+          // dot product instead of three, and D2 stays 2^-11 smaller
           tc_mma_f16(tmem, dah, dbh, idesc, (j | ks) != 0);
-          tc_mma_f16(tmem, dah, dbl, idesc, 1);
-          tc_mma_f16(tmem, dal, dbh, idesc, 1);
+          tc_mma_f16(tmem + BN, dah, dbl, idesc, (j | ks) != 0);
+          tc_mma_f16(tmem + BN, dal, dbh, idesc, 1);
         }
         tc_commit(&oempty[stg]);
       }
@@ -303,9 +308,12 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
         for (int cb = 0; cb < BN / 32; ++cb) {
           const int n0 = tn * BN + cb * 32;
           if (n0 >= M2) break;   // warp-uniform
-          uint32_t r[32];
+          uint32_t r[32], r2[32];
           tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), r);
+          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(BN + cb * 32), r2);
           tmem_wait_ld();
+#pragma unroll
+          for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(r2[q]));
           if (m < M2) {
             float* dst = U.P + (size_t)row * U.ld + cb * 32;
             if (n0 + 32 <= M2 && (M2 & 3) == 0) {
@@ -331,7 +339,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
   if (warp == GW) {
     __syncwarp();   // lane 0 ran the MMA loop alone; dealloc is warp-collective
     tc_fence_after();
-    tmem_dealloc(tmem, BN);
+    tmem_dealloc(tmem, 2 * BN);
   }
 }
 

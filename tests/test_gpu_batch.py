@@ -109,3 +109,16 @@ def test_batch_in_cuda_graph(fc):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(F, ref)
+
+
+def test_autotune_cache(fc, tmp_path, monkeypatch):
+    from paper_1010_5562_gb300 import autotune
+    monkeypatch.setenv("FCFS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    clips = small_batch()[:4]
+    x, y, s, off = (torch.from_numpy(a).cuda() for a in concat_clips(clips))
+    uc = autotune.tune_batch(x, y, s, off, clips[0].T, 40, reps=1)
+    assert uc in autotune.UNIT_CANDIDATES
+    assert (tmp_path / "tune.json").exists()
+    assert autotune.tune_batch(x, y, s, off, clips[0].T, 40) == uc   # served from the cache
+    sp = autotune.tune_forward(x[:clips[0].V], y[:clips[0].V], s[:clips[0].V], clips[0].T, 40, reps=1)
+    assert sp in autotune.SPLIT_CANDIDATES
