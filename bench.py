@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the adjoint, batch and large-clip measurements")
+    ap.add_argument("--only", choices=["step", "large", "batch", "adjoint"], default=None,
+                    help="run one workload warmup + steps times and print its mean time "
+                         "(for profiler command lines; not the benchmark line)")
     return ap.parse_args()
 
 
@@ -230,7 +233,9 @@ def traffic_per_launch():
         for line in txt.splitlines():
             if ":" in line:
                 k, v = line.split(":", 1)
-                got[k.strip().strip("-* `")] = v.strip().strip("`")
+                v = v.strip().split()
+                if v:
+                    got[k.strip().strip("-* `")] = v[0].strip("`")
         if got.get("source_sha256_16") == h:
             return float(got["dram_bytes_per_launch"])
     except Exception:
@@ -538,10 +543,44 @@ def extras_accuracy(line, extras):
             d["area_exact"] = int(d.pop("_A").item()) == A
 
 
+def run_only(args):
+    """One workload, warmup + steps calls, for profiler command lines."""
+    import torch
+    from paper_1010_5562_gb300 import build as B
+    B.build()
+    from paper_1010_5562_gb300 import fcfs
+    from synth import config_clip, config4_target, batch_clips, concat_clips
+    dev = torch.device("cuda", 0)
+    if args.only in ("step", "large", "adjoint"):
+        clip, K = config_clip({"step": 2, "large": 5, "adjoint": 4}[args.only])
+        x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))
+        if args.only == "adjoint":
+            G = torch.ones((2 * K + 1, 2 * K + 1), dtype=torch.complex64, device=dev)
+            fn = lambda: fcfs.adjoint(x, y, s, clip.T, K, G)
+        else:
+            fn = lambda: fcfs.forward(x, y, s, clip.T, K, prec="split_f16")
+    else:
+        clips, K = batch_clips()
+        x, y, s, off = (torch.from_numpy(a).to(dev) for a in concat_clips(clips))
+        fn = lambda: fcfs.batch(x, y, s, off, clips[0].T, K, prec="split_f16")
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fn()
+    torch.cuda.synchronize()
+    print(json.dumps({"only": args.only, "steps": args.steps,
+                      "ms_per_call": 1e3 * (time.perf_counter() - t0) / max(1, args.steps)}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_ours(args)
 
 
