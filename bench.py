@@ -4,7 +4,7 @@
 Step: one forward block F(k,l), |k|,|l| <= 256, of the synthetic Manhattan clip
 T=4096 with 2000 polygons (~12.6k signed corners), through the C ABI on the
 split-FP16 tensor-core path: tables, exact area and axis lines, tcgen05
-contraction, compensated split-K reduction and epilogue (four kernels).
+contraction, compensated split-K reduction and epilogue (five kernels).
 Metric: vertex-coefficient terms per second, V * (2K+1)^2 per step.
 
 Default run: N=1, warm-up 50, 5000 timed steps.  The clip's inputs are far

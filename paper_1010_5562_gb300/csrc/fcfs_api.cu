@@ -72,7 +72,7 @@ static int g_split_override = 0;   // testing/autotuning hook, 0 = automatic
 // Tag of the cached tables: their kind, period, fixed-point scale and offsets.
 static uint64_t table_tag(const Plan& pl) {
   uint64_t h = 0xCBF29CE484222325ull;   // FNV-1a over the fields that fix the table bytes
-  const uint64_t f[6] = {2u /* layout version */, (uint64_t)pl.T, (uint64_t)pl.fixq, (uint64_t)pl.full,
+  const uint64_t f[6] = {3u /* layout version */, (uint64_t)pl.T, (uint64_t)pl.fixq, (uint64_t)pl.full,
                          (uint64_t)pl.off_tab_f32, (uint64_t)pl.off_tab_fix};
   for (uint64_t v : f)
     for (int b = 0; b < 8; ++b) {
@@ -125,6 +125,8 @@ fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
   o = align_up(o + tab_fix_bytes(T, pl.full), kWsAlign);
   pl.off_axis = o;
   o = align_up(o + axis_bytes(K), kWsAlign);
+  pl.off_bins = o;
+  o = align_up(o + bins_bytes(T), kWsAlign);
   pl.off_hist = o;
   o = align_up(o + (size_t)2 * (T + 1) * sizeof(int), kWsAlign);
   pl.off_part = o;
@@ -199,15 +201,18 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
   prof_mark(0, st);
   FCFS_CU(launch_prep(pl, ws, validate, st));
   prof_mark(1, st);
-  prof_mark(2, st);
-  FCFS_CU(launch_axis(pl, x, y, s, ws, validate, st));
-  prof_mark(3, st);
+  // the contraction also bins the corners for the axis lines (Steps 2-3), so
+  // the axis DFT follows it; device validation keeps its own binning pass
+  pl.bin_in_gemm = validate ? 0 : 1;
   prof_mark(4, st);
   if (prec == FCFS_PREC_SPLIT_F16)
     FCFS_CU(launch_gemm_tc(pl, mp, ws, st));
   else
     FCFS_CU(launch_gemm_simt(pl, x, y, s, ws, st));
   prof_mark(5, st);
+  prof_mark(2, st);
+  FCFS_CU(launch_axis(pl, x, y, s, ws, validate, st));
+  prof_mark(3, st);
   prof_mark(6, st);
   FCFS_CU(launch_reduce(pl, ws, F, area, validate, st));
   prof_mark(7, st);

@@ -16,6 +16,7 @@
 namespace fcfs {
 
 fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl);
+
 fcfs_status check_ws(const Plan& pl, void* ws, size_t ws_bytes);
 bool make_vertex_maps(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, VertexMaps& mp);
 
@@ -37,6 +38,8 @@ static fcfs_status make_batch_plan(int64_t V, int32_t n, int32_t T, int32_t K, i
   pl.splits = (int)units_max;   // grid of the contraction kernel
   size_t o = pl.off_axis;       // tables stay where the single-clip plan put them
   o = align_up(o + (size_t)n * (4 * K + 1) * sizeof(long long), kWsAlign);
+  pl.off_bins = o;
+  o = align_up(o + (size_t)n * bins_bytes(T), kWsAlign);
   pl.off_hist = o;
   pl.off_units = o;
   o = align_up(o + (size_t)(n + 1) * sizeof(int), kWsAlign);
@@ -92,12 +95,13 @@ static fcfs_status batch_impl(const int32_t* x, const int32_t* y, const int8_t* 
   batch_units_kernel<<<1, 1024, 0, st>>>(pl, static_cast<uint8_t*>(ws));
   count_launch(1);
   if (cudaGetLastError() != cudaSuccess) return FCFS_ECUDA;
-  if (launch_axis(pl, x, y, s, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
+  pl.bin_in_gemm = 1;   // the contraction bins the corners; the axis DFT follows it
   if (V > 0) {
     const cudaError_t e = prec == FCFS_PREC_SPLIT_F16 ? launch_gemm_tc(pl, mp, ws, st)
                                                        : launch_gemm_simt(pl, x, y, s, ws, st);
     if (e != cudaSuccess) return FCFS_ECUDA;
   }
+  if (launch_axis(pl, x, y, s, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
   if (launch_reduce(pl, ws, F, area, false, st) != cudaSuccess) return FCFS_ECUDA;
   return FCFS_OK;
 }

@@ -30,16 +30,27 @@ struct Plan {
   int32_t splits;      // vertex splits (split-K)
   int32_t chunk;       // vertices per pipeline chunk
   int64_t split_len;   // vertices per split, a multiple of chunk
-  size_t off_status, off_tab_f32, off_tab_fix, off_axis, off_hist, off_part, total;
+  size_t off_status, off_tab_f32, off_tab_fix, off_axis, off_bins, off_hist, off_part, total;
   uint64_t tag;        // identifies the tables cached in this workspace layout
   // batch mode (several clips): the contraction kernels walk units
   // (clip, tile, vertex split) instead of (tile, split)
+  int32_t bin_in_gemm;         // 1: the contraction kernel bins the corners for the axis lines
   int32_t batch;               // 0: one clip; 1: batch
   int32_t n_clips;
   int64_t unit_vertices;       // vertices per unit (a multiple of chunk)
   const int64_t* offsets;      // device, n_clips + 1
   size_t off_units;            // int32 unit_start[n_clips + 1] in the workspace
 };
+
+// Bin one corner for the axis lines (Steps 2-3): bin_x[x] += s y, bin_y[y] += s x
+// (int64 integer atomics, exact and order-free).  Out-of-range corners are skipped.
+__device__ __forceinline__ void bin_corner(const Plan& pl, uint8_t* ws, int clip, int xv, int yv, int sgn) {
+  const int T = pl.T;
+  if (xv < 0 || xv > T || yv < 0 || yv > T || (sgn != 1 && sgn != -1)) return;
+  long long* b = reinterpret_cast<long long*>(ws + pl.off_bins) + (size_t)clip * 2 * (T + 1);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&b[xv]), (unsigned long long)((long long)sgn * yv));
+  atomicAdd(reinterpret_cast<unsigned long long*>(&b[T + 1 + yv]), (unsigned long long)((long long)sgn * xv));
+}
 
 // Work of one CTA of a contraction kernel: output tile, vertex range, and
 // where its FP32 partial tile goes (base and row stride).
@@ -49,6 +60,7 @@ struct Unit {
   float* P;
   int ld;
   bool live;
+  int clip;
 };
 
 // Single clip: blockIdx = (tile, split); batch: blockIdx.x = unit index.
@@ -64,6 +76,7 @@ __device__ inline Unit unit_of_block(const Plan& pl, uint8_t* ws, int bm, int bn
     u.ld = pl.M2;
     u.P = part + (size_t)split * pl.M2 * pl.M2 + (size_t)u.tm * bm * pl.M2 + (size_t)u.tn * bn;
     u.live = true;
+    u.clip = 0;
     return u;
   }
   const int* ustart = reinterpret_cast<const int*>(ws + pl.off_units);
@@ -76,6 +89,7 @@ __device__ inline Unit unit_of_block(const Plan& pl, uint8_t* ws, int bm, int bn
     if (ustart[mid] <= uid) lo = mid; else hi = mid;
   }
   const int c = lo;
+  u.clip = c;
   const long long cv0 = pl.offsets[c], cv1 = pl.offsets[c + 1];
   const int S = (int)((cv1 - cv0 + pl.unit_vertices - 1) / pl.unit_vertices);
   const int r = uid - ustart[c];
@@ -98,9 +112,13 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a -
 __host__ __device__ inline size_t tab_f32_bytes(int T, int full) {
   return full ? (size_t)T * 8 : align_up((size_t)(T / 4 + 1) * 4, 16);
 }
+// the fixed-point table is always quarter-wave (the axis kernels expand it)
 __host__ __device__ inline size_t tab_fix_bytes(int T, int full) {
-  return full ? (size_t)T * 8 : align_up((size_t)(T / 4 + 1) * 4, 16);
+  (void)full;
+  return align_up((size_t)(T / 4 + 1) * 4, 16);
 }
+// per clip: bin_x[T+1], bin_y[T+1] (int64)
+__host__ __device__ inline size_t bins_bytes(int T) { return (size_t)2 * (T + 1) * 8; }
 
 // Axis accumulators: int64 acc[4][K] then the int64 area
 //   acc[0][k-1] = sum s y cos(2 pi k x / T) 2^q     acc[1] = sum s y sin(...) 2^q

@@ -1,5 +1,7 @@
 // Table fill, exact area and axis lines, and the compensated split-K reduction
 // with the quarter-plane butterfly and the Prop. CFT scale factors.
+#include <algorithm>
+
 #include <math_constants.h>
 
 #include "fcfs_common.cuh"
@@ -33,8 +35,11 @@ __global__ void prep_kernel(Plan pl, uint8_t* ws, int validate) {
     st->detail = 0;
   }
   long long* acc = reinterpret_cast<long long*>(ws + pl.off_axis);
-  const long long nacc = (4LL * pl.K + 1) * (pl.batch ? pl.n_clips : 1);
+  const long long nclips = pl.batch ? pl.n_clips : 1;
+  const long long nacc = (4LL * pl.K + 1) * nclips;
   for (long long i = gid; i < nacc; i += gsz) acc[i] = 0;
+  long long* bins = reinterpret_cast<long long*>(ws + pl.off_bins);
+  for (long long i = gid; i < 2LL * (T + 1) * nclips; i += gsz) bins[i] = 0;
   if (validate) {
     int* hist = reinterpret_cast<int*>(ws + pl.off_hist);
     for (long long i = gid; i < 2LL * (T + 1); i += gsz) hist[i] = 0;
@@ -48,9 +53,9 @@ __global__ void prep_kernel(Plan pl, uint8_t* ws, int validate) {
       if (qd.cneg) c = -c;
       if (qd.sneg) s = -s;
       reinterpret_cast<float2*>(ws + pl.off_tab_f32)[p] = make_float2((float)c, (float)s);
-      reinterpret_cast<int2*>(ws + pl.off_tab_fix)[p] =
-          make_int2((int)llrint(c * scale), (int)llrint(s * scale));
     }
+    for (long long r = gid; r <= Q; r += gsz)
+      reinterpret_cast<int*>(ws + pl.off_tab_fix)[r] = (int)llrint(base_cos((int)r, T) * scale);
   } else {
     for (long long r = gid; r <= Q; r += gsz) {
       const double c = base_cos((int)r, T);
@@ -63,189 +68,145 @@ __global__ void prep_kernel(Plan pl, uint8_t* ws, int validate) {
 // ---------------------------------------------------------------------------
 // Area and axis lines, exact in 64-bit integers (Eqs. Fdc, Fk0, F0l; Steps 1-3).
 //
-//   area        = sum_v s_v x_v y_v                      (int64, exact)
-//   Sx(k)       = sum_v s_v y_v exp(-j 2 pi k x_v / T)   (F(k,0) = j T/(2 pi k) Sx(k))
-//   Sy(l)       = sum_v s_v x_v exp(-j 2 pi l y_v / T)   (F(0,l) = j T/(2 pi l) Sy(l))
-//
-// The twiddles are fixed-point integers round(cos * 2^q); products and sums
-// are exact int64, so the only error is the 2^-(q+1) rounding of each twiddle.
-// q is chosen on the host so that V * T * 2^q < 2^62: the final sums then fit,
-// and modular int64 addition makes the order of the partial sums irrelevant
-// (the result is bit-identical run to run).  Balance is not assumed.
-//
-// Block: 256 threads = 256 consecutive k; blockIdx.x picks a vertex range.
-// The 32 lanes of a warp read the table at phases k a mod T for consecutive k,
-// i.e. at stride a.  With a = 2^e u (u odd) that stride hits the same banks
-// 2^e times over, so full-period tables are expanded in shared memory into
-// decimated levels: level e holds the entries at multiples of 2^e and is read
-// at (k u) mod (T / 2^e), a unit stride in k, which is conflict-free.
+// Steps 2 and 3 of FCFS: bin the weights by coordinate, then take a 1-D DFT
+// of the bins.  bin_x[n] = sum over corners with x = n of s y (the signed
+// vertical-edge lengths at x = n), bin_y[n] = sum over y = n of s x, n in [0, T]:
+//   Sx(k) = sum_n bin_x[n] exp(-j 2 pi k n / T),  F(k,0) = j T/(2 pi k) Sx(k),
+//   Sy(l) = sum_n bin_y[n] exp(-j 2 pi l n / T),  F(0,l) = j T/(2 pi l) Sy(l),
+//   area  = sum_n n bin_x[n]                      (Step 1, Eq. Fdc).
+// Bins are int64 integer atomics (exact, order-free); the DFT multiplies them
+// by fixed-point twiddles round(cos * 2^q) in int64, with q chosen on the host
+// so that V * T * 2^q < 2^62 (no partial sum can overflow).  The only error is
+// the 2^-(q+1) rounding of each twiddle.  Balance is not assumed.  Work is
+// O(V) for the bins and O(T K) for the DFT instead of O(V K).
 // ---------------------------------------------------------------------------
 constexpr int kAxisThreads = 256;
-constexpr int kAxisStage = 256;
 
-template <bool FULL>
-__device__ __forceinline__ int2 fix_lookup(const void* tab, uint32_t p, uint32_t logQ) {
-  if (FULL) return reinterpret_cast<const int2*>(tab)[p];
-  const int* t = reinterpret_cast<const int*>(tab);
-  Quad qd = quad_split(p, logQ);
-  int c = t[qd.i1], s = t[qd.i2];
-  return make_int2(qd.cneg ? -c : c, qd.sneg ? -s : s);
+template <bool BATCH>
+__global__ void bin_kernel(Plan pl, const int32_t* __restrict__ x, const int32_t* __restrict__ y,
+                           const int8_t* __restrict__ s, uint8_t* ws, int validate) {
+  const int T = pl.T;
+  long long* bins = reinterpret_cast<long long*>(ws + pl.off_bins);
+  Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
+  int* hist = reinterpret_cast<int*>(ws + pl.off_hist);
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < pl.V;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int xv = x[v], yv = y[v], sgn = s[v];
+    const bool ok = xv >= 0 && xv <= T && yv >= 0 && yv <= T && (sgn == 1 || sgn == -1);
+    if (validate) {
+      if (!ok) {
+        set_status(st, FCFS_EINVAL_DATA, (unsigned)v);
+      } else {
+        atomicAdd(&hist[xv], sgn);
+        atomicAdd(&hist[T + 1 + yv], sgn);
+      }
+    }
+    if (!ok) continue;   // out-of-range corners are never binned
+    int c = 0;
+    if (BATCH) {   // last clip whose first vertex is <= v
+      int lo = 0, hi = pl.n_clips;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pl.offsets[mid] <= v) lo = mid; else hi = mid;
+      }
+      c = lo;
+    }
+    long long* b = bins + (size_t)c * 2 * (T + 1);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&b[xv]), (unsigned long long)((long long)sgn * yv));
+    atomicAdd(reinterpret_cast<unsigned long long*>(&b[T + 1 + yv]), (unsigned long long)((long long)sgn * xv));
+  }
 }
 
-// level of coordinate a in the decimated full-period table: (first entry, odd factor, index mask)
-__device__ __forceinline__ int3 decimate(int a, int T, int logT) {
-  const uint32_t am = (uint32_t)a & (uint32_t)(T - 1);
-  if (am == 0) return make_int3(0, 0, 0);           // phase 0 for every k
-  const int e = __ffs(am) - 1;
-  const int size = T >> e;
-  return make_int3(2 * T - 2 * size, (int)(am >> e), size - 1);
+// Decimated quarter-wave levels of the fixed-point table in shared memory:
+// level e holds C[m 2^e] for m in [0, Q >> e], so the phases k n mod T of 32
+// consecutive k (a stride-n access) are read at stride n >> ctz(n) in level
+// ctz(n), which is conflict-free.
+__device__ __forceinline__ int level_offset(int e, int logQ) {
+  // sum over e' < e of ((1 << (logQ - e')) + 1)
+  return ((1 << (logQ + 1)) - (1 << (logQ + 1 - e))) + e;
 }
 
 size_t axis_smem_bytes(int T, int full) {
-  return (full ? (size_t)2 * T * 8 : tab_fix_bytes(T, 0)) + 9 * kAxisStage * sizeof(int) +
-         kAxisStage * sizeof(long long);
+  (void)full;
+  const int Q = T / 4;
+  return align_up((size_t)(2 * Q + 32) * sizeof(int), 16);
 }
 
-template <bool FULL, bool BATCH>
-__global__ void __launch_bounds__(kAxisThreads) axis_kernel(Plan pl, const int32_t* __restrict__ x,
-                                                          const int32_t* __restrict__ y,
-                                                          const int8_t* __restrict__ s, uint8_t* ws, int vper,
-                                                          int validate) {
+template <bool BATCH>
+__global__ void __launch_bounds__(kAxisThreads) axis_dft_kernel(Plan pl, uint8_t* ws, int nper) {
   extern __shared__ __align__(128) uint8_t sm[];
-  const int T = pl.T;
-  const size_t tb = tab_fix_bytes(T, FULL);
-  const size_t tall = FULL ? (size_t)2 * T * 8 : tb;
-  int* sv = reinterpret_cast<int*>(sm + tall);   // per staged vertex: 8 ints
-  int* sclip = sv + 8 * kAxisStage;              // per staged vertex: clip index
-  long long* sarea = reinterpret_cast<long long*>(sclip + kAxisStage);   // s x y
+  int* lv = reinterpret_cast<int*>(sm);
+  const int T = pl.T, logT = pl.logT, logQ = logT - 2, Q = T / 4;
+  const size_t tb = tab_fix_bytes(T, 0);
   __shared__ uint64_t tbar;
   Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
   if (threadIdx.x == 0) {
     mbar_init(&tbar, 1);
     fence_mbar_init();
     mbar_arrive_expect_tx(&tbar, (uint32_t)tb);
-    bulk_load(sm, ws + pl.off_tab_fix, (uint32_t)tb, &tbar);
+    bulk_load(lv, ws + pl.off_tab_fix, (uint32_t)tb, &tbar);
   }
-  __syncthreads();   // barrier initialised before anyone waits on it
+  __syncthreads();
   mbar_wait(&tbar, 0, st, 20);
-  if (FULL) {
-    // decimated levels e = 1 .. logT-1 from level 0
-    int2* t2 = reinterpret_cast<int2*>(sm);
-    for (int e = 1; e < pl.logT; ++e) {
-      const int size = T >> e, off = 2 * T - 2 * size;
-      for (int m = threadIdx.x; m < size; m += blockDim.x) t2[off + m] = t2[m << e];
-    }
-    __syncthreads();
+  for (int e = 1; e <= logQ; ++e) {
+    const int off = level_offset(e, logQ), n = (Q >> e) + 1;
+    for (int m = threadIdx.x; m < n; m += blockDim.x) lv[off + m] = lv[m << e];
   }
-  const uint32_t mask = (uint32_t)T - 1u;
-  const uint32_t logQ = (uint32_t)pl.logT - 2u;
-  const int k = blockIdx.y * kAxisThreads + threadIdx.x + 1;
-  const long long v0 = (long long)blockIdx.x * vper;
-  const long long v1 = min((long long)pl.V, v0 + vper);
+  __syncthreads();
+
+  const int clip = blockIdx.z;
+  const long long* bx = reinterpret_cast<const long long*>(ws + pl.off_bins) + (size_t)clip * 2 * (T + 1);
+  const long long* by = bx + (T + 1);
+  const int k = blockIdx.x * kAxisThreads + threadIdx.x + 1;
+  const int n0 = blockIdx.y * nper, n1 = min(T + 1, n0 + nper);
   long long a0 = 0, a1 = 0, a2 = 0, a3 = 0, area = 0;
-  int* hist = reinterpret_cast<int*>(ws + pl.off_hist);
-  long long* acc = reinterpret_cast<long long*>(ws + pl.off_axis);
-  const int A = 4 * pl.K + 1;   // accumulators per clip
-  int cur = -1;                 // clip of the running sums
-  auto flush = [&](int c) {
-    long long* ac = acc + (size_t)c * A;
-    if (k <= pl.K) {
-      atomicAdd(reinterpret_cast<unsigned long long*>(&ac[k - 1]), (unsigned long long)a0);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&ac[pl.K + k - 1]), (unsigned long long)a1);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&ac[2 * pl.K + k - 1]), (unsigned long long)a2);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&ac[3 * pl.K + k - 1]), (unsigned long long)a3);
-    }
-    if (blockIdx.y == 0 && threadIdx.x == 0 && area != 0)
-      atomicAdd(reinterpret_cast<unsigned long long*>(&ac[4 * pl.K]), (unsigned long long)area);
-    a0 = a1 = a2 = a3 = area = 0;
-  };
-  for (long long b = v0; b < v1; b += kAxisStage) {
-    const int n = (int)min((long long)kAxisStage, v1 - b);
+  // bins are staged through shared memory in coalesced slices (a dependent
+  // global load per bin would leave the loop latency-bound)
+  __shared__ long long sbx[kAxisThreads], sby[kAxisThreads];
+  for (int b0 = n0; b0 < n1; b0 += kAxisThreads) {
+    const int cnt = min(kAxisThreads, n1 - b0);
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int xv = x[b + i], yv = y[b + i], sgn = s[b + i];
-      int* e = sv + 8 * i;
-      int c = 0;
-      if (BATCH) {   // last clip whose first vertex is <= b + i
-        int lo = 0, hi = pl.n_clips;
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (pl.offsets[mid] <= b + i) lo = mid; else hi = mid;
-        }
-        c = lo;
-      }
-      if (BATCH) {
-        sclip[i] = c;
-        sarea[i] = (long long)sgn * xv * (long long)yv;
-      } else if (blockIdx.y == 0) {
-        area += (long long)sgn * xv * (long long)yv;
-      }
-      if (FULL) {
-        const int3 dx = decimate(xv, T, pl.logT), dy = decimate(yv, T, pl.logT);
-        e[0] = dx.x; e[1] = dx.y; e[2] = dx.z; e[3] = sgn * yv;
-        e[4] = dy.x; e[5] = dy.y; e[6] = dy.z; e[7] = sgn * xv;
-      } else {
-        e[0] = xv; e[1] = sgn * yv; e[4] = yv; e[5] = sgn * xv;
-      }
-      if (blockIdx.y == 0) {
-        if (validate) {
-          const bool ok = xv >= 0 && xv <= T && yv >= 0 && yv <= T && (sgn == 1 || sgn == -1);
-          if (!ok) {
-            set_status(st, FCFS_EINVAL_DATA, (unsigned)(b + i));
-          } else {
-            atomicAdd(&hist[xv], sgn);
-            atomicAdd(&hist[T + 1 + yv], sgn);
-          }
-        }
-      }
+    if ((int)threadIdx.x < cnt) {
+      sbx[threadIdx.x] = bx[b0 + threadIdx.x];
+      sby[threadIdx.x] = by[b0 + threadIdx.x];
     }
     __syncthreads();
-    {
-      const int2* t2 = reinterpret_cast<const int2*>(sm);
-      const bool act = k <= pl.K;
-#pragma unroll 4
-      if (!BATCH) cur = 0;
-      for (int i = 0; i < n; ++i) {
-        if (BATCH && sclip[i] != cur) {   // block-uniform: the clips of the staged vertices
-          if (cur >= 0) flush(cur);
-          cur = sclip[i];
-        }
-        if (!act) continue;
-        const int4 ex = reinterpret_cast<const int4*>(sv + 8 * i)[0];
-        const int4 ey = reinterpret_cast<const int4*>(sv + 8 * i)[1];
-        int2 tx, ty;
-        int wy, wx;
-        if (FULL) {
-          tx = t2[ex.x + (int)(((uint32_t)k * (uint32_t)ex.y) & (uint32_t)ex.z)];
-          ty = t2[ey.x + (int)(((uint32_t)k * (uint32_t)ey.y) & (uint32_t)ey.z)];
-          wy = ex.w;
-          wx = ey.w;
-        } else {
-          tx = fix_lookup<false>(sm, ((uint32_t)k * (uint32_t)ex.x) & mask, logQ);
-          ty = fix_lookup<false>(sm, ((uint32_t)k * (uint32_t)ey.x) & mask, logQ);
-          wy = ex.y;
-          wx = ey.y;
-        }
-        a0 += (long long)tx.x * wy;
-        a1 += (long long)tx.y * wy;
-        a2 += (long long)ty.x * wx;
-        a3 += (long long)ty.y * wx;
-        // batch: the area sum_v s x y rides on thread 0 of the first k-block
-        if (BATCH && threadIdx.x == 0 && blockIdx.y == 0) area += sarea[i];
-      }
+  for (int i = 0; i < cnt; ++i) {
+    const int n = b0 + i;
+    const long long wx = sbx[i], wy = sby[i];   // same address across the block: broadcast
+    if (wx == 0 && wy == 0) continue;          // block-uniform
+    if (blockIdx.x == 0 && threadIdx.x == 0) area += (long long)n * wx;
+    if (k > pl.K) continue;
+    // phase k n mod T in the decimated level of n
+    const uint32_t nm = (uint32_t)n & (uint32_t)(T - 1);
+    int e = nm ? __ffs(nm) - 1 : 0;
+    uint32_t u = nm >> e;
+    if (e > logQ - 1) {   // n a multiple of T/4 (or 0): the level-0 lookup reads at most 4 entries
+      e = 0;
+      u = nm;
     }
+    const int lq = logQ - e;                     // log2 of this level's quarter period
+    const uint32_t p = ((uint32_t)k * u) & ((4u << lq) - 1u);
+    const Quad qd = quad_split(p, (uint32_t)lq);
+    const int* L = lv + level_offset(e, logQ);
+    int c = L[qd.i1], sn = L[qd.i2];
+    if (qd.cneg) c = -c;
+    if (qd.sneg) sn = -sn;
+    a0 += (long long)c * wx;
+    a1 += (long long)sn * wx;
+    a2 += (long long)c * wy;
+    a3 += (long long)sn * wy;
   }
-  if (!BATCH && blockIdx.y == 0) {   // single clip: the staging threads hold the area
-    for (int o = 16; o > 0; o >>= 1) area += __shfl_xor_sync(0xffffffffu, area, o);
-    if ((threadIdx.x & 31) != 0) area = 0;
-    __shared__ long long warea[kAxisThreads / 32];
-    if ((threadIdx.x & 31) == 0) warea[threadIdx.x >> 5] = area;
-    __syncthreads();
-    area = 0;
-    if (threadIdx.x == 0)
-      for (int w = 0; w < kAxisThreads / 32; ++w) area += warea[w];
   }
-  if (cur >= 0) flush(cur);
+  long long* acc = reinterpret_cast<long long*>(ws + pl.off_axis) + (size_t)clip * (4 * pl.K + 1);
+  if (k <= pl.K) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[k - 1]), (unsigned long long)a0);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[pl.K + k - 1]), (unsigned long long)a1);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[2 * pl.K + k - 1]), (unsigned long long)a2);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[3 * pl.K + k - 1]), (unsigned long long)a3);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && area != 0)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[4 * pl.K]), (unsigned long long)area);
 }
 
 // ---------------------------------------------------------------------------
@@ -382,7 +343,7 @@ __global__ void reduce_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, long
 cudaError_t launch_prep(const Plan& pl, void* ws, bool validate, cudaStream_t st) {
   // one thread per table entry on a cold workspace (the FP64 cospi is the cost)
   long long work = pl.full ? pl.T : pl.T / 4 + 1;
-  work = max(work, (4LL * pl.K + 1) * (pl.batch ? pl.n_clips : 1));
+  work = max(work, (4LL * pl.K + 1 + 2LL * (pl.T + 1)) * (pl.batch ? pl.n_clips : 1));
   if (validate) work = max(work, 2LL * (pl.T + 1));
   int blocks = (int)min((work + 63) / 64, 2048LL);
   // every kernel of a call asks for the largest shared-memory carveout, so the
@@ -395,22 +356,28 @@ cudaError_t launch_prep(const Plan& pl, void* ws, bool validate, cudaStream_t st
 
 cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, const int8_t* s, void* ws,
                         bool validate, cudaStream_t st) {
-  if (pl.V == 0) return cudaSuccess;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (pl.V > 0 && !pl.bin_in_gemm) {
+    const int blocks = (int)std::min<long long>((pl.V + 255) / 256, 8LL * sms);
+    if (pl.batch)
+      bin_kernel<true><<<blocks, 256, 0, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws), validate ? 1 : 0);
+    else
+      bin_kernel<false><<<blocks, 256, 0, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws), validate ? 1 : 0);
+    count_launch(1);
+    if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
+  }
   const int kblocks = (pl.K + kAxisThreads - 1) / kAxisThreads;
-  // equal vertex ranges, one block per SM and k-block
-  const long long target = max(1LL, (long long)sms / kblocks);
-  long long vper = max(8LL, (pl.V + target - 1) / target);
-  const int vblocks = (int)((pl.V + vper - 1) / vper);
+  const int clips = pl.batch ? pl.n_clips : 1;
+  const long long want = std::max(1LL, (long long)(2 * sms) / ((long long)kblocks * clips));
+  const int nper = (int)std::max(64LL, (pl.T + 1 + want - 1) / want);
+  const int nblocks = (pl.T + 1 + nper - 1) / nper;
   const size_t smem = axis_smem_bytes(pl.T, pl.full);
-  dim3 grid(vblocks, kblocks);
-  auto kern = pl.full ? (pl.batch ? axis_kernel<true, true> : axis_kernel<true, false>)
-                      : (pl.batch ? axis_kernel<false, true> : axis_kernel<false, false>);
+  auto kern = pl.batch ? axis_dft_kernel<true> : axis_dft_kernel<false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  kern<<<grid, kAxisThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws), (int)vper, validate ? 1 : 0);
+  kern<<<dim3(kblocks, nblocks, clips), kAxisThreads, smem, st>>>(pl, static_cast<uint8_t*>(ws), nper);
   count_launch(1);
   return cudaGetLastError();
 }

@@ -69,9 +69,11 @@ __global__ void __launch_bounds__(kSThreads, 2) gemm_simt_kernel(Plan pl, const 
     if (tid < kSChunk) {
       const long long v = b + tid;
       const bool ok = v < v1;
-      vx[tid] = ok ? x[v] : 0;
-      vy[tid] = ok ? y[v] : 0;
-      vs[tid] = ok ? (float)s[v] : 0.f;
+      const int xv = ok ? x[v] : 0, yv = ok ? y[v] : 0, sv = ok ? s[v] : 0;
+      vx[tid] = xv;
+      vy[tid] = yv;
+      vs[tid] = (float)sv;
+      if (ok && pl.bin_in_gemm && tm == 0 && tn == 0) bin_corner(pl, ws, U.clip, xv, yv, sv);
     }
     __syncthreads();
 #pragma unroll

@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     const uint32_t logQ = (uint32_t)pl.logT - 2u;
     const uint32_t ops_a = smem_u32(ops);
     const int coord_off = isA ? 0 : 384;
+    const bool do_bin = pl.bin_in_gemm && tm == 0 && tn == 0 && run == 0;
     // swizzled byte offset of this thread's 16-byte chunk in row r: (oct ^ (r & 7)) << 4;
     // rows 2(i0 + r) have r & 7 = 2r & 7 because i0 is a multiple of 8
     uint32_t xo[8];
@@ -239,6 +240,17 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
         vmask[q] = (lo_ok ? 0xFFFFu : 0u) | (hi_ok ? 0xFFFF0000u : 0u);
       }
       const bool masked = isA && (first + 8 > v1);
+      if (do_bin) {   // each corner of the chunk once: the 8 threads of A run 0
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int idx = off + oct * 8 + t;
+          if (first + t < v1) {
+            const int32_t* xs = reinterpret_cast<const int32_t*>(d);
+            const int32_t* ys = reinterpret_cast<const int32_t*>(d + 384);
+            bin_corner(pl, ws, U.clip, xs[idx], ys[idx], ss[idx]);
+          }
+        }
+      }
       // The next TMA write into this stage is an async-proxy write; the
       // mbarrier release alone does not order it after these generic-proxy
       // loads, which may still be in flight.  The proxy fence does.

@@ -197,4 +197,4 @@ def test_launch_counter(fc):
     x, y, s = to_dev(clip)
     n0 = fc.launch_count()
     fc.forward(x, y, s, clip.T, K, prec="split_f16")
-    assert fc.launch_count() - n0 == 4
+    assert fc.launch_count() - n0 == 4   # prep, contraction (bins the corners), axis DFT, reduce
