@@ -182,12 +182,19 @@ fcfs_status fcfs_forward_noalloc(const int32_t* x, const int32_t* y, const int8_
  * fcfs_profile_read() waits for the last event and writes up to n stage
  * durations in milliseconds (0: prep/tables, 1: area and axis lines,
  * 2: contraction, 3: reduce and epilogue).  Returns the number written.
+ * In a fused call (below) stages 1 and 3 run inside stage 2 and read 0.
  * fcfs_debug_set_splits(n) forces n vertex splits (0: automatic choice).
+ * fcfs_debug_set_fuse(0) makes fcfs_forward keep the axis-line DFT and the
+ * split-K reduction in kernels of their own; 1 (the default) lets the
+ * split-FP16 path run them inside the contraction kernel whenever its CTAs fit
+ * on the GPU at once (one cooperative launch; the results are the same up to
+ * FP32 rounding order, which is fixed either way).
  * Not thread-safe; meant for benchmarks and tests.
  */
 void fcfs_profile_enable(int32_t on);
 int32_t fcfs_profile_read(float* ms, int32_t n);
 void fcfs_debug_set_splits(int32_t n);
+void fcfs_debug_set_fuse(int32_t on);
 
 /* Vertex-split granularity of fcfs_batch: n pipeline chunks (64 corners on the
  * tensor path, 32 on the FP32 path) per unit; 0 restores the default of 4096

@@ -8,6 +8,8 @@
 
 #include <cudaTypedefs.h>
 
+#include <math_constants.h>
+
 #include "fcfs_common.cuh"
 
 namespace fcfs {
@@ -68,6 +70,7 @@ static int choose_splits(long long tiles, long long nchunks, long long slots, lo
 }
 
 static int g_split_override = 0;   // testing/autotuning hook, 0 = automatic
+static int g_fuse = 1;             // testing hook: 0 keeps the axis and reduce kernels separate
 
 // Tag of the cached tables: their kind, period, fixed-point scale and offsets.
 static uint64_t table_tag(const Plan& pl) {
@@ -96,6 +99,7 @@ fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
   pl.full = T <= kFullTableMaxT ? 1 : 0;
   pl.fixq = min(30, 62 - ceil_log2(std::max<long long>(V, 1)) - pl.logT);
   pl.M2 = 2 * K;
+  pl.quad_scale = (float)((double)T * (double)T / (4.0 * CUDART_PI * CUDART_PI));
   const bool tc = prec == FCFS_PREC_SPLIT_F16;
   if (tc) {
     pl.bm = 128;
@@ -142,7 +146,7 @@ fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 static std::once_flag g_encode_once;
 
-static bool encode_1d(CUtensorMap* map, const void* base, CUtensorMapDataType dt, uint64_t n) {
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   std::call_once(g_encode_once, [] {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -151,7 +155,11 @@ static bool encode_1d(CUtensorMap* map, const void* base, CUtensorMapDataType dt
         q == cudaDriverEntryPointSuccess)
       g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   });
-  if (!g_encode) return false;
+  return g_encode;
+}
+
+static bool encode_1d(CUtensorMap* map, const void* base, CUtensorMapDataType dt, uint64_t n) {
+  if (!encode_fn()) return false;
   cuuint64_t dims[1] = {n};
   cuuint64_t strides[1] = {0};
   cuuint32_t box[1] = {80};
@@ -166,6 +174,21 @@ bool make_vertex_maps(const int32_t* x, const int32_t* y, const int8_t* s, int64
   return encode_1d(&mp.x, x, CU_TENSOR_MAP_DATA_TYPE_INT32, (uint64_t)V) &&
          encode_1d(&mp.y, y, CU_TENSOR_MAP_DATA_TYPE_INT32, (uint64_t)V) &&
          encode_1d(&mp.s, s, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)V);
+}
+
+// The FP32 partials of a single clip as a 3-D tensor [split][row][col] of
+// M2 x M2 x splits floats; one box is the cos and sin rows of one k, 64 floats
+// (32 l values) wide, over every split (read by the fused tail).
+bool make_part_map(const Plan& pl, void* ws, CUtensorMap* map) {
+  if (!encode_fn() || pl.splits < 1 || pl.splits > 256 || (pl.M2 * 4) % 16 != 0) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)pl.M2, (cuuint64_t)pl.M2, (cuuint64_t)pl.splits};
+  cuuint64_t strides[2] = {(cuuint64_t)pl.M2 * 4, (cuuint64_t)pl.M2 * pl.M2 * 4};
+  cuuint32_t box[3] = {64, 2, (cuuint32_t)pl.splits};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, static_cast<uint8_t*>(ws) + pl.off_part, dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -196,7 +219,7 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
   if (r != FCFS_OK) return r;
   if ((r = check_ws(pl, ws, ws_bytes)) != FCFS_OK) return r;
   const bool validate = (flags & FCFS_FLAG_VALIDATE) != 0;
-  VertexMaps mp;
+  VertexMaps mp{};
   if (prec == FCFS_PREC_SPLIT_F16 && V > 0 && !make_vertex_maps(x, y, s, V, mp)) return FCFS_ECUDA;
   prof_mark(0, st);
   FCFS_CU(launch_prep(pl, ws, validate, st));
@@ -204,12 +227,25 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
   // the contraction also bins the corners for the axis lines (Steps 2-3), so
   // the axis DFT follows it; device validation keeps its own binning pass
   pl.bin_in_gemm = validate ? 0 : 1;
+  // one resident wave of tensor-core CTAs: they also sum the splits, take the
+  // axis DFT and write the output behind a grid barrier (two launches per call)
+  if (prec == FCFS_PREC_SPLIT_F16 && !validate && g_fuse && V > 0 && gemm_tc_fusable(pl) &&
+      make_part_map(pl, ws, &mp.part)) {
+    pl.fused = 1;
+    pl.F = reinterpret_cast<float2*>(F);
+    pl.area_out = reinterpret_cast<long long*>(area);
+  }
   prof_mark(4, st);
   if (prec == FCFS_PREC_SPLIT_F16)
     FCFS_CU(launch_gemm_tc(pl, mp, ws, st));
   else
     FCFS_CU(launch_gemm_simt(pl, x, y, s, ws, st));
   prof_mark(5, st);
+  if (pl.fused) {
+    for (int i = 2; i <= 3; ++i) prof_mark(i, st);
+    for (int i = 6; i <= 7; ++i) prof_mark(i, st);
+    return FCFS_OK;
+  }
   prof_mark(2, st);
   FCFS_CU(launch_axis(pl, x, y, s, ws, validate, st));
   prof_mark(3, st);
@@ -265,6 +301,7 @@ fcfs_status fcfs_get_status(const void* workspace, void* stream) {
 
 // Test hook: force the number of vertex splits (0 restores the automatic choice).
 void fcfs_debug_set_splits(int32_t s) { g_split_override = s; }
+void fcfs_debug_set_fuse(int32_t on) { g_fuse = on ? 1 : 0; }
 
 void fcfs_profile_enable(int32_t on) { g_prof = on != 0; }
 

@@ -89,7 +89,7 @@ static fcfs_status batch_impl(const int32_t* x, const int32_t* y, const int8_t* 
   fcfs_status r = make_batch_plan(V, n, T, K, prec, offsets, pl);
   if (r != FCFS_OK) return r;
   if ((r = check_ws(pl, ws, ws_bytes)) != FCFS_OK) return r;
-  VertexMaps mp;
+  VertexMaps mp{};
   if (prec == FCFS_PREC_SPLIT_F16 && V > 0 && !make_vertex_maps(x, y, s, V, mp)) return FCFS_ECUDA;
   if (launch_prep(pl, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
   batch_units_kernel<<<1, 1024, 0, st>>>(pl, static_cast<uint8_t*>(ws));

@@ -25,6 +25,7 @@ struct Plan {
   int32_t full;        // 1: full-period tables, 0: quarter-wave tables
   int32_t fixq;        // fixed-point scale 2^fixq of the axis-line table
   int32_t M2;          // 2K: rows (and columns) of the quarter-plane product
+  float quad_scale;    // T^2 / (4 pi^2), rounded once from FP64 (Eq. Fkl)
   int32_t bm, bn;      // GEMM tile
   int32_t tiles_m, tiles_n;
   int32_t splits;      // vertex splits (split-K)
@@ -35,6 +36,10 @@ struct Plan {
   // batch mode (several clips): the contraction kernels walk units
   // (clip, tile, vertex split) instead of (tile, split)
   int32_t bin_in_gemm;         // 1: the contraction kernel bins the corners for the axis lines
+  int32_t fused;               // 1: the contraction kernel also runs the split-K sum, the
+                               //    axis-line DFT and the output (cooperative launch)
+  float2* F;                   // output block (fused only)
+  long long* area_out;         // output area (fused only)
   int32_t batch;               // 0: one clip; 1: batch
   int32_t n_clips;
   int64_t unit_vertices;       // vertices per unit (a multiple of chunk)
@@ -195,6 +200,21 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// 3-D tiled TMA load of one box at (c0, c1, c2) (c0 innermost).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int32_t c0, int32_t c1, int32_t c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Prefetch a 16-byte aligned range (size a multiple of 16) into L2.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Plain bulk copy global -> shared (16-byte aligned, size a multiple of 16).
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
@@ -307,6 +327,7 @@ __device__ __forceinline__ float2 f32_lookup(const float* tab, uint32_t p, uint3
 // ---------------------------------------------------------------------------
 struct VertexMaps {
   CUtensorMap x, y, s;
+  CUtensorMap part;   // FP32 partials [split][row][col] (fused single-clip calls only)
 };
 
 cudaError_t launch_prep(const Plan& pl, void* ws, bool validate, cudaStream_t st);
@@ -315,6 +336,8 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
 cudaError_t launch_reduce(const Plan& pl, void* ws, float* F, int64_t* area, bool validate, cudaStream_t st);
 cudaError_t launch_gemm_simt(const Plan& pl, const int32_t* x, const int32_t* y, const int8_t* s, void* ws,
                              cudaStream_t st);
+bool gemm_tc_fusable(const Plan& pl);
+bool make_part_map(const Plan& pl, void* ws, CUtensorMap* map);
 cudaError_t launch_gemm_tc(const Plan& pl, const VertexMaps& maps, void* ws, cudaStream_t st);
 void count_launch(int n);
 

@@ -81,7 +81,7 @@ extern "C" fcfs_status fcfs_forward_noalloc(const int32_t* x, const int32_t* y, 
   if ((r = fit_plan(pl, FCFS_NOALLOC_SCRATCH_BYTES)) != FCFS_OK) return r;
   void* ws = nullptr;
   if ((r = scratch_on_current_device(&ws)) != FCFS_OK) return r;
-  VertexMaps mp;
+  VertexMaps mp{};
   if (prec == FCFS_PREC_SPLIT_F16 && V > 0 && !make_vertex_maps(x, y, s, V, mp)) return FCFS_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (launch_prep(pl, ws, false, st) != cudaSuccess) return FCFS_ECUDA;

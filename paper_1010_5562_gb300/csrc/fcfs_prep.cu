@@ -4,7 +4,7 @@
 
 #include <math_constants.h>
 
-#include "fcfs_common.cuh"
+#include "fcfs_epilogue.cuh"
 
 namespace fcfs {
 
@@ -33,6 +33,9 @@ __global__ void prep_kernel(Plan pl, uint8_t* ws, int validate) {
     Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
     st->code = 0;
     st->detail = 0;
+    unsigned* sync = reinterpret_cast<unsigned*>(ws + kSyncOffset);
+    sync[0] = 0;
+    sync[1] = 0;
   }
   long long* acc = reinterpret_cast<long long*>(ws + pl.off_axis);
   const long long nclips = pl.batch ? pl.n_clips : 1;
@@ -117,19 +120,9 @@ __global__ void bin_kernel(Plan pl, const int32_t* __restrict__ x, const int32_t
   }
 }
 
-// Decimated quarter-wave levels of the fixed-point table in shared memory:
-// level e holds C[m 2^e] for m in [0, Q >> e], so the phases k n mod T of 32
-// consecutive k (a stride-n access) are read at stride n >> ctz(n) in level
-// ctz(n), which is conflict-free.
-__device__ __forceinline__ int level_offset(int e, int logQ) {
-  // sum over e' < e of ((1 << (logQ - e')) + 1)
-  return ((1 << (logQ + 1)) - (1 << (logQ + 1 - e))) + e;
-}
-
 size_t axis_smem_bytes(int T, int full) {
   (void)full;
-  const int Q = T / 4;
-  return align_up((size_t)(2 * Q + 32) * sizeof(int), 16);
+  return align_up(axis_levels_ints(T) * sizeof(int), 16);
 }
 
 template <bool BATCH>
@@ -148,10 +141,7 @@ __global__ void __launch_bounds__(kAxisThreads) axis_dft_kernel(Plan pl, uint8_t
   }
   __syncthreads();
   mbar_wait(&tbar, 0, st, 20);
-  for (int e = 1; e <= logQ; ++e) {
-    const int off = level_offset(e, logQ), n = (Q >> e) + 1;
-    for (int m = threadIdx.x; m < n; m += blockDim.x) lv[off + m] = lv[m << e];
-  }
+  axis_build_levels(lv, T, logT);
   __syncthreads();
 
   const int clip = blockIdx.z;
@@ -177,25 +167,7 @@ __global__ void __launch_bounds__(kAxisThreads) axis_dft_kernel(Plan pl, uint8_t
     if (wx == 0 && wy == 0) continue;          // block-uniform
     if (blockIdx.x == 0 && threadIdx.x == 0) area += (long long)n * wx;
     if (k > pl.K) continue;
-    // phase k n mod T in the decimated level of n
-    const uint32_t nm = (uint32_t)n & (uint32_t)(T - 1);
-    int e = nm ? __ffs(nm) - 1 : 0;
-    uint32_t u = nm >> e;
-    if (e > logQ - 1) {   // n a multiple of T/4 (or 0): the level-0 lookup reads at most 4 entries
-      e = 0;
-      u = nm;
-    }
-    const int lq = logQ - e;                     // log2 of this level's quarter period
-    const uint32_t p = ((uint32_t)k * u) & ((4u << lq) - 1u);
-    const Quad qd = quad_split(p, (uint32_t)lq);
-    const int* L = lv + level_offset(e, logQ);
-    int c = L[qd.i1], sn = L[qd.i2];
-    if (qd.cneg) c = -c;
-    if (qd.sneg) sn = -sn;
-    a0 += (long long)c * wx;
-    a1 += (long long)sn * wx;
-    a2 += (long long)c * wy;
-    a3 += (long long)sn * wy;
+    axis_bin_add(lv, T, logQ, k, n, wx, wy, a0, a1, a2, a3);
   }
   }
   long long* acc = reinterpret_cast<long long*>(ws + pl.off_axis) + (size_t)clip * (4 * pl.K + 1);
@@ -224,17 +196,6 @@ __global__ void __launch_bounds__(kAxisThreads) axis_dft_kernel(Plan pl, uint8_t
 //    F(-k,-l) = conj F(k,l), F(-k,l) = conj F(k,-l) (real image).
 // The last thread to finish writes the table tag of the workspace.
 // ---------------------------------------------------------------------------
-struct CSum {
-  float hi, lo;
-};
-__device__ __forceinline__ void csum_add(CSum& a, float b) {
-  const float s = a.hi + b;
-  const float bb = s - a.hi;
-  const float e = (a.hi - (s - bb)) + (b - bb);
-  a.hi = s;
-  a.lo += e;
-}
-
 __global__ void reduce_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, long long* __restrict__ area_out,
                               int validate) {
   const int K = pl.K;
@@ -253,29 +214,9 @@ __global__ void reduce_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, long
   F += (size_t)clip * W * W;
   area_out += clip;
   const int k = (int)(idx / n1), l = (int)(idx % n1);
-  const double T = (double)pl.T;
   const long long* acc = reinterpret_cast<const long long*>(ws + pl.off_axis) + (size_t)clip * (4 * K + 1);
-  const double inv = ldexp(1.0, -pl.fixq);
-  if (k == 0 && l == 0) {
-    const long long a = acc[4 * K];
-    area_out[0] = a;
-    F[K * W + K] = make_float2((float)a, 0.f);
-    return;
-  }
-  if (l == 0 || k == 0) {
-    const int f = k + l;   // the nonzero one
-    const int base = (l == 0) ? 0 : 2 * K;
-    const double C = (double)acc[base + f - 1] * inv;
-    const double S = (double)acc[base + K + f - 1] * inv;
-    const double g = T / (2.0 * CUDART_PI * f);
-    const float re = (float)(g * S), im = (float)(g * C);
-    if (l == 0) {
-      F[(K + k) * W + K] = make_float2(re, im);
-      F[(K - k) * W + K] = make_float2(re, -im);
-    } else {
-      F[K * W + K + l] = make_float2(re, im);
-      F[K * W + K - l] = make_float2(re, -im);
-    }
+  if (k == 0 || l == 0) {
+    axis_entry(pl, acc, F, area_out, k == 0 ? (l == 0 ? 0 : K + l) : k);
     return;
   }
   const int M2 = pl.M2;
@@ -300,41 +241,7 @@ __global__ void reduce_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, long
     stride = (size_t)pl.bm * pl.bn;
     ld = pl.bn;
   }
-  CSum cc{0.f, 0.f}, cs{0.f, 0.f}, sc{0.f, 0.f}, ss{0.f, 0.f};
-  // issue a whole batch of split loads before the dependent sums (latency bound otherwise)
-  constexpr int kBatch = 8;
-  for (int sp0 = 0; sp0 < S; sp0 += kBatch) {
-    float2 r0[kBatch], r1[kBatch];
-#pragma unroll
-    for (int b = 0; b < kBatch; ++b) {
-      if (sp0 + b < S) {
-        r0[b] = __ldcs(reinterpret_cast<const float2*>(P + base + (size_t)(sp0 + b) * stride));
-        r1[b] = __ldcs(reinterpret_cast<const float2*>(P + base + (size_t)(sp0 + b) * stride + ld));
-      }
-    }
-#pragma unroll
-    for (int b = 0; b < kBatch; ++b) {
-      if (sp0 + b < S) {
-        csum_add(cc, r0[b].x);
-        csum_add(cs, r0[b].y);
-        csum_add(sc, r1[b].x);
-        csum_add(ss, r1[b].y);
-      }
-    }
-  }
-  // combine hi and lo parts; the cancellations below are exact or relative to
-  // the result, and the result is rounded to FP32 anyway
-  const float a = (float)(T * T / (4.0 * CUDART_PI * CUDART_PI)) / ((float)k * (float)l);
-  const float gr_p = (cc.hi - ss.hi) + (cc.lo - ss.lo);   // Re G(k,l)
-  const float gi_p = -((sc.hi + cs.hi) + (sc.lo + cs.lo)); // Im G(k,l)
-  const float gr_m = (cc.hi + ss.hi) + (cc.lo + ss.lo);   // Re G(k,-l)
-  const float gi_m = -((sc.hi - cs.hi) + (sc.lo - cs.lo)); // Im G(k,-l)
-  const float pr = -a * gr_p, pi = -a * gi_p;   // F(k,l)  = -a G(k,l)
-  const float mr = a * gr_m, mi = a * gi_m;     // F(k,-l) = +a G(k,-l)
-  F[(K + k) * W + (K + l)] = make_float2(pr, pi);
-  F[(K - k) * W + (K - l)] = make_float2(pr, -pi);
-  F[(K + k) * W + (K - l)] = make_float2(mr, mi);
-  F[(K - k) * W + (K + l)] = make_float2(mr, -mi);
+  quad_entry<false>(pl, P, base, stride, ld, S, F, k, l);
 }
 
 // ---------------------------------------------------------------------------

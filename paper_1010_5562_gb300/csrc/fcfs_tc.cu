@@ -25,7 +25,7 @@
 //                    and bulk-copies the sincos table once.
 // Every mbarrier wait is bounded: on time-out the status word gets
 // FCFS_ETIMEOUT and the CTA drains and exits normally.
-#include "fcfs_common.cuh"
+#include "fcfs_epilogue.cuh"
 
 namespace fcfs {
 
@@ -86,7 +86,8 @@ __device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_
 template <int BN, int STAGES, bool FULL>
 __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
-                   const __grid_constant__ CUtensorMap tms, Plan pl, uint8_t* ws) {
+                   const __grid_constant__ CUtensorMap tms, const __grid_constant__ CUtensorMap tmp, Plan pl,
+                   uint8_t* ws) {
   using L = TcLayout<BN, STAGES>;
   constexpr int GT = L::kGenThreads;
   constexpr int GW = L::kGenWarps;
@@ -104,7 +105,8 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
   uint64_t* vempty = vfull + kVStages;
   uint64_t* accfull = vempty + kVStages;
   uint64_t* tabbar = accfull + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tabbar + 1);
+  uint64_t* tailbar = tabbar + 1;   // fused tail: bins and fixed table, then staged partials
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tailbar + 2);
 
   Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
   const int tid = threadIdx.x;
@@ -127,6 +129,8 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     }
     mbar_init(accfull, 1);
     mbar_init(tabbar, 1);
+    mbar_init(&tailbar[0], 1);
+    mbar_init(&tailbar[1], 1);
     fence_mbar_init();
   }
   if (warp == GW) {
@@ -143,6 +147,8 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     if (lane == 0) {
       mbar_arrive_expect_tx(tabbar, (uint32_t)tb);
       bulk_load(tab, ws + pl.off_tab_f32, (uint32_t)tb, tabbar);
+      // the fused tail reads the fixed-point table after the main loop: have it in L2 by then
+      if (pl.fused) bulk_prefetch_l2(ws + pl.off_tab_fix, (uint32_t)tab_fix_bytes(pl.T, 0));
       int j = 0;
       for (; j < nch; ++j) {
         const int vs = j % kVStages;
@@ -353,11 +359,49 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     tc_fence_after();
     tmem_dealloc(tmem, 2 * BN);
   }
+  // single clip, cooperative launch: split-K sum, axis lines and output here.
+  // Every copy into shared memory has landed and every MMA has completed, so
+  // the operand stages are free; TMEM is released before the grid barrier.
+  if (pl.fused) fused_tail(pl, ws, sm, reinterpret_cast<int*>(tmem_slot + 1), &tailbar[0], &tailbar[1], &tmp);
 }
 
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+// CTAs of one kernel variant that fit on the device at once (attributes set on first use).
+template <int BN, int STAGES, bool FULL>
+static int tc_resident_ctas(size_t smem) {
+  constexpr int kMaxDev = 64;
+  static int cache[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 0;
+  if (cache[dev]) return cache[dev];
+  auto kern = gemm_tc_kernel<BN, STAGES, FULL>;
+  int per_sm = 0, sms = 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TcLayout<BN, STAGES>::kThreads, smem) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cache[dev] = per_sm * sms;
+  return cache[dev];
+}
+
+template <int BN, int STAGES, bool FULL>
+static bool fusable(const Plan& pl) {
+  if (pl.batch) return false;
+  const long long ctas = (long long)pl.tiles_m * pl.tiles_n * pl.splits;
+  if (ctas < 1) return false;
+  // partial rows are bulk-copied in 16-byte units: rows of 2K floats need K even
+  if (pl.K % 2 != 0) return false;
+  // the tail may use the operand stages and the FP32 table region (contiguous)
+  const size_t avail = (size_t)TcLayout<BN, STAGES>::kOps + align_up(tab_f32_bytes(pl.T, FULL), 128);
+  if (tail_smem(pl.T, pl.K, pl.splits, ctas, TcLayout<BN, STAGES>::kThreads).total > avail) return false;
+  return ctas <= tc_resident_ctas<BN, STAGES, FULL>(tc_smem_bytes<BN, STAGES>(pl.T, FULL));
+}
+
 template <int BN, int STAGES, bool FULL>
 static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cudaStream_t st) {
   const size_t smem = tc_smem_bytes<BN, STAGES>(pl.T, FULL);
@@ -366,9 +410,34 @@ static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cud
   if (e != cudaSuccess) return e;
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   dim3 grid = pl.batch ? dim3(pl.splits, 1) : dim3(pl.tiles_m * pl.tiles_n, pl.splits);
-  kern<<<grid, TcLayout<BN, STAGES>::kThreads, smem, st>>>(mp.x, mp.y, mp.s, pl, static_cast<uint8_t*>(ws));
+  if (pl.fused) {
+    // the fused tail waits at a grid barrier: every CTA must be resident,
+    // which a cooperative launch guarantees (or refuses to launch)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(TcLayout<BN, STAGES>::kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, mp.x, mp.y, mp.s, mp.part, pl, static_cast<uint8_t*>(ws));
+    count_launch(1);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
+  kern<<<grid, TcLayout<BN, STAGES>::kThreads, smem, st>>>(mp.x, mp.y, mp.s, mp.part, pl,
+                                                           static_cast<uint8_t*>(ws));
   count_launch(1);
   return cudaGetLastError();
+}
+
+bool gemm_tc_fusable(const Plan& pl) {
+  if (pl.splits == 0) return false;
+  if (pl.bn == 256) return pl.full && fusable<256, 2, true>(pl);
+  if (pl.full) return fusable<128, 3, true>(pl);
+  return fusable<128, 2, false>(pl);
 }
 
 cudaError_t launch_gemm_tc(const Plan& pl, const VertexMaps& mp, void* ws, cudaStream_t st) {

@@ -134,6 +134,12 @@ def set_splits(n):
     _lib.load().fcfs_debug_set_splits(int(n))
 
 
+def set_fuse(on):
+    """1 (default): the split-FP16 forward sums its splits and takes the axis DFT
+    inside the contraction kernel when its CTAs fit at once; 0: separate kernels."""
+    _lib.load().fcfs_debug_set_fuse(1 if on else 0)
+
+
 def set_batch_unit_chunks(n):
     """Vertex-split granularity of batch(): n pipeline chunks per unit (0: default)."""
     _lib.load().fcfs_set_batch_unit_chunks(int(n))

@@ -197,4 +197,38 @@ def test_launch_counter(fc):
     x, y, s = to_dev(clip)
     n0 = fc.launch_count()
     fc.forward(x, y, s, clip.T, K, prec="split_f16")
-    assert fc.launch_count() - n0 == 4   # prep, contraction (bins the corners), axis DFT, reduce
+    assert fc.launch_count() - n0 == 2   # prep, contraction (bins, sums splits, axis DFT, output)
+    fc.set_fuse(0)
+    try:
+        n0 = fc.launch_count()
+        fc.forward(x, y, s, clip.T, K, prec="split_f16")
+        assert fc.launch_count() - n0 == 4   # prep, contraction (bins the corners), axis DFT, reduce
+    finally:
+        fc.set_fuse(1)
+    n0 = fc.launch_count()
+    fc.forward(x, y, s, clip.T, K, prec="fp32")
+    assert fc.launch_count() - n0 == 4
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+@pytest.mark.parametrize("splits", [0, 3, 17])
+def test_fused_tail_matches_separate_kernels(fc, cfg, splits):
+    """The fused tail (grid barrier, split-K sum, axis DFT in the contraction
+    kernel) sums in the same order as the separate kernels: bit-identical."""
+    clip, K = config_clip(cfg)
+    x, y, s = to_dev(clip)
+    fc.set_splits(splits)
+    try:
+        need = fc.workspace_size(clip.V, clip.T, K, "split_f16")
+        w1, w0 = (fc.alloc_workspace(need, x.device) for _ in range(2))
+        F1, a1 = fc.forward(x, y, s, clip.T, K, prec="split_f16", workspace=w1)
+        fc.set_fuse(0)
+        F0, a0 = fc.forward(x, y, s, clip.T, K, prec="split_f16", workspace=w0)
+    finally:
+        fc.set_fuse(1)
+        fc.set_splits(0)
+    assert fc.get_status(w1) == "FCFS_OK" and fc.get_status(w0) == "FCFS_OK"
+    assert int(a1) == int(a0) == oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+    assert torch.equal(F1, F0)
+    Fo = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    assert np.max(np.abs(F1.cpu().numpy() - Fo)) / int(a1) <= TOL["split_f16"]
