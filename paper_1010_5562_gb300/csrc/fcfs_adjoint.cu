@@ -248,8 +248,7 @@ static cudaError_t launch_adj_gemm(const AdjPlan& ap, const int32_t* x, const in
   const int vb = (int)((ap.p.V + vper - 1) / vper);
   const size_t smem = align_up(tab_f32_bytes(ap.p.T, FULL), 128) + (size_t)ap.cols * R * sizeof(float);
   auto kern = adj_gemm_kernel<R, FULL>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  ensure_smem(reinterpret_cast<const void*>(kern), smem);
   kern<<<dim3(ap.row_tiles, vb, 2), kAdjThreads, smem, st>>>(ap, x, y, static_cast<uint8_t*>(ws), (int)vper);
   count_launch(1);
   return cudaGetLastError();

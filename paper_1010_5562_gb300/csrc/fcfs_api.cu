@@ -170,10 +170,62 @@ static bool encode_1d(CUtensorMap* map, const void* base, CUtensorMapDataType dt
   return r == CUDA_SUCCESS;
 }
 
+// A tensor map depends only on the address, the sizes and the box, so the
+// maps of the last call on this thread are reused when those repeat.
 bool make_vertex_maps(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, VertexMaps& mp) {
-  return encode_1d(&mp.x, x, CU_TENSOR_MAP_DATA_TYPE_INT32, (uint64_t)V) &&
-         encode_1d(&mp.y, y, CU_TENSOR_MAP_DATA_TYPE_INT32, (uint64_t)V) &&
-         encode_1d(&mp.s, s, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)V);
+  thread_local struct {
+    const void *x = nullptr, *y = nullptr, *s = nullptr;
+    int64_t V = -1;
+    CUtensorMap mx, my, ms;
+  } last;
+  if (last.x == x && last.y == y && last.s == s && last.V == V) {
+    mp.x = last.mx;
+    mp.y = last.my;
+    mp.s = last.ms;
+    return true;
+  }
+  if (!(encode_1d(&mp.x, x, CU_TENSOR_MAP_DATA_TYPE_INT32, (uint64_t)V) &&
+        encode_1d(&mp.y, y, CU_TENSOR_MAP_DATA_TYPE_INT32, (uint64_t)V) &&
+        encode_1d(&mp.s, s, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)V)))
+    return false;
+  last.x = x;
+  last.y = y;
+  last.s = s;
+  last.V = V;
+  last.mx = mp.x;
+  last.my = mp.y;
+  last.ms = mp.s;
+  return true;
+}
+
+cudaError_t ensure_smem(const void* fn, size_t bytes) {
+  struct Entry {
+    const void* fn;
+    int dev;
+    size_t bytes;
+  };
+  static std::mutex mu;
+  static Entry tab[256];
+  static int n = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  int i = 0;
+  for (; i < n; ++i)
+    if (tab[i].fn == fn && tab[i].dev == dev) break;
+  if (i < n && tab[i].bytes >= bytes) return cudaSuccess;
+  if (bytes > 0 && (e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) !=
+                       cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
+  if (i == n) {
+    if (n == 256) return cudaSuccess;   // table full: attributes set, just not remembered
+    tab[n++] = Entry{fn, dev, bytes};
+  } else {
+    tab[i].bytes = bytes;
+  }
+  return cudaSuccess;
 }
 
 // The FP32 partials of a single clip as a 3-D tensor [split][row][col] of
@@ -181,14 +233,29 @@ bool make_vertex_maps(const int32_t* x, const int32_t* y, const int8_t* s, int64
 // (32 l values) wide, over every split (read by the fused tail).
 bool make_part_map(const Plan& pl, void* ws, CUtensorMap* map) {
   if (!encode_fn() || pl.splits < 1 || pl.splits > 256 || (pl.M2 * 4) % 16 != 0) return false;
+  thread_local struct {
+    const void* base = nullptr;
+    int M2 = -1, S = -1;
+    CUtensorMap m;
+  } last;
+  const void* base = static_cast<uint8_t*>(ws) + pl.off_part;
+  if (last.base == base && last.M2 == pl.M2 && last.S == pl.splits) {
+    *map = last.m;
+    return true;
+  }
   cuuint64_t dims[3] = {(cuuint64_t)pl.M2, (cuuint64_t)pl.M2, (cuuint64_t)pl.splits};
   cuuint64_t strides[2] = {(cuuint64_t)pl.M2 * 4, (cuuint64_t)pl.M2 * pl.M2 * 4};
   cuuint32_t box[3] = {64, 2, (cuuint32_t)pl.splits};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, static_cast<uint8_t*>(ws) + pl.off_part, dims,
-                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return false;
+  last.base = base;
+  last.M2 = pl.M2;
+  last.S = pl.splits;
+  last.m = *map;
+  return true;
 }
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }

@@ -210,6 +210,22 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Fetch a tensor map (a __grid_constant__ kernel parameter) into the TMA
+// unit's descriptor cache ahead of its first use.
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the previous kernel of the stream runs;
+// griddep_wait() returns once that kernel has completed and its writes are
+// visible (immediately when there is no such dependency), and
+// griddep_launch_dependents() lets the next kernel start early.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Prefetch a 16-byte aligned range (size a multiple of 16) into L2.
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
@@ -336,6 +352,11 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
 cudaError_t launch_reduce(const Plan& pl, void* ws, float* F, int64_t* area, bool validate, cudaStream_t st);
 cudaError_t launch_gemm_simt(const Plan& pl, const int32_t* x, const int32_t* y, const int8_t* s, void* ws,
                              cudaStream_t st);
+// Give kernel `fn` at least `bytes` of dynamic shared memory and the largest
+// shared-memory carveout on the current device; the attributes are set once
+// per kernel, device and size (setting them costs a driver call per launch).
+cudaError_t ensure_smem(const void* fn, size_t bytes);
+
 bool gemm_tc_fusable(const Plan& pl);
 bool make_part_map(const Plan& pl, void* ws, CUtensorMap* map);
 cudaError_t launch_gemm_tc(const Plan& pl, const VertexMaps& maps, void* ws, cudaStream_t st);

@@ -330,7 +330,7 @@ __device__ inline void fused_tail(const Plan& pl, uint8_t* ws, uint8_t* smem, in
   if (threadIdx.x == 0) {
     // the bins and partials are generic-proxy writes of other CTAs (acquired
     // at the barrier); order them before this thread's async-proxy reads
-    asm volatile("fence.proxy.async;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     if (do_axis) {
       const uint32_t bb = 16u * (uint32_t)(T + 1), tb = (uint32_t)tab_fix_bytes(T, 0);
       mbar_arrive_expect_tx(bar_axis, bb + tb);
@@ -362,6 +362,7 @@ __device__ inline void fused_tail(const Plan& pl, uint8_t* ws, uint8_t* smem, in
       __syncthreads();
       long long v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       long long area = 0;
+#pragma unroll 4
       for (int n = threadIdx.x; n <= T; n += blockDim.x) {
         const long long wx = sbx[n], wy = sby[n];
         if ((wx | wy) == 0) continue;

@@ -24,6 +24,8 @@ namespace fcfs {
 __device__ __forceinline__ double base_cos(int r, int T) { return cospi(2.0 * (double)r / (double)T); }
 
 __global__ void prep_kernel(Plan pl, uint8_t* ws, int validate) {
+  // the contraction kernel behind this one may start its prologue now
+  griddep_launch_dependents();
   const int T = pl.T;
   const int logQ = pl.logT - 2;
   const int Q = T / 4;
@@ -255,7 +257,7 @@ cudaError_t launch_prep(const Plan& pl, void* ws, bool validate, cudaStream_t st
   int blocks = (int)min((work + 63) / 64, 2048LL);
   // every kernel of a call asks for the largest shared-memory carveout, so the
   // SMs never repartition L1/shared memory between the kernels of a call
-  cudaFuncSetAttribute(prep_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  ensure_smem(reinterpret_cast<const void*>(prep_kernel), 0);
   prep_kernel<<<blocks, 64, 0, st>>>(pl, static_cast<uint8_t*>(ws), validate ? 1 : 0);
   count_launch(1);
   return cudaGetLastError();
@@ -282,8 +284,7 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
   const int nblocks = (pl.T + 1 + nper - 1) / nper;
   const size_t smem = axis_smem_bytes(pl.T, pl.full);
   auto kern = pl.batch ? axis_dft_kernel<true> : axis_dft_kernel<false>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  ensure_smem(reinterpret_cast<const void*>(kern), smem);
   kern<<<dim3(kblocks, nblocks, clips), kAxisThreads, smem, st>>>(pl, static_cast<uint8_t*>(ws), nper);
   count_launch(1);
   return cudaGetLastError();
@@ -292,7 +293,7 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
 cudaError_t launch_reduce(const Plan& pl, void* ws, float* F, int64_t* area, bool validate, cudaStream_t st) {
   const long long n = (long long)(pl.K + 1) * (pl.K + 1);
   const dim3 blocks((unsigned)((n + 255) / 256), pl.batch ? pl.n_clips : 1);
-  cudaFuncSetAttribute(reduce_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  ensure_smem(reinterpret_cast<const void*>(reduce_kernel), 0);
   reduce_kernel<<<blocks, 256, 0, st>>>(pl, static_cast<uint8_t*>(ws), reinterpret_cast<float2*>(F),
                                         reinterpret_cast<long long*>(area), validate ? 1 : 0);
   count_launch(1);

@@ -130,12 +130,10 @@ cudaError_t launch_gemm_simt(const Plan& pl, const int32_t* x, const int32_t* y,
   const size_t smem = tab_f32_bytes(pl.T, pl.full) + 2 * kSChunk * kSB * sizeof(float) + 3 * kSChunk * 4;
   dim3 grid = pl.batch ? dim3(pl.splits, 1) : dim3(pl.tiles_m * pl.tiles_n, pl.splits);
   if (pl.full) {
-    cudaFuncSetAttribute(gemm_simt_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(gemm_simt_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    ensure_smem(reinterpret_cast<const void*>(gemm_simt_kernel<true>), smem);
     gemm_simt_kernel<true><<<grid, kSThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws));
   } else {
-    cudaFuncSetAttribute(gemm_simt_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(gemm_simt_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    ensure_smem(reinterpret_cast<const void*>(gemm_simt_kernel<false>), smem);
     gemm_simt_kernel<false><<<grid, kSThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws));
   }
   count_launch(1);

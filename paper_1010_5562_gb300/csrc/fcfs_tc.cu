@@ -112,6 +112,10 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
 
+  // launched behind the prep kernel (or, in a batch, the unit-list kernel):
+  // the unit list is read right away; a single clip's prologue below touches
+  // no memory those kernels write, so it overlaps them
+  if (pl.batch) griddep_wait();
   const Unit U = unit_of_block(pl, ws, kBM, BN);
   if (!U.live) return;   // unit slots beyond the batch's count: nothing allocated yet
   const int tm = U.tm, tn = U.tn;
@@ -133,6 +137,12 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     mbar_init(&tailbar[1], 1);
     fence_mbar_init();
   }
+  if (warp == GW + 1 && lane == 0) {
+    prefetch_tensormap(&tmx);
+    prefetch_tensormap(&tmy);
+    prefetch_tensormap(&tms);
+    if (pl.fused) prefetch_tensormap(&tmp);
+  }
   if (warp == GW) {
     tmem_alloc(tmem_slot, 2 * BN);   // D1 (hi*hi) and D2 (hi*lo + lo*hi)
     tmem_relinquish();
@@ -141,6 +151,8 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // tables, bins and counters are written by the prep kernel
+  if (!pl.batch) griddep_wait();
 
   if (warp == GW + 1) {
     // ---------------- TMA producer ----------------
@@ -214,7 +226,10 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     const uint32_t logQ = (uint32_t)pl.logT - 2u;
     const uint32_t ops_a = smem_u32(ops);
     const int coord_off = isA ? 0 : 384;
-    const bool do_bin = pl.bin_in_gemm && tm == 0 && tn == 0 && run == 0;
+    // every corner is binned once, spread over the tiles: the CTA of tile t
+    // bins the chunks j = t mod (tiles) of its vertex range
+    const int ntiles = pl.tiles_m * pl.tiles_n, tile = tm * pl.tiles_n + tn;
+    const bool bin_run = pl.bin_in_gemm && run == 0;
     // swizzled byte offset of this thread's 16-byte chunk in row r: (oct ^ (r & 7)) << 4;
     // rows 2(i0 + r) have r & 7 = 2r & 7 because i0 is a multiple of 8
     uint32_t xo[8];
@@ -246,7 +261,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
         vmask[q] = (lo_ok ? 0xFFFFu : 0u) | (hi_ok ? 0xFFFF0000u : 0u);
       }
       const bool masked = isA && (first + 8 > v1);
-      if (do_bin) {   // each corner of the chunk once: the 8 threads of A run 0
+      if (bin_run && j % ntiles == tile) {   // each corner of the chunk once: the 8 threads of A run 0
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int idx = off + oct * 8 + t;
@@ -406,31 +421,41 @@ template <int BN, int STAGES, bool FULL>
 static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cudaStream_t st) {
   const size_t smem = tc_smem_bytes<BN, STAGES>(pl.T, FULL);
   auto kern = gemm_tc_kernel<BN, STAGES, FULL>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
-  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   dim3 grid = pl.batch ? dim3(pl.splits, 1) : dim3(pl.tiles_m * pl.tiles_n, pl.splits);
+  // The kernel may start while the previous kernel of the stream finishes
+  // (programmatic stream serialisation; it waits for it in griddep_wait()).
+  // The fused tail waits at a grid barrier, so every CTA must be resident:
+  // a cooperative launch guarantees that (or refuses to launch).  Where the
+  // runtime refuses the two attributes together, the launch drops the first.
+  static bool pdl_ok = true;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(TcLayout<BN, STAGES>::kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[2];
+  int na = 0;
   if (pl.fused) {
-    // the fused tail waits at a grid barrier: every CTA must be resident,
-    // which a cooperative launch guarantees (or refuses to launch)
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(TcLayout<BN, STAGES>::kThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, mp.x, mp.y, mp.s, mp.part, pl, static_cast<uint8_t*>(ws));
-    count_launch(1);
-    return e != cudaSuccess ? e : cudaGetLastError();
+    at[na].id = cudaLaunchAttributeCooperative;
+    at[na++].val.cooperative = 1;
   }
-  kern<<<grid, TcLayout<BN, STAGES>::kThreads, smem, st>>>(mp.x, mp.y, mp.s, mp.part, pl,
-                                                           static_cast<uint8_t*>(ws));
+  if (pdl_ok) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na++].val.programmaticStreamSerializationAllowed = 1;
+  }
+  cfg.attrs = at;
+  cfg.numAttrs = na;
+  e = cudaLaunchKernelEx(&cfg, kern, mp.x, mp.y, mp.s, mp.part, pl, static_cast<uint8_t*>(ws));
+  if (e != cudaSuccess && pdl_ok) {
+    cudaGetLastError();
+    pdl_ok = false;
+    cfg.numAttrs = na - 1;
+    e = cudaLaunchKernelEx(&cfg, kern, mp.x, mp.y, mp.s, mp.part, pl, static_cast<uint8_t*>(ws));
+  }
   count_launch(1);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 bool gemm_tc_fusable(const Plan& pl) {

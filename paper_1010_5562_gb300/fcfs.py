@@ -59,9 +59,8 @@ def forward(x, y, s, T, K, prec="split_f16", validate=False, out=None, area_out=
         out = torch.empty((W, W), dtype=torch.complex64, device=dev)
     if area_out is None:
         area_out = torch.empty((1,), dtype=torch.int64, device=dev)
-    need = workspace_size(x.numel(), T, K, prec)
-    if workspace is None:
-        workspace = alloc_workspace(need, dev)
+    if workspace is None:   # (a given workspace is checked by the library)
+        workspace = alloc_workspace(workspace_size(x.numel(), T, K, prec), dev)
     code = lib.fcfs_forward(_ptr(x), _ptr(y), _ptr(s), x.numel(), int(T), int(K), _prec(prec),
                             FLAG_VALIDATE if validate else 0, _ptr(out), _ptr(area_out),
                             _ptr(workspace), workspace.numel(), _stream(stream))
