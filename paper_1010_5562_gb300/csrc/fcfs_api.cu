@@ -228,24 +228,24 @@ cudaError_t ensure_smem(const void* fn, size_t bytes) {
   return cudaSuccess;
 }
 
-// The FP32 partials of a single clip as a 3-D tensor [split][row][col] of
-// M2 x M2 x splits floats; one box is the cos and sin rows of one k, 64 floats
-// (32 l values) wide, over every split (read by the fused tail).
-bool make_part_map(const Plan& pl, void* ws, CUtensorMap* map) {
-  if (!encode_fn() || pl.splits < 1 || pl.splits > 256 || (pl.M2 * 4) % 16 != 0) return false;
+// The first `parts` FP32 partials of a single clip as a 3-D tensor
+// [part][row][col] of M2 x M2 x parts floats; one box is the cos and sin rows
+// of one k, 64 floats (32 l values) wide, over every part (read by the fused tail).
+bool make_part_map(const Plan& pl, void* ws, int parts, CUtensorMap* map) {
+  if (!encode_fn() || parts < 1 || parts > 256 || (pl.M2 * 4) % 16 != 0) return false;
   thread_local struct {
     const void* base = nullptr;
     int M2 = -1, S = -1;
     CUtensorMap m;
   } last;
   const void* base = static_cast<uint8_t*>(ws) + pl.off_part;
-  if (last.base == base && last.M2 == pl.M2 && last.S == pl.splits) {
+  if (last.base == base && last.M2 == pl.M2 && last.S == parts) {
     *map = last.m;
     return true;
   }
-  cuuint64_t dims[3] = {(cuuint64_t)pl.M2, (cuuint64_t)pl.M2, (cuuint64_t)pl.splits};
+  cuuint64_t dims[3] = {(cuuint64_t)pl.M2, (cuuint64_t)pl.M2, (cuuint64_t)parts};
   cuuint64_t strides[2] = {(cuuint64_t)pl.M2 * 4, (cuuint64_t)pl.M2 * pl.M2 * 4};
-  cuuint32_t box[3] = {64, 2, (cuuint32_t)pl.splits};
+  cuuint32_t box[3] = {64, 2, (cuuint32_t)parts};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -253,7 +253,7 @@ bool make_part_map(const Plan& pl, void* ws, CUtensorMap* map) {
   if (r != CUDA_SUCCESS) return false;
   last.base = base;
   last.M2 = pl.M2;
-  last.S = pl.splits;
+  last.S = parts;
   last.m = *map;
   return true;
 }
@@ -296,9 +296,10 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
   pl.bin_in_gemm = validate ? 0 : 1;
   // one resident wave of tensor-core CTAs: they also sum the splits, take the
   // axis DFT and write the output behind a grid barrier (two launches per call)
-  if (prec == FCFS_PREC_SPLIT_F16 && !validate && g_fuse && V > 0 && gemm_tc_fusable(pl) &&
-      make_part_map(pl, ws, &mp.part)) {
+  const int cluster = (prec == FCFS_PREC_SPLIT_F16 && !validate && g_fuse && V > 0) ? gemm_tc_fuse_cluster(pl) : 0;
+  if (cluster > 0 && make_part_map(pl, ws, pl.splits / cluster, &mp.part)) {
     pl.fused = 1;
+    pl.cluster = cluster;
     pl.F = reinterpret_cast<float2*>(F);
     pl.area_out = reinterpret_cast<long long*>(area);
   }

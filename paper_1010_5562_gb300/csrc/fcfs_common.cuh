@@ -38,6 +38,8 @@ struct Plan {
   int32_t bin_in_gemm;         // 1: the contraction kernel bins the corners for the axis lines
   int32_t fused;               // 1: the contraction kernel also runs the split-K sum, the
                                //    axis-line DFT and the output (cooperative launch)
+  int32_t cluster;             // fused: 2 when CTAs of consecutive split pairs form a cluster
+                               //    and add their partial tiles in shared memory first, else 1
   float2* F;                   // output block (fused only)
   long long* area_out;         // output area (fused only)
   int32_t batch;               // 0: one clip; 1: batch
@@ -226,6 +228,36 @@ __device__ __forceinline__ void griddep_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Thread-block clusters: rank, peer addresses, barrier, bulk copy to a peer
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the same shared-memory offset in CTA `rank`
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+// Every thread of every CTA of the cluster: orders shared-memory writes before
+// the barrier with accesses to them (from any CTA of the cluster) after it.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Bulk copy from this CTA's shared memory to a peer's (dst and bar are
+// shared::cluster addresses of the peer); 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_copy_to_peer(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "r"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the source reads of every committed bulk copy of this thread are done
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
 // Prefetch a 16-byte aligned range (size a multiple of 16) into L2.
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
@@ -357,8 +389,9 @@ cudaError_t launch_gemm_simt(const Plan& pl, const int32_t* x, const int32_t* y,
 // per kernel, device and size (setting them costs a driver call per launch).
 cudaError_t ensure_smem(const void* fn, size_t bytes);
 
-bool gemm_tc_fusable(const Plan& pl);
-bool make_part_map(const Plan& pl, void* ws, CUtensorMap* map);
+// 0: the call cannot be fused; else the cluster size (1 or 2) of the fused launch
+int gemm_tc_fuse_cluster(const Plan& pl);
+bool make_part_map(const Plan& pl, void* ws, int parts, CUtensorMap* map);
 cudaError_t launch_gemm_tc(const Plan& pl, const VertexMaps& maps, void* ws, cudaStream_t st);
 void count_launch(int n);
 

@@ -216,7 +216,7 @@ __device__ inline bool grid_barrier(unsigned* count, unsigned expected, Status* 
 //  2. one thread issues the CTA's copies: the bins and the fixed-point table
 //     (bulk copies, one mbarrier), then one tiled TMA load per unit of the
 //     CTA's share of the quarter plane -- the cos and sin rows of one k, 32
-//     consecutive l, every split: one box of the 3-D partials tensor map --
+//     consecutive l, every partial: one box of the 3-D partials tensor map --
 //     on a second mbarrier;
 //  3. the axis-line DFT of the CTA's share of the frequencies over all bins
 //     (in-CTA integer sums), while the partials land; CTA 0 also writes the
@@ -311,7 +311,8 @@ __device__ inline void fused_tail(const Plan& pl, uint8_t* ws, uint8_t* smem, in
   const unsigned nblk = gridDim.x * gridDim.y;
   const unsigned b = blockIdx.y * gridDim.x + blockIdx.x;
   if (!grid_barrier(&sync[0], nblk, st, 0x7000u, sflag)) return;
-  const int K = pl.K, T = pl.T, logQ = pl.logT - 2, S = pl.splits;
+  // partials left after the in-cluster sums: one per cluster of splits
+  const int K = pl.K, T = pl.T, logQ = pl.logT - 2, S = pl.splits / pl.cluster;
   float2* F = pl.F;
   const TailSmem ts = tail_smem(T, K, S, nblk, blockDim.x);
   uint8_t* stage = smem;

@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
   uint64_t* accfull = vempty + kVStages;
   uint64_t* tabbar = accfull + 1;
   uint64_t* tailbar = tabbar + 1;   // fused tail: bins and fixed table, then staged partials
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tailbar + 2);
+  uint64_t* recvbar = tailbar + 2;  // cluster pair: the peer's half tile has landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(recvbar + 1);
 
   Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
   const int tid = threadIdx.x;
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     mbar_init(tabbar, 1);
     mbar_init(&tailbar[0], 1);
     mbar_init(&tailbar[1], 1);
+    mbar_init(recvbar, 1);
     fence_mbar_init();
   }
   if (warp == GW + 1 && lane == 0) {
@@ -347,6 +349,14 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
           tmem_wait_ld();
 #pragma unroll
           for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(r2[q]));
+          if (pl.fused && pl.cluster == 2) {
+            // tile row `row` in shared memory, 16-byte chunks XOR-swizzled by row & 7
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              st_shared_v4(smem_u32(ops) + (uint32_t)row * (BN * 4) + ((uint32_t)((cb * 8 + q) ^ (row & 7)) << 4),
+                           r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+            continue;
+          }
           if (m < M2) {
             float* dst = U.P + (size_t)row * U.ld + cb * 32;
             if (n0 + 32 <= M2 && (M2 & 3) == 0) {
@@ -361,10 +371,56 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
             }
           }
         }
+      } else if (pl.fused && pl.cluster == 2) {
+        for (int c = 0; c < BN / 4; ++c)
+          st_shared_v4(smem_u32(ops) + (uint32_t)row * (BN * 4) + ((uint32_t)(c ^ (row & 7)) << 4), 0u, 0u, 0u, 0u);
       } else if (m < M2) {
         for (int n = tn * BN; n < min(M2, tn * BN + BN); ++n) U.P[(size_t)row * U.ld + (n - tn * BN)] = 0.f;
       }
     }
+  }
+
+  if (pl.fused && pl.cluster == 2) {
+    // Split pairs: the two CTAs of the cluster hold the same output tile for
+    // splits 2g and 2g + 1.  Each sends the half of its tile that the other
+    // sums (rows [64 r', 64 r' + 64) for peer rank r') with one bulk copy into
+    // the peer's shared memory, adds the received half to its own in split
+    // order and writes the sum as partial g: half the partial bytes in global
+    // memory.  The operand stages are free: the last MMA has completed.
+    constexpr uint32_t kRowBytes = BN * 4, kHalf = (kBM / 2) * kRowBytes;
+    const uint32_t rank = cluster_ctarank(), peer = rank ^ 1u;
+    const uint32_t tile = smem_u32(ops), recv = tile + kBM * kRowBytes;
+    if (tid == 0) mbar_arrive_expect_tx(recvbar, kHalf);   // before the barrier the peer's copy waits for
+    fence_proxy_async_smem();   // the tile (generic writes) before the bulk copy reads it
+    __syncwarp();               // the barrier is warp-aligned: reconverge after the role branches
+    cluster_sync_all();
+    if (tid == 0) {
+      bulk_copy_to_peer(mapa_shared(recv, peer), tile + peer * kHalf, kHalf, mapa_shared(smem_u32(recvbar), peer));
+      bulk_commit();
+    }
+    const bool got = mbar_wait(recvbar, 0, st, 9);
+    const int M2 = pl.M2;
+    float* out = reinterpret_cast<float*>(ws + pl.off_part) + (size_t)(blockIdx.y >> 1) * M2 * M2;
+    for (int e = tid; e < (kBM / 2) * (BN / 4) && got; e += L::kThreads) {
+      const int rr = e / (BN / 4), c = e % (BN / 4);
+      const int row = (int)rank * (kBM / 2) + rr;
+      const uint32_t sw = (uint32_t)rr * kRowBytes + ((uint32_t)(c ^ (row & 7)) << 4);
+      const float4 mine = *reinterpret_cast<const float4*>(ops + rank * kHalf + sw);
+      const float4 theirs = *reinterpret_cast<const float4*>(ops + kBM * kRowBytes + sw);
+      const float4 a = rank == 0 ? mine : theirs, b2 = rank == 0 ? theirs : mine;   // split 2g first
+      const float4 v = make_float4(a.x + b2.x, a.y + b2.y, a.z + b2.z, a.w + b2.w);
+      const int m = tm * kBM + row, n = tn * BN + 4 * c;
+      if (m < M2 && n < M2) {
+        float* dst = out + (size_t)m * M2 + n;
+        if (n + 4 <= M2) {
+          *reinterpret_cast<float4*>(dst) = v;
+        } else {
+          const float vv[4] = {v.x, v.y, v.z, v.w};
+          for (int i = 0; i < M2 - n; ++i) dst[i] = vv[i];
+        }
+      }
+    }
+    if (tid == 0) bulk_wait_read_all();   // the outgoing copy has read the tile before anything reuses it
   }
 
   tc_fence_before();
@@ -383,38 +439,70 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-// CTAs of one kernel variant that fit on the device at once (attributes set on first use).
+// CTAs of one kernel variant that fit on the device at once, in clusters of
+// C (1 or 2) along the split dimension (cached per device).
 template <int BN, int STAGES, bool FULL>
-static int tc_resident_ctas(size_t smem) {
+static int tc_resident_ctas(size_t smem, int C) {
   constexpr int kMaxDev = 64;
-  static int cache[kMaxDev] = {};
+  static int cache[kMaxDev][3] = {};
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 0;
-  if (cache[dev]) return cache[dev];
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev || C < 1 || C > 2) return 0;
+  if (cache[dev][C]) return cache[dev][C];
   auto kern = gemm_tc_kernel<BN, STAGES, FULL>;
-  int per_sm = 0, sms = 0;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TcLayout<BN, STAGES>::kThreads, smem) !=
-          cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
+  if (ensure_smem(reinterpret_cast<const void*>(kern), smem) != cudaSuccess) return 0;
+  int n = 0;
+  if (C == 1) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TcLayout<BN, STAGES>::kThreads, smem) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    n = per_sm * sms;
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1, C);
+    cfg.blockDim = dim3(TcLayout<BN, STAGES>::kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = C;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, reinterpret_cast<const void*>(kern), &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    n = clusters * C;
   }
-  cache[dev] = per_sm * sms;
-  return cache[dev];
+  cache[dev][C] = n;
+  return n;
 }
 
+// Cluster size of a fused launch of this variant (2: split pairs, 1: none), 0
+// if the call cannot be fused.
 template <int BN, int STAGES, bool FULL>
-static bool fusable(const Plan& pl) {
-  if (pl.batch) return false;
+static int fuse_cluster(const Plan& pl) {
+  if (pl.batch) return 0;
   const long long ctas = (long long)pl.tiles_m * pl.tiles_n * pl.splits;
-  if (ctas < 1) return false;
+  if (ctas < 1) return 0;
   // partial rows are bulk-copied in 16-byte units: rows of 2K floats need K even
-  if (pl.K % 2 != 0) return false;
+  if (pl.K % 2 != 0) return 0;
   // the tail may use the operand stages and the FP32 table region (contiguous)
   const size_t avail = (size_t)TcLayout<BN, STAGES>::kOps + align_up(tab_f32_bytes(pl.T, FULL), 128);
-  if (tail_smem(pl.T, pl.K, pl.splits, ctas, TcLayout<BN, STAGES>::kThreads).total > avail) return false;
-  return ctas <= tc_resident_ctas<BN, STAGES, FULL>(tc_smem_bytes<BN, STAGES>(pl.T, FULL));
+  const size_t smem = tc_smem_bytes<BN, STAGES>(pl.T, FULL);
+  for (int C : {2, 1}) {
+    if (pl.splits % C != 0) continue;
+    // a pair keeps its tile and the peer's half in the operand stages
+    if (C == 2 && (size_t)kBM * BN * 4 * 3 / 2 > (size_t)TcLayout<BN, STAGES>::kOps) continue;
+    if (tail_smem(pl.T, pl.K, pl.splits / C, ctas, TcLayout<BN, STAGES>::kThreads).total > avail) continue;
+    if (ctas <= tc_resident_ctas<BN, STAGES, FULL>(smem, C)) return C;
+  }
+  return 0;
 }
 
 template <int BN, int STAGES, bool FULL>
@@ -435,11 +523,17 @@ static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cud
   cfg.blockDim = dim3(TcLayout<BN, STAGES>::kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[2];
+  cudaLaunchAttribute at[3];
   int na = 0;
   if (pl.fused) {
     at[na].id = cudaLaunchAttributeCooperative;
     at[na++].val.cooperative = 1;
+    if (pl.cluster > 1) {
+      at[na].id = cudaLaunchAttributeClusterDimension;
+      at[na].val.clusterDim.x = 1;
+      at[na].val.clusterDim.y = pl.cluster;
+      at[na++].val.clusterDim.z = 1;
+    }
   }
   if (pdl_ok) {
     at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -458,11 +552,11 @@ static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cud
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-bool gemm_tc_fusable(const Plan& pl) {
-  if (pl.splits == 0) return false;
-  if (pl.bn == 256) return pl.full && fusable<256, 2, true>(pl);
-  if (pl.full) return fusable<128, 3, true>(pl);
-  return fusable<128, 2, false>(pl);
+int gemm_tc_fuse_cluster(const Plan& pl) {
+  if (pl.splits == 0) return 0;
+  if (pl.bn == 256) return pl.full ? fuse_cluster<256, 2, true>(pl) : 0;
+  if (pl.full) return fuse_cluster<128, 3, true>(pl);
+  return fuse_cluster<128, 2, false>(pl);
 }
 
 cudaError_t launch_gemm_tc(const Plan& pl, const VertexMaps& mp, void* ws, cudaStream_t st) {

@@ -211,10 +211,13 @@ def test_launch_counter(fc):
 
 
 @pytest.mark.parametrize("cfg", [1, 2])
-@pytest.mark.parametrize("splits", [0, 3, 17])
+@pytest.mark.parametrize("splits", [0, 2, 3, 16, 17])
 def test_fused_tail_matches_separate_kernels(fc, cfg, splits):
-    """The fused tail (grid barrier, split-K sum, axis DFT in the contraction
-    kernel) sums in the same order as the separate kernels: bit-identical."""
+    """The fused path (split pairs summed in shared memory, grid barrier,
+    split-K sum and axis DFT in the contraction kernel) against the separate
+    kernels.  With an odd split count there are no pairs and the summation
+    order is the same: bit-identical.  A pair adds its two partials in FP32
+    first: one more rounding.  Axis lines and areas are exact either way."""
     clip, K = config_clip(cfg)
     x, y, s = to_dev(clip)
     fc.set_splits(splits)
@@ -228,7 +231,14 @@ def test_fused_tail_matches_separate_kernels(fc, cfg, splits):
         fc.set_fuse(1)
         fc.set_splits(0)
     assert fc.get_status(w1) == "FCFS_OK" and fc.get_status(w0) == "FCFS_OK"
-    assert int(a1) == int(a0) == oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
-    assert torch.equal(F1, F0)
+    A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+    assert int(a1) == int(a0) == A
+    F1n, F0n = F1.cpu().numpy(), F0.cpu().numpy()
+    if splits % 2:
+        assert np.array_equal(F1n, F0n)
+    else:
+        assert np.max(np.abs(F1n - F0n)) / A <= 1e-7
+        np.testing.assert_array_equal(F1n[K, :], F0n[K, :])   # axis lines: exact integer sums
+        np.testing.assert_array_equal(F1n[:, K], F0n[:, K])
     Fo = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
-    assert np.max(np.abs(F1.cpu().numpy() - Fo)) / int(a1) <= TOL["split_f16"]
+    assert np.max(np.abs(F1n - Fo)) / A <= TOL["split_f16"]
