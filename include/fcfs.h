@@ -195,6 +195,11 @@ void fcfs_profile_enable(int32_t on);
 int32_t fcfs_profile_read(float* ms, int32_t n);
 void fcfs_debug_set_splits(int32_t n);
 void fcfs_debug_set_fuse(int32_t on);
+/* fcfs_debug_set_pair(0) keeps single-clip split-FP16 calls on one-CTA
+ * 128 x 256 tiles; 1 (the default) runs clips with 2K >= 256 on CTA pairs
+ * (2-SM MMA on 256 x 256 tiles).  Must not change between fcfs_workspace_size
+ * and the call that uses the workspace. */
+void fcfs_debug_set_pair(int32_t on);
 
 /* Vertex-split granularity of fcfs_batch: n pipeline chunks (64 corners on the
  * tensor path, 32 on the FP32 path) per unit; 0 restores the default of 4096

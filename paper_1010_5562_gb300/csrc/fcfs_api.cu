@@ -71,6 +71,7 @@ static int choose_splits(long long tiles, long long nchunks, long long slots, lo
 
 static int g_split_override = 0;   // testing/autotuning hook, 0 = automatic
 static int g_fuse = 1;             // testing hook: 0 keeps the axis and reduce kernels separate
+static int g_pair = 1;             // testing hook: 0 keeps single clips on one-CTA tiles
 
 // Tag of the cached tables: their kind, period, fixed-point scale and offsets.
 static uint64_t table_tag(const Plan& pl) {
@@ -85,7 +86,9 @@ static uint64_t table_tag(const Plan& pl) {
   return h | 1u;   // never 0, so zeroed memory is never mistaken for a tag
 }
 
-fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
+// single: a one-clip forward call, whose tensor-core contraction may run on
+// CTA pairs; batches and the adjoint use one-CTA tiles.
+fcfs_status make_plan_ex(int64_t V, int32_t T, int32_t K, int32_t prec, bool single, Plan& pl) {
   memset(&pl, 0, sizeof(pl));
   if (T < 4 || T > 65536 || (T & (T - 1)) != 0) return FCFS_EUNSUPPORTED;
   if (K < 1 || K > 4096) return FCFS_EUNSUPPORTED;
@@ -111,6 +114,13 @@ fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
   }
   pl.tiles_m = (pl.M2 + pl.bm - 1) / pl.bm;
   pl.tiles_n = (pl.M2 + pl.bn - 1) / pl.bn;
+  if (tc && single && g_pair && pl.M2 >= 256) {
+    // 256 x 256 tiles on CTA pairs: tile row pair (2 tm', 2 tm' + 1), one per CTA
+    pl.pair = 1;
+    pl.bn = 256;
+    pl.tiles_n = (pl.M2 + 255) / 256;
+    pl.tiles_m = 2 * pl.tiles_n;
+  }
   const long long nchunks = (V + pl.chunk - 1) / pl.chunk;
   const long long slots = (long long)sm_count() * (tc ? 1 : 2);
   int s = g_split_override > 0 ? (int)std::min<long long>(g_split_override, nchunks)
@@ -140,6 +150,10 @@ fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
   return FCFS_OK;
 }
 
+fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
+  return make_plan_ex(V, T, K, prec, false, pl);
+}
+
 // ---------------------------------------------------------------------------
 // Tensor maps for the 1-D TMA vertex loads
 // ---------------------------------------------------------------------------
@@ -158,45 +172,6 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return g_encode;
 }
 
-static bool encode_1d(CUtensorMap* map, const void* base, CUtensorMapDataType dt, uint64_t n) {
-  if (!encode_fn()) return false;
-  cuuint64_t dims[1] = {n};
-  cuuint64_t strides[1] = {0};
-  cuuint32_t box[1] = {80};
-  cuuint32_t estr[1] = {1};
-  CUresult r = g_encode(map, dt, 1, const_cast<void*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
-// A tensor map depends only on the address, the sizes and the box, so the
-// maps of the last call on this thread are reused when those repeat.
-bool make_vertex_maps(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, VertexMaps& mp) {
-  thread_local struct {
-    const void *x = nullptr, *y = nullptr, *s = nullptr;
-    int64_t V = -1;
-    CUtensorMap mx, my, ms;
-  } last;
-  if (last.x == x && last.y == y && last.s == s && last.V == V) {
-    mp.x = last.mx;
-    mp.y = last.my;
-    mp.s = last.ms;
-    return true;
-  }
-  if (!(encode_1d(&mp.x, x, CU_TENSOR_MAP_DATA_TYPE_INT32, (uint64_t)V) &&
-        encode_1d(&mp.y, y, CU_TENSOR_MAP_DATA_TYPE_INT32, (uint64_t)V) &&
-        encode_1d(&mp.s, s, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)V)))
-    return false;
-  last.x = x;
-  last.y = y;
-  last.s = s;
-  last.V = V;
-  last.mx = mp.x;
-  last.my = mp.y;
-  last.ms = mp.s;
-  return true;
-}
 
 cudaError_t ensure_smem(const void* fn, size_t bytes) {
   struct Entry {
@@ -282,12 +257,14 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
   if (V > 0 && (!x || !y || !s || !aligned16(x) || !aligned16(y) || !aligned16(s))) return FCFS_EINVAL;
   if (flags & ~(uint32_t)FCFS_FLAG_VALIDATE) return FCFS_EINVAL;
   Plan pl;
-  fcfs_status r = make_plan(V, T, K, prec, pl);
+  fcfs_status r = make_plan_ex(V, T, K, prec, true, pl);
   if (r != FCFS_OK) return r;
   if ((r = check_ws(pl, ws, ws_bytes)) != FCFS_OK) return r;
   const bool validate = (flags & FCFS_FLAG_VALIDATE) != 0;
   VertexMaps mp{};
-  if (prec == FCFS_PREC_SPLIT_F16 && V > 0 && !make_vertex_maps(x, y, s, V, mp)) return FCFS_ECUDA;
+  pl.vx = x;
+  pl.vy = y;
+  pl.vsg = s;
   prof_mark(0, st);
   FCFS_CU(launch_prep(pl, ws, validate, st));
   prof_mark(1, st);
@@ -348,7 +325,7 @@ uint64_t fcfs_launch_count(void) { return g_launches.load(); }
 
 size_t fcfs_workspace_size(int64_t V, int32_t T, int32_t K, int32_t prec) {
   Plan pl;
-  if (make_plan(V, T, K, prec, pl) != FCFS_OK) return 0;
+  if (make_plan_ex(V, T, K, prec, true, pl) != FCFS_OK) return 0;
   return pl.total;
 }
 
@@ -370,6 +347,7 @@ fcfs_status fcfs_get_status(const void* workspace, void* stream) {
 // Test hook: force the number of vertex splits (0 restores the automatic choice).
 void fcfs_debug_set_splits(int32_t s) { g_split_override = s; }
 void fcfs_debug_set_fuse(int32_t on) { g_fuse = on ? 1 : 0; }
+void fcfs_debug_set_pair(int32_t on) { g_pair = on ? 1 : 0; }
 
 void fcfs_profile_enable(int32_t on) { g_prof = on != 0; }
 

@@ -18,7 +18,6 @@ namespace fcfs {
 fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl);
 
 fcfs_status check_ws(const Plan& pl, void* ws, size_t ws_bytes);
-bool make_vertex_maps(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, VertexMaps& mp);
 
 static int g_unit_chunks = 0;   // 0: default (4096 corners per unit)
 
@@ -90,7 +89,9 @@ static fcfs_status batch_impl(const int32_t* x, const int32_t* y, const int8_t* 
   if (r != FCFS_OK) return r;
   if ((r = check_ws(pl, ws, ws_bytes)) != FCFS_OK) return r;
   VertexMaps mp{};
-  if (prec == FCFS_PREC_SPLIT_F16 && V > 0 && !make_vertex_maps(x, y, s, V, mp)) return FCFS_ECUDA;
+  pl.vx = x;
+  pl.vy = y;
+  pl.vsg = s;
   if (launch_prep(pl, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
   batch_units_kernel<<<1, 1024, 0, st>>>(pl, static_cast<uint8_t*>(ws));
   count_launch(1);

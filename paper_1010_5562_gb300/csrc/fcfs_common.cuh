@@ -35,11 +35,16 @@ struct Plan {
   uint64_t tag;        // identifies the tables cached in this workspace layout
   // batch mode (several clips): the contraction kernels walk units
   // (clip, tile, vertex split) instead of (tile, split)
+  int32_t pair;                // 1: the tensor-core contraction runs on CTA pairs (2-SM MMA,
+                               //    256 x 256 tiles; a CTA holds 128 rows of each)
   int32_t bin_in_gemm;         // 1: the contraction kernel bins the corners for the axis lines
   int32_t fused;               // 1: the contraction kernel also runs the split-K sum, the
                                //    axis-line DFT and the output (cooperative launch)
   int32_t cluster;             // fused: 2 when CTAs of consecutive split pairs form a cluster
                                //    and add their partial tiles in shared memory first, else 1
+  const int32_t* vx;           // corner coordinates and signs (device; read by the
+  const int32_t* vy;           //    tensor-core contraction)
+  const int8_t* vsg;
   float2* F;                   // output block (fused only)
   long long* area_out;         // output area (fused only)
   int32_t batch;               // 0: one clip; 1: batch
@@ -301,6 +306,70 @@ __device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint
       : "memory");
 }
 // Arrive on `bar` once every tcgen05 op issued so far by this thread has completed.
+// CTA-pair (2-SM) forms: the pair is ranks 0 and 1 of a cluster of two.
+// Allocation and release are collective (one warp in each CTA); the MMA is
+// issued by one thread of rank 0, reads A and B from both CTAs' shared memory
+// at the same offsets (rank r holds A rows [128 r, 128 r + 128) and B rows
+// [N/2 r, N/2 r + N/2)) and accumulates rows [128 r, ..) into rank r's TMEM.
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish_pair() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_mma_f16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                                uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// one arrive on the mbarrier at this offset in both CTAs of the pair once the
+// pair's MMAs issued so far have completed
+__device__ __forceinline__ void tc_commit_pair(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+// arrive on the mbarrier at this offset in CTA `rank` of the cluster (release at cluster scope)
+__device__ __forceinline__ void mbar_arrive_cluster(uint64_t* bar, uint32_t rank) {
+  uint32_t a;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(bar)), "r"(rank));
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded like mbar_wait, for barriers that threads of the peer CTA arrive on
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, Status* st, unsigned site) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  long long t0 = clock64();
+  while (!mbar_try_wait_cluster(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) {
+      set_status(st, FCFS_ETIMEOUT, site);
+      return false;
+    }
+  }
+  return true;
+}
+
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(bar))
@@ -373,9 +442,9 @@ __device__ __forceinline__ float2 f32_lookup(const float* tab, uint32_t p, uint3
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers (defined in the .cu files)
 // ---------------------------------------------------------------------------
+// Tensor maps of a contraction launch
 struct VertexMaps {
-  CUtensorMap x, y, s;
-  CUtensorMap part;   // FP32 partials [split][row][col] (fused single-clip calls only)
+  CUtensorMap part;   // FP32 partials [part][row][col] (fused single-clip calls only)
 };
 
 cudaError_t launch_prep(const Plan& pl, void* ws, bool validate, cudaStream_t st);

@@ -22,8 +22,7 @@
 
 namespace fcfs {
 
-fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl);
-bool make_vertex_maps(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, VertexMaps& mp);
+fcfs_status make_plan_ex(int64_t V, int32_t T, int32_t K, int32_t prec, bool single, Plan& pl);
 
 // The scratch array.  In host code its name is only a stand-in for the symbol,
 // not a device address: the device address comes from cudaGetSymbolAddress.
@@ -76,13 +75,15 @@ extern "C" fcfs_status fcfs_forward_noalloc(const int32_t* x, const int32_t* y, 
   const auto aligned16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   if (V > 0 && (!x || !y || !s || !aligned16(x) || !aligned16(y) || !aligned16(s))) return FCFS_EINVAL;
   Plan pl;
-  fcfs_status r = make_plan(V, T, K, prec, pl);
+  fcfs_status r = make_plan_ex(V, T, K, prec, true, pl);
   if (r != FCFS_OK) return r;
   if ((r = fit_plan(pl, FCFS_NOALLOC_SCRATCH_BYTES)) != FCFS_OK) return r;
   void* ws = nullptr;
   if ((r = scratch_on_current_device(&ws)) != FCFS_OK) return r;
   VertexMaps mp{};
-  if (prec == FCFS_PREC_SPLIT_F16 && V > 0 && !make_vertex_maps(x, y, s, V, mp)) return FCFS_ECUDA;
+  pl.vx = x;
+  pl.vy = y;
+  pl.vsg = s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (launch_prep(pl, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
   if (launch_axis(pl, x, y, s, ws, false, st) != cudaSuccess) return FCFS_ECUDA;

@@ -32,31 +32,31 @@ namespace fcfs {
 constexpr int kBM = 128;         // tile rows (64 k values x {cos, sin})
 constexpr int kCh = 64;          // vertices per chunk = one 128-byte swizzle row of FP16
 constexpr int kRun = 8;          // consecutive frequencies generated by one thread
-constexpr int kVStages = 2;
-constexpr int kBox = 80;         // TMA box: chunk plus up to 15 elements of alignment slack
-constexpr int kVStageBytes = 896;  // x @0 (320 B), y @384 (320 B), s @768 (80 B)
-constexpr uint32_t kVertexTx = kBox * 4 * 2 + kBox;
 
-template <int BN, int STAGES>
+// BN: output tile columns.  PAIR: the tile is computed by a CTA pair (2-SM
+// MMA, M = 256): each CTA holds 128 A rows and BN/2 B rows per stage.
+template <int BN, int STAGES, bool PAIR = false>
 struct TcLayout {
-  static constexpr int kATile = kBM * 128;         // bytes of one FP16 A tile (hi or lo)
-  static constexpr int kBTile = BN * 128;
+  static constexpr int kBRows = PAIR ? BN / 2 : BN;   // B rows in this CTA's shared memory
+  static constexpr int kATile = kBM * 128;             // bytes of one FP16 A tile (hi or lo)
+  static constexpr int kBTile = kBRows * 128;
   static constexpr int kStage = 2 * kATile + 2 * kBTile;
   static constexpr int kOps = STAGES * kStage;
-  // one generator thread per (vertex octet, run of kRun row pairs); two groups
-  // of such threads take alternate chunks
-  static constexpr int kGroups = 2;
+  // one generator thread per (vertex octet, run of kRun row pairs); groups of
+  // such threads take chunks in turn.  A pair's half tiles are smaller: one
+  // group of four warps per stage (a group owns its stage, so a stage barrier
+  // is never waited on two phases ahead)
+  static constexpr int kGroups = PAIR ? STAGES : 2;
   static constexpr int kRunsA = kBM / 2 / kRun;
-  static constexpr int kGroupThreads = (kBM / 2 + BN / 2) / kRun * 8;
+  static constexpr int kGroupThreads = (kBM / 2 + kBRows / 2) / kRun * 8;
   static constexpr int kGenThreads = kGroups * kGroupThreads;
   static constexpr int kGenWarps = kGenThreads / 32;
   static constexpr int kThreads = kGenThreads + 64;
 };
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool PAIR = false>
 size_t tc_smem_bytes(int T, int full) {
-  return 1024 + TcLayout<BN, STAGES>::kOps + align_up(tab_f32_bytes(T, full), 128) + kVStages * kVStageBytes +
-         256;
+  return 1024 + TcLayout<BN, STAGES, PAIR>::kOps + align_up(tab_f32_bytes(T, full), 128) + 256;
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
@@ -83,12 +83,10 @@ __device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_
   lo = h2_bits(__floats2half2_rn(v0 - hf.x, v1 - hf.y));
 }
 
-template <int BN, int STAGES, bool FULL>
-__global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
-                   const __grid_constant__ CUtensorMap tms, const __grid_constant__ CUtensorMap tmp, Plan pl,
-                   uint8_t* ws) {
-  using L = TcLayout<BN, STAGES>;
+template <int BN, int STAGES, bool FULL, bool PAIR>
+__global__ void __launch_bounds__(TcLayout<BN, STAGES, PAIR>::kThreads, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmp, Plan pl, uint8_t* ws) {
+  using L = TcLayout<BN, STAGES, PAIR>;
   constexpr int GT = L::kGenThreads;
   constexpr int GW = L::kGenWarps;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -97,13 +95,10 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
   const size_t tb = tab_f32_bytes(pl.T, FULL);
   uint8_t* ops = sm;
   float* tab = reinterpret_cast<float*>(sm + L::kOps);
-  uint8_t* vst = sm + L::kOps + align_up(tb, 128);   // TMA destinations: 128-byte aligned
-  uint64_t* bars = reinterpret_cast<uint64_t*>(vst + kVStages * kVStageBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kOps + align_up(tb, 128));
   uint64_t* ofull = bars;
   uint64_t* oempty = ofull + STAGES;
-  uint64_t* vfull = oempty + STAGES;
-  uint64_t* vempty = vfull + kVStages;
-  uint64_t* accfull = vempty + kVStages;
+  uint64_t* accfull = oempty + STAGES;
   uint64_t* tabbar = accfull + 1;
   uint64_t* tailbar = tabbar + 1;   // fused tail: bins and fixed table, then staged partials
   uint64_t* recvbar = tailbar + 2;  // cluster pair: the peer's half tile has landed
@@ -117,20 +112,27 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
   // the unit list is read right away; a single clip's prologue below touches
   // no memory those kernels write, so it overlaps them
   if (pl.batch) griddep_wait();
-  const Unit U = unit_of_block(pl, ws, kBM, BN);
+  Unit U = unit_of_block(pl, ws, kBM, BN);
   if (!U.live) return;   // unit slots beyond the batch's count: nothing allocated yet
+  // pair rank (0 issues the MMAs) and, for a pair, the 128-row half it holds:
+  // blockIdx.x = 2 (pair tile) + rank, pair tile = (row pair tm/2, column tile tn)
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  if (PAIR) {
+    const int ptile = blockIdx.x >> 1;
+    U.tm = 2 * (ptile / pl.tiles_n) + (int)rank;
+    U.tn = ptile % pl.tiles_n;
+    U.P = reinterpret_cast<float*>(ws + pl.off_part) + (size_t)blockIdx.y * pl.M2 * pl.M2 +
+          (size_t)U.tm * kBM * pl.M2 + (size_t)U.tn * BN;
+  }
   const int tm = U.tm, tn = U.tn;
   const long long v0 = U.v0, v1 = U.v1;
   const int nch = (int)((v1 - v0 + kCh - 1) / kCh);
 
   if (tid == GT + 32) {
     for (int i = 0; i < STAGES; ++i) {
-      mbar_init(&ofull[i], L::kGroupThreads);   // one group fills a chunk
+      // one group fills a chunk; a pair's rank-0 barrier counts both CTAs' groups
+      mbar_init(&ofull[i], PAIR ? 2 * L::kGroupThreads : L::kGroupThreads);
       mbar_init(&oempty[i], 1);
-    }
-    for (int i = 0; i < kVStages; ++i) {
-      mbar_init(&vfull[i], 1);
-      mbar_init(&vempty[i], L::kGroupThreads);
     }
     mbar_init(accfull, 1);
     mbar_init(tabbar, 1);
@@ -139,57 +141,53 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     mbar_init(recvbar, 1);
     fence_mbar_init();
   }
-  if (warp == GW + 1 && lane == 0) {
-    prefetch_tensormap(&tmx);
-    prefetch_tensormap(&tmy);
-    prefetch_tensormap(&tms);
-    if (pl.fused) prefetch_tensormap(&tmp);
-  }
+  if (warp == GW + 1 && lane == 0 && pl.fused) prefetch_tensormap(&tmp);
   if (warp == GW) {
-    tmem_alloc(tmem_slot, 2 * BN);   // D1 (hi*hi) and D2 (hi*lo + lo*hi)
-    tmem_relinquish();
+    if (PAIR) {   // collective with the peer's MMA warp
+      tmem_alloc_pair(tmem_slot, 2 * BN);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(tmem_slot, 2 * BN);   // D1 (hi*hi) and D2 (hi*lo + lo*hi)
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
+  // a pair's barriers are signalled from both CTAs: both must be initialised
+  if (PAIR) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   // tables, bins and counters are written by the prep kernel
   if (!pl.batch) griddep_wait();
 
   if (warp == GW + 1) {
-    // ---------------- TMA producer ----------------
+    // ---------------- table copy and corner binning ----------------
     if (lane == 0) {
       mbar_arrive_expect_tx(tabbar, (uint32_t)tb);
       bulk_load(tab, ws + pl.off_tab_f32, (uint32_t)tb, tabbar);
       // the fused tail reads the fixed-point table after the main loop: have it in L2 by then
       if (pl.fused) bulk_prefetch_l2(ws + pl.off_tab_fix, (uint32_t)tab_fix_bytes(pl.T, 0));
-      int j = 0;
-      for (; j < nch; ++j) {
-        const int vs = j % kVStages;
-        const uint32_t vph = (uint32_t)(j / kVStages) & 1u;
-        if (!mbar_wait(&vempty[vs], vph ^ 1u, st, 1)) break;
-        const long long cs = v0 + (long long)j * kCh;
-        const int a0 = (int)(cs & ~15LL);
-        uint8_t* d = vst + vs * kVStageBytes;
-        mbar_arrive_expect_tx(&vfull[vs], kVertexTx);
-        tma_load_1d(d, &tmx, a0, &vfull[vs]);
-        tma_load_1d(d + 384, &tmy, a0, &vfull[vs]);
-        tma_load_1d(d + 768, &tms, a0, &vfull[vs]);
-      }
-      // drain: every issued copy has landed before the CTA may exit
-      for (int q = max(0, j - kVStages); q < j; ++q)
-        mbar_wait(&vfull[q % kVStages], (uint32_t)(q / kVStages) & 1u, st, 2);
-      mbar_wait(tabbar, 0, st, 3);
     }
+    if (pl.bin_in_gemm) {
+      // every corner is binned once, spread over the tiles: the CTA of tile t
+      // bins the chunks j = t mod (tiles) of its vertex range (Steps 2-3)
+      const int ntiles = pl.tiles_m * pl.tiles_n, tile = tm * pl.tiles_n + tn;
+      for (int j = tile; j < nch; j += ntiles)
+        for (int t = lane; t < kCh; t += 32) {
+          const long long v = v0 + (long long)j * kCh + t;
+          if (v < v1) bin_corner(pl, ws, U.clip, __ldg(pl.vx + v), __ldg(pl.vy + v), (int)__ldg(pl.vsg + v));
+        }
+    }
+    if (lane == 0) mbar_wait(tabbar, 0, st, 3);   // the copy has landed before the CTA may exit
   } else if (warp == GW) {
     // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_f16_f32(kBM, BN);
+    if (lane == 0 && rank == 0) {
+      constexpr uint32_t idesc = idesc_f16_f32(PAIR ? 2 * kBM : kBM, BN);
       const uint32_t ops_a = smem_u32(ops);
       for (int j = 0; j < nch; ++j) {
         const int stg = j % STAGES;
         const uint32_t ph = (uint32_t)(j / STAGES) & 1u;
-        if (!mbar_wait(&ofull[stg], ph, st, 4)) break;
+        if (!(PAIR ? mbar_wait_cluster(&ofull[stg], ph, st, 4) : mbar_wait(&ofull[stg], ph, st, 4))) break;
         tc_fence_after();
         const uint32_t ahi = ops_a + stg * L::kStage;
         const uint32_t alo = ahi + L::kATile;
@@ -203,13 +201,19 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
           // the large hi*hi products and the small correction products go to
           // separate accumulators: each rounded add into D1 carries one 16-vertex
           // dot product instead of three, and D2 stays 2^-11 smaller
-          tc_mma_f16(tmem, dah, dbh, idesc, (j | ks) != 0);
-          tc_mma_f16(tmem + BN, dah, dbl, idesc, (j | ks) != 0);
-          tc_mma_f16(tmem + BN, dal, dbh, idesc, 1);
+          if (PAIR) {
+            tc_mma_f16_pair(tmem, dah, dbh, idesc, (j | ks) != 0);
+            tc_mma_f16_pair(tmem + BN, dah, dbl, idesc, (j | ks) != 0);
+            tc_mma_f16_pair(tmem + BN, dal, dbh, idesc, 1);
+          } else {
+            tc_mma_f16(tmem, dah, dbh, idesc, (j | ks) != 0);
+            tc_mma_f16(tmem + BN, dah, dbl, idesc, (j | ks) != 0);
+            tc_mma_f16(tmem + BN, dal, dbh, idesc, 1);
+          }
         }
-        tc_commit(&oempty[stg]);
+        if (PAIR) tc_commit_pair(&oempty[stg]); else tc_commit(&oempty[stg]);
       }
-      tc_commit(accfull);
+      if (PAIR) tc_commit_pair(accfull); else tc_commit(accfull);
     }
   } else {
     // ---------------- generators ----------------
@@ -222,16 +226,47 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     const int run = gtid >> 3;
     const bool isA = run < L::kRunsA;
     const int i0 = kRun * (isA ? run : run - L::kRunsA);       // first row pair in the tile
-    const uint32_t f0 = isA ? (uint32_t)(tm * (kBM / 2) + 1 + i0) : (uint32_t)(tn * (BN / 2) + 1 + i0);
+    // first frequency of the run: A rows of tile row tm; B rows of column tile
+    // tn (a pair's rank r holds B rows [BN/2 r, BN/2 r + BN/2))
+    const uint32_t f0 = isA ? (uint32_t)(tm * (kBM / 2) + 1 + i0)
+                            : (uint32_t)(tn * (BN / 2) + (int)rank * (L::kBRows / 2) + 1 + i0);
     const uint32_t mask = (uint32_t)pl.T - 1u;
     const uint32_t half = (uint32_t)pl.T >> 1;
     const uint32_t logQ = (uint32_t)pl.logT - 2u;
     const uint32_t ops_a = smem_u32(ops);
-    const int coord_off = isA ? 0 : 384;
-    // every corner is binned once, spread over the tiles: the CTA of tile t
-    // bins the chunks j = t mod (tiles) of its vertex range
-    const int ntiles = pl.tiles_m * pl.tiles_n, tile = tm * pl.tiles_n + tn;
-    const bool bin_run = pl.bin_in_gemm && run == 0;
+    // this thread's 8 vertices of a chunk: coordinates (x for A rows, y for B
+    // rows) and, for A, the corner signs, read through the read-only cache one
+    // group turn ahead of use; zero past the end of the vertex range
+    const int32_t* cptr = isA ? pl.vx : pl.vy;
+    auto fetch = [&](int jj, uint32_t (&c)[8], uint32_t& s0, uint32_t& s1) {
+      const long long first = v0 + (long long)jj * kCh + oct * 8;
+      if (first + 8 <= v1 && (first & 3) == 0) {
+        const int4 q0 = __ldg(reinterpret_cast<const int4*>(cptr + first));
+        const int4 q1 = __ldg(reinterpret_cast<const int4*>(cptr + first) + 1);
+        c[0] = (uint32_t)q0.x; c[1] = (uint32_t)q0.y; c[2] = (uint32_t)q0.z; c[3] = (uint32_t)q0.w;
+        c[4] = (uint32_t)q1.x; c[5] = (uint32_t)q1.y; c[6] = (uint32_t)q1.z; c[7] = (uint32_t)q1.w;
+      } else {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) c[t] = first + t < v1 ? (uint32_t)__ldg(cptr + first + t) : 0u;
+      }
+      s0 = s1 = 0u;
+      if (isA) {
+        if (first + 8 <= v1 && (first & 7) == 0) {
+          const uint2 w = __ldg(reinterpret_cast<const uint2*>(pl.vsg + first));
+          s0 = w.x;
+          s1 = w.y;
+        } else {
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            if (first + t < v1) {
+              const uint32_t byte = (uint32_t)(uint8_t)__ldg(pl.vsg + first + t) << (8 * (t & 3));
+              if (t < 4) s0 |= byte; else s1 |= byte;
+            }
+        }
+      }
+    };
+    uint32_t cc[8], cs0 = 0u, cs1 = 0u, nc8[8], ns0 = 0u, ns1 = 0u;
+    if (group < nch) fetch(group, cc, cs0, cs1);
     // swizzled byte offset of this thread's 16-byte chunk in row r: (oct ^ (r & 7)) << 4;
     // rows 2(i0 + r) have r & 7 = 2r & 7 because i0 is a multiple of 8
     uint32_t xo[8];
@@ -239,23 +274,16 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
     for (int c = 0; c < 8; ++c) xo[c] = (uint32_t)((oct ^ c) << 4);
     bool ok = mbar_wait(tabbar, 0, st, 5);
     for (int j = group; ok && j < nch; j += L::kGroups) {
-      const int vs = j % kVStages;
-      const uint32_t vph = (uint32_t)(j / kVStages) & 1u;
       const int stg = j % STAGES;
       const uint32_t ph = (uint32_t)(j / STAGES) & 1u;
-      if (!mbar_wait(&vfull[vs], vph, st, 6)) break;
+      if (j + L::kGroups < nch) fetch(j + L::kGroups, nc8, ns0, ns1);
       const long long cs = v0 + (long long)j * kCh;
-      const int off = (int)(cs & 15LL);
-      const uint8_t* d = vst + vs * kVStageBytes;
-      const int32_t* co = reinterpret_cast<const int32_t*>(d + coord_off);
-      const int8_t* ss = reinterpret_cast<const int8_t*>(d + 768);
       uint32_t a[8], add[8], vmask[4];
       const long long first = cs + oct * 8;
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
-        const int idx = off + oct * 8 + t;
-        a[t] = (uint32_t)co[idx];
-        add[t] = (isA && ss[idx] < 0) ? half : 0u;
+        a[t] = cc[t];
+        add[t] = (((t < 4 ? cs0 : cs1) >> (8 * (t & 3))) & 0x80u) ? half : 0u;   // s = -1: phase + T/2
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -263,22 +291,6 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
         vmask[q] = (lo_ok ? 0xFFFFu : 0u) | (hi_ok ? 0xFFFF0000u : 0u);
       }
       const bool masked = isA && (first + 8 > v1);
-      if (bin_run && j % ntiles == tile) {   // each corner of the chunk once: the 8 threads of A run 0
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int idx = off + oct * 8 + t;
-          if (first + t < v1) {
-            const int32_t* xs = reinterpret_cast<const int32_t*>(d);
-            const int32_t* ys = reinterpret_cast<const int32_t*>(d + 384);
-            bin_corner(pl, ws, U.clip, xs[idx], ys[idx], ss[idx]);
-          }
-        }
-      }
-      // The next TMA write into this stage is an async-proxy write; the
-      // mbarrier release alone does not order it after these generic-proxy
-      // loads, which may still be in flight.  The proxy fence does.
-      fence_proxy_async_smem();
-      mbar_arrive(&vempty[vs]);
       // anchors and steps from the table, before waiting for the stage
       float c[8], sn[8], wc[8], wsn[8];
 #pragma unroll
@@ -328,7 +340,11 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
         st_shared_v4(rs + lo_delta, sl[0], sl[1], sl[2], sl[3]);
       }
       fence_proxy_async_smem();
-      mbar_arrive(&ofull[stg]);
+      if (PAIR) mbar_arrive_cluster(&ofull[stg], 0); else mbar_arrive(&ofull[stg]);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) cc[t] = nc8[t];
+      cs0 = ns0;
+      cs1 = ns1;
     }
     // ---------------- epilogue: TMEM -> FP32 partials (warps 0-3) ----------------
     if (warp < 4) {
@@ -425,10 +441,16 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
 
   tc_fence_before();
   __syncthreads();
+  // a pair's MMAs, commits and arrivals reach both CTAs: neither releases its
+  // TMEM or leaves before both are done
+  if (PAIR) {
+    __syncwarp();
+    cluster_sync_all();
+  }
   if (warp == GW) {
     __syncwarp();   // lane 0 ran the MMA loop alone; dealloc is warp-collective
     tc_fence_after();
-    tmem_dealloc(tmem, 2 * BN);
+    if (PAIR) tmem_dealloc_pair(tmem, 2 * BN); else tmem_dealloc(tmem, 2 * BN);
   }
   // single clip, cooperative launch: split-K sum, axis lines and output here.
   // Every copy into shared memory has landed and every MMA has completed, so
@@ -440,20 +462,20 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES>::kThreads, 1)
 // Host side
 // ---------------------------------------------------------------------------
 // CTAs of one kernel variant that fit on the device at once, in clusters of
-// C (1 or 2) along the split dimension (cached per device).
-template <int BN, int STAGES, bool FULL>
+// C (1 or 2) along the split dimension, or in CTA pairs (cached per device).
+template <int BN, int STAGES, bool FULL, bool PAIR>
 static int tc_resident_ctas(size_t smem, int C) {
   constexpr int kMaxDev = 64;
   static int cache[kMaxDev][3] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev || C < 1 || C > 2) return 0;
   if (cache[dev][C]) return cache[dev][C];
-  auto kern = gemm_tc_kernel<BN, STAGES, FULL>;
+  auto kern = gemm_tc_kernel<BN, STAGES, FULL, PAIR>;
   if (ensure_smem(reinterpret_cast<const void*>(kern), smem) != cudaSuccess) return 0;
   int n = 0;
-  if (C == 1) {
+  if (C == 1 && !PAIR) {
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TcLayout<BN, STAGES>::kThreads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TcLayout<BN, STAGES, PAIR>::kThreads, smem) !=
             cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
       cudaGetLastError();
@@ -461,14 +483,15 @@ static int tc_resident_ctas(size_t smem, int C) {
     }
     n = per_sm * sms;
   } else {
+    const int cx = PAIR ? 2 : 1, cy = PAIR ? 1 : C;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(1, C);
-    cfg.blockDim = dim3(TcLayout<BN, STAGES>::kThreads);
+    cfg.gridDim = dim3(cx, cy);
+    cfg.blockDim = dim3(TcLayout<BN, STAGES, PAIR>::kThreads);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 1;
-    at[0].val.clusterDim.y = C;
+    at[0].val.clusterDim.x = cx;
+    at[0].val.clusterDim.y = cy;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
@@ -477,38 +500,40 @@ static int tc_resident_ctas(size_t smem, int C) {
       cudaGetLastError();
       return 0;
     }
-    n = clusters * C;
+    n = clusters * cx * cy;
   }
   cache[dev][C] = n;
   return n;
 }
 
-// Cluster size of a fused launch of this variant (2: split pairs, 1: none), 0
-// if the call cannot be fused.
-template <int BN, int STAGES, bool FULL>
+// Cluster size of a fused launch of this variant along the splits (2: split
+// pairs, 1: none), 0 if the call cannot be fused.  CTA-pair launches use no
+// split pairs.
+template <int BN, int STAGES, bool FULL, bool PAIR>
 static int fuse_cluster(const Plan& pl) {
+  using L = TcLayout<BN, STAGES, PAIR>;
   if (pl.batch) return 0;
   const long long ctas = (long long)pl.tiles_m * pl.tiles_n * pl.splits;
   if (ctas < 1) return 0;
   // partial rows are bulk-copied in 16-byte units: rows of 2K floats need K even
   if (pl.K % 2 != 0) return 0;
   // the tail may use the operand stages and the FP32 table region (contiguous)
-  const size_t avail = (size_t)TcLayout<BN, STAGES>::kOps + align_up(tab_f32_bytes(pl.T, FULL), 128);
-  const size_t smem = tc_smem_bytes<BN, STAGES>(pl.T, FULL);
+  const size_t avail = (size_t)L::kOps + align_up(tab_f32_bytes(pl.T, FULL), 128);
+  const size_t smem = tc_smem_bytes<BN, STAGES, PAIR>(pl.T, FULL);
   for (int C : {2, 1}) {
-    if (pl.splits % C != 0) continue;
-    // a pair keeps its tile and the peer's half in the operand stages
-    if (C == 2 && (size_t)kBM * BN * 4 * 3 / 2 > (size_t)TcLayout<BN, STAGES>::kOps) continue;
-    if (tail_smem(pl.T, pl.K, pl.splits / C, ctas, TcLayout<BN, STAGES>::kThreads).total > avail) continue;
-    if (ctas <= tc_resident_ctas<BN, STAGES, FULL>(smem, C)) return C;
+    if (pl.splits % C != 0 || (PAIR && C > 1)) continue;
+    // a split pair keeps its tile and the peer's half in the operand stages
+    if (C == 2 && (size_t)kBM * BN * 4 * 3 / 2 > (size_t)L::kOps) continue;
+    if (tail_smem(pl.T, pl.K, pl.splits / C, ctas, L::kThreads).total > avail) continue;
+    if (ctas <= tc_resident_ctas<BN, STAGES, FULL, PAIR>(smem, C)) return C;
   }
   return 0;
 }
 
-template <int BN, int STAGES, bool FULL>
+template <int BN, int STAGES, bool FULL, bool PAIR>
 static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cudaStream_t st) {
-  const size_t smem = tc_smem_bytes<BN, STAGES>(pl.T, FULL);
-  auto kern = gemm_tc_kernel<BN, STAGES, FULL>;
+  const size_t smem = tc_smem_bytes<BN, STAGES, PAIR>(pl.T, FULL);
+  auto kern = gemm_tc_kernel<BN, STAGES, FULL, PAIR>;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
   dim3 grid = pl.batch ? dim3(pl.splits, 1) : dim3(pl.tiles_m * pl.tiles_n, pl.splits);
@@ -516,24 +541,25 @@ static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cud
   // (programmatic stream serialisation; it waits for it in griddep_wait()).
   // The fused tail waits at a grid barrier, so every CTA must be resident:
   // a cooperative launch guarantees that (or refuses to launch).  Where the
-  // runtime refuses the two attributes together, the launch drops the first.
+  // runtime refuses programmatic serialisation with the other attributes,
+  // the launch drops it.
   static bool pdl_ok = true;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
-  cfg.blockDim = dim3(TcLayout<BN, STAGES>::kThreads);
+  cfg.blockDim = dim3(TcLayout<BN, STAGES, PAIR>::kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[3];
   int na = 0;
+  if (PAIR || (pl.fused && pl.cluster > 1)) {
+    at[na].id = cudaLaunchAttributeClusterDimension;
+    at[na].val.clusterDim.x = PAIR ? 2 : 1;
+    at[na].val.clusterDim.y = PAIR ? 1 : pl.cluster;
+    at[na++].val.clusterDim.z = 1;
+  }
   if (pl.fused) {
     at[na].id = cudaLaunchAttributeCooperative;
     at[na++].val.cooperative = 1;
-    if (pl.cluster > 1) {
-      at[na].id = cudaLaunchAttributeClusterDimension;
-      at[na].val.clusterDim.x = 1;
-      at[na].val.clusterDim.y = pl.cluster;
-      at[na++].val.clusterDim.z = 1;
-    }
   }
   if (pdl_ok) {
     at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -541,12 +567,12 @@ static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cud
   }
   cfg.attrs = at;
   cfg.numAttrs = na;
-  e = cudaLaunchKernelEx(&cfg, kern, mp.x, mp.y, mp.s, mp.part, pl, static_cast<uint8_t*>(ws));
+  e = cudaLaunchKernelEx(&cfg, kern, mp.part, pl, static_cast<uint8_t*>(ws));
   if (e != cudaSuccess && pdl_ok) {
     cudaGetLastError();
     pdl_ok = false;
     cfg.numAttrs = na - 1;
-    e = cudaLaunchKernelEx(&cfg, kern, mp.x, mp.y, mp.s, mp.part, pl, static_cast<uint8_t*>(ws));
+    e = cudaLaunchKernelEx(&cfg, kern, mp.part, pl, static_cast<uint8_t*>(ws));
   }
   count_launch(1);
   return e != cudaSuccess ? e : cudaGetLastError();
@@ -554,19 +580,21 @@ static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cud
 
 int gemm_tc_fuse_cluster(const Plan& pl) {
   if (pl.splits == 0) return 0;
-  if (pl.bn == 256) return pl.full ? fuse_cluster<256, 2, true>(pl) : 0;
-  if (pl.full) return fuse_cluster<128, 3, true>(pl);
-  return fuse_cluster<128, 2, false>(pl);
+  if (pl.pair) return pl.full ? fuse_cluster<256, 3, true, true>(pl) : fuse_cluster<256, 2, false, true>(pl);
+  if (pl.bn == 256) return pl.full ? fuse_cluster<256, 2, true, false>(pl) : 0;
+  if (pl.full) return fuse_cluster<128, 3, true, false>(pl);
+  return fuse_cluster<128, 2, false, false>(pl);
 }
 
 cudaError_t launch_gemm_tc(const Plan& pl, const VertexMaps& mp, void* ws, cudaStream_t st) {
   if (pl.splits == 0) return cudaSuccess;
+  if (pl.pair) return pl.full ? launch_tc<256, 3, true, true>(pl, mp, ws, st) : launch_tc<256, 2, false, true>(pl, mp, ws, st);
   if (pl.bn == 256) {
-    if (pl.full) return launch_tc<256, 2, true>(pl, mp, ws, st);
+    if (pl.full) return launch_tc<256, 2, true, false>(pl, mp, ws, st);
     return cudaErrorInvalidValue;   // quarter table does not fit beside 2 stages of 256
   }
-  if (pl.full) return launch_tc<128, 3, true>(pl, mp, ws, st);
-  return launch_tc<128, 2, false>(pl, mp, ws, st);
+  if (pl.full) return launch_tc<128, 3, true, false>(pl, mp, ws, st);
+  return launch_tc<128, 2, false, false>(pl, mp, ws, st);
 }
 
 size_t tc_smem_for(int bn, int T, int full) {

@@ -139,6 +139,12 @@ def set_fuse(on):
     _lib.load().fcfs_debug_set_fuse(1 if on else 0)
 
 
+def set_pair(on):
+    """1 (default): single clips with 2K >= 256 run on CTA pairs (2-SM MMA);
+    0: one-CTA tiles.  Allocate workspaces after changing it."""
+    _lib.load().fcfs_debug_set_pair(1 if on else 0)
+
+
 def set_batch_unit_chunks(n):
     """Vertex-split granularity of batch(): n pipeline chunks per unit (0: default)."""
     _lib.load().fcfs_set_batch_unit_chunks(int(n))

@@ -242,3 +242,36 @@ def test_fused_tail_matches_separate_kernels(fc, cfg, splits):
         np.testing.assert_array_equal(F1n[:, K], F0n[:, K])
     Fo = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
     assert np.max(np.abs(F1n - Fo)) / A <= TOL["split_f16"]
+
+
+@pytest.mark.parametrize("fuse", [1, 0])
+@pytest.mark.parametrize("splits", [0, 1, 5])
+def test_cta_pair_tiles_match_single_cta_tiles(fc, fuse, splits):
+    """Clips with 2K >= 256 run on CTA pairs (2-SM MMA, 256 x 256 tiles); the
+    operands and the accumulation order per output are those of one-CTA tiles,
+    so both agree to FP32 rounding and with the oracle; repeated calls on fresh
+    workspaces give identical blocks."""
+    clip, K = config_clip(2)
+    x, y, s = to_dev(clip)
+    A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+    Fo = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    out = {}
+    fc.set_fuse(fuse)
+    fc.set_splits(splits)
+    try:
+        for pair in (1, 0, 1):
+            fc.set_pair(pair)
+            ws = fc.alloc_workspace(fc.workspace_size(clip.V, clip.T, K, "split_f16"), x.device)
+            F, a = fc.forward(x, y, s, clip.T, K, prec="split_f16", workspace=ws)
+            assert fc.get_status(ws) == "FCFS_OK"
+            assert int(a) == A
+            Fn = F.cpu().numpy()
+            assert np.max(np.abs(Fn - Fo)) / A <= TOL["split_f16"]
+            if pair in out:
+                assert np.array_equal(out[pair], Fn)
+            out[pair] = Fn
+    finally:
+        fc.set_pair(1)
+        fc.set_splits(0)
+        fc.set_fuse(1)
+    assert np.max(np.abs(out[1] - out[0])) / A <= 1e-7
