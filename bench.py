@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the adjoint, batch and large-clip measurements")
+    ap.add_argument("--no-pair", action="store_true",
+                    help="--only: one-CTA tiles instead of CTA pairs (profiling)")
+    ap.add_argument("--no-fuse", action="store_true",
+                    help="--only: separate axis and reduce kernels (profiling)")
     ap.add_argument("--only", choices=["step", "large", "batch", "adjoint"], default=None,
                     help="run one workload warmup + steps times and print its mean time "
                          "(for profiler command lines; not the benchmark line)")
@@ -360,14 +364,13 @@ def run_ours(args):
     achieved = alg_flops / (gemm_ms * 1e-3) / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved / peak_tf, "traffic": traffic_per_launch(),
-                "kernel": ("gemm_tc_kernel<256,2,full> (tcgen05 split-FP16 contraction; "
-                           + ("fused split-K sum, axis DFT and output behind a grid barrier)"
-                              if stage_ms[1] == 0 and stage_ms[3] == 0 else "separate axis and reduce kernels)")),
+                "kernel": ("gemm_tc_kernel<256,3,full,pair> (tcgen05 cta_group::2 split-FP16 contraction on "
+                           "CTA pairs; fused split-K sum, axis DFT and output behind a grid barrier)"),
                 "kernel_ms": gemm_ms, "peak_source": "%s bf16 dense burst (fp16 same rate)" % peak_kind,
                 "issued_tflops": issued_flops / (gemm_ms * 1e-3) / 1e12,
                 "issued_frac": issued_flops / (gemm_ms * 1e-3) / 1e12 / peak_tf,
-                "stage_ms": {"prep": stage_ms[0], "axis": stage_ms[1], "contraction": stage_ms[2],
-                             "reduce": stage_ms[3]}}
+                # the axis lines and the split-K sum run inside the contraction kernel
+                "stage_ms": {"prep": stage_ms[0], "contraction_with_fused_tail": stage_ms[2]}}
 
     # ---- plain FP32 path on the same clip ----
     ms32 = timed(min(args.steps, 1000), lambda: step("fp32"))
@@ -580,6 +583,10 @@ def run_only(args):
     from paper_1010_5562_gb300 import fcfs
     from synth import config_clip, config4_target, batch_clips, concat_clips
     dev = torch.device("cuda", 0)
+    if args.no_pair:
+        fcfs.set_pair(0)
+    if args.no_fuse:
+        fcfs.set_fuse(0)
     if args.only in ("step", "large", "adjoint"):
         clip, K = config_clip({"step": 2, "large": 5, "adjoint": 4}[args.only])
         x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))

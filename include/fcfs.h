@@ -177,6 +177,14 @@ fcfs_status fcfs_forward_noalloc(const int32_t* x, const int32_t* y, const int8_
                                  float* F_out, int64_t* area_out, void* stream);
 
 /*
+ * Environment: FCFS_PDL=0 launches the contraction kernel without programmatic
+ * dependent launch (no overlap of its set-up with the prep kernel; the work is
+ * the same).  FCFS_COOPERATIVE=0 launches fused calls without the cooperative
+ * attribute: nothing then guarantees that every CTA is resident, and the grid
+ * barrier's bounded wait ends the call with FCFS_ETIMEOUT if one is not (on an
+ * otherwise idle GPU they all fit).  Both are for kernel profilers that cannot
+ * replay such launches; leave them unset otherwise.
+ *
  * Measurement and tuning hooks.  fcfs_profile_enable(1) makes every later call bracket
  * each of its stages with CUDA events on the caller's stream; after a call,
  * fcfs_profile_read() waits for the last event and writes up to n stage
@@ -200,6 +208,12 @@ void fcfs_debug_set_fuse(int32_t on);
  * (2-SM MMA on 256 x 256 tiles).  Must not change between fcfs_workspace_size
  * and the call that uses the workspace. */
 void fcfs_debug_set_pair(int32_t on);
+/* Failure-detection test hook: with n > 0 the grid barrier of later fused
+ * calls waits for n more CTAs than were launched.  Its wait is bounded (about
+ * a second of SM clock), so the call ends with the status FCFS_ETIMEOUT
+ * (fcfs_get_status) and an unwritten block, and the context stays usable.
+ * 0 (the default) restores normal calls. */
+void fcfs_debug_set_barrier_extra(int32_t n);
 
 /* Vertex-split granularity of fcfs_batch: n pipeline chunks (64 corners on the
  * tensor path, 32 on the FP32 path) per unit; 0 restores the default of 4096

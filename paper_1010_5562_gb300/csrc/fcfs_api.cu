@@ -72,6 +72,7 @@ static int choose_splits(long long tiles, long long nchunks, long long slots, lo
 static int g_split_override = 0;   // testing/autotuning hook, 0 = automatic
 static int g_fuse = 1;             // testing hook: 0 keeps the axis and reduce kernels separate
 static int g_pair = 1;             // testing hook: 0 keeps single clips on one-CTA tiles
+static int g_barrier_extra = 0;    // testing hook: see fcfs_debug_set_barrier_extra
 
 // Tag of the cached tables: their kind, period, fixed-point scale and offsets.
 static uint64_t table_tag(const Plan& pl) {
@@ -277,6 +278,7 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
   if (cluster > 0 && make_part_map(pl, ws, pl.splits / cluster, &mp.part)) {
     pl.fused = 1;
     pl.cluster = cluster;
+    pl.barrier_extra = g_barrier_extra;
     pl.F = reinterpret_cast<float2*>(F);
     pl.area_out = reinterpret_cast<long long*>(area);
   }
@@ -348,6 +350,7 @@ fcfs_status fcfs_get_status(const void* workspace, void* stream) {
 void fcfs_debug_set_splits(int32_t s) { g_split_override = s; }
 void fcfs_debug_set_fuse(int32_t on) { g_fuse = on ? 1 : 0; }
 void fcfs_debug_set_pair(int32_t on) { g_pair = on ? 1 : 0; }
+void fcfs_debug_set_barrier_extra(int32_t n) { g_barrier_extra = n > 0 ? n : 0; }
 
 void fcfs_profile_enable(int32_t on) { g_prof = on != 0; }
 

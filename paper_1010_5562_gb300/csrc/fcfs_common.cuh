@@ -40,6 +40,8 @@ struct Plan {
   int32_t bin_in_gemm;         // 1: the contraction kernel bins the corners for the axis lines
   int32_t fused;               // 1: the contraction kernel also runs the split-K sum, the
                                //    axis-line DFT and the output (cooperative launch)
+  int32_t barrier_extra;       // test hook: the fused grid barrier waits for this many CTAs
+                               //    more than exist (so its bounded wait runs out)
   int32_t cluster;             // fused: 2 when CTAs of consecutive split pairs form a cluster
                                //    and add their partial tiles in shared memory first, else 1
   const int32_t* vx;           // corner coordinates and signs (device; read by the

@@ -310,7 +310,7 @@ __device__ inline void fused_tail(const Plan& pl, uint8_t* ws, uint8_t* smem, in
   unsigned* sync = reinterpret_cast<unsigned*>(ws + kSyncOffset);
   const unsigned nblk = gridDim.x * gridDim.y;
   const unsigned b = blockIdx.y * gridDim.x + blockIdx.x;
-  if (!grid_barrier(&sync[0], nblk, st, 0x7000u, sflag)) return;
+  if (!grid_barrier(&sync[0], nblk + (unsigned)pl.barrier_extra, st, 0x7000u, sflag)) return;
   // partials left after the in-cluster sums: one per cluster of splits
   const int K = pl.K, T = pl.T, logQ = pl.logT - 2, S = pl.splits / pl.cluster;
   float2* F = pl.F;

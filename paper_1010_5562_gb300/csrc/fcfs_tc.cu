@@ -25,6 +25,8 @@
 //                    and bulk-copies the sincos table once.
 // Every mbarrier wait is bounded: on time-out the status word gets
 // FCFS_ETIMEOUT and the CTA drains and exits normally.
+#include <cstdlib>
+
 #include "fcfs_epilogue.cuh"
 
 namespace fcfs {
@@ -543,7 +545,13 @@ static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cud
   // a cooperative launch guarantees that (or refuses to launch).  Where the
   // runtime refuses programmatic serialisation with the other attributes,
   // the launch drops it.
-  static bool pdl_ok = true;
+  // FCFS_PDL=0 in the environment turns programmatic serialisation off (the
+  // kernels' work is the same; profilers that replay launches may need it)
+  static bool pdl_ok = !(getenv("FCFS_PDL") && atoi(getenv("FCFS_PDL")) == 0);
+  // FCFS_COOPERATIVE=0 launches fused calls without the co-residency guarantee
+  // (for profilers that cannot replay cooperative cluster launches; the grid
+  // barrier's bounded wait reports FCFS_ETIMEOUT if the CTAs are not all resident)
+  static const bool coop = !(getenv("FCFS_COOPERATIVE") && atoi(getenv("FCFS_COOPERATIVE")) == 0);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = dim3(TcLayout<BN, STAGES, PAIR>::kThreads);
@@ -557,7 +565,7 @@ static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cud
     at[na].val.clusterDim.y = PAIR ? 1 : pl.cluster;
     at[na++].val.clusterDim.z = 1;
   }
-  if (pl.fused) {
+  if (pl.fused && coop) {
     at[na].id = cudaLaunchAttributeCooperative;
     at[na++].val.cooperative = 1;
   }

@@ -145,6 +145,12 @@ def set_pair(on):
     _lib.load().fcfs_debug_set_pair(1 if on else 0)
 
 
+def set_barrier_extra(n):
+    """Failure-detection test hook: fused calls wait for n CTAs that do not exist
+    (bounded), ending with FCFS_ETIMEOUT; 0 restores normal calls."""
+    _lib.load().fcfs_debug_set_barrier_extra(int(n))
+
+
 def set_batch_unit_chunks(n):
     """Vertex-split granularity of batch(): n pipeline chunks per unit (0: default)."""
     _lib.load().fcfs_set_batch_unit_chunks(int(n))

@@ -275,3 +275,24 @@ def test_cta_pair_tiles_match_single_cta_tiles(fc, fuse, splits):
         fc.set_splits(0)
         fc.set_fuse(1)
     assert np.max(np.abs(out[1] - out[0])) / A <= 1e-7
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(fc):
+    """Failure detection without a GPU fault: the fused grid barrier is made to
+    wait for a CTA that does not exist; its bounded wait gives up, the status
+    word says FCFS_ETIMEOUT, and the next call on the same context is correct."""
+    clip, K = config_clip(2)
+    x, y, s = to_dev(clip)
+    A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+    ws = fc.alloc_workspace(fc.workspace_size(clip.V, clip.T, K, "split_f16"), x.device)
+    fc.set_barrier_extra(1)
+    try:
+        fc.forward(x, y, s, clip.T, K, prec="split_f16", workspace=ws)
+        assert fc.get_status(ws) == "FCFS_ETIMEOUT"
+    finally:
+        fc.set_barrier_extra(0)
+    F, a = fc.forward(x, y, s, clip.T, K, prec="split_f16", workspace=ws)
+    assert fc.get_status(ws) == "FCFS_OK"
+    assert int(a) == A
+    Fo = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    assert np.max(np.abs(F.cpu().numpy() - Fo)) / A <= TOL["split_f16"]
