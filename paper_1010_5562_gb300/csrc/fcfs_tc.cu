@@ -66,6 +66,10 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
                : "memory");
 }
 
+__device__ __forceinline__ void ld_shared_v4(uint32_t addr, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(a), "=r"(b), "=r"(c), "=r"(d) : "r"(addr) : "memory");
+}
+
 // Byte offset of 16-byte chunk `c` (8 vertices) of row `r` in a K-major SW128 tile.
 __device__ __forceinline__ uint32_t sw128(int r, int c) {
   return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
@@ -348,52 +352,70 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, PAIR>::kThreads, 1)
       cs0 = ns0;
       cs1 = ns1;
     }
-    // ---------------- epilogue: TMEM -> FP32 partials (warps 0-3) ----------------
-    if (warp < 4) {
-      const bool acc_ok = mbar_wait(accfull, 0, st, 8);
-      __syncwarp();   // tcgen05.ld is warp-collective: reconverge after the per-thread branches
+    // ---------------- epilogue: TMEM -> FP32 partials (generator warps 0-7) ----------------
+    // Warp w drains TMEM lane quadrant w mod 4 (tile rows 32 (w mod 4) ..) and
+    // every other 32-column block.  A 32 x 32 block goes through a padded
+    // shared-memory transpose (row stride 36 floats: the row-per-lane 16-byte
+    // writes and the 4-rows-per-instruction reads are both conflict-free), so
+    // each 16-byte global store instruction covers four whole 128-byte rows
+    // instead of 32 scattered 16-byte pieces.  The operand stages are free:
+    // the last MMA has completed.
+    constexpr int kEpiWarps = GW < 8 ? GW : 8;
+    if (warp < kEpiWarps) {
+      const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(accfull, 0, st, 8) ? 1 : 0) != 0;
       tc_fence_after();
       const int M2 = pl.M2;
-      const int row = warp * 32 + lane;
-      const int m = tm * kBM + row;
-      if (acc_ok && nch > 0) {
+      const int row0 = (warp & 3) * 32;
+      const bool split_pair = pl.fused && pl.cluster == 2;
+      const uint32_t tr = smem_u32(ops) + (uint32_t)warp * (32u * 36u * 4u);
 #pragma unroll 1
-        for (int cb = 0; cb < BN / 32; ++cb) {
-          const int n0 = tn * BN + cb * 32;
-          if (n0 >= M2) break;   // warp-uniform
-          uint32_t r[32], r2[32];
-          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), r);
-          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(BN + cb * 32), r2);
+      for (int cb = warp >> 2; cb < BN / 32; cb += kEpiWarps / 4) {
+        const int n0 = tn * BN + cb * 32;
+        if (n0 >= M2) break;   // warp-uniform
+        uint32_t r[32];
+        if (acc_ok && nch > 0) {
+          uint32_t r2[32];
+          tmem_ld32(tmem + ((uint32_t)row0 << 16) + (uint32_t)(cb * 32), r);
+          tmem_ld32(tmem + ((uint32_t)row0 << 16) + (uint32_t)(BN + cb * 32), r2);
           tmem_wait_ld();
 #pragma unroll
           for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(r2[q]));
-          if (pl.fused && pl.cluster == 2) {
-            // tile row `row` in shared memory, 16-byte chunks XOR-swizzled by row & 7
+        } else {
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-              st_shared_v4(smem_u32(ops) + (uint32_t)row * (BN * 4) + ((uint32_t)((cb * 8 + q) ^ (row & 7)) << 4),
-                           r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
-            continue;
-          }
-          if (m < M2) {
-            float* dst = U.P + (size_t)row * U.ld + cb * 32;
-            if (n0 + 32 <= M2 && (M2 & 3) == 0) {
+          for (int q = 0; q < 32; ++q) r[q] = 0u;
+        }
+        const int row = row0 + lane;
+        if (split_pair) {
+          // tile row `row` in shared memory, 16-byte chunks XOR-swizzled by row & 7
 #pragma unroll
-              for (int q = 0; q < 8; ++q)
-                reinterpret_cast<float4*>(dst)[q] =
-                    make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+          for (int q = 0; q < 8; ++q)
+            st_shared_v4(smem_u32(ops) + (uint32_t)row * (BN * 4) + ((uint32_t)((cb * 8 + q) ^ (row & 7)) << 4),
+                         r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+          continue;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          st_shared_v4(tr + (uint32_t)(lane * 36 + 4 * q) * 4u, r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+        __syncwarp();
+        const int c4 = lane & 7;   // 16-byte column chunk of the block
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int rr = 4 * i + (lane >> 3);   // block row
+          const int m = tm * kBM + row0 + rr, n = n0 + 4 * c4;
+          uint32_t v0, v1, v2, v3;
+          ld_shared_v4(tr + (uint32_t)(rr * 36 + 4 * c4) * 4u, v0, v1, v2, v3);
+          if (m < M2 && n < M2) {
+            float* dst = U.P + (size_t)(row0 + rr) * U.ld + cb * 32 + 4 * c4;
+            if (n + 4 <= M2 && (U.ld & 3) == 0) {
+              *reinterpret_cast<float4*>(dst) =
+                  make_float4(__uint_as_float(v0), __uint_as_float(v1), __uint_as_float(v2), __uint_as_float(v3));
             } else {
-              for (int q = 0; q < 32; ++q)
-                if (n0 + q < M2) dst[q] = __uint_as_float(r[q]);
+              const uint32_t vv[4] = {v0, v1, v2, v3};
+              for (int t = 0; t < 4 && n + t < M2; ++t) dst[t] = __uint_as_float(vv[t]);
             }
           }
         }
-      } else if (pl.fused && pl.cluster == 2) {
-        for (int c = 0; c < BN / 4; ++c)
-          st_shared_v4(smem_u32(ops) + (uint32_t)row * (BN * 4) + ((uint32_t)(c ^ (row & 7)) << 4), 0u, 0u, 0u, 0u);
-      } else if (m < M2) {
-        for (int n = tn * BN; n < min(M2, tn * BN + BN); ++n) U.P[(size_t)row * U.ld + (n - tn * BN)] = 0.f;
+        __syncwarp();
       }
     }
   }
