@@ -534,8 +534,22 @@ def run_extras(fcfs, dev, flush, stream, args):
         ms5 = _timed_ms(torch, lambda: fcfs.forward(x5, y5, s5, clip5.T, K5, prec=prec, out=F5, area_out=A5,
                                                     workspace=ws5, stream=stream), 3, flush, stream)
         big[prec] = {"value": clip5.V * W5 * W5 / (ms5 * 1e-3), "ms": ms5, "_F": F5, "_A": A5}
+    # adjoint of the large clip (FP32), seeded random cotangent over the full block
+    rng = np.random.default_rng(5)
+    G5 = torch.from_numpy((rng.standard_normal((W5, W5)) + 1j * rng.standard_normal((W5, W5)))
+                          .astype(np.complex64)).to(dev)
+    gx5 = torch.empty(clip5.V, dtype=torch.float32, device=dev)
+    gy5 = torch.empty_like(gx5)
+    wsa5 = torch.empty(fcfs._lib.load().fcfs_adjoint_workspace_size(clip5.V, clip5.T, K5, 0), dtype=torch.uint8,
+                       device=dev)
+    ms_a5 = _timed_ms(torch, lambda: fcfs.adjoint(x5, y5, s5, clip5.T, K5, G5, gx=gx5, gy=gy5, workspace=wsa5,
+                                                  stream=stream), 2, flush, stream)
+    big["adjoint_fp32"] = {"value": clip5.V * W5 * W5 / (ms_a5 * 1e-3), "ms": ms_a5,
+                           "cotangent": "seeded standard complex normal over the block",
+                           "_G": G5, "_g": (gx5, gy5)}
     out["large"] = {"workload": "clip T=65536, 150000 polygons, V=%d, K=1024 (2049x2049)" % clip5.V,
-                    "unit": UNIT, "split_f16": big["split_f16"], "fp32": big["fp32"], "_check": (clip5, K5)}
+                    "unit": UNIT, "split_f16": big["split_f16"], "fp32": big["fp32"],
+                    "adjoint_fp32": big["adjoint_fp32"], "_check": (clip5, K5)}
     return out
 
 
@@ -573,6 +587,13 @@ def extras_accuracy(line, extras):
             F5 = d.pop("_F").cpu().numpy()[np.ix_(pick + K5, pick + K5)]
             d["max_abs_err_over_area_sampled"] = float(np.max(np.abs(F5 - Fo)) / A)
             d["area_exact"] = int(d.pop("_A").item()) == A
+        d = line["large"]["adjoint_fp32"]
+        G5 = d.pop("_G").cpu().numpy().astype(np.complex128)
+        gx5, gy5 = (t.cpu().numpy().astype(np.float64) for t in d.pop("_g"))
+        idx = np.sort(np.random.default_rng(55).choice(clip5.V, 32, replace=False))
+        rx, ry = oracle.vertex_gradient(clip5.x[idx], clip5.y[idx], clip5.s[idx], clip5.T, K5, G5)
+        d["max_rel_err_sampled"] = max(float(np.max(np.abs(gx5[idx] - rx)) / np.max(np.abs(rx))),
+                                       float(np.max(np.abs(gy5[idx] - ry)) / np.max(np.abs(ry))))
 
 
 def run_only(args):

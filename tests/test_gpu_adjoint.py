@@ -118,3 +118,18 @@ def test_edge_chain_empty_and_direct(fc):
     ax = torch.tensor([1, 0, 1, 0], dtype=torch.int8, device="cuda")
     gE = fc.edge_chain(gx, gy, ev0, ev1, ax).cpu().tolist()
     assert gE == [30.0, 5.0, 70.0, 5.0]
+
+
+def test_config5_adjoint_sampled(fc):
+    """Workload 5 (T=65536, ~945k corners, K=1024): the FP32 adjoint of a seeded
+    random cotangent on the full block, checked on 48 sampled corners (the
+    oracle's derivative of each corner depends only on that corner)."""
+    clip, K = config_clip(5)
+    W = 2 * K + 1
+    rng = np.random.default_rng(5)
+    G = (rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))).astype(np.complex64)
+    gx, gy = gpu_grad(fc, clip, K, G.astype(np.complex128))
+    idx = np.sort(rng.choice(clip.V, 48, replace=False))
+    rx, ry = oracle.vertex_gradient(clip.x[idx], clip.y[idx], clip.s[idx], clip.T, K, G.astype(np.complex128))
+    ex, ey = rel(gx[idx], rx), rel(gy[idx], ry)
+    assert ex < 1e-4 and ey < 1e-4, (ex, ey)
