@@ -479,10 +479,19 @@ def run_extras(fcfs, dev, flush, stream, args):
     wsa = torch.empty(fcfs._lib.load().fcfs_adjoint_workspace_size(clip.V, T, K, 0), dtype=torch.uint8, device=dev)
     ms = _timed_ms(torch, lambda: fcfs.adjoint(x, y, s, T, K, G, gx=gx, gy=gy, workspace=wsa, stream=stream),
                    20, flush, stream)
+    gx16 = torch.empty_like(gx)
+    gy16 = torch.empty_like(gx)
+    wsa16 = torch.empty(fcfs._lib.load().fcfs_adjoint_workspace_size(clip.V, T, K, 1), dtype=torch.uint8,
+                        device=dev)
+    ms16 = _timed_ms(torch, lambda: fcfs.adjoint(x, y, s, T, K, G, prec="split_f16", gx=gx16, gy=gy16,
+                                                 workspace=wsa16, stream=stream), 20, flush, stream)
     out["adjoint"] = {"workload": "clip T=2048, 5000 polygons, V=%d, K=128, pupil-disc loss vs edges "
-                                  "jittered +-2; corner derivatives, FP32" % clip.V,
-                      "value": clip.V * W * W / (ms * 1e-3), "unit": UNIT, "ms": ms,
-                      "_check": (clip, tgt, K, G.cpu().numpy(), gx.cpu().numpy(), gy.cpu().numpy())}
+                                  "jittered +-2; corner derivatives" % clip.V,
+                      "value": clip.V * W * W / (ms16 * 1e-3), "unit": UNIT, "ms": ms16,
+                      "precision": "split_f16 (tcgen05 contraction)",
+                      "fp32": {"value": clip.V * W * W / (ms * 1e-3), "ms": ms},
+                      "_check": (clip, tgt, K, G.cpu().numpy(), gx.cpu().numpy(), gy.cpu().numpy(),
+                                 gx16.cpu().numpy(), gy16.cpu().numpy())}
 
     # batch: workload 3, one launch replayed from a CUDA graph vs one call per clip
     clips, K = batch_clips()
@@ -547,9 +556,18 @@ def run_extras(fcfs, dev, flush, stream, args):
     big["adjoint_fp32"] = {"value": clip5.V * W5 * W5 / (ms_a5 * 1e-3), "ms": ms_a5,
                            "cotangent": "seeded standard complex normal over the block",
                            "_G": G5, "_g": (gx5, gy5)}
+    gx5h = torch.empty_like(gx5)
+    gy5h = torch.empty_like(gx5)
+    wsa5h = torch.empty(fcfs._lib.load().fcfs_adjoint_workspace_size(clip5.V, clip5.T, K5, 1), dtype=torch.uint8,
+                        device=dev)
+    ms_a5h = _timed_ms(torch, lambda: fcfs.adjoint(x5, y5, s5, clip5.T, K5, G5, prec="split_f16", gx=gx5h, gy=gy5h,
+                                                   workspace=wsa5h, stream=stream), 3, flush, stream)
+    big["adjoint_split_f16"] = {"value": clip5.V * W5 * W5 / (ms_a5h * 1e-3), "ms": ms_a5h,
+                                "cotangent": "as adjoint_fp32", "_g": (gx5h, gy5h)}
     out["large"] = {"workload": "clip T=65536, 150000 polygons, V=%d, K=1024 (2049x2049)" % clip5.V,
                     "unit": UNIT, "split_f16": big["split_f16"], "fp32": big["fp32"],
-                    "adjoint_fp32": big["adjoint_fp32"], "_check": (clip5, K5)}
+                    "adjoint_split_f16": big["adjoint_split_f16"], "adjoint_fp32": big["adjoint_fp32"],
+                    "_check": (clip5, K5)}
     return out
 
 
@@ -559,11 +577,13 @@ def extras_accuracy(line, extras):
     import numpy as np
     import oracle
     if "adjoint" in extras:
-        clip, tgt, K, G, gx, gy = extras["adjoint"].pop("_check")
+        clip, tgt, K, G, gx, gy, gx16, gy16 = extras["adjoint"].pop("_check")
         rx, ry = oracle.vertex_gradient(clip.x, clip.y, clip.s, clip.T, K, G.astype(np.complex128))
-        rel = max(float(np.max(np.abs(gx - rx)) / np.max(np.abs(rx))),
-                  float(np.max(np.abs(gy - ry)) / np.max(np.abs(ry))))
-        line["adjoint"]["max_rel_err"] = rel
+
+        def rel(a, b_, c, d):
+            return max(float(np.max(np.abs(a - c)) / np.max(np.abs(c))), float(np.max(np.abs(b_ - d)) / np.max(np.abs(d))))
+        line["adjoint"]["max_rel_err"] = rel(gx16, gy16, rx, ry)
+        line["adjoint"]["fp32"]["max_rel_err"] = rel(gx, gy, rx, ry)
     if "batch" in extras:
         clips, K, Fb, Ab = extras["batch"].pop("_check")
         Fb = Fb.cpu().numpy()
@@ -589,11 +609,13 @@ def extras_accuracy(line, extras):
             d["area_exact"] = int(d.pop("_A").item()) == A
         d = line["large"]["adjoint_fp32"]
         G5 = d.pop("_G").cpu().numpy().astype(np.complex128)
-        gx5, gy5 = (t.cpu().numpy().astype(np.float64) for t in d.pop("_g"))
         idx = np.sort(np.random.default_rng(55).choice(clip5.V, 32, replace=False))
         rx, ry = oracle.vertex_gradient(clip5.x[idx], clip5.y[idx], clip5.s[idx], clip5.T, K5, G5)
-        d["max_rel_err_sampled"] = max(float(np.max(np.abs(gx5[idx] - rx)) / np.max(np.abs(rx))),
-                                       float(np.max(np.abs(gy5[idx] - ry)) / np.max(np.abs(ry))))
+        for key in ("adjoint_fp32", "adjoint_split_f16"):
+            d = line["large"][key]
+            gx5, gy5 = (t.cpu().numpy().astype(np.float64) for t in d.pop("_g"))
+            d["max_rel_err_sampled"] = max(float(np.max(np.abs(gx5[idx] - rx)) / np.max(np.abs(rx))),
+                                           float(np.max(np.abs(gy5[idx] - ry)) / np.max(np.abs(ry))))
 
 
 def run_only(args):

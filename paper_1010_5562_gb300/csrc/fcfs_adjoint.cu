@@ -20,6 +20,7 @@
 // transposed.
 #include <algorithm>
 
+#include <cuda_fp16.h>
 #include <math_constants.h>
 
 #include "fcfs_common.cuh"
@@ -28,6 +29,7 @@ namespace fcfs {
 
 fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl);
 fcfs_status check_ws(const Plan& pl, void* ws, size_t ws_bytes);
+static bool aligned16_ptr(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Workspace of an adjoint call: the forward plan's header and tables, then the
 // two transposed coefficient matrices Mt[col][row] (rows padded to kAdjRowsPad)
@@ -36,13 +38,18 @@ struct AdjPlan {
   Plan p;
   int rows, cols, rows_pad, R, row_tiles;
   size_t off_m, off_part, total;
+  // tensor-core contraction (split FP16): packed FP16 hi / lo coefficient
+  // matrices [hi|lo][matrix][nrows_pad][kdim_pad] and row scales
+  int tc, nrows_pad, kdim_pad;
+  size_t off_mp, off_scale;
 };
 constexpr int kAdjThreads = 128;
 constexpr size_t kAdjSmemBudget = 200 * 1024;
 
-static fcfs_status make_adj_plan(int64_t V, int32_t T, int32_t K, AdjPlan& ap) {
+static fcfs_status make_adj_plan(int64_t V, int32_t T, int32_t K, int32_t prec, AdjPlan& ap) {
   fcfs_status r = make_plan(V, T, K, FCFS_PREC_FP32, ap.p);
   if (r != FCFS_OK) return r;
+  ap.tc = prec == FCFS_PREC_SPLIT_F16 ? 1 : 0;
   ap.rows = 2 * K + 1;
   ap.cols = 2 * K + 2;
   const size_t tab = align_up(tab_f32_bytes(T, ap.p.full), 128);
@@ -55,11 +62,63 @@ static fcfs_status make_adj_plan(int64_t V, int32_t T, int32_t K, AdjPlan& ap) {
   size_t o = ap.p.off_part;   // the forward's split partials are not needed here
   ap.off_m = o;
   o = align_up(o + (size_t)2 * ap.cols * ap.rows_pad * sizeof(float), kWsAlign);
+  if (ap.tc) {
+    const int bnr = adj_tc_rows_per_tile(ap.p.full);
+    ap.row_tiles = (ap.rows + bnr - 1) / bnr;
+    ap.nrows_pad = ap.row_tiles * bnr;
+    ap.kdim_pad = (ap.cols + 63) / 64 * 64;
+    ap.off_mp = o;
+    o = align_up(o + (size_t)2 * 2 * ap.nrows_pad * ap.kdim_pad * sizeof(__half), kWsAlign);
+    ap.off_scale = o;
+    o = align_up(o + (size_t)2 * ap.rows * sizeof(float), kWsAlign);
+  }
   ap.off_part = o;
   o = align_up(o + (size_t)2 * ap.row_tiles * V * sizeof(float), kWsAlign);
   ap.total = o;
   ap.p.total = o;
   return FCFS_OK;
+}
+
+// Pack the coefficient matrices for the tensor-core contraction: row r' of
+// matrix m holds the original row r' + 1 (r' < 2K: k = r'/2 + 1, cos then sin)
+// or row 0 (r' = 2K, k = 0), zeros below; column 2K + 1 (the coordinate term)
+// is multiplied by T because the generated operand holds b / T.  Each row is
+// scaled by a power of two 2^-e that puts its largest magnitude in
+// [2^14, 2^15) (no FP16 overflow, exact to undo) and split into FP16
+// hi = rn(v) and lo = rn(v - hi).  Block (row, matrix).
+__global__ void adj_pack_kernel(AdjPlan ap, uint8_t* ws) {
+  const int rp = blockIdx.x, mat = blockIdx.y;
+  const int K = ap.p.K;
+  const float* Mt = reinterpret_cast<const float*>(ws + ap.off_m) + (size_t)mat * ap.cols * ap.rows_pad;
+  const int orig = rp < 2 * K ? rp + 1 : (rp == 2 * K ? 0 : -1);
+  const float Tf = (float)ap.p.T;
+  auto val = [&](int c) -> float {
+    if (orig < 0 || c >= ap.cols) return 0.f;
+    const float v = Mt[(size_t)c * ap.rows_pad + orig];
+    return c == 2 * K + 1 ? v * Tf : v;
+  };
+  __shared__ float red[256];
+  float mx = 0.f;
+  for (int c = threadIdx.x; c < ap.cols; c += blockDim.x) mx = fmaxf(mx, fabsf(val(c)));
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  const float rmax = red[0];
+  const int e = rmax > 0.f ? ilogbf(rmax) - 14 : 0;
+  const float scale = ldexpf(1.f, -e);
+  __half* hi = reinterpret_cast<__half*>(ws + ap.off_mp) + ((size_t)mat * ap.nrows_pad + rp) * ap.kdim_pad;
+  __half* lo = hi + (size_t)2 * ap.nrows_pad * ap.kdim_pad;
+  for (int c = threadIdx.x; c < ap.kdim_pad; c += blockDim.x) {
+    const float v = val(c) * scale;
+    const __half h = __float2half_rn(v);
+    hi[c] = h;
+    lo[c] = __float2half_rn(v - __half2float(h));
+  }
+  if (threadIdx.x == 0 && rp < ap.rows)
+    reinterpret_cast<float*>(ws + ap.off_scale)[(size_t)mat * ap.rows + rp] = ldexpf(1.f, e);
 }
 
 // Coefficient matrices.  Block (row, matrix): matrix 0 serves gx (D), matrix 1
@@ -271,17 +330,45 @@ static fcfs_status adjoint_impl(const int32_t* x, const int32_t* y, const int8_t
   if (prec != FCFS_PREC_FP32 && prec != FCFS_PREC_SPLIT_F16) return FCFS_EINVAL;
   if (!dF || (V > 0 && (!x || !y || !s || !gx || !gy))) return FCFS_EINVAL;
   AdjPlan ap;
-  fcfs_status r = make_adj_plan(V, T, K, ap);
+  fcfs_status r = make_adj_plan(V, T, K, prec, ap);
   if (r != FCFS_OK) return r;
   if ((r = check_ws(ap.p, ws, ws_bytes)) != FCFS_OK) return r;
   if (V == 0) return FCFS_OK;
+  if (ap.tc && (!aligned16_ptr(x) || !aligned16_ptr(y))) return FCFS_EINVAL;
   if (launch_prep(ap.p, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
   adj_coef_kernel<<<dim3(ap.rows, 2), kAdjThreads, 0, st>>>(ap, reinterpret_cast<const float2*>(dF),
                                                             static_cast<uint8_t*>(ws));
   count_launch(1);
   if (cudaGetLastError() != cudaSuccess) return FCFS_ECUDA;
-  const cudaError_t e = ap.p.full ? launch_adj_gemm_r<true>(ap, x, y, ws, st) : launch_adj_gemm_r<false>(ap, x, y, ws, st);
-  if (e != cudaSuccess) return FCFS_ECUDA;
+  if (ap.tc) {
+    adj_pack_kernel<<<dim3(ap.nrows_pad, 2), 256, 0, st>>>(ap, static_cast<uint8_t*>(ws));
+    count_launch(1);
+    if (cudaGetLastError() != cudaSuccess) return FCFS_ECUDA;
+    const int bnr = adj_tc_rows_per_tile(ap.p.full);
+    const __half* mp = reinterpret_cast<const __half*>(static_cast<uint8_t*>(ws) + ap.off_mp);
+    CUtensorMap mhi, mlo;
+    if (!encode_f16_2d_sw128(&mhi, mp, ap.kdim_pad, 2ull * ap.nrows_pad, 64, bnr) ||
+        !encode_f16_2d_sw128(&mlo, mp + (size_t)2 * ap.nrows_pad * ap.kdim_pad, ap.kdim_pad, 2ull * ap.nrows_pad,
+                             64, bnr))
+      return FCFS_ECUDA;
+    AdjTcArgs ar;
+    ar.pl = ap.p;
+    ar.pl.vx = x;
+    ar.pl.vy = y;
+    ar.pl.vsg = s;
+    ar.nrows = ap.rows;
+    ar.nrows_pad = ap.nrows_pad;
+    ar.kdim_pad = ap.kdim_pad;
+    ar.rtiles = ap.row_tiles;
+    ar.inv_T = 1.f / (float)T;
+    ar.off_scale = ap.off_scale;
+    ar.off_part = ap.off_part;
+    if (launch_adj_tc(ar, mhi, mlo, ws, st) != cudaSuccess) return FCFS_ECUDA;
+  } else {
+    const cudaError_t e =
+        ap.p.full ? launch_adj_gemm_r<true>(ap, x, y, ws, st) : launch_adj_gemm_r<false>(ap, x, y, ws, st);
+    if (e != cudaSuccess) return FCFS_ECUDA;
+  }
   const int blocks = (int)std::min<long long>((V + 255) / 256, 4096);
   adj_finalize_kernel<<<blocks, 256, 0, st>>>(ap, s, static_cast<uint8_t*>(ws), gx, gy);
   count_launch(1);
@@ -317,9 +404,9 @@ fcfs_status fcfs_edge_chain(const float* gx, const float* gy, const int32_t* ev0
 }
 
 size_t fcfs_adjoint_workspace_size(int64_t V, int32_t T, int32_t K, int32_t prec) {
-  (void)prec;
+  if (prec != FCFS_PREC_FP32 && prec != FCFS_PREC_SPLIT_F16) return 0;
   AdjPlan ap;
-  if (make_adj_plan(V, T, K, ap) != FCFS_OK) return 0;
+  if (make_adj_plan(V, T, K, prec, ap) != FCFS_OK) return 0;
   return ap.total;
 }
 

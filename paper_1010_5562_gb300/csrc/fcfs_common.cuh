@@ -460,6 +460,24 @@ cudaError_t launch_gemm_simt(const Plan& pl, const int32_t* x, const int32_t* y,
 // per kernel, device and size (setting them costs a driver call per launch).
 cudaError_t ensure_smem(const void* fn, size_t bytes);
 
+// Tensor-core adjoint (fcfs_adjoint_tc.cu): the plan's vx/vy point at the corners
+struct AdjTcArgs {
+  Plan pl;
+  int nrows;        // 2K + 1 rows of each coefficient matrix (k=1 cos, k=1 sin, ..., k=0)
+  int nrows_pad;    // rows per matrix in the packed arrays (a multiple of the row tile)
+  int kdim_pad;     // packed columns (2K + 2 rounded up to 64)
+  int rtiles;       // row tiles
+  float inv_T;
+  size_t off_scale; // float [2][nrows]: power-of-two row scales
+  size_t off_part;  // float [2][rtiles][V]: per-row-tile partial derivatives
+};
+int adj_tc_rows_per_tile(int full);
+cudaError_t launch_adj_tc(const AdjTcArgs& ar, const CUtensorMap& mhi, const CUtensorMap& mlo, void* ws,
+                          cudaStream_t st);
+// 2-D FP16 tensor map (cols innermost), 128-byte swizzle, box box_cols x box_rows
+bool encode_f16_2d_sw128(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_cols,
+                         uint32_t box_rows);
+
 // 0: the call cannot be fused; else the cluster size (1 or 2) of the fused launch
 int gemm_tc_fuse_cluster(const Plan& pl);
 bool make_part_map(const Plan& pl, void* ws, int parts, CUtensorMap* map);

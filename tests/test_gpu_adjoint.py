@@ -29,10 +29,10 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def gpu_grad(fc, clip, K, G):
+def gpu_grad(fc, clip, K, G, prec="fp32"):
     x, y, s = dev(clip.x), dev(clip.y), dev(clip.s)
     dF = torch.from_numpy(G.astype(np.complex64)).cuda()
-    gx, gy = fc.adjoint(x, y, s, clip.T, K, dF)
+    gx, gy = fc.adjoint(x, y, s, clip.T, K, dF, prec=prec)
     torch.cuda.synchronize()
     return gx.cpu().numpy().astype(np.float64), gy.cpu().numpy().astype(np.float64)
 
@@ -41,18 +41,26 @@ def rel(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-@pytest.mark.parametrize("K", [1, 7, 40, 64, 100])
-def test_random_cotangent(fc, K):
+PRECS = ["fp32", "split_f16"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("K", [1, 7, 40, 64, 100, 200])
+def test_random_cotangent(fc, K, prec):
+    """The split-FP16 path runs the contraction on the tensor cores (row tiles
+    of 128 coefficient rows; K = 64, 100, 200 give full, partial and one-row
+    last tiles); 30 polygons leave a partial tile of 256 corners."""
     clip = make_clip(512, 30, 700 + K, smin=6, smax=40)
     rng = np.random.default_rng(K)
     W = 2 * K + 1
     G = rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))
-    gx, gy = gpu_grad(fc, clip, K, G)
+    gx, gy = gpu_grad(fc, clip, K, G, prec)
     rx, ry = oracle.vertex_gradient(clip.x, clip.y, clip.s, clip.T, K, G)
     assert rel(gx, rx) < TOL and rel(gy, ry) < TOL, (rel(gx, rx), rel(gy, ry))
 
 
-def test_config4_pupil_loss_gradient(fc):
+@pytest.mark.parametrize("prec", PRECS)
+def test_config4_pupil_loss_gradient(fc, prec):
     """Workload 4: T=2048, ~31.7k corners, K=128, L = sum over k^2+l^2 <= K^2 of
     |F - F_target|^2 with the target's edges jittered by U{-2..2}."""
     clip, K = config_clip(4)
@@ -61,7 +69,7 @@ def test_config4_pupil_loss_gradient(fc):
     F = oracle.block(clip.x, clip.y, clip.s, T, K)
     Ft = oracle.block(tgt.x, tgt.y, tgt.s, T, K)
     _, G = oracle.pupil_loss(F, Ft, K)
-    gx, gy = gpu_grad(fc, clip, K, G)
+    gx, gy = gpu_grad(fc, clip, K, G, prec)
     rx, ry = oracle.vertex_gradient(clip.x, clip.y, clip.s, T, K, G)
     assert rel(gx, rx) < TOL and rel(gy, ry) < TOL, (rel(gx, rx), rel(gy, ry))
     # chained to edge positions on the GPU
@@ -120,7 +128,8 @@ def test_edge_chain_empty_and_direct(fc):
     assert gE == [30.0, 5.0, 70.0, 5.0]
 
 
-def test_config5_adjoint_sampled(fc):
+@pytest.mark.parametrize("prec", PRECS)
+def test_config5_adjoint_sampled(fc, prec):
     """Workload 5 (T=65536, ~945k corners, K=1024): the FP32 adjoint of a seeded
     random cotangent on the full block, checked on 48 sampled corners (the
     oracle's derivative of each corner depends only on that corner)."""
@@ -128,7 +137,7 @@ def test_config5_adjoint_sampled(fc):
     W = 2 * K + 1
     rng = np.random.default_rng(5)
     G = (rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))).astype(np.complex64)
-    gx, gy = gpu_grad(fc, clip, K, G.astype(np.complex128))
+    gx, gy = gpu_grad(fc, clip, K, G.astype(np.complex128), prec)
     idx = np.sort(rng.choice(clip.V, 48, replace=False))
     rx, ry = oracle.vertex_gradient(clip.x[idx], clip.y[idx], clip.s[idx], clip.T, K, G.astype(np.complex128))
     ex, ey = rel(gx[idx], rx), rel(gy[idx], ry)
