@@ -38,10 +38,10 @@ struct AdjPlan {
   Plan p;
   int rows, cols, rows_pad, R, row_tiles;
   size_t off_m, off_part, total;
-  // tensor-core contraction (split FP16): packed FP16 hi / lo coefficient
-  // matrices [hi|lo][matrix][nrows_pad][kdim_pad] and row scales
+  // tensor-core contraction (split FP16): the frequency block packed as FP16
+  // hi / lo [hi|lo][matrix][nrows_pad][kdim_pad], its row terms and the k = 0 row
   int tc, nrows_pad, kdim_pad;
-  size_t off_mp, off_scale;
+  size_t off_mp, off_rows, off_m0;
 };
 constexpr int kAdjThreads = 128;
 constexpr size_t kAdjSmemBudget = 200 * 1024;
@@ -56,21 +56,25 @@ static fcfs_status make_adj_plan(int64_t V, int32_t T, int32_t K, int32_t prec, 
   ap.R = 0;
   for (int R : {64, 32, 16, 8})
     if (!ap.R && tab + (size_t)ap.cols * R * sizeof(float) <= kAdjSmemBudget) ap.R = R;
-  if (!ap.R) return FCFS_EUNSUPPORTED;
+  if (!ap.R) {   // the FP32 contraction needs a row tile in shared memory; the tensor cores do not
+    if (!ap.tc) return FCFS_EUNSUPPORTED;
+    ap.R = 8;
+  }
   ap.row_tiles = (ap.rows + ap.R - 1) / ap.R;
   ap.rows_pad = ap.row_tiles * ap.R;
   size_t o = ap.p.off_part;   // the forward's split partials are not needed here
   ap.off_m = o;
   o = align_up(o + (size_t)2 * ap.cols * ap.rows_pad * sizeof(float), kWsAlign);
   if (ap.tc) {
-    const int bnr = adj_tc_rows_per_tile(ap.p.full);
-    ap.row_tiles = (ap.rows + bnr - 1) / bnr;
-    ap.nrows_pad = ap.row_tiles * bnr;
-    ap.kdim_pad = (ap.cols + 63) / 64 * 64;
+    ap.row_tiles = (2 * K + kAdjPairRows - 1) / kAdjPairRows;
+    ap.nrows_pad = ap.row_tiles * kAdjPairRows;
+    ap.kdim_pad = (2 * K + 63) / 64 * 64;
     ap.off_mp = o;
     o = align_up(o + (size_t)2 * 2 * ap.nrows_pad * ap.kdim_pad * sizeof(__half), kWsAlign);
-    ap.off_scale = o;
-    o = align_up(o + (size_t)2 * ap.rows * sizeof(float), kWsAlign);
+    ap.off_rows = o;
+    o = align_up(o + (size_t)2 * ap.nrows_pad * sizeof(float4), kWsAlign);
+    ap.off_m0 = o;
+    o = align_up(o + (size_t)2 * (ap.kdim_pad + 4) * sizeof(float), kWsAlign);
   }
   ap.off_part = o;
   o = align_up(o + (size_t)2 * ap.row_tiles * V * sizeof(float), kWsAlign);
@@ -79,27 +83,32 @@ static fcfs_status make_adj_plan(int64_t V, int32_t T, int32_t K, int32_t prec, 
   return FCFS_OK;
 }
 
-// Pack the coefficient matrices for the tensor-core contraction: row r' of
-// matrix m holds the original row r' + 1 (r' < 2K: k = r'/2 + 1, cos then sin)
-// or row 0 (r' = 2K, k = 0), zeros below; column 2K + 1 (the coordinate term)
-// is multiplied by T because the generated operand holds b / T.  Each row is
-// scaled by a power of two 2^-e that puts its largest magnitude in
-// [2^14, 2^15) (no FP16 overflow, exact to undo) and split into FP16
-// hi = rn(v) and lo = rn(v - hi).  Block (row, matrix).
+// Pack the coefficient matrices for the tensor-core contraction.  Block
+// (packed row rp, matrix):
+//  * rp < nrows_pad: frequency row rp (original row rp + 1: k = rp/2 + 1, cos
+//    then sin; zeros past 2K) over the 2K frequency columns, scaled by a power
+//    of two 2^-e that puts its largest magnitude in [2^14, 2^15) (no FP16
+//    overflow, exact to undo) and split into FP16 hi = rn(v), lo = rn(v - hi);
+//    its row terms (2^e, column-1 coefficient, column-b coefficient, 0) in FP32.
+//  * rp = nrows_pad: the k = 0 row over the frequency columns (zeros past 2K),
+//    then its column-1 and column-b coefficients, FP32.
 __global__ void adj_pack_kernel(AdjPlan ap, uint8_t* ws) {
   const int rp = blockIdx.x, mat = blockIdx.y;
-  const int K = ap.p.K;
+  const int nf = 2 * ap.p.K;
   const float* Mt = reinterpret_cast<const float*>(ws + ap.off_m) + (size_t)mat * ap.cols * ap.rows_pad;
-  const int orig = rp < 2 * K ? rp + 1 : (rp == 2 * K ? 0 : -1);
-  const float Tf = (float)ap.p.T;
-  auto val = [&](int c) -> float {
-    if (orig < 0 || c >= ap.cols) return 0.f;
-    const float v = Mt[(size_t)c * ap.rows_pad + orig];
-    return c == 2 * K + 1 ? v * Tf : v;
-  };
+  if (rp == ap.nrows_pad) {
+    float* m0 = reinterpret_cast<float*>(ws + ap.off_m0) + (size_t)mat * (ap.kdim_pad + 4);
+    for (int c = threadIdx.x; c < ap.kdim_pad + 4; c += blockDim.x) {
+      const int src = c < nf ? c : (c == ap.kdim_pad ? nf : (c == ap.kdim_pad + 1 ? nf + 1 : -1));
+      m0[c] = src < 0 ? 0.f : Mt[(size_t)src * ap.rows_pad];
+    }
+    return;
+  }
+  const int orig = rp < nf ? rp + 1 : -1;
+  auto val = [&](int c) -> float { return orig < 0 || c >= nf ? 0.f : Mt[(size_t)c * ap.rows_pad + orig]; };
   __shared__ float red[256];
   float mx = 0.f;
-  for (int c = threadIdx.x; c < ap.cols; c += blockDim.x) mx = fmaxf(mx, fabsf(val(c)));
+  for (int c = threadIdx.x; c < nf; c += blockDim.x) mx = fmaxf(mx, fabsf(val(c)));
   red[threadIdx.x] = mx;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -117,8 +126,11 @@ __global__ void adj_pack_kernel(AdjPlan ap, uint8_t* ws) {
     hi[c] = h;
     lo[c] = __float2half_rn(v - __half2float(h));
   }
-  if (threadIdx.x == 0 && rp < ap.rows)
-    reinterpret_cast<float*>(ws + ap.off_scale)[(size_t)mat * ap.rows + rp] = ldexpf(1.f, e);
+  if (threadIdx.x == 0)
+    reinterpret_cast<float4*>(ws + ap.off_rows)[(size_t)mat * ap.nrows_pad + rp] =
+        orig < 0 ? make_float4(0.f, 0.f, 0.f, 0.f)
+                 : make_float4(ldexpf(1.f, e), Mt[(size_t)nf * ap.rows_pad + orig],
+                               Mt[(size_t)(nf + 1) * ap.rows_pad + orig], 0.f);
 }
 
 // Coefficient matrices.  Block (row, matrix): matrix 0 serves gx (D), matrix 1
@@ -341,27 +353,26 @@ static fcfs_status adjoint_impl(const int32_t* x, const int32_t* y, const int8_t
   count_launch(1);
   if (cudaGetLastError() != cudaSuccess) return FCFS_ECUDA;
   if (ap.tc) {
-    adj_pack_kernel<<<dim3(ap.nrows_pad, 2), 256, 0, st>>>(ap, static_cast<uint8_t*>(ws));
+    adj_pack_kernel<<<dim3(ap.nrows_pad + 1, 2), 256, 0, st>>>(ap, static_cast<uint8_t*>(ws));
     count_launch(1);
     if (cudaGetLastError() != cudaSuccess) return FCFS_ECUDA;
-    const int bnr = adj_tc_rows_per_tile(ap.p.full);
     const __half* mp = reinterpret_cast<const __half*>(static_cast<uint8_t*>(ws) + ap.off_mp);
     CUtensorMap mhi, mlo;
-    if (!encode_f16_2d_sw128(&mhi, mp, ap.kdim_pad, 2ull * ap.nrows_pad, 64, bnr) ||
+    if (!encode_f16_2d_sw128(&mhi, mp, ap.kdim_pad, 2ull * ap.nrows_pad, 64, kAdjPairRows / 2) ||
         !encode_f16_2d_sw128(&mlo, mp + (size_t)2 * ap.nrows_pad * ap.kdim_pad, ap.kdim_pad, 2ull * ap.nrows_pad,
-                             64, bnr))
+                             64, kAdjPairRows / 2))
       return FCFS_ECUDA;
     AdjTcArgs ar;
     ar.pl = ap.p;
     ar.pl.vx = x;
     ar.pl.vy = y;
     ar.pl.vsg = s;
-    ar.nrows = ap.rows;
+    ar.nrows = 2 * K;
     ar.nrows_pad = ap.nrows_pad;
     ar.kdim_pad = ap.kdim_pad;
     ar.rtiles = ap.row_tiles;
-    ar.inv_T = 1.f / (float)T;
-    ar.off_scale = ap.off_scale;
+    ar.off_rows = ap.off_rows;
+    ar.off_m0 = ap.off_m0;
     ar.off_part = ap.off_part;
     if (launch_adj_tc(ar, mhi, mlo, ws, st) != cudaSuccess) return FCFS_ECUDA;
   } else {

@@ -1,24 +1,29 @@
 // Split-FP16 tensor-core adjoint: the contraction of the adjoint (see
-// fcfs_adjoint.cu for the formulation) on tcgen05.
+// fcfs_adjoint.cu for the formulation) on tcgen05, in CTA pairs.
 //
 // For matrix m (0: gx, 1: gy) and corner v with contraction coordinate b
-// (y for gx, x for gy) and epilogue coordinate a (x for gx, y for gy):
-//   Z[r, v] = sum_c M'[r, c] B'[c, v],   part[m][tile][v] = sum_{r in tile} A'[r, v] Z[r, v],
-// B'[., v] = (cos, sin of 2 pi l b / T for l = 1..K, 1, b / T, 0 ...),
-// A'[., v] = (cos, sin of 2 pi k a / T for k = 1..K, 1): the rows are ordered
-// (k=1 cos, k=1 sin, ..., k=K sin, k=0).
+// (y for gx, x for gy) and epilogue coordinate a (x for gx, y for gy), the
+// coefficient matrix M (rows: k = 0 | cos, sin of k for k = 1..K; columns: cos,
+// sin of l for l = 1..K | 1 | b) splits into the frequency block Mf (rows and
+// columns below 2K), the k = 0 row m0 and the columns 1 and b (s1, sb), so the
+// partial of row tile t is
+//   part[m][t][v] = sum_{r in t} A'[r, v] (sum_c Mf[r, c] B'[c, v] + s1[r] + sb[r] b)
+//                 + [t = 0] (sum_c m0[c] B'[c, v] + m0_1 + m0_b b),
+// with B'[., v] = (cos, sin of 2 pi l b / T)_l and A'[., v] = (cos, sin of 2 pi k a / T)_k,
+// rows and columns ordered (k=1 cos, k=1 sin, ..., k=K sin).
 //
-// The GEMM runs with the corners as the MMA's M dimension: a CTA holds 256
-// corners (two M = 128 accumulators in TMEM, lane = corner) against BNR rows
-// of M' (N), contracted over the columns c in chunks of 64.  M' is packed once
-// per call as FP16 hi + lo with a power-of-two scale per row (so that no entry
-// overflows FP16) and streamed by TMA in 128-byte swizzled K-major tiles; B' is
-// generated on chip like the forward operands (integer phase, table anchor,
-// angle addition over runs of 8 frequencies, hi = rn(v), lo = rn(v - hi)).
-// Products hi*hi go to accumulator D1, hi*lo + lo*hi to D2.  The epilogue is a
-// per-thread dot: the thread of TMEM lane v multiplies its row of D1 + D2 (one
-// value per M' row) by A'[., v], generated along k the same way, and writes the
-// partial of this row tile; the finalize kernel sums the row tiles.
+// Z = Mf B' runs on the tensor cores with the corners as the MMA's M
+// dimension: a CTA pair holds 256 corners (128 per CTA, TMEM lane = corner)
+// against 256 rows of Mf (N; each CTA stages 128 of them), contracted over the
+// columns in chunks of 64 by cta_group::2 MMAs that the pair's rank 0 issues.
+// Mf is packed once per call as FP16 hi + lo with a power-of-two scale per row
+// and streamed by TMA in 128-byte swizzled K-major tiles; B' is generated on
+// chip from the exact integer phase l b mod T (run anchors from a two-level
+// sincos table, angle addition over runs of 8 frequencies, hi = rn(v),
+// lo = rn(v - hi)).  Products hi*hi go to accumulator D1, hi*lo + lo*hi to D2.
+// The side terms stay FP32: the generator threads of row tile 0 accumulate the
+// k = 0 row from the B' values they generate, and the epilogue adds s1 + sb b
+// to each row before the per-corner dot with A'.
 #include <algorithm>
 
 #include "fcfs_common.cuh"
@@ -27,20 +32,17 @@ namespace fcfs {
 
 namespace {
 
-constexpr int kVT = 256;         // corners per CTA (two M = 128 sub-tiles)
-constexpr int kAC = 64;          // columns per chunk = one 128-byte swizzle row of FP16
-constexpr int kGenThreadsA = 256;   // one generator thread per corner
-constexpr int kThreadsA = kGenThreadsA + 64;
-
-template <int BNR>
-struct AdjTcLayout {
-  static constexpr int kATile = 128 * 128;   // one M = 128 sub-tile, FP16 (hi or lo)
-  static constexpr int kBTile = BNR * 128;
-  // A0_hi, A0_lo, A1_hi, A1_lo, B_hi, B_lo
-  static constexpr int kStage = 4 * kATile + 2 * kBTile;
-  static constexpr int kStages = 2;
-  static constexpr int kOps = kStages * kStage;
-};
+constexpr int kVP = 128;                  // corners per CTA (TMEM lanes)
+constexpr int kRH = kAdjPairRows / 2;     // coefficient rows staged per CTA
+constexpr int kAC = 64;                   // columns per chunk = one 128-byte swizzle row of FP16
+constexpr int kGen = 256;                 // generator / epilogue threads: two per corner
+constexpr int kThreadsA = kGen + 64;      // + MMA warp + TMA warp
+constexpr int kTile = 128 * 128;          // one 128-row FP16 tile of a chunk (hi or lo), bytes
+constexpr int kStage = 4 * kTile;         // corners hi, lo (generated), coefficient rows hi, lo (TMA)
+constexpr int kStages = 3;
+constexpr int kOps = kStages * kStage;
+constexpr int kTlMax = 512;               // two-level table entries for T <= 2^16
+constexpr size_t kAdjSmem = 1024 + kOps + kTlMax * 8 + kAdjPairRows * 16 + kVP * 4 + 256;
 
 __device__ __forceinline__ void st_shared_v4a(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
@@ -64,261 +66,287 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-template <int BNR, bool FULL>
+// Two-level sincos table: (cos, sin)(2 pi p / T) = coarse[p >> f] * fine[p mod 2^f],
+// both factors correctly rounded FP32 values copied from the plan's table.
+struct TwoLevel {
+  const float2* t;   // coarse [nc], then fine [2^f]
+  uint32_t f, fmask, nc;
+};
+__device__ __forceinline__ float2 tl_lookup(const TwoLevel& tl, uint32_t p) {
+  const float2 c = tl.t[p >> tl.f], d = tl.t[tl.nc + (p & tl.fmask)];
+  return make_float2(fmaf(c.x, d.x, -(c.y * d.y)), fmaf(c.y, d.x, c.x * d.y));
+}
+
 __global__ void __launch_bounds__(kThreadsA, 1)
     adj_tc_kernel(const __grid_constant__ CUtensorMap mhi, const __grid_constant__ CUtensorMap mlo, AdjTcArgs ar,
                   uint8_t* ws) {
-  using L = AdjTcLayout<BNR>;
-  constexpr int GW = kGenThreadsA / 32;
+  constexpr int GW = kGen / 32;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
   const Plan& pl = ar.pl;
-  const size_t tb = tab_f32_bytes(pl.T, FULL);
   uint8_t* ops = sm;
-  float* tab = reinterpret_cast<float*>(sm + L::kOps);
-  float* rscale = reinterpret_cast<float*>(sm + L::kOps + align_up(tb, 128));   // BNR row scales
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kOps + align_up(tb, 128) + BNR * 4);
-  uint64_t* full = bars;                 // [kStages]: generated A and loaded B of a chunk
-  uint64_t* empty = full + L::kStages;   // [kStages]: the chunk's MMAs completed
-  uint64_t* accfull = empty + L::kStages;
-  uint64_t* tabbar = accfull + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tabbar + 1);
+  float2* tlt = reinterpret_cast<float2*>(sm + kOps);
+  float4* rows = reinterpret_cast<float4*>(tlt + kTlMax);        // this pair's 256 row terms
+  float* comb = reinterpret_cast<float*>(rows + kAdjPairRows);   // second column half of each corner
+  uint64_t* ofull = reinterpret_cast<uint64_t*>(comb + kVP);     // [kStages] rank 0: chunk ready in both CTAs
+  uint64_t* tfull = ofull + kStages;                             // [kStages] this CTA's rows landed
+  uint64_t* empty = tfull + kStages;                             // [kStages] the chunk's MMAs completed
+  uint64_t* accfull = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfull + 1);
 
   Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int vt = blockIdx.x, rt = blockIdx.y, mat = blockIdx.z;
-  const long long vbase = (long long)vt * kVT;
-  const int nrows = ar.nrows;
-  const int r0 = rt * BNR;
-  const int nr = min(BNR, nrows - r0);
-  const int nmma = (nr + 15) / 16 * 16;   // MMA N: this tile's rows rounded up to 16
+  // blockIdx.x = 2 (corner pair tile) + rank; rank r holds corners [128 r, 128 r + 128)
+  // of the pair tile and coefficient rows [128 r, 128 r + 128) of row tile rt
+  const uint32_t rank = cluster_ctarank();
+  const int rt = blockIdx.y, mat = blockIdx.z;
+  const long long vbase = (long long)(blockIdx.x >> 1) * (2 * kVP) + (long long)rank * kVP;
+  const int r0 = rt * kAdjPairRows;
   const int nch = ar.kdim_pad / kAC;
 
-  if (tid == kGenThreadsA + 32) {
-    for (int i = 0; i < L::kStages; ++i) {
-      mbar_init(&full[i], kGenThreadsA + 1);   // every generator thread and the TMA thread
+  if (tid == kGen + 32) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&ofull[i], 2 * kGen + 1);   // both CTAs' generator threads and rank 1's row forwarder
+      mbar_init(&tfull[i], 1);
       mbar_init(&empty[i], 1);
     }
     mbar_init(accfull, 1);
-    mbar_init(tabbar, 1);
     fence_mbar_init();
   }
-  if (warp == GW) {
-    tmem_alloc(tmem_slot, 4 * BNR);   // sub-tile s: D1 at 2 s BNR, D2 at 2 s BNR + BNR
-    tmem_relinquish();
+  if (warp == GW) {   // collective with the peer's MMA warp: D1 at 0, D2 at 256
+    tmem_alloc_pair(tmem_slot, 2 * kAdjPairRows);
+    tmem_relinquish_pair();
   }
-  for (int i = tid; i < BNR; i += blockDim.x)
-    rscale[i] = i < nr ? __ldg(reinterpret_cast<const float*>(ws + ar.off_scale) + (size_t)mat * nrows + r0 + i)
-                       : 0.f;
+  const uint32_t logT = (uint32_t)pl.logT, f = (logT + 1u) / 2u, nc = 1u << (logT - f);
+  const TwoLevel tl{tlt, f, (1u << f) - 1u, nc};
+  if (tid < kGen) {
+    const float* gt = reinterpret_cast<const float*>(ws + pl.off_tab_f32);
+    const uint32_t logQ = logT - 2u;
+    for (uint32_t i = tid; i < nc + (1u << f); i += kGen) {
+      const uint32_t p = i < nc ? i << f : i - nc;
+      tlt[i] = pl.full ? f32_lookup<true>(gt, p, logQ) : f32_lookup<false>(gt, p, logQ);
+    }
+    const float4* gr = reinterpret_cast<const float4*>(ws + ar.off_rows) + (size_t)mat * ar.nrows_pad + r0;
+    for (int i = tid; i < kAdjPairRows; i += kGen) rows[i] = __ldg(gr + i);
+  }
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();   // the pair's barriers are signalled from both CTAs
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t mask = (uint32_t)pl.T - 1u;
-  const uint32_t logQ = (uint32_t)pl.logT - 2u;
   const int K = pl.K;
 
   if (warp == GW + 1) {
-    // ---------------- table copy and M' tiles (TMA) ----------------
+    // ---------------- coefficient rows (TMA) ----------------
     if (lane == 0) {
       prefetch_tensormap(&mhi);
       prefetch_tensormap(&mlo);
-      mbar_arrive_expect_tx(tabbar, (uint32_t)tb);
-      bulk_load(tab, ws + pl.off_tab_f32, (uint32_t)tb, tabbar);
+      const int row = mat * ar.nrows_pad + r0 + (int)rank * kRH;
       int j = 0;
       for (; j < nch; ++j) {
-        const int s = j % L::kStages;
-        const uint32_t ph = (uint32_t)(j / L::kStages) & 1u;
+        const int s = j % kStages;
+        const uint32_t ph = (uint32_t)(j / kStages) & 1u;
         if (!mbar_wait(&empty[s], ph ^ 1u, st, 40)) break;
-        uint8_t* stage = ops + (size_t)s * L::kStage;
-        mbar_arrive_expect_tx(&full[s], 2u * L::kBTile);
-        // rows past the matrix read as zeros; coordinate 2 selects (matrix)
-        tma_load_2d(stage + 4 * L::kATile, &mhi, j * kAC, mat * ar.nrows_pad + r0, &full[s]);
-        tma_load_2d(stage + 4 * L::kATile + L::kBTile, &mlo, j * kAC, mat * ar.nrows_pad + r0, &full[s]);
+        uint8_t* bt = ops + (size_t)s * kStage + 2 * kTile;
+        mbar_arrive_expect_tx(&tfull[s], 2u * kTile);
+        tma_load_2d(bt, &mhi, j * kAC, row, &tfull[s]);
+        tma_load_2d(bt + kTile, &mlo, j * kAC, row, &tfull[s]);
       }
-      // drain: every issued copy has landed before the CTA may exit
-      for (int q = max(0, j - L::kStages); q < j; ++q)
-        mbar_wait(&full[q % L::kStages], (uint32_t)(q / L::kStages) & 1u, st, 41);
-      mbar_wait(tabbar, 0, st, 42);
+      // every issued copy has landed before the CTA may exit
+      for (int q = max(0, j - kStages); q < j; ++q)
+        mbar_wait(&tfull[q % kStages], (uint32_t)(q / kStages) & 1u, st, 41);
     }
   } else if (warp == GW) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      const uint32_t idesc = idesc_f16_f32(128, nmma);
+    if (lane == 0 && rank == 0) {
+      // ---------------- MMA issuer (rank 0 for the pair) ----------------
+      constexpr uint32_t idesc = idesc_f16_f32(2 * kVP, kAdjPairRows);
       const uint32_t ops_a = smem_u32(ops);
       for (int j = 0; j < nch; ++j) {
-        const int s = j % L::kStages;
-        const uint32_t ph = (uint32_t)(j / L::kStages) & 1u;
-        if (!mbar_wait(&full[s], ph, st, 43)) break;
+        const int s = j % kStages;
+        const uint32_t ph = (uint32_t)(j / kStages) & 1u;
+        if (!mbar_wait_cluster(&ofull[s], ph, st, 43) || !mbar_wait(&tfull[s], ph, st, 47)) break;
         tc_fence_after();
-        const uint32_t base = ops_a + s * L::kStage;
-        const uint32_t bhi = base + 4 * L::kATile, blo = bhi + L::kBTile;
+        const uint32_t ahi = ops_a + s * kStage, alo = ahi + kTile, bhi = alo + kTile, blo = bhi + kTile;
 #pragma unroll
         for (int ks = 0; ks < kAC / 16; ++ks) {
           const uint32_t o = ks * 32;
+          const uint64_t dah = sdesc_sw128(ahi + o), dal = sdesc_sw128(alo + o);
           const uint64_t dbh = sdesc_sw128(bhi + o), dbl = sdesc_sw128(blo + o);
-#pragma unroll
-          for (int sub = 0; sub < 2; ++sub) {
-            const uint32_t ahi = base + sub * 2 * L::kATile, alo = ahi + L::kATile;
-            const uint64_t dah = sdesc_sw128(ahi + o), dal = sdesc_sw128(alo + o);
-            const uint32_t d1 = tmem + (uint32_t)(sub * 2 * BNR), d2 = d1 + BNR;
-            tc_mma_f16(d1, dah, dbh, idesc, (j | ks) != 0);
-            tc_mma_f16(d2, dah, dbl, idesc, (j | ks) != 0);
-            tc_mma_f16(d2, dal, dbh, idesc, 1);
-          }
+          tc_mma_f16_pair(tmem, dah, dbh, idesc, (j | ks) != 0);
+          tc_mma_f16_pair(tmem + kAdjPairRows, dah, dbl, idesc, (j | ks) != 0);
+          tc_mma_f16_pair(tmem + kAdjPairRows, dal, dbh, idesc, 1);
         }
-        tc_commit(&empty[s]);
+        tc_commit_pair(&empty[s]);
       }
-      tc_commit(accfull);
+      tc_commit_pair(accfull);
+    } else if (lane == 0) {
+      // rank 1: each chunk's rows have landed here -> count it on rank 0's barrier
+      for (int j = 0; j < nch; ++j) {
+        const int s = j % kStages;
+        if (!mbar_wait(&tfull[s], (uint32_t)(j / kStages) & 1u, st, 48)) break;
+        mbar_arrive_cluster(&ofull[s], 0);
+      }
     }
   } else {
-    // ---------------- generators: one thread per corner ----------------
-    // Corner i = tid of the CTA's 256 (sub-tile i / 128, row i % 128).  A chunk
-    // of 64 columns holds l = 32 j + 1 .. 32 j + 32 as (cos, sin) pairs, the
-    // last chunks also the columns 1 and b / T and zero padding.
-    const int sub = tid >> 7, row = tid & 127;
-    const long long v = vbase + tid;
+    // ---------------- generators: two threads per corner ----------------
+    // Thread (corner i, half g) writes columns 32 g .. 32 g + 31 of row i of
+    // each chunk: l = 32 j + 16 g + 1 .. + 16 as (cos, sin) pairs, zeros past K.
+    const int cidx = tid & (kVP - 1), g = tid >> 7;
+    const long long v = vbase + cidx;
     const bool live = v < pl.V;
     const int32_t* cbp = mat == 0 ? pl.vy : pl.vx;
     const uint32_t b = live ? (uint32_t)__ldg(cbp + v) : 0u;
+    const float* m0 = reinterpret_cast<const float*>(ws + ar.off_m0) + (size_t)mat * (ar.kdim_pad + 4);
+    const bool krow = rt == 0;   // row tile 0 also carries the k = 0 row
+    const float2 w = tl_lookup(tl, b & mask);   // step cos, sin(2 pi b / T)
     const uint32_t ops_a = smem_u32(ops);
-    bool ok = mbar_wait(tabbar, 0, st, 44);
-    const float2 w = f32_lookup<FULL>(tab, b & mask, logQ);   // step cos/sin(2 pi b / T)
-    for (int j = 0; ok && j < nch; ++j) {
-      const int s = j % L::kStages;
-      const uint32_t ph = (uint32_t)(j / L::kStages) & 1u;
+    float acc0 = 0.f;
+    for (int j = 0; j < nch; ++j) {
+      const int s = j % kStages;
+      const uint32_t ph = (uint32_t)(j / kStages) & 1u;
       if (!mbar_wait(&empty[s], ph ^ 1u, st, 45)) break;
-      const uint32_t hi_row = ops_a + s * L::kStage + sub * 2 * L::kATile + (uint32_t)row * 128u;
+      const uint32_t hi_row = ops_a + s * kStage + (uint32_t)cidx * 128u;
 #pragma unroll
-      for (int run = 0; run < 4; ++run) {   // 8 frequencies = 16 columns = two 16-byte chunks
-        const int l0 = 32 * j + 8 * run + 1;   // first frequency of the run
-        uint32_t hv[8], lv[8];
+      for (int run = 0; run < 2; ++run) {
+        const int q = 2 * g + run;              // run of 8 frequencies = 16 columns = two 16-byte chunks
+        const int l0 = 32 * j + 8 * q + 1;
+        float cv[8], sv[8];
         if (l0 + 7 <= K) {
-          const float2 an = f32_lookup<FULL>(tab, (uint32_t)l0 * b & mask, logQ);
+          const float2 an = tl_lookup(tl, (uint32_t)l0 * b & mask);
           float c = an.x, sn = an.y;
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            float c1 = fmaf(c, w.x, -(sn * w.y)), s1 = fmaf(sn, w.x, c * w.y);
-            split_pair(c, sn, hv[2 * t], lv[2 * t]);
-            c = c1;
-            sn = s1;
-            c1 = fmaf(c, w.x, -(sn * w.y));
-            s1 = fmaf(sn, w.x, c * w.y);
-            split_pair(c, sn, hv[2 * t + 1], lv[2 * t + 1]);
+          for (int t = 0; t < 8; ++t) {
+            cv[t] = c;
+            sv[t] = sn;
+            const float c1 = fmaf(c, w.x, -(sn * w.y)), s1 = fmaf(sn, w.x, c * w.y);
             c = c1;
             sn = s1;
           }
         } else {
-          // the run crosses the end of the frequencies: direct lookups, then
-          // the columns 1 and b / T, then zeros
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
-            const int l = l0 + t;
-            float c = 0.f, sn = 0.f;
-            if (l <= K) {
-              const float2 e = f32_lookup<FULL>(tab, (uint32_t)l * b & mask, logQ);
-              c = e.x;
-              sn = e.y;
-            } else if (l == K + 1) {
-              c = live ? 1.f : 0.f;
-              sn = (float)b * ar.inv_T;
+            cv[t] = sv[t] = 0.f;
+            if (l0 + t <= K) {
+              const float2 e = tl_lookup(tl, (uint32_t)(l0 + t) * b & mask);
+              cv[t] = e.x;
+              sv[t] = e.y;
             }
-            split_pair(c, sn, hv[t], lv[t]);
           }
         }
         if (!live) {
 #pragma unroll
-          for (int t = 0; t < 8; ++t) hv[t] = lv[t] = 0u;
+          for (int t = 0; t < 8; ++t) cv[t] = sv[t] = 0.f;
         }
-        const uint32_t c0 = (uint32_t)(2 * run), c1 = c0 + 1;
-        const uint32_t o0 = (c0 ^ (uint32_t)(row & 7)) << 4, o1 = (c1 ^ (uint32_t)(row & 7)) << 4;
+        if (krow) {
+          const float4* mp = reinterpret_cast<const float4*>(m0 + 2 * (l0 - 1));
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 m = __ldg(mp + u);
+            acc0 = fmaf(m.x, cv[2 * u], acc0);
+            acc0 = fmaf(m.y, sv[2 * u], acc0);
+            acc0 = fmaf(m.z, cv[2 * u + 1], acc0);
+            acc0 = fmaf(m.w, sv[2 * u + 1], acc0);
+          }
+        }
+        uint32_t hv[8], lv[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) split_pair(cv[t], sv[t], hv[t], lv[t]);
+        const uint32_t c0 = (uint32_t)(2 * q), c1 = c0 + 1;
+        const uint32_t o0 = (c0 ^ (uint32_t)(cidx & 7)) << 4, o1 = (c1 ^ (uint32_t)(cidx & 7)) << 4;
         st_shared_v4a(hi_row + o0, hv[0], hv[1], hv[2], hv[3]);
         st_shared_v4a(hi_row + o1, hv[4], hv[5], hv[6], hv[7]);
-        st_shared_v4a(hi_row + L::kATile + o0, lv[0], lv[1], lv[2], lv[3]);
-        st_shared_v4a(hi_row + L::kATile + o1, lv[4], lv[5], lv[6], lv[7]);
+        st_shared_v4a(hi_row + kTile + o0, lv[0], lv[1], lv[2], lv[3]);
+        st_shared_v4a(hi_row + kTile + o1, lv[4], lv[5], lv[6], lv[7]);
       }
       fence_proxy_async_smem();
-      mbar_arrive(&full[s]);
+      mbar_arrive_cluster(&ofull[s], 0);
     }
 
     // ---------------- epilogue: per-corner dot with A' ----------------
-    // warp w drains TMEM lanes 32 (w mod 4) .. of sub-tile w / 4: the thread
-    // of lane row holds Z[r, corner] for this tile's rows r
+    // warp w reads TMEM lanes 32 (w mod 4) .. +31 (its corners) over the
+    // columns of tile rows [128 g, 128 g + 128)
     const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(accfull, 0, st, 46) ? 1 : 0) != 0;
     tc_fence_after();
     const int32_t* cap = mat == 0 ? pl.vx : pl.vy;
     const uint32_t a = live ? (uint32_t)__ldg(cap + v) : 0u;
-    const float2 wa = f32_lookup<FULL>(tab, a & mask, logQ);
+    const float2 wa = tl_lookup(tl, a & mask);
+    const float fb = (float)b;
     const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
-    float outv = 0.f;
+    float outv = acc0;
     if (acc_ok) {
-      for (int cb = 0; cb < nmma; cb += 32) {   // 32 rows = 16 frequencies (or the k = 0 row)
+      for (int cb = 0; cb < kRH; cb += 32) {   // 32 rows = 16 frequencies
+        const int n0 = g * kRH + cb;           // tile row of the first column
         uint32_t d1[32], d2[32];
-        tmem_ld32(tmem + lane_base + (uint32_t)(sub * 2 * BNR + cb), d1);
-        tmem_ld32(tmem + lane_base + (uint32_t)(sub * 2 * BNR + BNR + cb), d2);
+        tmem_ld32(tmem + lane_base + (uint32_t)n0, d1);
+        tmem_ld32(tmem + lane_base + (uint32_t)(kAdjPairRows + n0), d2);
         tmem_wait_ld();
-        // rows r0 + cb + 2 i (cos) and + 1 (sin) of frequency k = (r0 + cb) / 2 + 1 + i
-        const int kb = (r0 + cb) / 2 + 1;
+        const int kb = (r0 + n0) / 2 + 1;      // rows n0 + 2 i (cos), + 1 (sin) of frequency kb + i
         float c = 0.f, sn = 0.f;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const int rr = cb + 2 * i;   // row within the tile
-          if (i % 8 == 0) {            // anchor of a run of 8 frequencies
-            const float2 an = f32_lookup<FULL>(tab, (uint32_t)(kb + i) * a & mask, logQ);
+          if (i % 8 == 0) {
+            const float2 an = tl_lookup(tl, (uint32_t)(kb + i) * a & mask);
             c = an.x;
             sn = an.y;
           }
-          const int rg = r0 + rr;      // global row
-          if (rr < nr) {
-            const float z0 = (__uint_as_float(d1[2 * i]) + __uint_as_float(d2[2 * i])) * rscale[rr];
-            const float av0 = rg < 2 * K ? c : 1.f;   // the last row is k = 0
-            outv = fmaf(av0, z0, outv);
-          }
-          if (rr + 1 < nr && rg + 1 < 2 * K) {
-            const float z1 = (__uint_as_float(d1[2 * i + 1]) + __uint_as_float(d2[2 * i + 1])) * rscale[rr + 1];
-            outv = fmaf(sn, z1, outv);
-          }
+          const float4 q0 = rows[n0 + 2 * i], q1 = rows[n0 + 2 * i + 1];
+          const float z0 =
+              fmaf(__uint_as_float(d1[2 * i]) + __uint_as_float(d2[2 * i]), q0.x, fmaf(q0.z, fb, q0.y));
+          const float z1 =
+              fmaf(__uint_as_float(d1[2 * i + 1]) + __uint_as_float(d2[2 * i + 1]), q1.x, fmaf(q1.z, fb, q1.y));
+          outv = fmaf(c, z0, outv);
+          outv = fmaf(sn, z1, outv);
           const float c1 = fmaf(c, wa.x, -(sn * wa.y)), s1 = fmaf(sn, wa.x, c * wa.y);
           c = c1;
           sn = s1;
         }
       }
     }
-    if (live) reinterpret_cast<float*>(ws + ar.off_part)[((size_t)mat * ar.rtiles + rt) * pl.V + v] = outv;
+    if (g == 1) comb[cidx] = outv;
+    asm volatile("bar.sync 1, %0;" ::"n"(kGen) : "memory");
+    if (g == 0 && live) {
+      float tot = outv + comb[cidx];
+      if (krow) tot += fmaf(m0[ar.kdim_pad + 1], fb, m0[ar.kdim_pad]);
+      reinterpret_cast<float*>(ws + ar.off_part)[((size_t)mat * ar.rtiles + rt) * pl.V + v] = tot;
+    }
   }
 
+  // the pair's MMAs, commits and arrivals reach both CTAs: neither releases
+  // its TMEM or leaves before both are done
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();
   if (warp == GW) {
-    __syncwarp();
+    __syncwarp();   // lane 0 ran the MMA loop alone; dealloc is warp-collective
     tc_fence_after();
-    tmem_dealloc(tmem, 4 * BNR);
+    tmem_dealloc_pair(tmem, 2 * kAdjPairRows);
   }
-}
-
-template <int BNR, bool FULL>
-cudaError_t launch_adj_tc_t(const AdjTcArgs& ar, const CUtensorMap& mhi, const CUtensorMap& mlo, void* ws,
-                            cudaStream_t st) {
-  using L = AdjTcLayout<BNR>;
-  const size_t smem = 1024 + L::kOps + align_up(tab_f32_bytes(ar.pl.T, FULL), 128) + BNR * 4 + 256;
-  auto kern = adj_tc_kernel<BNR, FULL>;
-  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), smem);
-  if (e != cudaSuccess) return e;
-  const dim3 grid((unsigned)((ar.pl.V + kVT - 1) / kVT), (unsigned)ar.rtiles, 2);
-  kern<<<grid, kThreadsA, smem, st>>>(mhi, mlo, ar, static_cast<uint8_t*>(ws));
-  count_launch(1);
-  return cudaGetLastError();
 }
 
 }  // namespace
 
-int adj_tc_rows_per_tile(int full) { return full ? 128 : 64; }
-
 cudaError_t launch_adj_tc(const AdjTcArgs& ar, const CUtensorMap& mhi, const CUtensorMap& mlo, void* ws,
                           cudaStream_t st) {
-  if (ar.pl.full) return launch_adj_tc_t<128, true>(ar, mhi, mlo, ws, st);
-  return launch_adj_tc_t<64, false>(ar, mhi, mlo, ws, st);
+  if (ar.pl.logT > 16) return cudaErrorInvalidValue;   // the two-level table holds T <= 2^16
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(adj_tc_kernel), kAdjSmem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * ((ar.pl.V + 2 * kVP - 1) / (2 * kVP))), (unsigned)ar.rtiles, 2);
+  cfg.blockDim = dim3(kThreadsA);
+  cfg.dynamicSmemBytes = kAdjSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, adj_tc_kernel, mhi, mlo, ar, static_cast<uint8_t*>(ws));
+  count_launch(1);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace fcfs

@@ -460,18 +460,20 @@ cudaError_t launch_gemm_simt(const Plan& pl, const int32_t* x, const int32_t* y,
 // per kernel, device and size (setting them costs a driver call per launch).
 cudaError_t ensure_smem(const void* fn, size_t bytes);
 
-// Tensor-core adjoint (fcfs_adjoint_tc.cu): the plan's vx/vy point at the corners
+// Tensor-core adjoint (fcfs_adjoint_tc.cu): the plan's vx/vy point at the corners.
+// The contraction covers the 2K frequency rows and 2K frequency columns of each
+// coefficient matrix; the k = 0 row and the columns 1 and b are FP32 side terms.
+constexpr int kAdjPairRows = 256;   // coefficient rows per CTA pair (MMA N)
 struct AdjTcArgs {
   Plan pl;
-  int nrows;        // 2K + 1 rows of each coefficient matrix (k=1 cos, k=1 sin, ..., k=0)
-  int nrows_pad;    // rows per matrix in the packed arrays (a multiple of the row tile)
-  int kdim_pad;     // packed columns (2K + 2 rounded up to 64)
-  int rtiles;       // row tiles
-  float inv_T;
-  size_t off_scale; // float [2][nrows]: power-of-two row scales
+  int nrows;        // 2K contraction rows of each matrix (k=1 cos, k=1 sin, ..., k=K sin)
+  int nrows_pad;    // rows per matrix in the packed arrays (a multiple of kAdjPairRows)
+  int kdim_pad;     // packed columns (2K rounded up to 64)
+  int rtiles;       // row tiles of kAdjPairRows
+  size_t off_rows;  // float4 [2][nrows_pad]: (row scale, column-1 term, column-b term, 0)
+  size_t off_m0;    // float [2][kdim_pad + 4]: the k = 0 row over the columns, then its 1 and b terms
   size_t off_part;  // float [2][rtiles][V]: per-row-tile partial derivatives
 };
-int adj_tc_rows_per_tile(int full);
 cudaError_t launch_adj_tc(const AdjTcArgs& ar, const CUtensorMap& mhi, const CUtensorMap& mlo, void* ws,
                           cudaStream_t st);
 // 2-D FP16 tensor map (cols innermost), 128-byte swizzle, box box_cols x box_rows
