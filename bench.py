@@ -51,7 +51,9 @@ def parse():
                     help="--only: one-CTA tiles instead of CTA pairs (profiling)")
     ap.add_argument("--no-fuse", action="store_true",
                     help="--only: separate axis and reduce kernels (profiling)")
-    ap.add_argument("--only", choices=["step", "large", "batch", "adjoint"], default=None,
+    ap.add_argument("--prec", choices=["split_f16", "fp32"], default="split_f16",
+                    help="--only adjoint / adjoint_large: contraction precision")
+    ap.add_argument("--only", choices=["step", "large", "batch", "adjoint", "adjoint_large"], default=None,
                     help="run one workload warmup + steps times and print its mean time "
                          "(for profiler command lines; not the benchmark line)")
     return ap.parse_args()
@@ -630,12 +632,13 @@ def run_only(args):
         fcfs.set_pair(0)
     if args.no_fuse:
         fcfs.set_fuse(0)
-    if args.only in ("step", "large", "adjoint"):
-        clip, K = config_clip({"step": 2, "large": 5, "adjoint": 4}[args.only])
+    if args.only in ("step", "large", "adjoint", "adjoint_large"):
+        clip, K = config_clip({"step": 2, "large": 5, "adjoint": 4, "adjoint_large": 5}[args.only])
         x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))
-        if args.only == "adjoint":
-            G = torch.ones((2 * K + 1, 2 * K + 1), dtype=torch.complex64, device=dev)
-            fn = lambda: fcfs.adjoint(x, y, s, clip.T, K, G)
+        if args.only.startswith("adjoint"):
+            gen = torch.Generator(device="cpu").manual_seed(7)
+            G = torch.randn((2 * K + 1, 2 * K + 1), dtype=torch.complex64, generator=gen).to(dev)
+            fn = lambda: fcfs.adjoint(x, y, s, clip.T, K, G, prec=args.prec)
         else:
             fn = lambda: fcfs.forward(x, y, s, clip.T, K, prec="split_f16")
     else:

@@ -24,6 +24,7 @@
 #include <math_constants.h>
 
 #include "fcfs_common.cuh"
+#include "fcfs_epilogue.cuh"
 
 namespace fcfs {
 
@@ -134,62 +135,71 @@ __global__ void adj_pack_kernel(AdjPlan ap, uint8_t* ws) {
 }
 
 // Coefficient matrices.  Block (row, matrix): matrix 0 serves gx (D), matrix 1
-// serves gy (D transposed).  FP64 for the folding, stored as FP32.
+// serves gy (D transposed).  With a_l = T / (2 pi l), H(k,l) = j a_l D(k,l) and
+// H(k,-l) = -j a_l D(k,-l), so Hp(k,l) = j a_l (D(k,l) - D(k,-l)) and
+// Hm(k,l) = a_l (D(k,l) + D(k,-l)); the folds over +-k are linear, so each
+// stored coefficient is a_l times a signed sum of four cotangent entries
+// (FP32).  The column-1 coefficient fold(C_k, C_-k) is minus the compensated
+// sum of the row's cos-column coefficients plus T fold(D(k,0), D(-k,0)), the
+// latter in FP64 (the k = 0 / l = 0 polynomial factor).
 __global__ void adj_coef_kernel(AdjPlan ap, const float2* __restrict__ dF, uint8_t* ws) {
   const int K = ap.p.K, W = 2 * K + 1;
   const int row = blockIdx.x, mat = blockIdx.y;
-  const double T = (double)ap.p.T;
   float* Mt = reinterpret_cast<float*>(ws + ap.off_m) + (size_t)mat * ap.cols * ap.rows_pad;
   const int k = (row + 1) / 2;
   const int kind = row == 0 ? 0 : (row & 1 ? 1 : 2);   // 0: k = 0, 1: cos row, 2: sin row
-  // D(k,l) of this matrix
-  auto D = [&](int kk, int ll) -> double2 {
+  // D(kk, ll) = conj(G) of this matrix
+  auto D = [&](int kk, int ll) -> float2 {
     const float2 g = mat == 0 ? dF[(size_t)(kk + K) * W + (ll + K)] : dF[(size_t)(ll + K) * W + (kk + K)];
-    return make_double2((double)g.x, -(double)g.y);
+    return make_float2(g.x, -g.y);
   };
-  // H(kk, l) = D(kk, l) * j T / (2 pi l)
-  auto H = [&](int kk, int ll) -> double2 {
-    const double2 d = D(kk, ll);
-    const double a = T / (2.0 * CUDART_PI * (double)ll);
-    return make_double2(-d.y * a, d.x * a);
-  };
-  auto fold = [&](double2 zk, double2 zmk) -> double {
-    return kind == 0 ? zk.x : (kind == 1 ? zk.x + zmk.x : zk.y - zmk.y);
-  };
-  __shared__ double red[2][2][kAdjThreads];   // partial sums of C_k and C_-k
-  double2 ck = make_double2(0, 0), cmk = make_double2(0, 0);
+  const float t2pi = (float)((double)ap.p.T / (2.0 * CUDART_PI));
+  CSum csum{0.f, 0.f};   // sum over l of the cos-column coefficients
   for (int l = 1 + threadIdx.x; l <= K; l += blockDim.x) {
-    const double2 hk = H(k, l), hkm = H(k, -l), hmk = H(-k, l), hmkm = H(-k, -l);
-    ck.x += hk.x + hkm.x;
-    ck.y += hk.y + hkm.y;
-    cmk.x += hmk.x + hmkm.x;
-    cmk.y += hmk.y + hmkm.y;
-    // Hp = H(k,l) + H(k,-l), Hm = -j (H(k,l) - H(k,-l)); same for -k
-    const double2 hp_k = make_double2(hk.x + hkm.x, hk.y + hkm.y);
-    const double2 hm_k = make_double2(hk.y - hkm.y, -(hk.x - hkm.x));
-    const double2 hp_mk = make_double2(hmk.x + hmkm.x, hmk.y + hmkm.y);
-    const double2 hm_mk = make_double2(hmk.y - hmkm.y, -(hmk.x - hmkm.x));
-    Mt[(size_t)(2 * (l - 1)) * ap.rows_pad + row] = (float)(-fold(hp_k, hp_mk));
-    Mt[(size_t)(2 * (l - 1) + 1) * ap.rows_pad + row] = (float)(-fold(hm_k, hm_mk));
+    const float a = t2pi / (float)l;
+    const float2 dkp = D(k, l), dkm = D(k, -l);
+    float vc, vs;   // coefficients of columns 2(l-1) (cos) and 2(l-1)+1 (sin)
+    if (kind == 0) {
+      vc = a * (dkp.y - dkm.y);
+      vs = -a * (dkp.x + dkm.x);
+    } else {
+      const float2 dmp = D(-k, l), dmm = D(-k, -l);
+      if (kind == 1) {
+        vc = a * ((dkp.y - dkm.y) + (dmp.y - dmm.y));
+        vs = -a * ((dkp.x + dkm.x) + (dmp.x + dmm.x));
+      } else {
+        vc = -a * ((dkp.x - dkm.x) - (dmp.x - dmm.x));
+        vs = -a * ((dkp.y + dkm.y) - (dmp.y + dmm.y));
+      }
+    }
+    Mt[(size_t)(2 * (l - 1)) * ap.rows_pad + row] = vc;
+    Mt[(size_t)(2 * (l - 1) + 1) * ap.rows_pad + row] = vs;
+    csum_add(csum, vc);
   }
-  red[0][0][threadIdx.x] = ck.x;
-  red[0][1][threadIdx.x] = ck.y;
-  red[1][0][threadIdx.x] = cmk.x;
-  red[1][1][threadIdx.x] = cmk.y;
+  // block sum of the (hi, lo) pairs in a fixed tree order
+  __shared__ float red[2][kAdjThreads / 32];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float h2 = __shfl_down_sync(0xffffffffu, csum.hi, o), l2 = __shfl_down_sync(0xffffffffu, csum.lo, o);
+    csum_add(csum, h2);
+    csum.lo += l2;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = csum.hi;
+    red[1][threadIdx.x >> 5] = csum.lo;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s4[4] = {0, 0, 0, 0};
-    for (int t = 0; t < (int)blockDim.x; ++t) {
-      s4[0] += red[0][0][t];
-      s4[1] += red[0][1][t];
-      s4[2] += red[1][0][t];
-      s4[3] += red[1][1][t];
+    CSum tot{0.f, 0.f};
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) {
+      csum_add(tot, red[0][w]);
+      tot.lo += red[1][w];
     }
-    const double2 dk0 = D(k, 0), dmk0 = D(-k, 0);
-    const double2 Ck = make_double2(s4[0] + T * dk0.x, s4[1] + T * dk0.y);
-    const double2 Cmk = make_double2(s4[2] + T * dmk0.x, s4[3] + T * dmk0.y);
-    Mt[(size_t)(2 * K) * ap.rows_pad + row] = (float)fold(Ck, Cmk);
-    Mt[(size_t)(2 * K + 1) * ap.rows_pad + row] = (float)(-fold(dk0, dmk0));
+    const float2 dk0 = D(k, 0), dmk0 = D(-k, 0);
+    const double f0 = kind == 0 ? (double)dk0.x
+                                : (kind == 1 ? (double)dk0.x + (double)dmk0.x : (double)dk0.y - (double)dmk0.y);
+    Mt[(size_t)(2 * K) * ap.rows_pad + row] = (float)(-((double)tot.hi + (double)tot.lo) + (double)ap.p.T * f0);
+    Mt[(size_t)(2 * K + 1) * ap.rows_pad + row] = (float)(-f0);
   }
   // padding rows of the last tile
   if (row == 0)

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kThreadsA, 1)
 
   if (tid == kGen + 32) {
     for (int i = 0; i < kStages; ++i) {
-      mbar_init(&ofull[i], 2 * kGen + 1);   // both CTAs' generator threads and rank 1's row forwarder
+      mbar_init(&ofull[i], 2 * (kGen / 32) + 1);   // both CTAs' generator warps and rank 1's row forwarder
       mbar_init(&tfull[i], 1);
       mbar_init(&empty[i], 1);
     }
@@ -206,7 +206,8 @@ __global__ void __launch_bounds__(kThreadsA, 1)
     for (int j = 0; j < nch; ++j) {
       const int s = j % kStages;
       const uint32_t ph = (uint32_t)(j / kStages) & 1u;
-      if (!mbar_wait(&empty[s], ph ^ 1u, st, 45)) break;
+      // warp-uniform: the warp's lanes arrive together below
+      if (!__all_sync(0xffffffffu, mbar_wait(&empty[s], ph ^ 1u, st, 45) ? 1 : 0)) break;
       const uint32_t hi_row = ops_a + s * kStage + (uint32_t)cidx * 128u;
 #pragma unroll
       for (int run = 0; run < 2; ++run) {
@@ -260,8 +261,11 @@ __global__ void __launch_bounds__(kThreadsA, 1)
         st_shared_v4a(hi_row + kTile + o0, lv[0], lv[1], lv[2], lv[3]);
         st_shared_v4a(hi_row + kTile + o1, lv[4], lv[5], lv[6], lv[7]);
       }
+      // every lane's writes are made visible to the tensor core's proxy, then
+      // one arrival per warp (release at cluster scope) on rank 0's barrier
       fence_proxy_async_smem();
-      mbar_arrive_cluster(&ofull[s], 0);
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(&ofull[s], 0);
     }
 
     // ---------------- epilogue: per-corner dot with A' ----------------
