@@ -214,6 +214,14 @@ void fcfs_debug_set_pair(int32_t on);
  * (fcfs_get_status) and an unwritten block, and the context stays usable.
  * 0 (the default) restores normal calls. */
 void fcfs_debug_set_barrier_extra(int32_t n);
+/* Row-binned contraction of single-clip split-FP16 calls on CTA pairs (the
+ * corners grouped by y, the off-axis block contracted over the T + 1 values of
+ * y instead of the V corners; the binning of Steps 2-3 carried into Step 4):
+ * mode 0 never, 1 (the default) when V >= 8 (T + 1), 2 whenever the call is
+ * eligible (split FP16, 2K >= 256, no device validation).  Same results within
+ * the split-FP16 error bound.  Must not change between fcfs_workspace_size and
+ * the call that uses the workspace. */
+void fcfs_debug_set_hybrid(int32_t mode);
 
 /* Vertex-split granularity of fcfs_batch: n pipeline chunks (64 corners on the
  * tensor path, 32 on the FP32 path) per unit; 0 restores the default of 4096

@@ -73,6 +73,7 @@ static int g_split_override = 0;   // testing/autotuning hook, 0 = automatic
 static int g_fuse = 1;             // testing hook: 0 keeps the axis and reduce kernels separate
 static int g_pair = 1;             // testing hook: 0 keeps single clips on one-CTA tiles
 static int g_barrier_extra = 0;    // testing hook: see fcfs_debug_set_barrier_extra
+static int g_hybrid = 1;           // 0: never group by y, 1: automatic, 2: whenever eligible
 
 // Tag of the cached tables: their kind, period, fixed-point scale and offsets.
 static uint64_t table_tag(const Plan& pl) {
@@ -153,6 +154,30 @@ fcfs_status make_plan_ex(int64_t V, int32_t T, int32_t K, int32_t prec, bool sin
 
 fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
   return make_plan_ex(V, T, K, prec, false, pl);
+}
+
+// Row-binned contraction (corners grouped by y, contraction over the T + 1
+// values of y): eligible for a single-clip split-FP16 call on CTA pairs; taken
+// automatically when the corners outnumber the y values 8 to 1.
+static bool hybrid_wanted(const Plan& pl, bool validate) {
+  if (g_hybrid == 0 || validate || !pl.pair || pl.prec != FCFS_PREC_SPLIT_F16 || pl.V <= 0 || pl.logT > 16)
+    return false;
+  return g_hybrid == 2 || pl.V >= 8LL * (pl.T + 1);
+}
+
+// Turn a single-clip pair plan into the row-binned one: splits over 64-y
+// chunks and the grouping, permutation and H regions after the partials.
+static void plan_hybrid(Plan& pl) {
+  pl.hyb = 1;
+  pl.ny_pad = (pl.T + 1 + 63) / 64 * 64;
+  const long long nchunks = pl.ny_pad / 64;
+  const int s = g_split_override > 0 ? (int)std::min<long long>(g_split_override, nchunks)
+                                     : choose_splits((long long)pl.tiles_m * pl.tiles_n, nchunks, sm_count(), 4);
+  const long long per = (nchunks + s - 1) / s;
+  pl.split_len = per * 64;
+  pl.splits = (int)((nchunks + per - 1) / per);
+  size_t o = align_up(pl.off_part + (size_t)pl.splits * pl.M2 * pl.M2 * sizeof(float), kWsAlign);
+  pl.total = hybrid_extra_bytes(pl.V, pl.T, pl.M2, pl.ny_pad, pl.off_ycnt, pl.off_perm, pl.off_h, o);
 }
 
 // ---------------------------------------------------------------------------
@@ -272,8 +297,9 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
   Plan pl;
   fcfs_status r = make_plan_ex(V, T, K, prec, true, pl);
   if (r != FCFS_OK) return r;
-  if ((r = check_ws(pl, ws, ws_bytes)) != FCFS_OK) return r;
   const bool validate = (flags & FCFS_FLAG_VALIDATE) != 0;
+  if (hybrid_wanted(pl, validate)) plan_hybrid(pl);
+  if ((r = check_ws(pl, ws, ws_bytes)) != FCFS_OK) return r;
   VertexMaps mp{};
   pl.vx = x;
   pl.vy = y;
@@ -283,10 +309,11 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
   prof_mark(1, st);
   // the contraction also bins the corners for the axis lines (Steps 2-3), so
   // the axis DFT follows it; device validation keeps its own binning pass
-  pl.bin_in_gemm = validate ? 0 : 1;
+  pl.bin_in_gemm = (validate || pl.hyb) ? 0 : 1;
   // one resident wave of tensor-core CTAs: they also sum the splits, take the
   // axis DFT and write the output behind a grid barrier (two launches per call)
-  const int cluster = (prec == FCFS_PREC_SPLIT_F16 && !validate && g_fuse && V > 0) ? gemm_tc_fuse_cluster(pl) : 0;
+  const int cluster =
+      (prec == FCFS_PREC_SPLIT_F16 && !validate && !pl.hyb && g_fuse && V > 0) ? gemm_tc_fuse_cluster(pl) : 0;
   if (cluster > 0 && make_part_map(pl, ws, pl.splits / cluster, &mp.part)) {
     pl.fused = 1;
     pl.cluster = cluster;
@@ -295,7 +322,9 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
     pl.area_out = reinterpret_cast<long long*>(area);
   }
   prof_mark(4, st);
-  if (prec == FCFS_PREC_SPLIT_F16)
+  if (pl.hyb)
+    FCFS_CU(launch_hybrid(pl, ws, st));
+  else if (prec == FCFS_PREC_SPLIT_F16)
     FCFS_CU(launch_gemm_tc(pl, mp, ws, st));
   else
     FCFS_CU(launch_gemm_simt(pl, x, y, s, ws, st));
@@ -340,7 +369,12 @@ uint64_t fcfs_launch_count(void) { return g_launches.load(); }
 size_t fcfs_workspace_size(int64_t V, int32_t T, int32_t K, int32_t prec) {
   Plan pl;
   if (make_plan_ex(V, T, K, prec, true, pl) != FCFS_OK) return 0;
-  return pl.total;
+  size_t total = pl.total;   // covers calls with device validation, which never group by y
+  if (hybrid_wanted(pl, false)) {
+    plan_hybrid(pl);
+    total = std::max(total, pl.total);
+  }
+  return total;
 }
 
 fcfs_status fcfs_forward(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, int32_t T, int32_t K,
@@ -363,6 +397,7 @@ void fcfs_debug_set_splits(int32_t s) { g_split_override = s; }
 void fcfs_debug_set_fuse(int32_t on) { g_fuse = on ? 1 : 0; }
 void fcfs_debug_set_pair(int32_t on) { g_pair = on ? 1 : 0; }
 void fcfs_debug_set_barrier_extra(int32_t n) { g_barrier_extra = n > 0 ? n : 0; }
+void fcfs_debug_set_hybrid(int32_t mode) { g_hybrid = mode < 0 ? 0 : (mode > 2 ? 2 : mode); }
 
 void fcfs_profile_enable(int32_t on) { g_prof = on != 0; }
 

@@ -54,6 +54,14 @@ struct Plan {
   int64_t unit_vertices;       // vertices per unit (a multiple of chunk)
   const int64_t* offsets;      // device, n_clips + 1
   size_t off_units;            // int32 unit_start[n_clips + 1] in the workspace
+  // row-binned contraction (single clip, many more corners than y values):
+  // the corners are grouped by y and the contraction runs over the T + 1 values
+  // of y; the splits then cut the y range (split_len counts y values)
+  int32_t hyb;
+  int32_t ny_pad;              // T + 1 rounded up to the chunk (64)
+  size_t off_ycnt;             // int32 [3][T + 2]: count, start offset and cursor per y
+  size_t off_perm;             // int32 [V]: corner indices grouped by y
+  size_t off_h;                // FP16 [2][M2][ny_pad]: H = sum over a y group of s A, hi then lo
 };
 
 // Bin one corner for the axis lines (Steps 2-3): bin_x[x] += s y, bin_y[y] += s x
@@ -476,6 +484,12 @@ struct AdjTcArgs {
 };
 cudaError_t launch_adj_tc(const AdjTcArgs& ar, const CUtensorMap& mhi, const CUtensorMap& mlo, void* ws,
                           cudaStream_t st);
+// Row-binned contraction (fcfs_hybrid.cu): grouping, H, and the contraction
+// over y into the plan's FP32 partial planes.
+cudaError_t launch_hybrid(const Plan& pl, void* ws, cudaStream_t st);
+// Workspace regions of the row-binned contraction placed from `base`; returns the end.
+size_t hybrid_extra_bytes(int64_t V, int T, int M2, int ny_pad, size_t& off_ycnt, size_t& off_perm, size_t& off_h,
+                          size_t base);
 // 2-D FP16 tensor map (cols innermost), 128-byte swizzle, box box_cols x box_rows
 bool encode_f16_2d_sw128(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_cols,
                          uint32_t box_rows);

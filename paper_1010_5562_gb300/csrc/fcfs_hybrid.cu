@@ -1,0 +1,541 @@
+// Row-binned contraction for clips with many more corners than y values.
+//
+// The quarter-plane product of the contraction (see fcfs_tc.cu),
+//   P[m, n] = sum_v s_v A[m, x_v] B[n, y_v],
+// regrouped by the corners' y -- the binning of Steps 2-3 applied to the
+// off-axis block, as in the sparse-image form of Step 4 --
+//   P[m, n] = sum_{y=0..T} H[m, y] B[n, y],   H[m, y] = sum_{v: y_v = y} s_v A[m, x_v],
+// contracts over the T + 1 values of y instead of the V corners.  Stages:
+//   1. group the corners by y: count per y, exclusive scan, scatter of the
+//      corner indices (the order inside a group is free: stage 2 is exact);
+//   2. H in 64-bit fixed point from the integer sincos table (the phase k x mod T
+//      read from the decimated quarter-wave levels, as in the axis DFT): exact
+//      integer sums, hence independent of the order; then FP32, scaled by a
+//      power of two 2^-e_y per y where a group is large (no FP16 overflow),
+//      and split into FP16 hi = rn(h), lo = rn(h - hi);
+//   3. the contraction on CTA pairs: H tiles by TMA, B generated on chip from
+//      the exact phase l y mod T (two-level sincos table, angle addition over
+//      runs of 8 frequencies) times 2^e_y, three split products into two TMEM
+//      accumulators, FP32 partial tiles per y split for the compensated split-K
+//      sum of the reduce kernel.
+#include <algorithm>
+
+#include "fcfs_epilogue.cuh"
+
+namespace fcfs {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Stage 1: group the corners by y
+// ---------------------------------------------------------------------------
+// int32 count[T + 2], start[T + 2], cursor[T + 2], then int8 e_y[ny_pad]
+struct YGroups {
+  int *cnt, *start, *cur;
+  int8_t* ey;
+};
+__host__ __device__ inline YGroups ygroups(const Plan& pl, uint8_t* ws) {
+  YGroups g;
+  g.cnt = reinterpret_cast<int*>(ws + pl.off_ycnt);
+  g.start = g.cnt + (pl.T + 2);
+  g.cur = g.start + (pl.T + 2);
+  g.ey = reinterpret_cast<int8_t*>(g.cur + (pl.T + 2));
+  return g;
+}
+__host__ __device__ inline size_t ygroups_bytes(int T, int ny_pad) { return (size_t)3 * (T + 2) * 4 + ny_pad; }
+
+__global__ void hyb_count_kernel(Plan pl, uint8_t* ws) {
+  const YGroups g = ygroups(pl, ws);
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < pl.V; v += (long long)gridDim.x * blockDim.x) {
+    const int y = __ldg(pl.vy + v);
+    if (y >= 0 && y <= pl.T) atomicAdd(&g.cnt[y], 1);
+  }
+}
+
+// One CTA: exclusive scan of the T + 1 counts into start (and the cursors),
+// start[T + 1] = the number of grouped corners; the per-y exponent
+// e_y = clamp(ceil(log2 count) - 14, 0, 15), so that |H[., y]| 2^-e_y <= 2^14.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) hyb_scan_kernel(Plan pl, uint8_t* ws) {
+  const YGroups g = ygroups(pl, ws);
+  const int n = pl.T + 1;
+  const int per = (n + kScanThreads - 1) / kScanThreads;
+  const int b = min(n, (int)threadIdx.x * per), e = min(n, b + per);
+  int sum = 0;
+  for (int i = b; i < e; ++i) sum += g.cnt[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  __shared__ int wsum[kScanThreads / 32];
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    wsum[lane] = w;   // inclusive over warps
+  }
+  __syncthreads();
+  int run = incl - sum + (warp > 0 ? wsum[warp - 1] : 0);
+  for (int i = b; i < e; ++i) {
+    g.start[i] = run;
+    g.cur[i] = run;
+    run += g.cnt[i];
+  }
+  if (threadIdx.x == kScanThreads - 1) g.start[n] = run;
+  for (int i = threadIdx.x; i < pl.ny_pad; i += kScanThreads) {
+    int ex = 0;
+    if (i < n && g.cnt[i] > (1 << 14)) {
+      int l = 0;
+      while ((1 << l) < g.cnt[i] && l < 31) ++l;
+      ex = min(15, l - 14);
+    }
+    g.ey[i] = (int8_t)ex;
+  }
+}
+
+__global__ void hyb_scatter_kernel(Plan pl, uint8_t* ws) {
+  const YGroups g = ygroups(pl, ws);
+  int* perm = reinterpret_cast<int*>(ws + pl.off_perm);
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < pl.V; v += (long long)gridDim.x * blockDim.x) {
+    const int y = __ldg(pl.vy + v);
+    if (y >= 0 && y <= pl.T) perm[atomicAdd(&g.cur[y], 1)] = (int)v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 2: H
+// ---------------------------------------------------------------------------
+constexpr int kHY = 64;          // y values per item (one contraction chunk)
+constexpr int kHF = 128;         // frequencies per pass (256 rows of H)
+constexpr int kHGroups = 4;      // thread groups; group q takes the item's y octets q, q + 4
+constexpr int kHThreads = kHF * kHGroups;
+constexpr int kHCache = 4096;    // corners of an item staged in shared memory
+
+size_t hyb_h_smem(int T) {
+  return align_up(axis_levels_ints(T) * 4, 16) + (size_t)kHCache * 8 + (kHY + 1) * 4 + 16;
+}
+
+// Persistent: CTA b takes items (64-y chunks) b, b + grid, ...; per item it
+// stages the grouped corners' (x mod T, s) in shared memory, then thread
+// (group q, frequency k) sums s_v (cos, sin)(2 pi k x_v / T) over each group of
+// its y octets for every frequency pass.
+__global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* ws) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  const int T = pl.T, K = pl.K, logQ = pl.logT - 2;
+  int* lv = reinterpret_cast<int*>(sm);
+  int2* vc = reinterpret_cast<int2*>(sm + align_up(axis_levels_ints(T) * 4, 16));
+  int* soff = reinterpret_cast<int*>(vc + kHCache);
+  const YGroups g = ygroups(pl, ws);
+  const int* perm = reinterpret_cast<const int*>(ws + pl.off_perm);
+  __half* Hhi = reinterpret_cast<__half*>(ws + pl.off_h);
+  __half* Hlo = Hhi + (size_t)pl.M2 * pl.ny_pad;
+  const uint32_t mask = (uint32_t)T - 1u;
+
+  // level 0 = the fixed-point quarter-wave table, then the decimated levels
+  const int* tq = reinterpret_cast<const int*>(ws + pl.off_tab_fix);
+  for (int i = threadIdx.x; i <= T / 4; i += blockDim.x) lv[i] = tq[i];
+  __syncthreads();
+  axis_build_levels(lv, T, pl.logT);
+
+  const int q = threadIdx.x / kHF, t = threadIdx.x % kHF;
+  const int nitems = pl.ny_pad / kHY;
+  const float inv_q = ldexpf(1.f, -pl.fixq);
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int y0 = item * kHY;
+    __syncthreads();   // the previous item's readers are done (and the levels are built)
+    const int a = g.start[min(y0, T + 1)], b = g.start[min(y0 + kHY, T + 1)];
+    const bool cached = b - a <= kHCache;
+    for (int i = threadIdx.x; i <= kHY; i += blockDim.x) soff[i] = g.start[min(y0 + i, T + 1)] - a;
+    if (cached)
+      for (int i = threadIdx.x; i < b - a; i += blockDim.x) {
+        const int v = perm[a + i];
+        vc[i] = make_int2((int)((uint32_t)__ldg(pl.vx + v) & mask), (int)__ldg(pl.vsg + v));
+      }
+    __syncthreads();
+    for (int k0 = 1; k0 <= K; k0 += kHF) {
+      const int k = k0 + t;
+      if (k > K) continue;
+      for (int oc = q; oc < kHY / 8; oc += kHGroups) {
+        uint32_t hc[4], hs[4], lc[4], ls[4];
+#pragma unroll
+        for (int yy = 0; yy < 8; ++yy) {
+          const int y = oc * 8 + yy;
+          long long ac = 0, as = 0, d0 = 0, d1 = 0;
+          for (int i = soff[y]; i < soff[y + 1]; ++i) {
+            int2 e;
+            if (cached) {
+              e = vc[i];
+            } else {
+              const int v = perm[a + i];
+              e = make_int2((int)((uint32_t)__ldg(pl.vx + v) & mask), (int)__ldg(pl.vsg + v));
+            }
+            axis_bin_add(lv, T, logQ, k, e.x, (long long)e.y, 0, ac, as, d0, d1);
+          }
+          const float sc = ldexpf(inv_q, -(int)g.ey[y0 + y]);
+          const float fc = __ll2float_rn(ac) * sc, fs = __ll2float_rn(as) * sc;
+          const __half c_hi = __float2half_rn(fc), s_hi = __float2half_rn(fs);
+          const __half c_lo = __float2half_rn(fc - __half2float(c_hi)), s_lo = __float2half_rn(fs - __half2float(s_hi));
+          uint16_t u;
+          const int sh = 16 * (yy & 1);
+          memcpy(&u, &c_hi, 2);
+          hc[yy >> 1] = (yy & 1 ? hc[yy >> 1] : 0u) | ((uint32_t)u << sh);
+          memcpy(&u, &s_hi, 2);
+          hs[yy >> 1] = (yy & 1 ? hs[yy >> 1] : 0u) | ((uint32_t)u << sh);
+          memcpy(&u, &c_lo, 2);
+          lc[yy >> 1] = (yy & 1 ? lc[yy >> 1] : 0u) | ((uint32_t)u << sh);
+          memcpy(&u, &s_lo, 2);
+          ls[yy >> 1] = (yy & 1 ? ls[yy >> 1] : 0u) | ((uint32_t)u << sh);
+        }
+        // rows 2(k-1) (cos) and 2(k-1)+1 (sin), columns y0 + 8 oc .. + 8
+        const size_t rc = (size_t)(2 * (k - 1)) * pl.ny_pad + y0 + 8 * oc, rs = rc + pl.ny_pad;
+        *reinterpret_cast<uint4*>(Hhi + rc) = make_uint4(hc[0], hc[1], hc[2], hc[3]);
+        *reinterpret_cast<uint4*>(Hhi + rs) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
+        *reinterpret_cast<uint4*>(Hlo + rc) = make_uint4(lc[0], lc[1], lc[2], lc[3]);
+        *reinterpret_cast<uint4*>(Hlo + rs) = make_uint4(ls[0], ls[1], ls[2], ls[3]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 3: the contraction over y on CTA pairs
+// ---------------------------------------------------------------------------
+constexpr int kGS = 3;                   // stages
+constexpr int kGGroup = 64;              // generator threads per chunk: 8 y octets x 8 runs of 8 frequencies
+constexpr int kGGen = kGS * kGGroup;     // group g fills the chunks of stage g
+constexpr int kGThreads = kGGen + 64;    // + MMA warp + TMA warp
+constexpr int kGTile = 128 * 128;        // one 128-row FP16 tile of a chunk (hi or lo), bytes
+constexpr int kGStage = 4 * kGTile;      // H hi, H lo (TMA), B hi, B lo (generated)
+constexpr int kGOps = kGS * kGStage;
+constexpr int kTlMax = 512;              // two-level table entries for T <= 2^16
+constexpr size_t kGSmem = 1024 + kGOps + kTlMax * 8 + 256;
+
+__device__ __forceinline__ void st_shared_v4h(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+__device__ __forceinline__ void ld_shared_v4h(uint32_t addr, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(a), "=r"(b), "=r"(c), "=r"(d) : "r"(addr) : "memory");
+}
+__device__ __forceinline__ void split2h(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(v0, v1);
+  const float2 hf = __half22float2(h);
+  memcpy(&hi, &h, 4);
+  const __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+  memcpy(&lo, &l, 4);
+}
+__device__ __forceinline__ void tma_load_2dh(void* dst, const CUtensorMap* map, int32_t c0, int32_t c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+// (cos, sin)(2 pi p / T) = coarse[p >> f] * fine[p mod 2^f] (correctly rounded FP32 factors)
+struct TwoLevelH {
+  const float2* t;
+  uint32_t f, fmask, nc;
+};
+__device__ __forceinline__ float2 tl_lookup_h(const TwoLevelH& tl, uint32_t p) {
+  const float2 c = tl.t[p >> tl.f], d = tl.t[tl.nc + (p & tl.fmask)];
+  return make_float2(fmaf(c.x, d.x, -(c.y * d.y)), fmaf(c.y, d.x, c.x * d.y));
+}
+
+// blockIdx.x = 2 (pair tile) + rank, blockIdx.y = y split.  Rank r holds H
+// rows [128 tm, 128 tm + 128) (tm = 2 (pair tile / tiles_n) + r) and the B
+// rows of frequencies l in tn 128 + 64 r + [1, 64].
+__global__ void __launch_bounds__(kGThreads, 1)
+    hyb_gemm_kernel(const __grid_constant__ CUtensorMap hhi, const __grid_constant__ CUtensorMap hlo, Plan pl,
+                    uint8_t* ws) {
+  constexpr int GW = kGGen / 32;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  uint8_t* ops = sm;
+  float2* tlt = reinterpret_cast<float2*>(sm + kGOps);
+  uint64_t* ofull = reinterpret_cast<uint64_t*>(tlt + kTlMax);   // [kGS] rank 0: chunk ready in both CTAs
+  uint64_t* tfull = ofull + kGS;                                 // [kGS] this CTA's H tiles landed
+  uint64_t* empty = tfull + kGS;                                 // [kGS] the chunk's MMAs completed
+  uint64_t* accfull = empty + kGS;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfull + 1);
+
+  Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t rank = cluster_ctarank();
+  const int ptile = blockIdx.x >> 1;
+  const int tm = 2 * (ptile / pl.tiles_n) + (int)rank, tn = ptile % pl.tiles_n;
+  const int y0 = blockIdx.y * (int)pl.split_len;
+  const int y1 = min(pl.ny_pad, y0 + (int)pl.split_len);
+  const int nch = max(0, (y1 - y0) / 64);
+
+  if (tid == kGGen + 32) {
+    for (int i = 0; i < kGS; ++i) {
+      mbar_init(&ofull[i], 2 * (kGGroup / 32) + 1);   // one group's warps in both CTAs, rank 1's forwarder
+      mbar_init(&tfull[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(accfull, 1);
+    fence_mbar_init();
+  }
+  if (warp == GW) {   // collective with the peer's MMA warp: D1 at 0, D2 at 256
+    tmem_alloc_pair(tmem_slot, 512);
+    tmem_relinquish_pair();
+  }
+  const uint32_t logT = (uint32_t)pl.logT, f = (logT + 1u) / 2u, nc = 1u << (logT - f);
+  const TwoLevelH tl{tlt, f, (1u << f) - 1u, nc};
+  if (tid < kGGen) {
+    const float* gt = reinterpret_cast<const float*>(ws + pl.off_tab_f32);
+    const uint32_t logQ = logT - 2u;
+    for (uint32_t i = tid; i < nc + (1u << f); i += kGGen) {
+      const uint32_t p = i < nc ? i << f : i - nc;
+      tlt[i] = pl.full ? f32_lookup<true>(gt, p, logQ) : f32_lookup<false>(gt, p, logQ);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == GW + 1) {
+    // ---------------- H tiles (TMA) ----------------
+    if (lane == 0) {
+      prefetch_tensormap(&hhi);
+      prefetch_tensormap(&hlo);
+      int j = 0;
+      for (; j < nch; ++j) {
+        const int s = j % kGS;
+        const uint32_t ph = (uint32_t)(j / kGS) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, st, 60)) break;
+        uint8_t* at = ops + (size_t)s * kGStage;
+        mbar_arrive_expect_tx(&tfull[s], 2u * kGTile);
+        // rows past 2K read as zeros
+        tma_load_2dh(at, &hhi, y0 + j * 64, tm * 128, &tfull[s]);
+        tma_load_2dh(at + kGTile, &hlo, y0 + j * 64, tm * 128, &tfull[s]);
+      }
+      for (int q = max(0, j - kGS); q < j; ++q) mbar_wait(&tfull[q % kGS], (uint32_t)(q / kGS) & 1u, st, 61);
+    }
+  } else if (warp == GW) {
+    if (lane == 0 && rank == 0) {
+      // ---------------- MMA issuer (rank 0 for the pair) ----------------
+      constexpr uint32_t idesc = idesc_f16_f32(256, 256);
+      const uint32_t ops_a = smem_u32(ops);
+      for (int j = 0; j < nch; ++j) {
+        const int s = j % kGS;
+        const uint32_t ph = (uint32_t)(j / kGS) & 1u;
+        if (!mbar_wait_cluster(&ofull[s], ph, st, 62) || !mbar_wait(&tfull[s], ph, st, 63)) break;
+        tc_fence_after();
+        const uint32_t ahi = ops_a + s * kGStage, alo = ahi + kGTile, bhi = alo + kGTile, blo = bhi + kGTile;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint32_t o = ks * 32;
+          const uint64_t dah = sdesc_sw128(ahi + o), dal = sdesc_sw128(alo + o);
+          const uint64_t dbh = sdesc_sw128(bhi + o), dbl = sdesc_sw128(blo + o);
+          tc_mma_f16_pair(tmem, dah, dbh, idesc, (j | ks) != 0);
+          tc_mma_f16_pair(tmem + 256, dah, dbl, idesc, (j | ks) != 0);
+          tc_mma_f16_pair(tmem + 256, dal, dbh, idesc, 1);
+        }
+        tc_commit_pair(&empty[s]);
+      }
+      tc_commit_pair(accfull);
+    } else if (lane == 0) {
+      // rank 1: each chunk's H tiles have landed here -> count it on rank 0's barrier
+      for (int j = 0; j < nch; ++j) {
+        const int s = j % kGS;
+        if (!mbar_wait(&tfull[s], (uint32_t)(j / kGS) & 1u, st, 64)) break;
+        mbar_arrive_cluster(&ofull[s], 0);
+      }
+    }
+  } else {
+    // ---------------- generators: B rows of this CTA ----------------
+    const int group = tid / kGGroup, gtid = tid % kGGroup;
+    const int oct = gtid & 7, run = gtid >> 3;
+    const int i0 = 8 * run;   // first row pair of the run in this CTA's B tile
+    const uint32_t f0 = (uint32_t)(tn * 128 + (int)rank * 64 + 1 + i0);
+    const uint32_t mask = (uint32_t)pl.T - 1u;
+    const uint32_t ops_a = smem_u32(ops);
+    const YGroups yg = ygroups(pl, ws);
+    uint32_t xo[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) xo[c] = (uint32_t)((oct ^ c) << 4);
+    for (int j = group; j < nch; j += kGS) {
+      const int s = j % kGS;
+      const uint32_t ph = (uint32_t)(j / kGS) & 1u;
+      const int yb = y0 + j * 64 + oct * 8;   // this thread's 8 consecutive y
+      const uint2 ex = __ldg(reinterpret_cast<const uint2*>(yg.ey + yb));
+      float c[8], sn[8], wc[8], wsn[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const uint32_t yv = (uint32_t)(yb + t);
+        const float2 an = tl_lookup_h(tl, (f0 * yv) & mask);
+        const float2 w = tl_lookup_h(tl, yv & mask);
+        const int e = (int)(int8_t)(((t < 4 ? ex.x : ex.y) >> (8 * (t & 3))) & 0xFFu);
+        const float sc = ldexpf(1.f, e);   // undoes H's 2^-e_y exactly
+        c[t] = an.x * sc;
+        sn[t] = an.y * sc;
+        wc[t] = w.x;
+        wsn[t] = w.y;
+      }
+      if (!__all_sync(0xffffffffu, mbar_wait(&empty[s], ph ^ 1u, st, 65) ? 1 : 0)) break;
+      const uint32_t tile_hi = ops_a + s * kGStage + 2u * kGTile + 256u * (uint32_t)i0;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        if (r) {
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const float ncs = fmaf(c[t], wc[t], -(sn[t] * wsn[t]));
+            const float nsn = fmaf(sn[t], wc[t], c[t] * wsn[t]);
+            c[t] = ncs;
+            sn[t] = nsn;
+          }
+        }
+        uint32_t ch[4], cl[4], sh[4], sl[4];
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          split2h(c[2 * qq], c[2 * qq + 1], ch[qq], cl[qq]);
+          split2h(sn[2 * qq], sn[2 * qq + 1], sh[qq], sl[qq]);
+        }
+        // cos row 2(i0 + r) and sin row 2(i0 + r) + 1 of the hi and lo tiles
+        const uint32_t rc = tile_hi + 256u * r + xo[(2 * r) & 7];
+        const uint32_t rs = tile_hi + 256u * r + 128u + xo[(2 * r + 1) & 7];
+        st_shared_v4h(rc, ch[0], ch[1], ch[2], ch[3]);
+        st_shared_v4h(rs, sh[0], sh[1], sh[2], sh[3]);
+        st_shared_v4h(rc + kGTile, cl[0], cl[1], cl[2], cl[3]);
+        st_shared_v4h(rs + kGTile, sl[0], sl[1], sl[2], sl[3]);
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(&ofull[s], 0);
+    }
+
+    // ---------------- epilogue: TMEM -> FP32 partial tile (warps 0-3) ----------------
+    // Warp w drains TMEM lanes 32 w .. (tile rows) over the 256 columns; each
+    // 32 x 32 block goes through a padded shared-memory transpose (row stride
+    // 36 floats) so that the global stores cover whole 128-byte rows.  The
+    // operand stages are free: the last MMA has completed.
+    if (warp < 4) {
+      const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(accfull, 0, st, 66) ? 1 : 0) != 0;
+      tc_fence_after();
+      const int M2 = pl.M2;
+      const int row0 = warp * 32;
+      const uint32_t tr = smem_u32(ops) + (uint32_t)warp * (32u * 36u * 4u);
+      float* P = reinterpret_cast<float*>(ws + pl.off_part) + (size_t)blockIdx.y * M2 * M2;
+#pragma unroll 1
+      for (int cb = 0; cb < 8; ++cb) {
+        const int n0 = tn * 256 + cb * 32;
+        if (n0 >= M2) break;   // warp-uniform
+        uint32_t r[32];
+        if (acc_ok && nch > 0) {
+          uint32_t r2[32];
+          tmem_ld32(tmem + ((uint32_t)row0 << 16) + (uint32_t)(cb * 32), r);
+          tmem_ld32(tmem + ((uint32_t)row0 << 16) + (uint32_t)(256 + cb * 32), r2);
+          tmem_wait_ld();
+#pragma unroll
+          for (int qq = 0; qq < 32; ++qq) r[qq] = __float_as_uint(__uint_as_float(r[qq]) + __uint_as_float(r2[qq]));
+        } else {
+#pragma unroll
+          for (int qq = 0; qq < 32; ++qq) r[qq] = 0u;
+        }
+#pragma unroll
+        for (int qq = 0; qq < 8; ++qq)
+          st_shared_v4h(tr + (uint32_t)(lane * 36 + 4 * qq) * 4u, r[4 * qq], r[4 * qq + 1], r[4 * qq + 2],
+                        r[4 * qq + 3]);
+        __syncwarp();
+        const int c4 = lane & 7;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int rr = 4 * i + (lane >> 3);
+          const int m = tm * 128 + row0 + rr, n = n0 + 4 * c4;
+          uint32_t v0, v1, v2, v3;
+          ld_shared_v4h(tr + (uint32_t)(rr * 36 + 4 * c4) * 4u, v0, v1, v2, v3);
+          if (m < M2 && n < M2) {
+            float* dst = P + (size_t)m * M2 + n;
+            if (n + 4 <= M2 && (M2 & 3) == 0) {   // 16-byte aligned rows only when 2K is a multiple of 4
+              *reinterpret_cast<float4*>(dst) =
+                  make_float4(__uint_as_float(v0), __uint_as_float(v1), __uint_as_float(v2), __uint_as_float(v3));
+            } else {
+              const uint32_t vv[4] = {v0, v1, v2, v3};
+              for (int t = 0; t < 4 && n + t < M2; ++t) dst[t] = __uint_as_float(vv[t]);
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  if (warp == GW) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc_pair(tmem, 512);
+  }
+}
+
+}  // namespace
+
+size_t hybrid_extra_bytes(int64_t V, int T, int M2, int ny_pad, size_t& off_ycnt, size_t& off_perm, size_t& off_h,
+                          size_t base) {
+  size_t o = base;
+  off_ycnt = o;
+  o = align_up(o + ygroups_bytes(T, ny_pad), kWsAlign);
+  off_perm = o;
+  o = align_up(o + (size_t)std::max<int64_t>(V, 1) * 4, kWsAlign);
+  off_h = o;
+  o = align_up(o + (size_t)2 * M2 * ny_pad * 2, kWsAlign);
+  return o;
+}
+
+cudaError_t launch_hybrid(const Plan& pl, void* ws_, cudaStream_t st) {
+  uint8_t* ws = static_cast<uint8_t*>(ws_);
+  if (!pl.hyb || !pl.pair || pl.logT > 16) return cudaErrorInvalidValue;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaMemsetAsync(ws + pl.off_ycnt, 0, (size_t)(pl.T + 2) * 4, st);
+  if (e != cudaSuccess) return e;
+  const int vblocks = (int)std::max<long long>(1, std::min<long long>((pl.V + 255) / 256, 8LL * sms));
+  hyb_count_kernel<<<vblocks, 256, 0, st>>>(pl, ws);
+  hyb_scan_kernel<<<1, kScanThreads, 0, st>>>(pl, ws);
+  hyb_scatter_kernel<<<vblocks, 256, 0, st>>>(pl, ws);
+  count_launch(3);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t hs = hyb_h_smem(pl.T);
+  if ((e = ensure_smem(reinterpret_cast<const void*>(hyb_h_kernel), hs)) != cudaSuccess) return e;
+  hyb_h_kernel<<<std::min(pl.ny_pad / kHY, sms), kHThreads, hs, st>>>(pl, ws);
+  count_launch(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+  const __half* h = reinterpret_cast<const __half*>(ws + pl.off_h);
+  CUtensorMap mhi, mlo;
+  if (!encode_f16_2d_sw128(&mhi, h, pl.ny_pad, pl.M2, 64, 128) ||
+      !encode_f16_2d_sw128(&mlo, h + (size_t)pl.M2 * pl.ny_pad, pl.ny_pad, pl.M2, 64, 128))
+    return cudaErrorInvalidValue;
+  if ((e = ensure_smem(reinterpret_cast<const void*>(hyb_gemm_kernel), kGSmem)) != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(pl.tiles_m * pl.tiles_n), (unsigned)pl.splits);
+  cfg.blockDim = dim3(kGThreads);
+  cfg.dynamicSmemBytes = kGSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, hyb_gemm_kernel, mhi, mlo, pl, ws);
+  count_launch(1);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+}  // namespace fcfs

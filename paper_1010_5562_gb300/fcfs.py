@@ -151,6 +151,12 @@ def set_barrier_extra(n):
     _lib.load().fcfs_debug_set_barrier_extra(int(n))
 
 
+def set_hybrid(mode):
+    """Row-binned contraction of single-clip split-FP16 calls (corners grouped
+    by y): 0 never, 1 automatic (V >= 8 (T + 1)), 2 whenever eligible."""
+    _lib.load().fcfs_debug_set_hybrid(int(mode))
+
+
 def set_batch_unit_chunks(n):
     """Vertex-split granularity of batch(): n pipeline chunks per unit (0: default)."""
     _lib.load().fcfs_set_batch_unit_chunks(int(n))
