@@ -29,20 +29,25 @@ namespace {
 // ---------------------------------------------------------------------------
 // Stage 1: group the corners by y
 // ---------------------------------------------------------------------------
-// int32 count[T + 2], start[T + 2], cursor[T + 2], then int8 e_y[ny_pad]
+// int32 count, start and cursor per y (each T + 2 entries padded to a multiple
+// of 4, so that the scan moves 16-byte vectors), then int8 e_y[ny_pad]
+__host__ __device__ inline int ygroups_stride(int T) { return (T + 2 + 3) & ~3; }
 struct YGroups {
   int *cnt, *start, *cur;
   int8_t* ey;
 };
 __host__ __device__ inline YGroups ygroups(const Plan& pl, uint8_t* ws) {
+  const int st = ygroups_stride(pl.T);
   YGroups g;
   g.cnt = reinterpret_cast<int*>(ws + pl.off_ycnt);
-  g.start = g.cnt + (pl.T + 2);
-  g.cur = g.start + (pl.T + 2);
-  g.ey = reinterpret_cast<int8_t*>(g.cur + (pl.T + 2));
+  g.start = g.cnt + st;
+  g.cur = g.start + st;
+  g.ey = reinterpret_cast<int8_t*>(g.cur + st);
   return g;
 }
-__host__ __device__ inline size_t ygroups_bytes(int T, int ny_pad) { return (size_t)3 * (T + 2) * 4 + ny_pad; }
+__host__ __device__ inline size_t ygroups_bytes(int T, int ny_pad) {
+  return (size_t)3 * ygroups_stride(T) * 4 + ny_pad;
+}
 
 __global__ void hyb_count_kernel(Plan pl, uint8_t* ws) {
   const YGroups g = ygroups(pl, ws);
@@ -53,43 +58,54 @@ __global__ void hyb_count_kernel(Plan pl, uint8_t* ws) {
 }
 
 // One CTA: exclusive scan of the T + 1 counts into start (and the cursors),
-// start[T + 1] = the number of grouped corners; the per-y exponent
-// e_y = clamp(ceil(log2 count) - 14, 0, 15), so that |H[., y]| 2^-e_y <= 2^14.
+// start[T + 1] = the number of grouped corners, in tiles of 4 entries per
+// thread; the per-y exponent e_y = clamp(ceil(log2 count) - 14, 0, 15), so
+// that |H[., y]| 2^-e_y <= 2^14.
 constexpr int kScanThreads = 1024;
 __global__ void __launch_bounds__(kScanThreads) hyb_scan_kernel(Plan pl, uint8_t* ws) {
   const YGroups g = ygroups(pl, ws);
   const int n = pl.T + 1;
-  const int per = (n + kScanThreads - 1) / kScanThreads;
-  const int b = min(n, (int)threadIdx.x * per), e = min(n, b + per);
-  int sum = 0;
-  for (int i = b; i < e; ++i) sum += g.cnt[i];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int incl = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
   __shared__ int wsum[kScanThreads / 32];
-  if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    int w = wsum[lane];
+  int carry = 0;
+  for (int base = 0; base < n; base += 4 * kScanThreads) {
+    const int i0 = base + 4 * (int)threadIdx.x;
+    int4 c = make_int4(0, 0, 0, 0);
+    if (i0 < n) {   // the vector stays inside the padded array
+      c = *reinterpret_cast<const int4*>(g.cnt + i0);
+      if (i0 + 1 >= n) c.y = 0;
+      if (i0 + 2 >= n) c.z = 0;
+      if (i0 + 3 >= n) c.w = 0;
+    }
+    const int tsum = c.x + c.y + c.z + c.w;
+    int incl = tsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += t;
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
     }
-    wsum[lane] = w;   // inclusive over warps
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      int w = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += t;
+      }
+      wsum[lane] = w;   // inclusive over warps
+    }
+    __syncthreads();
+    if (i0 < n) {
+      const int e0 = carry + (warp > 0 ? wsum[warp - 1] : 0) + incl - tsum;
+      const int4 st4 = make_int4(e0, e0 + c.x, e0 + c.x + c.y, e0 + c.x + c.y + c.z);
+      *reinterpret_cast<int4*>(g.start + i0) = st4;
+      *reinterpret_cast<int4*>(g.cur + i0) = st4;
+    }
+    carry += wsum[kScanThreads / 32 - 1];
+    __syncthreads();   // wsum is reused by the next tile
   }
-  __syncthreads();
-  int run = incl - sum + (warp > 0 ? wsum[warp - 1] : 0);
-  for (int i = b; i < e; ++i) {
-    g.start[i] = run;
-    g.cur[i] = run;
-    run += g.cnt[i];
-  }
-  if (threadIdx.x == kScanThreads - 1) g.start[n] = run;
+  if (threadIdx.x == 0) g.start[n] = carry;
   for (int i = threadIdx.x; i < pl.ny_pad; i += kScanThreads) {
     int ex = 0;
     if (i < n && g.cnt[i] > (1 << 14)) {
@@ -113,25 +129,40 @@ __global__ void hyb_scatter_kernel(Plan pl, uint8_t* ws) {
 // ---------------------------------------------------------------------------
 // Stage 2: H
 // ---------------------------------------------------------------------------
-constexpr int kHY = 64;          // y values per item (one contraction chunk)
+constexpr int kHY = 64;          // y values per chunk (one contraction chunk)
 constexpr int kHF = 128;         // frequencies per pass (256 rows of H)
-constexpr int kHGroups = 4;      // thread groups; group q takes the item's y octets q, q + 4
+constexpr int kHGroups = 4;      // thread groups; group q takes the chunk's y octets q, q + 4
 constexpr int kHThreads = kHF * kHGroups;
-constexpr int kHCache = 4096;    // corners of an item staged in shared memory
+constexpr int kHCache = 4096;    // corners of a chunk staged in shared memory
 
 size_t hyb_h_smem(int T) {
-  return align_up(axis_levels_ints(T) * 4, 16) + (size_t)kHCache * 8 + (kHY + 1) * 4 + 16;
+  return align_up(axis_levels_ints(T) * 4, 16) + (size_t)kHCache * 16 + (kHY + 1) * 4 + 16;
 }
 
-// Persistent: CTA b takes items (64-y chunks) b, b + grid, ...; per item it
-// stages the grouped corners' (x mod T, s) in shared memory, then thread
-// (group q, frequency k) sums s_v (cos, sin)(2 pi k x_v / T) over each group of
-// its y octets for every frequency pass.
+// A staged corner: the phase k x mod T of every frequency k is read at index
+// k u (mod 4 Q) of the decimated level that starts at lbase (quarter period
+// Q = 2^lq; u odd unless x mod T is a multiple of T/4), which keeps the 32
+// consecutive frequencies of a warp on distinct banks; sflip = 1 for s = -1.
+__device__ __forceinline__ int4 stage_corner(uint32_t xm, int sgn, int logQ) {
+  int e = xm ? __ffs(xm) - 1 : 0;
+  uint32_t u = xm >> e;
+  if (e > logQ - 1) {   // x a multiple of T/4 (or 0): level 0 reads at most 4 entries
+    e = 0;
+    u = xm;
+  }
+  const int lq = logQ - e;
+  return make_int4((int)u, level_offset(e, logQ), lq | ((sgn < 0 ? 1 : 0) << 8), 1 << lq);
+}
+
+// Units (64-y chunk, pass of 128 frequencies) in chunk-major order; CTA b takes
+// the contiguous range [b U / G, (b + 1) U / G), so a chunk's corners are
+// staged once for all its passes.  Thread (group q, frequency k) sums
+// s_v (cos, sin)(2 pi k x_v / T) over each group of its y octets, exactly.
 __global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* ws) {
   extern __shared__ __align__(16) uint8_t sm[];
   const int T = pl.T, K = pl.K, logQ = pl.logT - 2;
   int* lv = reinterpret_cast<int*>(sm);
-  int2* vc = reinterpret_cast<int2*>(sm + align_up(axis_levels_ints(T) * 4, 16));
+  int4* vc = reinterpret_cast<int4*>(sm + align_up(axis_levels_ints(T) * 4, 16));
   int* soff = reinterpret_cast<int*>(vc + kHCache);
   const YGroups g = ygroups(pl, ws);
   const int* perm = reinterpret_cast<const int*>(ws + pl.off_perm);
@@ -146,61 +177,76 @@ __global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* w
   axis_build_levels(lv, T, pl.logT);
 
   const int q = threadIdx.x / kHF, t = threadIdx.x % kHF;
-  const int nitems = pl.ny_pad / kHY;
+  const int npass = (K + kHF - 1) / kHF;
+  const long long units = (long long)(pl.ny_pad / kHY) * npass;
+  const int u0 = (int)(units * blockIdx.x / gridDim.x), u1 = (int)(units * (blockIdx.x + 1) / gridDim.x);
   const float inv_q = ldexpf(1.f, -pl.fixq);
-  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int y0 = item * kHY;
-    __syncthreads();   // the previous item's readers are done (and the levels are built)
-    const int a = g.start[min(y0, T + 1)], b = g.start[min(y0 + kHY, T + 1)];
-    const bool cached = b - a <= kHCache;
-    for (int i = threadIdx.x; i <= kHY; i += blockDim.x) soff[i] = g.start[min(y0 + i, T + 1)] - a;
-    if (cached)
-      for (int i = threadIdx.x; i < b - a; i += blockDim.x) {
-        const int v = perm[a + i];
-        vc[i] = make_int2((int)((uint32_t)__ldg(pl.vx + v) & mask), (int)__ldg(pl.vsg + v));
-      }
-    __syncthreads();
-    for (int k0 = 1; k0 <= K; k0 += kHF) {
-      const int k = k0 + t;
-      if (k > K) continue;
-      for (int oc = q; oc < kHY / 8; oc += kHGroups) {
-        uint32_t hc[4], hs[4], lc[4], ls[4];
-#pragma unroll
-        for (int yy = 0; yy < 8; ++yy) {
-          const int y = oc * 8 + yy;
-          long long ac = 0, as = 0, d0 = 0, d1 = 0;
-          for (int i = soff[y]; i < soff[y + 1]; ++i) {
-            int2 e;
-            if (cached) {
-              e = vc[i];
-            } else {
-              const int v = perm[a + i];
-              e = make_int2((int)((uint32_t)__ldg(pl.vx + v) & mask), (int)__ldg(pl.vsg + v));
-            }
-            axis_bin_add(lv, T, logQ, k, e.x, (long long)e.y, 0, ac, as, d0, d1);
-          }
-          const float sc = ldexpf(inv_q, -(int)g.ey[y0 + y]);
-          const float fc = __ll2float_rn(ac) * sc, fs = __ll2float_rn(as) * sc;
-          const __half c_hi = __float2half_rn(fc), s_hi = __float2half_rn(fs);
-          const __half c_lo = __float2half_rn(fc - __half2float(c_hi)), s_lo = __float2half_rn(fs - __half2float(s_hi));
-          uint16_t u;
-          const int sh = 16 * (yy & 1);
-          memcpy(&u, &c_hi, 2);
-          hc[yy >> 1] = (yy & 1 ? hc[yy >> 1] : 0u) | ((uint32_t)u << sh);
-          memcpy(&u, &s_hi, 2);
-          hs[yy >> 1] = (yy & 1 ? hs[yy >> 1] : 0u) | ((uint32_t)u << sh);
-          memcpy(&u, &c_lo, 2);
-          lc[yy >> 1] = (yy & 1 ? lc[yy >> 1] : 0u) | ((uint32_t)u << sh);
-          memcpy(&u, &s_lo, 2);
-          ls[yy >> 1] = (yy & 1 ? ls[yy >> 1] : 0u) | ((uint32_t)u << sh);
+  int staged = -1, a = 0;
+  bool cached = false;
+  for (int unit = u0; unit < u1; ++unit) {
+    const int chunk = unit / npass, k = (unit % npass) * kHF + 1 + t;
+    const int y0 = chunk * kHY;
+    if (chunk != staged) {   // CTA-uniform
+      __syncthreads();       // the previous chunk's readers are done (and the levels are built)
+      a = g.start[min(y0, T + 1)];
+      const int b = g.start[min(y0 + kHY, T + 1)];
+      cached = b - a <= kHCache;
+      for (int i = threadIdx.x; i <= kHY; i += blockDim.x) soff[i] = g.start[min(y0 + i, T + 1)] - a;
+      if (cached)
+        for (int i = threadIdx.x; i < b - a; i += blockDim.x) {
+          const int v = perm[a + i];
+          vc[i] = stage_corner((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
         }
-        // rows 2(k-1) (cos) and 2(k-1)+1 (sin), columns y0 + 8 oc .. + 8
-        const size_t rc = (size_t)(2 * (k - 1)) * pl.ny_pad + y0 + 8 * oc, rs = rc + pl.ny_pad;
-        *reinterpret_cast<uint4*>(Hhi + rc) = make_uint4(hc[0], hc[1], hc[2], hc[3]);
-        *reinterpret_cast<uint4*>(Hhi + rs) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
-        *reinterpret_cast<uint4*>(Hlo + rc) = make_uint4(lc[0], lc[1], lc[2], lc[3]);
-        *reinterpret_cast<uint4*>(Hlo + rs) = make_uint4(ls[0], ls[1], ls[2], ls[3]);
+      __syncthreads();
+      staged = chunk;
+    }
+    if (k > K) continue;
+    for (int oc = q; oc < kHY / 8; oc += kHGroups) {
+      uint32_t hc[4], hs[4], lc[4], ls[4];
+#pragma unroll
+      for (int yy = 0; yy < 8; ++yy) {
+        const int y = oc * 8 + yy;
+        long long ac = 0, as = 0;
+        for (int i = soff[y]; i < soff[y + 1]; ++i) {
+          int4 cn;
+          if (cached) {
+            cn = vc[i];
+          } else {
+            const int v = perm[a + i];
+            cn = stage_corner((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
+          }
+          const int lq = cn.z & 0xFF, Q = cn.w;
+          const uint32_t sf = (uint32_t)cn.z >> 8;
+          const uint32_t p = ((uint32_t)k * (uint32_t)cn.x) & (4u * (uint32_t)Q - 1u);
+          const uint32_t qd = p >> lq, r = p & (uint32_t)(Q - 1);
+          const bool odd = qd & 1u;
+          const int* L = lv + cn.y;
+          const int c = L[odd ? Q - r : r], sn = L[odd ? r : Q - r];
+          // cos < 0 in quadrants 1, 2; sin < 0 in quadrants 2, 3; s = -1 flips both
+          ac += ((((qd + 1u) >> 1) & 1u) ^ sf) ? -c : c;
+          as += ((qd >> 1) ^ sf) ? -sn : sn;
+        }
+        const float sc = ldexpf(inv_q, -(int)g.ey[y0 + y]);
+        const float fc = __ll2float_rn(ac) * sc, fs = __ll2float_rn(as) * sc;
+        const __half c_hi = __float2half_rn(fc), s_hi = __float2half_rn(fs);
+        const __half c_lo = __float2half_rn(fc - __half2float(c_hi)), s_lo = __float2half_rn(fs - __half2float(s_hi));
+        uint16_t u;
+        const int sh = 16 * (yy & 1);
+        memcpy(&u, &c_hi, 2);
+        hc[yy >> 1] = (yy & 1 ? hc[yy >> 1] : 0u) | ((uint32_t)u << sh);
+        memcpy(&u, &s_hi, 2);
+        hs[yy >> 1] = (yy & 1 ? hs[yy >> 1] : 0u) | ((uint32_t)u << sh);
+        memcpy(&u, &c_lo, 2);
+        lc[yy >> 1] = (yy & 1 ? lc[yy >> 1] : 0u) | ((uint32_t)u << sh);
+        memcpy(&u, &s_lo, 2);
+        ls[yy >> 1] = (yy & 1 ? ls[yy >> 1] : 0u) | ((uint32_t)u << sh);
       }
+      // rows 2(k-1) (cos) and 2(k-1)+1 (sin), columns y0 + 8 oc .. + 8
+      const size_t rc = (size_t)(2 * (k - 1)) * pl.ny_pad + y0 + 8 * oc, rs = rc + pl.ny_pad;
+      *reinterpret_cast<uint4*>(Hhi + rc) = make_uint4(hc[0], hc[1], hc[2], hc[3]);
+      *reinterpret_cast<uint4*>(Hhi + rs) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
+      *reinterpret_cast<uint4*>(Hlo + rc) = make_uint4(lc[0], lc[1], lc[2], lc[3]);
+      *reinterpret_cast<uint4*>(Hlo + rs) = make_uint4(ls[0], ls[1], ls[2], ls[3]);
     }
   }
 }
@@ -501,7 +547,7 @@ cudaError_t launch_hybrid(const Plan& pl, void* ws_, cudaStream_t st) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaMemsetAsync(ws + pl.off_ycnt, 0, (size_t)(pl.T + 2) * 4, st);
+  cudaError_t e = cudaMemsetAsync(ws + pl.off_ycnt, 0, (size_t)ygroups_stride(pl.T) * 4, st);
   if (e != cudaSuccess) return e;
   const int vblocks = (int)std::max<long long>(1, std::min<long long>((pl.V + 255) / 256, 8LL * sms));
   hyb_count_kernel<<<vblocks, 256, 0, st>>>(pl, ws);
@@ -511,7 +557,8 @@ cudaError_t launch_hybrid(const Plan& pl, void* ws_, cudaStream_t st) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t hs = hyb_h_smem(pl.T);
   if ((e = ensure_smem(reinterpret_cast<const void*>(hyb_h_kernel), hs)) != cudaSuccess) return e;
-  hyb_h_kernel<<<std::min(pl.ny_pad / kHY, sms), kHThreads, hs, st>>>(pl, ws);
+  const long long hunits = (long long)(pl.ny_pad / kHY) * ((pl.K + kHF - 1) / kHF);
+  hyb_h_kernel<<<(int)std::min<long long>(hunits, sms), kHThreads, hs, st>>>(pl, ws);
   count_launch(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
