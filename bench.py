@@ -545,6 +545,19 @@ def run_extras(fcfs, dev, flush, stream, args):
         ms5 = _timed_ms(torch, lambda: fcfs.forward(x5, y5, s5, clip5.T, K5, prec=prec, out=F5, area_out=A5,
                                                     workspace=ws5, stream=stream), 3, flush, stream)
         big[prec] = {"value": clip5.V * W5 * W5 / (ms5 * 1e-3), "ms": ms5, "_F": F5, "_A": A5}
+    big["split_f16"]["contraction"] = "corners grouped by y: T+1 contraction columns instead of V corners"
+    # the direct contraction over the V corners on the same clip, for comparison
+    fcfs.set_hybrid(0)
+    try:
+        F5d = torch.empty((W5, W5), dtype=torch.complex64, device=dev)
+        A5d = torch.empty(1, dtype=torch.int64, device=dev)
+        ws5d = torch.empty(fcfs.workspace_size(clip5.V, clip5.T, K5, "split_f16"), dtype=torch.uint8, device=dev)
+        ms5d = _timed_ms(torch, lambda: fcfs.forward(x5, y5, s5, clip5.T, K5, prec="split_f16", out=F5d,
+                                                     area_out=A5d, workspace=ws5d, stream=stream), 3, flush, stream)
+    finally:
+        fcfs.set_hybrid(1)
+    big["split_f16_direct"] = {"value": clip5.V * W5 * W5 / (ms5d * 1e-3), "ms": ms5d,
+                               "contraction": "over the V corners (CTA pairs)"}
     # adjoint of the large clip (FP32), seeded random cotangent over the full block
     rng = np.random.default_rng(5)
     G5 = torch.from_numpy((rng.standard_normal((W5, W5)) + 1j * rng.standard_normal((W5, W5)))
@@ -567,7 +580,8 @@ def run_extras(fcfs, dev, flush, stream, args):
     big["adjoint_split_f16"] = {"value": clip5.V * W5 * W5 / (ms_a5h * 1e-3), "ms": ms_a5h,
                                 "cotangent": "as adjoint_fp32", "_g": (gx5h, gy5h)}
     out["large"] = {"workload": "clip T=65536, 150000 polygons, V=%d, K=1024 (2049x2049)" % clip5.V,
-                    "unit": UNIT, "split_f16": big["split_f16"], "fp32": big["fp32"],
+                    "unit": UNIT, "split_f16": big["split_f16"], "split_f16_direct": big["split_f16_direct"],
+                    "fp32": big["fp32"],
                     "adjoint_split_f16": big["adjoint_split_f16"], "adjoint_fp32": big["adjoint_fp32"],
                     "_check": (clip5, K5)}
     return out
