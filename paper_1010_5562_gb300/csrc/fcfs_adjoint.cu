@@ -25,6 +25,7 @@
 
 #include "fcfs_common.cuh"
 #include "fcfs_epilogue.cuh"
+#include "fcfs_group.cuh"
 
 namespace fcfs {
 
@@ -43,6 +44,9 @@ struct AdjPlan {
   // hi / lo [hi|lo][matrix][nrows_pad][kdim_pad], its row terms and the k = 0 row
   int tc, nrows_pad, kdim_pad;
   size_t off_mp, off_rows, off_m0;
+  // grouped tensor-core contraction: the corners grouped by y and by x
+  int grouped, ny_pad;
+  size_t off_groups;
 };
 constexpr int kAdjThreads = 128;
 constexpr size_t kAdjSmemBudget = 200 * 1024;
@@ -51,6 +55,9 @@ static fcfs_status make_adj_plan(int64_t V, int32_t T, int32_t K, int32_t prec, 
   fcfs_status r = make_plan(V, T, K, FCFS_PREC_FP32, ap.p);
   if (r != FCFS_OK) return r;
   ap.tc = prec == FCFS_PREC_SPLIT_F16 ? 1 : 0;
+  ap.grouped = 0;
+  ap.ny_pad = 0;
+  ap.off_groups = 0;
   ap.rows = 2 * K + 1;
   ap.cols = 2 * K + 2;
   const size_t tab = align_up(tab_f32_bytes(T, ap.p.full), 128);
@@ -76,6 +83,20 @@ static fcfs_status make_adj_plan(int64_t V, int32_t T, int32_t K, int32_t prec, 
     o = align_up(o + (size_t)2 * ap.nrows_pad * sizeof(float4), kWsAlign);
     ap.off_m0 = o;
     o = align_up(o + (size_t)2 * (ap.kdim_pad + 4) * sizeof(float), kWsAlign);
+    // many more corners than coordinate values: the MMA runs over the T + 1
+    // values of b and the epilogue over the corners grouped by b -- taken
+    // automatically when that still fills the GPU with a wave of CTAs (the
+    // epilogue of a CTA then takes all corners of its 128 values of b)
+    const int mode = hybrid_mode();
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long gctas = 2LL * 2 * ap.row_tiles * ((T + 1 + kAdjPairRows - 1) / kAdjPairRows);
+    ap.grouped = V > 0 && (mode == 2 || (mode == 1 && V >= 8LL * (T + 1) && gctas >= sms)) ? 1 : 0;
+    ap.ny_pad = (T + 1 + 63) / 64 * 64;
+    if (ap.grouped) {
+      ap.off_groups = o;
+      o = align_up(o + 2 * group_bytes(V, T, ap.ny_pad), kWsAlign);
+    }
   }
   ap.off_part = o;
   o = align_up(o + (size_t)2 * ap.row_tiles * V * sizeof(float), kWsAlign);
@@ -384,6 +405,13 @@ static fcfs_status adjoint_impl(const int32_t* x, const int32_t* y, const int8_t
     ar.off_rows = ap.off_rows;
     ar.off_m0 = ap.off_m0;
     ar.off_part = ap.off_part;
+    ar.grouped = ap.grouped;
+    ar.ny_pad = ap.ny_pad;
+    ar.off_groups = ap.off_groups;
+    // gx contracts over y, gy over x: group the corners by y and by x
+    if (ap.grouped &&
+        launch_grouping(y, x, V, T, ap.ny_pad, static_cast<uint8_t*>(ws) + ap.off_groups, st) != cudaSuccess)
+      return FCFS_ECUDA;
     if (launch_adj_tc(ar, mhi, mlo, ws, st) != cudaSuccess) return FCFS_ECUDA;
   } else {
     const cudaError_t e =

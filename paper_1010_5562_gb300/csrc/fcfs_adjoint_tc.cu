@@ -24,9 +24,18 @@
 // The side terms stay FP32: the generator threads of row tile 0 accumulate the
 // k = 0 row from the B' values they generate, and the epilogue adds s1 + sb b
 // to each row before the per-corner dot with A'.
+//
+// Grouped form (many more corners than values of b): B' depends on the corner
+// only through b, so the MMA's M dimension runs over the T + 1 values of b
+// instead of the V corners (Z[r, b] for every b), and the epilogue takes the
+// corners of the CTA's 128 values of b (grouped by b, fcfs_group.cuh): Z goes
+// from TMEM to shared memory (row scale and side terms applied), then each
+// thread forms the dot of one corner at a time with its A' over the tile's 256
+// rows.
 #include <algorithm>
 
 #include "fcfs_common.cuh"
+#include "fcfs_group.cuh"
 
 namespace fcfs {
 
@@ -42,7 +51,11 @@ constexpr int kStage = 4 * kTile;         // corners hi, lo (generated), coeffic
 constexpr int kStages = 3;
 constexpr int kOps = kStages * kStage;
 constexpr int kTlMax = 512;               // two-level table entries for T <= 2^16
-constexpr size_t kAdjSmem = 1024 + kOps + kTlMax * 8 + kAdjPairRows * 16 + kVP * 4 + 256;
+constexpr size_t kAdjSmem = 1024 + kOps + kTlMax * 8 + kAdjPairRows * 16 + 2 * kVP * 4 + 256;
+// grouped epilogue: Z [256 rows][128 b] FP32 and staged corners in the operand stages
+constexpr int kZBytes = kAdjPairRows * kVP * 4;
+constexpr int kCornerCache = (kOps - kZBytes) / 16;
+static_assert(kCornerCache >= 1024, "room for staged corners");
 
 __device__ __forceinline__ void st_shared_v4a(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
@@ -77,6 +90,7 @@ __device__ __forceinline__ float2 tl_lookup(const TwoLevel& tl, uint32_t p) {
   return make_float2(fmaf(c.x, d.x, -(c.y * d.y)), fmaf(c.y, d.x, c.x * d.y));
 }
 
+template <bool GROUPED>
 __global__ void __launch_bounds__(kThreadsA, 1)
     adj_tc_kernel(const __grid_constant__ CUtensorMap mhi, const __grid_constant__ CUtensorMap mlo, AdjTcArgs ar,
                   uint8_t* ws) {
@@ -88,8 +102,8 @@ __global__ void __launch_bounds__(kThreadsA, 1)
   uint8_t* ops = sm;
   float2* tlt = reinterpret_cast<float2*>(sm + kOps);
   float4* rows = reinterpret_cast<float4*>(tlt + kTlMax);        // this pair's 256 row terms
-  float* comb = reinterpret_cast<float*>(rows + kAdjPairRows);   // second column half of each corner
-  uint64_t* ofull = reinterpret_cast<uint64_t*>(comb + kVP);     // [kStages] rank 0: chunk ready in both CTAs
+  float* comb = reinterpret_cast<float*>(rows + kAdjPairRows);   // [2][kVP]: column halves of each corner
+  uint64_t* ofull = reinterpret_cast<uint64_t*>(comb + 2 * kVP); // [kStages] rank 0: chunk ready in both CTAs
   uint64_t* tfull = ofull + kStages;                             // [kStages] this CTA's rows landed
   uint64_t* empty = tfull + kStages;                             // [kStages] the chunk's MMAs completed
   uint64_t* accfull = empty + kStages;
@@ -98,7 +112,8 @@ __global__ void __launch_bounds__(kThreadsA, 1)
   Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // blockIdx.x = 2 (corner pair tile) + rank; rank r holds corners [128 r, 128 r + 128)
-  // of the pair tile and coefficient rows [128 r, 128 r + 128) of row tile rt
+  // of the pair tile (grouped: values of b) and coefficient rows [128 r, 128 r + 128)
+  // of row tile rt
   const uint32_t rank = cluster_ctarank();
   const int rt = blockIdx.y, mat = blockIdx.z;
   const long long vbase = (long long)(blockIdx.x >> 1) * (2 * kVP) + (long long)rank * kVP;
@@ -194,10 +209,10 @@ __global__ void __launch_bounds__(kThreadsA, 1)
     // Thread (corner i, half g) writes columns 32 g .. 32 g + 31 of row i of
     // each chunk: l = 32 j + 16 g + 1 .. + 16 as (cos, sin) pairs, zeros past K.
     const int cidx = tid & (kVP - 1), g = tid >> 7;
-    const long long v = vbase + cidx;
-    const bool live = v < pl.V;
+    const long long v = vbase + cidx;   // the corner, or (grouped) the value b itself
+    const bool live = GROUPED ? v <= pl.T : v < pl.V;
     const int32_t* cbp = mat == 0 ? pl.vy : pl.vx;
-    const uint32_t b = live ? (uint32_t)__ldg(cbp + v) : 0u;
+    const uint32_t b = !live ? 0u : (GROUPED ? (uint32_t)v : (uint32_t)__ldg(cbp + v));
     const float* m0 = reinterpret_cast<const float*>(ws + ar.off_m0) + (size_t)mat * (ar.kdim_pad + 4);
     const bool krow = rt == 0;   // row tile 0 also carries the k = 0 row
     const float2 w = tl_lookup(tl, b & mask);   // step cos, sin(2 pi b / T)
@@ -269,10 +284,76 @@ __global__ void __launch_bounds__(kThreadsA, 1)
     }
 
     // ---------------- epilogue: per-corner dot with A' ----------------
-    // warp w reads TMEM lanes 32 (w mod 4) .. +31 (its corners) over the
-    // columns of tile rows [128 g, 128 g + 128)
+    // warp w reads TMEM lanes 32 (w mod 4) .. +31 (its corners, or values of b)
+    // over the columns of tile rows [128 g, 128 g + 128)
     const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(accfull, 0, st, 46) ? 1 : 0) != 0;
     tc_fence_after();
+    if constexpr (GROUPED) {
+      // (1) Z[r, b] -> shared memory zs[r][b - b0] with the row scale and the
+      // side terms; the operand stages are free: the last MMA has completed
+      float* zs = reinterpret_cast<float*>(ops);
+      const float fb = (float)b;
+      const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
+      for (int cb = 0; cb < kRH; cb += 32) {
+        const int n0 = g * kRH + cb;
+        uint32_t d1[32], d2[32];
+        if (acc_ok) {
+          tmem_ld32(tmem + lane_base + (uint32_t)n0, d1);
+          tmem_ld32(tmem + lane_base + (uint32_t)(kAdjPairRows + n0), d2);
+          tmem_wait_ld();
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) d1[i] = d2[i] = 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float4 qr = rows[n0 + i];
+          zs[(n0 + i) * kVP + cidx] =
+              fmaf(__uint_as_float(d1[i]) + __uint_as_float(d2[i]), qr.x, fmaf(qr.z, fb, qr.y));
+        }
+      }
+      comb[g * kVP + cidx] = acc0;   // the k = 0 row's two column halves (row tile 0)
+      // (2) the corners whose b falls in [b0, b0 + 128), staged in pieces
+      const Groups gr = groups_at(ws + ar.off_groups + (size_t)mat * group_bytes(pl.V, pl.T, ar.ny_pad), pl.T,
+                                  ar.ny_pad);
+      int4* sc = reinterpret_cast<int4*>(ops + kZBytes);
+      const int b0 = (int)vbase;
+      const int cs = gr.start[min(b0, pl.T + 1)], ce = gr.start[min(b0 + kVP, pl.T + 1)];
+      const int32_t* cap = mat == 0 ? pl.vx : pl.vy;
+      const float m01 = m0[ar.kdim_pad], m0b = m0[ar.kdim_pad + 1];
+      const int kb = r0 / 2 + 1;   // frequency of tile rows 0 (cos) and 1 (sin)
+      float* part = reinterpret_cast<float*>(ws + ar.off_part) + ((size_t)mat * ar.rtiles + rt) * pl.V;
+      for (int pc = cs; pc < ce; pc += kCornerCache) {
+        const int pn = min(kCornerCache, ce - pc);
+        asm volatile("bar.sync 1, %0;" ::"n"(kGen) : "memory");   // zs written / previous piece read
+        for (int i = tid; i < pn; i += kGen) {
+          const int vv = gr.perm[pc + i];
+          sc[i] = make_int4(vv, __ldg(cap + vv), __ldg(cbp + vv) - b0, 0);
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(kGen) : "memory");
+        for (int i = tid; i < pn; i += kGen) {
+          const int4 e = sc[i];
+          const uint32_t av = (uint32_t)e.y;
+          const int bl = e.z;
+          float acc = krow ? comb[bl] + comb[kVP + bl] + fmaf(m0b, (float)(b0 + bl), m01) : 0.f;
+          const float2 wav = tl_lookup(tl, av & mask);
+          for (int f = 0; f < kRH; f += 8) {   // runs of 8 frequencies = 16 tile rows
+            const float2 an = tl_lookup(tl, (uint32_t)(kb + f) * av & mask);
+            float c = an.x, sn = an.y;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const int r = 2 * (f + t);
+              acc = fmaf(c, zs[r * kVP + bl], acc);
+              acc = fmaf(sn, zs[(r + 1) * kVP + bl], acc);
+              const float c1 = fmaf(c, wav.x, -(sn * wav.y)), s1 = fmaf(sn, wav.x, c * wav.y);
+              c = c1;
+              sn = s1;
+            }
+          }
+          part[e.x] = acc;
+        }
+      }
+    } else {
     const int32_t* cap = mat == 0 ? pl.vx : pl.vy;
     const uint32_t a = live ? (uint32_t)__ldg(cap + v) : 0u;
     const float2 wa = tl_lookup(tl, a & mask);
@@ -315,6 +396,7 @@ __global__ void __launch_bounds__(kThreadsA, 1)
       if (krow) tot += fmaf(m0[ar.kdim_pad + 1], fb, m0[ar.kdim_pad]);
       reinterpret_cast<float*>(ws + ar.off_part)[((size_t)mat * ar.rtiles + rt) * pl.V + v] = tot;
     }
+    }
   }
 
   // the pair's MMAs, commits and arrivals reach both CTAs: neither releases
@@ -334,10 +416,12 @@ __global__ void __launch_bounds__(kThreadsA, 1)
 cudaError_t launch_adj_tc(const AdjTcArgs& ar, const CUtensorMap& mhi, const CUtensorMap& mlo, void* ws,
                           cudaStream_t st) {
   if (ar.pl.logT > 16) return cudaErrorInvalidValue;   // the two-level table holds T <= 2^16
-  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(adj_tc_kernel), kAdjSmem);
+  auto kern = ar.grouped ? adj_tc_kernel<true> : adj_tc_kernel<false>;
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), kAdjSmem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(2 * ((ar.pl.V + 2 * kVP - 1) / (2 * kVP))), (unsigned)ar.rtiles, 2);
+  const long long mrows = ar.grouped ? (long long)ar.pl.T + 1 : ar.pl.V;   // corners or values of b
+  cfg.gridDim = dim3((unsigned)(2 * ((mrows + 2 * kVP - 1) / (2 * kVP))), (unsigned)ar.rtiles, 2);
   cfg.blockDim = dim3(kThreadsA);
   cfg.dynamicSmemBytes = kAdjSmem;
   cfg.stream = st;
@@ -348,7 +432,7 @@ cudaError_t launch_adj_tc(const AdjTcArgs& ar, const CUtensorMap& mhi, const CUt
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, adj_tc_kernel, mhi, mlo, ar, static_cast<uint8_t*>(ws));
+  e = cudaLaunchKernelEx(&cfg, kern, mhi, mlo, ar, static_cast<uint8_t*>(ws));
   count_launch(1);
   return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -156,6 +156,8 @@ fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
   return make_plan_ex(V, T, K, prec, false, pl);
 }
 
+int hybrid_mode() { return g_hybrid; }
+
 // Row-binned contraction (corners grouped by y, contraction over the T + 1
 // values of y): eligible for a single-clip split-FP16 call on CTA pairs; taken
 // automatically when the corners outnumber the y values 8 to 1.
@@ -177,7 +179,7 @@ static void plan_hybrid(Plan& pl) {
   pl.split_len = per * 64;
   pl.splits = (int)((nchunks + per - 1) / per);
   size_t o = align_up(pl.off_part + (size_t)pl.splits * pl.M2 * pl.M2 * sizeof(float), kWsAlign);
-  pl.total = hybrid_extra_bytes(pl.V, pl.T, pl.M2, pl.ny_pad, pl.off_ycnt, pl.off_perm, pl.off_h, o);
+  pl.total = hybrid_extra_bytes(pl.V, pl.T, pl.M2, pl.ny_pad, pl.off_ycnt, pl.off_h, o);
 }
 
 // ---------------------------------------------------------------------------

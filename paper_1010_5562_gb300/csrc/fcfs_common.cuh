@@ -59,8 +59,7 @@ struct Plan {
   // of y; the splits then cut the y range (split_len counts y values)
   int32_t hyb;
   int32_t ny_pad;              // T + 1 rounded up to the chunk (64)
-  size_t off_ycnt;             // int32 [3][T + 2]: count, start offset and cursor per y
-  size_t off_perm;             // int32 [V]: corner indices grouped by y
+  size_t off_ycnt;             // the corners grouped by y (fcfs_group.cuh)
   size_t off_h;                // FP16 [2][M2][ny_pad]: H = sum over a y group of s A, hi then lo
 };
 
@@ -481,15 +480,19 @@ struct AdjTcArgs {
   size_t off_rows;  // float4 [2][nrows_pad]: (row scale, column-1 term, column-b term, 0)
   size_t off_m0;    // float [2][kdim_pad + 4]: the k = 0 row over the columns, then its 1 and b terms
   size_t off_part;  // float [2][rtiles][V]: per-row-tile partial derivatives
+  int grouped;      // 1: corners grouped by b, the MMA's M dimension over the T + 1 values of b
+  int ny_pad;       // grouped: T + 1 rounded up to 64 (the groups' exponent array)
+  size_t off_groups;  // grouped: by y (gx), then by x (gy) (fcfs_group.cuh)
 };
+// Row-binned (grouped) mode of the forward and adjoint calls: 0 never, 1 automatic, 2 forced
+int hybrid_mode();
 cudaError_t launch_adj_tc(const AdjTcArgs& ar, const CUtensorMap& mhi, const CUtensorMap& mlo, void* ws,
                           cudaStream_t st);
 // Row-binned contraction (fcfs_hybrid.cu): grouping, H, and the contraction
 // over y into the plan's FP32 partial planes.
 cudaError_t launch_hybrid(const Plan& pl, void* ws, cudaStream_t st);
 // Workspace regions of the row-binned contraction placed from `base`; returns the end.
-size_t hybrid_extra_bytes(int64_t V, int T, int M2, int ny_pad, size_t& off_ycnt, size_t& off_perm, size_t& off_h,
-                          size_t base);
+size_t hybrid_extra_bytes(int64_t V, int T, int M2, int ny_pad, size_t& off_ycnt, size_t& off_h, size_t base);
 // 2-D FP16 tensor map (cols innermost), 128-byte swizzle, box box_cols x box_rows
 bool encode_f16_2d_sw128(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint32_t box_cols,
                          uint32_t box_rows);

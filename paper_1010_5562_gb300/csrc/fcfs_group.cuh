@@ -1,0 +1,49 @@
+// Grouping of corners by one integer coordinate in [0, T] (a counting sort),
+// shared by the row-binned forward contraction (groups by y) and the grouped
+// adjoint contraction (groups by y for gx and by x for gy).
+//
+// Per coordinate, one workspace region:
+//   int32 count[S], start[S], cursor[S]   S = group_stride(T) >= T + 2, a multiple of 4
+//   int8  e[ny_pad]                       exponent of the power-of-two scale of a
+//                                         large group (ceil(log2 count) - 14, clamped
+//                                         to [0, 15]; 0 for groups of <= 2^14 corners)
+//   int32 perm[V]                         corner indices, group after group
+// start[T + 1] is the number of grouped corners; corners whose coordinate is
+// outside [0, T] are left out.  The order inside a group is whatever the
+// atomic cursors give: users must not depend on it.
+#pragma once
+
+#include "fcfs_common.cuh"
+
+namespace fcfs {
+
+__host__ __device__ inline int group_stride(int T) { return (T + 2 + 3) & ~3; }
+
+__host__ __device__ inline size_t group_bytes(int64_t V, int T, int ny_pad) {
+  return align_up(align_up((size_t)3 * group_stride(T) * 4 + (size_t)ny_pad, 16) + (size_t)(V > 0 ? V : 1) * 4, 256);
+}
+
+struct Groups {
+  int *cnt, *start, *cur;
+  int8_t* ey;
+  int* perm;
+};
+
+__host__ __device__ inline Groups groups_at(uint8_t* base, int T, int ny_pad) {
+  const int st = group_stride(T);
+  Groups g;
+  g.cnt = reinterpret_cast<int*>(base);
+  g.start = g.cnt + st;
+  g.cur = g.start + st;
+  g.ey = reinterpret_cast<int8_t*>(g.cur + st);
+  g.perm = reinterpret_cast<int*>(base + align_up((size_t)3 * st * 4 + (size_t)ny_pad, 16));
+  return g;
+}
+
+// Group the V corners by c0 (and, with c1 != nullptr, separately by c1 into
+// the next region, base + group_bytes): a memset and three kernels (count,
+// scan, scatter) whatever the number of coordinates.
+cudaError_t launch_grouping(const int32_t* c0, const int32_t* c1, int64_t V, int T, int ny_pad, uint8_t* base,
+                            cudaStream_t st);
+
+}  // namespace fcfs

@@ -21,55 +21,37 @@
 #include <algorithm>
 
 #include "fcfs_epilogue.cuh"
+#include "fcfs_group.cuh"
 
 namespace fcfs {
 
 namespace {
 
 // ---------------------------------------------------------------------------
-// Stage 1: group the corners by y
+// Stage 1: grouping (fcfs_group.cuh); blockIdx.y selects the coordinate
 // ---------------------------------------------------------------------------
-// int32 count, start and cursor per y (each T + 2 entries padded to a multiple
-// of 4, so that the scan moves 16-byte vectors), then int8 e_y[ny_pad]
-__host__ __device__ inline int ygroups_stride(int T) { return (T + 2 + 3) & ~3; }
-struct YGroups {
-  int *cnt, *start, *cur;
-  int8_t* ey;
-};
-__host__ __device__ inline YGroups ygroups(const Plan& pl, uint8_t* ws) {
-  const int st = ygroups_stride(pl.T);
-  YGroups g;
-  g.cnt = reinterpret_cast<int*>(ws + pl.off_ycnt);
-  g.start = g.cnt + st;
-  g.cur = g.start + st;
-  g.ey = reinterpret_cast<int8_t*>(g.cur + st);
-  return g;
-}
-__host__ __device__ inline size_t ygroups_bytes(int T, int ny_pad) {
-  return (size_t)3 * ygroups_stride(T) * 4 + ny_pad;
-}
-
-__global__ void hyb_count_kernel(Plan pl, uint8_t* ws) {
-  const YGroups g = ygroups(pl, ws);
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < pl.V; v += (long long)gridDim.x * blockDim.x) {
-    const int y = __ldg(pl.vy + v);
-    if (y >= 0 && y <= pl.T) atomicAdd(&g.cnt[y], 1);
+__global__ void group_count_kernel(const int32_t* __restrict__ c0, const int32_t* __restrict__ c1, long long V,
+                                   int T, int ny_pad, uint8_t* base) {
+  const int32_t* c = blockIdx.y ? c1 : c0;
+  const Groups g = groups_at(base + blockIdx.y * group_bytes(V, T, ny_pad), T, ny_pad);
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    const int y = __ldg(c + v);
+    if (y >= 0 && y <= T) atomicAdd(&g.cnt[y], 1);
   }
 }
 
-// One CTA: exclusive scan of the T + 1 counts into start (and the cursors),
-// start[T + 1] = the number of grouped corners, in tiles of 4 entries per
-// thread; the per-y exponent e_y = clamp(ceil(log2 count) - 14, 0, 15), so
-// that |H[., y]| 2^-e_y <= 2^14.
+// One CTA per coordinate: exclusive scan of the T + 1 counts into start (and
+// the cursors) in tiles of 4 entries per thread, start[T + 1] = the number of
+// grouped corners; the exponents e of the large groups.
 constexpr int kScanThreads = 1024;
-__global__ void __launch_bounds__(kScanThreads) hyb_scan_kernel(Plan pl, uint8_t* ws) {
-  const YGroups g = ygroups(pl, ws);
-  const int n = pl.T + 1;
+__global__ void __launch_bounds__(kScanThreads) group_scan_kernel(long long V, int T, int ny_pad, uint8_t* base) {
+  const Groups g = groups_at(base + blockIdx.x * group_bytes(V, T, ny_pad), T, ny_pad);
+  const int n = T + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ int wsum[kScanThreads / 32];
   int carry = 0;
-  for (int base = 0; base < n; base += 4 * kScanThreads) {
-    const int i0 = base + 4 * (int)threadIdx.x;
+  for (int b0 = 0; b0 < n; b0 += 4 * kScanThreads) {
+    const int i0 = b0 + 4 * (int)threadIdx.x;
     int4 c = make_int4(0, 0, 0, 0);
     if (i0 < n) {   // the vector stays inside the padded array
       c = *reinterpret_cast<const int4*>(g.cnt + i0);
@@ -106,7 +88,7 @@ __global__ void __launch_bounds__(kScanThreads) hyb_scan_kernel(Plan pl, uint8_t
     __syncthreads();   // wsum is reused by the next tile
   }
   if (threadIdx.x == 0) g.start[n] = carry;
-  for (int i = threadIdx.x; i < pl.ny_pad; i += kScanThreads) {
+  for (int i = threadIdx.x; i < ny_pad; i += kScanThreads) {
     int ex = 0;
     if (i < n && g.cnt[i] > (1 << 14)) {
       int l = 0;
@@ -117,12 +99,13 @@ __global__ void __launch_bounds__(kScanThreads) hyb_scan_kernel(Plan pl, uint8_t
   }
 }
 
-__global__ void hyb_scatter_kernel(Plan pl, uint8_t* ws) {
-  const YGroups g = ygroups(pl, ws);
-  int* perm = reinterpret_cast<int*>(ws + pl.off_perm);
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < pl.V; v += (long long)gridDim.x * blockDim.x) {
-    const int y = __ldg(pl.vy + v);
-    if (y >= 0 && y <= pl.T) perm[atomicAdd(&g.cur[y], 1)] = (int)v;
+__global__ void group_scatter_kernel(const int32_t* __restrict__ c0, const int32_t* __restrict__ c1, long long V,
+                                     int T, int ny_pad, uint8_t* base) {
+  const int32_t* c = blockIdx.y ? c1 : c0;
+  const Groups g = groups_at(base + blockIdx.y * group_bytes(V, T, ny_pad), T, ny_pad);
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    const int y = __ldg(c + v);
+    if (y >= 0 && y <= T) g.perm[atomicAdd(&g.cur[y], 1)] = (int)v;
   }
 }
 
@@ -164,8 +147,8 @@ __global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* w
   int* lv = reinterpret_cast<int*>(sm);
   int4* vc = reinterpret_cast<int4*>(sm + align_up(axis_levels_ints(T) * 4, 16));
   int* soff = reinterpret_cast<int*>(vc + kHCache);
-  const YGroups g = ygroups(pl, ws);
-  const int* perm = reinterpret_cast<const int*>(ws + pl.off_perm);
+  const Groups g = groups_at(ws + pl.off_ycnt, T, pl.ny_pad);
+  const int* perm = g.perm;
   __half* Hhi = reinterpret_cast<__half*>(ws + pl.off_h);
   __half* Hlo = Hhi + (size_t)pl.M2 * pl.ny_pad;
   const uint32_t mask = (uint32_t)T - 1u;
@@ -407,7 +390,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const uint32_t f0 = (uint32_t)(tn * 128 + (int)rank * 64 + 1 + i0);
     const uint32_t mask = (uint32_t)pl.T - 1u;
     const uint32_t ops_a = smem_u32(ops);
-    const YGroups yg = ygroups(pl, ws);
+    const Groups yg = groups_at(ws + pl.off_ycnt, pl.T, pl.ny_pad);
     uint32_t xo[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) xo[c] = (uint32_t)((oct ^ c) << 4);
@@ -529,16 +512,32 @@ __global__ void __launch_bounds__(kGThreads, 1)
 
 }  // namespace
 
-size_t hybrid_extra_bytes(int64_t V, int T, int M2, int ny_pad, size_t& off_ycnt, size_t& off_perm, size_t& off_h,
-                          size_t base) {
+size_t hybrid_extra_bytes(int64_t V, int T, int M2, int ny_pad, size_t& off_ycnt, size_t& off_h, size_t base) {
   size_t o = base;
   off_ycnt = o;
-  o = align_up(o + ygroups_bytes(T, ny_pad), kWsAlign);
-  off_perm = o;
-  o = align_up(o + (size_t)std::max<int64_t>(V, 1) * 4, kWsAlign);
+  o = align_up(o + group_bytes(V, T, ny_pad), kWsAlign);
   off_h = o;
   o = align_up(o + (size_t)2 * M2 * ny_pad * 2, kWsAlign);
   return o;
+}
+
+cudaError_t launch_grouping(const int32_t* c0, const int32_t* c1, int64_t V, int T, int ny_pad, uint8_t* base,
+                            cudaStream_t st) {
+  const int nc = c1 ? 2 : 1;
+  const size_t gb = group_bytes(V, T, ny_pad);
+  for (int i = 0; i < nc; ++i) {
+    const cudaError_t e = cudaMemsetAsync(base + i * gb, 0, (size_t)group_stride(T) * 4, st);
+    if (e != cudaSuccess) return e;
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int vblocks = (int)std::max<long long>(1, std::min<long long>((V + 255) / 256, 8LL * sms));
+  group_count_kernel<<<dim3(vblocks, nc), 256, 0, st>>>(c0, c1, V, T, ny_pad, base);
+  group_scan_kernel<<<nc, kScanThreads, 0, st>>>(V, T, ny_pad, base);
+  group_scatter_kernel<<<dim3(vblocks, nc), 256, 0, st>>>(c0, c1, V, T, ny_pad, base);
+  count_launch(3);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_hybrid(const Plan& pl, void* ws_, cudaStream_t st) {
@@ -547,14 +546,8 @@ cudaError_t launch_hybrid(const Plan& pl, void* ws_, cudaStream_t st) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaMemsetAsync(ws + pl.off_ycnt, 0, (size_t)ygroups_stride(pl.T) * 4, st);
+  cudaError_t e = launch_grouping(pl.vy, nullptr, pl.V, pl.T, pl.ny_pad, ws + pl.off_ycnt, st);
   if (e != cudaSuccess) return e;
-  const int vblocks = (int)std::max<long long>(1, std::min<long long>((pl.V + 255) / 256, 8LL * sms));
-  hyb_count_kernel<<<vblocks, 256, 0, st>>>(pl, ws);
-  hyb_scan_kernel<<<1, kScanThreads, 0, st>>>(pl, ws);
-  hyb_scatter_kernel<<<vblocks, 256, 0, st>>>(pl, ws);
-  count_launch(3);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t hs = hyb_h_smem(pl.T);
   if ((e = ensure_smem(reinterpret_cast<const void*>(hyb_h_kernel), hs)) != cudaSuccess) return e;
   const long long hunits = (long long)(pl.ny_pad / kHY) * ((pl.K + kHF - 1) / kHF);

@@ -142,3 +142,65 @@ def test_config5_adjoint_sampled(fc, prec):
     rx, ry = oracle.vertex_gradient(clip.x[idx], clip.y[idx], clip.s[idx], clip.T, K, G.astype(np.complex128))
     ex, ey = rel(gx[idx], rx), rel(gy[idx], ry)
     assert ex < 1e-4 and ey < 1e-4, (ex, ey)
+
+
+def grad_mode(fc, clip, K, G, mode):
+    fc.set_hybrid(mode)   # the adjoint sizes its workspace inside the call
+    try:
+        return gpu_grad(fc, clip, K, G, "split_f16")
+    finally:
+        fc.set_hybrid(1)
+
+
+@pytest.mark.parametrize("K", [1, 7, 64, 129, 200])
+def test_grouped_adjoint_random_cotangent(fc, K):
+    """Corners grouped by b (y for gx, x for gy): the MMA's M dimension runs over
+    the T + 1 values of b and the epilogue over each value's corners.  Forced on
+    a small clip: against the oracle and against the per-corner contraction."""
+    clip = make_clip(512, 30, 900 + K, smin=6, smax=40)
+    rng = np.random.default_rng(100 + K)
+    W = 2 * K + 1
+    G = rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))
+    gx, gy = grad_mode(fc, clip, K, G, 2)
+    gx0, gy0 = grad_mode(fc, clip, K, G, 0)
+    rx, ry = oracle.vertex_gradient(clip.x, clip.y, clip.s, clip.T, K, G)
+    assert rel(gx, rx) < TOL and rel(gy, ry) < TOL, (rel(gx, rx), rel(gy, ry))
+    assert rel(gx, gx0) < 2e-6 and rel(gy, gy0) < 2e-6, (rel(gx, gx0), rel(gy, gy0))
+
+
+def test_grouped_adjoint_large_groups(fc):
+    """10000 rectangles 5 wide on y in [0, 50]: the y groups of 20000 corners
+    exceed the epilogue's staging (4096 corners), so the CTA of b in [0, 128)
+    takes them in pieces.  Sampled corners against the oracle."""
+    from synth import clip_from_rings, rect_ring
+    T, K = 65536, 128
+    clip = clip_from_rings(T, [rect_ring(6 * i, 0, 6 * i + 5, 50) for i in range(10000)])
+    rng = np.random.default_rng(9)
+    W = 2 * K + 1
+    G = rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))
+    gx, gy = grad_mode(fc, clip, K, G, 1)   # V = 40000 < 8 (T + 1): forced below
+    gx2, gy2 = grad_mode(fc, clip, K, G, 2)
+    idx = np.sort(rng.choice(clip.V, 48, replace=False))
+    rx, ry = oracle.vertex_gradient(clip.x[idx], clip.y[idx], clip.s[idx], T, K, G)
+    for a, b in ((gx2[idx], rx), (gy2[idx], ry), (gx[idx], rx), (gy[idx], ry)):
+        assert rel(a, b) < TOL, rel(a, b)
+
+
+def test_grouped_adjoint_launches(fc):
+    """Grouped: prep, coefficients, pack, count, scan, scatter, contraction,
+    finalize; per corner: prep, coefficients, pack, contraction, finalize.
+    Workload 4 stays per corner automatically: its grouped form would have 36
+    CTAs, less than a wave."""
+    clip, K = config_clip(4)
+    x, y, s = dev(clip.x), dev(clip.y), dev(clip.s)
+    dF = torch.zeros((2 * K + 1, 2 * K + 1), dtype=torch.complex64, device="cuda")
+    n0 = fc.launch_count()
+    fc.adjoint(x, y, s, clip.T, K, dF, prec="split_f16")
+    assert fc.launch_count() - n0 == 5
+    fc.set_hybrid(2)
+    try:
+        n0 = fc.launch_count()
+        fc.adjoint(x, y, s, clip.T, K, dF, prec="split_f16")
+        assert fc.launch_count() - n0 == 8
+    finally:
+        fc.set_hybrid(1)
