@@ -331,26 +331,40 @@ __global__ void __launch_bounds__(kThreadsA, 1)
           sc[i] = make_int4(vv, __ldg(cap + vv), __ldg(cbp + vv) - b0, 0);
         }
         asm volatile("bar.sync 1, %0;" ::"n"(kGen) : "memory");
-        for (int i = tid; i < pn; i += kGen) {
-          const int4 e = sc[i];
-          const uint32_t av = (uint32_t)e.y;
-          const int bl = e.z;
-          float acc = krow ? comb[bl] + comb[kVP + bl] + fmaf(m0b, (float)(b0 + bl), m01) : 0.f;
-          const float2 wav = tl_lookup(tl, av & mask);
+        // two corners per thread at a time, separate cos and sin sums: four
+        // independent FMA chains and two angle-addition chains
+        for (int i = tid; i < pn; i += 2 * kGen) {
+          const bool two = i + kGen < pn;
+          const int4 e0 = sc[i], e1 = two ? sc[i + kGen] : e0;
+          const uint32_t a0 = (uint32_t)e0.y, a1 = (uint32_t)e1.y;
+          const int bl0 = e0.z, bl1 = e1.z;
+          float c0s = 0.f, s0s = 0.f, c1s = 0.f, s1s = 0.f;
+          const float2 w0 = tl_lookup(tl, a0 & mask), w1 = tl_lookup(tl, a1 & mask);
           for (int f = 0; f < kRH; f += 8) {   // runs of 8 frequencies = 16 tile rows
-            const float2 an = tl_lookup(tl, (uint32_t)(kb + f) * av & mask);
-            float c = an.x, sn = an.y;
+            const float2 n0 = tl_lookup(tl, (uint32_t)(kb + f) * a0 & mask);
+            const float2 n1 = tl_lookup(tl, (uint32_t)(kb + f) * a1 & mask);
+            float ca = n0.x, sa = n0.y, cb2 = n1.x, sb2 = n1.y;
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
               const int r = 2 * (f + t);
-              acc = fmaf(c, zs[r * kVP + bl], acc);
-              acc = fmaf(sn, zs[(r + 1) * kVP + bl], acc);
-              const float c1 = fmaf(c, wav.x, -(sn * wav.y)), s1 = fmaf(sn, wav.x, c * wav.y);
-              c = c1;
-              sn = s1;
+              c0s = fmaf(ca, zs[r * kVP + bl0], c0s);
+              s0s = fmaf(sa, zs[(r + 1) * kVP + bl0], s0s);
+              c1s = fmaf(cb2, zs[r * kVP + bl1], c1s);
+              s1s = fmaf(sb2, zs[(r + 1) * kVP + bl1], s1s);
+              const float ca1 = fmaf(ca, w0.x, -(sa * w0.y)), sa1 = fmaf(sa, w0.x, ca * w0.y);
+              const float cb1 = fmaf(cb2, w1.x, -(sb2 * w1.y)), sb1 = fmaf(sb2, w1.x, cb2 * w1.y);
+              ca = ca1;
+              sa = sa1;
+              cb2 = cb1;
+              sb2 = sb1;
             }
           }
-          part[e.x] = acc;
+          const float k00 = krow ? comb[bl0] + comb[kVP + bl0] + fmaf(m0b, (float)(b0 + bl0), m01) : 0.f;
+          part[e0.x] = k00 + (c0s + s0s);
+          if (two) {
+            const float k01 = krow ? comb[bl1] + comb[kVP + bl1] + fmaf(m0b, (float)(b0 + bl1), m01) : 0.f;
+            part[e1.x] = k01 + (c1s + s1s);
+          }
         }
       }
     } else {

@@ -164,6 +164,8 @@ __global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* w
   const long long units = (long long)(pl.ny_pad / kHY) * npass;
   const int u0 = (int)(units * blockIdx.x / gridDim.x), u1 = (int)(units * (blockIdx.x + 1) / gridDim.x);
   const float inv_q = ldexpf(1.f, -pl.fixq);
+  // groups of up to this many corners sum in int32 (each term is at most 2^fixq)
+  const int small_group = (1 << (31 - pl.fixq)) - 1;
   int staged = -1, a = 0;
   bool cached = false;
   for (int unit = u0; unit < u1; ++unit) {
@@ -189,8 +191,8 @@ __global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* w
 #pragma unroll
       for (int yy = 0; yy < 8; ++yy) {
         const int y = oc * 8 + yy;
-        long long ac = 0, as = 0;
-        for (int i = soff[y]; i < soff[y + 1]; ++i) {
+        // one term s_v (cos, sin)(2 pi k x_v / T) of the fixed-point table
+        auto term = [&](int i, auto& ac_, auto& as_) {
           int4 cn;
           if (cached) {
             cn = vc[i];
@@ -206,8 +208,17 @@ __global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* w
           const int* L = lv + cn.y;
           const int c = L[odd ? Q - r : r], sn = L[odd ? r : Q - r];
           // cos < 0 in quadrants 1, 2; sin < 0 in quadrants 2, 3; s = -1 flips both
-          ac += ((((qd + 1u) >> 1) & 1u) ^ sf) ? -c : c;
-          as += ((qd >> 1) ^ sf) ? -sn : sn;
+          ac_ += ((((qd + 1u) >> 1) & 1u) ^ sf) ? -c : c;
+          as_ += ((qd >> 1) ^ sf) ? -sn : sn;
+        };
+        long long ac = 0, as = 0;
+        if (soff[y + 1] - soff[y] <= small_group) {   // warp-uniform: |sum| < 2^31 in int32
+          int ac32 = 0, as32 = 0;
+          for (int i = soff[y]; i < soff[y + 1]; ++i) term(i, ac32, as32);
+          ac = ac32;
+          as = as32;
+        } else {
+          for (int i = soff[y]; i < soff[y + 1]; ++i) term(i, ac, as);
         }
         const float sc = ldexpf(inv_q, -(int)g.ey[y0 + y]);
         const float fc = __ll2float_rn(ac) * sc, fs = __ll2float_rn(as) * sc;
