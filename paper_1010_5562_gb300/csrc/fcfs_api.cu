@@ -160,11 +160,14 @@ int hybrid_mode() { return g_hybrid; }
 
 // Row-binned contraction (corners grouped by y, contraction over the T + 1
 // values of y): eligible for a single-clip split-FP16 call on CTA pairs; taken
-// automatically when the corners outnumber the y values 8 to 1.
+// automatically when the corners outnumber the y values 8 to 1 and K >= 256.
+// Per corner, H costs ~K fixed-point terms on the CUDA cores and the direct
+// contraction ~(2K)^2 tensor-core MACs per output pair: they break even near
+// K ~ 110, so at smaller K grouping gains little and adds launches.
 static bool hybrid_wanted(const Plan& pl, bool validate) {
   if (g_hybrid == 0 || validate || !pl.pair || pl.prec != FCFS_PREC_SPLIT_F16 || pl.V <= 0 || pl.logT > 16)
     return false;
-  return g_hybrid == 2 || pl.V >= 8LL * (pl.T + 1);
+  return g_hybrid == 2 || (pl.V >= 8LL * (pl.T + 1) && pl.K >= 256);
 }
 
 // Turn a single-clip pair plan into the row-binned one: splits over 64-y

@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "fcfs_common.cuh"
+#include "fcfs_group.cuh"
 
 namespace fcfs {
 
@@ -29,17 +30,47 @@ static fcfs_status make_batch_plan(int64_t V, int32_t n, int32_t T, int32_t K, i
   pl.batch = 1;
   pl.n_clips = n;
   pl.offsets = offsets;
+  size_t o = pl.off_axis;       // tables stay where the single-clip plan put them
+  o = align_up(o + (size_t)n * (4 * K + 1) * sizeof(long long), kWsAlign);
+  pl.off_bins = o;
+  o = align_up(o + (size_t)n * bins_bytes(T), kWsAlign);
+  pl.off_hist = o;
+  // Grouped batch (corners of each clip grouped by y, every clip contracted
+  // over its T + 1 values of y on CTA pairs): split FP16, 2K >= 256; taken
+  // automatically with on average 8 corners or more per value of y and
+  // K >= 256 (the single-clip rule)
+  const int mode = hybrid_mode();
+  if (prec == FCFS_PREC_SPLIT_F16 && pl.M2 >= 256 && pl.logT <= 16 && V > 0 && n <= 65535 &&
+      (mode == 2 || (mode == 1 && V >= 8LL * n * (T + 1) && K >= 256))) {
+    pl.hyb = 1;
+    pl.pair = 1;
+    pl.bn = 256;
+    pl.tiles_n = (pl.M2 + 255) / 256;
+    pl.tiles_m = 2 * pl.tiles_n;
+    pl.ny_pad = (T + 1 + 63) / 64 * 64;
+    const long long nchunks = pl.ny_pad / 64;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long ctas1 = (long long)n * pl.tiles_m * pl.tiles_n;   // CTAs of one y split
+    const long long s = std::min<long long>(nchunks, std::max<long long>(1, (2LL * sms + ctas1 - 1) / ctas1));
+    const long long per = (nchunks + s - 1) / s;
+    pl.split_len = per * 64;
+    pl.splits = (int)((nchunks + per - 1) / per);
+    pl.off_part = o;
+    o = align_up(o + (size_t)n * pl.splits * pl.M2 * pl.M2 * sizeof(float), kWsAlign);
+    pl.off_ycnt = o;
+    o = align_up(o + batch_group_bytes(V, n, T, pl.ny_pad), kWsAlign);
+    pl.off_h = o;
+    o = align_up(o + (size_t)n * 2 * pl.M2 * pl.ny_pad * 2, kWsAlign);
+    pl.total = o;
+    return FCFS_OK;
+  }
   const int chunks = g_unit_chunks > 0 ? g_unit_chunks : 4096 / pl.chunk;
   pl.unit_vertices = (int64_t)chunks * pl.chunk;
   const long long tiles = (long long)pl.tiles_m * pl.tiles_n;
   const long long units_max = tiles * ((V + pl.unit_vertices - 1) / pl.unit_vertices + n);
   if (units_max >= (1LL << 31)) return FCFS_EUNSUPPORTED;
   pl.splits = (int)units_max;   // grid of the contraction kernel
-  size_t o = pl.off_axis;       // tables stay where the single-clip plan put them
-  o = align_up(o + (size_t)n * (4 * K + 1) * sizeof(long long), kWsAlign);
-  pl.off_bins = o;
-  o = align_up(o + (size_t)n * bins_bytes(T), kWsAlign);
-  pl.off_hist = o;
   pl.off_units = o;
   o = align_up(o + (size_t)(n + 1) * sizeof(int), kWsAlign);
   pl.off_part = o;
@@ -93,6 +124,13 @@ static fcfs_status batch_impl(const int32_t* x, const int32_t* y, const int8_t* 
   pl.vy = y;
   pl.vsg = s;
   if (launch_prep(pl, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
+  if (pl.hyb) {   // grouped: grouping, H, contraction over y; binning, axis DFT, reduce
+    pl.bin_in_gemm = 0;
+    if (launch_hybrid(pl, ws, st) != cudaSuccess) return FCFS_ECUDA;
+    if (launch_axis(pl, x, y, s, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
+    if (launch_reduce(pl, ws, F, area, false, st) != cudaSuccess) return FCFS_ECUDA;
+    return FCFS_OK;
+  }
   batch_units_kernel<<<1, 1024, 0, st>>>(pl, static_cast<uint8_t*>(ws));
   count_launch(1);
   if (cudaGetLastError() != cudaSuccess) return FCFS_ECUDA;

@@ -46,6 +46,8 @@ __device__ __forceinline__ void axis_build_levels(int* lv, int T, int logT) {
 }
 
 // Add bin n (weights wx = bin_x[n], wy = bin_y[n]) to the four sums of frequency k.
+// W32: both weights fit in int32, so each product is one 32 x 32 -> 64-bit multiply.
+template <bool W32 = false>
 __device__ __forceinline__ void axis_bin_add(const int* lv, int T, int logQ, int k, int n, long long wx,
                                              long long wy, long long& a0, long long& a1, long long& a2,
                                              long long& a3) {
@@ -64,11 +66,20 @@ __device__ __forceinline__ void axis_bin_add(const int* lv, int T, int logQ, int
   int c = L[qd.i1], sn = L[qd.i2];
   if (qd.cneg) c = -c;
   if (qd.sneg) sn = -sn;
-  a0 += (long long)c * wx;
-  a1 += (long long)sn * wx;
-  a2 += (long long)c * wy;
-  a3 += (long long)sn * wy;
+  if (W32) {
+    const int x32 = (int)wx, y32 = (int)wy;
+    a0 += (long long)c * x32;
+    a1 += (long long)sn * x32;
+    a2 += (long long)c * y32;
+    a3 += (long long)sn * y32;
+  } else {
+    a0 += (long long)c * wx;
+    a1 += (long long)sn * wx;
+    a2 += (long long)c * wy;
+    a3 += (long long)sn * wy;
+  }
 }
+__device__ __forceinline__ bool fits_i32(long long w) { return w == (long long)(int)w; }
 
 // F(+-f, 0) (row) or F(0, +-f) (column) from the fixed-point sums
 // Cq = sum w cos * 2^q, Sq = sum w sin * 2^q: F = (T / 2 pi f)(S + jC).
@@ -298,10 +309,18 @@ __device__ __forceinline__ void k_bin_add(const KLevel& kl, int n, long long wx,
   int c = kl.L[qd.i1], sn = kl.L[qd.i2];
   if (qd.cneg) c = -c;
   if (qd.sneg) sn = -sn;
-  a0 += (long long)c * wx;
-  a1 += (long long)sn * wx;
-  a2 += (long long)c * wy;
-  a3 += (long long)sn * wy;
+  if (fits_i32(wx) && fits_i32(wy)) {   // one 32 x 32 -> 64-bit multiply per product
+    const int x32 = (int)wx, y32 = (int)wy;
+    a0 += (long long)c * x32;
+    a1 += (long long)sn * x32;
+    a2 += (long long)c * y32;
+    a3 += (long long)sn * y32;
+  } else {
+    a0 += (long long)c * wx;
+    a1 += (long long)sn * wx;
+    a2 += (long long)c * wy;
+    a3 += (long long)sn * wy;
+  }
 }
 
 __device__ inline void fused_tail(const Plan& pl, uint8_t* ws, uint8_t* smem, int* sflag, uint64_t* bar_axis,

@@ -40,6 +40,26 @@ __host__ __device__ inline Groups groups_at(uint8_t* base, int T, int ny_pad) {
   return g;
 }
 
+// A batch of n clips grouped by y, clip by clip: count, start and cursor rows
+// [n][S], exponents [n][ny_pad], then one perm[V] (start values are positions
+// in it; clip c's corners fill [offsets[c], offsets[c + 1])).
+__host__ __device__ inline size_t batch_group_bytes(int64_t V, int n, int T, int ny_pad) {
+  return align_up(align_up((size_t)3 * n * group_stride(T) * 4 + (size_t)n * ny_pad, 16) + (size_t)(V > 0 ? V : 1) * 4,
+                  256);
+}
+__host__ __device__ inline Groups groups_clip(uint8_t* base, int T, int ny_pad, int n, int c, int64_t V) {
+  (void)V;
+  const size_t st = group_stride(T);
+  int* cnt0 = reinterpret_cast<int*>(base);
+  Groups g;
+  g.cnt = cnt0 + (size_t)c * st;
+  g.start = cnt0 + (size_t)n * st + (size_t)c * st;
+  g.cur = cnt0 + (size_t)2 * n * st + (size_t)c * st;
+  g.ey = reinterpret_cast<int8_t*>(cnt0 + (size_t)3 * n * st) + (size_t)c * ny_pad;
+  g.perm = reinterpret_cast<int*>(base + align_up((size_t)3 * n * st * 4 + (size_t)n * ny_pad, 16));
+  return g;
+}
+
 // Group the V corners by c0 (and, with c1 != nullptr, separately by c1 into
 // the next region, base + group_bytes): a memset and three kernels (count,
 // scan, scatter) whatever the number of coordinates.

@@ -40,16 +40,15 @@ __global__ void group_count_kernel(const int32_t* __restrict__ c0, const int32_t
   }
 }
 
-// One CTA per coordinate: exclusive scan of the T + 1 counts into start (and
-// the cursors) in tiles of 4 entries per thread, start[T + 1] = the number of
-// grouped corners; the exponents e of the large groups.
+// One CTA: exclusive scan of the T + 1 counts of g into start (and the
+// cursors), plus `first`, in tiles of 4 entries per thread; start[T + 1] =
+// first + the number of grouped corners; the exponents e of the large groups.
 constexpr int kScanThreads = 1024;
-__global__ void __launch_bounds__(kScanThreads) group_scan_kernel(long long V, int T, int ny_pad, uint8_t* base) {
-  const Groups g = groups_at(base + blockIdx.x * group_bytes(V, T, ny_pad), T, ny_pad);
+__device__ void scan_groups(const Groups& g, int T, int ny_pad, int first) {
   const int n = T + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ int wsum[kScanThreads / 32];
-  int carry = 0;
+  int carry = first;
   for (int b0 = 0; b0 < n; b0 += 4 * kScanThreads) {
     const int i0 = b0 + 4 * (int)threadIdx.x;
     int4 c = make_int4(0, 0, 0, 0);
@@ -99,6 +98,41 @@ __global__ void __launch_bounds__(kScanThreads) group_scan_kernel(long long V, i
   }
 }
 
+// One CTA per coordinate.
+__global__ void __launch_bounds__(kScanThreads) group_scan_kernel(long long V, int T, int ny_pad, uint8_t* base) {
+  scan_groups(groups_at(base + blockIdx.x * group_bytes(V, T, ny_pad), T, ny_pad), T, ny_pad, 0);
+}
+
+// Batch: clip c = blockIdx.y groups its corners [offsets[c], offsets[c + 1])
+// by y into its own count/start/cursor rows; start values are positions in
+// the shared perm (the clip's corners fill [offsets[c], offsets[c + 1])).
+__global__ void batch_group_count_kernel(const int32_t* __restrict__ y, const int64_t* __restrict__ offsets, int n,
+                                         int T, int ny_pad, long long V, uint8_t* base) {
+  const int c = blockIdx.y;
+  const Groups g = groups_clip(base, T, ny_pad, n, c, V);
+  const long long v0 = offsets[c], v1 = offsets[c + 1];
+  for (long long v = v0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; v < v1; v += (long long)gridDim.x * blockDim.x) {
+    const int yv = __ldg(y + v);
+    if (yv >= 0 && yv <= T) atomicAdd(&g.cnt[yv], 1);
+  }
+}
+__global__ void __launch_bounds__(kScanThreads) batch_group_scan_kernel(const int64_t* __restrict__ offsets, int n,
+                                                                        int T, int ny_pad, long long V,
+                                                                        uint8_t* base) {
+  const int c = blockIdx.x;
+  scan_groups(groups_clip(base, T, ny_pad, n, c, V), T, ny_pad, (int)offsets[c]);
+}
+__global__ void batch_group_scatter_kernel(const int32_t* __restrict__ y, const int64_t* __restrict__ offsets, int n,
+                                           int T, int ny_pad, long long V, uint8_t* base) {
+  const int c = blockIdx.y;
+  const Groups g = groups_clip(base, T, ny_pad, n, c, V);
+  const long long v0 = offsets[c], v1 = offsets[c + 1];
+  for (long long v = v0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; v < v1; v += (long long)gridDim.x * blockDim.x) {
+    const int yv = __ldg(y + v);
+    if (yv >= 0 && yv <= T) g.perm[atomicAdd(&g.cur[yv], 1)] = (int)v;
+  }
+}
+
 __global__ void group_scatter_kernel(const int32_t* __restrict__ c0, const int32_t* __restrict__ c1, long long V,
                                      int T, int ny_pad, uint8_t* base) {
   const int32_t* c = blockIdx.y ? c1 : c0;
@@ -137,21 +171,23 @@ __device__ __forceinline__ int4 stage_corner(uint32_t xm, int sgn, int logQ) {
   return make_int4((int)u, level_offset(e, logQ), lq | ((sgn < 0 ? 1 : 0) << 8), 1 << lq);
 }
 
-// Units (64-y chunk, pass of 128 frequencies) in chunk-major order; CTA b takes
-// the contiguous range [b U / G, (b + 1) U / G), so a chunk's corners are
-// staged once for all its passes.  Thread (group q, frequency k) sums
-// s_v (cos, sin)(2 pi k x_v / T) over each group of its y octets, exactly.
+// Items (clip, 64-y chunk) are taken from a work counter (clips differ in
+// size by orders of magnitude, so a static split leaves CTAs idle); per item
+// the chunk's corners are staged once, then for every pass of 128 frequencies
+// thread (group q, frequency k) sums s_v (cos, sin)(2 pi k x_v / T) over each
+// group of its y octets, exactly.
 __global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* ws) {
   extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ int s_item;
   const int T = pl.T, K = pl.K, logQ = pl.logT - 2;
   int* lv = reinterpret_cast<int*>(sm);
   int4* vc = reinterpret_cast<int4*>(sm + align_up(axis_levels_ints(T) * 4, 16));
   int* soff = reinterpret_cast<int*>(vc + kHCache);
-  const Groups g = groups_at(ws + pl.off_ycnt, T, pl.ny_pad);
-  const int* perm = g.perm;
-  __half* Hhi = reinterpret_cast<__half*>(ws + pl.off_h);
-  __half* Hlo = Hhi + (size_t)pl.M2 * pl.ny_pad;
+  const int nclips = pl.batch ? pl.n_clips : 1;
+  __half* Hhi0 = reinterpret_cast<__half*>(ws + pl.off_h);
+  __half* Hlo0 = Hhi0 + (size_t)nclips * pl.M2 * pl.ny_pad;
   const uint32_t mask = (uint32_t)T - 1u;
+  unsigned* counter = reinterpret_cast<unsigned*>(ws + kSyncOffset) + 2;   // zeroed by the prep kernel
 
   // level 0 = the fixed-point quarter-wave table, then the decimated levels
   const int* tq = reinterpret_cast<const int*>(ws + pl.off_tab_fix);
@@ -160,87 +196,93 @@ __global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* w
   axis_build_levels(lv, T, pl.logT);
 
   const int q = threadIdx.x / kHF, t = threadIdx.x % kHF;
-  const int npass = (K + kHF - 1) / kHF;
-  const long long units = (long long)(pl.ny_pad / kHY) * npass;
-  const int u0 = (int)(units * blockIdx.x / gridDim.x), u1 = (int)(units * (blockIdx.x + 1) / gridDim.x);
+  const int npass = (K + kHF - 1) / kHF, nchunk = pl.ny_pad / kHY;
+  const long long nitems = (long long)nclips * nchunk;
   const float inv_q = ldexpf(1.f, -pl.fixq);
   // groups of up to this many corners sum in int32 (each term is at most 2^fixq)
   const int small_group = (1 << (31 - pl.fixq)) - 1;
-  int staged = -1, a = 0;
-  bool cached = false;
-  for (int unit = u0; unit < u1; ++unit) {
-    const int chunk = unit / npass, k = (unit % npass) * kHF + 1 + t;
+  for (;;) {
+    __syncthreads();   // the previous item's readers are done (and the levels are built)
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int cu = s_item;   // (clip, chunk)
+    if (cu >= nitems) break;
+    const int clip = cu / nchunk, chunk = cu % nchunk;
     const int y0 = chunk * kHY;
-    if (chunk != staged) {   // CTA-uniform
-      __syncthreads();       // the previous chunk's readers are done (and the levels are built)
-      a = g.start[min(y0, T + 1)];
-      const int b = g.start[min(y0 + kHY, T + 1)];
-      cached = b - a <= kHCache;
-      for (int i = threadIdx.x; i <= kHY; i += blockDim.x) soff[i] = g.start[min(y0 + i, T + 1)] - a;
-      if (cached)
-        for (int i = threadIdx.x; i < b - a; i += blockDim.x) {
-          const int v = perm[a + i];
-          vc[i] = stage_corner((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
-        }
-      __syncthreads();
-      staged = chunk;
-    }
-    if (k > K) continue;
-    for (int oc = q; oc < kHY / 8; oc += kHGroups) {
-      uint32_t hc[4], hs[4], lc[4], ls[4];
-#pragma unroll
-      for (int yy = 0; yy < 8; ++yy) {
-        const int y = oc * 8 + yy;
-        // one term s_v (cos, sin)(2 pi k x_v / T) of the fixed-point table
-        auto term = [&](int i, auto& ac_, auto& as_) {
-          int4 cn;
-          if (cached) {
-            cn = vc[i];
-          } else {
-            const int v = perm[a + i];
-            cn = stage_corner((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
-          }
-          const int lq = cn.z & 0xFF, Q = cn.w;
-          const uint32_t sf = (uint32_t)cn.z >> 8;
-          const uint32_t p = ((uint32_t)k * (uint32_t)cn.x) & (4u * (uint32_t)Q - 1u);
-          const uint32_t qd = p >> lq, r = p & (uint32_t)(Q - 1);
-          const bool odd = qd & 1u;
-          const int* L = lv + cn.y;
-          const int c = L[odd ? Q - r : r], sn = L[odd ? r : Q - r];
-          // cos < 0 in quadrants 1, 2; sin < 0 in quadrants 2, 3; s = -1 flips both
-          ac_ += ((((qd + 1u) >> 1) & 1u) ^ sf) ? -c : c;
-          as_ += ((qd >> 1) ^ sf) ? -sn : sn;
-        };
-        long long ac = 0, as = 0;
-        if (soff[y + 1] - soff[y] <= small_group) {   // warp-uniform: |sum| < 2^31 in int32
-          int ac32 = 0, as32 = 0;
-          for (int i = soff[y]; i < soff[y + 1]; ++i) term(i, ac32, as32);
-          ac = ac32;
-          as = as32;
-        } else {
-          for (int i = soff[y]; i < soff[y + 1]; ++i) term(i, ac, as);
-        }
-        const float sc = ldexpf(inv_q, -(int)g.ey[y0 + y]);
-        const float fc = __ll2float_rn(ac) * sc, fs = __ll2float_rn(as) * sc;
-        const __half c_hi = __float2half_rn(fc), s_hi = __float2half_rn(fs);
-        const __half c_lo = __float2half_rn(fc - __half2float(c_hi)), s_lo = __float2half_rn(fs - __half2float(s_hi));
-        uint16_t u;
-        const int sh = 16 * (yy & 1);
-        memcpy(&u, &c_hi, 2);
-        hc[yy >> 1] = (yy & 1 ? hc[yy >> 1] : 0u) | ((uint32_t)u << sh);
-        memcpy(&u, &s_hi, 2);
-        hs[yy >> 1] = (yy & 1 ? hs[yy >> 1] : 0u) | ((uint32_t)u << sh);
-        memcpy(&u, &c_lo, 2);
-        lc[yy >> 1] = (yy & 1 ? lc[yy >> 1] : 0u) | ((uint32_t)u << sh);
-        memcpy(&u, &s_lo, 2);
-        ls[yy >> 1] = (yy & 1 ? ls[yy >> 1] : 0u) | ((uint32_t)u << sh);
+    const Groups g = pl.batch ? groups_clip(ws + pl.off_ycnt, T, pl.ny_pad, nclips, clip, pl.V)
+                              : groups_at(ws + pl.off_ycnt, T, pl.ny_pad);
+    const int* perm = g.perm;
+    __half* Hhi = Hhi0 + (size_t)clip * pl.M2 * pl.ny_pad;
+    __half* Hlo = Hlo0 + (size_t)clip * pl.M2 * pl.ny_pad;
+    const int a = g.start[min(y0, T + 1)];
+    const int b = g.start[min(y0 + kHY, T + 1)];
+    const bool cached = b - a <= kHCache;
+    for (int i = threadIdx.x; i <= kHY; i += blockDim.x) soff[i] = g.start[min(y0 + i, T + 1)] - a;
+    if (cached)
+      for (int i = threadIdx.x; i < b - a; i += blockDim.x) {
+        const int v = perm[a + i];
+        vc[i] = stage_corner((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
       }
-      // rows 2(k-1) (cos) and 2(k-1)+1 (sin), columns y0 + 8 oc .. + 8
-      const size_t rc = (size_t)(2 * (k - 1)) * pl.ny_pad + y0 + 8 * oc, rs = rc + pl.ny_pad;
-      *reinterpret_cast<uint4*>(Hhi + rc) = make_uint4(hc[0], hc[1], hc[2], hc[3]);
-      *reinterpret_cast<uint4*>(Hhi + rs) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
-      *reinterpret_cast<uint4*>(Hlo + rc) = make_uint4(lc[0], lc[1], lc[2], lc[3]);
-      *reinterpret_cast<uint4*>(Hlo + rs) = make_uint4(ls[0], ls[1], ls[2], ls[3]);
+    __syncthreads();
+    for (int pass = 0; pass < npass; ++pass) {
+      const int k = pass * kHF + 1 + t;
+      if (k > K) continue;
+      for (int oc = q; oc < kHY / 8; oc += kHGroups) {
+        uint32_t hc[4], hs[4], lc[4], ls[4];
+  #pragma unroll
+        for (int yy = 0; yy < 8; ++yy) {
+          const int y = oc * 8 + yy;
+          // one term s_v (cos, sin)(2 pi k x_v / T) of the fixed-point table
+          auto term = [&](int i, auto& ac_, auto& as_) {
+            int4 cn;
+            if (cached) {
+              cn = vc[i];
+            } else {
+              const int v = perm[a + i];
+              cn = stage_corner((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
+            }
+            const int lq = cn.z & 0xFF, Q = cn.w;
+            const uint32_t sf = (uint32_t)cn.z >> 8;
+            const uint32_t p = ((uint32_t)k * (uint32_t)cn.x) & (4u * (uint32_t)Q - 1u);
+            const uint32_t qd = p >> lq, r = p & (uint32_t)(Q - 1);
+            const bool odd = qd & 1u;
+            const int* L = lv + cn.y;
+            const int c = L[odd ? Q - r : r], sn = L[odd ? r : Q - r];
+            // cos < 0 in quadrants 1, 2; sin < 0 in quadrants 2, 3; s = -1 flips both
+            ac_ += ((((qd + 1u) >> 1) & 1u) ^ sf) ? -c : c;
+            as_ += ((qd >> 1) ^ sf) ? -sn : sn;
+          };
+          long long ac = 0, as = 0;
+          if (soff[y + 1] - soff[y] <= small_group) {   // warp-uniform: |sum| < 2^31 in int32
+            int ac32 = 0, as32 = 0;
+            for (int i = soff[y]; i < soff[y + 1]; ++i) term(i, ac32, as32);
+            ac = ac32;
+            as = as32;
+          } else {
+            for (int i = soff[y]; i < soff[y + 1]; ++i) term(i, ac, as);
+          }
+          const float sc = ldexpf(inv_q, -(int)g.ey[y0 + y]);
+          const float fc = __ll2float_rn(ac) * sc, fs = __ll2float_rn(as) * sc;
+          const __half c_hi = __float2half_rn(fc), s_hi = __float2half_rn(fs);
+          const __half c_lo = __float2half_rn(fc - __half2float(c_hi)), s_lo = __float2half_rn(fs - __half2float(s_hi));
+          uint16_t u;
+          const int sh = 16 * (yy & 1);
+          memcpy(&u, &c_hi, 2);
+          hc[yy >> 1] = (yy & 1 ? hc[yy >> 1] : 0u) | ((uint32_t)u << sh);
+          memcpy(&u, &s_hi, 2);
+          hs[yy >> 1] = (yy & 1 ? hs[yy >> 1] : 0u) | ((uint32_t)u << sh);
+          memcpy(&u, &c_lo, 2);
+          lc[yy >> 1] = (yy & 1 ? lc[yy >> 1] : 0u) | ((uint32_t)u << sh);
+          memcpy(&u, &s_lo, 2);
+          ls[yy >> 1] = (yy & 1 ? ls[yy >> 1] : 0u) | ((uint32_t)u << sh);
+        }
+        // rows 2(k-1) (cos) and 2(k-1)+1 (sin), columns y0 + 8 oc .. + 8
+        const size_t rc = (size_t)(2 * (k - 1)) * pl.ny_pad + y0 + 8 * oc, rs = rc + pl.ny_pad;
+        *reinterpret_cast<uint4*>(Hhi + rc) = make_uint4(hc[0], hc[1], hc[2], hc[3]);
+        *reinterpret_cast<uint4*>(Hhi + rs) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
+        *reinterpret_cast<uint4*>(Hlo + rc) = make_uint4(lc[0], lc[1], lc[2], lc[3]);
+        *reinterpret_cast<uint4*>(Hlo + rs) = make_uint4(ls[0], ls[1], ls[2], ls[3]);
+      }
     }
   }
 }
@@ -314,6 +356,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
   const int y0 = blockIdx.y * (int)pl.split_len;
   const int y1 = min(pl.ny_pad, y0 + (int)pl.split_len);
   const int nch = max(0, (y1 - y0) / 64);
+  const int clip = blockIdx.z;   // batch: the clip; 0 for a single clip
 
   if (tid == kGGen + 32) {
     for (int i = 0; i < kGS; ++i) {
@@ -356,9 +399,10 @@ __global__ void __launch_bounds__(kGThreads, 1)
         if (!mbar_wait(&empty[s], ph ^ 1u, st, 60)) break;
         uint8_t* at = ops + (size_t)s * kGStage;
         mbar_arrive_expect_tx(&tfull[s], 2u * kGTile);
-        // rows past 2K read as zeros
-        tma_load_2dh(at, &hhi, y0 + j * 64, tm * 128, &tfull[s]);
-        tma_load_2dh(at + kGTile, &hlo, y0 + j * 64, tm * 128, &tfull[s]);
+        // rows past the last clip's 2K read as zeros; a tile's rows past 2K of
+        // another clip only feed partial rows that are never stored
+        tma_load_2dh(at, &hhi, y0 + j * 64, clip * pl.M2 + tm * 128, &tfull[s]);
+        tma_load_2dh(at + kGTile, &hlo, y0 + j * 64, clip * pl.M2 + tm * 128, &tfull[s]);
       }
       for (int q = max(0, j - kGS); q < j; ++q) mbar_wait(&tfull[q % kGS], (uint32_t)(q / kGS) & 1u, st, 61);
     }
@@ -401,7 +445,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const uint32_t f0 = (uint32_t)(tn * 128 + (int)rank * 64 + 1 + i0);
     const uint32_t mask = (uint32_t)pl.T - 1u;
     const uint32_t ops_a = smem_u32(ops);
-    const Groups yg = groups_at(ws + pl.off_ycnt, pl.T, pl.ny_pad);
+    const Groups yg = pl.batch ? groups_clip(ws + pl.off_ycnt, pl.T, pl.ny_pad, pl.n_clips, clip, pl.V)
+                               : groups_at(ws + pl.off_ycnt, pl.T, pl.ny_pad);
     uint32_t xo[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) xo[c] = (uint32_t)((oct ^ c) << 4);
@@ -466,7 +511,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
       const int M2 = pl.M2;
       const int row0 = warp * 32;
       const uint32_t tr = smem_u32(ops) + (uint32_t)warp * (32u * 36u * 4u);
-      float* P = reinterpret_cast<float*>(ws + pl.off_part) + (size_t)blockIdx.y * M2 * M2;
+      float* P = reinterpret_cast<float*>(ws + pl.off_part) + ((size_t)clip * pl.splits + blockIdx.y) * M2 * M2;
 #pragma unroll 1
       for (int cb = 0; cb < 8; ++cb) {
         const int n0 = tn * 256 + cb * 32;
@@ -557,23 +602,41 @@ cudaError_t launch_hybrid(const Plan& pl, void* ws_, cudaStream_t st) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = launch_grouping(pl.vy, nullptr, pl.V, pl.T, pl.ny_pad, ws + pl.off_ycnt, st);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  const int nclips = pl.batch ? pl.n_clips : 1;
+  if (pl.batch) {
+    // per clip: counts, scan (one CTA per clip), scatter
+    if ((e = cudaMemsetAsync(ws + pl.off_ycnt, 0, (size_t)nclips * group_stride(pl.T) * 4, st)) != cudaSuccess)
+      return e;
+    const long long per_clip = (pl.V + nclips - 1) / nclips;
+    const int bx = (int)std::max<long long>(1, std::min<long long>((per_clip + 255) / 256, 64));
+    batch_group_count_kernel<<<dim3(bx, nclips), 256, 0, st>>>(pl.vy, pl.offsets, nclips, pl.T, pl.ny_pad, pl.V,
+                                                              ws + pl.off_ycnt);
+    batch_group_scan_kernel<<<nclips, kScanThreads, 0, st>>>(pl.offsets, nclips, pl.T, pl.ny_pad, pl.V,
+                                                            ws + pl.off_ycnt);
+    batch_group_scatter_kernel<<<dim3(bx, nclips), 256, 0, st>>>(pl.vy, pl.offsets, nclips, pl.T, pl.ny_pad, pl.V,
+                                                                ws + pl.off_ycnt);
+    count_launch(3);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if ((e = launch_grouping(pl.vy, nullptr, pl.V, pl.T, pl.ny_pad, ws + pl.off_ycnt, st)) != cudaSuccess) {
+    return e;
+  }
   const size_t hs = hyb_h_smem(pl.T);
   if ((e = ensure_smem(reinterpret_cast<const void*>(hyb_h_kernel), hs)) != cudaSuccess) return e;
-  const long long hunits = (long long)(pl.ny_pad / kHY) * ((pl.K + kHF - 1) / kHF);
-  hyb_h_kernel<<<(int)std::min<long long>(hunits, sms), kHThreads, hs, st>>>(pl, ws);
+  const long long hitems = (long long)nclips * (pl.ny_pad / kHY);
+  hyb_h_kernel<<<(int)std::min<long long>(hitems, sms), kHThreads, hs, st>>>(pl, ws);
   count_launch(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
   const __half* h = reinterpret_cast<const __half*>(ws + pl.off_h);
   CUtensorMap mhi, mlo;
-  if (!encode_f16_2d_sw128(&mhi, h, pl.ny_pad, pl.M2, 64, 128) ||
-      !encode_f16_2d_sw128(&mlo, h + (size_t)pl.M2 * pl.ny_pad, pl.ny_pad, pl.M2, 64, 128))
+  const uint64_t hrows = (uint64_t)nclips * pl.M2;   // clips stacked: row clip 2K + r
+  if (!encode_f16_2d_sw128(&mhi, h, pl.ny_pad, hrows, 64, 128) ||
+      !encode_f16_2d_sw128(&mlo, h + (size_t)hrows * pl.ny_pad, pl.ny_pad, hrows, 64, 128))
     return cudaErrorInvalidValue;
   if ((e = ensure_smem(reinterpret_cast<const void*>(hyb_gemm_kernel), kGSmem)) != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(pl.tiles_m * pl.tiles_n), (unsigned)pl.splits);
+  cfg.gridDim = dim3((unsigned)(pl.tiles_m * pl.tiles_n), (unsigned)pl.splits, (unsigned)nclips);
   cfg.blockDim = dim3(kGThreads);
   cfg.dynamicSmemBytes = kGSmem;
   cfg.stream = st;

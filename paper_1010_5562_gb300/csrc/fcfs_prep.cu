@@ -38,6 +38,7 @@ __global__ void prep_kernel(Plan pl, uint8_t* ws, int validate) {
     unsigned* sync = reinterpret_cast<unsigned*>(ws + kSyncOffset);
     sync[0] = 0;
     sync[1] = 0;
+    sync[2] = 0;   // work counter of the grouped contraction's H kernel
   }
   long long* acc = reinterpret_cast<long long*>(ws + pl.off_axis);
   const long long nclips = pl.batch ? pl.n_clips : 1;
@@ -169,7 +170,10 @@ __global__ void __launch_bounds__(kAxisThreads) axis_dft_kernel(Plan pl, uint8_t
     if (wx == 0 && wy == 0) continue;          // block-uniform
     if (blockIdx.x == 0 && threadIdx.x == 0) area += (long long)n * wx;
     if (k > pl.K) continue;
-    axis_bin_add(lv, T, logQ, k, n, wx, wy, a0, a1, a2, a3);
+    if (fits_i32(wx) && fits_i32(wy))   // block-uniform
+      axis_bin_add<true>(lv, T, logQ, k, n, wx, wy, a0, a1, a2, a3);
+    else
+      axis_bin_add(lv, T, logQ, k, n, wx, wy, a0, a1, a2, a3);
   }
   }
   long long* acc = reinterpret_cast<long long*>(ws + pl.off_axis) + (size_t)clip * (4 * pl.K + 1);
@@ -223,14 +227,14 @@ __global__ void reduce_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, long
   }
   const int M2 = pl.M2;
   const float* P = reinterpret_cast<const float*>(ws + pl.off_part);
-  // where split sp of entry (k, l) lives: single clip, P[sp][m][n]; batch,
-  // the unit's own bm x bn tile
+  // where split sp of entry (k, l) lives: single clip, P[sp][m][n]; grouped
+  // batch, P[clip][sp][m][n]; batch, the unit's own bm x bn tile
   const int m = 2 * (k - 1), n = 2 * (l - 1);
   size_t base, stride, ld;
   int S;
-  if (!pl.batch) {
+  if (!pl.batch || pl.hyb) {
     S = pl.splits;
-    base = (size_t)m * M2 + n;
+    base = ((size_t)clip * S * M2 + m) * M2 + n;
     stride = (size_t)M2 * M2;
     ld = M2;
   } else {
@@ -279,7 +283,10 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
   }
   const int kblocks = (pl.K + kAxisThreads - 1) / kAxisThreads;
   const int clips = pl.batch ? pl.n_clips : 1;
-  const long long want = std::max(1LL, (long long)(2 * sms) / ((long long)kblocks * clips));
+  // blocks per SM to aim for: many when the level tables are small (each
+  // block builds its own), two for the 128 KB tables of large periods
+  const long long per_sm = pl.T <= 8192 ? 16 : 2;
+  const long long want = std::max(1LL, per_sm * sms / ((long long)kblocks * clips));
   const int nper = (int)std::max(64LL, (pl.T + 1 + want - 1) / want);
   const int nblocks = (pl.T + 1 + nper - 1) / nper;
   const size_t smem = axis_smem_bytes(pl.T, pl.full);

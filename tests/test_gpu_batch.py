@@ -122,3 +122,66 @@ def test_autotune_cache(fc, tmp_path, monkeypatch):
     assert autotune.tune_batch(x, y, s, off, clips[0].T, 40) == uc   # served from the cache
     sp = autotune.tune_forward(x[:clips[0].V], y[:clips[0].V], s[:clips[0].V], clips[0].T, 40, reps=1)
     assert sp in autotune.SPLIT_CANDIDATES
+
+
+def run_batch_mode(fc, clips, K, mode):
+    fc.set_hybrid(mode)   # the batch sizes its workspace inside the call
+    try:
+        return run_batch(fc, clips, K, "split_f16")
+    finally:
+        fc.set_hybrid(1)
+
+
+@pytest.mark.parametrize("K", [128, 129, 200])
+def test_grouped_batch_against_oracle(fc, K):
+    """Each clip's corners grouped by y and contracted over its T + 1 values of y
+    (one launch per stage for the whole batch), forced on the small batch: an
+    empty clip, a one-polygon clip, ragged 2K."""
+    clips = small_batch()
+    F, area = run_batch_mode(fc, clips, K, 2)
+    for c, clip in enumerate(clips):
+        if clip.V == 0:
+            assert area[c] == 0 and not np.any(F[c])
+        else:
+            check_clip(F[c], area[c], clip, K, "split_f16")
+
+
+def test_grouped_batch_matches_direct(fc):
+    """24 clips of workload 3 (T=2048, K=128): grouped and direct (unit-list)
+    batches agree to FP32 rounding; repeated grouped calls are bit-identical."""
+    clips, K = batch_clips(n_clips=24)
+    Fg, ag = run_batch_mode(fc, clips, K, 2)
+    Fg2, _ = run_batch_mode(fc, clips, K, 2)
+    Fd, ad = run_batch_mode(fc, clips, K, 0)
+    assert np.array_equal(Fg, Fg2)
+    assert np.array_equal(ag, ad)
+    for c, clip in enumerate(clips):
+        A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+        assert np.max(np.abs(Fg[c] - Fd[c])) / A <= 2e-6
+
+
+def test_grouped_batch_in_cuda_graph(fc):
+    clips = small_batch()
+    x, y, s, off = (torch.from_numpy(a).cuda() for a in concat_clips(clips))
+    K, T = 128, clips[0].T
+    W = 2 * K + 1
+    F = torch.empty((len(clips), W, W), dtype=torch.complex64, device="cuda")
+    area = torch.empty((len(clips),), dtype=torch.int64, device="cuda")
+    fc.set_hybrid(2)
+    try:
+        ws = torch.empty(fc._lib.load().fcfs_batch_workspace_size(x.numel(), len(clips), T, K, 1),
+                         dtype=torch.uint8, device="cuda")
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            fc.batch(x, y, s, off, T, K, out=F, area_out=area, workspace=ws, stream=st)   # warm-up
+        torch.cuda.synchronize()
+        ref = F.clone()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            fc.batch(x, y, s, off, T, K, out=F, area_out=area, workspace=ws, stream=st)
+        F.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+    finally:
+        fc.set_hybrid(1)
+    assert torch.equal(F, ref)
