@@ -157,6 +157,7 @@ fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
 }
 
 int hybrid_mode() { return g_hybrid; }
+bool pair_enabled() { return g_pair != 0; }
 
 // Row-binned contraction (corners grouped by y, contraction over the T + 1
 // values of y): eligible for a single-clip split-FP16 call on CTA pairs; taken

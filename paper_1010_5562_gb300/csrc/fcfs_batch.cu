@@ -67,14 +67,21 @@ static fcfs_status make_batch_plan(int64_t V, int32_t n, int32_t T, int32_t K, i
   }
   const int chunks = g_unit_chunks > 0 ? g_unit_chunks : 4096 / pl.chunk;
   pl.unit_vertices = (int64_t)chunks * pl.chunk;
-  const long long tiles = (long long)pl.tiles_m * pl.tiles_n;
+  // split FP16 with 2K >= 256: units on CTA pairs (256 x 256 tiles, 2-SM MMA)
+  if (prec == FCFS_PREC_SPLIT_F16 && pl.M2 >= 256 && pair_enabled()) {
+    pl.pair = 1;
+    pl.bn = 256;
+    pl.tiles_n = (pl.M2 + 255) / 256;
+    pl.tiles_m = 2 * pl.tiles_n;
+  }
+  const long long tiles = pl.pair ? (long long)pl.tiles_n * pl.tiles_n : (long long)pl.tiles_m * pl.tiles_n;
   const long long units_max = tiles * ((V + pl.unit_vertices - 1) / pl.unit_vertices + n);
-  if (units_max >= (1LL << 31)) return FCFS_EUNSUPPORTED;
-  pl.splits = (int)units_max;   // grid of the contraction kernel
+  if (units_max >= (1LL << 30)) return FCFS_EUNSUPPORTED;
+  pl.splits = (int)units_max;   // unit slots of the contraction kernel (CTA pairs: 2 CTAs each)
   pl.off_units = o;
   o = align_up(o + (size_t)(n + 1) * sizeof(int), kWsAlign);
   pl.off_part = o;
-  o = align_up(o + (size_t)units_max * pl.bm * pl.bn * sizeof(float), kWsAlign);
+  o = align_up(o + (size_t)units_max * (pl.pair ? 2 : 1) * pl.bm * pl.bn * sizeof(float), kWsAlign);
   pl.total = o;
   return FCFS_OK;
 }
@@ -82,7 +89,7 @@ static fcfs_status make_batch_plan(int64_t V, int32_t n, int32_t T, int32_t K, i
 // unit_start[c] = sum over clips c' < c of tiles * ceil(V_c' / U); unit_start[n] = total
 __global__ void __launch_bounds__(1024) batch_units_kernel(Plan pl, uint8_t* ws) {
   int* ustart = reinterpret_cast<int*>(ws + pl.off_units);
-  const int n = pl.n_clips, tiles = pl.tiles_m * pl.tiles_n;
+  const int n = pl.n_clips, tiles = pl.pair ? pl.tiles_n * pl.tiles_n : pl.tiles_m * pl.tiles_n;
   const int per = (n + blockDim.x - 1) / blockDim.x;
   const int c0 = min(n, (int)threadIdx.x * per), c1 = min(n, c0 + per);
   auto units = [&](int c) {

@@ -100,8 +100,10 @@ __device__ inline Unit unit_of_block(const Plan& pl, uint8_t* ws, int bm, int bn
     u.clip = 0;
     return u;
   }
+  // batch on CTA pairs: blockIdx.x = 2 unit + rank, the unit's tile is a
+  // 256 x 256 pair tile of which rank r holds rows [128 r, 128 r + 128)
   const int* ustart = reinterpret_cast<const int*>(ws + pl.off_units);
-  const int uid = blockIdx.x;
+  const int uid = pl.pair ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   u.live = uid < ustart[pl.n_clips];
   if (!u.live) return u;
   int lo = 0, hi = pl.n_clips;   // last clip c with ustart[c] <= uid
@@ -115,12 +117,19 @@ __device__ inline Unit unit_of_block(const Plan& pl, uint8_t* ws, int bm, int bn
   const int S = (int)((cv1 - cv0 + pl.unit_vertices - 1) / pl.unit_vertices);
   const int r = uid - ustart[c];
   const int tile = r / S, sp = r % S;
-  u.tm = tile / pl.tiles_n;
-  u.tn = tile % pl.tiles_n;
   u.v0 = cv0 + (long long)sp * pl.unit_vertices;
   u.v1 = min(cv1, u.v0 + pl.unit_vertices);
   u.ld = bn;
-  u.P = part + (size_t)uid * bm * bn;
+  if (pl.pair) {
+    const int rank = (int)(blockIdx.x & 1u);   // the cluster is (2, 1, 1)
+    u.tm = 2 * (tile / pl.tiles_n) + rank;
+    u.tn = tile % pl.tiles_n;
+    u.P = part + (size_t)uid * (2 * bm) * bn + (size_t)rank * bm * bn;
+  } else {
+    u.tm = tile / pl.tiles_n;
+    u.tn = tile % pl.tiles_n;
+    u.P = part + (size_t)uid * bm * bn;
+  }
   return u;
 }
 
@@ -486,6 +495,8 @@ struct AdjTcArgs {
 };
 // Row-binned (grouped) mode of the forward and adjoint calls: 0 never, 1 automatic, 2 forced
 int hybrid_mode();
+// CTA pairs for 2K >= 256 on the split-FP16 path (fcfs_debug_set_pair)
+bool pair_enabled();
 cudaError_t launch_adj_tc(const AdjTcArgs& ar, const CUtensorMap& mhi, const CUtensorMap& mlo, void* ws,
                           cudaStream_t st);
 // Row-binned contraction (fcfs_hybrid.cu): grouping, H, and the contraction

@@ -241,10 +241,11 @@ __global__ void reduce_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, long
     const int* ustart = reinterpret_cast<const int*>(ws + pl.off_units);
     const long long vc = pl.offsets[clip + 1] - pl.offsets[clip];
     S = (int)((vc + pl.unit_vertices - 1) / pl.unit_vertices);
-    const int tm = m / pl.bm, tn = n / pl.bn;
+    const int bmu = pl.pair ? 2 * pl.bm : pl.bm;   // a unit's tile: one CTA's, or a pair's
+    const int tm = m / bmu, tn = n / pl.bn;
     const size_t u0 = (size_t)ustart[clip] + (size_t)(tm * pl.tiles_n + tn) * S;
-    base = u0 * pl.bm * pl.bn + (size_t)(m - tm * pl.bm) * pl.bn + (n - tn * pl.bn);
-    stride = (size_t)pl.bm * pl.bn;
+    base = u0 * bmu * pl.bn + (size_t)(m - tm * bmu) * pl.bn + (n - tn * pl.bn);
+    stride = (size_t)bmu * pl.bn;
     ld = pl.bn;
   }
   quad_entry<false>(pl, P, base, stride, ld, S, F, k, l);

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, PAIR>::kThreads, 1)
   // pair rank (0 issues the MMAs) and, for a pair, the 128-row half it holds:
   // blockIdx.x = 2 (pair tile) + rank, pair tile = (row pair tm/2, column tile tn)
   const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
-  if (PAIR) {
+  if (PAIR && !pl.batch) {   // a batch unit already names its pair tile (unit_of_block)
     const int ptile = blockIdx.x >> 1;
     U.tm = 2 * (ptile / pl.tiles_n) + (int)rank;
     U.tn = ptile % pl.tiles_n;
@@ -560,7 +560,7 @@ static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cud
   auto kern = gemm_tc_kernel<BN, STAGES, FULL, PAIR>;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
-  dim3 grid = pl.batch ? dim3(pl.splits, 1) : dim3(pl.tiles_m * pl.tiles_n, pl.splits);
+  dim3 grid = pl.batch ? dim3(PAIR ? 2 * pl.splits : pl.splits, 1) : dim3(pl.tiles_m * pl.tiles_n, pl.splits);
   // The kernel may start while the previous kernel of the stream finishes
   // (programmatic stream serialisation; it waits for it in griddep_wait()).
   // The fused tail waits at a grid barrier, so every CTA must be resident:
