@@ -79,6 +79,29 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Packed FP32 pairs (Blackwell f32x2): d = a * b + c and d = a * b elementwise,
+// each element rounded as its scalar counterpart.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+// One angle-addition step (c, s) -> (c w.x - s w.y, s w.x + c w.y) in two packed operations.
+__device__ __forceinline__ float2 rot2(float2 v, float2 w) {
+  return ffma2(make_float2(v.y, v.x), make_float2(-w.y, w.y), fmul2(v, make_float2(w.x, w.x)));
+}
+
 // Two-level sincos table: (cos, sin)(2 pi p / T) = coarse[p >> f] * fine[p mod 2^f],
 // both factors correctly rounded FP32 values copied from the plan's table.
 struct TwoLevel {
@@ -289,9 +312,10 @@ __global__ void __launch_bounds__(kThreadsA, 1)
     const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(accfull, 0, st, 46) ? 1 : 0) != 0;
     tc_fence_after();
     if constexpr (GROUPED) {
-      // (1) Z[r, b] -> shared memory zs[r][b - b0] with the row scale and the
-      // side terms; the operand stages are free: the last MMA has completed
-      float* zs = reinterpret_cast<float*>(ops);
+      // (1) Z[r, b] -> shared memory zs[f][b - b0] = (cos row 2f, sin row 2f + 1)
+      // with the row scale and the side terms; the operand stages are free:
+      // the last MMA has completed
+      float2* zs = reinterpret_cast<float2*>(ops);
       const float fb = (float)b;
       const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
       for (int cb = 0; cb < kRH; cb += 32) {
@@ -306,10 +330,11 @@ __global__ void __launch_bounds__(kThreadsA, 1)
           for (int i = 0; i < 32; ++i) d1[i] = d2[i] = 0u;
         }
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float4 qr = rows[n0 + i];
-          zs[(n0 + i) * kVP + cidx] =
-              fmaf(__uint_as_float(d1[i]) + __uint_as_float(d2[i]), qr.x, fmaf(qr.z, fb, qr.y));
+        for (int i = 0; i < 32; i += 2) {
+          const float4 q0 = rows[n0 + i], q1 = rows[n0 + i + 1];
+          zs[((n0 + i) / 2) * kVP + cidx] =
+              make_float2(fmaf(__uint_as_float(d1[i]) + __uint_as_float(d2[i]), q0.x, fmaf(q0.z, fb, q0.y)),
+                          fmaf(__uint_as_float(d1[i + 1]) + __uint_as_float(d2[i + 1]), q1.x, fmaf(q1.z, fb, q1.y)));
         }
       }
       comb[g * kVP + cidx] = acc0;   // the k = 0 row's two column halves (row tile 0)
@@ -331,39 +356,32 @@ __global__ void __launch_bounds__(kThreadsA, 1)
           sc[i] = make_int4(vv, __ldg(cap + vv), __ldg(cbp + vv) - b0, 0);
         }
         asm volatile("bar.sync 1, %0;" ::"n"(kGen) : "memory");
-        // two corners per thread at a time, separate cos and sin sums: four
-        // independent FMA chains and two angle-addition chains
+        // two corners per thread at a time; a frequency's (cos, sin) pair is
+        // one packed FMA into a (cos, sin) sum and two packed operations of
+        // angle addition
         for (int i = tid; i < pn; i += 2 * kGen) {
           const bool two = i + kGen < pn;
           const int4 e0 = sc[i], e1 = two ? sc[i + kGen] : e0;
           const uint32_t a0 = (uint32_t)e0.y, a1 = (uint32_t)e1.y;
           const int bl0 = e0.z, bl1 = e1.z;
-          float c0s = 0.f, s0s = 0.f, c1s = 0.f, s1s = 0.f;
+          float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
           const float2 w0 = tl_lookup(tl, a0 & mask), w1 = tl_lookup(tl, a1 & mask);
           for (int f = 0; f < kRH; f += 8) {   // runs of 8 frequencies = 16 tile rows
-            const float2 n0 = tl_lookup(tl, (uint32_t)(kb + f) * a0 & mask);
-            const float2 n1 = tl_lookup(tl, (uint32_t)(kb + f) * a1 & mask);
-            float ca = n0.x, sa = n0.y, cb2 = n1.x, sb2 = n1.y;
+            float2 v0 = tl_lookup(tl, (uint32_t)(kb + f) * a0 & mask);
+            float2 v1 = tl_lookup(tl, (uint32_t)(kb + f) * a1 & mask);
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-              const int r = 2 * (f + t);
-              c0s = fmaf(ca, zs[r * kVP + bl0], c0s);
-              s0s = fmaf(sa, zs[(r + 1) * kVP + bl0], s0s);
-              c1s = fmaf(cb2, zs[r * kVP + bl1], c1s);
-              s1s = fmaf(sb2, zs[(r + 1) * kVP + bl1], s1s);
-              const float ca1 = fmaf(ca, w0.x, -(sa * w0.y)), sa1 = fmaf(sa, w0.x, ca * w0.y);
-              const float cb1 = fmaf(cb2, w1.x, -(sb2 * w1.y)), sb1 = fmaf(sb2, w1.x, cb2 * w1.y);
-              ca = ca1;
-              sa = sa1;
-              cb2 = cb1;
-              sb2 = sb1;
+              s0 = ffma2(v0, zs[(f + t) * kVP + bl0], s0);
+              s1 = ffma2(v1, zs[(f + t) * kVP + bl1], s1);
+              v0 = rot2(v0, w0);
+              v1 = rot2(v1, w1);
             }
           }
           const float k00 = krow ? comb[bl0] + comb[kVP + bl0] + fmaf(m0b, (float)(b0 + bl0), m01) : 0.f;
-          part[e0.x] = k00 + (c0s + s0s);
+          part[e0.x] = k00 + (s0.x + s0.y);
           if (two) {
             const float k01 = krow ? comb[bl1] + comb[kVP + bl1] + fmaf(m0b, (float)(b0 + bl1), m01) : 0.f;
-            part[e1.x] = k01 + (c1s + s1s);
+            part[e1.x] = k01 + (s1.x + s1.y);
           }
         }
       }
