@@ -309,18 +309,10 @@ __device__ __forceinline__ void k_bin_add(const KLevel& kl, int n, long long wx,
   int c = kl.L[qd.i1], sn = kl.L[qd.i2];
   if (qd.cneg) c = -c;
   if (qd.sneg) sn = -sn;
-  if (fits_i32(wx) && fits_i32(wy)) {   // one 32 x 32 -> 64-bit multiply per product
-    const int x32 = (int)wx, y32 = (int)wy;
-    a0 += (long long)c * x32;
-    a1 += (long long)sn * x32;
-    a2 += (long long)c * y32;
-    a3 += (long long)sn * y32;
-  } else {
-    a0 += (long long)c * wx;
-    a1 += (long long)sn * wx;
-    a2 += (long long)c * wy;
-    a3 += (long long)sn * wy;
-  }
+  a0 += (long long)c * wx;
+  a1 += (long long)sn * wx;
+  a2 += (long long)c * wy;
+  a3 += (long long)sn * wy;
 }
 
 __device__ inline void fused_tail(const Plan& pl, uint8_t* ws, uint8_t* smem, int* sflag, uint64_t* bar_axis,
