@@ -51,7 +51,8 @@ constexpr int kStage = 4 * kTile;         // corners hi, lo (generated), coeffic
 constexpr int kStages = 3;
 constexpr int kOps = kStages * kStage;
 constexpr int kTlMax = 512;               // two-level table entries for T <= 2^16
-constexpr size_t kAdjSmem = 1024 + kOps + kTlMax * 8 + kAdjPairRows * 16 + 2 * kVP * 4 + 256;
+constexpr int kM0Cache = 2048;            // k = 0 row columns kept in shared memory (2K <= 2048)
+constexpr size_t kAdjSmem = 1024 + kOps + kTlMax * 8 + kAdjPairRows * 16 + 2 * kVP * 4 + kM0Cache * 4 + 256;
 // grouped epilogue: Z [256 rows][128 b] FP32 and staged corners in the operand stages
 constexpr int kZBytes = kAdjPairRows * kVP * 4;
 constexpr int kCornerCache = (kOps - kZBytes) / 16;
@@ -126,9 +127,11 @@ __global__ void __launch_bounds__(kThreadsA, 1)
   float2* tlt = reinterpret_cast<float2*>(sm + kOps);
   float4* rows = reinterpret_cast<float4*>(tlt + kTlMax);        // this pair's 256 row terms
   float* comb = reinterpret_cast<float*>(rows + kAdjPairRows);   // [2][kVP]: column halves of each corner
-  uint64_t* ofull = reinterpret_cast<uint64_t*>(comb + 2 * kVP); // [kStages] rank 0: chunk ready in both CTAs
+  float* m0s = comb + 2 * kVP;                                    // [kM0Cache]: the k = 0 row (row tile 0)
+  uint64_t* ofull = reinterpret_cast<uint64_t*>(m0s + kM0Cache); // [kStages] rank 0: rank 1's chunk is ready
   uint64_t* tfull = ofull + kStages;                             // [kStages] this CTA's rows landed
-  uint64_t* empty = tfull + kStages;                             // [kStages] the chunk's MMAs completed
+  uint64_t* gfull = tfull + kStages;                             // [kStages] this CTA's corners are generated
+  uint64_t* empty = gfull + kStages;                             // [kStages] the chunk's MMAs completed
   uint64_t* accfull = empty + kStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfull + 1);
 
@@ -142,10 +145,17 @@ __global__ void __launch_bounds__(kThreadsA, 1)
   const long long vbase = (long long)(blockIdx.x >> 1) * (2 * kVP) + (long long)rank * kVP;
   const int r0 = rt * kAdjPairRows;
   const int nch = ar.kdim_pad / kAC;
+  // this thread's corner coordinates, loaded first so that their latency
+  // overlaps the prologue (generator threads: corner tid mod 128)
+  const long long v_me = vbase + (tid & (kVP - 1));
+  const bool live_me = tid < kGen && (GROUPED ? v_me <= pl.T : v_me < pl.V);
+  const uint32_t b_me = !live_me ? 0u : (GROUPED ? (uint32_t)v_me : (uint32_t)__ldg((mat == 0 ? pl.vy : pl.vx) + v_me));
+  const uint32_t a_me = (!live_me || GROUPED) ? 0u : (uint32_t)__ldg((mat == 0 ? pl.vx : pl.vy) + v_me);
 
   if (tid == kGen + 32) {
     for (int i = 0; i < kStages; ++i) {
-      mbar_init(&ofull[i], 2 * (kGen / 32) + 1);   // both CTAs' generator warps and rank 1's row forwarder
+      mbar_init(&ofull[i], 1);             // rank 1's forwarder (its corners and rows)
+      mbar_init(&gfull[i], kGen / 32);     // this CTA's generator warps
       mbar_init(&tfull[i], 1);
       mbar_init(&empty[i], 1);
     }
@@ -167,6 +177,11 @@ __global__ void __launch_bounds__(kThreadsA, 1)
     }
     const float4* gr = reinterpret_cast<const float4*>(ws + ar.off_rows) + (size_t)mat * ar.nrows_pad + r0;
     for (int i = tid; i < kAdjPairRows; i += kGen) rows[i] = __ldg(gr + i);
+    // the k = 0 row (row tile 0 only): read from shared memory by the generators
+    if (rt == 0 && ar.kdim_pad <= kM0Cache) {
+      const float* m0g = reinterpret_cast<const float*>(ws + ar.off_m0) + (size_t)mat * (ar.kdim_pad + 4);
+      for (int i = tid; i < ar.kdim_pad; i += kGen) m0s[i] = __ldg(m0g + i);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -204,7 +219,9 @@ __global__ void __launch_bounds__(kThreadsA, 1)
       for (int j = 0; j < nch; ++j) {
         const int s = j % kStages;
         const uint32_t ph = (uint32_t)(j / kStages) & 1u;
-        if (!mbar_wait_cluster(&ofull[s], ph, st, 43) || !mbar_wait(&tfull[s], ph, st, 47)) break;
+        if (!mbar_wait(&gfull[s], ph, st, 44) || !mbar_wait(&tfull[s], ph, st, 47) ||
+            !mbar_wait_cluster(&ofull[s], ph, st, 43))
+          break;
         tc_fence_after();
         const uint32_t ahi = ops_a + s * kStage, alo = ahi + kTile, bhi = alo + kTile, blo = bhi + kTile;
 #pragma unroll
@@ -220,10 +237,13 @@ __global__ void __launch_bounds__(kThreadsA, 1)
       }
       tc_commit_pair(accfull);
     } else if (lane == 0) {
-      // rank 1: each chunk's rows have landed here -> count it on rank 0's barrier
+      // rank 1: each chunk's corners are generated and its rows have landed
+      // here -> one arrival (release at cluster scope) on rank 0's barrier, so
+      // that the generator warps only arrive locally
       for (int j = 0; j < nch; ++j) {
         const int s = j % kStages;
-        if (!mbar_wait(&tfull[s], (uint32_t)(j / kStages) & 1u, st, 48)) break;
+        const uint32_t ph = (uint32_t)(j / kStages) & 1u;
+        if (!mbar_wait(&gfull[s], ph, st, 42) || !mbar_wait(&tfull[s], ph, st, 48)) break;
         mbar_arrive_cluster(&ofull[s], 0);
       }
     }
@@ -232,15 +252,16 @@ __global__ void __launch_bounds__(kThreadsA, 1)
     // Thread (corner i, half g) writes columns 32 g .. 32 g + 31 of row i of
     // each chunk: l = 32 j + 16 g + 1 .. + 16 as (cos, sin) pairs, zeros past K.
     const int cidx = tid & (kVP - 1), g = tid >> 7;
-    const long long v = vbase + cidx;   // the corner, or (grouped) the value b itself
-    const bool live = GROUPED ? v <= pl.T : v < pl.V;
+    const long long v = v_me;   // the corner, or (grouped) the value b itself
+    const bool live = live_me;
     const int32_t* cbp = mat == 0 ? pl.vy : pl.vx;
-    const uint32_t b = !live ? 0u : (GROUPED ? (uint32_t)v : (uint32_t)__ldg(cbp + v));
+    const uint32_t b = b_me;
     const float* m0 = reinterpret_cast<const float*>(ws + ar.off_m0) + (size_t)mat * (ar.kdim_pad + 4);
+    const float* m0r = ar.kdim_pad <= kM0Cache ? m0s : m0;   // the shared copy when it fits
     const bool krow = rt == 0;   // row tile 0 also carries the k = 0 row
     const float2 w = tl_lookup(tl, b & mask);   // step cos, sin(2 pi b / T)
     const uint32_t ops_a = smem_u32(ops);
-    float acc0 = 0.f;
+    float acc0 = 0.f, acc0b = 0.f;   // chains over the cos and the sin columns
     for (int j = 0; j < nch; ++j) {
       const int s = j % kStages;
       const uint32_t ph = (uint32_t)(j / kStages) & 1u;
@@ -279,14 +300,16 @@ __global__ void __launch_bounds__(kThreadsA, 1)
           for (int t = 0; t < 8; ++t) cv[t] = sv[t] = 0.f;
         }
         if (krow) {
-          const float4* mp = reinterpret_cast<const float4*>(m0 + 2 * (l0 - 1));
+          const float4* mp = reinterpret_cast<const float4*>(m0r + 2 * (l0 - 1));
+          float4 m[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) m[u] = mp[u];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const float4 m = __ldg(mp + u);
-            acc0 = fmaf(m.x, cv[2 * u], acc0);
-            acc0 = fmaf(m.y, sv[2 * u], acc0);
-            acc0 = fmaf(m.z, cv[2 * u + 1], acc0);
-            acc0 = fmaf(m.w, sv[2 * u + 1], acc0);
+            acc0 = fmaf(m[u].x, cv[2 * u], acc0);
+            acc0b = fmaf(m[u].y, sv[2 * u], acc0b);
+            acc0 = fmaf(m[u].z, cv[2 * u + 1], acc0);
+            acc0b = fmaf(m[u].w, sv[2 * u + 1], acc0b);
           }
         }
         uint32_t hv[8], lv[8];
@@ -300,11 +323,13 @@ __global__ void __launch_bounds__(kThreadsA, 1)
         st_shared_v4a(hi_row + kTile + o1, lv[4], lv[5], lv[6], lv[7]);
       }
       // every lane's writes are made visible to the tensor core's proxy, then
-      // one arrival per warp (release at cluster scope) on rank 0's barrier
+      // one arrival per warp on this CTA's barrier
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive_cluster(&ofull[s], 0);
+      if (lane == 0) mbar_arrive(&gfull[s]);
     }
+
+    acc0 += acc0b;
 
     // ---------------- epilogue: per-corner dot with A' ----------------
     // warp w reads TMEM lanes 32 (w mod 4) .. +31 (its corners, or values of b)
@@ -386,12 +411,11 @@ __global__ void __launch_bounds__(kThreadsA, 1)
         }
       }
     } else {
-    const int32_t* cap = mat == 0 ? pl.vx : pl.vy;
-    const uint32_t a = live ? (uint32_t)__ldg(cap + v) : 0u;
+    const uint32_t a = a_me;
     const float2 wa = tl_lookup(tl, a & mask);
     const float fb = (float)b;
     const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
-    float outv = acc0;
+    float outv = acc0, outs = 0.f;   // cos-row and sin-row chains
     if (acc_ok) {
       for (int cb = 0; cb < kRH; cb += 32) {   // 32 rows = 16 frequencies
         const int n0 = g * kRH + cb;           // tile row of the first column
@@ -414,13 +438,14 @@ __global__ void __launch_bounds__(kThreadsA, 1)
           const float z1 =
               fmaf(__uint_as_float(d1[2 * i + 1]) + __uint_as_float(d2[2 * i + 1]), q1.x, fmaf(q1.z, fb, q1.y));
           outv = fmaf(c, z0, outv);
-          outv = fmaf(sn, z1, outv);
+          outs = fmaf(sn, z1, outs);
           const float c1 = fmaf(c, wa.x, -(sn * wa.y)), s1 = fmaf(sn, wa.x, c * wa.y);
           c = c1;
           sn = s1;
         }
       }
     }
+    outv += outs;
     if (g == 1) comb[cidx] = outv;
     asm volatile("bar.sync 1, %0;" ::"n"(kGen) : "memory");
     if (g == 0 && live) {
