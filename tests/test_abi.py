@@ -68,3 +68,36 @@ def test_no_cpu_fallback(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         _lib.load()
+
+
+def test_grouped_plan_workspaces(lib):
+    """Host plans of the grouped (row-binned) contraction, through the size
+    functions (no device work): it is taken automatically for V >= 8 (T + 1)
+    and K >= 256 on the split-FP16 path, its workspace holds H (2 x 2K x
+    (T + 1 rounded up to 64) FP16), forcing it on a small clip grows the
+    workspace, and the plain FP32 path never groups."""
+    V, T, K = 945450, 65536, 1024
+    h_bytes = 2 * (2 * K) * 65600 * 2
+    try:
+        lib.fcfs_debug_set_hybrid(0)
+        direct = lib.fcfs_workspace_size(V, T, K, 1)
+        direct32 = lib.fcfs_workspace_size(V, T, K, 0)
+        adj_direct = lib.fcfs_adjoint_workspace_size(V, T, K, 1)
+        small_direct = lib.fcfs_workspace_size(12576, 4096, 256, 1)
+        small_direct32 = lib.fcfs_workspace_size(12576, 4096, 256, 0)
+        batch_direct = lib.fcfs_batch_workspace_size(100000, 8, 2048, 128, 1)
+        k128_direct = lib.fcfs_workspace_size(V, T, 128, 1)
+        lib.fcfs_debug_set_hybrid(1)
+        auto = lib.fcfs_workspace_size(V, T, K, 1)
+        assert auto >= h_bytes and auto >= direct   # grouped: H, or the validation plan
+        assert lib.fcfs_workspace_size(V, T, K, 0) == direct32
+        # K = 128 is below the automatic threshold: the direct plan
+        assert lib.fcfs_workspace_size(V, T, 128, 1) == k128_direct
+        # the adjoint groups by y and by x: two permutations of V corners more
+        assert lib.fcfs_adjoint_workspace_size(V, T, K, 1) >= adj_direct + 2 * 4 * V
+        lib.fcfs_debug_set_hybrid(2)
+        assert lib.fcfs_workspace_size(12576, 4096, 256, 1) > small_direct
+        assert lib.fcfs_batch_workspace_size(100000, 8, 2048, 128, 1) > batch_direct
+        assert lib.fcfs_workspace_size(12576, 4096, 256, 0) == small_direct32   # FP32 never groups
+    finally:
+        lib.fcfs_debug_set_hybrid(1)
