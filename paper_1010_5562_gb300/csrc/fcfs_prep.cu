@@ -128,12 +128,23 @@ size_t axis_smem_bytes(int T, int full) {
   return align_up(axis_levels_ints(T) * sizeof(int), 16);
 }
 
+// Block (frequency block, bin slice, clip): thread (group q, kt) takes
+// frequency k = 128 blockIdx.x + kt + 1 over the bins of the slice with index
+// q mod G (G groups of kAxisThreads threads, so that the large-period blocks,
+// one per SM for their 128 KB of levels, still keep 16 warps busy); the groups'
+// sums are added in shared memory and then, exactly, into the clip's totals.
+constexpr int kAxisGroupsMax = 4;
 template <bool BATCH>
-__global__ void __launch_bounds__(kAxisThreads) axis_dft_kernel(Plan pl, uint8_t* ws, int nper) {
+__global__ void __launch_bounds__(kAxisThreads * kAxisGroupsMax) axis_dft_kernel(Plan pl, uint8_t* ws, int nper) {
   extern __shared__ __align__(128) uint8_t sm[];
   int* lv = reinterpret_cast<int*>(sm);
-  const int T = pl.T, logT = pl.logT, logQ = logT - 2, Q = T / 4;
+  const int T = pl.T, logT = pl.logT, logQ = logT - 2;
   const size_t tb = tab_fix_bytes(T, 0);
+  // after the levels: staged bins (one per thread) and, for several groups,
+  // their partial sums [group][5][kAxisThreads]
+  long long* sbx = reinterpret_cast<long long*>(sm + align_up(axis_levels_ints(T) * sizeof(int), 16));
+  long long* sby = sbx + blockDim.x;
+  long long* red = sby + blockDim.x;
   __shared__ uint64_t tbar;
   Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
   if (threadIdx.x == 0) {
@@ -147,35 +158,55 @@ __global__ void __launch_bounds__(kAxisThreads) axis_dft_kernel(Plan pl, uint8_t
   axis_build_levels(lv, T, logT);
   __syncthreads();
 
+  const int G = blockDim.x / kAxisThreads;
+  const int grp = threadIdx.x / kAxisThreads, kt = threadIdx.x % kAxisThreads;
   const int clip = blockIdx.z;
   const long long* bx = reinterpret_cast<const long long*>(ws + pl.off_bins) + (size_t)clip * 2 * (T + 1);
   const long long* by = bx + (T + 1);
-  const int k = blockIdx.x * kAxisThreads + threadIdx.x + 1;
+  const int k = blockIdx.x * kAxisThreads + kt + 1;
   const int n0 = blockIdx.y * nper, n1 = min(T + 1, n0 + nper);
   long long a0 = 0, a1 = 0, a2 = 0, a3 = 0, area = 0;
   // bins are staged through shared memory in coalesced slices (a dependent
   // global load per bin would leave the loop latency-bound)
-  __shared__ long long sbx[kAxisThreads], sby[kAxisThreads];
-  for (int b0 = n0; b0 < n1; b0 += kAxisThreads) {
-    const int cnt = min(kAxisThreads, n1 - b0);
+  for (int b0 = n0; b0 < n1; b0 += blockDim.x) {
+    const int cnt = min((int)blockDim.x, n1 - b0);
     __syncthreads();
     if ((int)threadIdx.x < cnt) {
       sbx[threadIdx.x] = bx[b0 + threadIdx.x];
       sby[threadIdx.x] = by[b0 + threadIdx.x];
     }
     __syncthreads();
-  for (int i = 0; i < cnt; ++i) {
-    const int n = b0 + i;
-    const long long wx = sbx[i], wy = sby[i];   // same address across the block: broadcast
-    if (wx == 0 && wy == 0) continue;          // block-uniform
-    if (blockIdx.x == 0 && threadIdx.x == 0) area += (long long)n * wx;
-    if (k > pl.K) continue;
-    if (fits_i32(wx) && fits_i32(wy))   // block-uniform
-      axis_bin_add<true>(lv, T, logQ, k, n, wx, wy, a0, a1, a2, a3);
-    else
-      axis_bin_add(lv, T, logQ, k, n, wx, wy, a0, a1, a2, a3);
+    for (int i = grp; i < cnt; i += G) {
+      const int n = b0 + i;
+      const long long wx = sbx[i], wy = sby[i];   // same address across the group: broadcast
+      if (wx == 0 && wy == 0) continue;          // group-uniform
+      if (blockIdx.x == 0 && kt == 0) area += (long long)n * wx;
+      if (k > pl.K) continue;
+      if (fits_i32(wx) && fits_i32(wy))   // group-uniform
+        axis_bin_add<true>(lv, T, logQ, k, n, wx, wy, a0, a1, a2, a3);
+      else
+        axis_bin_add(lv, T, logQ, k, n, wx, wy, a0, a1, a2, a3);
+    }
   }
+  if (G > 1) {   // add the groups' sums (integers: exact in any order)
+    long long* r = red + (size_t)grp * 5 * kAxisThreads + kt;
+    r[0] = a0;
+    r[kAxisThreads] = a1;
+    r[2 * kAxisThreads] = a2;
+    r[3 * kAxisThreads] = a3;
+    r[4 * kAxisThreads] = area;
+    __syncthreads();
+    if (grp == 0)
+      for (int q = 1; q < G; ++q) {
+        const long long* rq = red + (size_t)q * 5 * kAxisThreads + kt;
+        a0 += rq[0];
+        a1 += rq[kAxisThreads];
+        a2 += rq[2 * kAxisThreads];
+        a3 += rq[3 * kAxisThreads];
+        area += rq[4 * kAxisThreads];
+      }
   }
+  if (grp != 0) return;
   long long* acc = reinterpret_cast<long long*>(ws + pl.off_axis) + (size_t)clip * (4 * pl.K + 1);
   if (k <= pl.K) {
     atomicAdd(reinterpret_cast<unsigned long long*>(&acc[k - 1]), (unsigned long long)a0);
@@ -183,7 +214,7 @@ __global__ void __launch_bounds__(kAxisThreads) axis_dft_kernel(Plan pl, uint8_t
     atomicAdd(reinterpret_cast<unsigned long long*>(&acc[2 * pl.K + k - 1]), (unsigned long long)a2);
     atomicAdd(reinterpret_cast<unsigned long long*>(&acc[3 * pl.K + k - 1]), (unsigned long long)a3);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && area != 0)
+  if (blockIdx.x == 0 && kt == 0 && area != 0)
     atomicAdd(reinterpret_cast<unsigned long long*>(&acc[4 * pl.K]), (unsigned long long)area);
 }
 
@@ -290,10 +321,13 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
   const long long want = std::max(1LL, per_sm * sms / ((long long)kblocks * clips));
   const int nper = (int)std::max(64LL, (pl.T + 1 + want - 1) / want);
   const int nblocks = (pl.T + 1 + nper - 1) / nper;
-  const size_t smem = axis_smem_bytes(pl.T, pl.full);
+  const int groups = pl.T > 8192 ? kAxisGroupsMax : 1;   // large periods: one block per SM
+  const int threads = kAxisThreads * groups;
+  const size_t smem = axis_smem_bytes(pl.T, pl.full) + (size_t)2 * threads * sizeof(long long) +
+                      (groups > 1 ? (size_t)groups * 5 * kAxisThreads * sizeof(long long) : 0);
   auto kern = pl.batch ? axis_dft_kernel<true> : axis_dft_kernel<false>;
   ensure_smem(reinterpret_cast<const void*>(kern), smem);
-  kern<<<dim3(kblocks, nblocks, clips), kAxisThreads, smem, st>>>(pl, static_cast<uint8_t*>(ws), nper);
+  kern<<<dim3(kblocks, nblocks, clips), threads, smem, st>>>(pl, static_cast<uint8_t*>(ws), nper);
   count_launch(1);
   return cudaGetLastError();
 }
