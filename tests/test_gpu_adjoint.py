@@ -168,6 +168,20 @@ def test_grouped_adjoint_random_cotangent(fc, K):
     assert rel(gx, gx0) < 2e-6 and rel(gy, gy0) < 2e-6, (rel(gx, gx0), rel(gy, gy0))
 
 
+def test_grouped_adjoint_tiny_period(fc):
+    """T = 4 (five values of b, a one-level sincos table) and T = 16, forced grouped."""
+    from synth import clip_from_rings, rect_ring
+    for T, rings in ((4, [rect_ring(1, 1, 2, 3)]), (16, [rect_ring(1, 2, 5, 9), rect_ring(9, 0, 16, 4)])):
+        clip = clip_from_rings(T, rings)
+        K = 20
+        rng = np.random.default_rng(T)
+        W = 2 * K + 1
+        G = rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))
+        gx, gy = grad_mode(fc, clip, K, G, 2)
+        rx, ry = oracle.vertex_gradient(clip.x, clip.y, clip.s, clip.T, K, G)
+        assert rel(gx, rx) < TOL and rel(gy, ry) < TOL, (T, rel(gx, rx), rel(gy, ry))
+
+
 def test_grouped_adjoint_large_groups(fc):
     """10000 rectangles 5 wide on y in [0, 50]: the y groups of 20000 corners
     exceed the epilogue's staging (4096 corners), so the CTA of b in [0, 128)

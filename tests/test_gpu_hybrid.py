@@ -58,6 +58,7 @@ CASES = [
     (2048, 600, 13, 8, 60, 129),      # 2K = 258: a 2-row tail tile
     (8192, 900, 14, 20, 200, 128),    # largest full-period table
     (65536, 1000, 15, 20, 2000, 130), # quarter-wave tables, sparse y
+    (16, 4, 16, 1, 3, 128),           # tiny period: one y chunk, K >> T
 ]
 
 
