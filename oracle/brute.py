@@ -9,6 +9,9 @@ closed form of the transform:
 * the cell integral of the Fourier basis (Eq. inner_prod) by Gauss-Legendre
   quadrature on each unit interval, c_k(i) = integral_i^{i+1} e^{-j 2 pi k t / T} dt;
 * F(k, l) = sum over occupied cells of c_k(i) c_l(j) (separability of the basis).
+
+``cosine_block`` does the same with the cosine basis cos(pi k t / T) of the
+continuous cosine series.
 """
 import numpy as np
 
@@ -55,3 +58,20 @@ def block(x, y, offsets, T, K):
     f = np.arange(-K, K + 1)
     C = cell_integrals(f, T)
     return C @ occ @ C.T
+
+
+def cell_integrals_cos(freq, T, nodes=32):
+    """Cc[f, i] = integral_i^{i+1} cos(pi f t / T) dt by Gauss-Legendre."""
+    t, w = np.polynomial.legendre.leggauss(nodes)
+    u = 0.5 * (t + 1.0)
+    pos = np.arange(T)[:, None] + u[None, :]
+    freq = np.asarray(freq, dtype=np.float64)
+    ph = np.cos(np.pi * freq[:, None, None] * pos[None, :, :] / T)
+    return np.sum(ph * (0.5 * w)[None, None, :], axis=2)
+
+
+def cosine_block(x, y, offsets, T, K):
+    """C[k, l] = sum over occupied unit cells of Cc_k(i) Cc_l(j), 0 <= k, l <= K."""
+    occ = rasterise(x, y, offsets, T).astype(np.float64)
+    Cc = cell_integrals_cos(np.arange(0, K + 1), T)
+    return Cc @ occ @ Cc.T

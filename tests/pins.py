@@ -171,3 +171,102 @@ def tiny_clips():
             make_clip(24, 4, 12, smin=3, smax=9, wmin=1, margin=1),
             make_clip(32, 4, 13, smin=4, smax=14, wmin=1, margin=1),
             make_clip(32, 9, 14, smin=3, smax=8, wmin=1, margin=1, mix=RECT_ONLY)]
+
+
+# ---------------------------------------------------------------------------
+# Continuous cosine series, C(k, l) = integral of the image times
+# cos(pi k x / T) cos(pi l y / T), 0 <= k, l <= K.
+# ---------------------------------------------------------------------------
+def _gl_cos_integral(freq, a, b, T, nodes=64):
+    """integral_a^b cos(pi f t / T) dt by Gauss-Legendre."""
+    t, w = np.polynomial.legendre.leggauss(nodes)
+    mid, half = 0.5 * (a + b), 0.5 * (b - a)
+    pts = mid + half * t
+    freq = np.asarray(freq, dtype=np.float64)
+    return half * np.sum(w[None, :] * np.cos(np.pi * freq[:, None] * pts[None, :] / T), axis=1)
+
+
+def pin_cosine_brute(clip, K):
+    """The cosine oracle equals unit-cell rasterisation plus quadrature."""
+    C1 = oracle.cosine_block(clip.x, clip.y, clip.s, clip.T, K)
+    C3 = brute.cosine_block(clip.x, clip.y, clip.poly_offsets, clip.T, K)
+    return np.max(np.abs(C1 - C3)) / max(abs(C3[0, 0]), 1)
+
+
+def pin_cosine_fourier(clip, K):
+    """cos a cos b = (cos(a + b) + cos(a - b)) / 2, so with the Fourier block of
+    period 2T (whose basis at (k, l) is exp(-j pi (k x + l y) / T)):
+    C(k, l) = Re(F_2T(k, l) + F_2T(k, -l)) / 2."""
+    C = oracle.cosine_block(clip.x, clip.y, clip.s, clip.T, K)
+    F = oracle.block(clip.x, clip.y, clip.s, 2 * clip.T, K)
+    ref = 0.5 * np.real(F[K:, K:] + F[K:, K::-1])
+    return np.max(np.abs(C - ref)) / max(abs(ref[0, 0]), 1)
+
+
+def pin_cosine_rectangle(T, x1, y1, x2, y2, K):
+    """A rectangle's cosine block is the outer product of the two interval
+    integrals of the 1-D cosines (quadrature, no closed form)."""
+    c = clip_from_rings(T, [rect_ring(x1, y1, x2, y2)])
+    C = oracle.cosine_block(c.x, c.y, c.s, T, K)
+    f = np.arange(0, K + 1)
+    ref = np.outer(_gl_cos_integral(f, x1, x2, T), _gl_cos_integral(f, y1, y2, T))
+    return np.max(np.abs(C - ref)) / ((x2 - x1) * (y2 - y1))
+
+
+def _reflect_rings(clip, how):
+    """Rings of the clip reflected in x (x -> T - x) or across the diagonal
+    (x <-> y), re-ordered so that each stays clockwise with a horizontal first edge."""
+    rings = []
+    for m in range(clip.n_polys):
+        rx, ry = clip.ring(m)
+        n = rx.shape[0]
+        if how == "mirror_x":   # v1, v0, v_{n-1}, ..., v2: first edge = old edge 0, reversed
+            order = np.concatenate([[1, 0], np.arange(n - 1, 1, -1)])
+            rings.append((clip.T - rx[order], ry[order]))
+        else:                   # v0, v_{n-1}, ..., v1: first edge = old last (vertical) edge
+            order = np.concatenate([[0], np.arange(n - 1, 0, -1)])
+            rings.append((ry[order], rx[order]))
+    return clip_from_rings(clip.T, rings)
+
+
+def pin_cosine_symmetry(clip, K):
+    """cos(pi k (T - x) / T) = (-1)^k cos(pi k x / T): mirroring the clip in x
+    multiplies row k by (-1)^k; swapping x and y transposes the block."""
+    C = oracle.cosine_block(clip.x, clip.y, clip.s, clip.T, K)
+    cm = _reflect_rings(clip, "mirror_x")
+    ct = _reflect_rings(clip, "transpose")
+    Cm = oracle.cosine_block(cm.x, cm.y, cm.s, clip.T, K)
+    Ct = oracle.cosine_block(ct.x, ct.y, ct.s, clip.T, K)
+    sgn = (-1.0) ** np.arange(K + 1)
+    e1 = np.max(np.abs(Cm - sgn[:, None] * C))
+    e2 = np.max(np.abs(Ct - C.T))
+    return max(e1, e2) / max(abs(C[0, 0]), 1)
+
+
+def pin_cosine_special(T, K):
+    """Orthogonality on [0, T]: the full square has C = T^2 at (0, 0) and 0
+    elsewhere; the strip [0, T] x [0, h] has C(k, l) = 0 for k >= 1 and
+    C(0, l) = T integral_0^h cos(pi l y / T) dy."""
+    sq = clip_from_rings(T, [rect_ring(0, 0, T, T)])
+    C = oracle.cosine_block(sq.x, sq.y, sq.s, T, K)
+    ref = np.zeros_like(C)
+    ref[0, 0] = T * T
+    e1 = np.max(np.abs(C - ref)) / (T * T)
+    h = T // 2 + 1
+    st = clip_from_rings(T, [rect_ring(0, 0, T, h)])
+    C2 = oracle.cosine_block(st.x, st.y, st.s, T, K)
+    ref2 = np.zeros_like(C2)
+    ref2[0, :] = T * _gl_cos_integral(np.arange(0, K + 1), 0, h, T)
+    e2 = np.max(np.abs(C2 - ref2)) / (T * h)
+    return max(e1, e2)
+
+
+def cosine_bessel_sum(clip, K):
+    """(1/T^2) sum_{k,l <= K} w_k w_l C(k, l)^2 with w_0 = 1, w_k = 2: the squared
+    norm of the image's projection on the first K + 1 cosines per axis
+    (orthogonal basis with norms T and T/2), at most the area (Bessel) and
+    tending to it as K grows (Parseval; the image is an indicator)."""
+    C = oracle.cosine_block(clip.x, clip.y, clip.s, clip.T, K)
+    w = np.full(K + 1, 2.0)
+    w[0] = 1.0
+    return float(np.sum(w[:, None] * w[None, :] * C * C)) / (clip.T * clip.T)
