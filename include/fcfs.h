@@ -152,6 +152,39 @@ fcfs_status fcfs_batch(const int32_t* x, const int32_t* y, const int8_t* s,
                        void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * Continuous cosine series of one clip (the cosine extension of FCFS named in
+ * the concluding section; the paper gives no formula, so this keeps the
+ * conventions of the Fourier block: the inner product with the basis, no
+ * basis normalisation, C(0,0) = area):
+ *
+ *     C(k,l) = integral over the image of cos(pi k x / T) cos(pi l y / T) dx dy,
+ *     0 <= k, l <= K.
+ *
+ * With the same signed quadrants, C = Xc diag(s) Yc^T,
+ * Xc[k,v] = integral_{x_v}^T cos(pi k t / T) dt = -(T / (pi k)) sin(pi k x_v / T)
+ * (T - x_v at k = 0).  For a balanced corner set this reduces to the exact
+ * area at (0,0), the axis lines C(k,0) = (T/(pi k)) sum s y sin(pi k x / T)
+ * (exact integer sums, as Eqs. Fk0 and F0l) and
+ * C(k,l) = T^2/(pi^2 k l) sum s sin(pi k x / T) sin(pi l y / T): the
+ * quarter-plane contraction at period 2T with sine rows only.
+ *   x, y, s, V : as for fcfs_forward; coordinates 0 <= x, y <= T.
+ *   T          : power of two, 4 <= T <= 32768 (the tables have period 2T).
+ *   K          : 1 <= K <= 4096.
+ *   prec       : FCFS_PREC_SPLIT_F16 (tensor cores on CTA pairs) or FCFS_PREC_FP32.
+ *   flags      : must be 0 (no device validation).
+ *   C_out      : (K+1)^2 float32 (device), row-major, C_out[k*(K+1) + l] = C(k,l),
+ *                written completely.
+ *   area_out   : one int64 (device), the exact area C(0,0).
+ *   workspace  : >= fcfs_cosine_workspace_size(V, T, K, prec) bytes, 256-byte aligned.
+ * Four kernels; returns FCFS_OK once enqueued.
+ */
+size_t fcfs_cosine_workspace_size(int64_t V, int32_t T, int32_t K, int32_t prec);
+fcfs_status fcfs_cosine(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V,
+                        int32_t T, int32_t K, int32_t prec, uint32_t flags,
+                        float* C_out, int64_t* area_out,
+                        void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * Forward block for callers that cannot allocate device memory (no counterpart
  * in the paper; it exists for such callers).  Some code cannot call cudaMalloc
  * where it needs the transform: a plugin whose host framework owns all device

@@ -89,8 +89,9 @@ static uint64_t table_tag(const Plan& pl) {
 }
 
 // single: a one-clip forward call, whose tensor-core contraction may run on
-// CTA pairs; batches and the adjoint use one-CTA tiles.
-fcfs_status make_plan_ex(int64_t V, int32_t T, int32_t K, int32_t prec, bool single, Plan& pl) {
+// CTA pairs; batches and the adjoint use one-CTA tiles.  cosine: the cosine
+// series of a clip of period T / 2 (K sine rows, tensor cores always on pairs).
+static fcfs_status plan_impl(int64_t V, int32_t T, int32_t K, int32_t prec, bool single, bool cosine, Plan& pl) {
   memset(&pl, 0, sizeof(pl));
   if (T < 4 || T > 65536 || (T & (T - 1)) != 0) return FCFS_EUNSUPPORTED;
   if (K < 1 || K > 4096) return FCFS_EUNSUPPORTED;
@@ -101,11 +102,12 @@ fcfs_status make_plan_ex(int64_t V, int32_t T, int32_t K, int32_t prec, bool sin
   pl.K = K;
   pl.prec = prec;
   pl.logT = ceil_log2(T);
-  pl.full = T <= kFullTableMaxT ? 1 : 0;
-  pl.fixq = min(30, 62 - ceil_log2(std::max<long long>(V, 1)) - pl.logT);
-  pl.M2 = 2 * K;
-  pl.quad_scale = (float)((double)T * (double)T / (4.0 * CUDART_PI * CUDART_PI));
   const bool tc = prec == FCFS_PREC_SPLIT_F16;
+  pl.full = T <= (tc ? kTcFullTableMaxT : kFullTableMaxT) ? 1 : 0;
+  pl.fixq = min(30, 62 - ceil_log2(std::max<long long>(V, 1)) - pl.logT);
+  pl.cosine = cosine ? 1 : 0;
+  pl.M2 = cosine ? K : 2 * K;
+  pl.quad_scale = (float)((double)T * (double)T / (4.0 * CUDART_PI * CUDART_PI));
   if (tc) {
     pl.bm = 128;
     pl.bn = (pl.full && pl.M2 > 128) ? 256 : 128;
@@ -116,7 +118,7 @@ fcfs_status make_plan_ex(int64_t V, int32_t T, int32_t K, int32_t prec, bool sin
   }
   pl.tiles_m = (pl.M2 + pl.bm - 1) / pl.bm;
   pl.tiles_n = (pl.M2 + pl.bn - 1) / pl.bn;
-  if (tc && single && g_pair && pl.M2 >= 256) {
+  if (tc && single && (cosine || (g_pair && pl.M2 >= 256))) {
     // 256 x 256 tiles on CTA pairs: tile row pair (2 tm', 2 tm' + 1), one per CTA
     pl.pair = 1;
     pl.bn = 256;
@@ -152,8 +154,21 @@ fcfs_status make_plan_ex(int64_t V, int32_t T, int32_t K, int32_t prec, bool sin
   return FCFS_OK;
 }
 
+fcfs_status make_plan_ex(int64_t V, int32_t T, int32_t K, int32_t prec, bool single, Plan& pl) {
+  return plan_impl(V, T, K, prec, single, false, pl);
+}
+
 fcfs_status make_plan(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
   return make_plan_ex(V, T, K, prec, false, pl);
+}
+
+// The cosine series of a clip of period T works on sines of period 2T.
+fcfs_status make_plan_cosine(int64_t V, int32_t T, int32_t K, int32_t prec, Plan& pl) {
+  if (T < 4 || T > 32768 || (T & (T - 1)) != 0) {
+    memset(&pl, 0, sizeof(pl));
+    return FCFS_EUNSUPPORTED;
+  }
+  return plan_impl(V, 2 * T, K, prec, true, true, pl);
 }
 
 int hybrid_mode() { return g_hybrid; }

@@ -16,6 +16,9 @@ namespace fcfs {
 // Workspace plan (host and device agree on every offset)
 // ---------------------------------------------------------------------------
 constexpr int kFullTableMaxT = 8192;   // full-period tables up to this T, quarter-wave above
+// tensor-core contractions hold 192 KiB of operand stages beside the FP32 table,
+// so their full-period tables stop at T = 4096 (32 KiB)
+constexpr int kTcFullTableMaxT = 4096;
 constexpr int kWsAlign = 256;
 
 struct Plan {
@@ -61,6 +64,9 @@ struct Plan {
   int32_t ny_pad;              // T + 1 rounded up to the chunk (64)
   size_t off_ycnt;             // the corners grouped by y (fcfs_group.cuh)
   size_t off_h;                // FP16 [2][M2][ny_pad]: H = sum over a y group of s A, hi then lo
+  // continuous cosine series: T is twice the clip's period and the M2 = K rows
+  // (and columns) of the contraction are sin(2 pi f a / T), f = 1..K, only
+  int32_t cosine;
 };
 
 // Bin one corner for the axis lines (Steps 2-3): bin_x[x] += s y, bin_y[y] += s x

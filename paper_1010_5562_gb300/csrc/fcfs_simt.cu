@@ -6,7 +6,10 @@
 //   B[2j, v] =     cos(2 pi l_j y_v / T),  B[2j+1, v] =     sin(2 pi l_j y_v / T),
 //
 // with k_i = i + 1, l_j = j + 1.  The 2 x 2 blocks (CC, CS; SC, SS) of P give
-// G(k, +-l) in the reduce kernel.  Operands are generated per 32-vertex chunk
+// G(k, +-l) in the reduce kernel.  COS (continuous cosine series): row m holds
+// s_v sin(2 pi (m + 1) x_v / T) alone (columns likewise with y), so the row pair
+// (2i, 2i+1) of a tile takes the sines of frequencies 2i + 1 and 2i + 2.
+// Operands are generated per 32-vertex chunk
 // into shared memory from the FP32 table (exact integer phase), never stored
 // to global memory.  Each 256-thread block owns a 128 x 128 tile of P and one
 // vertex split; each thread accumulates an 8 x 8 register tile in FP32.
@@ -18,7 +21,7 @@ constexpr int kSB = 128;       // tile rows = tile columns
 constexpr int kSChunk = 32;    // vertices per chunk
 constexpr int kSThreads = 256;
 
-template <bool FULL>
+template <bool FULL, bool COS = false>
 __global__ void __launch_bounds__(kSThreads, 2) gemm_simt_kernel(Plan pl, const int32_t* __restrict__ x,
                                                                 const int32_t* __restrict__ y,
                                                                 const int8_t* __restrict__ s, uint8_t* ws) {
@@ -80,10 +83,20 @@ __global__ void __launch_bounds__(kSThreads, 2) gemm_simt_kernel(Plan pl, const 
     for (int t = 0; t < kSChunk / 4; ++t) {
       const int j = gv + 4 * t;
       const float sg = vs[j];
-      const float2 a = f32_lookup<FULL>(tab, (kg * (uint32_t)vx[j]) & mask, logQ);
-      const float2 bb = f32_lookup<FULL>(tab, (lg * (uint32_t)vy[j]) & mask, logQ);
-      reinterpret_cast<float2*>(As + j * kSB)[gp] = make_float2(sg * a.x, sg * a.y);
-      reinterpret_cast<float2*>(Bs + j * kSB)[gp] = bb;
+      if (COS) {
+        const uint32_t kc = (uint32_t)(tm * kSB + 2 * gp + 1), lc = (uint32_t)(tn * kSB + 2 * gp + 1);
+        const float a0 = f32_lookup<FULL>(tab, (kc * (uint32_t)vx[j]) & mask, logQ).y;
+        const float a1 = f32_lookup<FULL>(tab, ((kc + 1u) * (uint32_t)vx[j]) & mask, logQ).y;
+        const float b0 = f32_lookup<FULL>(tab, (lc * (uint32_t)vy[j]) & mask, logQ).y;
+        const float b1 = f32_lookup<FULL>(tab, ((lc + 1u) * (uint32_t)vy[j]) & mask, logQ).y;
+        reinterpret_cast<float2*>(As + j * kSB)[gp] = make_float2(sg * a0, sg * a1);
+        reinterpret_cast<float2*>(Bs + j * kSB)[gp] = make_float2(b0, b1);
+      } else {
+        const float2 a = f32_lookup<FULL>(tab, (kg * (uint32_t)vx[j]) & mask, logQ);
+        const float2 bb = f32_lookup<FULL>(tab, (lg * (uint32_t)vy[j]) & mask, logQ);
+        reinterpret_cast<float2*>(As + j * kSB)[gp] = make_float2(sg * a.x, sg * a.y);
+        reinterpret_cast<float2*>(Bs + j * kSB)[gp] = bb;
+      }
     }
     __syncthreads();
 #pragma unroll 4
@@ -129,7 +142,11 @@ cudaError_t launch_gemm_simt(const Plan& pl, const int32_t* x, const int32_t* y,
   if (pl.splits == 0) return cudaSuccess;
   const size_t smem = tab_f32_bytes(pl.T, pl.full) + 2 * kSChunk * kSB * sizeof(float) + 3 * kSChunk * 4;
   dim3 grid = pl.batch ? dim3(pl.splits, 1) : dim3(pl.tiles_m * pl.tiles_n, pl.splits);
-  if (pl.full) {
+  if (pl.cosine) {
+    auto kern = pl.full ? gemm_simt_kernel<true, true> : gemm_simt_kernel<false, true>;
+    ensure_smem(reinterpret_cast<const void*>(kern), smem);
+    kern<<<grid, kSThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws));
+  } else if (pl.full) {
     ensure_smem(reinterpret_cast<const void*>(gemm_simt_kernel<true>), smem);
     gemm_simt_kernel<true><<<grid, kSThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws));
   } else {

@@ -13,7 +13,11 @@
 // per frequency; every value is therefore a deterministic function of
 // (frequency, coordinate), so the two corners of an edge still get identical
 // (or exactly opposite) operands.  The corner sign s_v is folded into the
-// anchor phase (s = -1 adds T/2).  CTA roles:
+// anchor phase (s = -1 adds T/2).  COS (continuous cosine series): row m of
+// the product holds sin(2 pi (m + 1) a / T) alone, so a run covers 16
+// consecutive frequencies: the thread advances by two frequencies per row pair
+// (a step read at phase 2a) and takes the odd one's sine from one more
+// rotation.  CTA roles:
 //   generator warps  write the hi and lo tiles of a 64-vertex chunk into shared
 //                    memory (K-major, 128-byte swizzle); warps 0-3 then drain
 //                    TMEM in the epilogue;
@@ -89,7 +93,7 @@ __device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_
   lo = h2_bits(__floats2half2_rn(v0 - hf.x, v1 - hf.y));
 }
 
-template <int BN, int STAGES, bool FULL, bool PAIR>
+template <int BN, int STAGES, bool FULL, bool PAIR, bool COS = false>
 __global__ void __launch_bounds__(TcLayout<BN, STAGES, PAIR>::kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmp, Plan pl, uint8_t* ws) {
   using L = TcLayout<BN, STAGES, PAIR>;
@@ -234,8 +238,10 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, PAIR>::kThreads, 1)
     const int i0 = kRun * (isA ? run : run - L::kRunsA);       // first row pair in the tile
     // first frequency of the run: A rows of tile row tm; B rows of column tile
     // tn (a pair's rank r holds B rows [BN/2 r, BN/2 r + BN/2))
-    const uint32_t f0 = isA ? (uint32_t)(tm * (kBM / 2) + 1 + i0)
+    const uint32_t fp = isA ? (uint32_t)(tm * (kBM / 2) + 1 + i0)
                             : (uint32_t)(tn * (BN / 2) + (int)rank * (L::kBRows / 2) + 1 + i0);
+    // COS: row pair p of the tile holds frequencies 2p + 1 and 2p + 2
+    const uint32_t f0 = COS ? 2u * fp - 1u : fp;
     const uint32_t mask = (uint32_t)pl.T - 1u;
     const uint32_t half = (uint32_t)pl.T >> 1;
     const uint32_t logQ = (uint32_t)pl.logT - 2u;
@@ -298,7 +304,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, PAIR>::kThreads, 1)
       }
       const bool masked = isA && (first + 8 > v1);
       // anchors and steps from the table, before waiting for the stage
-      float c[8], sn[8], wc[8], wsn[8];
+      float c[8], sn[8], wc[8], wsn[8], wc2[8], ws2[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const float2 an = f32_lookup<FULL>(tab, (f0 * a[t] + add[t]) & mask, logQ);
@@ -307,6 +313,11 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, PAIR>::kThreads, 1)
         sn[t] = an.y;
         wc[t] = w.x;
         wsn[t] = w.y;
+        if (COS) {
+          const float2 w2 = f32_lookup<FULL>(tab, (2u * a[t]) & mask, logQ);
+          wc2[t] = w2.x;
+          ws2[t] = w2.y;
+        }
       }
       if (!mbar_wait(&oempty[stg], ph ^ 1u, st, 7)) break;
       const uint32_t tile_hi = ops_a + stg * L::kStage + (isA ? 0u : 2u * L::kATile) + 256u * (uint32_t)i0;
@@ -316,17 +327,30 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, PAIR>::kThreads, 1)
         if (r) {
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
-            const float nc = fmaf(c[t], wc[t], -(sn[t] * wsn[t]));
-            const float ns = fmaf(sn[t], wc[t], c[t] * wsn[t]);
+            const float uc = COS ? wc2[t] : wc[t], us = COS ? ws2[t] : wsn[t];
+            const float nc = fmaf(c[t], uc, -(sn[t] * us));
+            const float ns = fmaf(sn[t], uc, c[t] * us);
             c[t] = nc;
             sn[t] = ns;
           }
         }
         uint32_t ch[4], cl[4], sh[4], sl[4];
+        if (COS) {
+          // rows 2(i0 + r) and 2(i0 + r) + 1: the sines of frequencies f and f + 1
+          float s1[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          split2(c[2 * q], c[2 * q + 1], ch[q], cl[q]);
-          split2(sn[2 * q], sn[2 * q + 1], sh[q], sl[q]);
+          for (int t = 0; t < 8; ++t) s1[t] = fmaf(sn[t], wc[t], c[t] * wsn[t]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            split2(sn[2 * q], sn[2 * q + 1], ch[q], cl[q]);
+            split2(s1[2 * q], s1[2 * q + 1], sh[q], sl[q]);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            split2(c[2 * q], c[2 * q + 1], ch[q], cl[q]);
+            split2(sn[2 * q], sn[2 * q + 1], sh[q], sl[q]);
+          }
         }
         if (masked) {
 #pragma unroll
@@ -337,7 +361,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, PAIR>::kThreads, 1)
             sl[q] &= vmask[q];
           }
         }
-        // cos row 2(i0 + r) and sin row 2(i0 + r) + 1 of the hi and lo tiles
+        // cos row 2(i0 + r) and sin row 2(i0 + r) + 1 of the hi and lo tiles (COS: both sines)
         const uint32_t rc = tile_hi + 256u * r + xo[(2 * r) & 7];
         const uint32_t rs = tile_hi + 256u * r + 128u + xo[(2 * r + 1) & 7];
         st_shared_v4(rc, ch[0], ch[1], ch[2], ch[3]);
@@ -366,7 +390,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, PAIR>::kThreads, 1)
       tc_fence_after();
       const int M2 = pl.M2;
       const int row0 = (warp & 3) * 32;
-      const bool split_pair = pl.fused && pl.cluster == 2;
+      const bool split_pair = !COS && pl.fused && pl.cluster == 2;
       const uint32_t tr = smem_u32(ops) + (uint32_t)warp * (32u * 36u * 4u);
 #pragma unroll 1
       for (int cb = warp >> 2; cb < BN / 32; cb += kEpiWarps / 4) {
@@ -420,7 +444,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, PAIR>::kThreads, 1)
     }
   }
 
-  if (pl.fused && pl.cluster == 2) {
+  if (!COS && pl.fused && pl.cluster == 2) {
     // Split pairs: the two CTAs of the cluster hold the same output tile for
     // splits 2g and 2g + 1.  Each sends the half of its tile that the other
     // sums (rows [64 r', 64 r' + 64) for peer rank r') with one bulk copy into
@@ -479,7 +503,9 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, PAIR>::kThreads, 1)
   // single clip, cooperative launch: split-K sum, axis lines and output here.
   // Every copy into shared memory has landed and every MMA has completed, so
   // the operand stages are free; TMEM is released before the grid barrier.
-  if (pl.fused) fused_tail(pl, ws, sm, reinterpret_cast<int*>(tmem_slot + 1), &tailbar[0], &tailbar[1], &tmp);
+  if constexpr (!COS) {
+    if (pl.fused) fused_tail(pl, ws, sm, reinterpret_cast<int*>(tmem_slot + 1), &tailbar[0], &tailbar[1], &tmp);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -554,10 +580,10 @@ static int fuse_cluster(const Plan& pl) {
   return 0;
 }
 
-template <int BN, int STAGES, bool FULL, bool PAIR>
+template <int BN, int STAGES, bool FULL, bool PAIR, bool COS = false>
 static cudaError_t launch_tc(const Plan& pl, const VertexMaps& mp, void* ws, cudaStream_t st) {
   const size_t smem = tc_smem_bytes<BN, STAGES, PAIR>(pl.T, FULL);
-  auto kern = gemm_tc_kernel<BN, STAGES, FULL, PAIR>;
+  auto kern = gemm_tc_kernel<BN, STAGES, FULL, PAIR, COS>;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
   dim3 grid = pl.batch ? dim3(PAIR ? 2 * pl.splits : pl.splits, 1) : dim3(pl.tiles_m * pl.tiles_n, pl.splits);
@@ -618,6 +644,11 @@ int gemm_tc_fuse_cluster(const Plan& pl) {
 
 cudaError_t launch_gemm_tc(const Plan& pl, const VertexMaps& mp, void* ws, cudaStream_t st) {
   if (pl.splits == 0) return cudaSuccess;
+  if (pl.cosine) {   // cosine series: CTA pairs only, never fused
+    if (!pl.pair || pl.fused || pl.batch) return cudaErrorInvalidValue;
+    return pl.full ? launch_tc<256, 3, true, true, true>(pl, mp, ws, st)
+                   : launch_tc<256, 2, false, true, true>(pl, mp, ws, st);
+  }
   if (pl.pair) return pl.full ? launch_tc<256, 3, true, true>(pl, mp, ws, st) : launch_tc<256, 2, false, true>(pl, mp, ws, st);
   if (pl.bn == 256) {
     if (pl.full) return launch_tc<256, 2, true, false>(pl, mp, ws, st);

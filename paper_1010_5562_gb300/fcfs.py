@@ -9,8 +9,8 @@ import torch
 from . import _lib
 from ._lib import FCFSError, PREC, FLAG_VALIDATE
 
-__all__ = ["forward", "adjoint", "edge_chain", "batch", "workspace_size", "get_status",
-           "launch_count", "FCFSError"]
+__all__ = ["forward", "adjoint", "edge_chain", "batch", "cosine", "workspace_size",
+           "cosine_workspace_size", "get_status", "launch_count", "FCFSError"]
 
 
 def _ptr(t):
@@ -115,6 +115,29 @@ def batch(x, y, s, offsets, T, K, prec="split_f16", validate=False, out=None, ar
                           _prec(prec), FLAG_VALIDATE if validate else 0, _ptr(out), _ptr(area_out),
                           _ptr(workspace), workspace.numel(), _stream(stream))
     _lib.check("fcfs_batch", code)
+    return out, area_out
+
+
+def cosine_workspace_size(V, T, K, prec="split_f16"):
+    return int(_lib.load().fcfs_cosine_workspace_size(int(V), int(T), int(K), _prec(prec)))
+
+
+def cosine(x, y, s, T, K, prec="split_f16", out=None, area_out=None, workspace=None, stream=None):
+    """Continuous cosine series C(k, l), 0 <= k, l <= K, of one clip: float32
+    (K+1, K+1) and the int64 area."""
+    _check_vertices(x, y, s)
+    lib = _lib.load()
+    dev = x.device
+    n1 = int(K) + 1
+    if out is None:
+        out = torch.empty((n1, n1), dtype=torch.float32, device=dev)
+    if area_out is None:
+        area_out = torch.empty((1,), dtype=torch.int64, device=dev)
+    if workspace is None:
+        workspace = alloc_workspace(cosine_workspace_size(x.numel(), T, K, prec), dev)
+    code = lib.fcfs_cosine(_ptr(x), _ptr(y), _ptr(s), x.numel(), int(T), int(K), _prec(prec), 0,
+                           _ptr(out), _ptr(area_out), _ptr(workspace), workspace.numel(), _stream(stream))
+    _lib.check("fcfs_cosine", code)
     return out, area_out
 
 

@@ -101,3 +101,25 @@ def test_grouped_plan_workspaces(lib):
         assert lib.fcfs_workspace_size(12576, 4096, 256, 0) == small_direct32   # FP32 never groups
     finally:
         lib.fcfs_debug_set_hybrid(1)
+
+
+def test_cosine_host_checks(lib):
+    """The cosine-series entry points: sizes and host-detectable errors."""
+    cw = lib.fcfs_cosine_workspace_size
+    for prec in (0, 1):
+        a = cw(12576, 4096, 256, prec)
+        b = cw(0, 4096, 256, prec)
+        assert a > b > 0 and a % 256 == 0
+        # its K x K partial planes are a quarter of the Fourier block's 2K x 2K
+        assert a < lib.fcfs_workspace_size(12576, 8192, 256, prec)
+    assert cw(100, 32768, 64, 1) > 0          # largest period: sines of period 2T = 65536
+    assert cw(100, 65536, 64, 1) == 0         # 2T beyond the tables
+    assert cw(100, 1000, 8, 1) == 0           # T not a power of two
+    assert cw(100, 256, 0, 1) == 0            # K = 0
+    f = lib.fcfs_cosine
+    assert f(None, None, None, 0, 256, 8, 1, 0, None, None, None, 0, None) == 1       # NULL output
+    assert f(None, None, None, 0, 256, 8, 1, 1, 16, 16, None, 0, None) == 1           # flags must be 0
+    assert f(None, None, None, 0, 65536, 8, 1, 0, 16, 16, None, 0, None) == 6         # T too large
+    assert f(None, None, None, 0, 256, 8, 7, 0, 16, 16, None, 0, None) == 1           # bad precision
+    assert f(None, None, None, 0, 256, 8, 1, 0, 16, 16, None, 0, None) == 3           # no workspace
+    assert f(20, 32, 48, 10, 256, 8, 1, 0, 16, 16, 256, 1 << 20, None) == 1           # misaligned corners

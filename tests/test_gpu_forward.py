@@ -117,6 +117,15 @@ def test_tiny_period_and_border(fc, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("K", [100, 160])
+def test_period_8192(fc, prec, K):
+    # T = 8192: full-period table on the plain path, quarter-wave tables beside
+    # the tensor-core operand stages; K = 100 on one-CTA tiles, 160 on CTA pairs
+    clip = make_clip(8192, 800, 8192, smin=20, smax=200)
+    check(fc, clip, K, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("T,n,smax", [(16384, 1500, 400), (65536, 1000, 2000)])
 def test_quarter_wave_tables(fc, prec, T, n, smax):
     # periods above 8192 use the quarter-wave tables; clips fill ~15% of the period

@@ -56,7 +56,7 @@ CASES = [
     (256, 40, 11, 4, 30, 128),        # y range of 5 chunks, one pair tile
     (1024, 300, 12, 6, 40, 200),      # 2K = 400: ragged pair tiles
     (2048, 600, 13, 8, 60, 129),      # 2K = 258: a 2-row tail tile
-    (8192, 900, 14, 20, 200, 128),    # largest full-period table
+    (8192, 900, 14, 20, 200, 128),    # quarter-wave tables from T = 8192 on (tensor-core plans)
     (65536, 1000, 15, 20, 2000, 130), # quarter-wave tables, sparse y
     (16, 4, 16, 1, 3, 128),           # tiny period: one y chunk, K >> T
 ]
