@@ -46,14 +46,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the adjoint, batch and large-clip measurements")
+                    help="skip the adjoint, batch, large-clip and cosine-series measurements")
     ap.add_argument("--no-pair", action="store_true",
                     help="--only: one-CTA tiles instead of CTA pairs (profiling)")
     ap.add_argument("--no-fuse", action="store_true",
                     help="--only: separate axis and reduce kernels (profiling)")
     ap.add_argument("--prec", choices=["split_f16", "fp32"], default="split_f16",
-                    help="--only adjoint / adjoint_large: contraction precision")
-    ap.add_argument("--only", choices=["step", "large", "batch", "adjoint", "adjoint_large"], default=None,
+                    help="--only adjoint / adjoint_large / cosine / cosine_large: contraction precision")
+    ap.add_argument("--only", choices=["step", "large", "batch", "adjoint", "adjoint_large", "cosine",
+                                       "cosine_large"], default=None,
                     help="run one workload warmup + steps times and print its mean time "
                          "(for profiler command lines; not the benchmark line)")
     return ap.parse_args()
@@ -429,7 +430,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    for k in ("adjoint", "batch", "large"):
+    for k in ("adjoint", "batch", "large", "cosine"):
         if k in extras:
             line[k] = extras[k]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -592,12 +593,46 @@ def run_extras(fcfs, dev, flush, stream, args):
                                                    workspace=wsa5h, stream=stream), 3, flush, stream)
     big["adjoint_split_f16"] = {"value": clip5.V * W5 * W5 / (ms_a5h * 1e-3), "ms": ms_a5h,
                                 "cotangent": "as adjoint_fp32", "_g": (gx5h, gy5h)}
+    out["cosine"] = cosine_extras(fcfs, dev, flush, stream)
     out["large"] = {"workload": "clip T=65536, 150000 polygons, V=%d, K=1024 (2049x2049)" % clip5.V,
                     "unit": UNIT, "split_f16": big["split_f16"], "split_f16_direct": big["split_f16_direct"],
                     "fp32": big["fp32"],
                     "adjoint_split_f16": big["adjoint_split_f16"], "adjoint_fp32": big["adjoint_fp32"],
                     "_check": (clip5, K5)}
     return out
+
+
+def cosine_large_clip():
+    """~0.95M corners at T = 32768 (the largest period of the cosine series),
+    the corner density of the T = 65536 workload."""
+    from synth import make_clip
+    return make_clip(32768, 150000, 1006, smin=20, smax=80, wmin=4, margin=1), 1024
+
+
+def cosine_extras(fcfs, dev, flush, stream):
+    """Continuous cosine series C(k, l), 0 <= k, l <= K: the bench clip
+    (T = 4096, K = 256) and a large clip (T = 32768, ~0.95M corners, K = 1024),
+    both precisions.  Terms: V (K + 1)^2 vertex-coefficient pairs per call."""
+    import torch
+    from synth import config_clip
+    res = {"unit": UNIT}
+    for key, (clip, K) in (("clip_T4096_K256", config_clip(2)), ("clip_T32768_K1024", cosine_large_clip())):
+        x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))
+        d = {"V": clip.V, "T": clip.T, "K": K}
+        for prec in ("split_f16", "fp32"):
+            C = torch.empty((K + 1, K + 1), dtype=torch.float32, device=dev)
+            A = torch.empty(1, dtype=torch.int64, device=dev)
+            ws = torch.empty(fcfs.cosine_workspace_size(clip.V, clip.T, K, prec), dtype=torch.uint8, device=dev)
+            n = 20 if K <= 256 else 3
+            ms = _timed_ms(torch, lambda: fcfs.cosine(x, y, s, clip.T, K, prec=prec, out=C, area_out=A,
+                                                      workspace=ws, stream=stream), n, flush, stream)
+            e = {"value": clip.V * (K + 1) ** 2 / (ms * 1e-3), "ms": ms, "_C": C, "_A": A}
+            if prec == "split_f16":   # 3 split products of a K x K x V contraction, whole call
+                e["issued_tflops_whole_call"] = 3 * 2.0 * clip.V * K * K / (ms * 1e-3) / 1e12
+            d[prec] = e
+        d["_clip"] = clip
+        res[key] = d
+    return res
 
 
 def extras_accuracy(line, extras):
@@ -626,6 +661,24 @@ def extras_accuracy(line, extras):
         line["batch"]["max_abs_err_over_area_sampled"] = worst
         line["batch"]["areas_exact"] = bool(all(int(Ab[c]) == oracle.area_exact(cl.x, cl.y, cl.s, cl.T)
                                                 for c, cl in enumerate(clips)))
+    if "cosine" in extras:
+        for key, d in line["cosine"].items():
+            if not isinstance(d, dict):
+                continue
+            clip, K = d.pop("_clip"), d["K"]
+            Aexact = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+            if K <= 256:
+                pick = np.arange(K + 1)
+                sampled = False
+            else:
+                pick = np.unique(np.concatenate([[0, 1, 2, K - 1, K], np.random.default_rng(6).integers(0, K + 1, 20)]))
+                sampled = True
+            Co = oracle.cosine_entries(clip.x, clip.y, clip.s, clip.T, pick, pick)
+            for prec in ("split_f16", "fp32"):
+                e = d[prec]
+                C = e.pop("_C").cpu().numpy().astype(np.float64)[np.ix_(pick, pick)]
+                e["max_abs_err_over_area" + ("_sampled" if sampled else "")] = float(np.max(np.abs(C - Co)) / Aexact)
+                e["area_exact"] = int(e.pop("_A").item()) == Aexact
     if "large" in extras:
         clip5, K5 = extras["large"].pop("_check")
         A = oracle.area_exact(clip5.x, clip5.y, clip5.s, clip5.T)
@@ -659,7 +712,11 @@ def run_only(args):
         fcfs.set_pair(0)
     if args.no_fuse:
         fcfs.set_fuse(0)
-    if args.only in ("step", "large", "adjoint", "adjoint_large"):
+    if args.only in ("cosine", "cosine_large"):
+        clip, K = config_clip(2) if args.only == "cosine" else cosine_large_clip()
+        x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))
+        fn = lambda: fcfs.cosine(x, y, s, clip.T, K, prec=args.prec)
+    elif args.only in ("step", "large", "adjoint", "adjoint_large"):
         clip, K = config_clip({"step": 2, "large": 5, "adjoint": 4, "adjoint_large": 5}[args.only])
         x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))
         if args.only.startswith("adjoint"):
