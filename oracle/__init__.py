@@ -11,8 +11,10 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 * ``sparse_fft`` (O4): Steps 1-4 of FCFS with numpy's FFT.
 * ``brute`` (O3): unit-cell rasterisation plus quadrature, tiny periods only.
 * ``cosine``: the continuous cosine series (direct vertex sum with full tails).
+* ``haar``: the pruned continuous Haar transform (per-polygon recursion with Alg. 1).
 """
-from . import fcfs_oracle, edge_form, sparse_fft, brute, cosine
+from . import fcfs_oracle, edge_form, sparse_fft, brute, cosine, haar
 from .fcfs_oracle import (block, block_entries, tail_integral, area_exact, pupil_mask,
                           pupil_loss, vertex_gradient, edge_gradient, relative_error, freqs)
 from .cosine import cosine_block, cosine_entries
+from .haar import pcht

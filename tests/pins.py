@@ -270,3 +270,65 @@ def cosine_bessel_sum(clip, K):
     w = np.full(K + 1, 2.0)
     w[0] = 1.0
     return float(np.sum(w[:, None] * w[None, :] * C * C)) / (clip.T * clip.T)
+
+
+# ---------------------------------------------------------------------------
+# Continuous Haar transform (PCHT), coefficients in the square layout of
+# oracle.haar: W[0,0] scaling, level-j bands hg [2^j + kx, ky], gh [kx, 2^j + ky],
+# hh [2^j + kx, 2^j + ky].
+# ---------------------------------------------------------------------------
+def dht_square(img):
+    """Orthonormal 2-D discrete Haar transform of an N x N image (N = 2^n) by the
+    textbook pyramid: at each level the 2 x 2 blocks (p00 p01; p10 p11), first
+    index along x, give the scaling part (p00 + p01 + p10 + p11) / 2 and the
+    details (p00 + p01 - p10 - p11) / 2 (x), (p00 - p01 + p10 - p11) / 2 (y),
+    (p00 - p01 - p10 + p11) / 2 (both)."""
+    a = np.asarray(img, dtype=np.float64)
+    n = a.shape[0]
+    W = np.zeros_like(a)
+    while n > 1:
+        h = n // 2
+        p00, p01, p10, p11 = a[0::2, 0::2], a[0::2, 1::2], a[1::2, 0::2], a[1::2, 1::2]
+        W[h:n, 0:h] = (p00 + p01 - p10 - p11) / 2
+        W[0:h, h:n] = (p00 - p01 + p10 - p11) / 2
+        W[h:n, h:n] = (p00 - p01 - p10 + p11) / 2
+        a = (p00 + p01 + p10 + p11) / 2
+        n = h
+    W[0, 0] = a[0, 0]
+    return W
+
+
+def pin_haar_dht(clip, J=None):
+    """The CHT and DHT coefficients coincide for lattice polygons (Sec. II-C): the
+    PCHT to level J equals the top-left 2^J square of the DHT of the unit-cell
+    rasterisation (point-in-polygon, no corners, no Alg. 1).  Exact."""
+    from oracle import haar
+    N = clip.T
+    n = int(np.log2(N))
+    J = n if J is None else J
+    W = haar.pcht(clip.x, clip.y, clip.poly_offsets, N, J)
+    D = dht_square(brute.rasterise(clip.x, clip.y, clip.poly_offsets, N))
+    return float(np.max(np.abs(W - D[:1 << J, :1 << J])))
+
+
+def pin_haar_parseval(clip):
+    """Orthonormal and complete for unit-cell images at J = log2 N: the squared
+    coefficients sum to the integral of f^2 = the area (disjoint polygons)."""
+    from oracle import haar
+    N = clip.T
+    W = haar.pcht(clip.x, clip.y, clip.poly_offsets, N, int(np.log2(N)))
+    A = oracle.area_exact(clip.x, clip.y, clip.s, N)
+    return abs(float(np.sum(W * W)) - A) / A
+
+
+def pin_haar_half_tile(N, J):
+    """f = indicator of [0, N/2) x [0, N): <f, phi_000> = (N^2/2)/N = N/2, the
+    level-0 x-detail (2^0/N)(A00 + A01 - A10 - A11) = (N^2/2)/N = N/2, all else 0."""
+    from oracle import haar
+    c = clip_from_rings(N, [rect_ring(0, 0, N // 2, N)])
+    W = haar.pcht(c.x, c.y, c.poly_offsets, N, J)
+    ref = np.zeros_like(W)
+    ref[0, 0] = N / 2
+    if J > 0:
+        ref[1, 0] = N / 2
+    return float(np.max(np.abs(W - ref))) / N
