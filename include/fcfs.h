@@ -185,6 +185,35 @@ fcfs_status fcfs_cosine(const int32_t* x, const int32_t* y, const int8_t* s, int
                         void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * Continuous Haar transform of one clip (Sec. II-C; the PCHT of Sec. III-B
+ * computes the same coefficients by a pruned recursion per polygon):
+ * coefficients up to level J of the orthonormal 2-D Haar basis of the tile
+ * [0,T) x [0,T), as one square of side 2^J (FP64, row-major, first index
+ * along x):
+ *     W[0][0]               = <f, phi_000>             = area / T
+ *     W[2^j + kx][ky]       = <f, psi^(hg)_{j,kx,ky}>  (detail along x)
+ *     W[kx][2^j + ky]       = <f, psi^(gh)_{j,kx,ky}>  (detail along y)
+ *     W[2^j + kx][2^j + ky] = <f, psi^(hh)_{j,kx,ky}>
+ * for 0 <= j < J, 0 <= kx, ky < 2^j.  With A_nm the areas of the image in the
+ * four children of the dyadic square (j, kx, ky) (n along x, m along y), the
+ * details are (2^j / T)(A00 + A01 - A10 - A11), (2^j / T)(A00 - A01 + A10 - A11)
+ * and (2^j / T)(A00 - A01 - A10 + A11).  The areas are exact integers, so every
+ * coefficient is exact in FP64.
+ *   x, y, s, V : signed corners as for fcfs_forward; 0 <= x, y <= T.
+ *   T          : power of two, 4 <= T <= 65536.
+ *   J          : 0 <= J <= min(log2 T, 14).
+ *   flags      : must be 0.
+ *   W_out      : 4^J doubles (device), written completely.
+ *   workspace  : >= fcfs_haar_workspace_size(V, T, J) bytes, 256-byte aligned
+ *                (an int64 grid of 4^J level-J cell areas and smaller grids).
+ * Returns FCFS_OK once enqueued.
+ */
+size_t fcfs_haar_workspace_size(int64_t V, int32_t T, int32_t J);
+fcfs_status fcfs_haar(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V,
+                      int32_t T, int32_t J, uint32_t flags, double* W_out,
+                      void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * Forward block for callers that cannot allocate device memory (no counterpart
  * in the paper; it exists for such callers).  Some code cannot call cudaMalloc
  * where it needs the transform: a plugin whose host framework owns all device

@@ -26,6 +26,8 @@ SIGNATURES = {
     "fcfs_batch": (C.c_int, [_p, _p, _p, _p, _i32, _i64, _i32, _i32, _i32, _u32, _p, _p, _p, _sz, _p]),
     "fcfs_cosine_workspace_size": (_sz, [_i64, _i32, _i32, _i32]),
     "fcfs_cosine": (C.c_int, [_p, _p, _p, _i64, _i32, _i32, _i32, _u32, _p, _p, _p, _sz, _p]),
+    "fcfs_haar_workspace_size": (_sz, [_i64, _i32, _i32]),
+    "fcfs_haar": (C.c_int, [_p, _p, _p, _i64, _i32, _i32, _u32, _p, _p, _sz, _p]),
     "fcfs_get_status": (C.c_int, [_p, _p]),
     "fcfs_forward_noalloc": (C.c_int, [_p, _p, _p, _i64, _i32, _i32, _i32, _u32, _p, _p, _p]),
     "fcfs_debug_set_splits": (None, [_i32]),

@@ -9,8 +9,8 @@ import torch
 from . import _lib
 from ._lib import FCFSError, PREC, FLAG_VALIDATE
 
-__all__ = ["forward", "adjoint", "edge_chain", "batch", "cosine", "workspace_size",
-           "cosine_workspace_size", "get_status", "launch_count", "FCFSError"]
+__all__ = ["forward", "adjoint", "edge_chain", "batch", "cosine", "haar", "workspace_size",
+           "cosine_workspace_size", "haar_workspace_size", "get_status", "launch_count", "FCFSError"]
 
 
 def _ptr(t):
@@ -139,6 +139,27 @@ def cosine(x, y, s, T, K, prec="split_f16", out=None, area_out=None, workspace=N
                            _ptr(out), _ptr(area_out), _ptr(workspace), workspace.numel(), _stream(stream))
     _lib.check("fcfs_cosine", code)
     return out, area_out
+
+
+def haar_workspace_size(V, T, J):
+    return int(_lib.load().fcfs_haar_workspace_size(int(V), int(T), int(J)))
+
+
+def haar(x, y, s, T, J, out=None, workspace=None, stream=None):
+    """Continuous Haar coefficients of one clip up to level J: float64 (2^J, 2^J)
+    in the square layout of include/fcfs.h (W[0, 0] = area / T)."""
+    _check_vertices(x, y, s)
+    lib = _lib.load()
+    dev = x.device
+    G = 1 << int(J)
+    if out is None:
+        out = torch.empty((G, G), dtype=torch.float64, device=dev)
+    if workspace is None:
+        workspace = alloc_workspace(haar_workspace_size(x.numel(), T, J), dev)
+    code = lib.fcfs_haar(_ptr(x), _ptr(y), _ptr(s), x.numel(), int(T), int(J), 0, _ptr(out),
+                         _ptr(workspace), workspace.numel(), _stream(stream))
+    _lib.check("fcfs_haar", code)
+    return out
 
 
 def get_status(workspace, stream=None):

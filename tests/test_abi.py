@@ -123,3 +123,20 @@ def test_cosine_host_checks(lib):
     assert f(None, None, None, 0, 256, 8, 7, 0, 16, 16, None, 0, None) == 1           # bad precision
     assert f(None, None, None, 0, 256, 8, 1, 0, 16, 16, None, 0, None) == 3           # no workspace
     assert f(20, 32, 48, 10, 256, 8, 1, 0, 16, 16, 256, 1 << 20, None) == 1           # misaligned corners
+
+
+def test_haar_host_checks(lib):
+    """The Haar-transform entry points: sizes and host-detectable errors."""
+    hw = lib.fcfs_haar_workspace_size
+    a = hw(12576, 4096, 12)
+    assert a >= 8 * 4 ** 12 and a % 256 == 0             # the level-12 area grid
+    assert hw(0, 4096, 0) > 0 and hw(100, 16, 4) > 0
+    assert hw(100, 4096, 13) == 0                         # J > log2 T
+    assert hw(100, 65536, 15) == 0                        # J > 14
+    assert hw(100, 1000, 4) == 0 and hw(100, 256, -1) == 0
+    f = lib.fcfs_haar
+    assert f(None, None, None, 0, 256, 4, 0, None, None, 0, None) == 1        # NULL output
+    assert f(None, None, None, 0, 256, 4, 1, 16, None, 0, None) == 1          # flags must be 0
+    assert f(None, None, None, 0, 256, 9, 0, 16, None, 0, None) == 6          # J too large
+    assert f(None, None, None, 0, 256, 4, 0, 16, None, 0, None) == 3          # no workspace
+    assert f(20, 32, 48, 10, 256, 4, 0, 16, 256, 1 << 20, None) == 1          # misaligned corners
