@@ -35,6 +35,7 @@ WORKLOAD = ("clip T=4096, 2000 rectilinear polygons (rect/L/T/U/plus/stair, side
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gemm_tc_T4096_K256.md")
 FALLBACK_BF16_TFLOPS = 1900.0
+FALLBACK_HBM_GBS = 6800.0
 
 
 def parse():
@@ -54,7 +55,7 @@ def parse():
     ap.add_argument("--prec", choices=["split_f16", "fp32"], default="split_f16",
                     help="--only adjoint / adjoint_large / cosine / cosine_large: contraction precision")
     ap.add_argument("--only", choices=["step", "large", "batch", "adjoint", "adjoint_large", "cosine",
-                                       "cosine_large"], default=None,
+                                       "cosine_large", "haar", "haar_large"], default=None,
                     help="run one workload warmup + steps times and print its mean time "
                          "(for profiler command lines; not the benchmark line)")
     return ap.parse_args()
@@ -430,7 +431,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    for k in ("adjoint", "batch", "large", "cosine"):
+    for k in ("adjoint", "batch", "large", "cosine", "haar"):
         if k in extras:
             line[k] = extras[k]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -594,6 +595,7 @@ def run_extras(fcfs, dev, flush, stream, args):
     big["adjoint_split_f16"] = {"value": clip5.V * W5 * W5 / (ms_a5h * 1e-3), "ms": ms_a5h,
                                 "cotangent": "as adjoint_fp32", "_g": (gx5h, gy5h)}
     out["cosine"] = cosine_extras(fcfs, dev, flush, stream)
+    out["haar"] = haar_extras(fcfs, dev, flush, stream)
     out["large"] = {"workload": "clip T=65536, 150000 polygons, V=%d, K=1024 (2049x2049)" % clip5.V,
                     "unit": UNIT, "split_f16": big["split_f16"], "split_f16_direct": big["split_f16_direct"],
                     "fp32": big["fp32"],
@@ -631,6 +633,45 @@ def cosine_extras(fcfs, dev, flush, stream):
                 e["issued_tflops_whole_call"] = 3 * 2.0 * clip.V * K * K / (ms * 1e-3) / 1e12
             d[prec] = e
         d["_clip"] = clip
+        res[key] = d
+    return res
+
+
+def measured_hbm():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def haar_extras(fcfs, dev, flush, stream):
+    """Continuous Haar transform (all 4^J coefficients up to level J): the bench
+    clip at full depth (T = 4096, J = 12) and the T = 65536 clip at J = 14.
+    HBM roofline of the whole call: algorithmic bytes = the corners read once
+    (9 B each) plus the FP64 coefficients written once (8 B each); the pipeline
+    moves about 48 B per cell (zero, row scan read and write, column sums, the
+    fused column scan read, coefficients)."""
+    import torch
+    from synth import config_clip
+    peak, src = measured_hbm()
+    res = {"unit": "coefficients/s", "hbm_peak_gbs": peak, "peak_source": src}
+    for key, ci, J in (("clip_T4096_J12", 2, 12), ("clip_T65536_J14", 5, 14)):
+        clip, _ = config_clip(ci)
+        x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))
+        G = 1 << J
+        W = torch.empty((G, G), dtype=torch.float64, device=dev)
+        ws = torch.empty(fcfs.haar_workspace_size(clip.V, clip.T, J), dtype=torch.uint8, device=dev)
+        ms = _timed_ms(torch, lambda: fcfs.haar(x, y, s, clip.T, J, out=W, workspace=ws, stream=stream),
+                       10 if J <= 12 else 3, flush, stream)
+        alg = 9.0 * clip.V + 8.0 * G * G
+        d = {"V": clip.V, "T": clip.T, "J": J, "value": G * G / (ms * 1e-3), "ms": ms,
+             "algorithmic_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9,
+             "frac_of_hbm_peak": alg / (ms * 1e-3) / 1e9 / peak,
+             "moved_bytes_est": 48.0 * G * G + 9.0 * clip.V,
+             "moved_gbs_est": (48.0 * G * G + 9.0 * clip.V) / (ms * 1e-3) / 1e9}
+        if J == 12:
+            d["_check"] = (clip, W)
         res[key] = d
     return res
 
@@ -679,6 +720,25 @@ def extras_accuracy(line, extras):
                 C = e.pop("_C").cpu().numpy().astype(np.float64)[np.ix_(pick, pick)]
                 e["max_abs_err_over_area" + ("_sampled" if sampled else "")] = float(np.max(np.abs(C - Co)) / Aexact)
                 e["area_exact"] = int(e.pop("_A").item()) == Aexact
+    if "haar" in extras:
+        import time as _t
+        from oracle import haar as _haar
+        d = line["haar"]["clip_T4096_J12"]
+        clip, W = d.pop("_check")
+        # the oracle (per-polygon pruned recursion) on the first 200 polygons;
+        # its cost is linear in the polygons, so the full clip takes about 10x
+        n_s = 200
+        sub = clip.poly_offsets[:n_s + 1]
+        t0 = _t.perf_counter()
+        _haar.pcht(clip.x[:sub[-1]], clip.y[:sub[-1]], sub, clip.T, 12)
+        dt = _t.perf_counter() - t0
+        d["cpu_oracle"] = {"kind": "oracle", "cores": 1, "sample": "first %d of %d polygons, J = 12" % (n_s, clip.n_polys),
+                           "value": (1 << 24) / (dt * clip.n_polys / n_s), "unit": "coefficients/s",
+                           "seconds_sample": dt}
+        Wg = W.cpu().numpy()
+        A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+        d["parseval_rel_err"] = abs(float(np.sum(Wg * Wg)) - A) / A
+        d["scaling_coefficient_exact"] = bool(Wg[0, 0] == A / clip.T)
     if "large" in extras:
         clip5, K5 = extras["large"].pop("_check")
         A = oracle.area_exact(clip5.x, clip5.y, clip5.s, clip5.T)
@@ -712,7 +772,12 @@ def run_only(args):
         fcfs.set_pair(0)
     if args.no_fuse:
         fcfs.set_fuse(0)
-    if args.only in ("cosine", "cosine_large"):
+    if args.only in ("haar", "haar_large"):
+        clip, _ = config_clip(2 if args.only == "haar" else 5)
+        x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))
+        J = 12 if args.only == "haar" else 14
+        fn = lambda: fcfs.haar(x, y, s, clip.T, J)
+    elif args.only in ("cosine", "cosine_large"):
         clip, K = config_clip(2) if args.only == "cosine" else cosine_large_clip()
         x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))
         fn = lambda: fcfs.cosine(x, y, s, clip.T, K, prec=args.prec)

@@ -27,8 +27,20 @@
 //    per parent; each is an integer times 2^(j - log2 N), exact in FP64.
 // Kernels: Z zeroed (memset), splat, row scan (one CTA per row), column sums
 // per (strip of 32 columns, row segment), column scan fused with the pyramid
-// of each 32 x 32 tile (five levels), then pyramid passes on the coarse area
-// grids until one cell is left.  Everything is exact integer arithmetic.
+// of each 32 x 32 tile (five levels; one warp per strip segment), then pyramid
+// passes on the coarse area grids until one cell is left.  Everything is exact
+// integer arithmetic; the FP64 coefficients are assembled from their bits.
+//
+// Element type of Z.  No value held in Z after any of its passes is a running
+// area: a row-scanned entry is the difference of two vertically adjacent cell
+// areas, a fully scanned one a cell area, so |value| <= w^2, and a 32 x 32
+// tile's area is at most (32 w)^2.  For w <= 1024 all of them fit in int32 and
+// Z, its scans and the tile pyramid run in 32-bit integers (half the bytes and
+// the instructions); intermediate sums of the atomics and scans may wrap,
+// which two's-complement addition undoes exactly.  Larger cells use int64.
+// The coarse area grids are int64 throughout.
+#include <type_traits>
+
 #include "fcfs_common.cuh"
 
 namespace fcfs {
@@ -37,11 +49,13 @@ namespace {
 
 constexpr int kHT = 32;          // pyramid tile side (five levels per pass)
 constexpr int kHThreads = 256;
-constexpr int kHaarMaxJ = 14;    // 2^28 cells: 2 GiB of int64 areas, 2 GiB of FP64 output
+constexpr int kHaarMaxJ = 14;    // 2^28 cells: 1-2 GiB of cell areas, 2 GiB of FP64 output
+constexpr int kNarrowMaxW = 1024;   // cell side up to which Z is int32
 
 struct HaarPlan {
   int J, logN, G, N;
   int64_t V;
+  int narrow;                    // 1: Z in int32 (cell side <= kNarrowMaxW)
   int strips, segs, tiles_per_seg;
   int npass;                     // pyramid passes, the fused one first; pass p leaves a grid of coarse_side[p]
   size_t off_z, off_colsum, off_coarse[6], total;
@@ -65,20 +79,24 @@ fcfs_status make_haar_plan(int64_t V, int32_t T, int32_t J, HaarPlan& hp) {
   hp.N = T;
   hp.V = V;
   hp.G = 1 << J;
+  hp.narrow = (T >> J) <= kNarrowMaxW ? 1 : 0;
+  const size_t elem = hp.narrow ? 4 : 8;
   const int t = hp.G < kHT ? hp.G : kHT;
   const int tiles = hp.G / t;
   hp.strips = tiles;
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int segs = (2 * sms + hp.strips - 1) / hp.strips;
+  // row segments: about 24 warps per SM for the fused column scan (each warp
+  // walks its segment's tiles one after another)
+  int segs = (24 * sms + hp.strips - 1) / hp.strips;
   segs = segs < 1 ? 1 : (segs > tiles ? tiles : segs);
   hp.tiles_per_seg = (tiles + segs - 1) / segs;
   hp.segs = (tiles + hp.tiles_per_seg - 1) / hp.tiles_per_seg;
   size_t o = 256;   // header: the status word
   hp.off_z = o;
-  o = align_up(o + (size_t)hp.G * hp.G * 8, kWsAlign);
+  o = align_up(o + (size_t)hp.G * hp.G * elem, kWsAlign);
   hp.off_colsum = o;
-  o = align_up(o + (size_t)hp.segs * hp.G * 8, kWsAlign);
+  o = align_up(o + (size_t)hp.segs * hp.G * elem, kWsAlign);
   int side = tiles;   // side of the area grid each pass leaves, down to one cell
   for (;;) {
     hp.coarse_side[hp.npass] = side;
@@ -95,10 +113,14 @@ fcfs_status make_haar_plan(int64_t V, int32_t T, int32_t J, HaarPlan& hp) {
 __device__ __forceinline__ void red_add(long long* p, long long v) {
   atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
+__device__ __forceinline__ void red_add(int* p, long long v) {
+  atomicAdd(reinterpret_cast<unsigned int*>(p), (unsigned int)v);   // modulo 2^32
+}
 
 // Four splat weights per corner; corners outside [0, N] are dropped.
+template <typename E>
 __global__ void haar_splat_kernel(const int32_t* __restrict__ x, const int32_t* __restrict__ y,
-                                  const int8_t* __restrict__ s, long long V, int N, int J, int lw, long long* Z) {
+                                  const int8_t* __restrict__ s, long long V, int N, int J, int lw, E* Z) {
   const int G = 1 << J;
   const long long w = 1LL << lw;   // cell side N / 2^J
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
@@ -106,7 +128,7 @@ __global__ void haar_splat_kernel(const int32_t* __restrict__ x, const int32_t* 
     if (xv < 0 || xv >= N || yv < 0 || yv >= N || (sv != 1 && sv != -1)) continue;   // x = N: empty quadrant
     const int c = xv >> lw, d = yv >> lw;
     const long long r = (long long)(c + 1) * w - xv, q = (long long)(d + 1) * w - yv;   // in (0, w]
-    long long* row = Z + (size_t)c * G;
+    E* row = Z + (size_t)c * G;
     red_add(row + d, sv * r * q);
     if (q < w && d + 1 < G) red_add(row + d + 1, sv * r * (w - q));
     if (r < w && c + 1 < G) {
@@ -116,41 +138,51 @@ __global__ void haar_splat_kernel(const int32_t* __restrict__ x, const int32_t* 
   }
 }
 
-__device__ __forceinline__ long long warp_incl_scan(long long v, int lane) {
+template <typename E>
+__device__ __forceinline__ E warp_incl_scan(E v, int lane) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    const long long t = __shfl_up_sync(0xffffffffu, v, d);
+    const E t = __shfl_up_sync(0xffffffffu, v, d);
     if (lane >= d) v += t;
   }
   return v;
 }
 
-__device__ __forceinline__ long long warp_sum(long long v) {
+template <typename E>
+__device__ __forceinline__ E warp_sum(E v) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
   return v;
 }
 
+// 32-bit sums wrap (modulo 2^32) instead of overflowing
+__device__ __forceinline__ int wadd(int a, int b) { return (int)((unsigned)a + (unsigned)b); }
+__device__ __forceinline__ long long wadd(long long a, long long b) { return a + b; }
+
 // Inclusive prefix sum along every row of Z (G x G), in place.  One CTA per
 // row; warp w owns the segment [w seg, (w+1) seg): it sums the segment, the
 // CTA combines the eight totals, and each warp rescans its segment in chunks
 // of 32 (one element per lane) from its offset.
-__global__ void __launch_bounds__(kHThreads) haar_row_scan_kernel(long long* Z, int G) {
-  __shared__ long long tot[kHThreads / 32];
+template <typename E>
+__global__ void __launch_bounds__(kHThreads) haar_row_scan_kernel(E* Z, int G) {
+  using U = typename std::conditional<sizeof(E) == 4, unsigned, unsigned long long>::type;
+  __shared__ U tot[kHThreads / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  long long* row = Z + (size_t)blockIdx.x * G;
+  U* row = reinterpret_cast<U*>(Z) + (size_t)blockIdx.x * G;
   const int seg = (G + kHThreads / 32 - 1) / (kHThreads / 32);
   const int b = warp * seg, e = min(G, b + seg);
-  long long sum = 0;
+  U sum = 0;
+#pragma unroll 8
   for (int i = b + lane; i < e; i += 32) sum += row[i];
   sum = warp_sum(sum);
   if (lane == 0) tot[warp] = sum;
   __syncthreads();
-  long long off = 0;
+  U off = 0;
   for (int w2 = 0; w2 < warp; ++w2) off += tot[w2];
+#pragma unroll 4
   for (int i0 = b; i0 < e; i0 += 32) {   // warp-uniform
     const int i = i0 + lane;
-    long long v = i < e ? row[i] : 0;
+    U v = i < e ? row[i] : 0;
     v = warp_incl_scan(v, lane);
     if (i < e) row[i] = v + off;
     off += __shfl_sync(0xffffffffu, v, 31);
@@ -158,147 +190,250 @@ __global__ void __launch_bounds__(kHThreads) haar_row_scan_kernel(long long* Z, 
 }
 
 // colsum[seg][col] = sum of Z over the rows of segment seg, for the 32 columns
-// of strip blockIdx.x.
-__global__ void __launch_bounds__(kHThreads) haar_colsum_kernel(const long long* __restrict__ Z, int G,
-                                                                int rows_per_seg, long long* colsum) {
-  __shared__ long long part[kHThreads / 32][kHT];
+// of strip blockIdx.x (modulo the width of E: only differences of them are used).
+template <typename E>
+__global__ void __launch_bounds__(kHThreads) haar_colsum_kernel(const E* __restrict__ Z, int G, int rows_per_seg,
+                                                                E* colsum) {
+  using U = typename std::conditional<sizeof(E) == 4, unsigned, unsigned long long>::type;
+  __shared__ U part[kHThreads / 32][kHT];
   const int t = G < kHT ? G : kHT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int col = blockIdx.x * t + lane;
   const int r0 = blockIdx.y * rows_per_seg, r1 = min(G, r0 + rows_per_seg);
-  long long sum = 0;
+  const U* Zu = reinterpret_cast<const U*>(Z);
+  U sum = 0;
   if (lane < t)
-    for (int r = r0 + warp; r < r1; r += kHThreads / 32) sum += Z[(size_t)r * G + col];
+    for (int r = r0 + warp; r < r1; r += kHThreads / 32) sum += Zu[(size_t)r * G + col];
   part[warp][lane] = sum;
   __syncthreads();
   if (warp == 0 && lane < t) {
-    long long tsum = 0;
+    U tsum = 0;
     for (int w2 = 0; w2 < kHThreads / 32; ++w2) tsum += part[w2][lane];
-    colsum[(size_t)blockIdx.y * G + col] = tsum;
+    reinterpret_cast<U*>(colsum)[(size_t)blockIdx.y * G + col] = tsum;
   }
+}
+
+// num * 2^e as an IEEE-754 binary64 value, built from the format's fields with
+// integer operations only (GB300 runs FP64 conversions and scaling at a small
+// fraction of its integer rate): the sign bit, the biased exponent of the
+// leading one, and the bits below the leading one as the 52-bit fraction.
+// Exact for |num| < 2^53; the numerators here are at most 4 N^2 <= 2^34 and
+// the exponents stay in the normal range (e >= -16).
+__device__ __forceinline__ double dyadic(long long num, int e) {
+  if (num == 0) return 0.0;
+  const unsigned long long sign = num < 0 ? (1ULL << 63) : 0ULL;
+  const unsigned long long m = num < 0 ? (unsigned long long)(-num) : (unsigned long long)num;
+  const int msb = 63 - __clzll((long long)m);
+  const unsigned long long frac = ((m << (63 - msb)) << 1) >> 12;
+  const unsigned long long expo = (unsigned long long)(msb + e + 1023) << 52;
+  return __longlong_as_double((long long)(sign | expo | frac));
+}
+// the same for |num| < 2^31: the fraction is the bits below the leading one
+// shifted up to 52 bits, split into the two 32-bit halves of the value
+__device__ __forceinline__ double dyadic(int num, int e) {
+  if (num == 0) return 0.0;
+  const unsigned sign = num < 0 ? 0x80000000u : 0u;
+  const unsigned m = num < 0 ? (unsigned)(-num) : (unsigned)num;
+  const int msb = 31 - __clz(m);
+  const unsigned long long frac = (unsigned long long)(m ^ (1u << msb)) << (52 - msb);
+  const unsigned hi = sign | ((unsigned)(msb + e + 1023) << 20) | (unsigned)(frac >> 32);
+  return __hiloint2double((int)hi, (int)(unsigned)frac);
+}
+
+// One parent (p, q) at level j: its three wavelet coefficients go to W and its
+// area is returned.  a holds the children (level j + 1 areas); (ti, tj) is the
+// tile, h its parents per side at this level; W has side WG <= 2^14, so its
+// offsets fit in 32 bits.
+template <typename E>
+__device__ __forceinline__ E parent(E (*a)[kHT + 1], int p, int q, int ti, int tj, int h, int j, int logN, double* W,
+                                    int WG) {
+  const E a00 = a[2 * p][2 * q], a01 = a[2 * p][2 * q + 1];
+  const E a10 = a[2 * p + 1][2 * q], a11 = a[2 * p + 1][2 * q + 1];
+  const unsigned P = 1u << j;
+  const unsigned kx = (unsigned)(ti * h + p), ky = (unsigned)(tj * h + q);
+  const int e = j - logN;
+  W[(P + kx) * (unsigned)WG + ky] = dyadic((E)((a00 + a01) - (a10 + a11)), e);
+  W[kx * (unsigned)WG + P + ky] = dyadic((E)((a00 - a01) + (a10 - a11)), e);
+  W[(P + kx) * (unsigned)WG + P + ky] = dyadic((E)((a00 - a01) - (a10 - a11)), e);
+  return (a00 + a01) + (a10 + a11);
 }
 
 // Reduce the t x t tile of level-L cell areas in a[][] through log2 t levels:
 // the wavelet coefficients of levels L - 1 .. L - log2 t go to W (side WG), and
 // a[0][0] ends as the tile's area.  (ti, tj): the tile's position in tiles.
+// Levels with more than 64 parents use the whole CTA; warp 0 finishes the
+// rest alone (threads of the other warps return at once).
 __device__ void tile_pyramid(long long (*a)[kHT + 1], int t, int ti, int tj, int L, int logN, double* W, int WG) {
   const int tid = threadIdx.x;
-  int cl = L;
-  for (int sd = t; sd > 1; sd >>= 1, --cl) {
-    const int h = sd >> 1, j = cl - 1;
+  int cl = L, sd = t;
+  for (; sd > 1 && (sd >> 1) * (sd >> 1) > 64; sd >>= 1, --cl) {
+    const int h = sd >> 1;
     const bool act = tid < h * h;
     const int p = act ? tid / h : 0, q = act ? tid % h : 0;
-    long long area = 0;
-    if (act) {
-      const long long a00 = a[2 * p][2 * q], a01 = a[2 * p][2 * q + 1];
-      const long long a10 = a[2 * p + 1][2 * q], a11 = a[2 * p + 1][2 * q + 1];
-      area = (a00 + a01) + (a10 + a11);
-      const long long P = 1LL << j;
-      const long long kx = (long long)ti * h + p, ky = (long long)tj * h + q;
-      const int e = j - logN;
-      W[(size_t)(P + kx) * WG + ky] = ldexp((double)((a00 + a01) - (a10 + a11)), e);
-      W[(size_t)kx * WG + P + ky] = ldexp((double)((a00 - a01) + (a10 - a11)), e);
-      W[(size_t)(P + kx) * WG + P + ky] = ldexp((double)((a00 - a01) - (a10 - a11)), e);
-    }
+    const long long area = act ? parent(a, p, q, ti, tj, h, cl - 1, logN, W, WG) : 0;
     __syncthreads();
     if (act) a[p][q] = area;
     __syncthreads();
   }
+  if (tid >= 32) return;
+  for (; sd > 1; sd >>= 1, --cl) {
+    const int h = sd >> 1, np = h * h;   // at most 64 parents: two per lane
+    long long ar[2] = {0, 0};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int idx = tid + 32 * u;
+      if (idx < np) ar[u] = parent(a, idx / h, idx % h, ti, tj, h, cl - 1, logN, W, WG);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int idx = tid + 32 * u;
+      if (idx < np) a[idx / h][idx % h] = ar[u];
+    }
+    __syncwarp();
+  }
 }
 
-// SCAN: blockIdx = (strip, segment); the CTA walks the segment's tiles of the
-// row-scanned Z from top to bottom, finishing the column scan with carries
-// (the column sums of the segments above, then of the tiles it has done), and
-// reduces each tile.  !SCAN: one CTA per tile of an area grid of side G.
-// Each tile's area goes to coarse[ti][tj] (side G / t); the last pass (G == t)
-// also writes W[0][0] = area / N.
-template <bool SCAN>
-__global__ void __launch_bounds__(kHThreads) haar_pyramid_kernel(const long long* __restrict__ A, int G, int L,
-                                                                 int logN, const long long* __restrict__ colsum,
-                                                                 int tiles_per_seg, long long* coarse, double* W,
-                                                                 int WG) {
-  __shared__ long long a[kHT][kHT + 1];
-  __shared__ long long carry[kHT];
+// The t x t tile in a[][] (the warp's own shared memory) reduced through
+// log2 t levels by one warp (up to 256 parents a level: eight per lane);
+// a[0][0] ends as the tile's area.
+template <typename E>
+__device__ void warp_pyramid(E (*a)[kHT + 1], int t, int ti, int tj, int L, int logN, double* W, int WG, int lane) {
+  int cl = L;
+  for (int sd = t; sd > 1; sd >>= 1, --cl) {
+    const int h = sd >> 1, lh = __ffs(h) - 1, np = h * h;
+    E ar[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = lane + 32 * u;
+      ar[u] = idx < np ? parent(a, idx >> lh, idx & (h - 1), ti, tj, h, cl - 1, logN, W, WG) : (E)0;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = lane + 32 * u;
+      if (idx < np) a[idx >> lh][idx & (h - 1)] = ar[u];
+    }
+    __syncwarp();
+  }
+}
+
+constexpr int kStripWarps = 8;
+
+template <typename E>
+size_t strip_smem_bytes() { return (size_t)kStripWarps * kHT * (kHT + 1) * sizeof(E); }
+
+// Column scan of the row-scanned Z fused with the pyramid of its tiles.  One
+// warp per (strip of t columns, segment of tiles_per_seg tile rows), no block
+// barrier: lane c owns column c of the strip.  Per tile it loads its t values
+// (independent loads), adds them down the column in registers from the carry
+// (the column sums of the segments above, then of the tiles done), stages the
+// tile in the warp's shared memory and reduces it (levels J - 1 .. J - log2 t).
+// The tile's area goes to coarse; with a single tile, W[0][0] too.
+template <typename E>
+__global__ void __launch_bounds__(kStripWarps * 32, sizeof(E) == 4 ? 3 : 2) haar_strip_kernel(const E* __restrict__ Z, int G, int J, int logN,
+                                                                     const E* __restrict__ colsum, int strips,
+                                                                     int segs, int tiles_per_seg, long long* coarse,
+                                                                     double* W) {
+  extern __shared__ __align__(16) unsigned char hsm_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kStripWarps + warp;
+  if (gw >= strips * segs) return;   // whole warps; nothing below waits on other warps
+  E(*a)[kHT + 1] = reinterpret_cast<E(*)[kHT + 1]>(hsm_raw + (size_t)warp * kHT * (kHT + 1) * sizeof(E));
   const int t = G < kHT ? G : kHT;
   const int tiles = G / t;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  int tj, ti0, ti1;
-  if (SCAN) {
-    tj = blockIdx.x;
-    ti0 = blockIdx.y * tiles_per_seg;
-    ti1 = min(tiles, ti0 + tiles_per_seg);
-    if (tid < t) {
-      long long c0 = 0;
-      for (int sg = 0; sg < (int)blockIdx.y; ++sg) c0 += colsum[(size_t)sg * G + tj * t + tid];
-      carry[tid] = c0;
-    }
-  } else {
-    ti0 = blockIdx.x / tiles;
-    tj = blockIdx.x % tiles;
-    ti1 = ti0 + 1;
-  }
+  const int tj = gw % strips, sg = gw / strips;
+  const int ti0 = sg * tiles_per_seg, ti1 = min(tiles, ti0 + tiles_per_seg);
+  const bool col_ok = lane < t;
+  E carry = 0;
+  if (col_ok)
+    for (int s2 = 0; s2 < sg; ++s2) carry = wadd(carry, colsum[(size_t)s2 * G + tj * t + lane]);
   for (int ti = ti0; ti < ti1; ++ti) {
-    __syncthreads();
+    E v[kHT];
+    const E* src = Z + (size_t)ti * t * G + (size_t)tj * t + lane;
 #pragma unroll
-    for (int k = 0; k < kHT * kHT / kHThreads; ++k) {
-      const int r = (tid >> 5) + (kHThreads / 32) * k, c = tid & 31;
-      if (r < t && c < t) a[r][c] = A[(size_t)(ti * t + r) * G + tj * t + c];
+    for (int r = 0; r < kHT; ++r) v[r] = (col_ok && r < t) ? src[(size_t)r * G] : (E)0;
+    __syncwarp();   // lane 0's read of the previous tile's a[0][0] is done
+#pragma unroll
+    for (int r = 0; r < kHT; ++r) {
+      carry = wadd(carry, v[r]);
+      if (col_ok && r < t) a[r][lane] = carry;
     }
-    __syncthreads();
-    if (SCAN) {   // inclusive scan down each column of the tile, from the carry
-      for (int cc = warp; cc < t; cc += kHThreads / 32) {
-        long long v = lane < t ? a[lane][cc] : 0;
-        v = warp_incl_scan(v, lane) + carry[cc];
-        if (lane < t) a[lane][cc] = v;
-        const long long last = __shfl_sync(0xffffffffu, v, t - 1);
-        __syncwarp();
-        if (lane == 0) carry[cc] = last;
-      }
-      __syncthreads();
-    }
-    tile_pyramid(a, t, ti, tj, L, logN, W, WG);
-    if (tid == 0) {
-      const long long area = a[0][0];
+    __syncwarp();
+    warp_pyramid(a, t, ti, tj, J, logN, W, G, lane);
+    if (lane == 0) {
+      const long long area = (long long)a[0][0];
       coarse[(size_t)ti * tiles + tj] = area;
-      if (tiles == 1) W[0] = ldexp((double)area, -logN);
+      if (tiles == 1) W[0] = dyadic(area, -logN);
     }
   }
 }
 
-cudaError_t launch_haar(const HaarPlan& hp, const int32_t* x, const int32_t* y, const int8_t* s, uint8_t* ws,
-                        double* W, cudaStream_t st) {
+// One CTA per t x t tile of a coarse area grid of side G (cells of level L):
+// the tile's levels L - 1 .. L - log2 t; its area goes to coarse[ti][tj], and
+// the last pass (a single tile) writes W[0][0] = area / N.
+__global__ void __launch_bounds__(kHThreads) haar_coarse_kernel(const long long* __restrict__ A, int G, int L,
+                                                                int logN, long long* coarse, double* W, int WG) {
+  __shared__ long long a[kHT][kHT + 1];
+  const int t = G < kHT ? G : kHT;
+  const int tiles = G / t;
+  const int tid = threadIdx.x;
+  const int ti = blockIdx.x / tiles, tj = blockIdx.x % tiles;
+#pragma unroll
+  for (int k = 0; k < kHT * kHT / kHThreads; ++k) {
+    const int r = (tid >> 5) + (kHThreads / 32) * k, c = tid & 31;
+    if (r < t && c < t) a[r][c] = A[(size_t)(ti * t + r) * G + tj * t + c];
+  }
+  __syncthreads();
+  tile_pyramid(a, t, ti, tj, L, logN, W, WG);
+  if (tid == 0) {
+    const long long area = a[0][0];
+    coarse[(size_t)ti * tiles + tj] = area;
+    if (tiles == 1) W[0] = dyadic(area, -logN);
+  }
+}
+
+template <typename E>
+cudaError_t launch_haar_t(const HaarPlan& hp, const int32_t* x, const int32_t* y, const int8_t* s, uint8_t* ws,
+                          double* W, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(ws, 0, hp.off_colsum, st);   // header and Z
   if (e != cudaSuccess) return e;
-  long long* Z = reinterpret_cast<long long*>(ws + hp.off_z);
+  E* Z = reinterpret_cast<E*>(ws + hp.off_z);
   const int G = hp.G, t = G < kHT ? G : kHT;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (hp.V > 0) {
     const int blocks = (int)std::min<long long>((hp.V + 255) / 256, 8LL * sms);
-    haar_splat_kernel<<<blocks, 256, 0, st>>>(x, y, s, hp.V, hp.N, hp.J, hp.logN - hp.J, Z);
+    haar_splat_kernel<E><<<blocks, 256, 0, st>>>(x, y, s, hp.V, hp.N, hp.J, hp.logN - hp.J, Z);
     count_launch(1);
   }
-  haar_row_scan_kernel<<<G, kHThreads, 0, st>>>(Z, G);
+  haar_row_scan_kernel<E><<<G, kHThreads, 0, st>>>(Z, G);
   count_launch(1);
-  long long* colsum = reinterpret_cast<long long*>(ws + hp.off_colsum);
-  haar_colsum_kernel<<<dim3(hp.strips, hp.segs), kHThreads, 0, st>>>(Z, G, hp.tiles_per_seg * t, colsum);
+  E* colsum = reinterpret_cast<E*>(ws + hp.off_colsum);
+  haar_colsum_kernel<E><<<dim3(hp.strips, hp.segs), kHThreads, 0, st>>>(Z, G, hp.tiles_per_seg * t, colsum);
   count_launch(1);
   long long* coarse = reinterpret_cast<long long*>(ws + hp.off_coarse[0]);
-  haar_pyramid_kernel<true><<<dim3(hp.strips, hp.segs), kHThreads, 0, st>>>(Z, G, hp.J, hp.logN, colsum,
-                                                                            hp.tiles_per_seg, coarse, W, G);
+  const int warps = hp.strips * hp.segs;
+  ensure_smem(reinterpret_cast<const void*>(haar_strip_kernel<E>), strip_smem_bytes<E>());
+  haar_strip_kernel<E><<<(warps + kStripWarps - 1) / kStripWarps, kStripWarps * 32, strip_smem_bytes<E>(), st>>>(
+      Z, G, hp.J, hp.logN, colsum, hp.strips, hp.segs, hp.tiles_per_seg, coarse, W);
   count_launch(1);
   int L = hp.J - ilog2(t);
   for (int p = 1; p < hp.npass; ++p) {
     const int g = hp.coarse_side[p - 1], tt = g < kHT ? g : kHT;
     long long* next = reinterpret_cast<long long*>(ws + hp.off_coarse[p]);
-    haar_pyramid_kernel<false><<<(g / tt) * (g / tt), kHThreads, 0, st>>>(coarse, g, L, hp.logN, nullptr, 0, next,
-                                                                         W, G);
+    haar_coarse_kernel<<<(g / tt) * (g / tt), kHThreads, 0, st>>>(coarse, g, L, hp.logN, next, W, G);
     count_launch(1);
     coarse = next;
     L -= ilog2(tt);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_haar(const HaarPlan& hp, const int32_t* x, const int32_t* y, const int8_t* s, uint8_t* ws,
+                        double* W, cudaStream_t st) {
+  return hp.narrow ? launch_haar_t<int>(hp, x, y, s, ws, W, st) : launch_haar_t<long long>(hp, x, y, s, ws, W, st);
 }
 
 }  // namespace

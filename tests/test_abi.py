@@ -129,7 +129,8 @@ def test_haar_host_checks(lib):
     """The Haar-transform entry points: sizes and host-detectable errors."""
     hw = lib.fcfs_haar_workspace_size
     a = hw(12576, 4096, 12)
-    assert a >= 8 * 4 ** 12 and a % 256 == 0             # the level-12 area grid
+    assert a >= 4 * 4 ** 12 and a % 256 == 0             # the level-12 cell grid (int32: cells of side 1)
+    assert hw(100, 65536, 5) >= 8 * 4 ** 5                # cells of side 2048: int64 grid
     assert hw(0, 4096, 0) > 0 and hw(100, 16, 4) > 0
     assert hw(100, 4096, 13) == 0                         # J > log2 T
     assert hw(100, 65536, 15) == 0                        # J > 14

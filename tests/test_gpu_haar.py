@@ -65,6 +65,19 @@ def test_haar_every_level_of_a_tiny_tile(fc):
         assert np.array_equal(W, haar.pcht(clip.x, clip.y, clip.poly_offsets, 16, J)), J
 
 
+def test_haar_wide_cells(fc):
+    """Cells wider than 1024 (Z and the tile pyramid in 64-bit integers) and the
+    boundary w = 1024 (the widest cells on the 32-bit path)."""
+    clip = make_clip(8192, 200, 68, smin=20, smax=400)
+    for J in range(5):   # w = 8192 .. 512
+        W = gpu_haar(fc, clip, J).cpu().numpy()
+        assert np.array_equal(W, haar.pcht(clip.x, clip.y, clip.poly_offsets, 8192, J)), J
+    clip = make_clip(65536, 300, 67, smin=20, smax=2000)
+    for J in (5, 6):     # w = 2048, 1024
+        W = gpu_haar(fc, clip, J).cpu().numpy()
+        assert np.array_equal(W, haar.pcht(clip.x, clip.y, clip.poly_offsets, 65536, J)), J
+
+
 def test_haar_workload2_clip(fc):
     """The T = 4096 bench clip (2000 polygons) at full depth J = 12: 16.8M
     coefficients, bit-exact; Parseval gives the area."""
