@@ -450,10 +450,18 @@ def run_ours(args):
         if extras:
             extras_accuracy(line, extras)
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(strip_private(line)), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def strip_private(obj):
+    """Drop the bookkeeping entries (keys starting with '_') that the accuracy
+    pass consumes, e.g. when it is skipped."""
+    if isinstance(obj, dict):
+        return {k: strip_private(v) for k, v in obj.items() if not str(k).startswith("_")}
+    return obj
 
 
 # ---------------------------------------------------------------------------
