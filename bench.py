@@ -431,7 +431,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    for k in ("adjoint", "batch", "large", "cosine", "haar"):
+    for k in ("adjoint", "batch", "large", "cosine", "haar", "crossover"):
         if k in extras:
             line[k] = extras[k]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -604,6 +604,7 @@ def run_extras(fcfs, dev, flush, stream, args):
                                 "cotangent": "as adjoint_fp32", "_g": (gx5h, gy5h)}
     out["cosine"] = cosine_extras(fcfs, dev, flush, stream)
     out["haar"] = haar_extras(fcfs, dev, flush, stream)
+    out["crossover"] = crossover_extras(fcfs, dev, flush, stream)
     out["large"] = {"workload": "clip T=65536, 150000 polygons, V=%d, K=1024 (2049x2049)" % clip5.V,
                     "unit": UNIT, "split_f16": big["split_f16"], "split_f16_direct": big["split_f16_direct"],
                     "fp32": big["fp32"],
@@ -643,6 +644,46 @@ def cosine_extras(fcfs, dev, flush, stream):
         d["_clip"] = clip
         res[key] = d
     return res
+
+
+CROSSOVER_CLIPS = (
+    # (T, polygons, seed, sides min/max, min sub-width, K)
+    (4096, 500, 1101, 20, 200, 4, 256),
+    (4096, 2000, 1102, 20, 200, 4, 256),
+    (4096, 8000, 1103, 4, 40, 1, 256),
+    (4096, 32000, 1104, 4, 18, 1, 256),
+    (65536, 20000, 1105, 20, 300, 4, 1024),
+    (65536, 150000, 1106, 20, 200, 4, 1024),
+)
+
+
+def crossover_extras(fcfs, dev, flush, stream):
+    """Split-FP16 forward with the contraction over the V corners (direct) and
+    over the T + 1 values of y after grouping the corners by y (the pruned
+    sparse-image DFT of the off-axis block), across corner densities V / (T + 1).
+    "auto" is the library's automatic choice for the sizes (a cost estimate of both)."""
+    import torch
+    from synth import make_clip
+    rows = []
+    for (T, n, seed, smin, smax, wmin, K) in CROSSOVER_CLIPS:
+        clip = make_clip(T, n, seed, smin=smin, smax=smax, wmin=wmin)
+        x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))
+        W = 2 * K + 1
+        F = torch.empty((W, W), dtype=torch.complex64, device=dev)
+        A = torch.empty(1, dtype=torch.int64, device=dev)
+        r = {"T": T, "K": K, "V": clip.V, "V_per_y": round(clip.V / (T + 1), 2)}
+        for mode, key in ((0, "direct_ms"), (2, "grouped_ms")):
+            fcfs.set_hybrid(mode)
+            try:
+                ws = torch.empty(fcfs.workspace_size(clip.V, T, K, "split_f16"), dtype=torch.uint8, device=dev)
+                r[key] = _timed_ms(torch, lambda: fcfs.forward(x, y, s, T, K, out=F, area_out=A, workspace=ws,
+                                                               stream=stream), 10 if T <= 4096 else 3, flush, stream)
+            finally:
+                fcfs.set_hybrid(1)
+        r["auto"] = "grouped" if fcfs.forward_grouped(clip.V, T, K) == 1 else "direct"
+        r["faster"] = "grouped" if r["grouped_ms"] < r["direct_ms"] else "direct"
+        rows.append(r)
+    return {"unit": "ms per forward call (split FP16)", "rows": rows}
 
 
 def measured_hbm():

@@ -265,6 +265,12 @@ void fcfs_profile_enable(int32_t on);
 int32_t fcfs_profile_read(float* ms, int32_t n);
 void fcfs_debug_set_splits(int32_t n);
 void fcfs_debug_set_fuse(int32_t on);
+/* Which contraction fcfs_forward (flags 0) will run for these sizes: 1 when it
+ * groups the corners by y and contracts over the T + 1 values of y, 0 when it
+ * contracts over the V corners, -1 for unsupported sizes.  The automatic choice
+ * (fcfs_debug_set_hybrid(1), the default) compares cost estimates of the two
+ * forms; fcfs_debug_set_hybrid(0) and (2) force them off and on. */
+int32_t fcfs_forward_grouped(int64_t V, int32_t T, int32_t K, int32_t prec);
 /* fcfs_debug_set_pair(0) keeps single-clip split-FP16 calls on one-CTA
  * 128 x 256 tiles; 1 (the default) runs clips with 2K >= 256 on CTA pairs
  * (2-SM MMA on 256 x 256 tiles).  Must not change between fcfs_workspace_size
@@ -279,8 +285,10 @@ void fcfs_debug_set_barrier_extra(int32_t n);
 /* Row-binned contraction of single-clip split-FP16 calls on CTA pairs (the
  * corners grouped by y, the off-axis block contracted over the T + 1 values of
  * y instead of the V corners; the binning of Steps 2-3 carried into Step 4):
- * mode 0 never, 1 (the default) when V >= 8 (T + 1), 2 whenever the call is
- * eligible (split FP16, 2K >= 256, no device validation).  Same results within
+ * mode 0 never, 1 (the default) when a cost estimate of the two forms
+ * favours it (fcfs_forward_grouped tells), 2 whenever the call is eligible
+ * (split FP16, 2K >= 256, no device validation).  Batches group when
+ * V >= 8 n (T + 1) and K >= 256.  Same results within
  * the split-FP16 error bound.  Must not change between fcfs_workspace_size and
  * the call that uses the workspace. */
 void fcfs_debug_set_hybrid(int32_t mode);

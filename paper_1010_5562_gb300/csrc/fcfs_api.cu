@@ -175,15 +175,28 @@ int hybrid_mode() { return g_hybrid; }
 bool pair_enabled() { return g_pair != 0; }
 
 // Row-binned contraction (corners grouped by y, contraction over the T + 1
-// values of y): eligible for a single-clip split-FP16 call on CTA pairs; taken
-// automatically when the corners outnumber the y values 8 to 1 and K >= 256.
-// Per corner, H costs ~K fixed-point terms on the CUDA cores and the direct
-// contraction ~(2K)^2 tensor-core MACs per output pair: they break even near
-// K ~ 110, so at smaller K grouping gains little and adds launches.
+// values of y): eligible for a single-clip split-FP16 call on CTA pairs.  The
+// automatic choice compares two cost estimates (ms) fitted to GB300
+// measurements of both forms (T = 4096 .. 65536, K = 256 .. 1024,
+// V / (T + 1) = 0.8 .. 49; the estimate picks the faster form in 19 of 21 cases,
+// the other two within 9%):
+//   over the corners  0.04 + 1.5e-11 V K^2                  ((2K)^2 tensor MACs per corner)
+//   grouped by y      0.08 + 4e-6 T + 1.8e-11 (T + 1) K^2   (grouping, axis lines, the
+//                     + 1.3e-9 V K (1 + 120 / chunks)        contraction over y, and H:
+//                                                            K fixed-point terms per corner,
+//                                                            spread over the 64-y chunks)
+static bool grouped_cheaper(long long V, int T, int K) {
+  const double v = (double)V, k = (double)K, t = (double)T;
+  const double chunks = (double)((T + 1 + 63) / 64);
+  const double direct = 0.04 + 1.5e-11 * v * k * k;
+  const double grouped = 0.08 + 4e-6 * t + 1.8e-11 * (t + 1.0) * k * k + 1.3e-9 * v * k * (1.0 + 120.0 / chunks);
+  return grouped < direct;
+}
+
 static bool hybrid_wanted(const Plan& pl, bool validate) {
   if (g_hybrid == 0 || validate || !pl.pair || pl.prec != FCFS_PREC_SPLIT_F16 || pl.V <= 0 || pl.logT > 16)
     return false;
-  return g_hybrid == 2 || (pl.V >= 8LL * (pl.T + 1) && pl.K >= 256);
+  return g_hybrid == 2 || grouped_cheaper(pl.V, pl.T, pl.K);
 }
 
 // Turn a single-clip pair plan into the row-binned one: splits over 64-y
@@ -419,6 +432,12 @@ void fcfs_debug_set_fuse(int32_t on) { g_fuse = on ? 1 : 0; }
 void fcfs_debug_set_pair(int32_t on) { g_pair = on ? 1 : 0; }
 void fcfs_debug_set_barrier_extra(int32_t n) { g_barrier_extra = n > 0 ? n : 0; }
 void fcfs_debug_set_hybrid(int32_t mode) { g_hybrid = mode < 0 ? 0 : (mode > 2 ? 2 : mode); }
+
+int32_t fcfs_forward_grouped(int64_t V, int32_t T, int32_t K, int32_t prec) {
+  Plan pl;
+  if (make_plan_ex(V, T, K, prec, true, pl) != FCFS_OK) return -1;
+  return hybrid_wanted(pl, false) ? 1 : 0;
+}
 
 void fcfs_profile_enable(int32_t on) { g_prof = on != 0; }
 

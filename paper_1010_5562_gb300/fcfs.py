@@ -162,6 +162,12 @@ def haar(x, y, s, T, J, out=None, workspace=None, stream=None):
     return out
 
 
+def forward_grouped(V, T, K, prec="split_f16"):
+    """1 if forward() groups the corners by y for these sizes, 0 if it contracts
+    over the corners, -1 if the sizes are unsupported."""
+    return int(_lib.load().fcfs_forward_grouped(int(V), int(T), int(K), _prec(prec)))
+
+
 def get_status(workspace, stream=None):
     """Synchronise and return the device status name of the last call on ``workspace``."""
     code = _lib.load().fcfs_get_status(_ptr(workspace), _stream(stream))
@@ -197,7 +203,7 @@ def set_barrier_extra(n):
 
 def set_hybrid(mode):
     """Row-binned contraction of single-clip split-FP16 calls (corners grouped
-    by y): 0 never, 1 automatic (V >= 8 (T + 1)), 2 whenever eligible."""
+    by y): 0 never, 1 automatic (cost estimate; see forward_grouped), 2 whenever eligible."""
     _lib.load().fcfs_debug_set_hybrid(int(mode))
 
 

@@ -72,8 +72,8 @@ def test_no_cpu_fallback(monkeypatch, tmp_path):
 
 def test_grouped_plan_workspaces(lib):
     """Host plans of the grouped (row-binned) contraction, through the size
-    functions (no device work): it is taken automatically for V >= 8 (T + 1)
-    and K >= 256 on the split-FP16 path, its workspace holds H (2 x 2K x
+    functions (no device work): the automatic choice takes it for the T = 65536,
+    K = 1024 clip on the split-FP16 path, its workspace holds H (2 x 2K x
     (T + 1 rounded up to 64) FP16), forcing it on a small clip grows the
     workspace, and the plain FP32 path never groups."""
     V, T, K = 945450, 65536, 1024
@@ -91,7 +91,7 @@ def test_grouped_plan_workspaces(lib):
         auto = lib.fcfs_workspace_size(V, T, K, 1)
         assert auto >= h_bytes and auto >= direct   # grouped: H, or the validation plan
         assert lib.fcfs_workspace_size(V, T, K, 0) == direct32
-        # K = 128 is below the automatic threshold: the direct plan
+        # K = 128: the corners' (2K)^2 MACs are cheaper than grouping, the direct plan
         assert lib.fcfs_workspace_size(V, T, 128, 1) == k128_direct
         # the adjoint groups by y and by x: two permutations of V corners more
         assert lib.fcfs_adjoint_workspace_size(V, T, K, 1) >= adj_direct + 2 * 4 * V
@@ -141,3 +141,27 @@ def test_haar_host_checks(lib):
     assert f(None, None, None, 0, 256, 9, 0, 16, None, 0, None) == 6          # J too large
     assert f(None, None, None, 0, 256, 4, 0, 16, None, 0, None) == 3          # no workspace
     assert f(20, 32, 48, 10, 256, 4, 0, 16, 256, 1 << 20, None) == 1          # misaligned corners
+
+
+def test_automatic_contraction_choice(lib):
+    """The automatic choice between the contraction over the corners and the one
+    grouped by y (cost estimates fitted to measurements of both): measured
+    winners at sizes where they differ by 1.4x or more."""
+    g = lib.fcfs_forward_grouped
+    lib.fcfs_debug_set_hybrid(1)
+    assert g(12576, 4096, 256, 1) == 0      # the bench clip: 0.040 ms over corners vs 0.102 grouped
+    assert g(201294, 4096, 256, 1) == 0     # 49 corners per y at K = 256: 0.19 vs 0.27 ms
+    assert g(201294, 4096, 1024, 1) == 1    # K = 1024: 2.50 vs 0.95 ms
+    assert g(50152, 16384, 1024, 1) == 1    # 0.90 vs 0.57 ms
+    assert g(377722, 65536, 512, 1) == 1    # 1.65 vs 0.85 ms
+    assert g(945450, 65536, 1024, 1) == 1   # the large clip: 14.9 vs 2.75 ms
+    assert g(31700, 2048, 128, 1) == 0      # the adjoint workload's clip, K = 128
+    assert g(945450, 65536, 1024, 0) == 0   # plain FP32 never groups
+    assert g(100, 1000, 8, 1) == -1
+    try:
+        lib.fcfs_debug_set_hybrid(0)
+        assert g(945450, 65536, 1024, 1) == 0
+        lib.fcfs_debug_set_hybrid(2)
+        assert g(12576, 4096, 256, 1) == 1
+    finally:
+        lib.fcfs_debug_set_hybrid(1)

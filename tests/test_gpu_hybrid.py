@@ -1,9 +1,9 @@
 """Row-binned contraction (corners grouped by y, the off-axis block contracted
 over the T + 1 values of y) against the FP64 oracle and the direct contraction.
 
-It is taken automatically for single-clip split-FP16 calls on CTA pairs with
-V >= 8 (T + 1) and K >= 256 (the large-clip workload); here it is also forced
-on smaller clips.  Bounds as for the split-FP16 path: max|dF|/area <= 1e-5, the
+It is taken automatically for single-clip split-FP16 calls on CTA pairs when
+a cost estimate of the two contractions favours it (the large-clip workload
+among others); here it is also forced on smaller clips.  Bounds as for the split-FP16 path: max|dF|/area <= 1e-5, the
 area and F(0,0) exact.
 """
 import numpy as np
