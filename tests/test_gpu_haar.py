@@ -73,7 +73,7 @@ def test_haar_wide_cells(fc):
         W = gpu_haar(fc, clip, J).cpu().numpy()
         assert np.array_equal(W, haar.pcht(clip.x, clip.y, clip.poly_offsets, 8192, J)), J
     clip = make_clip(65536, 300, 67, smin=20, smax=2000)
-    for J in (5, 6):     # w = 2048, 1024
+    for J in (0, 1, 5, 6):   # w = 65536 (splat weights up to 2^32), 32768, 2048, 1024
         W = gpu_haar(fc, clip, J).cpu().numpy()
         assert np.array_equal(W, haar.pcht(clip.x, clip.y, clip.poly_offsets, 65536, J)), J
 
