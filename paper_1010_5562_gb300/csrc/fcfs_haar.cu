@@ -161,31 +161,66 @@ __device__ __forceinline__ long long wadd(long long a, long long b) { return a +
 
 // Inclusive prefix sum along every row of Z (G x G), in place.  One CTA per
 // row; warp w owns the segment [w seg, (w+1) seg): it sums the segment, the
-// CTA combines the eight totals, and each warp rescans its segment in chunks
-// of 32 (one element per lane) from its offset.
+// CTA combines the eight totals, and each warp rescans its segment from its
+// offset.  When a segment is a whole number of warp-wide vector chunks (G a
+// multiple of 8 * 32 * 16 B), lanes move 16 bytes at a time: each scans its
+// vector locally, the warp scans the lane totals, and the vector is stored
+// back; otherwise one element per lane and chunk.
 template <typename E>
 __global__ void __launch_bounds__(kHThreads) haar_row_scan_kernel(E* Z, int G) {
   using U = typename std::conditional<sizeof(E) == 4, unsigned, unsigned long long>::type;
-  __shared__ U tot[kHThreads / 32];
+  constexpr int kVec = 16 / sizeof(U);
+  struct alignas(16) Vec {
+    U v[kVec];
+  };
+  constexpr int kWarps = kHThreads / 32;
+  __shared__ U tot[kWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   U* row = reinterpret_cast<U*>(Z) + (size_t)blockIdx.x * G;
-  const int seg = (G + kHThreads / 32 - 1) / (kHThreads / 32);
+  const bool vec = G % (kWarps * 32 * kVec) == 0;   // warp-uniform (and CTA-uniform)
+  const int seg = (G + kWarps - 1) / kWarps;
   const int b = warp * seg, e = min(G, b + seg);
   U sum = 0;
+  if (vec) {
+    const Vec* rv = reinterpret_cast<const Vec*>(row);
+#pragma unroll 4
+    for (int i = b / kVec + lane; i < e / kVec; i += 32) {
+      const Vec x = rv[i];
+#pragma unroll
+      for (int k = 0; k < kVec; ++k) sum += x.v[k];
+    }
+  } else {
 #pragma unroll 8
-  for (int i = b + lane; i < e; i += 32) sum += row[i];
+    for (int i = b + lane; i < e; i += 32) sum += row[i];
+  }
   sum = warp_sum(sum);
   if (lane == 0) tot[warp] = sum;
   __syncthreads();
   U off = 0;
   for (int w2 = 0; w2 < warp; ++w2) off += tot[w2];
+  if (vec) {
+    Vec* rv = reinterpret_cast<Vec*>(row);
+#pragma unroll 2
+    for (int i0 = b / kVec; i0 < e / kVec; i0 += 32) {   // warp-uniform; e - b a multiple of 32 kVec
+      Vec x = rv[i0 + lane];
+#pragma unroll
+      for (int k = 1; k < kVec; ++k) x.v[k] += x.v[k - 1];
+      const U incl = warp_incl_scan(x.v[kVec - 1], lane);
+      const U before = off + (incl - x.v[kVec - 1]);
+#pragma unroll
+      for (int k = 0; k < kVec; ++k) x.v[k] += before;
+      rv[i0 + lane] = x;
+      off += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  } else {
 #pragma unroll 4
-  for (int i0 = b; i0 < e; i0 += 32) {   // warp-uniform
-    const int i = i0 + lane;
-    U v = i < e ? row[i] : 0;
-    v = warp_incl_scan(v, lane);
-    if (i < e) row[i] = v + off;
-    off += __shfl_sync(0xffffffffu, v, 31);
+    for (int i0 = b; i0 < e; i0 += 32) {   // warp-uniform
+      const int i = i0 + lane;
+      U v = i < e ? row[i] : 0;
+      v = warp_incl_scan(v, lane);
+      if (i < e) row[i] = v + off;
+      off += __shfl_sync(0xffffffffu, v, 31);
+    }
   }
 }
 
@@ -348,11 +383,16 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(E) == 4 ? 3 : 2) haar
   E carry = 0;
   if (col_ok)
     for (int s2 = 0; s2 < sg; ++s2) carry = wadd(carry, colsum[(size_t)s2 * G + tj * t + lane]);
-  for (int ti = ti0; ti < ti1; ++ti) {
-    E v[kHT];
+  // the tile's column values: loaded one tile ahead, so that the loads of tile
+  // ti + 1 are in flight while tile ti is reduced
+  E v[kHT];
+  auto fetch = [&](int ti) {
     const E* src = Z + (size_t)ti * t * G + (size_t)tj * t + lane;
 #pragma unroll
     for (int r = 0; r < kHT; ++r) v[r] = (col_ok && r < t) ? src[(size_t)r * G] : (E)0;
+  };
+  if (ti0 < ti1) fetch(ti0);
+  for (int ti = ti0; ti < ti1; ++ti) {
     __syncwarp();   // lane 0's read of the previous tile's a[0][0] is done
 #pragma unroll
     for (int r = 0; r < kHT; ++r) {
@@ -360,6 +400,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(E) == 4 ? 3 : 2) haar
       if (col_ok && r < t) a[r][lane] = carry;
     }
     __syncwarp();
+    if (ti + 1 < ti1) fetch(ti + 1);
     warp_pyramid(a, t, ti, tj, J, logN, W, G, lane);
     if (lane == 0) {
       const long long area = (long long)a[0][0];
