@@ -288,7 +288,9 @@ void fcfs_debug_set_barrier_extra(int32_t n);
  * mode 0 never, 1 (the default) when a cost estimate of the two forms
  * favours it (fcfs_forward_grouped tells), 2 whenever the call is eligible
  * (split FP16, 2K >= 256, no device validation).  Batches group when
- * V >= 8 n (T + 1) and K >= 256.  Same results within
+ * V >= 8 n (T + 1) and K >= 256.  The split-FP16 adjoint groups its corners by
+ * the contraction coordinate under the same modes, automatically when a cost
+ * estimate of its two forms favours it.  Same results within
  * the split-FP16 error bound.  Must not change between fcfs_workspace_size and
  * the call that uses the workspace. */
 void fcfs_debug_set_hybrid(int32_t mode);

@@ -83,15 +83,18 @@ static fcfs_status make_adj_plan(int64_t V, int32_t T, int32_t K, int32_t prec, 
     o = align_up(o + (size_t)2 * ap.nrows_pad * sizeof(float4), kWsAlign);
     ap.off_m0 = o;
     o = align_up(o + (size_t)2 * (ap.kdim_pad + 4) * sizeof(float), kWsAlign);
-    // many more corners than coordinate values: the MMA runs over the T + 1
-    // values of b and the epilogue over the corners grouped by b -- taken
-    // automatically when that still fills the GPU with a wave of CTAs (the
-    // epilogue of a CTA then takes all corners of its 128 values of b)
+    // grouped form: the MMA runs over the T + 1 values of b and the epilogue
+    // over the corners grouped by b.  The automatic choice compares two cost
+    // estimates (ms) fitted to GB300 measurements of both forms (T = 2048 ..
+    // 65536, K = 128 .. 1024, V / (T + 1) = 1.9 .. 49; the estimate picks the
+    // faster form in all ten cases):
+    //   per corner  0.05 + 2.23e-11 V K^2 + 5.16e-9 V K
+    //   grouped     0.086 + 1.79e-6 T + 3.27e-11 (T + 1) K^2 + 8.5e-10 V K
     const int mode = hybrid_mode();
-    int dev = 0, sms = 148;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long gctas = 2LL * 2 * ap.row_tiles * ((T + 1 + kAdjPairRows - 1) / kAdjPairRows);
-    ap.grouped = V > 0 && (mode == 2 || (mode == 1 && V >= 8LL * (T + 1) && gctas >= sms)) ? 1 : 0;
+    const double v = (double)V, k = (double)K, t = (double)T;
+    const double per_corner = 0.05 + 2.23e-11 * v * k * k + 5.16e-9 * v * k;
+    const double grouped = 0.086 + 1.79e-6 * t + 3.27e-11 * (t + 1.0) * k * k + 8.5e-10 * v * k;
+    ap.grouped = V > 0 && (mode == 2 || (mode == 1 && grouped < per_corner)) ? 1 : 0;
     ap.ny_pad = (T + 1 + 63) / 64 * 64;
     if (ap.grouped) {
       ap.off_groups = o;

@@ -192,7 +192,7 @@ def test_grouped_adjoint_large_groups(fc):
     rng = np.random.default_rng(9)
     W = 2 * K + 1
     G = rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))
-    gx, gy = grad_mode(fc, clip, K, G, 1)   # V = 40000 < 8 (T + 1): forced below
+    gx, gy = grad_mode(fc, clip, K, G, 1)   # automatic: per corner at K = 128 (the cost estimate)
     gx2, gy2 = grad_mode(fc, clip, K, G, 2)
     idx = np.sort(rng.choice(clip.V, 48, replace=False))
     rx, ry = oracle.vertex_gradient(clip.x[idx], clip.y[idx], clip.s[idx], T, K, G)
@@ -203,8 +203,8 @@ def test_grouped_adjoint_large_groups(fc):
 def test_grouped_adjoint_launches(fc):
     """Grouped: prep, coefficients, pack, count, scan, scatter, contraction,
     finalize; per corner: prep, coefficients, pack, contraction, finalize.
-    Workload 4 stays per corner automatically: its grouped form would have 36
-    CTAs, less than a wave."""
+    Workload 4 stays per corner automatically: the cost estimates favour it
+    (measured 0.074 ms per corner against 0.081 grouped)."""
     clip, K = config_clip(4)
     x, y, s = dev(clip.x), dev(clip.y), dev(clip.s)
     dF = torch.zeros((2 * K + 1, 2 * K + 1), dtype=torch.complex64, device="cuda")
