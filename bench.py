@@ -262,6 +262,21 @@ def traffic_per_launch():
     return None
 
 
+def whole_job_rate(local_ms, units_per_step, steps, world, device="cpu"):
+    """Throughput of `world` replicas that each process `units_per_step` units
+    in each of `steps` steps: the slowest rank bounds the job, so the time is
+    the maximum over ranks (one all-reduce when world > 1) and the rate is
+    world * units_per_step * steps / that time.  Returns (rate per second, ms)."""
+    t = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return world * units_per_step * steps / (t * 1e-3), t
+
+
 def run_ours(args):
     import torch
 
@@ -344,12 +359,7 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
     if clocks is not None:
         clocks["window"] = "nvidia-smi every 100 ms, the step running 0.3 s before and after the timed steps"
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n_terms * args.steps / (total_ms * 1e-3)
+    value, total_ms = whole_job_rate(sum(ms), n_terms, args.steps, world, dev)
 
     # ---- per-kernel roofline of the contraction (events around the kernel) ----
     reps = min(args.steps, 500)
