@@ -1,4 +1,5 @@
-"""Writes tests/golden/*.json from the FP64 oracle only.
+"""Writes tests/golden/*.json from the oracles only (Fourier block, cosine
+series, Haar transform).
 
 The paper prints no numeric worked example for the Fourier series (its only
 worked figure, the pruned Haar flow of u(t-3) on [0, 8), carries no values), so
@@ -47,6 +48,18 @@ def main():
                "used in the Haar flow figure (Fig. sigflow), T=8, K=2",
         area=oracle.area_exact(r.x, r.y, r.s, 8),
         entries=sample(F, 2, [(0, 0), (1, 0), (2, 0), (1, 1), (0, 1)]))
+    clip, K = config_clip(1)
+    C = oracle.cosine_block(clip.x, clip.y, clip.s, clip.T, K)
+    out["cosine_config1"] = dict(
+        source="oracle.cosine_block on synth.config_clip(1): T=256, 16 rectangles, V=64, K=32",
+        area=oracle.area_exact(clip.x, clip.y, clip.s, clip.T),
+        entries=[[int(k), int(l), float(C[k, l])] for k, l in
+                 [(0, 0), (1, 0), (0, 1), (1, 1), (2, 5), (7, 3), (K, K), (K, 0), (13, 29)]])
+    W = oracle.pcht(L.x, L.y, L.poly_offsets, 16, 4)
+    out["haar_L_shape"] = dict(
+        source="oracle.pcht on the L-shaped ring (2,11)(9,11)(9,3)(6,3)(6,7)(2,7), N=16, J=4 "
+               "(the full 16 x 16 coefficient square, row-major)",
+        area=oracle.area_exact(L.x, L.y, L.s, 16), square=[float(v) for v in W.reshape(-1)])
     with open(os.path.join(HERE, "oracle_samples.json"), "w") as fh:
         json.dump(out, fh, indent=1)
 

@@ -36,3 +36,20 @@ def test_golden_step():
     g = {(k, l): complex(re, im) for k, l, re, im in GOLD["step_u_t_minus_3"]["entries"]}
     assert abs(g[(0, 1)]) < 1e-12 and abs(g[(1, 1)]) < 1e-12
     assert abs(g[(0, 0)] - 40) < 1e-12
+
+
+def test_golden_cosine():
+    g = GOLD["cosine_config1"]
+    clip, K = config_clip(1)
+    C = oracle.cosine_block(clip.x, clip.y, clip.s, clip.T, K)
+    assert C[0, 0] == g["area"]
+    for k, l, v in g["entries"]:
+        assert abs(C[k, l] - v) <= 1e-12 * g["area"]
+
+
+def test_golden_haar():
+    g = GOLD["haar_L_shape"]
+    L = clip_from_rings(16, [([2, 9, 9, 6, 6, 2], [11, 11, 3, 3, 7, 7])])
+    W = oracle.pcht(L.x, L.y, L.poly_offsets, 16, 4)
+    assert np.array_equal(W.reshape(-1), np.array(g["square"]))   # exact dyadic values
+    assert W[0, 0] * 16 == g["area"]

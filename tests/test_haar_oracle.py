@@ -146,3 +146,24 @@ def test_mutant_is_caught(name, monkeypatch):
     monkeypatch.setattr(haar, attr, fn)
     errs = _run_pins()
     assert max(errs.values()) > 1e-3, (name, errs)
+
+
+def test_step_of_the_flow_figure():
+    """Fig. sigflow prunes the 1-D Haar flow of f(t) = u(t - 3) on [0, 8) to the
+    supports that straddle t = 3: [0, 8), [0, 4) and [2, 4).  On the tile its
+    2-D extension [3, 8) x [0, 8) (N = 8, J = 3) is constant along y, so only
+    the x-details (hg) of those supports are nonzero, at every ky.  From the
+    definitions (areas of the children A_nm, n along x):
+      <f, phi_000> = 40 / 8 = 5;
+      j = 0: (2^0 / 8)((4 + 4) - (16 + 16)) = -3;
+      j = 1, kx = 0 (children of side 2): (2 / 8)((0 + 0) - (2 + 2)) = -1;
+      j = 2, kx = 1 (children of side 1): (4 / 8)((0 + 0) - (1 + 1)) = -1."""
+    from synth import clip_from_rings, rect_ring
+    c = clip_from_rings(8, [rect_ring(3, 0, 8, 8)])
+    W = haar.pcht(c.x, c.y, c.poly_offsets, 8, 3)
+    ref = np.zeros((8, 8))
+    ref[0, 0] = 5.0
+    ref[1, 0] = -3.0
+    ref[2, 0] = ref[2, 1] = -1.0
+    ref[4 + 1, 0:4] = -1.0
+    assert np.array_equal(W, ref)
