@@ -19,6 +19,7 @@
 // terms).  One call: prep (tables at period T2), the contraction (tensor cores
 // on CTA pairs, or the plain FP32 kernel), the axis DFT, and the reduction below.
 #include "fcfs_epilogue.cuh"
+#include "fcfs_launch.cuh"
 
 namespace fcfs {
 
@@ -34,6 +35,7 @@ fcfs_status check_ws(const Plan& pl, void* ws, size_t ws_bytes);
 //          TwoSum with the rounding errors carried in a second float.
 __global__ void cosine_reduce_kernel(Plan pl, uint8_t* ws, float* __restrict__ C,
                                      long long* __restrict__ area_out) {
+  griddep_wait();   // launched behind the axis DFT (programmatic dependent launch)
   const int K = pl.K;
   const long long n1 = (long long)K + 1;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,10 +78,8 @@ __global__ void cosine_reduce_kernel(Plan pl, uint8_t* ws, float* __restrict__ C
 static cudaError_t launch_cosine_reduce(const Plan& pl, void* ws, float* C, int64_t* area, cudaStream_t st) {
   const long long n = (long long)(pl.K + 1) * (pl.K + 1);
   ensure_smem(reinterpret_cast<const void*>(cosine_reduce_kernel), 0);
-  cosine_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pl, static_cast<uint8_t*>(ws), C,
-                                                                     reinterpret_cast<long long*>(area));
-  count_launch(1);
-  return cudaGetLastError();
+  return launch_after(cosine_reduce_kernel, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, pl,
+                      static_cast<uint8_t*>(ws), C, reinterpret_cast<long long*>(area));
 }
 
 }  // namespace fcfs

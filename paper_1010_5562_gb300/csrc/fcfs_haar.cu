@@ -41,7 +41,7 @@
 // The coarse area grids are int64 throughout.
 #include <type_traits>
 
-#include "fcfs_common.cuh"
+#include "fcfs_launch.cuh"
 
 namespace fcfs {
 
@@ -168,6 +168,7 @@ __device__ __forceinline__ long long wadd(long long a, long long b) { return a +
 // back; otherwise one element per lane and chunk.
 template <typename E>
 __global__ void __launch_bounds__(kHThreads) haar_row_scan_kernel(E* Z, int G) {
+  griddep_wait();   // launched behind the splat (programmatic dependent launch)
   using U = typename std::conditional<sizeof(E) == 4, unsigned, unsigned long long>::type;
   constexpr int kVec = 16 / sizeof(U);
   struct alignas(16) Vec {
@@ -229,6 +230,7 @@ __global__ void __launch_bounds__(kHThreads) haar_row_scan_kernel(E* Z, int G) {
 template <typename E>
 __global__ void __launch_bounds__(kHThreads) haar_colsum_kernel(const E* __restrict__ Z, int G, int rows_per_seg,
                                                                 E* colsum) {
+  griddep_wait();   // launched behind the row scan
   using U = typename std::conditional<sizeof(E) == 4, unsigned, unsigned long long>::type;
   __shared__ U part[kHThreads / 32][kHT];
   const int t = G < kHT ? G : kHT;
@@ -370,6 +372,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(E) == 4 ? 3 : 2) haar
                                                                      const E* __restrict__ colsum, int strips,
                                                                      int segs, int tiles_per_seg, long long* coarse,
                                                                      double* W) {
+  griddep_wait();   // launched behind the column sums
   extern __shared__ __align__(16) unsigned char hsm_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * kStripWarps + warp;
@@ -415,6 +418,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(E) == 4 ? 3 : 2) haar
 // the last pass (a single tile) writes W[0][0] = area / N.
 __global__ void __launch_bounds__(kHThreads) haar_coarse_kernel(const long long* __restrict__ A, int G, int L,
                                                                 int logN, long long* coarse, double* W, int WG) {
+  griddep_wait();   // launched behind the previous pyramid pass
   __shared__ long long a[kHT][kHT + 1];
   const int t = G < kHT ? G : kHT;
   const int tiles = G / t;
@@ -449,23 +453,25 @@ cudaError_t launch_haar_t(const HaarPlan& hp, const int32_t* x, const int32_t* y
     haar_splat_kernel<E><<<blocks, 256, 0, st>>>(x, y, s, hp.V, hp.N, hp.J, hp.logN - hp.J, Z);
     count_launch(1);
   }
-  haar_row_scan_kernel<E><<<G, kHThreads, 0, st>>>(Z, G);
-  count_launch(1);
+  if ((e = launch_after(haar_row_scan_kernel<E>, dim3(G), dim3(kHThreads), 0, st, Z, G)) != cudaSuccess) return e;
   E* colsum = reinterpret_cast<E*>(ws + hp.off_colsum);
-  haar_colsum_kernel<E><<<dim3(hp.strips, hp.segs), kHThreads, 0, st>>>(Z, G, hp.tiles_per_seg * t, colsum);
-  count_launch(1);
+  if ((e = launch_after(haar_colsum_kernel<E>, dim3(hp.strips, hp.segs), dim3(kHThreads), 0, st, Z, G,
+                        hp.tiles_per_seg * t, colsum)) != cudaSuccess)
+    return e;
   long long* coarse = reinterpret_cast<long long*>(ws + hp.off_coarse[0]);
   const int warps = hp.strips * hp.segs;
   ensure_smem(reinterpret_cast<const void*>(haar_strip_kernel<E>), strip_smem_bytes<E>());
-  haar_strip_kernel<E><<<(warps + kStripWarps - 1) / kStripWarps, kStripWarps * 32, strip_smem_bytes<E>(), st>>>(
-      Z, G, hp.J, hp.logN, colsum, hp.strips, hp.segs, hp.tiles_per_seg, coarse, W);
-  count_launch(1);
+  if ((e = launch_after(haar_strip_kernel<E>, dim3((warps + kStripWarps - 1) / kStripWarps), dim3(kStripWarps * 32),
+                        strip_smem_bytes<E>(), st, (const E*)Z, G, hp.J, hp.logN, (const E*)colsum, hp.strips,
+                        hp.segs, hp.tiles_per_seg, coarse, W)) != cudaSuccess)
+    return e;
   int L = hp.J - ilog2(t);
   for (int p = 1; p < hp.npass; ++p) {
     const int g = hp.coarse_side[p - 1], tt = g < kHT ? g : kHT;
     long long* next = reinterpret_cast<long long*>(ws + hp.off_coarse[p]);
-    haar_coarse_kernel<<<(g / tt) * (g / tt), kHThreads, 0, st>>>(coarse, g, L, hp.logN, next, W, G);
-    count_launch(1);
+    if ((e = launch_after(haar_coarse_kernel, dim3((g / tt) * (g / tt)), dim3(kHThreads), 0, st,
+                          (const long long*)coarse, g, L, hp.logN, next, W, G)) != cudaSuccess)
+      return e;
     coarse = next;
     L -= ilog2(tt);
   }

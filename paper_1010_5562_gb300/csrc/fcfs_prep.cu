@@ -5,6 +5,7 @@
 #include <math_constants.h>
 
 #include "fcfs_epilogue.cuh"
+#include "fcfs_launch.cuh"
 
 namespace fcfs {
 
@@ -91,6 +92,7 @@ constexpr int kAxisThreads = 256;
 template <bool BATCH>
 __global__ void bin_kernel(Plan pl, const int32_t* __restrict__ x, const int32_t* __restrict__ y,
                            const int8_t* __restrict__ s, uint8_t* ws, int validate) {
+  griddep_wait();   // launched behind the previous kernel (programmatic dependent launch)
   const int T = pl.T;
   long long* bins = reinterpret_cast<long long*>(ws + pl.off_bins);
   Status* st = reinterpret_cast<Status*>(ws + pl.off_status);
@@ -136,6 +138,7 @@ size_t axis_smem_bytes(int T, int full) {
 constexpr int kAxisGroupsMax = 4;
 template <bool BATCH>
 __global__ void __launch_bounds__(kAxisThreads * kAxisGroupsMax) axis_dft_kernel(Plan pl, uint8_t* ws, int nper) {
+  griddep_wait();   // launched behind the previous kernel (programmatic dependent launch)
   extern __shared__ __align__(128) uint8_t sm[];
   int* lv = reinterpret_cast<int*>(sm);
   const int T = pl.T, logT = pl.logT, logQ = logT - 2;
@@ -235,6 +238,7 @@ __global__ void __launch_bounds__(kAxisThreads * kAxisGroupsMax) axis_dft_kernel
 // ---------------------------------------------------------------------------
 __global__ void reduce_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, long long* __restrict__ area_out,
                               int validate) {
+  griddep_wait();   // launched behind the previous kernel (programmatic dependent launch)
   const int K = pl.K;
   const long long n1 = (long long)K + 1;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -306,12 +310,9 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (pl.V > 0 && !pl.bin_in_gemm) {
     const int blocks = (int)std::min<long long>((pl.V + 255) / 256, 8LL * sms);
-    if (pl.batch)
-      bin_kernel<true><<<blocks, 256, 0, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws), validate ? 1 : 0);
-    else
-      bin_kernel<false><<<blocks, 256, 0, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws), validate ? 1 : 0);
-    count_launch(1);
-    if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
+    const cudaError_t e = launch_after(pl.batch ? bin_kernel<true> : bin_kernel<false>, dim3(blocks), dim3(256), 0,
+                                       st, pl, x, y, s, static_cast<uint8_t*>(ws), validate ? 1 : 0);
+    if (e != cudaSuccess) return e;
   }
   const int kblocks = (pl.K + kAxisThreads - 1) / kAxisThreads;
   const int clips = pl.batch ? pl.n_clips : 1;
@@ -327,19 +328,16 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
                       (groups > 1 ? (size_t)groups * 5 * kAxisThreads * sizeof(long long) : 0);
   auto kern = pl.batch ? axis_dft_kernel<true> : axis_dft_kernel<false>;
   ensure_smem(reinterpret_cast<const void*>(kern), smem);
-  kern<<<dim3(kblocks, nblocks, clips), threads, smem, st>>>(pl, static_cast<uint8_t*>(ws), nper);
-  count_launch(1);
-  return cudaGetLastError();
+  return launch_after(kern, dim3(kblocks, nblocks, clips), dim3(threads), smem, st, pl, static_cast<uint8_t*>(ws),
+                      nper);
 }
 
 cudaError_t launch_reduce(const Plan& pl, void* ws, float* F, int64_t* area, bool validate, cudaStream_t st) {
   const long long n = (long long)(pl.K + 1) * (pl.K + 1);
   const dim3 blocks((unsigned)((n + 255) / 256), pl.batch ? pl.n_clips : 1);
   ensure_smem(reinterpret_cast<const void*>(reduce_kernel), 0);
-  reduce_kernel<<<blocks, 256, 0, st>>>(pl, static_cast<uint8_t*>(ws), reinterpret_cast<float2*>(F),
-                                        reinterpret_cast<long long*>(area), validate ? 1 : 0);
-  count_launch(1);
-  return cudaGetLastError();
+  return launch_after(reduce_kernel, blocks, dim3(256), 0, st, pl, static_cast<uint8_t*>(ws),
+                      reinterpret_cast<float2*>(F), reinterpret_cast<long long*>(area), validate ? 1 : 0);
 }
 
 }  // namespace fcfs

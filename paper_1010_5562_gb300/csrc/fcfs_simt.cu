@@ -13,7 +13,7 @@
 // into shared memory from the FP32 table (exact integer phase), never stored
 // to global memory.  Each 256-thread block owns a 128 x 128 tile of P and one
 // vertex split; each thread accumulates an 8 x 8 register tile in FP32.
-#include "fcfs_common.cuh"
+#include "fcfs_launch.cuh"
 
 namespace fcfs {
 
@@ -25,6 +25,7 @@ template <bool FULL, bool COS = false>
 __global__ void __launch_bounds__(kSThreads, 2) gemm_simt_kernel(Plan pl, const int32_t* __restrict__ x,
                                                                 const int32_t* __restrict__ y,
                                                                 const int8_t* __restrict__ s, uint8_t* ws) {
+  griddep_wait();   // launched behind the prep kernel (programmatic dependent launch)
   extern __shared__ __align__(128) uint8_t sm[];
   const size_t tb = tab_f32_bytes(pl.T, FULL);
   float* tab = reinterpret_cast<float*>(sm);
@@ -142,19 +143,10 @@ cudaError_t launch_gemm_simt(const Plan& pl, const int32_t* x, const int32_t* y,
   if (pl.splits == 0) return cudaSuccess;
   const size_t smem = tab_f32_bytes(pl.T, pl.full) + 2 * kSChunk * kSB * sizeof(float) + 3 * kSChunk * 4;
   dim3 grid = pl.batch ? dim3(pl.splits, 1) : dim3(pl.tiles_m * pl.tiles_n, pl.splits);
-  if (pl.cosine) {
-    auto kern = pl.full ? gemm_simt_kernel<true, true> : gemm_simt_kernel<false, true>;
-    ensure_smem(reinterpret_cast<const void*>(kern), smem);
-    kern<<<grid, kSThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws));
-  } else if (pl.full) {
-    ensure_smem(reinterpret_cast<const void*>(gemm_simt_kernel<true>), smem);
-    gemm_simt_kernel<true><<<grid, kSThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws));
-  } else {
-    ensure_smem(reinterpret_cast<const void*>(gemm_simt_kernel<false>), smem);
-    gemm_simt_kernel<false><<<grid, kSThreads, smem, st>>>(pl, x, y, s, static_cast<uint8_t*>(ws));
-  }
-  count_launch(1);
-  return cudaGetLastError();
+  auto kern = pl.cosine ? (pl.full ? gemm_simt_kernel<true, true> : gemm_simt_kernel<false, true>)
+                        : (pl.full ? gemm_simt_kernel<true> : gemm_simt_kernel<false>);
+  ensure_smem(reinterpret_cast<const void*>(kern), smem);
+  return launch_after(kern, grid, dim3(kSThreads), smem, st, pl, x, y, s, static_cast<uint8_t*>(ws));
 }
 
 }  // namespace fcfs
