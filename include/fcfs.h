@@ -24,6 +24,11 @@
  * (Eqs. Fk0, F0l), and F(k,l), k,l != 0, is -T^2/(4 pi^2 k l) times the 2-D DFT
  * of the sparse +-1 corner image at (k mod T, l mod T) (Eq. Fkl, Step 4).
  *
+ * The same corner set also gives two other transforms of the clip: the
+ * continuous cosine series (fcfs_cosine, the extension named in the
+ * concluding section) and the continuous Haar transform that the PCHT of
+ * Sec. III-B computes (fcfs_haar).
+ *
  * Common conventions.
  *  - Every array pointer is a DEVICE pointer owned by the caller.  The library
  *    allocates nothing on the device; scratch memory is the caller's workspace.
