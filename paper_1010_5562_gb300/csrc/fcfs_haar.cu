@@ -25,8 +25,10 @@
 //  * Row scans, then column scans, give the exact int64 areas A_J.
 //  * A pyramid of 2 x 2 sums gives the coarser areas and the three signed sums
 //    per parent; each is an integer times 2^(j - log2 N), exact in FP64.
-// Kernels: Z zeroed (memset), splat, row scan (one CTA per row), column sums
-// per (strip of 32 columns, row segment), column scan fused with the pyramid
+// Kernels: the corners grouped by x (count, scan, scatter), each row of Z built
+// from its corners and scanned in shared memory (one CTA per row, one write of
+// the row), column sums per (strip of 32 columns, row segment), column scan
+// fused with the pyramid
 // of each 32 x 32 tile (five levels; one warp per strip segment), then pyramid
 // passes on the coarse area grids until one cell is left.  Everything is exact
 // integer arithmetic; the FP64 coefficients are assembled from their bits.
@@ -41,6 +43,7 @@
 // The coarse area grids are int64 throughout.
 #include <type_traits>
 
+#include "fcfs_group.cuh"
 #include "fcfs_launch.cuh"
 
 namespace fcfs {
@@ -58,7 +61,8 @@ struct HaarPlan {
   int narrow;                    // 1: Z in int32 (cell side <= kNarrowMaxW)
   int strips, segs, tiles_per_seg;
   int npass;                     // pyramid passes, the fused one first; pass p leaves a grid of coarse_side[p]
-  size_t off_z, off_colsum, off_coarse[6], total;
+  int ny_pad;                    // T + 1 rounded up to 64 (the grouping's exponent array)
+  size_t off_z, off_colsum, off_coarse[6], off_groups, total;
   int coarse_side[6];
 };
 
@@ -106,36 +110,11 @@ fcfs_status make_haar_plan(int64_t V, int32_t T, int32_t J, HaarPlan& hp) {
     if (side == 1) break;
     side = side / (side < kHT ? side : kHT);
   }
+  hp.ny_pad = (T + 1 + 63) / 64 * 64;
+  hp.off_groups = o;
+  o = align_up(o + group_bytes(V, T, hp.ny_pad), kWsAlign);
   hp.total = o;
   return FCFS_OK;
-}
-
-__device__ __forceinline__ void red_add(long long* p, long long v) {
-  atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
-}
-__device__ __forceinline__ void red_add(int* p, long long v) {
-  atomicAdd(reinterpret_cast<unsigned int*>(p), (unsigned int)v);   // modulo 2^32
-}
-
-// Four splat weights per corner; corners outside [0, N] are dropped.
-template <typename E>
-__global__ void haar_splat_kernel(const int32_t* __restrict__ x, const int32_t* __restrict__ y,
-                                  const int8_t* __restrict__ s, long long V, int N, int J, int lw, E* Z) {
-  const int G = 1 << J;
-  const long long w = 1LL << lw;   // cell side N / 2^J
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
-    const int xv = x[v], yv = y[v], sv = s[v];
-    if (xv < 0 || xv >= N || yv < 0 || yv >= N || (sv != 1 && sv != -1)) continue;   // x = N: empty quadrant
-    const int c = xv >> lw, d = yv >> lw;
-    const long long r = (long long)(c + 1) * w - xv, q = (long long)(d + 1) * w - yv;   // in (0, w]
-    E* row = Z + (size_t)c * G;
-    red_add(row + d, sv * r * q);
-    if (q < w && d + 1 < G) red_add(row + d + 1, sv * r * (w - q));
-    if (r < w && c + 1 < G) {
-      red_add(row + G + d, sv * (w - r) * q);
-      if (q < w && d + 1 < G) red_add(row + G + d + 1, sv * (w - r) * (w - q));
-    }
-  }
 }
 
 template <typename E>
@@ -159,69 +138,66 @@ __device__ __forceinline__ E warp_sum(E v) {
 __device__ __forceinline__ int wadd(int a, int b) { return (int)((unsigned)a + (unsigned)b); }
 __device__ __forceinline__ long long wadd(long long a, long long b) { return a + b; }
 
-// Inclusive prefix sum along every row of Z (G x G), in place.  One CTA per
-// row; warp w owns the segment [w seg, (w+1) seg): it sums the segment, the
-// CTA combines the eight totals, and each warp rescans its segment from its
-// offset.  When a segment is a whole number of warp-wide vector chunks (G a
-// multiple of 8 * 32 * 16 B), lanes move 16 bytes at a time: each scans its
-// vector locally, the warp scans the lane totals, and the vector is stored
-// back; otherwise one element per lane and chunk.
+// Row i of Z, built and scanned along the row in shared memory, written once.
+// Along x the quadrant of a corner in cell row c = floor(x / w) covers row c
+// over r = (c + 1) w - x and every later row over w: after the column scan
+// that is the two-point splat r at c, w - r at c + 1.  So row i receives the
+// corners of rows i (weight r) and i - 1 (weight w - r), found through the
+// grouping of the corners by x, each splatted along y as q at d = floor(y / w)
+// and w - q at d + 1; the inclusive scan along the row follows.  Corners with
+// x or y outside [0, N) or a sign other than +-1 add nothing.  One CTA per
+// row; the scan is done by warps over chunks of 32 (conflict-free reads).
 template <typename E>
-__global__ void __launch_bounds__(kHThreads) haar_row_scan_kernel(E* Z, int G) {
-  griddep_wait();   // launched behind the splat (programmatic dependent launch)
+__global__ void __launch_bounds__(kHThreads) haar_row_build_kernel(const int32_t* __restrict__ x,
+                                                                   const int32_t* __restrict__ y,
+                                                                   const int8_t* __restrict__ s,
+                                                                   const int* __restrict__ start,
+                                                                   const int* __restrict__ perm, int N, int G,
+                                                                   int lw, E* Z) {
+  griddep_wait();   // launched behind the grouping (programmatic dependent launch)
   using U = typename std::conditional<sizeof(E) == 4, unsigned, unsigned long long>::type;
-  constexpr int kVec = 16 / sizeof(U);
-  struct alignas(16) Vec {
-    U v[kVec];
-  };
   constexpr int kWarps = kHThreads / 32;
+  extern __shared__ __align__(16) unsigned char hraw[];
+  U* row = reinterpret_cast<U*>(hraw);
   __shared__ U tot[kWarps];
+  const int i = blockIdx.x;
+  const long long w = 1LL << lw;
+  for (int j = threadIdx.x; j < G; j += blockDim.x) row[j] = 0;
+  __syncthreads();
+  const int xlo = (i > 0 ? i - 1 : 0) << lw;
+  const int xhi = min(N, (i + 1) << lw);   // corners with x in [xlo, xhi): rows i - 1 and i
+  const int b0 = start[xlo], e0 = start[xhi];
+  for (int j = b0 + (int)threadIdx.x; j < e0; j += blockDim.x) {
+    const int v = perm[j];
+    const int xv = __ldg(x + v), yv = __ldg(y + v), sv = __ldg(s + v);
+    if (yv < 0 || yv >= N || (sv != 1 && sv != -1)) continue;
+    const int c = xv >> lw;
+    const long long r = (long long)(c + 1) * w - xv;   // in (0, w]
+    const long long wx = c == i ? r : w - r;
+    if (wx == 0) continue;
+    const int d = yv >> lw;
+    const long long q = (long long)(d + 1) * w - yv;
+    atomicAdd(&row[d], (U)(sv * wx * q));
+    if (q < w && d + 1 < G) atomicAdd(&row[d + 1], (U)(sv * wx * (w - q)));
+  }
+  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  U* row = reinterpret_cast<U*>(Z) + (size_t)blockIdx.x * G;
-  const bool vec = G % (kWarps * 32 * kVec) == 0;   // warp-uniform (and CTA-uniform)
   const int seg = (G + kWarps - 1) / kWarps;
   const int b = warp * seg, e = min(G, b + seg);
   U sum = 0;
-  if (vec) {
-    const Vec* rv = reinterpret_cast<const Vec*>(row);
-#pragma unroll 4
-    for (int i = b / kVec + lane; i < e / kVec; i += 32) {
-      const Vec x = rv[i];
-#pragma unroll
-      for (int k = 0; k < kVec; ++k) sum += x.v[k];
-    }
-  } else {
-#pragma unroll 8
-    for (int i = b + lane; i < e; i += 32) sum += row[i];
-  }
+  for (int j = b + lane; j < e; j += 32) sum += row[j];
   sum = warp_sum(sum);
   if (lane == 0) tot[warp] = sum;
   __syncthreads();
   U off = 0;
   for (int w2 = 0; w2 < warp; ++w2) off += tot[w2];
-  if (vec) {
-    Vec* rv = reinterpret_cast<Vec*>(row);
-#pragma unroll 2
-    for (int i0 = b / kVec; i0 < e / kVec; i0 += 32) {   // warp-uniform; e - b a multiple of 32 kVec
-      Vec x = rv[i0 + lane];
-#pragma unroll
-      for (int k = 1; k < kVec; ++k) x.v[k] += x.v[k - 1];
-      const U incl = warp_incl_scan(x.v[kVec - 1], lane);
-      const U before = off + (incl - x.v[kVec - 1]);
-#pragma unroll
-      for (int k = 0; k < kVec; ++k) x.v[k] += before;
-      rv[i0 + lane] = x;
-      off += __shfl_sync(0xffffffffu, incl, 31);
-    }
-  } else {
-#pragma unroll 4
-    for (int i0 = b; i0 < e; i0 += 32) {   // warp-uniform
-      const int i = i0 + lane;
-      U v = i < e ? row[i] : 0;
-      v = warp_incl_scan(v, lane);
-      if (i < e) row[i] = v + off;
-      off += __shfl_sync(0xffffffffu, v, 31);
-    }
+  U* out = reinterpret_cast<U*>(Z) + (size_t)i * G;
+  for (int j0 = b; j0 < e; j0 += 32) {   // warp-uniform
+    const int j = j0 + lane;
+    U v = j < e ? row[j] : 0;
+    v = warp_incl_scan(v, lane);
+    if (j < e) out[j] = v + off;
+    off += __shfl_sync(0xffffffffu, v, 31);
   }
 }
 
@@ -230,7 +206,7 @@ __global__ void __launch_bounds__(kHThreads) haar_row_scan_kernel(E* Z, int G) {
 template <typename E>
 __global__ void __launch_bounds__(kHThreads) haar_colsum_kernel(const E* __restrict__ Z, int G, int rows_per_seg,
                                                                 E* colsum) {
-  griddep_wait();   // launched behind the row scan
+  griddep_wait();   // launched behind the row build
   using U = typename std::conditional<sizeof(E) == 4, unsigned, unsigned long long>::type;
   __shared__ U part[kHThreads / 32][kHT];
   const int t = G < kHT ? G : kHT;
@@ -441,19 +417,19 @@ __global__ void __launch_bounds__(kHThreads) haar_coarse_kernel(const long long*
 template <typename E>
 cudaError_t launch_haar_t(const HaarPlan& hp, const int32_t* x, const int32_t* y, const int8_t* s, uint8_t* ws,
                           double* W, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(ws, 0, hp.off_colsum, st);   // header and Z
+  cudaError_t e = cudaMemsetAsync(ws, 0, 256, st);   // the header (status word)
   if (e != cudaSuccess) return e;
   E* Z = reinterpret_cast<E*>(ws + hp.off_z);
   const int G = hp.G, t = G < kHT ? G : kHT;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (hp.V > 0) {
-    const int blocks = (int)std::min<long long>((hp.V + 255) / 256, 8LL * sms);
-    haar_splat_kernel<E><<<blocks, 256, 0, st>>>(x, y, s, hp.V, hp.N, hp.J, hp.logN - hp.J, Z);
-    count_launch(1);
-  }
-  if ((e = launch_after(haar_row_scan_kernel<E>, dim3(G), dim3(kHThreads), 0, st, Z, G)) != cudaSuccess) return e;
+  // the corners grouped by x (counting sort), then every row of Z built once
+  uint8_t* gb = ws + hp.off_groups;
+  if ((e = launch_grouping(x, nullptr, hp.V, hp.N, hp.ny_pad, gb, st)) != cudaSuccess) return e;
+  const Groups g = groups_at(gb, hp.N, hp.ny_pad);
+  const size_t row_smem = (size_t)G * sizeof(E);
+  ensure_smem(reinterpret_cast<const void*>(haar_row_build_kernel<E>), row_smem);
+  if ((e = launch_after(haar_row_build_kernel<E>, dim3(G), dim3(kHThreads), row_smem, st, x, y, s,
+                        (const int*)g.start, (const int*)g.perm, hp.N, G, hp.logN - hp.J, Z)) != cudaSuccess)
+    return e;
   E* colsum = reinterpret_cast<E*>(ws + hp.off_colsum);
   if ((e = launch_after(haar_colsum_kernel<E>, dim3(hp.strips, hp.segs), dim3(kHThreads), 0, st, Z, G,
                         hp.tiles_per_seg * t, colsum)) != cudaSuccess)

@@ -22,6 +22,7 @@
 
 #include "fcfs_epilogue.cuh"
 #include "fcfs_group.cuh"
+#include "fcfs_launch.cuh"
 
 namespace fcfs {
 
@@ -32,6 +33,7 @@ namespace {
 // ---------------------------------------------------------------------------
 __global__ void group_count_kernel(const int32_t* __restrict__ c0, const int32_t* __restrict__ c1, long long V,
                                    int T, int ny_pad, uint8_t* base) {
+  griddep_wait();   // may be launched behind the previous kernel (programmatic dependent launch)
   const int32_t* c = blockIdx.y ? c1 : c0;
   const Groups g = groups_at(base + blockIdx.y * group_bytes(V, T, ny_pad), T, ny_pad);
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
@@ -100,6 +102,7 @@ __device__ void scan_groups(const Groups& g, int T, int ny_pad, int first) {
 
 // One CTA per coordinate.
 __global__ void __launch_bounds__(kScanThreads) group_scan_kernel(long long V, int T, int ny_pad, uint8_t* base) {
+  griddep_wait();
   scan_groups(groups_at(base + blockIdx.x * group_bytes(V, T, ny_pad), T, ny_pad), T, ny_pad, 0);
 }
 
@@ -135,6 +138,7 @@ __global__ void batch_group_scatter_kernel(const int32_t* __restrict__ y, const 
 
 __global__ void group_scatter_kernel(const int32_t* __restrict__ c0, const int32_t* __restrict__ c1, long long V,
                                      int T, int ny_pad, uint8_t* base) {
+  griddep_wait();
   const int32_t* c = blockIdx.y ? c1 : c0;
   const Groups g = groups_at(base + blockIdx.y * group_bytes(V, T, ny_pad), T, ny_pad);
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
@@ -589,11 +593,15 @@ cudaError_t launch_grouping(const int32_t* c0, const int32_t* c1, int64_t V, int
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int vblocks = (int)std::max<long long>(1, std::min<long long>((V + 255) / 256, 8LL * sms));
-  group_count_kernel<<<dim3(vblocks, nc), 256, 0, st>>>(c0, c1, V, T, ny_pad, base);
-  group_scan_kernel<<<nc, kScanThreads, 0, st>>>(V, T, ny_pad, base);
-  group_scatter_kernel<<<dim3(vblocks, nc), 256, 0, st>>>(c0, c1, V, T, ny_pad, base);
-  count_launch(3);
-  return cudaGetLastError();
+  cudaError_t e;
+  if ((e = launch_after(group_count_kernel, dim3(vblocks, nc), dim3(256), 0, st, c0, c1, (long long)V, T, ny_pad,
+                        base)) != cudaSuccess)
+    return e;
+  if ((e = launch_after(group_scan_kernel, dim3(nc), dim3(kScanThreads), 0, st, (long long)V, T, ny_pad, base)) !=
+      cudaSuccess)
+    return e;
+  return launch_after(group_scatter_kernel, dim3(vblocks, nc), dim3(256), 0, st, c0, c1, (long long)V, T, ny_pad,
+                      base);
 }
 
 cudaError_t launch_hybrid(const Plan& pl, void* ws_, cudaStream_t st) {

@@ -108,7 +108,7 @@ def test_haar_deterministic_and_launches(fc):
     ws = fc.alloc_workspace(fc.haar_workspace_size(clip.V, clip.T, 10), x.device)
     n0 = fc.launch_count()
     W1 = fc.haar(x, y, s, clip.T, 10, workspace=ws).clone()
-    assert fc.launch_count() - n0 == 5   # splat, row scan, column sums, scan + pyramid, pyramid of the 32 x 32 grid
+    assert fc.launch_count() - n0 == 7   # grouping by x (3), row build, column sums, scan + pyramid, 32 x 32 grid
     W2 = fc.haar(x, y, s, clip.T, 10, workspace=ws)
     torch.cuda.synchronize()
     assert torch.equal(W1, W2)
