@@ -20,17 +20,17 @@
 //    i over w for i > c = floor(x_v / w), over r = (c + 1) w - x_v for i = c and
 //    not at all below: the inclusive prefix sum of the two-point splat r at c,
 //    w - r at c + 1.  So the cell areas are the 2-D inclusive prefix sum of
-//        Z = sum_v s_v (r e_c + (w - r) e_{c+1}) (q e_d + (w - q) e_{d+1})^T,
-//    four integer atomics per corner (points past the grid dropped).
-//  * Row scans, then column scans, give the exact int64 areas A_J.
+//        Z = sum_v s_v (r e_c + (w - r) e_{c+1}) (q e_d + (w - q) e_{d+1})^T
+//    (points past the grid dropped).
+//  * Row scans, then column scans, give the exact integer areas A_J.
 //  * A pyramid of 2 x 2 sums gives the coarser areas and the three signed sums
 //    per parent; each is an integer times 2^(j - log2 N), exact in FP64.
-// Kernels: the corners grouped by x (count, scan, scatter), each row of Z built
-// from its corners and scanned in shared memory (one CTA per row, one write of
-// the row), column sums per (strip of 32 columns, row segment), column scan
-// fused with the pyramid
-// of each 32 x 32 tile (five levels; one warp per strip segment), then pyramid
-// passes on the coarse area grids until one cell is left.  Everything is exact
+// Kernels: the corners grouped by x (count, scan, scatter); each row of Z built
+// in shared memory from the corners of its own and the previous cell row,
+// scanned there and written once (one CTA per row); column sums per (strip of
+// 32 columns, row segment); the column scan fused with the pyramid of each
+// 32 x 32 tile (five levels; one warp per strip segment); then pyramid passes
+// on the coarse area grids until one cell is left.  Everything is exact
 // integer arithmetic; the FP64 coefficients are assembled from their bits.
 //
 // Element type of Z.  No value held in Z after any of its passes is a running
@@ -38,8 +38,8 @@
 // areas, a fully scanned one a cell area, so |value| <= w^2, and a 32 x 32
 // tile's area is at most (32 w)^2.  For w <= 1024 all of them fit in int32 and
 // Z, its scans and the tile pyramid run in 32-bit integers (half the bytes and
-// the instructions); intermediate sums of the atomics and scans may wrap,
-// which two's-complement addition undoes exactly.  Larger cells use int64.
+// the instructions); intermediate sums of the row atomics and the scans may
+// wrap, which two's-complement addition undoes exactly.  Larger cells use int64.
 // The coarse area grids are int64 throughout.
 #include <type_traits>
 
