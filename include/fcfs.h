@@ -276,6 +276,10 @@ void fcfs_debug_set_fuse(int32_t on);
  * (fcfs_debug_set_hybrid(1), the default) compares cost estimates of the two
  * forms; fcfs_debug_set_hybrid(0) and (2) force them off and on. */
 int32_t fcfs_forward_grouped(int64_t V, int32_t T, int32_t K, int32_t prec);
+/* The same for fcfs_adjoint: 1 when its tensor-core contraction runs over the
+ * values of the grouped coordinate, 0 per corner (and always 0 for FP32), -1
+ * for unsupported sizes or precision. */
+int32_t fcfs_adjoint_grouped(int64_t V, int32_t T, int32_t K, int32_t prec);
 /* fcfs_debug_set_pair(0) keeps single-clip split-FP16 calls on one-CTA
  * 128 x 256 tiles; 1 (the default) runs clips with 2K >= 256 on CTA pairs
  * (2-SM MMA on 256 x 256 tiles).  Must not change between fcfs_workspace_size

@@ -36,6 +36,7 @@ SIGNATURES = {
     "fcfs_debug_set_barrier_extra": (None, [_i32]),
     "fcfs_debug_set_hybrid": (None, [_i32]),
     "fcfs_forward_grouped": (_i32, [_i64, _i32, _i32, _i32]),
+    "fcfs_adjoint_grouped": (_i32, [_i64, _i32, _i32, _i32]),
     "fcfs_profile_enable": (None, [_i32]),
     "fcfs_set_batch_unit_chunks": (None, [_i32]),
     "fcfs_profile_read": (_i32, [C.POINTER(C.c_float), _i32]),

@@ -462,6 +462,13 @@ size_t fcfs_adjoint_workspace_size(int64_t V, int32_t T, int32_t K, int32_t prec
   return ap.total;
 }
 
+int32_t fcfs_adjoint_grouped(int64_t V, int32_t T, int32_t K, int32_t prec) {
+  if (prec != FCFS_PREC_FP32 && prec != FCFS_PREC_SPLIT_F16) return -1;
+  AdjPlan ap;
+  if (make_adj_plan(V, T, K, prec, ap) != FCFS_OK) return -1;
+  return ap.grouped ? 1 : 0;
+}
+
 fcfs_status fcfs_adjoint(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, int32_t T, int32_t K,
                          int32_t prec, const float* dF, float* gx, float* gy, void* workspace, size_t ws_bytes,
                          void* stream) {

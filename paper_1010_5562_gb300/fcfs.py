@@ -168,6 +168,12 @@ def forward_grouped(V, T, K, prec="split_f16"):
     return int(_lib.load().fcfs_forward_grouped(int(V), int(T), int(K), _prec(prec)))
 
 
+def adjoint_grouped(V, T, K, prec="split_f16"):
+    """1 if adjoint() groups the corners for these sizes, 0 if it works per
+    corner, -1 if the sizes or the precision are unsupported."""
+    return int(_lib.load().fcfs_adjoint_grouped(int(V), int(T), int(K), _prec(prec)))
+
+
 def get_status(workspace, stream=None):
     """Synchronise and return the device status name of the last call on ``workspace``."""
     code = _lib.load().fcfs_get_status(_ptr(workspace), _stream(stream))

@@ -165,3 +165,41 @@ def test_automatic_contraction_choice(lib):
         assert g(12576, 4096, 256, 1) == 1
     finally:
         lib.fcfs_debug_set_hybrid(1)
+
+
+# Sizes of the sweeps the automatic choices were fitted to: (T, K, V, faster form),
+# measured on the GB300 (ms per call, split FP16); "tie" marks cases within 2%.
+FORWARD_SWEEP = [
+    (4096, 256, 3144, "direct"), (4096, 256, 12622, "direct"), (4096, 256, 50386, "direct"),
+    (4096, 256, 201294, "direct"), (65536, 1024, 125716, "grouped"), (65536, 1024, 945586, "grouped"),
+    (4096, 512, 12622, "direct"), (4096, 512, 50386, "tie"), (4096, 512, 201294, "grouped"),
+    (4096, 1024, 12622, "direct"), (4096, 1024, 50386, "grouped"), (4096, 1024, 201294, "grouped"),
+    (16384, 512, 50152, "grouped"), (16384, 512, 200908, "grouped"), (16384, 1024, 50152, "grouped"),
+    (16384, 1024, 200908, "grouped"), (65536, 512, 125716, "direct"), (65536, 512, 377722, "grouped"),
+    (65536, 512, 945586, "grouped"), (65536, 1024, 377722, "grouped"), (65536, 256, 945586, "grouped"),
+]
+ADJOINT_SWEEP = [
+    (2048, 128, 31700, "direct"), (4096, 256, 12622, "tie"), (4096, 256, 50386, "grouped"),
+    (4096, 256, 201294, "grouped"), (4096, 1024, 50386, "grouped"), (16384, 512, 200908, "grouped"),
+    (65536, 1024, 125716, "grouped"), (65536, 512, 377722, "grouped"), (65536, 256, 945586, "grouped"),
+    (65536, 1024, 945586, "grouped"),
+]
+
+
+def test_automatic_choices_against_the_sweeps(lib):
+    """The cost estimates pick the measured faster form: the forward in all but
+    two near-ties, the adjoint in all."""
+    lib.fcfs_debug_set_hybrid(1)
+    misses = []
+    for T, K, V, best in FORWARD_SWEEP:
+        got = "grouped" if lib.fcfs_forward_grouped(V, T, K, 1) == 1 else "direct"
+        if best != "tie" and got != best:
+            misses.append((T, K, V, got))
+    # the two near-ties: T = 4096, K = 1024, V = 12622 (0.265 ms direct against 0.289
+    # grouped) and T = 16384, K = 512, V = 50152 (0.271 direct against 0.251 grouped)
+    assert sorted(misses) == sorted([(4096, 1024, 12622, "grouped"), (16384, 512, 50152, "direct")]), misses
+    for T, K, V, best in ADJOINT_SWEEP:
+        got = "grouped" if lib.fcfs_adjoint_grouped(V, T, K, 1) == 1 else "direct"
+        assert best == "tie" or got == best, (T, K, V, got)
+    assert lib.fcfs_adjoint_grouped(945586, 65536, 1024, 0) == 0    # the FP32 adjoint never groups
+    assert lib.fcfs_adjoint_grouped(100, 1000, 8, 1) == -1
