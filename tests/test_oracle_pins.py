@@ -128,3 +128,19 @@ def test_edge_gradient_finite_differences_on_polygon():
         fd = (lp - lm) / (2 * h)
         worst = max(worst, abs(fd - gE[e]) / max(abs(gE).max(), 1e-300))
     assert worst < 1e-6
+
+
+def test_bessel_bound_and_parseval_convergence():
+    """The Fourier basis of the period is orthogonal with squared norm T^2, so
+    (1/T^2) sum over |k|,|l| <= K of |F(k,l)|^2 is the squared norm of the image's
+    projection: never above the integral of f^2 = the area (Bessel), increasing
+    in K and tending to the area (Parseval; the image is an indicator)."""
+    for c in pins.tiny_clips()[:2]:
+        A = oracle.area_exact(c.x, c.y, c.s, c.T)
+        sums = []
+        for K in (4, 16, 64, 256):
+            F = oracle.block(c.x, c.y, c.s, c.T, K)
+            sums.append(float(np.sum(np.abs(F) ** 2)) / (c.T * c.T) / A)
+        assert all(v <= 1.0 + 1e-12 for v in sums), sums
+        assert all(b > a for a, b in zip(sums, sums[1:])), sums
+        assert sums[-1] > 0.99, sums
