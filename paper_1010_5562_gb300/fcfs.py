@@ -10,7 +10,8 @@ from . import _lib
 from ._lib import FCFSError, PREC, FLAG_VALIDATE
 
 __all__ = ["forward", "adjoint", "edge_chain", "batch", "cosine", "haar", "workspace_size",
-           "cosine_workspace_size", "haar_workspace_size", "get_status", "launch_count", "FCFSError"]
+           "cosine_workspace_size", "haar_workspace_size", "forward_grouped", "adjoint_grouped",
+           "get_status", "launch_count", "FCFSError"]
 
 
 def _ptr(t):

@@ -203,3 +203,14 @@ def test_automatic_choices_against_the_sweeps(lib):
         assert best == "tie" or got == best, (T, K, V, got)
     assert lib.fcfs_adjoint_grouped(945586, 65536, 1024, 0) == 0    # the FP32 adjoint never groups
     assert lib.fcfs_adjoint_grouped(100, 1000, 8, 1) == -1
+
+
+def test_python_contraction_queries(lib):
+    """The binding's queries answer as the C ABI does (host only, no device work)."""
+    from paper_1010_5562_gb300 import fcfs
+    assert fcfs.forward_grouped(945450, 65536, 1024) == 1
+    assert fcfs.forward_grouped(12576, 4096, 256) == 0
+    assert fcfs.adjoint_grouped(945586, 65536, 1024) == 1
+    assert fcfs.adjoint_grouped(31700, 2048, 128) == 0
+    assert fcfs.adjoint_grouped(945586, 65536, 1024, prec="fp32") == 0
+    assert fcfs.forward_grouped(100, 1000, 8) == -1
