@@ -332,3 +332,46 @@ def pin_haar_half_tile(N, J):
     if J > 0:
         ref[1, 0] = N / 2
     return float(np.max(np.abs(W - ref))) / N
+
+
+def _r2(n):
+    """Representations of n as a^2 + b^2 over ordered signed pairs, by Jacobi's
+    two-square theorem: r2(0) = 1, r2(n) = 4 (d1(n) - d3(n)) with d_i the number
+    of divisors of n congruent to i mod 4.  Number theory only: no disc test."""
+    if n == 0:
+        return 1
+    d1 = d3 = 0
+    i = 1
+    while i * i <= n:
+        if n % i == 0:
+            for d in {i, n // i}:
+                if d % 4 == 1:
+                    d1 += 1
+                elif d % 4 == 3:
+                    d3 += 1
+        i += 1
+    return 4 * (d1 - d3)
+
+
+def pin_pupil(Ks=(0, 1, 2, 3, 5, 8, 13, 32)):
+    """The pupil disc of Sec. I, k^2 + l^2 <= K^2 on the (2K+1)^2 block, against
+    facts fixed by arithmetic: its size is the Gauss circle count sum_{n <= K^2}
+    r2(n) (1, 5, 13, 29, 81, 197, 529, 3209 for the Ks above), it is symmetric
+    under k -> -k, l -> -l and transposition, and the rim points (+-K, 0),
+    (0, +-K) belong to it while (K, 1) does not.  Returns the number of
+    violated facts (0 when all hold)."""
+    bad = 0
+    for K in Ks:
+        m = np.asarray(oracle.pupil_mask(K), dtype=bool)
+        if m.shape != (2 * K + 1, 2 * K + 1):
+            bad += 1
+            continue
+        if int(m.sum()) != sum(_r2(n) for n in range(K * K + 1)):
+            bad += 1
+        if not (np.array_equal(m, m[::-1, :]) and np.array_equal(m, m[:, ::-1]) and np.array_equal(m, m.T)):
+            bad += 1
+        if K >= 1:
+            c = K   # index of frequency 0
+            if not (m[c + K, c] and m[c - K, c] and m[c, c + K] and m[c, c - K]) or m[c + K, c + 1]:
+                bad += 1
+    return bad

@@ -16,6 +16,7 @@ _orig_tail = fo.tail_integral
 _orig_phase = fo._phase_exp
 _orig_entries = fo.block_entries
 _orig_vgrad = fo.vertex_gradient
+_orig_pupil = fo.pupil_mask
 
 
 def _tail_no_constant(freq, coord, T):
@@ -66,6 +67,20 @@ def _vgrad_conj_cotangent(x, y, s, T, K, G):
     return _orig_vgrad(x, y, s, T, K, np.conj(G))
 
 
+def _pupil_strict(K):
+    f = np.arange(-K, K + 1)
+    return (f[:, None] ** 2 + f[None, :] ** 2) < K * K
+
+
+def _pupil_half_radius(K):
+    f = np.arange(-K, K + 1)
+    return (f[:, None] ** 2 + f[None, :] ** 2) <= (K // 2) ** 2
+
+
+def _pupil_square(K):
+    return np.ones((2 * K + 1, 2 * K + 1), dtype=bool)
+
+
 MUTANTS = {
     "tail_no_constant": ("tail_integral", _tail_no_constant),
     "tail_k0_uses_a": ("tail_integral", _tail_k0_wrong),
@@ -77,6 +92,9 @@ MUTANTS = {
     "grad_sign": ("vertex_gradient", _vgrad_sign),
     "grad_swapped": ("vertex_gradient", _vgrad_swapped),
     "grad_conj_cotangent": ("vertex_gradient", _vgrad_conj_cotangent),
+    "pupil_strict": ("pupil_mask", _pupil_strict),
+    "pupil_half_radius": ("pupil_mask", _pupil_half_radius),
+    "pupil_square": ("pupil_mask", _pupil_square),
 }
 
 
@@ -93,6 +111,7 @@ def _run_pins():
     target, _ = config4_target(clip)
     errs["edge_grad"] = pins.pin_edge_gradient_boundary(clip, target, 6)
     errs["vertex_fd"] = pins.pin_vertex_gradient_fd(clip, target, 6, [0, 5])
+    errs["pupil"] = float(pins.pin_pupil())
     return errs
 
 

@@ -144,3 +144,9 @@ def test_bessel_bound_and_parseval_convergence():
         assert all(v <= 1.0 + 1e-12 for v in sums), sums
         assert all(b > a for a, b in zip(sums, sums[1:])), sums
         assert sums[-1] > 0.99, sums
+
+
+def test_pupil_disc_lattice_count():
+    """The pupil mask of Sec. I against the Gauss circle count from Jacobi's
+    two-square theorem, its symmetries and its rim points."""
+    assert pins.pin_pupil() == 0
