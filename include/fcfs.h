@@ -230,18 +230,26 @@ fcfs_status fcfs_haar(const int32_t* x, const int32_t* y, const int8_t* s, int64
  * exits.  Nothing is allocated per call, by the caller or by the library.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    The address is looked up again when the device's context has changed
+ *    since (for example after cudaDeviceReset, which reloads the module).
  *  - All calls share the array and it keeps the last call's contents (cached
  *    sincos tables; each call zeroes its accumulators itself).  Calls that
  *    overlap on the GPU (other streams, unordered host threads) race: issue
  *    them one after another.
  *  - A clip whose workspace exceeds the array runs with fewer vertex splits;
  *    if even one split does not fit (about K > 1400), FCFS_EUNSUPPORTED.
- *  - flags must be 0 (no device validation); device-side status is not exposed.
+ *  - flags must be 0 (no device validation).  Device-side status (a bounded
+ *    wait that gave up) is read with fcfs_noalloc_status.
  */
 #define FCFS_NOALLOC_SCRATCH_BYTES (32u << 20)
 fcfs_status fcfs_forward_noalloc(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V,
                                  int32_t T, int32_t K, int32_t prec, uint32_t flags,
                                  float* F_out, int64_t* area_out, void* stream);
+
+/* Status word of the last fcfs_forward_noalloc call on the current device:
+ * waits for `stream`, then returns FCFS_ETIMEOUT if a bounded device wait of
+ * that call gave up, FCFS_OK otherwise (FCFS_ECUDA if the read fails). */
+fcfs_status fcfs_noalloc_status(void* stream);
 
 /*
  * Environment: FCFS_PDL=0 launches the contraction kernel without programmatic

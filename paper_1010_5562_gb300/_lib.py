@@ -30,6 +30,7 @@ SIGNATURES = {
     "fcfs_haar": (C.c_int, [_p, _p, _p, _i64, _i32, _i32, _u32, _p, _p, _sz, _p]),
     "fcfs_get_status": (C.c_int, [_p, _p]),
     "fcfs_forward_noalloc": (C.c_int, [_p, _p, _p, _i64, _i32, _i32, _i32, _u32, _p, _p, _p]),
+    "fcfs_noalloc_status": (C.c_int, [_p]),
     "fcfs_debug_set_splits": (None, [_i32]),
     "fcfs_debug_set_fuse": (None, [_i32]),
     "fcfs_debug_set_pair": (None, [_i32]),

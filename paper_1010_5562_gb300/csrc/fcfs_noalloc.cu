@@ -18,6 +18,8 @@
 // rejected with FCFS_EUNSUPPORTED.
 #include <mutex>
 
+#include <cudaTypedefs.h>
+
 #include "fcfs_common.cuh"
 
 namespace fcfs {
@@ -31,21 +33,57 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[FCFS_NOALLOC_SC
 namespace {
 
 constexpr int kMaxDevices = 64;
+struct ScratchSlot {
+  unsigned long long ctx_id;   // driver context the address belongs to (0: none yet)
+  void* ptr;
+};
 std::mutex g_scratch_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
+ScratchSlot g_scratch[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the first call on a device does this set-up).
+PFN_cuCtxGetCurrent_v4000 g_ctx_current = nullptr;
+PFN_cuCtxGetId_v12000 g_ctx_id = nullptr;
+std::once_flag g_ctx_once;
+
+// Unique id of the context current on this thread (0 if none or unknown).
+// Context ids are never reused within a process, unlike context handles.
+unsigned long long current_context_id() {
+  std::call_once(g_ctx_once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f);
+  });
+  if (!g_ctx_current || !g_ctx_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_current(&c) != CUDA_SUCCESS || c == nullptr) return 0;
+  if (g_ctx_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device.  The address is
+// looked up (cudaGetSymbolAddress, which allocates nothing) on the first call
+// on a device and again whenever the device's context has changed since (after
+// cudaDeviceReset the module is loaded anew and the old address is invalid).
 fcfs_status scratch_on_current_device(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FCFS_ECUDA;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
+  ScratchSlot& sl = g_scratch[dev];
+  unsigned long long id = current_context_id();
+  if (sl.ptr == nullptr || id == 0 || id != sl.ctx_id) {
     void* p = nullptr;
+    // also makes the device's primary context current if none is
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return FCFS_ECUDA;
-    g_scratch_ptr[dev] = p;
+    sl.ptr = p;
+    sl.ctx_id = id ? id : current_context_id();
   }
-  *out = g_scratch_ptr[dev];
+  *out = sl.ptr;
   return FCFS_OK;
 }
 
@@ -92,4 +130,17 @@ extern "C" fcfs_status fcfs_forward_noalloc(const int32_t* x, const int32_t* y, 
   if (e != cudaSuccess) return FCFS_ECUDA;
   if (launch_reduce(pl, ws, F_out, area_out, false, st) != cudaSuccess) return FCFS_ECUDA;
   return FCFS_OK;
+}
+
+// Status word of the last call on this device: waits for `stream`, then reads
+// the status the kernels wrote into the scratch array (a bounded wait that gave
+// up, FCFS_ETIMEOUT; otherwise FCFS_OK).
+extern "C" fcfs_status fcfs_noalloc_status(void* stream) {
+  void* ws = nullptr;
+  fcfs_status r = scratch_on_current_device(&ws);
+  if (r != FCFS_OK) return r;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return FCFS_ECUDA;
+  Status h{0, 0};
+  if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return FCFS_ECUDA;
+  return static_cast<fcfs_status>(h.code);
 }

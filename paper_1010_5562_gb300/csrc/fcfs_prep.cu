@@ -52,6 +52,11 @@ __global__ void prep_kernel(Plan pl, uint8_t* ws, int validate) {
     for (long long i = gid; i < 2LL * (T + 1); i += gsz) hist[i] = 0;
   }
   if (*reinterpret_cast<volatile const unsigned long long*>(ws + kTagOffset) == pl.tag) return;
+  // The tables are about to change: drop the old tag first, so that a call that
+  // fails after this kernel cannot leave a tag that vouches for the tables of
+  // another period (every CTA that sees a mismatch rebuilds, so the cleared tag
+  // never makes one skip).
+  if (threadIdx.x == 0) *reinterpret_cast<volatile unsigned long long*>(ws + kTagOffset) = 0ull;
   const double scale = ldexp(1.0, pl.fixq);
   if (pl.full) {
     for (long long p = gid; p < T; p += gsz) {

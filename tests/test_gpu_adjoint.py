@@ -141,7 +141,7 @@ def test_config5_adjoint_sampled(fc, prec):
     idx = np.sort(rng.choice(clip.V, 48, replace=False))
     rx, ry = oracle.vertex_gradient(clip.x[idx], clip.y[idx], clip.s[idx], clip.T, K, G.astype(np.complex128))
     ex, ey = rel(gx[idx], rx), rel(gy[idx], ry)
-    assert ex < 1e-4 and ey < 1e-4, (ex, ey)
+    assert ex < 1e-5 and ey < 1e-5, (ex, ey)
 
 
 def grad_mode(fc, clip, K, G, mode):

@@ -33,10 +33,20 @@ def run_batch(fc, clips, K, prec):
     return F.cpu().numpy().astype(np.complex128), area.cpu().numpy()
 
 
+_ORACLE_CACHE = {}
+
+
+def _oracle_block(clip, K):
+    key = (clip.T, K, clip.V, clip.x.tobytes(), clip.y.tobytes(), clip.s.tobytes())
+    if key not in _ORACLE_CACHE:   # both precisions compare with the same block
+        _ORACLE_CACHE[key] = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    return _ORACLE_CACHE[key]
+
+
 def check_clip(F, area, clip, K, prec):
     A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
     assert int(area) == A
-    Fo = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    Fo = _oracle_block(clip, K)
     err = np.max(np.abs(F - Fo)) / max(A, 1)
     assert err <= TOL[prec], err
 
@@ -77,14 +87,15 @@ def test_batch_matches_single_clip_calls(fc, prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_config3_full_batch(fc, prec):
-    """512 clips, T=2048, V_c log-uniform in [1e3, 1e5], K=128; a spread of clips
-    is checked against the oracle, every area exactly."""
+    """512 clips, T=2048, V_c log-uniform in [1e3, 1e5], K=128; 64 clips spread
+    evenly over the range of V (the smallest and largest included) are checked
+    against the oracle element by element, every area exactly."""
     clips, K = batch_clips()
     F, area = run_batch(fc, clips, K, prec)
     for c, clip in enumerate(clips):
         assert int(area[c]) == oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
     order = np.argsort([cl.V for cl in clips])
-    for c in order[[0, 1, 128, 256, 384, 510, 511]]:
+    for c in order[np.unique(np.linspace(0, len(clips) - 1, 64).round().astype(int))]:
         check_clip(F[c], area[c], clips[c], K, prec)
 
 

@@ -4,10 +4,11 @@ fcfs_forward_noalloc runs the same transform as fcfs_forward but takes no
 workspace: its scratch is a fixed array inside the library.  It is meant for
 code that cannot call cudaMalloc where it needs the transform (a plugin whose
 host framework owns all device memory, a real-time loop that must not stall
-on an allocation).  This file is collected last and also runs alone.
+on an allocation).  Its blocks are checked against the FP64 oracle, two calls
+in a row (the second reuses what the first left in the array), including
+clips whose automatic split count does not fit the array and runs shrunk.
+This file is collected last and also runs alone.
 """
-import ctypes as C
-
 import numpy as np
 import pytest
 import torch
@@ -38,25 +39,61 @@ def _noalloc(lib, x, y, s, T, K, prec):
     code = lib.fcfs_forward_noalloc(x.data_ptr(), y.data_ptr(), s.data_ptr(), x.numel(), T, K, PREC[prec], 0,
                                     F.data_ptr(), area.data_ptr(), stream)
     assert code == 0, code
-    torch.cuda.synchronize()
+    assert lib.fcfs_noalloc_status(stream) == 0
     return F.cpu().numpy().astype(np.complex128), int(area.item())
 
 
 @pytest.mark.parametrize("prec", ["fp32", "split_f16"])
 @pytest.mark.parametrize("cfg", [1, 2])
-def test_noalloc_matches_forward_twice(lib, prec, cfg):
-    from paper_1010_5562_gb300 import fcfs
+def test_noalloc_matches_oracle_twice(lib, prec, cfg):
     clip, K = config_clip(cfg)
     x, y, s = (torch.from_numpy(a).cuda() for a in (clip.x, clip.y, clip.s))
-    Fr, ar = fcfs.forward(x, y, s, clip.T, K, prec=prec)
-    torch.cuda.synchronize()
-    Fr = Fr.cpu().numpy().astype(np.complex128)
+    Fo = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
     A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
     for _ in range(2):   # the second call reuses the array the first one left behind
         F, area = _noalloc(lib, x, y, s, clip.T, K, prec)
-        assert area == int(ar.item()) == A
+        assert area == A
         assert np.all(np.isfinite(F))
-        assert np.max(np.abs(F - Fr)) / A <= TOL[prec]
+        assert np.max(np.abs(F - Fo)) / A <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_f16"])
+def test_noalloc_shrinks_the_split_count(lib, prec):
+    """64 forced vertex splits of the T = 4096, K = 256 clip need 64 MiB of
+    partial planes: the call runs with as many splits as the array holds."""
+    clip, K = config_clip(2)
+    x, y, s = (torch.from_numpy(a).cuda() for a in (clip.x, clip.y, clip.s))
+    Fo = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+    lib.fcfs_debug_set_splits(64)
+    try:
+        for _ in range(2):
+            F, area = _noalloc(lib, x, y, s, clip.T, K, prec)
+            assert area == A
+            assert np.max(np.abs(F - Fo)) / A <= TOL[prec]
+    finally:
+        lib.fcfs_debug_set_splits(0)
+
+
+def test_noalloc_large_block_one_split(lib):
+    """K = 1024 on the T = 4096 clip: 16 MiB per split, so only one split fits
+    beside the tables; sampled rows against the oracle, then a smaller K again
+    (the array's tables and tag from the K = 1024 call are reused)."""
+    clip, _ = config_clip(2)
+    K = 1024
+    x, y, s = (torch.from_numpy(a).cuda() for a in (clip.x, clip.y, clip.s))
+    A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+    rows = np.array([-K, -K + 1, -517, -64, -1, 0, 1, 2, 255, 700, K - 1, K])
+    Fo = oracle.block_entries(clip.x, clip.y, clip.s, clip.T, rows, oracle.freqs(K))
+    for _ in range(2):
+        F, area = _noalloc(lib, x, y, s, clip.T, K, "split_f16")
+        assert area == A
+        assert np.all(np.isfinite(F))
+        assert np.max(np.abs(F[rows + K, :] - Fo)) / A <= TOL["split_f16"]
+    Ks = 64
+    F, area = _noalloc(lib, x, y, s, clip.T, Ks, "fp32")
+    Fo = oracle.block(clip.x, clip.y, clip.s, clip.T, Ks)
+    assert area == A and np.max(np.abs(F - Fo)) / A <= TOL["fp32"]
 
 
 def test_noalloc_rejects_what_does_not_fit(lib):
