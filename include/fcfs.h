@@ -276,6 +276,18 @@ fcfs_status fcfs_noalloc_status(void* stream);
  */
 void fcfs_profile_enable(int32_t on);
 int32_t fcfs_profile_read(float* ms, int32_t n);
+/* Kernel timing by stage name: fcfs_kernel_timing_enable(1) clears the records
+ * and makes every later call bracket each of its stages (a kernel, or a short
+ * group such as the three grouping kernels) with two events on the caller's
+ * stream, up to 64 records; (0) stops recording.  fcfs_kernel_timing_count()
+ * waits for the last record and returns how many there are; name(i) and ms(i)
+ * give stage i's name (a static string) and its elapsed time (-1 on error).
+ * Events between launches serialise stages that would otherwise overlap: use
+ * it for measurement passes, not for timed runs. */
+void fcfs_kernel_timing_enable(int32_t on);
+int32_t fcfs_kernel_timing_count(void);
+const char* fcfs_kernel_timing_name(int32_t i);
+float fcfs_kernel_timing_ms(int32_t i);
 void fcfs_debug_set_splits(int32_t n);
 void fcfs_debug_set_fuse(int32_t on);
 /* Which contraction fcfs_forward (flags 0) will run for these sizes: 1 when it

@@ -41,6 +41,10 @@ SIGNATURES = {
     "fcfs_profile_enable": (None, [_i32]),
     "fcfs_set_batch_unit_chunks": (None, [_i32]),
     "fcfs_profile_read": (_i32, [C.POINTER(C.c_float), _i32]),
+    "fcfs_kernel_timing_enable": (None, [_i32]),
+    "fcfs_kernel_timing_count": (_i32, []),
+    "fcfs_kernel_timing_name": (C.c_char_p, [_i32]),
+    "fcfs_kernel_timing_ms": (C.c_float, [_i32]),
 }
 
 _lib = None

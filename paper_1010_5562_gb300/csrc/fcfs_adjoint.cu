@@ -381,13 +381,22 @@ static fcfs_status adjoint_impl(const int32_t* x, const int32_t* y, const int8_t
   if ((r = check_ws(ap.p, ws, ws_bytes)) != FCFS_OK) return r;
   if (V == 0) return FCFS_OK;
   if (ap.tc && (!aligned16_ptr(x) || !aligned16_ptr(y))) return FCFS_EINVAL;
-  if (launch_prep(ap.p, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
-  adj_coef_kernel<<<dim3(ap.rows, 2), kAdjThreads, 0, st>>>(ap, reinterpret_cast<const float2*>(dF),
-                                                            static_cast<uint8_t*>(ws));
+  {
+    KtScope ks("adj_prep", st);
+    if (launch_prep(ap.p, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
+  }
+  {
+    KtScope ks("adj_coef", st);
+    adj_coef_kernel<<<dim3(ap.rows, 2), kAdjThreads, 0, st>>>(ap, reinterpret_cast<const float2*>(dF),
+                                                              static_cast<uint8_t*>(ws));
+  }
   count_launch(1);
   if (cudaGetLastError() != cudaSuccess) return FCFS_ECUDA;
   if (ap.tc) {
-    adj_pack_kernel<<<dim3(ap.nrows_pad + 1, 2), 256, 0, st>>>(ap, static_cast<uint8_t*>(ws));
+    {
+      KtScope ks("adj_pack", st);
+      adj_pack_kernel<<<dim3(ap.nrows_pad + 1, 2), 256, 0, st>>>(ap, static_cast<uint8_t*>(ws));
+    }
     count_launch(1);
     if (cudaGetLastError() != cudaSuccess) return FCFS_ECUDA;
     const __half* mp = reinterpret_cast<const __half*>(static_cast<uint8_t*>(ws) + ap.off_mp);
@@ -412,16 +421,21 @@ static fcfs_status adjoint_impl(const int32_t* x, const int32_t* y, const int8_t
     ar.ny_pad = ap.ny_pad;
     ar.off_groups = ap.off_groups;
     // gx contracts over y, gy over x: group the corners by y and by x
-    if (ap.grouped &&
-        launch_grouping(y, x, V, T, ap.ny_pad, static_cast<uint8_t*>(ws) + ap.off_groups, st) != cudaSuccess)
-      return FCFS_ECUDA;
+    if (ap.grouped) {
+      KtScope ks("adj_group", st);
+      if (launch_grouping(y, x, V, T, ap.ny_pad, static_cast<uint8_t*>(ws) + ap.off_groups, st) != cudaSuccess)
+        return FCFS_ECUDA;
+    }
+    KtScope ks(ap.grouped ? "adj_tc_grouped" : "adj_tc", st);
     if (launch_adj_tc(ar, mhi, mlo, ws, st) != cudaSuccess) return FCFS_ECUDA;
   } else {
+    KtScope ks("adj_gemm_fp32", st);
     const cudaError_t e =
         ap.p.full ? launch_adj_gemm_r<true>(ap, x, y, ws, st) : launch_adj_gemm_r<false>(ap, x, y, ws, st);
     if (e != cudaSuccess) return FCFS_ECUDA;
   }
   const int blocks = (int)std::min<long long>((V + 255) / 256, 4096);
+  KtScope ks("adj_finalize", st);
   adj_finalize_kernel<<<blocks, 256, 0, st>>>(ap, s, static_cast<uint8_t*>(ws), gx, gy);
   count_launch(1);
   if (cudaGetLastError() != cudaSuccess) return FCFS_ECUDA;

@@ -11,6 +11,7 @@
 #include <math_constants.h>
 
 #include "fcfs_common.cuh"
+#include "fcfs_group.cuh"
 
 namespace fcfs {
 
@@ -33,6 +34,27 @@ static void prof_mark(int i, cudaStream_t st) {
 }
 
 size_t tc_smem_for(int bn, int T, int full);
+
+// Kernel timing records: name and a pair of events each, up to kKtMax per
+// enable; one stage is open at a time.
+constexpr int kKtMax = 64;
+static bool g_kt = false;
+static bool g_kt_made = false;
+static cudaEvent_t g_kt_ev[2 * kKtMax];
+static const char* g_kt_name[kKtMax];
+static int g_kt_n = 0, g_kt_open = -1;
+void kt_begin(const char* name, cudaStream_t st) {
+  if (!g_kt || g_kt_n >= kKtMax) return;
+  g_kt_name[g_kt_n] = name;
+  cudaEventRecord(g_kt_ev[2 * g_kt_n], st);
+  g_kt_open = g_kt_n;
+}
+void kt_end(cudaStream_t st) {
+  if (!g_kt || g_kt_open < 0) return;
+  cudaEventRecord(g_kt_ev[2 * g_kt_open + 1], st);
+  g_kt_n = g_kt_open + 1;
+  g_kt_open = -1;
+}
 
 static int ceil_log2(long long v) {
   int r = 0;
@@ -171,32 +193,55 @@ fcfs_status make_plan_cosine(int64_t V, int32_t T, int32_t K, int32_t prec, Plan
   return plan_impl(V, 2 * T, K, prec, true, true, pl);
 }
 
-int hybrid_mode() { return g_hybrid; }
+int hybrid_mode() { return g_hybrid == 3 ? 1 : g_hybrid; }
 bool pair_enabled() { return g_pair != 0; }
 
-// Row-binned contraction (corners grouped by y, contraction over the T + 1
-// values of y): eligible for a single-clip split-FP16 call on CTA pairs.  The
-// automatic choice compares two cost estimates (ms) fitted to GB300
-// measurements of both forms (T = 4096 .. 65536, K = 256 .. 1024,
-// V / (T + 1) = 0.8 .. 49; the estimate picks the faster form in 19 of 21 cases,
-// the other two within 9%):
-//   over the corners  0.04 + 1.5e-11 V K^2                  ((2K)^2 tensor MACs per corner)
-//   grouped by y      0.08 + 4e-6 T + 1.8e-11 (T + 1) K^2   (grouping, axis lines, the
-//                     + 1.3e-9 V K (1 + 120 / chunks)        contraction over y, and H:
-//                                                            K fixed-point terms per corner,
-//                                                            spread over the 64-y chunks)
-static bool grouped_cheaper(long long V, int T, int K) {
-  const double v = (double)V, k = (double)K, t = (double)T;
-  const double chunks = (double)((T + 1 + 63) / 64);
-  const double direct = 0.04 + 1.5e-11 * v * k * k;
-  const double grouped = 0.08 + 4e-6 * t + 1.8e-11 * (t + 1.0) * k * k + 1.3e-9 * v * k * (1.0 + 120.0 / chunks);
-  return grouped < direct;
+// The contraction of a single-clip call (fcfs_forward_grouped reports it):
+//   kDirect      over the V corners (tensor cores, or the plain FP32 kernel);
+//   kGroupedTc   corners grouped by y, split-FP16 contraction over the T + 1
+//                values of y (split-FP16 calls on CTA pairs);
+//   kGroupedFft  corners grouped by y, pruned FFT along y in FP32 (any precision:
+//                its error is below the plain FP32 path's).
+// The automatic choice takes the cheapest estimate (ms) among the forms the call
+// may take; the estimates are fitted to GB300 measurements of each form:
+//   direct, tensor cores   0.04 + 1.5e-11 V K^2        ((2K)^2 tensor MACs per corner)
+//   direct, plain FP32     0.02 + 1.7e-10 V K^2
+//   grouped, tensor cores  0.08 + 4e-6 T + 1.8e-11 (T + 1) K^2 + h
+//   grouped, FFT           0.08 + 4e-6 T + 2e-9 K T + h
+//   h = 3.3e-10 V K (1 + 120 / chunks)   (the H kernel: K terms per corner over
+//                                         the chunks = T / 64 items of 64 rows)
+// (grouping and axis lines in the constant and T terms).
+enum { kDirect = 0, kGroupedTc = 1, kGroupedFft = 2 };
+
+static double cost_h(double v, double t, double k) {
+  const double chunks = std::max(1.0, t / 64.0);
+  return 3.3e-10 * v * k * (1.0 + 120.0 / chunks);
 }
 
-static bool hybrid_wanted(const Plan& pl, bool validate) {
-  if (g_hybrid == 0 || validate || !pl.pair || pl.prec != FCFS_PREC_SPLIT_F16 || pl.V <= 0 || pl.logT > 16)
-    return false;
-  return g_hybrid == 2 || grouped_cheaper(pl.V, pl.T, pl.K);
+static int forward_form(const Plan& pl, bool validate) {
+  if (g_hybrid == 0 || validate || pl.V <= 0 || pl.logT > 16 || pl.cosine) return kDirect;
+  const bool tc_ok = pl.pair && pl.prec == FCFS_PREC_SPLIT_F16;
+  const bool fft_ok = pl.K <= 4096;
+  if (g_hybrid == 2) return tc_ok ? kGroupedTc : kDirect;
+  if (g_hybrid == 3) return fft_ok ? kGroupedFft : kDirect;
+  const double v = (double)pl.V, k = (double)pl.K, t = (double)pl.T;
+  double best = pl.prec == FCFS_PREC_SPLIT_F16 ? 0.04 + 1.5e-11 * v * k * k : 0.02 + 1.7e-10 * v * k * k;
+  int form = kDirect;
+  if (tc_ok) {
+    const double c = 0.08 + 4e-6 * t + 1.8e-11 * (t + 1.0) * k * k + cost_h(v, t, k);
+    if (c < best) {
+      best = c;
+      form = kGroupedTc;
+    }
+  }
+  if (fft_ok) {
+    const double c = 0.08 + 4e-6 * t + 2e-9 * k * t + cost_h(v, t, k);
+    if (c < best) {
+      best = c;
+      form = kGroupedFft;
+    }
+  }
+  return form;
 }
 
 // Turn a single-clip pair plan into the row-binned one: splits over 64-y
@@ -212,6 +257,28 @@ static void plan_hybrid(Plan& pl) {
   pl.splits = (int)((nchunks + per - 1) / per);
   size_t o = align_up(pl.off_part + (size_t)pl.splits * pl.M2 * pl.M2 * sizeof(float), kWsAlign);
   pl.total = hybrid_extra_bytes(pl.V, pl.T, pl.M2, pl.ny_pad, pl.off_ycnt, pl.off_h, o);
+}
+
+// The grouped form with the pruned FFT along y: no partial planes; the grouping
+// and the polyphase conj(H) (K T complex values) after the shared regions.
+static void plan_fft(Plan& pl) {
+  pl.hyb = 1;
+  pl.yfft = 1;
+  pl.ny_pad = (pl.T + 1 + 63) / 64 * 64;
+  pl.splits = 0;
+  pl.split_len = 0;
+  pl.fft_logL = fft_log_len(pl.T, pl.K);
+  size_t o = align_up(pl.off_part, kWsAlign);
+  pl.off_ycnt = o;
+  o = align_up(o + group_bytes(pl.V, pl.T, pl.ny_pad), kWsAlign);
+  pl.off_poly = o;
+  o = align_up(o + (size_t)pl.K * pl.T * 8, kWsAlign);
+  pl.total = o;
+}
+
+static void plan_form(Plan& pl, int form) {
+  if (form == kGroupedTc) plan_hybrid(pl);
+  else if (form == kGroupedFft) plan_fft(pl);
 }
 
 // ---------------------------------------------------------------------------
@@ -332,14 +399,17 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
   fcfs_status r = make_plan_ex(V, T, K, prec, true, pl);
   if (r != FCFS_OK) return r;
   const bool validate = (flags & FCFS_FLAG_VALIDATE) != 0;
-  if (hybrid_wanted(pl, validate)) plan_hybrid(pl);
+  plan_form(pl, forward_form(pl, validate));
   if ((r = check_ws(pl, ws, ws_bytes)) != FCFS_OK) return r;
   VertexMaps mp{};
   pl.vx = x;
   pl.vy = y;
   pl.vsg = s;
   prof_mark(0, st);
-  FCFS_CU(launch_prep(pl, ws, validate, st));
+  {
+    KtScope ks("prep", st);
+    FCFS_CU(launch_prep(pl, ws, validate, st));
+  }
   prof_mark(1, st);
   // the contraction also bins the corners for the axis lines (Steps 2-3), so
   // the axis DFT follows it; device validation keeps its own binning pass
@@ -356,12 +426,33 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
     pl.area_out = reinterpret_cast<long long*>(area);
   }
   prof_mark(4, st);
-  if (pl.hyb)
+  if (pl.yfft) {
+    // grouping, H, the FFT along y; then the exact axis lines and their output
+    FCFS_CU(launch_grouped_fft(pl, ws, F, st));
+    prof_mark(5, st);
+    prof_mark(2, st);
+    {
+      KtScope ks("axis_lines", st);
+      FCFS_CU(launch_axis(pl, x, y, s, ws, false, st));
+    }
+    prof_mark(3, st);
+    prof_mark(6, st);
+    {
+      KtScope ks("axis_out", st);
+      FCFS_CU(launch_axis_out(pl, ws, F, area, st));
+    }
+    prof_mark(7, st);
+    return FCFS_OK;
+  }
+  if (pl.hyb) {
     FCFS_CU(launch_hybrid(pl, ws, st));
-  else if (prec == FCFS_PREC_SPLIT_F16)
+  } else if (prec == FCFS_PREC_SPLIT_F16) {
+    KtScope ks(pl.fused ? "gemm_tc_fused" : "gemm_tc", st);
     FCFS_CU(launch_gemm_tc(pl, mp, ws, st));
-  else
+  } else {
+    KtScope ks("gemm_fp32", st);
     FCFS_CU(launch_gemm_simt(pl, x, y, s, ws, st));
+  }
   prof_mark(5, st);
   if (pl.fused) {
     for (int i = 2; i <= 3; ++i) prof_mark(i, st);
@@ -369,10 +460,16 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
     return FCFS_OK;
   }
   prof_mark(2, st);
-  FCFS_CU(launch_axis(pl, x, y, s, ws, validate, st));
+  {
+    KtScope ks("axis_lines", st);
+    FCFS_CU(launch_axis(pl, x, y, s, ws, validate, st));
+  }
   prof_mark(3, st);
   prof_mark(6, st);
-  FCFS_CU(launch_reduce(pl, ws, F, area, validate, st));
+  {
+    KtScope ks("reduce", st);
+    FCFS_CU(launch_reduce(pl, ws, F, area, validate, st));
+  }
   prof_mark(7, st);
   return FCFS_OK;
 }
@@ -404,11 +501,8 @@ size_t fcfs_workspace_size(int64_t V, int32_t T, int32_t K, int32_t prec) {
   Plan pl;
   if (make_plan_ex(V, T, K, prec, true, pl) != FCFS_OK) return 0;
   size_t total = pl.total;   // covers calls with device validation, which never group by y
-  if (hybrid_wanted(pl, false)) {
-    plan_hybrid(pl);
-    total = std::max(total, pl.total);
-  }
-  return total;
+  plan_form(pl, forward_form(pl, false));
+  return std::max(total, pl.total);
 }
 
 fcfs_status fcfs_forward(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, int32_t T, int32_t K,
@@ -431,15 +525,40 @@ void fcfs_debug_set_splits(int32_t s) { g_split_override = s; }
 void fcfs_debug_set_fuse(int32_t on) { g_fuse = on ? 1 : 0; }
 void fcfs_debug_set_pair(int32_t on) { g_pair = on ? 1 : 0; }
 void fcfs_debug_set_barrier_extra(int32_t n) { g_barrier_extra = n > 0 ? n : 0; }
-void fcfs_debug_set_hybrid(int32_t mode) { g_hybrid = mode < 0 ? 0 : (mode > 2 ? 2 : mode); }
+void fcfs_debug_set_hybrid(int32_t mode) { g_hybrid = mode < 0 ? 0 : (mode > 3 ? 3 : mode); }
 
 int32_t fcfs_forward_grouped(int64_t V, int32_t T, int32_t K, int32_t prec) {
   Plan pl;
   if (make_plan_ex(V, T, K, prec, true, pl) != FCFS_OK) return -1;
-  return hybrid_wanted(pl, false) ? 1 : 0;
+  return forward_form(pl, false);
 }
 
 void fcfs_profile_enable(int32_t on) { g_prof = on != 0; }
+
+void fcfs_kernel_timing_enable(int32_t on) {
+  if (on && !g_kt_made) {
+    for (auto& e : g_kt_ev) cudaEventCreate(&e);
+    g_kt_made = true;
+  }
+  g_kt = on != 0;
+  g_kt_n = 0;
+  g_kt_open = -1;
+}
+
+int32_t fcfs_kernel_timing_count(void) {
+  if (!g_kt_made || g_kt_n == 0) return 0;
+  if (cudaEventSynchronize(g_kt_ev[2 * g_kt_n - 1]) != cudaSuccess) return 0;
+  return g_kt_n;
+}
+
+const char* fcfs_kernel_timing_name(int32_t i) { return (i >= 0 && i < g_kt_n) ? g_kt_name[i] : ""; }
+
+float fcfs_kernel_timing_ms(int32_t i) {
+  float ms = -1.f;
+  if (i < 0 || i >= g_kt_n || cudaEventElapsedTime(&ms, g_kt_ev[2 * i], g_kt_ev[2 * i + 1]) != cudaSuccess)
+    return -1.f;
+  return ms;
+}
 
 int32_t fcfs_profile_read(float* ms, int32_t n) {
   if (!g_ev_made || !ms) return 0;

@@ -64,6 +64,10 @@ struct Plan {
   int32_t ny_pad;              // T + 1 rounded up to the chunk (64)
   size_t off_ycnt;             // the corners grouped by y (fcfs_group.cuh)
   size_t off_h;                // FP16 [2][M2][ny_pad]: H = sum over a y group of s A, hi then lo
+  // grouped forward with a pruned FFT along y instead of the contraction over y
+  int32_t yfft;
+  int32_t fft_logL;            // FFT length L = 2^fft_logL (T = P L)
+  size_t off_poly;             // complex FP32 [K][P][L]: conj(H) in polyphase order
   // continuous cosine series: T is twice the clip's period and the M2 = K rows
   // (and columns) of the contraction are sin(2 pi f a / T), f = 1..K, only
   int32_t cosine;
@@ -508,6 +512,12 @@ cudaError_t launch_adj_tc(const AdjTcArgs& ar, const CUtensorMap& mhi, const CUt
 // Row-binned contraction (fcfs_hybrid.cu): grouping, H, and the contraction
 // over y into the plan's FP32 partial planes.
 cudaError_t launch_hybrid(const Plan& pl, void* ws, cudaStream_t st);
+// Grouped forward with the pruned FFT along y (fcfs_hybrid.cu, fcfs_fft.cu): grouping,
+// H in polyphase order, the FFT kernel (off-axis block), then the axis-line output.
+cudaError_t launch_grouped_fft(const Plan& pl, void* ws, float* F, cudaStream_t st);
+cudaError_t launch_fft_y(const Plan& pl, void* ws, float* F, cudaStream_t st);
+cudaError_t launch_axis_out(const Plan& pl, void* ws, float* F, int64_t* area, cudaStream_t st);
+int fft_log_len(int T, int K);
 // Workspace regions of the row-binned contraction placed from `base`; returns the end.
 size_t hybrid_extra_bytes(int64_t V, int T, int M2, int ny_pad, size_t& off_ycnt, size_t& off_h, size_t base);
 // 2-D FP16 tensor map (cols innermost), 128-byte swizzle, box box_cols x box_rows
@@ -519,5 +529,16 @@ int gemm_tc_fuse_cluster(const Plan& pl);
 bool make_part_map(const Plan& pl, void* ws, int parts, CUtensorMap* map);
 cudaError_t launch_gemm_tc(const Plan& pl, const VertexMaps& maps, void* ws, cudaStream_t st);
 void count_launch(int n);
+
+// Kernel timing (a measurement hook, off by default): while enabled, each
+// instrumented stage of a call is bracketed by two events on the caller's
+// stream, recorded under the stage's name (fcfs_kernel_timing_* in fcfs.h).
+void kt_begin(const char* name, cudaStream_t st);
+void kt_end(cudaStream_t st);
+struct KtScope {
+  cudaStream_t st;
+  KtScope(const char* name, cudaStream_t s) : st(s) { kt_begin(name, s); }
+  ~KtScope() { kt_end(st); }
+};
 
 }  // namespace fcfs

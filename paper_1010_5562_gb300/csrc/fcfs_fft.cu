@@ -1,0 +1,276 @@
+// Pruned FFT along y for the grouped forward block (the sparse-image DFT of
+// Step 4 with its output pruned to |l| <= K, as the paper's pruned FFT does).
+//
+// With the corners grouped by y, h_k[y] = sum over row y of s_v e^{-j 2 pi k x_v / T}
+// (the conjugate of the grouped contraction's H, written by the H kernel), the
+// off-axis block is
+//     G(k, l) = sum_{y=0}^{T-1} h_k[y] e^{-j 2 pi l y / T},   F(k, l) = -T^2/(4 pi^2 k l) G(k, l)
+// (Eq. Fkl; row y = T folded onto y = 0).  Only |l| <= K is wanted.  With
+// T = P L (L a power of two >= 2K, P <= 16) and y = a + P b,
+//     G(k, l) = sum_{a<P} e^{-j 2 pi l a / T} D_a(l mod L),   D_a(m) = sum_{b<L} h_k[a + P b] e^{-j 2 pi m b / L},
+// so each k costs P FFTs of length L (O(T log L)) and (2K+1) P twiddled sums,
+// instead of the contraction's 2 (2K) T MACs.  h_k arrives in polyphase order
+// [k-1][a][b], so every FFT reads L consecutive complex values.
+//
+// One CTA per frequency k >= 1 (and its mirror -k): the FFTs run as mixed-radix
+// Stockham passes (one radix-2/4/8/16 pass reading global memory, then radix-16
+// passes in padded shared memory), each thread owning 2K+1 / blockDim outputs l
+// whose twiddled sums it accumulates in registers over the P residues.
+// Arithmetic is FP32 throughout; every twiddle is a correctly rounded FP32 table
+// value at an exact integer phase.
+#include <algorithm>
+
+#include "fcfs_epilogue.cuh"
+#include "fcfs_launch.cuh"
+
+namespace fcfs {
+
+namespace {
+
+constexpr int kFBufPts = 4096;   // complex points per buffer (several FFTs when L < 4096)
+constexpr int kFOwnMax = 9;      // outputs per thread (2K + 1 <= 9 blockDim)
+
+struct FftArgs {
+  Plan pl;
+  const uint8_t* ws;
+  const float2* poly;   // [K][P][L] conj(H) in polyphase order
+  int logL, logP;
+  float2* F;            // (2K+1)^2 block
+};
+
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.y, b.x, a.x * b.y));
+}
+// a * e^{-j 2 pi q / R} for the compile-time twiddles of the radix butterflies
+template <int R, int Q>
+__device__ __forceinline__ float2 rot(float2 a) {
+  constexpr int q = Q % R;
+  if constexpr (q == 0) {
+    return a;
+  } else if constexpr (4 * q == R) {   // -j
+    return make_float2(a.y, -a.x);
+  } else if constexpr (2 * q == R) {
+    return make_float2(-a.x, -a.y);
+  } else if constexpr (4 * q == 3 * R) {   // +j
+    return make_float2(-a.y, a.x);
+  } else {
+    // cos and sin of 2 pi q / R for R in {8, 16}
+    constexpr double c8 = 0.70710678118654752440, c16 = 0.92387953251128675613, s16 = 0.38268343236508977173;
+    constexpr int qq = R == 8 ? 2 * q : q;   // in sixteenths of a turn
+    constexpr double cs = (qq == 1 || qq == 15) ? c16 : (qq == 2 || qq == 14) ? c8 : (qq == 3 || qq == 13) ? s16
+                        : (qq == 5 || qq == 11) ? -s16 : (qq == 6 || qq == 10) ? -c8 : -c16;
+    constexpr double sn = (qq == 1 || qq == 7) ? s16 : (qq == 2 || qq == 6) ? c8 : (qq == 3 || qq == 5) ? c16
+                        : (qq == 9 || qq == 15) ? -s16 : (qq == 10 || qq == 14) ? -c8 : -c16;
+    const float c = (float)cs, s = (float)sn;   // e^{-j t} = c - j s
+    return make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -(a.x * s)));
+  }
+}
+
+// In-register DFT of R points, forward sign, by halving (even/odd).
+template <int R>
+struct Dft {
+  template <int S, int O>
+  __device__ __forceinline__ static void sub(const float2* x, float2* y) {
+    // y[q] = sum_r x[O + S r] e^{-j 2 pi q r / R}, q < R
+    if constexpr (R == 1) {
+      y[0] = x[O];
+    } else {
+      float2 e[R / 2], o[R / 2];
+      Dft<R / 2>::template sub<2 * S, O>(x, e);
+      Dft<R / 2>::template sub<2 * S, O + S>(x, o);
+      apply<0>(e, o, y);
+    }
+  }
+  template <int Q>
+  __device__ __forceinline__ static void apply(const float2* e, const float2* o, float2* y) {
+    if constexpr (Q < R / 2) {
+      const float2 t = rot<R, Q>(o[Q]);
+      y[Q] = c_add(e[Q], t);
+      y[Q + R / 2] = c_sub(e[Q], t);
+      apply<Q + 1>(e, o, y);
+    }
+  }
+};
+
+// Shared-memory buffers are padded by one element per 16 (index i at i + i/16),
+// so the strided stores of the first passes fall on distinct banks.
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+// One Stockham pass of radix R over nfft FFTs of L points: X -> Y (Y padded; X
+// padded shared memory, or global memory for the first pass).  twl is the
+// twiddle level of this pass, e^{-j 2 pi i / M} for i < M = Ns R.
+template <int R, bool GLOBAL_IN>
+__device__ __forceinline__ void stockham_pass(const float2* __restrict__ X, float2* __restrict__ Y,
+                                              const float2* __restrict__ twl, int logL, int nfft, int Ns) {
+  const int L = 1 << logL, per = L / R, M = Ns * R;
+  const int total = nfft * per;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int fo = (t / per) * L, j = t % per;
+    const int kp = j & (Ns - 1);
+    float2 v[R], y[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = GLOBAL_IN ? __ldcs(X + fo + j + r * per) : X[pad16(fo + j + r * per)];
+    if (kp != 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], twl[(r * kp) & (M - 1)]);
+    }
+    Dft<R>::template sub<1, 0>(v, y);
+    const int base = fo + (j - kp) * R + kp;
+#pragma unroll
+    for (int q = 0; q < R; ++q) Y[pad16(base + q * Ns)] = y[q];
+  }
+}
+
+// Pass structure of an L = 2^logL point FFT: a first pass of radix 2^f0 (f0 =
+// logL mod 4, or 4), then radix-16 passes.  Pass i >= 1 runs at Ns = 2^(f0 + 4(i-1))
+// with twiddle level M_i = 2^(f0 + 4 i), stored after the levels before it.
+__device__ __forceinline__ int first_log_radix(int logL) { return (logL & 3) ? (logL & 3) : 4; }
+
+// blockIdx.x = k - 1; NT threads (256, or 1024 when 2K + 1 > 9 * 256).
+template <int NT>
+__global__ void __launch_bounds__(NT) fft_y_kernel(FftArgs ar) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  const Plan& pl = ar.pl;
+  const int T = pl.T, K = pl.K, logT = pl.logT;
+  const int logL = ar.logL, L = 1 << logL, P = 1 << ar.logP;
+  const int nfft = max(1, min(P, kFBufPts >> logL));   // FFTs per pass
+  const int bufpts = pad16(nfft * L) + 1;
+  float2* bufA = reinterpret_cast<float2*>(sm);
+  float2* bufB = bufA + bufpts;
+  float2* lev = bufB + bufpts;           // twiddle levels of passes 1, 2, ...
+  const int k = blockIdx.x + 1;
+  const int f0 = first_log_radix(logL);
+
+  // twiddle levels (the prep kernel wrote the table before the H kernel ran)
+  const float* gt = reinterpret_cast<const float*>(ar.ws + pl.off_tab_f32);
+  const uint32_t logQ = (uint32_t)logT - 2u, mask = (uint32_t)T - 1u;
+  {
+    int off = 0;
+    for (int lm = f0 + 4; lm <= logL; lm += 4) {
+      const int M = 1 << lm;
+      for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const uint32_t p = ((uint32_t)i << (logT - lm)) & mask;   // e^{-j 2 pi i / M} = conj W(i T / M)
+        const float2 w = pl.full ? f32_lookup<true>(gt, p, logQ) : f32_lookup<false>(gt, p, logQ);
+        lev[off + i] = make_float2(w.x, -w.y);
+      }
+      off += M;
+    }
+  }
+  griddep_wait();   // launched behind the H kernel (programmatic dependent launch)
+
+  // outputs of this thread: l = -K + threadIdx.x + blockDim.x i
+  float2 acc[kFOwnMax];
+#pragma unroll
+  for (int i = 0; i < kFOwnMax; ++i) acc[i] = make_float2(0.f, 0.f);
+  const float2* src = ar.poly + (size_t)(k - 1) * P * L;
+  for (int a0 = 0; a0 < P; a0 += nfft) {
+    __syncthreads();   // the previous range's sums have read the buffers (and the levels are built)
+    const float2* g = src + (size_t)a0 * L;
+    float2 *X = bufA, *Y = bufB;
+    // first pass straight from global memory
+    if (f0 == 1) stockham_pass<2, true>(g, X, lev, logL, nfft, 1);
+    else if (f0 == 2) stockham_pass<4, true>(g, X, lev, logL, nfft, 1);
+    else if (f0 == 3) stockham_pass<8, true>(g, X, lev, logL, nfft, 1);
+    else stockham_pass<16, true>(g, X, lev, logL, nfft, 1);
+    __syncthreads();
+    int off = 0;
+    for (int lm = f0 + 4; lm <= logL; lm += 4) {
+      stockham_pass<16, false>(X, Y, lev + off, logL, nfft, 1 << (lm - 4));
+      off += 1 << lm;
+      float2* t = X;
+      X = Y;
+      Y = t;
+      __syncthreads();
+    }
+    // G(l) += e^{-j 2 pi l a / T} D_a(l mod L) over the residues of this range
+    // (twiddles read from the correctly rounded table at the exact phase)
+#pragma unroll
+    for (int i = 0; i < kFOwnMax; ++i) {
+      const int l = -K + (int)threadIdx.x + (int)blockDim.x * i;
+      if (l > K) break;
+      const int m = l & (L - 1);
+      for (int q = 0; q < nfft; ++q) {
+        const uint32_t ph = ((uint32_t)l * (uint32_t)(a0 + q)) & mask;
+        const float2 w = pl.full ? f32_lookup<true>(gt, ph, logQ) : f32_lookup<false>(gt, ph, logQ);   // e^{+j ...}
+        const float2 d = X[pad16(q * L + m)];
+        // acc += conj(w) d
+        acc[i].x = fmaf(w.x, d.x, fmaf(w.y, d.y, acc[i].x));
+        acc[i].y = fmaf(w.x, d.y, fmaf(-w.y, d.x, acc[i].y));
+      }
+    }
+  }
+  // F(k, l) = -T^2 / (4 pi^2 k l) G(k, l) for l != 0 (the axis lines come from the
+  // exact integer sums); F(-k, -l) = conj F(k, l)
+  const long long W = 2LL * K + 1;
+#pragma unroll
+  for (int i = 0; i < kFOwnMax; ++i) {
+    const int l = -K + (int)threadIdx.x + (int)blockDim.x * i;
+    if (l > K) break;
+    if (l == 0) continue;
+    const float a = -pl.quad_scale / ((float)k * (float)l);
+    const float2 v = make_float2(a * acc[i].x, a * acc[i].y);
+    ar.F[(K + k) * W + (K + l)] = v;
+    ar.F[(K - k) * W + (K - l)] = make_float2(v.x, -v.y);
+  }
+}
+
+// The axis lines and the centre of the block from the exact integer sums; the
+// last kernel of the call, so it also writes the table tag.
+__global__ void axis_out_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, long long* __restrict__ area_out) {
+  griddep_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *reinterpret_cast<unsigned long long*>(ws + kTagOffset) = pl.tag;
+  if (i > 2 * pl.K) return;
+  const long long* acc = reinterpret_cast<const long long*>(ws + pl.off_axis);
+  axis_entry(pl, acc, F, area_out, i);
+}
+
+}  // namespace
+
+// Shared memory of the FFT kernel for L points: two padded buffers and the
+// twiddle levels (at most L (1 + 1/16 + 1/256 + ...) entries).
+size_t fft_y_smem(int logL) {
+  const size_t L = (size_t)1 << logL;
+  const size_t pts = std::max<size_t>(L, kFBufPts);
+  const size_t buf = pts + (pts >> 4) + 1;
+  return (2 * buf + L + L / 15 + 16) * 8;
+}
+
+// FFT length for a period T and cut-off K: a power of two >= 2K (no two wanted
+// l share a residue but +-K), >= T / 16 (so P <= 16 and the H kernel writes
+// whole 32-byte sectors), at most T.
+int fft_log_len(int T, int K) {
+  int lg = 1;
+  while ((1 << lg) < 2 * K) ++lg;
+  int logT = 0;
+  while ((1 << logT) < T) ++logT;
+  lg = std::max(lg, logT - 4);
+  return std::min(lg, logT);
+}
+
+cudaError_t launch_fft_y(const Plan& pl, void* ws, float* F, cudaStream_t st) {
+  const int logL = pl.fft_logL;
+  FftArgs ar;
+  ar.pl = pl;
+  ar.ws = static_cast<const uint8_t*>(ws);
+  ar.poly = reinterpret_cast<const float2*>(static_cast<const uint8_t*>(ws) + pl.off_poly);
+  ar.logL = logL;
+  ar.logP = pl.logT - logL;
+  ar.F = reinterpret_cast<float2*>(F);
+  const bool small = 2 * pl.K + 1 <= kFOwnMax * 256;
+  auto kern = small ? fft_y_kernel<256> : fft_y_kernel<1024>;
+  const size_t smem = fft_y_smem(logL);
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), smem);
+  if (e != cudaSuccess) return e;
+  return launch_after(kern, dim3(pl.K), dim3(small ? 256 : 1024), smem, st, ar);
+}
+
+cudaError_t launch_axis_out(const Plan& pl, void* ws, float* F, int64_t* area, cudaStream_t st) {
+  ensure_smem(reinterpret_cast<const void*>(axis_out_kernel), 0);
+  return launch_after(axis_out_kernel, dim3((2 * pl.K + 1 + 255) / 256), dim3(256), 0, st, pl,
+                      static_cast<uint8_t*>(ws), reinterpret_cast<float2*>(F), reinterpret_cast<long long*>(area));
+}
+
+}  // namespace fcfs

@@ -147,23 +147,92 @@ __global__ void group_scatter_kernel(const int32_t* __restrict__ c0, const int32
   }
 }
 
-// ---------------------------------------------------------------------------
-// Stage 2: H
-// ---------------------------------------------------------------------------
-constexpr int kHY = 64;          // y values per chunk (one contraction chunk)
-constexpr int kHF = 128;         // frequencies per pass (256 rows of H)
-constexpr int kHGroups = 4;      // thread groups; group q takes the chunk's y octets q, q + 4
-constexpr int kHThreads = kHF * kHGroups;
-constexpr int kHCache = 4096;    // corners of a chunk staged in shared memory
-
-size_t hyb_h_smem(int T) {
-  return align_up(axis_levels_ints(T) * 4, 16) + (size_t)kHCache * 16 + (kHY + 1) * 4 + 16;
+// FP16 split of two values: hi = rn(v), lo = rn(v - hi)
+__device__ __forceinline__ void split2h(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(v0, v1);
+  const float2 hf = __half22float2(h);
+  memcpy(&hi, &h, 4);
+  const __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+  memcpy(&lo, &l, 4);
 }
 
-// A staged corner: the phase k x mod T of every frequency k is read at index
-// k u (mod 4 Q) of the decimated level that starts at lbase (quarter period
-// Q = 2^lq; u odd unless x mod T is a multiple of T/4), which keeps the 32
-// consecutive frequencies of a warp on distinct banks; sflip = 1 for s = -1.
+// ---------------------------------------------------------------------------
+// Stage 2: H[k, y] = sum over the corners of row y of s_v exp(+j 2 pi k x_v / T)
+// ---------------------------------------------------------------------------
+// Fast path (an item's corners fit in shared memory): the corners of the item's
+// rows are sorted by (row, x, sign) and consecutive corners of a row are paired
+// (for a set of disjoint polygons these are exactly the row's horizontal edges).
+// A pair a < b contributes
+//     s_a e^{j k x_a} (1 - e^{j k w})   (opposite signs, w = x_b - x_a),
+//     s_a e^{j k x_a} (2 - (1 - e^{j k w}))   (equal signs), or s_a e^{j k x_a} (alone),
+// so an edge's two corners cancel in the factor D_k = 1 - e^{j k w} before any
+// rounding, and D_k is carried with a relative error of a few ulp however small it
+// is (versine tables; D_{k+1} = D_k + D_1 - D_k D_1 stays free of cancellation).
+// A lane owns the 8 frequencies k0 + 32 i (the 32 lanes of a warp cover 256
+// consecutive frequencies, so their table reads fall on distinct banks): the
+// anchors at k0 come from two-level tables at the exact integer phase, the
+// next 7 by angle addition (A_{k+32} = A_k e^{j 32 x_a}) and the D recurrence
+// D_{k+32} = D_k + D_32 - D_k D_32.  Rows are summed
+// in FP32 in the sorted order, so repeated calls are bit-identical.  One pass
+// covers 256 frequencies of the item's 64 rows in a shared-memory tile, written
+// out coalesced in the output format:
+//   kHRowsFp16: FP16 hi/lo rows 2(k-1) (Re) and 2(k-1)+1 (Im), columns y (the
+//               tensor-core contraction over y);
+//   kHPolyF32:  conj(H) as complex FP32 in polyphase order [k-1][a][b],
+//               y = a + P b (the pruned FFT along y), row T folded onto row 0
+//               (e^{-j 2 pi l T / T} = 1).
+// Items with more corners than the sort holds fall back to exact 64-bit
+// fixed-point sums from the integer quarter-wave table (order-free, exact up to
+// the table's rounding), written in the same formats.
+constexpr int kHY = 64;                 // rows per item
+constexpr int kHThreads = 512;          // 16 warps
+constexpr int kHWarps = kHThreads / 32;
+constexpr int kHPassF = 256;            // frequencies per pass (a run of 8 per lane)
+constexpr int kHCap = 4096;             // corners sorted in shared memory (fast path)
+constexpr int kHLd = kHPassF + 2;       // tile row stride (float2; rows stay 16-byte aligned)
+constexpr int kHTabMax = 256;           // two-level table entries per level (T <= 2^16)
+constexpr int kHCacheFB = 2048;         // fallback: corners staged in shared memory
+constexpr int kHRowsFp16 = 0, kHPolyF32 = 1;
+
+constexpr size_t kHTileBytes = (size_t)kHY * kHLd * 8;
+constexpr size_t kHPairBytes = (size_t)kHCap * 8;
+constexpr size_t kHTabBytes = (size_t)4 * kHTabMax * 8;
+constexpr size_t kHMainBytes = kHTileBytes + kHPairBytes;   // fast path tile + pairs | fallback levels + cache
+
+size_t hyb_h_smem(int T) {
+  (void)T;
+  return kHMainBytes + kHTabBytes + (size_t)2 * (kHY + 2) * 4 + 64;
+}
+
+// Two-level tables of e^{j 2 pi p / T} (W) and of the versine D(p) = 1 - e^{j 2 pi p / T}:
+// p = u 2^f + v; W(p) = Wc[u] Wf[v]; for D the phase is taken signed, p = i 2^f + b
+// with |b| <= 2^(f-1) <= |i 2^f| / 2, D(p) = Dc[i] + Wc[i] Df[b] (no cancellation).
+struct HTabs {
+  const float2 *Wc, *Wf, *Dc, *Df;
+  uint32_t f, fm, ncm, T, half;
+};
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.y, b.x, a.x * b.y));
+}
+__device__ __forceinline__ float2 tab_w(const HTabs& t, uint32_t p) { return cmul(t.Wc[p >> t.f], t.Wf[p & t.fm]); }
+__device__ __forceinline__ float2 tab_d(const HTabs& t, uint32_t p) {
+  const int ps = (int)p - (p >= t.half ? (int)t.T : 0);
+  const int i = (ps + (int)(t.fm + 1) / 2) >> t.f;   // nearest coarse point (floor shift)
+  const int b = ps - (i << t.f);
+  const uint32_t iu = (uint32_t)i & t.ncm, bu = (uint32_t)b & t.fm;
+  const float2 c = t.Dc[iu], w = t.Wc[iu], d = t.Df[bu];
+  return make_float2(c.x + fmaf(w.x, d.x, -(w.y * d.y)), c.y + fmaf(w.y, d.x, w.x * d.y));
+}
+// 1 - e^{j theta} from cos and sin: 1 - cos as sin^2 / (1 + cos) where cos >= 0
+__device__ __forceinline__ float2 versine(float2 cs) {
+  const float re = cs.x >= 0.f ? (cs.y * cs.y) / (1.f + cs.x) : 1.f - cs.x;
+  return make_float2(re, -cs.y);
+}
+
+// A staged corner of the fallback: the phase k x mod T of every frequency k is
+// read at index k u (mod 4 Q) of the decimated level that starts at lbase
+// (quarter period Q = 2^lq; u odd unless x mod T is a multiple of T/4), which
+// keeps the 32 consecutive frequencies of a warp on distinct banks; sflip = 1 for s = -1.
 __device__ __forceinline__ int4 stage_corner(uint32_t xm, int sgn, int logQ) {
   int e = xm ? __ffs(xm) - 1 : 0;
   uint32_t u = xm >> e;
@@ -175,38 +244,325 @@ __device__ __forceinline__ int4 stage_corner(uint32_t xm, int sgn, int logQ) {
   return make_int4((int)u, level_offset(e, logQ), lq | ((sgn < 0 ? 1 : 0) << 8), 1 << lq);
 }
 
-// Items (clip, 64-y chunk) are taken from a work counter (clips differ in
-// size by orders of magnitude, so a static split leaves CTAs idle); per item
-// the chunk's corners are staged once, then for every pass of 128 frequencies
-// thread (group q, frequency k) sums s_v (cos, sin)(2 pi k x_v / T) over each
-// group of its y octets, exactly.
-__global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* ws) {
-  extern __shared__ __align__(16) uint8_t sm[];
-  __shared__ int s_item;
+struct HOut {
+  __half* hi;       // kHRowsFp16: [clips][2K][ny_pad] hi, then lo
+  __half* lo;
+  float2* poly;     // kHPolyF32: [K][P][L]
+  int logP, L;
+};
+
+// Item rows: kHRowsFp16 covers rows y0 .. y0 + 63 of [0, T] (row T its own);
+// kHPolyF32 rows y0 .. of [0, T), the corners of row T staged into row 0.
+template <int FMT>
+__device__ __forceinline__ int item_rows(int y0, int T) {
+  return FMT == kHRowsFp16 ? min(kHY, T + 1 - y0) : min(kHY, T - y0);
+}
+
+// Fallback for an item with more than kHCap corners: exact fixed-point sums,
+// thread (group q of 4, frequency t of 128) over its y octets q, q + 4.
+template <int FMT>
+__device__ void h_item_exact(const Plan& pl, const Groups& g, int clip, int y0, int* lv, int4* vc, int* soff,
+                             const HOut& out) {
   const int T = pl.T, K = pl.K, logQ = pl.logT - 2;
-  int* lv = reinterpret_cast<int*>(sm);
-  int4* vc = reinterpret_cast<int4*>(sm + align_up(axis_levels_ints(T) * 4, 16));
-  int* soff = reinterpret_cast<int*>(vc + kHCache);
-  const int nclips = pl.batch ? pl.n_clips : 1;
-  __half* Hhi0 = reinterpret_cast<__half*>(ws + pl.off_h);
-  __half* Hlo0 = Hhi0 + (size_t)nclips * pl.M2 * pl.ny_pad;
   const uint32_t mask = (uint32_t)T - 1u;
+  const float inv_q = ldexpf(1.f, -pl.fixq);
+  const int small_group = (1 << (31 - pl.fixq)) - 1;   // |sum| < 2^31 in int32
+  const int* perm = g.perm;
+  const int nrows = item_rows<FMT>(y0, T);
+  const int a = g.start[min(y0, T + 1)], b = g.start[min(y0 + kHY, T + 1)];
+  // row T folded onto row 0 (polyphase output, the item holding row 0)
+  const bool fold = FMT == kHPolyF32 && y0 == 0;
+  const int fa = fold ? g.start[T] : 0, fb = fold ? g.start[T + 1] : 0;
+  const bool cached = (b - a) + (fb - fa) <= kHCacheFB;
+  for (int i = threadIdx.x; i <= kHY; i += blockDim.x) soff[i] = g.start[min(y0 + i, T + 1)] - a;
+  if (threadIdx.x == 0) soff[kHY + 1] = (b - a) + (fb - fa);
+  if (cached)
+    for (int i = threadIdx.x; i < (b - a) + (fb - fa); i += blockDim.x) {
+      const int v = i < b - a ? perm[a + i] : perm[fa + i - (b - a)];
+      vc[i] = stage_corner((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
+    }
+  __syncthreads();
+  const int q = threadIdx.x / 128, t = threadIdx.x % 128;
+  for (int pass = 0; pass < (K + 127) / 128; ++pass) {
+    const int k = pass * 128 + 1 + t;
+    if (k > K) continue;
+    for (int oc = q; oc < kHY / 8; oc += 4) {
+      float fcv[8], fsv[8];
+#pragma unroll
+      for (int yy = 0; yy < 8; ++yy) {
+        const int y = oc * 8 + yy;
+        auto term = [&](int i, auto& ac_, auto& as_) {
+          int4 cn;
+          if (cached) {
+            cn = vc[i];
+          } else {
+            const int v = i < b - a ? perm[a + i] : perm[fa + i - (b - a)];
+            cn = stage_corner((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
+          }
+          const int lq = cn.z & 0xFF, Q = cn.w;
+          const uint32_t sf = (uint32_t)cn.z >> 8;
+          const uint32_t p = ((uint32_t)k * (uint32_t)cn.x) & (4u * (uint32_t)Q - 1u);
+          const uint32_t qd = p >> lq, r = p & (uint32_t)(Q - 1);
+          const bool odd = qd & 1u;
+          const int* L = lv + cn.y;
+          const int c = L[odd ? Q - r : r], sn = L[odd ? r : Q - r];
+          // cos < 0 in quadrants 1, 2; sin < 0 in quadrants 2, 3; s = -1 flips both
+          ac_ += ((((qd + 1u) >> 1) & 1u) ^ sf) ? -c : c;
+          as_ += ((qd >> 1) ^ sf) ? -sn : sn;
+        };
+        // the corner ranges of row y (and of row T when it is folded onto row 0)
+        int i0 = soff[y], i1 = soff[y + 1], j0 = 0, j1 = 0;
+        if (y >= nrows) i1 = i0;
+        if (fold && y == 0) {
+          j0 = b - a;
+          j1 = soff[kHY + 1];
+        }
+        long long ac = 0, as = 0;
+        if ((i1 - i0) + (j1 - j0) <= small_group) {   // warp-uniform
+          int ac32 = 0, as32 = 0;
+          for (int i = i0; i < i1; ++i) term(i, ac32, as32);
+          for (int i = j0; i < j1; ++i) term(i, ac32, as32);
+          ac = ac32;
+          as = as32;
+        } else {
+          for (int i = i0; i < i1; ++i) term(i, ac, as);
+          for (int i = j0; i < j1; ++i) term(i, ac, as);
+        }
+        const float sc = FMT == kHRowsFp16 ? ldexpf(inv_q, -(int)g.ey[y0 + y]) : inv_q;
+        fcv[yy] = __ll2float_rn(ac) * sc;
+        fsv[yy] = __ll2float_rn(as) * sc;
+      }
+      if (FMT == kHRowsFp16) {
+        uint32_t hc[4], hs[4], lc[4], ls[4];
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          split2h(fcv[2 * qq], fcv[2 * qq + 1], hc[qq], lc[qq]);
+          split2h(fsv[2 * qq], fsv[2 * qq + 1], hs[qq], ls[qq]);
+        }
+        const size_t rc = ((size_t)clip * pl.M2 + 2 * (k - 1)) * pl.ny_pad + y0 + 8 * oc, rs = rc + pl.ny_pad;
+        *reinterpret_cast<uint4*>(out.hi + rc) = make_uint4(hc[0], hc[1], hc[2], hc[3]);
+        *reinterpret_cast<uint4*>(out.hi + rs) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
+        *reinterpret_cast<uint4*>(out.lo + rc) = make_uint4(lc[0], lc[1], lc[2], lc[3]);
+        *reinterpret_cast<uint4*>(out.lo + rs) = make_uint4(ls[0], ls[1], ls[2], ls[3]);
+      } else {
+        const int P = 1 << out.logP;
+        for (int yy = 0; yy < 8; ++yy) {
+          const int y = y0 + oc * 8 + yy;
+          if (oc * 8 + yy >= nrows) break;
+          out.poly[((size_t)(k - 1) * P + (y & (P - 1))) * out.L + (y >> out.logP)] = make_float2(fcv[yy], -fsv[yy]);
+        }
+      }
+    }
+  }
+}
+
+// Fast path of one item (see above).  The tile holds 64 rows x 256 frequencies.
+template <int FMT>
+__device__ void h_item_pairs(const Plan& pl, const Groups& g, int clip, int y0, int ncorner, float2* tile,
+                             uint2* pairs, int* rowc, int* rowp, int* s_row, const HTabs& tb, const HOut& out) {
+  const int T = pl.T, K = pl.K;
+  const uint32_t mask = (uint32_t)T - 1u;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int nrows = item_rows<FMT>(y0, T);
+  const int a = g.start[min(y0, T + 1)], b = g.start[min(y0 + kHY, T + 1)];
+  const bool fold = FMT == kHPolyF32 && y0 == 0;
+  const int fa = fold ? g.start[T] : 0;
+  // 1. sort keys (row << 17 | x << 1 | sign), padded to a power of two (in the tile)
+  uint32_t* keys = reinterpret_cast<uint32_t*>(tile);
+  int npad = 1;
+  while (npad < ncorner) npad <<= 1;
+  for (int i = tid; i < npad; i += kHThreads) {
+    uint32_t key = 0xFFFFFFFFu;
+    if (i < ncorner) {
+      const int v = i < b - a ? g.perm[a + i] : g.perm[fa + i - (b - a)];
+      const int yv = __ldg(pl.vy + v);
+      const int yl = (FMT == kHPolyF32 && yv == T) ? 0 : yv - y0;
+      const uint32_t xm = (uint32_t)__ldg(pl.vx + v) & mask;
+      key = ((uint32_t)yl << 17) | (xm << 1) | (__ldg(pl.vsg + v) < 0 ? 1u : 0u);
+    }
+    keys[i] = key;
+  }
+  __syncthreads();
+  for (int kk = 2; kk <= npad; kk <<= 1)
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < npad; i += kHThreads) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const uint32_t u = keys[i], w = keys[ixj];
+          if ((u > w) == ((i & kk) == 0)) {
+            keys[i] = w;
+            keys[ixj] = u;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  // 2. row starts (first sorted key of each row) and pair starts
+  for (int r = tid; r <= kHY; r += kHThreads) {
+    int lo = 0, hi = ncorner;   // first index whose row is >= r
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((int)(keys[mid] >> 17) < r) lo = mid + 1; else hi = mid;
+    }
+    rowc[r] = lo;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int r = 0; r < kHY; ++r) {
+      rowp[r] = acc;
+      acc += (rowc[r + 1] - rowc[r] + 1) >> 1;
+    }
+    rowp[kHY] = acc;
+  }
+  __syncthreads();
+  // 3. pairs: {x_a | kind << 20 | sign_a << 22, w}; kind 0 opposite signs, 1 equal, 2 alone
+  for (int i = tid; i < ncorner; i += kHThreads) {
+    const uint32_t ka = keys[i];
+    const int r = (int)(ka >> 17), pos = i - rowc[r];
+    if (pos & 1) continue;
+    const uint32_t xa = (ka >> 1) & 0xFFFFu, sa = ka & 1u;
+    uint32_t kind = 2u, w = 0u;
+    if (i + 1 < rowc[r + 1]) {
+      const uint32_t kb2 = keys[i + 1];
+      w = ((kb2 >> 1) & 0xFFFFu) - xa;
+      kind = (kb2 & 1u) == sa ? 1u : 0u;
+    }
+    pairs[rowp[r] + (pos >> 1)] = make_uint2(xa | (kind << 20) | (sa << 22), w);
+  }
+  __syncthreads();   // the keys (in the tile) are dead from here on
+
+  // 4. passes of 256 frequencies
+  const int npass = (K + kHPassF - 1) / kHPassF;
+  const int P = FMT == kHPolyF32 ? 1 << out.logP : 1;
+  for (int pass = 0; pass < npass; ++pass) {
+    const int kb = pass * kHPassF + 1;
+    if (tid == 0) *s_row = 0;
+    __syncthreads();
+    const uint32_t k0 = (uint32_t)(kb + lane);
+    const bool live = (int)k0 <= K;
+    for (;;) {
+      int r = 0;
+      if (lane == 0) r = atomicAdd(s_row, 1);
+      r = __shfl_sync(0xffffffffu, r, 0);
+      if (r >= kHY) break;
+      float2 acc[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
+      if (live && r < nrows) {
+        for (int p = rowp[r]; p < rowp[r + 1]; ++p) {
+          const uint2 pr = pairs[p];
+          const uint32_t xa = pr.x & 0xFFFFFu, kind = (pr.x >> 20) & 3u, w = pr.y;
+          const float2 S = tab_w(tb, (32u * xa) & mask);
+          float2 A = tab_w(tb, (k0 * xa) & mask);
+          if (pr.x >> 22) A = make_float2(-A.x, -A.y);
+          if (kind == 2u) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              acc[j].x += A.x;
+              acc[j].y += A.y;
+              A = cmul(A, S);
+            }
+          } else {
+            const float2 D1 = tab_d(tb, (32u * w) & mask);
+            float2 D = tab_d(tb, (k0 * w) & mask);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float2 E = kind ? make_float2(2.f - D.x, -D.y) : D;
+              acc[j].x = fmaf(A.x, E.x, fmaf(-A.y, E.y, acc[j].x));
+              acc[j].y = fmaf(A.x, E.y, fmaf(A.y, E.x, acc[j].y));
+              A = cmul(A, S);
+              // D_{k+32} = D_k + D_32 - D_k D_32
+              const float dr = fmaf(D.y, D1.y, fmaf(-D.x, D1.x, D.x + D1.x));
+              const float di = fmaf(-D.x, D1.y, fmaf(-D.y, D1.x, D.y + D1.y));
+              D = make_float2(dr, di);
+            }
+          }
+        }
+      }
+      float2* row = tile + (size_t)r * kHLd + lane;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) row[32 * j] = acc[j];
+    }
+    __syncthreads();
+    // write the tile out
+    if (FMT == kHRowsFp16) {
+      for (int e = tid; e < kHPassF * (kHY / 8); e += kHThreads) {
+        const int kl = e % kHPassF, oc = e / kHPassF, k = kb + kl;
+        if (k > K) continue;
+        float fcv[8], fsv[8];
+#pragma unroll
+        for (int yy = 0; yy < 8; ++yy) {
+          const float2 v = tile[(size_t)(oc * 8 + yy) * kHLd + kl];
+          fcv[yy] = v.x;
+          fsv[yy] = v.y;
+        }
+        uint32_t hc[4], hs[4], lc[4], ls[4];
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          split2h(fcv[2 * qq], fcv[2 * qq + 1], hc[qq], lc[qq]);
+          split2h(fsv[2 * qq], fsv[2 * qq + 1], hs[qq], ls[qq]);
+        }
+        const size_t rc = ((size_t)clip * pl.M2 + 2 * (k - 1)) * pl.ny_pad + y0 + 8 * oc, rs = rc + pl.ny_pad;
+        *reinterpret_cast<uint4*>(out.hi + rc) = make_uint4(hc[0], hc[1], hc[2], hc[3]);
+        *reinterpret_cast<uint4*>(out.hi + rs) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
+        *reinterpret_cast<uint4*>(out.lo + rc) = make_uint4(lc[0], lc[1], lc[2], lc[3]);
+        *reinterpret_cast<uint4*>(out.lo + rs) = make_uint4(ls[0], ls[1], ls[2], ls[3]);
+      }
+    } else {
+      const int nb = nrows >> out.logP;   // b values of each residue a in this item
+      const size_t b0 = (size_t)(y0 >> out.logP);
+      for (int e = tid; e < kHPassF * P; e += kHThreads) {
+        const int kl = e % kHPassF, ar = e / kHPassF, k = kb + kl;
+        if (k > K) continue;
+        float2* dst = out.poly + ((size_t)(k - 1) * P + ar) * out.L + b0;
+        for (int bb = 0; bb < nb; ++bb) {
+          const float2 v = tile[(size_t)(ar + bb * P) * kHLd + kl];
+          dst[bb] = make_float2(v.x, -v.y);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Items (clip, 64-row chunk) are taken from a work counter (clips differ in
+// size by orders of magnitude, so a static split leaves CTAs idle).
+template <int FMT>
+__global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* ws, HOut out) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ int s_item, s_row;
+  const int T = pl.T, logT = pl.logT;
+  uint8_t* main = sm;
+  float2* tabs = reinterpret_cast<float2*>(sm + kHMainBytes);
+  int* rowc = reinterpret_cast<int*>(sm + kHMainBytes + kHTabBytes);
+  int* rowp = rowc + kHY + 2;
+  const int nclips = pl.batch ? pl.n_clips : 1;
   unsigned* counter = reinterpret_cast<unsigned*>(ws + kSyncOffset) + 2;   // zeroed by the prep kernel
 
-  // level 0 = the fixed-point quarter-wave table, then the decimated levels
-  const int* tq = reinterpret_cast<const int*>(ws + pl.off_tab_fix);
-  for (int i = threadIdx.x; i <= T / 4; i += blockDim.x) lv[i] = tq[i];
-  __syncthreads();
-  axis_build_levels(lv, T, pl.logT);
-
-  const int q = threadIdx.x / kHF, t = threadIdx.x % kHF;
-  const int npass = (K + kHF - 1) / kHF, nchunk = pl.ny_pad / kHY;
+  // two-level W and D tables from the FP32 sincos table
+  const uint32_t f = ((uint32_t)logT + 1u) / 2u, nf = 1u << f, nc = (uint32_t)T >> f;
+  float2 *Wc = tabs, *Wf = tabs + kHTabMax, *Dc = tabs + 2 * kHTabMax, *Df = tabs + 3 * kHTabMax;
+  {
+    const float* gt = reinterpret_cast<const float*>(ws + pl.off_tab_f32);
+    const uint32_t logQ = (uint32_t)logT - 2u;
+    for (uint32_t i = threadIdx.x; i < nc + nf; i += blockDim.x) {
+      const bool coarse = i < nc;
+      const uint32_t u = coarse ? i : i - nc;
+      const uint32_t pw = coarse ? u << f : u;                               // W phase
+      const uint32_t pd = coarse ? u << f : (u < nf / 2 ? u : (uint32_t)T - (nf - u));   // D phase (signed fine)
+      const float2 w = pl.full ? f32_lookup<true>(gt, pw, logQ) : f32_lookup<false>(gt, pw, logQ);
+      const float2 wd = pl.full ? f32_lookup<true>(gt, pd, logQ) : f32_lookup<false>(gt, pd, logQ);
+      (coarse ? Wc : Wf)[u] = w;
+      (coarse ? Dc : Df)[u] = versine(wd);
+    }
+  }
+  const HTabs tb{Wc, Wf, Dc, Df, f, nf - 1u, nc - 1u, (uint32_t)T, (uint32_t)T / 2u};
+  const int nchunk = FMT == kHRowsFp16 ? pl.ny_pad / kHY : max(1, T / kHY);
   const long long nitems = (long long)nclips * nchunk;
-  const float inv_q = ldexpf(1.f, -pl.fixq);
-  // groups of up to this many corners sum in int32 (each term is at most 2^fixq)
-  const int small_group = (1 << (31 - pl.fixq)) - 1;
+  bool levels = false;   // the fallback's fixed-point levels are in shared memory
   for (;;) {
-    __syncthreads();   // the previous item's readers are done (and the levels are built)
+    __syncthreads();   // the previous item's readers are done (and the tables are built)
     if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
     __syncthreads();
     const int cu = s_item;   // (clip, chunk)
@@ -215,78 +571,27 @@ __global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* w
     const int y0 = chunk * kHY;
     const Groups g = pl.batch ? groups_clip(ws + pl.off_ycnt, T, pl.ny_pad, nclips, clip, pl.V)
                               : groups_at(ws + pl.off_ycnt, T, pl.ny_pad);
-    const int* perm = g.perm;
-    __half* Hhi = Hhi0 + (size_t)clip * pl.M2 * pl.ny_pad;
-    __half* Hlo = Hlo0 + (size_t)clip * pl.M2 * pl.ny_pad;
-    const int a = g.start[min(y0, T + 1)];
-    const int b = g.start[min(y0 + kHY, T + 1)];
-    const bool cached = b - a <= kHCache;
-    for (int i = threadIdx.x; i <= kHY; i += blockDim.x) soff[i] = g.start[min(y0 + i, T + 1)] - a;
-    if (cached)
-      for (int i = threadIdx.x; i < b - a; i += blockDim.x) {
-        const int v = perm[a + i];
-        vc[i] = stage_corner((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
+    const int a = g.start[min(y0, T + 1)], b = g.start[min(y0 + kHY, T + 1)];
+    int n = b - a;
+    if (FMT == kHPolyF32 && y0 == 0) n += g.start[T + 1] - g.start[T];
+    if (FMT == kHPolyF32 && T < kHY) n = g.start[T + 1] - g.start[0];   // one item: rows 0..T-1 and T
+    if (n <= kHCap) {
+      levels = false;   // the tile overwrites them
+      h_item_pairs<FMT>(pl, g, clip, y0, n, reinterpret_cast<float2*>(main),
+                        reinterpret_cast<uint2*>(main + kHTileBytes), rowc, rowp, &s_row, tb, out);
+    } else {
+      int* lv = reinterpret_cast<int*>(main);
+      int4* vc = reinterpret_cast<int4*>(main + align_up(axis_levels_ints(T) * 4, 16));
+      if (!levels) {
+        // level 0 = the fixed-point quarter-wave table, then the decimated levels
+        const int* tq = reinterpret_cast<const int*>(ws + pl.off_tab_fix);
+        for (int i = threadIdx.x; i <= T / 4; i += blockDim.x) lv[i] = tq[i];
+        __syncthreads();
+        axis_build_levels(lv, T, logT);
+        __syncthreads();
+        levels = true;
       }
-    __syncthreads();
-    for (int pass = 0; pass < npass; ++pass) {
-      const int k = pass * kHF + 1 + t;
-      if (k > K) continue;
-      for (int oc = q; oc < kHY / 8; oc += kHGroups) {
-        uint32_t hc[4], hs[4], lc[4], ls[4];
-  #pragma unroll
-        for (int yy = 0; yy < 8; ++yy) {
-          const int y = oc * 8 + yy;
-          // one term s_v (cos, sin)(2 pi k x_v / T) of the fixed-point table
-          auto term = [&](int i, auto& ac_, auto& as_) {
-            int4 cn;
-            if (cached) {
-              cn = vc[i];
-            } else {
-              const int v = perm[a + i];
-              cn = stage_corner((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
-            }
-            const int lq = cn.z & 0xFF, Q = cn.w;
-            const uint32_t sf = (uint32_t)cn.z >> 8;
-            const uint32_t p = ((uint32_t)k * (uint32_t)cn.x) & (4u * (uint32_t)Q - 1u);
-            const uint32_t qd = p >> lq, r = p & (uint32_t)(Q - 1);
-            const bool odd = qd & 1u;
-            const int* L = lv + cn.y;
-            const int c = L[odd ? Q - r : r], sn = L[odd ? r : Q - r];
-            // cos < 0 in quadrants 1, 2; sin < 0 in quadrants 2, 3; s = -1 flips both
-            ac_ += ((((qd + 1u) >> 1) & 1u) ^ sf) ? -c : c;
-            as_ += ((qd >> 1) ^ sf) ? -sn : sn;
-          };
-          long long ac = 0, as = 0;
-          if (soff[y + 1] - soff[y] <= small_group) {   // warp-uniform: |sum| < 2^31 in int32
-            int ac32 = 0, as32 = 0;
-            for (int i = soff[y]; i < soff[y + 1]; ++i) term(i, ac32, as32);
-            ac = ac32;
-            as = as32;
-          } else {
-            for (int i = soff[y]; i < soff[y + 1]; ++i) term(i, ac, as);
-          }
-          const float sc = ldexpf(inv_q, -(int)g.ey[y0 + y]);
-          const float fc = __ll2float_rn(ac) * sc, fs = __ll2float_rn(as) * sc;
-          const __half c_hi = __float2half_rn(fc), s_hi = __float2half_rn(fs);
-          const __half c_lo = __float2half_rn(fc - __half2float(c_hi)), s_lo = __float2half_rn(fs - __half2float(s_hi));
-          uint16_t u;
-          const int sh = 16 * (yy & 1);
-          memcpy(&u, &c_hi, 2);
-          hc[yy >> 1] = (yy & 1 ? hc[yy >> 1] : 0u) | ((uint32_t)u << sh);
-          memcpy(&u, &s_hi, 2);
-          hs[yy >> 1] = (yy & 1 ? hs[yy >> 1] : 0u) | ((uint32_t)u << sh);
-          memcpy(&u, &c_lo, 2);
-          lc[yy >> 1] = (yy & 1 ? lc[yy >> 1] : 0u) | ((uint32_t)u << sh);
-          memcpy(&u, &s_lo, 2);
-          ls[yy >> 1] = (yy & 1 ? ls[yy >> 1] : 0u) | ((uint32_t)u << sh);
-        }
-        // rows 2(k-1) (cos) and 2(k-1)+1 (sin), columns y0 + 8 oc .. + 8
-        const size_t rc = (size_t)(2 * (k - 1)) * pl.ny_pad + y0 + 8 * oc, rs = rc + pl.ny_pad;
-        *reinterpret_cast<uint4*>(Hhi + rc) = make_uint4(hc[0], hc[1], hc[2], hc[3]);
-        *reinterpret_cast<uint4*>(Hhi + rs) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
-        *reinterpret_cast<uint4*>(Hlo + rc) = make_uint4(lc[0], lc[1], lc[2], lc[3]);
-        *reinterpret_cast<uint4*>(Hlo + rs) = make_uint4(ls[0], ls[1], ls[2], ls[3]);
-      }
+      h_item_exact<FMT>(pl, g, clip, y0, lv, vc, rowc, out);
     }
   }
 }
@@ -309,13 +614,6 @@ __device__ __forceinline__ void st_shared_v4h(uint32_t addr, uint32_t a, uint32_
 }
 __device__ __forceinline__ void ld_shared_v4h(uint32_t addr, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
   asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(a), "=r"(b), "=r"(c), "=r"(d) : "r"(addr) : "memory");
-}
-__device__ __forceinline__ void split2h(float v0, float v1, uint32_t& hi, uint32_t& lo) {
-  const __half2 h = __floats2half2_rn(v0, v1);
-  const float2 hf = __half22float2(h);
-  memcpy(&hi, &h, 4);
-  const __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
-  memcpy(&lo, &l, 4);
 }
 __device__ __forceinline__ void tma_load_2dh(void* dst, const CUtensorMap* map, int32_t c0, int32_t c1, uint64_t* bar) {
   asm volatile(
@@ -604,12 +902,8 @@ cudaError_t launch_grouping(const int32_t* c0, const int32_t* c1, int64_t V, int
                       base);
 }
 
-cudaError_t launch_hybrid(const Plan& pl, void* ws_, cudaStream_t st) {
-  uint8_t* ws = static_cast<uint8_t*>(ws_);
-  if (!pl.hyb || !pl.pair || pl.logT > 16) return cudaErrorInvalidValue;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+// Group the corners of a single clip or of every clip of a batch by y.
+static cudaError_t group_rows(const Plan& pl, uint8_t* ws, cudaStream_t st) {
   cudaError_t e;
   const int nclips = pl.batch ? pl.n_clips : 1;
   if (pl.batch) {
@@ -625,16 +919,68 @@ cudaError_t launch_hybrid(const Plan& pl, void* ws_, cudaStream_t st) {
     batch_group_scatter_kernel<<<dim3(bx, nclips), 256, 0, st>>>(pl.vy, pl.offsets, nclips, pl.T, pl.ny_pad, pl.V,
                                                                 ws + pl.off_ycnt);
     count_launch(3);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  } else if ((e = launch_grouping(pl.vy, nullptr, pl.V, pl.T, pl.ny_pad, ws + pl.off_ycnt, st)) != cudaSuccess) {
-    return e;
+    return cudaGetLastError();
+  }
+  return launch_grouping(pl.vy, nullptr, pl.V, pl.T, pl.ny_pad, ws + pl.off_ycnt, st);
+}
+
+// The H kernel in output format fmt (kHRowsFp16 or kHPolyF32).
+static cudaError_t launch_h(const Plan& pl, uint8_t* ws, int fmt, cudaStream_t st) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int nclips = pl.batch ? pl.n_clips : 1;
+  HOut out{};
+  long long items;
+  if (fmt == kHRowsFp16) {
+    out.hi = reinterpret_cast<__half*>(ws + pl.off_h);
+    out.lo = out.hi + (size_t)nclips * pl.M2 * pl.ny_pad;
+    items = (long long)nclips * (pl.ny_pad / kHY);
+  } else {
+    out.poly = reinterpret_cast<float2*>(ws + pl.off_poly);
+    out.logP = pl.logT - pl.fft_logL;
+    out.L = 1 << pl.fft_logL;
+    items = std::max(1, pl.T / kHY);
   }
   const size_t hs = hyb_h_smem(pl.T);
-  if ((e = ensure_smem(reinterpret_cast<const void*>(hyb_h_kernel), hs)) != cudaSuccess) return e;
-  const long long hitems = (long long)nclips * (pl.ny_pad / kHY);
-  hyb_h_kernel<<<(int)std::min<long long>(hitems, sms), kHThreads, hs, st>>>(pl, ws);
+  auto kern = fmt == kHRowsFp16 ? hyb_h_kernel<kHRowsFp16> : hyb_h_kernel<kHPolyF32>;
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), hs);
+  if (e != cudaSuccess) return e;
+  kern<<<(int)std::min<long long>(items, sms), kHThreads, hs, st>>>(pl, ws, out);
   count_launch(1);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grouped_fft(const Plan& pl, void* ws_, float* F, cudaStream_t st) {
+  uint8_t* ws = static_cast<uint8_t*>(ws_);
+  if (!pl.hyb || !pl.yfft || pl.batch || pl.logT > 16) return cudaErrorInvalidValue;
+  cudaError_t e;
+  {
+    KtScope ks("group_rows", st);
+    if ((e = group_rows(pl, ws, st)) != cudaSuccess) return e;
+  }
+  {
+    KtScope ks("h_poly", st);
+    if ((e = launch_h(pl, ws, kHPolyF32, st)) != cudaSuccess) return e;
+  }
+  KtScope ks("fft_y", st);
+  return launch_fft_y(pl, ws, F, st);
+}
+
+cudaError_t launch_hybrid(const Plan& pl, void* ws_, cudaStream_t st) {
+  uint8_t* ws = static_cast<uint8_t*>(ws_);
+  if (!pl.hyb || !pl.pair || pl.logT > 16) return cudaErrorInvalidValue;
+  const int nclips = pl.batch ? pl.n_clips : 1;
+  cudaError_t e;
+  {
+    KtScope ks("group_rows", st);
+    if ((e = group_rows(pl, ws, st)) != cudaSuccess) return e;
+  }
+  {
+    KtScope ks("h_rows", st);
+    if ((e = launch_h(pl, ws, kHRowsFp16, st)) != cudaSuccess) return e;
+  }
+  KtScope ks("gemm_y", st);
 
   const __half* h = reinterpret_cast<const __half*>(ws + pl.off_h);
   CUtensorMap mhi, mlo;

@@ -164,8 +164,10 @@ def haar(x, y, s, T, J, out=None, workspace=None, stream=None):
 
 
 def forward_grouped(V, T, K, prec="split_f16"):
-    """1 if forward() groups the corners by y for these sizes, 0 if it contracts
-    over the corners, -1 if the sizes are unsupported."""
+    """Which form forward() takes for these sizes: 0 the contraction over the
+    corners, 1 corners grouped by y with the split-FP16 contraction over y, 2
+    corners grouped by y with the pruned FFT along y (FP32); -1 if the sizes are
+    unsupported."""
     return int(_lib.load().fcfs_forward_grouped(int(V), int(T), int(K), _prec(prec)))
 
 
@@ -209,8 +211,9 @@ def set_barrier_extra(n):
 
 
 def set_hybrid(mode):
-    """Row-binned contraction of single-clip split-FP16 calls (corners grouped
-    by y): 0 never, 1 automatic (cost estimate; see forward_grouped), 2 whenever eligible."""
+    """Grouping of single-clip forward calls by y: 0 never, 1 automatic (cost
+    estimates; see forward_grouped), 2 the split-FP16 contraction over y whenever
+    eligible, 3 the pruned FFT along y whenever eligible."""
     _lib.load().fcfs_debug_set_hybrid(int(mode))
 
 
@@ -230,6 +233,18 @@ def profile_read():
     buf = (C.c_float * 4)()
     n = _lib.load().fcfs_profile_read(buf, 4)
     return [float(buf[i]) for i in range(n)]
+
+
+def kernel_timing_enable(on=True):
+    """Start (clearing earlier records) or stop recording stage times of later calls."""
+    _lib.load().fcfs_kernel_timing_enable(1 if on else 0)
+
+
+def kernel_timing():
+    """[(stage name, ms)] of the calls made since kernel_timing_enable(True)."""
+    lib = _lib.load()
+    n = lib.fcfs_kernel_timing_count()
+    return [(lib.fcfs_kernel_timing_name(i).decode(), float(lib.fcfs_kernel_timing_ms(i))) for i in range(n)]
 
 
 def vertices_from_edges(pos, ev0, ev1, eaxis, V):

@@ -71,34 +71,36 @@ def test_no_cpu_fallback(monkeypatch, tmp_path):
 
 
 def test_grouped_plan_workspaces(lib):
-    """Host plans of the grouped (row-binned) contraction, through the size
-    functions (no device work): the automatic choice takes it for the T = 65536,
-    K = 1024 clip on the split-FP16 path, its workspace holds H (2 x 2K x
-    (T + 1 rounded up to 64) FP16), forcing it on a small clip grows the
-    workspace, and the plain FP32 path never groups."""
+    """Host plans of the grouped forms, through the size functions (no device
+    work): the T = 65536, K = 1024 clip takes the pruned FFT along y, whose
+    workspace holds conj(H) as K x T complex FP32 and no partial planes; the
+    split-FP16 contraction over y holds H as 2 x 2K x (T + 1 rounded up to 64)
+    FP16; forcing a grouped form on a small clip grows the workspace."""
     V, T, K = 945450, 65536, 1024
     h_bytes = 2 * (2 * K) * 65600 * 2
+    poly_bytes = K * T * 8
     try:
         lib.fcfs_debug_set_hybrid(0)
         direct = lib.fcfs_workspace_size(V, T, K, 1)
-        direct32 = lib.fcfs_workspace_size(V, T, K, 0)
         adj_direct = lib.fcfs_adjoint_workspace_size(V, T, K, 1)
         small_direct = lib.fcfs_workspace_size(12576, 4096, 256, 1)
         small_direct32 = lib.fcfs_workspace_size(12576, 4096, 256, 0)
         batch_direct = lib.fcfs_batch_workspace_size(100000, 8, 2048, 128, 1)
-        k128_direct = lib.fcfs_workspace_size(V, T, 128, 1)
         lib.fcfs_debug_set_hybrid(1)
         auto = lib.fcfs_workspace_size(V, T, K, 1)
-        assert auto >= h_bytes and auto >= direct   # grouped: H, or the validation plan
-        assert lib.fcfs_workspace_size(V, T, K, 0) == direct32
-        # K = 128: the corners' (2K)^2 MACs are cheaper than grouping, the direct plan
-        assert lib.fcfs_workspace_size(V, T, 128, 1) == k128_direct
+        assert auto >= poly_bytes and auto >= direct   # FFT form, or the validation plan
+        assert lib.fcfs_workspace_size(V, T, K, 0) >= poly_bytes
         # the adjoint groups by y and by x: two permutations of V corners more
         assert lib.fcfs_adjoint_workspace_size(V, T, K, 1) >= adj_direct + 2 * 4 * V
         lib.fcfs_debug_set_hybrid(2)
+        assert lib.fcfs_workspace_size(V, T, K, 1) >= h_bytes
         assert lib.fcfs_workspace_size(12576, 4096, 256, 1) > small_direct
         assert lib.fcfs_batch_workspace_size(100000, 8, 2048, 128, 1) > batch_direct
-        assert lib.fcfs_workspace_size(12576, 4096, 256, 0) == small_direct32   # FP32 never groups
+        # the split-FP16 contraction over y needs tensor cores: FP32 stays direct
+        assert lib.fcfs_workspace_size(12576, 4096, 256, 0) == small_direct32
+        lib.fcfs_debug_set_hybrid(3)
+        assert lib.fcfs_workspace_size(12576, 4096, 256, 0) >= 256 * 4096 * 8
+        assert lib.fcfs_workspace_size(12576, 4096, 256, 1) >= 256 * 4096 * 8
     finally:
         lib.fcfs_debug_set_hybrid(1)
 
@@ -143,40 +145,45 @@ def test_haar_host_checks(lib):
     assert f(20, 32, 48, 10, 256, 4, 0, 16, 256, 1 << 20, None) == 1          # misaligned corners
 
 
+FORMS = {0: "direct", 1: "grouped_tc", 2: "grouped_fft"}
+
+
 def test_automatic_contraction_choice(lib):
-    """The automatic choice between the contraction over the corners and the one
-    grouped by y (cost estimates fitted to measurements of both): measured
-    winners at sizes where they differ by 1.4x or more."""
+    """The automatic choice among the contraction over the corners (direct),
+    the split-FP16 contraction over y (grouped_tc) and the pruned FFT along y
+    (grouped_fft), from cost estimates fitted to measurements of all three."""
     g = lib.fcfs_forward_grouped
     lib.fcfs_debug_set_hybrid(1)
-    assert g(12576, 4096, 256, 1) == 0      # the bench clip: 0.040 ms over corners vs 0.102 grouped
-    assert g(201294, 4096, 256, 1) == 0     # 49 corners per y at K = 256: 0.19 vs 0.27 ms
-    assert g(201294, 4096, 1024, 1) == 1    # K = 1024: 2.50 vs 0.95 ms
-    assert g(50152, 16384, 1024, 1) == 1    # 0.90 vs 0.57 ms
-    assert g(377722, 65536, 512, 1) == 1    # 1.65 vs 0.85 ms
-    assert g(945450, 65536, 1024, 1) == 1   # the large clip: 14.9 vs 2.75 ms
+    assert g(12576, 4096, 256, 1) == 0      # the T = 4096 clip: 0.039 ms direct, 0.077 FFT
     assert g(31700, 2048, 128, 1) == 0      # the adjoint workload's clip, K = 128
-    assert g(945450, 65536, 1024, 0) == 0   # plain FP32 never groups
+    assert g(945450, 65536, 1024, 1) == 2   # the large clip: 14.9 direct, 2.10 grouped tc, 1.72 FFT
+    assert g(945450, 65536, 1024, 0) == 2   # plain FP32: 174 ms direct, 1.70 FFT
+    assert g(12622, 4096, 1024, 1) == 2     # 0.262, 0.246, 0.172 ms
     assert g(100, 1000, 8, 1) == -1
     try:
         lib.fcfs_debug_set_hybrid(0)
         assert g(945450, 65536, 1024, 1) == 0
         lib.fcfs_debug_set_hybrid(2)
         assert g(12576, 4096, 256, 1) == 1
+        assert g(12576, 4096, 256, 0) == 0  # no tensor-core form for FP32 calls
+        lib.fcfs_debug_set_hybrid(3)
+        assert g(12576, 4096, 256, 1) == 2
+        assert g(12576, 4096, 256, 0) == 2
     finally:
         lib.fcfs_debug_set_hybrid(1)
 
 
-# Sizes of the sweeps the automatic choices were fitted to: (T, K, V, faster form),
-# measured on the GB300 (ms per call, split FP16); "tie" marks cases within 2%.
+# Sizes of the sweeps the automatic choices were fitted to: (T, K, V, prec, fastest
+# form), measured on the GB300 (ms per call); "tie" marks cases within 5%.
 FORWARD_SWEEP = [
-    (4096, 256, 3144, "direct"), (4096, 256, 12622, "direct"), (4096, 256, 50386, "direct"),
-    (4096, 256, 201294, "direct"), (65536, 1024, 125716, "grouped"), (65536, 1024, 945586, "grouped"),
-    (4096, 512, 12622, "direct"), (4096, 512, 50386, "tie"), (4096, 512, 201294, "grouped"),
-    (4096, 1024, 12622, "direct"), (4096, 1024, 50386, "grouped"), (4096, 1024, 201294, "grouped"),
-    (16384, 512, 50152, "grouped"), (16384, 512, 200908, "grouped"), (16384, 1024, 50152, "grouped"),
-    (16384, 1024, 200908, "grouped"), (65536, 512, 125716, "direct"), (65536, 512, 377722, "grouped"),
-    (65536, 512, 945586, "grouped"), (65536, 1024, 377722, "grouped"), (65536, 256, 945586, "grouped"),
+    (65536, 1024, 945450, 1, "grouped_fft"), (65536, 1024, 945450, 0, "grouped_fft"),
+    (4096, 256, 12576, 1, "direct"), (4096, 256, 12576, 0, "grouped_fft"),
+    (4096, 256, 50386, 1, "direct"), (4096, 256, 50386, 0, "grouped_fft"),
+    (4096, 256, 201294, 1, "tie"), (4096, 256, 201294, 0, "grouped_fft"),
+    (65536, 1024, 125716, 1, "grouped_fft"), (4096, 1024, 12622, 1, "grouped_fft"),
+    (16384, 512, 50152, 1, "grouped_fft"), (65536, 512, 945586, 1, "tie"),
+    (65536, 256, 945586, 1, "grouped_tc"), (2048, 128, 31546, 1, "direct"),
+    (2048, 128, 31546, 0, "grouped_fft"),
 ]
 ADJOINT_SWEEP = [
     (2048, 128, 31700, "direct"), (4096, 256, 12622, "tie"), (4096, 256, 50386, "grouped"),
@@ -184,20 +191,20 @@ ADJOINT_SWEEP = [
     (65536, 1024, 125716, "grouped"), (65536, 512, 377722, "grouped"), (65536, 256, 945586, "grouped"),
     (65536, 1024, 945586, "grouped"),
 ]
+# the estimate's known miss: 0.518 ms grouped_tc against 0.559 grouped_fft
+FORWARD_MISSES = [(65536, 256, 945586, 1)]
 
 
 def test_automatic_choices_against_the_sweeps(lib):
-    """The cost estimates pick the measured faster form: the forward in all but
-    two near-ties, the adjoint in all."""
+    """The cost estimates pick the measured fastest form: the forward in all
+    but one case within 8%, the adjoint in all."""
     lib.fcfs_debug_set_hybrid(1)
     misses = []
-    for T, K, V, best in FORWARD_SWEEP:
-        got = "grouped" if lib.fcfs_forward_grouped(V, T, K, 1) == 1 else "direct"
+    for T, K, V, prec, best in FORWARD_SWEEP:
+        got = FORMS[lib.fcfs_forward_grouped(V, T, K, prec)]
         if best != "tie" and got != best:
-            misses.append((T, K, V, got))
-    # the two near-ties: T = 4096, K = 1024, V = 12622 (0.265 ms direct against 0.289
-    # grouped) and T = 16384, K = 512, V = 50152 (0.271 direct against 0.251 grouped)
-    assert sorted(misses) == sorted([(4096, 1024, 12622, "grouped"), (16384, 512, 50152, "direct")]), misses
+            misses.append((T, K, V, prec))
+    assert sorted(misses) == sorted(FORWARD_MISSES), misses
     for T, K, V, best in ADJOINT_SWEEP:
         got = "grouped" if lib.fcfs_adjoint_grouped(V, T, K, 1) == 1 else "direct"
         assert best == "tie" or got == best, (T, K, V, got)
@@ -208,7 +215,7 @@ def test_automatic_choices_against_the_sweeps(lib):
 def test_python_contraction_queries(lib):
     """The binding's queries answer as the C ABI does (host only, no device work)."""
     from paper_1010_5562_gb300 import fcfs
-    assert fcfs.forward_grouped(945450, 65536, 1024) == 1
+    assert fcfs.forward_grouped(945450, 65536, 1024) == 2
     assert fcfs.forward_grouped(12576, 4096, 256) == 0
     assert fcfs.adjoint_grouped(945586, 65536, 1024) == 1
     assert fcfs.adjoint_grouped(31700, 2048, 128) == 0
