@@ -1,19 +1,22 @@
 #!/usr/bin/env python3
 """Throughput of the FCFS block transform on GB300, one JSON line on stdout.
 
-Step: one forward block F(k,l), |k|,|l| <= 256, of the synthetic Manhattan clip
-T=4096 with 2000 polygons (~12.6k signed corners), through the C ABI on the
-split-FP16 tensor-core path: tables, exact area and axis lines, tcgen05
-contraction, compensated split-K reduction and epilogue (five kernels).
-Metric: vertex-coefficient terms per second, V * (2K+1)^2 per step.
+Step: one forward block F(k,l), |k|,|l| <= 1024, of the synthetic Manhattan
+clip T=65536 with 150000 polygons (945450 signed corners), and one adjoint of
+that block (the derivative of every corner for a seeded complex cotangent over
+the whole block), through the C ABI on the split-FP16 precision class (the
+library picks its fastest form per call: the forward groups the corners by y
+and takes a pruned FFT along y, the adjoint groups them by y and by x for its
+tensor-core contraction).  Metric: vertex-coefficient terms per second,
+2 V (2K+1)^2 per step (the adjoint counts the forward's terms).
 
-Default run: N=1, warm-up 50, 5000 timed steps.  The clip's inputs are far
-smaller than L2, so L2 is flushed (a 256 MiB write) before every timed step,
-outside the timed events.  Under torchrun each rank runs its own replica of the
-clip on its own GPU (no collective; weak scaling); rank 0 prints the line.
+Default run: N=1, warm-up 5, 20 timed steps; the workspaces (over 1 GB)
+exceed L2 and L2 is also flushed (a 256 MiB write) before every timed step,
+outside the timed events.  Under torchrun each rank runs its own replica of
+the clip on its own GPU (no collective; weak scaling); rank 0 prints the line.
 
 --impl reference times the FP64 oracle instead (the plain CPU implementation
-of the definition, on the host cores), on row samples of the same block.
+of the definition, on the host cores), on a bounded sample of the same step.
 """
 import argparse
 import hashlib
@@ -30,31 +33,33 @@ sys.path.insert(0, ROOT)
 
 METRIC = "vertex·coefficient terms/s (fwd, adjoint) vs plain FP32 GPU at stated rel error"
 UNIT = "terms/s"
-WORKLOAD = ("clip T=4096, 2000 rectilinear polygons (rect/L/T/U/plus/stair, sides 20-89), "
-            "V=12576 signed corners, K=256 (513x513 complex64 block), forward")
+WORKLOAD = ("clip T=65536, 150000 rectilinear polygons (rect/L/T/U/plus/stair, sides 20-166), V=945450 signed "
+            "corners, K=1024 (2049x2049 complex64 block); step = forward block + adjoint (corner derivatives "
+            "for a seeded complex cotangent over the block)")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gemm_tc_T4096_K256.md")
 FALLBACK_BF16_TFLOPS = 1900.0
 FALLBACK_HBM_GBS = 6800.0
+SMS, FP32_LANES = 152, 128   # GB300: SMs, FP32 lanes per SM (the FP32 FMA peak)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5000)
-    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the adjoint, batch, large-clip and cosine-series measurements")
+                    help="skip the other workloads (adjoint, batch, T=4096 clip, forms, cosine, Haar, crossover)")
     ap.add_argument("--no-pair", action="store_true",
                     help="--only: one-CTA tiles instead of CTA pairs (profiling)")
     ap.add_argument("--no-fuse", action="store_true",
                     help="--only: separate axis and reduce kernels (profiling)")
     ap.add_argument("--prec", choices=["split_f16", "fp32"], default="split_f16",
                     help="--only adjoint / adjoint_large / cosine / cosine_large: contraction precision")
-    ap.add_argument("--only", choices=["step", "large", "batch", "adjoint", "adjoint_large", "cosine",
+    ap.add_argument("--only", choices=["step", "clip4096", "large", "batch", "adjoint", "adjoint_large", "cosine",
                                        "cosine_large", "haar", "haar_large"], default=None,
                     help="run one workload warmup + steps times and print its mean time "
                          "(for profiler command lines; not the benchmark line)")
@@ -85,43 +90,76 @@ def host_cores():
 
 def workload():
     from synth import config_clip
-    clip, K = config_clip(2)
-    return clip, K
+    return config_clip(5)
+
+
+def cotangent(K):
+    """The seeded cotangent of the step's adjoint: standard complex normal over the block."""
+    import numpy as np
+    W = 2 * K + 1
+    rng = np.random.default_rng(5)
+    return (rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))).astype(np.complex64)
 
 
 def terms(clip, K):
-    return clip.V * (2 * K + 1) ** 2
+    """Terms of one step: the forward's V (2K+1)^2 and the adjoint's as many."""
+    return 2 * clip.V * (2 * K + 1) ** 2
 
 
 # ---------------------------------------------------------------------------
 # the oracle as CPU baseline (the only place bench.py runs oracle/)
 # ---------------------------------------------------------------------------
-def oracle_rows(clip, K, rows, start):
-    """F(k, l) for `rows` consecutive k (cycling over [-K, K]) and every l."""
+SAMPLE_N = 24   # frequencies per axis of one oracle sample's sub-block of F
+
+
+def sample_corners(clip, K):
+    """Corners of one sample's adjoint half: as many terms as its forward half."""
+    return max(1, int(round(SAMPLE_N * SAMPLE_N * clip.V / (2 * K + 1) ** 2)))
+
+
+def oracle_sample(clip, K, G, i):
+    """The i-th bounded sample of the step on the oracle: a SAMPLE_N x SAMPLE_N
+    sub-block of F (seeded rows and columns; the first sample holds 0, +-1 and
+    +-K on both axes) and the derivatives of sample_corners() seeded corners for
+    the full cotangent (both halves have SAMPLE_N^2 V terms).
+    Returns (rows, cols, F sub-block, corner indices, gx, gy, terms)."""
     import numpy as np
     import oracle
+    W = 2 * K + 1
+    rng = np.random.default_rng(100 + i)
     f = np.arange(-K, K + 1)
-    ks = f[(start + np.arange(rows)) % f.shape[0]]
-    return oracle.block_entries(clip.x, clip.y, clip.s, clip.T, ks, f)
+    if i == 0:
+        fixed = np.array([0, 1, -1, K, -K])
+        rest = rng.choice(np.setdiff1d(f, fixed), 2 * (SAMPLE_N - fixed.size), replace=False)
+        rows = np.sort(np.concatenate([fixed, rest[:SAMPLE_N - fixed.size]]))
+        cols = np.sort(np.concatenate([fixed, rest[SAMPLE_N - fixed.size:]]))
+    else:
+        rows = np.sort(rng.choice(f, SAMPLE_N, replace=False))
+        cols = np.sort(rng.choice(f, SAMPLE_N, replace=False))
+    nc = sample_corners(clip, K)
+    idx = np.sort(rng.choice(clip.V, nc, replace=False))
+    Fr = oracle.block_entries(clip.x, clip.y, clip.s, clip.T, rows, cols)
+    gx, gy = oracle.vertex_gradient(clip.x[idx], clip.y[idx], clip.s[idx], clip.T, K, G.astype(np.complex128))
+    return rows, cols, Fr, idx, gx, gy, SAMPLE_N * SAMPLE_N * clip.V + nc * W * W
 
 
-def cpu_baseline(clip, K, seconds):
-    """Full oracle blocks, repeated for about `seconds` of CPU time."""
-    import oracle
+def cpu_baseline(clip, K, G, seconds):
+    """Oracle samples of the step, repeated for about `seconds` of CPU time."""
     t0 = time.perf_counter()
-    runs = 0
-    F = None
+    n_terms = 0
+    samples = []
     while True:
-        F = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
-        runs += 1
+        r = oracle_sample(clip, K, G, len(samples))
+        samples.append(r)
+        n_terms += r[6]
         el = time.perf_counter() - t0
-        if runs >= 2 and el >= seconds:
+        if el >= seconds:
             break
-    value = terms(clip, K) * runs / el
-    info = {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-            "sample": "%d full 513x513 blocks of the T=4096 clip in %.1f s (FP64 numpy, BLAS matmul)"
-                      % (runs, el)}
-    return info, F, oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+    info = {"value": n_terms / el, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "sample": ("%d samples in %.1f s, each a %dx%d sub-block of the 2049x2049 forward block and the "
+                       "derivatives of %d corners (adjoint, full cotangent) of the T=65536 clip (FP64 numpy, "
+                       "BLAS matmul)" % (len(samples), el, SAMPLE_N, SAMPLE_N, len(samples[0][3])))}
+    return info, samples
 
 
 def run_reference(args):
@@ -129,29 +167,26 @@ def run_reference(args):
     if rank != 0:
         return 0
     clip, K = workload()
-    W = 2 * K + 1
-    t0 = time.perf_counter()
-    oracle_rows(clip, K, 8, 0)
-    per_row = (time.perf_counter() - t0) / 8
-    budget = 90.0
-    rows = int(max(1, min(W, budget / max(1, args.steps + args.warmup) / per_row)))
+    G = cotangent(K)
     for i in range(args.warmup):
-        oracle_rows(clip, K, rows, i * rows)
+        oracle_sample(clip, K, G, i)
     t0 = time.perf_counter()
+    n_terms = 0
     for i in range(args.steps):
-        oracle_rows(clip, K, rows, (args.warmup + i) * rows)
+        n_terms += oracle_sample(clip, K, G, args.warmup + i)[6]
     el = time.perf_counter() - t0
-    n_terms = clip.V * rows * W * args.steps
     value = n_terms / el
     cores = host_cores()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_rows_per_step": rows,
-                                        "l2": "n/a (host)"},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (host)",
+                                        "sample_per_step": "a %dx%d sub-block of F + the adjoint of %d corners"
+                                                           % (SAMPLE_N, SAMPLE_N, sample_corners(clip, K))},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "%d block rows x 513 columns per step (FP64 numpy)" % rows},
+                         "sample": "per step: a %dx%d sub-block of F and the derivatives of %d corners (FP64 numpy)"
+                                   % (SAMPLE_N, SAMPLE_N, sample_corners(clip, K))},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -277,7 +312,73 @@ def whole_job_rate(local_ms, units_per_step, steps, world, device="cpu"):
     return world * units_per_step * steps / (t * 1e-3), t
 
 
+def peaks():
+    """(bf16 dense TFLOP/s burst, HBM GB/s, SM max MHz, source) from MEASURED_PEAKS.json."""
+    try:
+        with open(PEAKS_FILE) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops"]), float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return FALLBACK_BF16_TFLOPS, FALLBACK_HBM_GBS, 2070.0, "fallback"
+
+
+def stage_work(name, clip, K):
+    """Roofline of one library stage on the step's clip: (bound, algorithmic work
+    per launch, unit of the rate, what the work counts), or None for stages
+    that are latency-bound glue (prep, grouping, outputs)."""
+    V, T, M2 = float(clip.V), float(clip.T), 2.0 * K
+    if name in ("h_poly", "h_rows"):
+        return ("alu", 8.0 * V * K, "TFLOP/s",
+                "8 FP32 flops per corner-frequency term (form s e^{j 2 pi k x / T} from table values, add it)")
+    if name == "fft_y":
+        return ("hbm", K * T * 8.0 + 2.0 * K * (2 * K) * 8.0, "GB/s",
+                "conj(H) read once (K T complex64) + rows k and -k of the block written once")
+    if name == "gemm_y":
+        return ("tensor", 2.0 * (T + 1) * M2 * M2, "TFLOP/s", "2 (T+1) (2K)^2: one real MAC per y-frequency term")
+    if name in ("gemm_tc", "gemm_tc_fused"):
+        return ("tensor", 2.0 * V * M2 * M2, "TFLOP/s", "2 V (2K)^2: one real MAC per corner-coefficient term")
+    if name == "adj_tc_grouped":
+        return ("tensor", 4.0 * (T + 1) * M2 * M2, "TFLOP/s",
+                "2 matrices (gx, gy) x 2 (T+1) (2K)^2: one real MAC per b-value-coefficient term")
+    if name == "adj_tc":
+        return ("tensor", 4.0 * V * M2 * M2, "TFLOP/s", "2 matrices x 2 V (2K)^2")
+    if name == "axis_lines":
+        return ("alu", 4.0 * K * (T + 1), "Tops/s", "4 K (T+1) exact integer MACs (the two axis lines)")
+    return None
+
+
+def roofline_of(stages, clip, K):
+    """The dominant stage of the step (largest mean time) against its roofline."""
+    bf16, hbm, mhz, src = peaks()
+    fp32 = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    ranked = sorted(stages.items(), key=lambda kv: -kv[1])
+    name, ms = ranked[0]
+    w = stage_work(name, clip, K)
+    out = {"kernel": name, "kernel_ms": ms,
+           "stage_ms": {k: round(v, 4) for k, v in ranked}}
+    if w is None:
+        out.update({"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
+        return out
+    bound, work, unit, what = w
+    if bound == "tensor":
+        peak, psrc = bf16, "%s bf16 dense burst (fp16 same rate)" % src
+        achieved = work / (ms * 1e-3) / 1e12
+        out["issued_tflops"] = 3.0 * achieved     # hi*hi + hi*lo + lo*hi
+        out["issued_frac"] = 3.0 * achieved / peak
+    elif bound == "hbm":
+        peak, psrc = hbm, "%s STREAM-style copy" % src
+        achieved = work / (ms * 1e-3) / 1e9
+    else:
+        peak = fp32
+        psrc = "derived: %d SMs x %d FP32 lanes x 2 flops x %.0f MHz (%s SM max clock)" % (SMS, FP32_LANES, mhz, src)
+        achieved = work / (ms * 1e-3) / 1e12
+    out.update({"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": None, "work": what, "peak_source": psrc})
+    return out
+
+
 def run_ours(args):
+    import numpy as np
     import torch
 
     rank, world, local = dist_env()
@@ -291,27 +392,29 @@ def run_ours(args):
     from paper_1010_5562_gb300 import build as B
     B.build()
     from paper_1010_5562_gb300 import fcfs
+    lib = fcfs._lib.load()
 
     clip, K = workload()
     T, V = clip.T, clip.V
     W = 2 * K + 1
     n_terms = terms(clip, K)
+    Gh = cotangent(K)
     x = torch.from_numpy(clip.x).to(dev)
     y = torch.from_numpy(clip.y).to(dev)
     s = torch.from_numpy(clip.s).to(dev)
+    G = torch.from_numpy(Gh).to(dev)
     F = torch.empty((W, W), dtype=torch.complex64, device=dev)
     area = torch.empty((1,), dtype=torch.int64, device=dev)
+    gx = torch.empty(V, dtype=torch.float32, device=dev)
+    gy = torch.empty_like(gx)
     ws = torch.empty(fcfs.workspace_size(V, T, K, "split_f16"), dtype=torch.uint8, device=dev)
-    F32 = torch.empty_like(F)
-    ws32 = torch.empty(fcfs.workspace_size(V, T, K, "fp32"), dtype=torch.uint8, device=dev)
+    wsa = torch.empty(lib.fcfs_adjoint_workspace_size(V, T, K, 1), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(prec="split_f16"):
-        if prec == "split_f16":
-            fcfs.forward(x, y, s, T, K, prec=prec, out=F, area_out=area, workspace=ws, stream=stream)
-        else:
-            fcfs.forward(x, y, s, T, K, prec=prec, out=F32, area_out=area, workspace=ws32, stream=stream)
+    def step():
+        fcfs.forward(x, y, s, T, K, prec="split_f16", out=F, area_out=area, workspace=ws, stream=stream)
+        fcfs.adjoint(x, y, s, T, K, G, prec="split_f16", gx=gx, gy=gy, workspace=wsa, stream=stream)
 
     def timed(n, fn):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
@@ -326,17 +429,15 @@ def run_ours(args):
     for _ in range(max(3, args.warmup)):
         flush.fill_(1)
         step()
-    step("fp32")
     torch.cuda.synchronize(dev)
 
     # ---- main timed region ----
-    # The timed steps can take only milliseconds, less than the sampling period
-    # of nvidia-smi, so the same step also runs (untimed) for a few sampling
-    # periods before and after them: the clock samples are taken under that load.
+    # The clock samples are taken while the same step keeps the GPU busy for a
+    # few sampling periods before and after the timed steps.
     def keep_busy(seconds):
         t0 = time.perf_counter()
         while time.perf_counter() - t0 < seconds:
-            for _ in range(20):
+            for _ in range(4):
                 flush.fill_(1)
                 step()
             torch.cuda.synchronize(dev)
@@ -344,7 +445,7 @@ def run_ours(args):
     sampler = ClockSampler(gpu_index_for_smi(local)) if rank == 0 else None
     if sampler:
         sampler.start()
-        keep_busy(0.3)
+        keep_busy(0.4)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -355,86 +456,103 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     if sampler:
-        keep_busy(0.3)
+        keep_busy(0.4)
     clocks = sampler.stop() if sampler else None
     if clocks is not None:
-        clocks["window"] = "nvidia-smi every 100 ms, the step running 0.3 s before and after the timed steps"
+        clocks["window"] = "nvidia-smi every 100 ms, the step running 0.4 s before and after the timed steps"
     value, total_ms = whole_job_rate(sum(ms), n_terms, args.steps, world, dev)
 
-    # ---- per-kernel roofline of the contraction (events around the kernel) ----
-    reps = min(args.steps, 500)
-    fcfs.profile_enable(True)
-    stage = []
+    # ---- per-stage times (events around each library stage, separate pass) ----
+    reps = 3
+    acc = {}
+    fwd_ms = adj_ms = 0.0
     for _ in range(reps):
         flush.fill_(1)
+        fcfs.kernel_timing_enable(True)
         step()
-        stage.append(fcfs.profile_read())
-    fcfs.profile_enable(False)
-    gemm_ms = statistics.mean(r[2] for r in stage)
-    stage_ms = [statistics.mean(r[i] for r in stage) for i in range(4)]
-    alg_flops = 2.0 * V * (2 * K) ** 2          # one real MAC per off-axis term
-    issued_flops = 3.0 * alg_flops               # hi*hi + hi*lo + lo*hi
-    peak_tf, peak_kind = measured_peak()
-    achieved = alg_flops / (gemm_ms * 1e-3) / 1e12
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved / peak_tf, "traffic": traffic_per_launch(),
-                "kernel": ("gemm_tc_kernel<256,3,full,pair> (tcgen05 cta_group::2 split-FP16 contraction on "
-                           "CTA pairs; fused split-K sum, axis DFT and output behind a grid barrier)"),
-                "kernel_ms": gemm_ms, "peak_source": "%s bf16 dense burst (fp16 same rate)" % peak_kind,
-                "issued_tflops": issued_flops / (gemm_ms * 1e-3) / 1e12,
-                "issued_frac": issued_flops / (gemm_ms * 1e-3) / 1e12 / peak_tf,
-                # the axis lines and the split-K sum run inside the contraction kernel
-                "stage_ms": {"prep": stage_ms[0], "contraction_with_fused_tail": stage_ms[2]}}
+        for name, t in fcfs.kernel_timing():
+            acc[name] = acc.get(name, 0.0) + t / reps
+            if name.startswith("adj_"):
+                adj_ms += t / reps
+            else:
+                fwd_ms += t / reps
+    fcfs.kernel_timing_enable(False)
+    roofline = roofline_of(acc, clip, K)
+    forms = {0: "direct", 1: "grouped_tc", 2: "grouped_fft"}
+    parts = {"forward": {"form": forms.get(fcfs.forward_grouped(V, T, K), "?"), "stages_ms": round(fwd_ms, 4),
+                         "value": V * W * W / (fwd_ms * 1e-3)},
+             "adjoint": {"form": "grouped" if fcfs.adjoint_grouped(V, T, K) == 1 else "per corner",
+                         "stages_ms": round(adj_ms, 4), "value": V * W * W / (adj_ms * 1e-3)}}
 
-    # ---- plain FP32 path on the same clip ----
-    ms32 = timed(min(args.steps, 1000), lambda: step("fp32"))
+    # ---- plain FP32 on the same clip (forward and adjoint) ----
+    F32 = torch.empty_like(F)
+    gx32 = torch.empty_like(gx)
+    gy32 = torch.empty_like(gx)
+    ws32 = torch.empty(fcfs.workspace_size(V, T, K, "fp32"), dtype=torch.uint8, device=dev)
+    wsa32 = torch.empty(lib.fcfs_adjoint_workspace_size(V, T, K, 0), dtype=torch.uint8, device=dev)
+
+    def step32():
+        fcfs.forward(x, y, s, T, K, prec="fp32", out=F32, area_out=area, workspace=ws32, stream=stream)
+        fcfs.adjoint(x, y, s, T, K, G, prec="fp32", gx=gx32, gy=gy32, workspace=wsa32, stream=stream)
+
+    step32()
+    ms32 = timed(2, step32)
     value32 = world * n_terms / (statistics.mean(ms32) * 1e-3)
 
-    # ---- end to end: pinned host inputs in, block out ----
-    # x, y and s travel in one pinned staging buffer (16-byte aligned views on
-    # both sides), F and the area come back as one block: one copy each way
+    # ---- end to end: pinned host inputs in, block and derivatives out ----
+    # x, y, s and the cotangent travel in one pinned staging buffer (16-byte
+    # aligned views on both sides); F, the area and the derivatives come back as
+    # one block: one copy each way per step.
     a16 = lambda n: (n + 15) // 16 * 16
     ox, oy, osg = 0, a16(4 * V), 2 * a16(4 * V)
-    nin = osg + a16(V)
+    og = osg + a16(V)
+    nin = og + W * W * 8
     hin = torch.zeros(nin, dtype=torch.uint8).pin_memory()
     hin[ox:ox + 4 * V].copy_(torch.from_numpy(clip.x).view(torch.uint8))
     hin[oy:oy + 4 * V].copy_(torch.from_numpy(clip.y).view(torch.uint8))
     hin[osg:osg + V].copy_(torch.from_numpy(clip.s).view(torch.uint8))
-    din = torch.empty(nin, dtype=torch.uint8, device=dev)
-    ex, ey = din[ox:ox + 4 * V].view(torch.int32), din[oy:oy + 4 * V].view(torch.int32)
-    es = din[osg:osg + V].view(torch.int8)
-    nout = W * W * 8 + 8
-    dout = torch.empty(nout, dtype=torch.uint8, device=dev)
-    eF = dout[:W * W * 8].view(torch.complex64).view(W, W)
-    ea = dout[W * W * 8:].view(torch.int64)
-    hout = torch.empty(nout, dtype=torch.uint8).pin_memory()
+    hin[og:].copy_(torch.from_numpy(Gh).view(torch.uint8).reshape(-1))
+    of, oa, ogx = 0, W * W * 8, W * W * 8 + 16
+    ogy = ogx + a16(4 * V)
+    nout = ogy + a16(4 * V)
+    Fref, gxref, gyref = F.cpu(), gx.cpu(), gy.cpu()
 
-    def e2e_step():
-        din.copy_(hin, non_blocking=True)
-        fcfs.forward(ex, ey, es, T, K, prec="split_f16", out=eF, area_out=ea, workspace=ws, stream=stream)
-        hout.copy_(dout, non_blocking=True)
-
-    for _ in range(5):
-        e2e_step()
-    mse = timed(min(args.steps, 1000), e2e_step)
-    torch.cuda.synchronize(dev)
-    e2e_ok = bool(torch.equal(hout[:W * W * 8].view(torch.complex64).view(W, W), F.cpu()))
-
-    # Pipelined: steps alternate between two streams, so one step's copies run on
-    # the copy engines while another step computes.  Eight buffer sets (inputs,
-    # block, workspace) rotate; together they exceed L2 (129 MB), so a set comes
-    # back cold, and set i is reused on the same stream 8 steps later (no race).
-    n_sets = 8
-    sets = []
-    for _ in range(n_sets):
+    def make_set():
         d_in = torch.empty(nin, dtype=torch.uint8, device=dev)
         d_out = torch.empty(nout, dtype=torch.uint8, device=dev)
-        sets.append(dict(din=d_in, dout=d_out, ws=torch.empty_like(ws),
-                         hout=torch.empty(nout, dtype=torch.uint8).pin_memory(),
-                         x=d_in[ox:ox + 4 * V].view(torch.int32), y=d_in[oy:oy + 4 * V].view(torch.int32),
-                         s=d_in[osg:osg + V].view(torch.int8),
-                         F=d_out[:W * W * 8].view(torch.complex64).view(W, W), a=d_out[W * W * 8:].view(torch.int64)))
-    set_bytes = nin + nout + ws.numel()
+        return dict(din=d_in, dout=d_out, ws=torch.empty_like(ws), wsa=torch.empty_like(wsa),
+                    hout=torch.empty(nout, dtype=torch.uint8).pin_memory(),
+                    x=d_in[ox:ox + 4 * V].view(torch.int32), y=d_in[oy:oy + 4 * V].view(torch.int32),
+                    s=d_in[osg:osg + V].view(torch.int8), G=d_in[og:].view(torch.complex64).view(W, W),
+                    F=d_out[of:of + W * W * 8].view(torch.complex64).view(W, W),
+                    a=d_out[oa:oa + 8].view(torch.int64), gx=d_out[ogx:ogx + 4 * V].view(torch.float32),
+                    gy=d_out[ogy:ogy + 4 * V].view(torch.float32))
+
+    def run_set(b, st):
+        b["din"].copy_(hin, non_blocking=True)
+        fcfs.forward(b["x"], b["y"], b["s"], T, K, prec="split_f16", out=b["F"], area_out=b["a"],
+                     workspace=b["ws"], stream=st)
+        fcfs.adjoint(b["x"], b["y"], b["s"], T, K, b["G"], prec="split_f16", gx=b["gx"], gy=b["gy"],
+                     workspace=b["wsa"], stream=st)
+        b["hout"].copy_(b["dout"], non_blocking=True)
+
+    def same(b):
+        h = b["hout"]
+        return (torch.equal(h[of:of + W * W * 8].view(torch.complex64).view(W, W), Fref)
+                and torch.equal(h[ogx:ogx + 4 * V].view(torch.float32), gxref)
+                and torch.equal(h[ogy:ogy + 4 * V].view(torch.float32), gyref))
+
+    one = make_set()
+    for _ in range(2):
+        run_set(one, stream)
+    mse = timed(min(args.steps, 10), lambda: run_set(one, stream))
+    torch.cuda.synchronize(dev)
+    e2e_ok = bool(same(one))
+    # Pipelined: steps alternate between two streams, so one step's copies run on
+    # the copy engines while the other computes; sets are reused on the same
+    # stream only (no race), and together they exceed L2.
+    n_sets = 2
+    sets = [one, make_set()]
     lanes = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
 
     def e2e_pipelined(n):
@@ -445,61 +563,77 @@ def run_ours(args):
         for i in range(n):
             ln, b = lanes[i % 2], sets[i % n_sets]
             with torch.cuda.stream(ln):
-                b["din"].copy_(hin, non_blocking=True)
-                fcfs.forward(b["x"], b["y"], b["s"], T, K, prec="split_f16", out=b["F"], area_out=b["a"],
-                             workspace=b["ws"], stream=ln)
-                b["hout"].copy_(b["dout"], non_blocking=True)
+                run_set(b, ln)
         for ln in lanes:
             stream.wait_stream(ln)
         t1.record(stream)
         torch.cuda.synchronize(dev)
         return t0.elapsed_time(t1) / n
 
-    e2e_pipelined(2 * n_sets)
-    ms_pipe = e2e_pipelined(min(args.steps, 1000))
-    pipe_ok = all(bool(torch.equal(b["hout"][:W * W * 8].view(torch.complex64).view(W, W), F.cpu())) for b in sets)
+    e2e_pipelined(4)
+    ms_pipe = e2e_pipelined(max(4, min(args.steps, 20)))
+    pipe_ok = all(same(b) for b in sets)
+    set_bytes = nin + nout + ws.numel() + wsa.numel()
     e2e = {"value": world * n_terms / (ms_pipe * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": int(nin), "d2h_bytes_per_step": int(nout),
-           "copies": ("every step: one H2D of x, y, s from pinned host memory and one D2H of F and the area; "
-                      "steps alternate between two streams so copies overlap another step's compute; "
-                      "%d buffer sets in rotation (%.0f MB, more than L2)" % (n_sets, n_sets * set_bytes / 1e6)),
+           "copies": ("every step: one H2D of x, y, s and the cotangent from pinned host memory and one D2H "
+                      "of F, the area and both derivatives; steps alternate between two streams so copies "
+                      "overlap the other step's compute; %d buffer sets (%.0f MB each)"
+                      % (n_sets, set_bytes / 1e6)),
            "ms_per_step": ms_pipe, "matches_device_step": bool(e2e_ok and pipe_ok),
            "serial": {"value": world * n_terms / (statistics.mean(mse) * 1e-3), "ms_per_step": statistics.mean(mse),
                       "note": "one stream, events around each step, L2 flushed between steps"}}
+    del sets, one
 
     extras = {} if (world > 1 or args.no_extras) else run_extras(fcfs, dev, flush, stream, args)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f16",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded Manhattan clip; stands in for the paper's proprietary 22 nm layout)",
-        "config": {"workload": WORKLOAD, "precision": "split_f16 (hi+lo FP16 operands, FP32 accumulate, "
-                   "TwoSum-compensated split-K sum)", "T": T, "K": K, "V": V,
-                   "l2": "flushed before every timed step (256 MiB write, outside the events)",
+        "config": {"workload": WORKLOAD,
+                   "precision": ("split_f16 class (max|dF|/area <= 1e-5): the library's fastest form per call; "
+                                 "forward: corners grouped by y, FP32 pair sums and pruned FFT along y (FP32 "
+                                 "arithmetic); adjoint: split-FP16 tcgen05 contraction grouped by y and by x"),
+                   "T": T, "K": K, "V": V,
+                   "l2": "workspaces exceed L2, and L2 is flushed before every timed step (256 MiB write, "
+                         "outside the events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline,
-        "plain_fp32": {"value": value32, "unit": UNIT, "ms_per_step": statistics.mean(ms32)},
+        "parts": parts,
+        "plain_fp32": {"value": value32, "unit": UNIT, "ms_per_step": statistics.mean(ms32),
+                       "forward_form": forms.get(fcfs.forward_grouped(V, T, K, prec="fp32"), "?"),
+                       "adjoint_form": "per corner (FP32 CUDA cores)"},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    for k in ("adjoint", "batch", "large", "cosine", "haar", "crossover"):
+    for k in ("adjoint", "batch", "clip_T4096", "large", "cosine", "haar", "crossover"):
         if k in extras:
             line[k] = extras[k]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import numpy as np
-        cb, Fo, A = cpu_baseline(clip, K, args.cpu_seconds)
+        cb, samples = cpu_baseline(clip, K, Gh, args.cpu_seconds)
         line["cpu_baseline"] = cb
-        step()
-        step("fp32")
-        torch.cuda.synchronize(dev)
-        errs = {}
-        for name, t in (("split_f16", F), ("fp32", F32)):
-            Fg = t.cpu().numpy().astype(np.complex128)
-            errs[name] = float(np.max(np.abs(Fg - Fo)) / A)
-        line["accuracy"] = {"max_abs_err_over_area": errs, "area_exact": int(area.item()) == A,
-                            "reference": "FP64 oracle (direct signed-quadrant vertex sum)"}
+        import oracle
+        A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+        Fg, F32g = F.cpu().numpy().astype(np.complex128), F32.cpu().numpy().astype(np.complex128)
+        gxs, gys = gx.cpu().numpy().astype(np.float64), gy.cpu().numpy().astype(np.float64)
+        gx3, gy3 = gx32.cpu().numpy().astype(np.float64), gy32.cpu().numpy().astype(np.float64)
+        err_f = err_f32 = err_g = err_g32 = 0.0
+        for rows, cols, Fr, idx, ox_, oy_, _ in samples:
+            sub = np.ix_(rows + K, cols + K)
+            err_f = max(err_f, float(np.max(np.abs(Fg[sub] - Fr)) / A))
+            err_f32 = max(err_f32, float(np.max(np.abs(F32g[sub] - Fr)) / A))
+            sc = max(float(np.max(np.abs(ox_))), float(np.max(np.abs(oy_))))
+            err_g = max(err_g, float(max(np.max(np.abs(gxs[idx] - ox_)), np.max(np.abs(gys[idx] - oy_)))) / sc)
+            err_g32 = max(err_g32, float(max(np.max(np.abs(gx3[idx] - ox_)), np.max(np.abs(gy3[idx] - oy_)))) / sc)
+        line["accuracy"] = {
+            "forward_max_abs_err_over_area_sampled": err_f, "fp32_forward_max_abs_err_over_area_sampled": err_f32,
+            "adjoint_max_rel_err_sampled": err_g, "fp32_adjoint_max_rel_err_sampled": err_g32,
+            "area_exact": int(area.item()) == A,
+            "sample": "the oracle samples of cpu_baseline: sub-blocks of F and the derivatives of their corners",
+            "reference": "FP64 oracle (direct signed-quadrant vertex sum and its derivative)"}
         if extras:
             extras_accuracy(line, extras)
     if rank == 0:
@@ -609,60 +743,70 @@ def run_extras(fcfs, dev, flush, stream, args):
                     "unit_chunks": uc, "launch": "one fcfs_batch call replayed from a CUDA graph",
                     "_check": (clips, K, Fb, Ab)}
 
-    # large clip: workload 5, both precisions
+    # large clip (the step's clip): every forward form, forced
     clip5, K5 = config_clip(5)
     W5 = 2 * K5 + 1
     x5, y5, s5 = (torch.from_numpy(a).to(dev) for a in (clip5.x, clip5.y, clip5.s))
-    big = {}
+    forms = {}
+    for mode, key, prec in ((0, "direct_tc", "split_f16"), (2, "grouped_tc", "split_f16"),
+                            (3, "grouped_fft", "split_f16")):
+        fcfs.set_hybrid(mode)
+        try:
+            F5 = torch.empty((W5, W5), dtype=torch.complex64, device=dev)
+            A5 = torch.empty(1, dtype=torch.int64, device=dev)
+            ws5 = torch.empty(fcfs.workspace_size(clip5.V, clip5.T, K5, prec), dtype=torch.uint8, device=dev)
+            fn = lambda: fcfs.forward(x5, y5, s5, clip5.T, K5, prec=prec, out=F5, area_out=A5, workspace=ws5,
+                                      stream=stream)
+            ms5 = _timed_ms(torch, fn, 3, flush, stream)
+            flush.fill_(1)
+            fcfs.kernel_timing_enable(True)
+            fn()
+            kt = fcfs.kernel_timing()
+            fcfs.kernel_timing_enable(False)
+        finally:
+            fcfs.set_hybrid(1)
+        forms[key] = {"ms": ms5, "value": clip5.V * W5 * W5 / (ms5 * 1e-3),
+                      "stages_ms": {n: round(t, 4) for n, t in kt}, "_F": F5, "_A": A5}
+    out["large"] = {"workload": "clip T=65536, 150000 polygons, V=%d, K=1024 (2049x2049), forward forms "
+                                "forced one by one" % clip5.V, "unit": UNIT,
+                    "auto": {0: "direct_tc", 1: "grouped_tc", 2: "grouped_fft"}[fcfs.forward_grouped(clip5.V, clip5.T, K5)],
+                    "forms": forms, "_check": (clip5, K5)}
+
+    # the T = 4096 clip: one forward block (the contraction over its corners)
+    clip2, K2 = config_clip(2)
+    W2 = 2 * K2 + 1
+    x2, y2, s2 = (torch.from_numpy(a).to(dev) for a in (clip2.x, clip2.y, clip2.s))
+    F2 = torch.empty((W2, W2), dtype=torch.complex64, device=dev)
+    A2 = torch.empty(1, dtype=torch.int64, device=dev)
+    d2 = {"workload": "clip T=4096, 2000 polygons, V=%d, K=256 (513x513), forward" % clip2.V, "unit": UNIT}
     for prec in ("split_f16", "fp32"):
-        F5 = torch.empty((W5, W5), dtype=torch.complex64, device=dev)
-        A5 = torch.empty(1, dtype=torch.int64, device=dev)
-        ws5 = torch.empty(fcfs.workspace_size(clip5.V, clip5.T, K5, prec), dtype=torch.uint8, device=dev)
-        ms5 = _timed_ms(torch, lambda: fcfs.forward(x5, y5, s5, clip5.T, K5, prec=prec, out=F5, area_out=A5,
-                                                    workspace=ws5, stream=stream), 3, flush, stream)
-        big[prec] = {"value": clip5.V * W5 * W5 / (ms5 * 1e-3), "ms": ms5, "_F": F5, "_A": A5}
-    big["split_f16"]["contraction"] = "corners grouped by y: T+1 contraction columns instead of V corners"
-    # the direct contraction over the V corners on the same clip, for comparison
-    fcfs.set_hybrid(0)
-    try:
-        F5d = torch.empty((W5, W5), dtype=torch.complex64, device=dev)
-        A5d = torch.empty(1, dtype=torch.int64, device=dev)
-        ws5d = torch.empty(fcfs.workspace_size(clip5.V, clip5.T, K5, "split_f16"), dtype=torch.uint8, device=dev)
-        ms5d = _timed_ms(torch, lambda: fcfs.forward(x5, y5, s5, clip5.T, K5, prec="split_f16", out=F5d,
-                                                     area_out=A5d, workspace=ws5d, stream=stream), 3, flush, stream)
-    finally:
-        fcfs.set_hybrid(1)
-    big["split_f16_direct"] = {"value": clip5.V * W5 * W5 / (ms5d * 1e-3), "ms": ms5d,
-                               "contraction": "over the V corners (CTA pairs)"}
-    # adjoint of the large clip (FP32), seeded random cotangent over the full block
-    rng = np.random.default_rng(5)
-    G5 = torch.from_numpy((rng.standard_normal((W5, W5)) + 1j * rng.standard_normal((W5, W5)))
-                          .astype(np.complex64)).to(dev)
-    gx5 = torch.empty(clip5.V, dtype=torch.float32, device=dev)
-    gy5 = torch.empty_like(gx5)
-    wsa5 = torch.empty(fcfs._lib.load().fcfs_adjoint_workspace_size(clip5.V, clip5.T, K5, 0), dtype=torch.uint8,
-                       device=dev)
-    ms_a5 = _timed_ms(torch, lambda: fcfs.adjoint(x5, y5, s5, clip5.T, K5, G5, gx=gx5, gy=gy5, workspace=wsa5,
-                                                  stream=stream), 2, flush, stream)
-    big["adjoint_fp32"] = {"value": clip5.V * W5 * W5 / (ms_a5 * 1e-3), "ms": ms_a5,
-                           "cotangent": "seeded standard complex normal over the block",
-                           "_G": G5, "_g": (gx5, gy5)}
-    gx5h = torch.empty_like(gx5)
-    gy5h = torch.empty_like(gx5)
-    wsa5h = torch.empty(fcfs._lib.load().fcfs_adjoint_workspace_size(clip5.V, clip5.T, K5, 1), dtype=torch.uint8,
-                        device=dev)
-    ms_a5h = _timed_ms(torch, lambda: fcfs.adjoint(x5, y5, s5, clip5.T, K5, G5, prec="split_f16", gx=gx5h, gy=gy5h,
-                                                   workspace=wsa5h, stream=stream), 3, flush, stream)
-    big["adjoint_split_f16"] = {"value": clip5.V * W5 * W5 / (ms_a5h * 1e-3), "ms": ms_a5h,
-                                "cotangent": "as adjoint_fp32", "_g": (gx5h, gy5h)}
+        ws2 = torch.empty(fcfs.workspace_size(clip2.V, clip2.T, K2, prec), dtype=torch.uint8, device=dev)
+        fn = lambda: fcfs.forward(x2, y2, s2, clip2.T, K2, prec=prec, out=F2, area_out=A2, workspace=ws2,
+                                  stream=stream)
+        ms2 = _timed_ms(torch, fn, 200, flush, stream)
+        st = {}
+        for _ in range(20):
+            flush.fill_(1)
+            fcfs.kernel_timing_enable(True)
+            fn()
+            for n, t in fcfs.kernel_timing():
+                st[n] = st.get(n, 0.0) + t / 20
+        fcfs.kernel_timing_enable(False)
+        e = {"ms": ms2, "value": clip2.V * W2 * W2 / (ms2 * 1e-3),
+             "form": {0: "direct", 1: "grouped_tc", 2: "grouped_fft"}[fcfs.forward_grouped(clip2.V, clip2.T, K2, prec=prec)],
+             "_F": F2.cpu()}
+        if prec == "split_f16":
+            rf = roofline_of(st, clip2, K2)
+            rf["traffic"] = traffic_per_launch()
+            e["roofline"] = rf
+        else:
+            e["stages_ms"] = {n: round(t, 4) for n, t in st.items()}
+        d2[prec] = e
+    d2["_check"] = clip2, K2
+    out["clip_T4096"] = d2
     out["cosine"] = cosine_extras(fcfs, dev, flush, stream)
     out["haar"] = haar_extras(fcfs, dev, flush, stream)
     out["crossover"] = crossover_extras(fcfs, dev, flush, stream)
-    out["large"] = {"workload": "clip T=65536, 150000 polygons, V=%d, K=1024 (2049x2049)" % clip5.V,
-                    "unit": UNIT, "split_f16": big["split_f16"], "split_f16_direct": big["split_f16_direct"],
-                    "fp32": big["fp32"],
-                    "adjoint_split_f16": big["adjoint_split_f16"], "adjoint_fp32": big["adjoint_fp32"],
-                    "_check": (clip5, K5)}
     return out
 
 
@@ -711,10 +855,11 @@ CROSSOVER_CLIPS = (
 
 
 def crossover_extras(fcfs, dev, flush, stream):
-    """Split-FP16 forward with the contraction over the V corners (direct) and
-    over the T + 1 values of y after grouping the corners by y (the pruned
-    sparse-image DFT of the off-axis block), across corner densities V / (T + 1).
-    "auto" is the library's automatic choice for the sizes (a cost estimate of both)."""
+    """Forward with the contraction over the V corners (direct), with the corners
+    grouped by y and the split-FP16 contraction over the T + 1 values of y
+    (grouped_tc), and with the pruned FFT along y (grouped_fft), across corner
+    densities V / (T + 1).  "auto" is the library's automatic choice for the
+    sizes (cost estimates of all three)."""
     import torch
     from synth import make_clip
     rows = []
@@ -725,7 +870,7 @@ def crossover_extras(fcfs, dev, flush, stream):
         F = torch.empty((W, W), dtype=torch.complex64, device=dev)
         A = torch.empty(1, dtype=torch.int64, device=dev)
         r = {"T": T, "K": K, "V": clip.V, "V_per_y": round(clip.V / (T + 1), 2)}
-        for mode, key in ((0, "direct_ms"), (2, "grouped_ms")):
+        for mode, key in ((0, "direct_ms"), (2, "grouped_tc_ms"), (3, "grouped_fft_ms")):
             fcfs.set_hybrid(mode)
             try:
                 ws = torch.empty(fcfs.workspace_size(clip.V, T, K, "split_f16"), dtype=torch.uint8, device=dev)
@@ -733,10 +878,10 @@ def crossover_extras(fcfs, dev, flush, stream):
                                                                stream=stream), 10 if T <= 4096 else 3, flush, stream)
             finally:
                 fcfs.set_hybrid(1)
-        r["auto"] = "grouped" if fcfs.forward_grouped(clip.V, T, K) == 1 else "direct"
-        r["faster"] = "grouped" if r["grouped_ms"] < r["direct_ms"] else "direct"
+        r["auto"] = {0: "direct", 1: "grouped_tc", 2: "grouped_fft"}[fcfs.forward_grouped(clip.V, T, K)]
+        r["fastest"] = min(("direct", "grouped_tc", "grouped_fft"), key=lambda f: r[f + "_ms"])
         rows.append(r)
-    return {"unit": "ms per forward call (split FP16)", "rows": rows}
+    return {"unit": "ms per forward call (split-FP16 class)", "rows": rows}
 
 
 def measured_hbm():
@@ -848,20 +993,17 @@ def extras_accuracy(line, extras):
         A = oracle.area_exact(clip5.x, clip5.y, clip5.s, clip5.T)
         pick = np.unique(np.array([0, 1, -1, 2, -2, 7, -13, 100, -333, 512, K5, -K5, K5 - 1]))
         Fo = oracle.block_entries(clip5.x, clip5.y, clip5.s, clip5.T, pick, pick)
-        for prec in ("split_f16", "fp32"):
-            d = line["large"][prec]
+        for key, d in line["large"]["forms"].items():
             F5 = d.pop("_F").cpu().numpy()[np.ix_(pick + K5, pick + K5)]
             d["max_abs_err_over_area_sampled"] = float(np.max(np.abs(F5 - Fo)) / A)
             d["area_exact"] = int(d.pop("_A").item()) == A
-        d = line["large"]["adjoint_fp32"]
-        G5 = d.pop("_G").cpu().numpy().astype(np.complex128)
-        idx = np.sort(np.random.default_rng(55).choice(clip5.V, 32, replace=False))
-        rx, ry = oracle.vertex_gradient(clip5.x[idx], clip5.y[idx], clip5.s[idx], clip5.T, K5, G5)
-        for key in ("adjoint_fp32", "adjoint_split_f16"):
-            d = line["large"][key]
-            gx5, gy5 = (t.cpu().numpy().astype(np.float64) for t in d.pop("_g"))
-            d["max_rel_err_sampled"] = max(float(np.max(np.abs(gx5[idx] - rx)) / np.max(np.abs(rx))),
-                                           float(np.max(np.abs(gy5[idx] - ry)) / np.max(np.abs(ry))))
+    if "clip_T4096" in extras:
+        clip2, K2 = extras["clip_T4096"].pop("_check")
+        A = oracle.area_exact(clip2.x, clip2.y, clip2.s, clip2.T)
+        Fo = oracle.block(clip2.x, clip2.y, clip2.s, clip2.T, K2)
+        for prec in ("split_f16", "fp32"):
+            d = line["clip_T4096"][prec]
+            d["max_abs_err_over_area"] = float(np.max(np.abs(d.pop("_F").numpy().astype(np.complex128) - Fo)) / A)
 
 
 def run_only(args):
@@ -885,8 +1027,16 @@ def run_only(args):
         clip, K = config_clip(2) if args.only == "cosine" else cosine_large_clip()
         x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))
         fn = lambda: fcfs.cosine(x, y, s, clip.T, K, prec=args.prec)
-    elif args.only in ("step", "large", "adjoint", "adjoint_large"):
-        clip, K = config_clip({"step": 2, "large": 5, "adjoint": 4, "adjoint_large": 5}[args.only])
+    elif args.only == "step":   # the benchmark step: forward and adjoint of the large clip
+        clip, K = workload()
+        x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))
+        G = torch.from_numpy(cotangent(K)).to(dev)
+
+        def fn():
+            fcfs.forward(x, y, s, clip.T, K, prec="split_f16")
+            fcfs.adjoint(x, y, s, clip.T, K, G, prec="split_f16")
+    elif args.only in ("clip4096", "large", "adjoint", "adjoint_large"):
+        clip, K = config_clip({"clip4096": 2, "large": 5, "adjoint": 4, "adjoint_large": 5}[args.only])
         x, y, s = (torch.from_numpy(a).to(dev) for a in (clip.x, clip.y, clip.s))
         if args.only.startswith("adjoint"):
             gen = torch.Generator(device="cpu").manual_seed(7)

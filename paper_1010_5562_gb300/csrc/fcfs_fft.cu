@@ -98,12 +98,24 @@ struct Dft {
 // so the strided stores of the first passes fall on distinct banks.
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
+// Twiddle level of a pass, e^{-j 2 pi i / M} for i < M: a table of M entries
+// for M <= 256, else the product hi[i >> 6] lo[i & 63] of two correctly
+// rounded tables (M / 64 and 64 entries).
+struct TwLevel {
+  const float2* hi;
+  const float2* lo;
+  int two;
+};
+__device__ __forceinline__ float2 tw_at(const TwLevel& t, int i) {
+  return t.two ? c_mul(t.hi[i >> 6], t.lo[i & 63]) : t.hi[i];
+}
+
 // One Stockham pass of radix R over nfft FFTs of L points: X -> Y (Y padded; X
-// padded shared memory, or global memory for the first pass).  twl is the
-// twiddle level of this pass, e^{-j 2 pi i / M} for i < M = Ns R.
-template <int R, bool GLOBAL_IN>
+// padded, or unpadded for the first pass, which reads the buffer the bulk copy
+// filled).
+template <int R, bool RAW_IN>
 __device__ __forceinline__ void stockham_pass(const float2* __restrict__ X, float2* __restrict__ Y,
-                                              const float2* __restrict__ twl, int logL, int nfft, int Ns) {
+                                              const TwLevel& twl, int logL, int nfft, int Ns) {
   const int L = 1 << logL, per = L / R, M = Ns * R;
   const int total = nfft * per;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
@@ -111,10 +123,10 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ X, floa
     const int kp = j & (Ns - 1);
     float2 v[R], y[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = GLOBAL_IN ? __ldcs(X + fo + j + r * per) : X[pad16(fo + j + r * per)];
+    for (int r = 0; r < R; ++r) v[r] = RAW_IN ? X[fo + j + r * per] : X[pad16(fo + j + r * per)];
     if (kp != 0) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], twl[(r * kp) & (M - 1)]);
+      for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], tw_at(twl, (r * kp) & (M - 1)));
     }
     Dft<R>::template sub<1, 0>(v, y);
     const int base = fo + (j - kp) * R + kp;
@@ -128,20 +140,31 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ X, floa
 // with twiddle level M_i = 2^(f0 + 4 i), stored after the levels before it.
 __device__ __forceinline__ int first_log_radix(int logL) { return (logL & 3) ? (logL & 3) : 4; }
 
-// blockIdx.x = k - 1; NT threads (256, or 1024 when 2K + 1 > 9 * 256).
+// Entries of the twiddle level of size 2^lm.
+__host__ __device__ __forceinline__ int level_entries(int lm) { return lm <= 8 ? 1 << lm : (1 << (lm - 6)) + 64; }
+
+// blockIdx.x = k - 1; NT threads (256, or 1024 when 2K + 1 > 9 * 256).  The
+// residues' inputs arrive by bulk copy into an unpadded buffer, the next range's
+// copy overlapping this range's later passes and sums.
 template <int NT>
 __global__ void __launch_bounds__(NT) fft_y_kernel(FftArgs ar) {
   extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ __align__(8) uint64_t full_bar;
   const Plan& pl = ar.pl;
   const int T = pl.T, K = pl.K, logT = pl.logT;
   const int logL = ar.logL, L = 1 << logL, P = 1 << ar.logP;
   const int nfft = max(1, min(P, kFBufPts >> logL));   // FFTs per pass
-  const int bufpts = pad16(nfft * L) + 1;
-  float2* bufA = reinterpret_cast<float2*>(sm);
+  const int pts = nfft * L;
+  const int bufpts = (pad16(pts) + 2) & ~1;            // keeps the next buffer 16-byte aligned
+  float2* raw = reinterpret_cast<float2*>(sm);         // bulk-copy target, pts entries
+  float2* bufA = raw + pts;
   float2* bufB = bufA + bufpts;
-  float2* lev = bufB + bufpts;           // twiddle levels of passes 1, 2, ...
+  float2* lev = bufB + bufpts;                         // twiddle levels of passes 1, 2, ...
   const int k = blockIdx.x + 1;
   const int f0 = first_log_radix(logL);
+  Status* st = reinterpret_cast<Status*>(const_cast<uint8_t*>(ar.ws) + pl.off_status);
+  const uint32_t bytes = (uint32_t)pts * 8u;
+  const float2* src = ar.poly + (size_t)(k - 1) * P * L;
 
   // twiddle levels (the prep kernel wrote the table before the H kernel ran)
   const float* gt = reinterpret_cast<const float*>(ar.ws + pl.off_tab_f32);
@@ -149,36 +172,55 @@ __global__ void __launch_bounds__(NT) fft_y_kernel(FftArgs ar) {
   {
     int off = 0;
     for (int lm = f0 + 4; lm <= logL; lm += 4) {
-      const int M = 1 << lm;
-      for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        const uint32_t p = ((uint32_t)i << (logT - lm)) & mask;   // e^{-j 2 pi i / M} = conj W(i T / M)
+      const int n = level_entries(lm);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        // direct level: entry i; two-level: hi entries i < 2^(lm-6) are 64 i, lo entries the first 64
+        const int e = lm <= 8 ? i : (i < (1 << (lm - 6)) ? 64 * i : i - (1 << (lm - 6)));
+        const uint32_t p = ((uint32_t)e << (logT - lm)) & mask;   // e^{-j 2 pi e / M} = conj W(e T / M)
         const float2 w = pl.full ? f32_lookup<true>(gt, p, logQ) : f32_lookup<false>(gt, p, logQ);
         lev[off + i] = make_float2(w.x, -w.y);
       }
-      off += M;
+      off += n;
     }
   }
+  if (threadIdx.x == 0) {
+    mbar_init(&full_bar, 1);
+    fence_mbar_init();
+  }
   griddep_wait();   // launched behind the H kernel (programmatic dependent launch)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&full_bar, bytes);
+    bulk_load(raw, src, bytes, &full_bar);
+  }
 
   // outputs of this thread: l = -K + threadIdx.x + blockDim.x i
   float2 acc[kFOwnMax];
 #pragma unroll
   for (int i = 0; i < kFOwnMax; ++i) acc[i] = make_float2(0.f, 0.f);
-  const float2* src = ar.poly + (size_t)(k - 1) * P * L;
-  for (int a0 = 0; a0 < P; a0 += nfft) {
-    __syncthreads();   // the previous range's sums have read the buffers (and the levels are built)
-    const float2* g = src + (size_t)a0 * L;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int a0 = 0; a0 < P && ok; a0 += nfft) {
+    ok = mbar_wait(&full_bar, phase, st, 90);
+    phase ^= 1u;
+    if (!ok) break;   // FCFS_ETIMEOUT is recorded; the copy did not land
     float2 *X = bufA, *Y = bufB;
-    // first pass straight from global memory
-    if (f0 == 1) stockham_pass<2, true>(g, X, lev, logL, nfft, 1);
-    else if (f0 == 2) stockham_pass<4, true>(g, X, lev, logL, nfft, 1);
-    else if (f0 == 3) stockham_pass<8, true>(g, X, lev, logL, nfft, 1);
-    else stockham_pass<16, true>(g, X, lev, logL, nfft, 1);
-    __syncthreads();
+    const TwLevel none{lev, lev, 0};
+    if (f0 == 1) stockham_pass<2, true>(raw, X, none, logL, nfft, 1);
+    else if (f0 == 2) stockham_pass<4, true>(raw, X, none, logL, nfft, 1);
+    else if (f0 == 3) stockham_pass<8, true>(raw, X, none, logL, nfft, 1);
+    else stockham_pass<16, true>(raw, X, none, logL, nfft, 1);
+    __syncthreads();   // raw is read: the next range's copy may land in it
+    if (threadIdx.x == 0 && a0 + nfft < P) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&full_bar, bytes);
+      bulk_load(raw, src + (size_t)(a0 + nfft) * L, bytes, &full_bar);
+    }
     int off = 0;
     for (int lm = f0 + 4; lm <= logL; lm += 4) {
-      stockham_pass<16, false>(X, Y, lev + off, logL, nfft, 1 << (lm - 4));
-      off += 1 << lm;
+      const TwLevel tl{lev + off, lev + off + (lm <= 8 ? 0 : (1 << (lm - 6))), lm <= 8 ? 0 : 1};
+      stockham_pass<16, false>(X, Y, tl, logL, nfft, 1 << (lm - 4));
+      off += level_entries(lm);
       float2* t = X;
       X = Y;
       Y = t;
@@ -200,7 +242,9 @@ __global__ void __launch_bounds__(NT) fft_y_kernel(FftArgs ar) {
         acc[i].y = fmaf(w.x, d.y, fmaf(-w.y, d.x, acc[i].y));
       }
     }
+    __syncthreads();   // the sums have read X before the next range's passes overwrite it
   }
+  if (!ok) return;
   // F(k, l) = -T^2 / (4 pi^2 k l) G(k, l) for l != 0 (the axis lines come from the
   // exact integer sums); F(-k, -l) = conj F(k, l)
   const long long W = 2LL * K + 1;
@@ -229,13 +273,16 @@ __global__ void axis_out_kernel(Plan pl, uint8_t* ws, float2* __restrict__ F, lo
 
 }  // namespace
 
-// Shared memory of the FFT kernel for L points: two padded buffers and the
-// twiddle levels (at most L (1 + 1/16 + 1/256 + ...) entries).
+// Shared memory of the FFT kernel for L points: the bulk-copy buffer, two
+// padded buffers and the twiddle levels.
 size_t fft_y_smem(int logL) {
   const size_t L = (size_t)1 << logL;
   const size_t pts = std::max<size_t>(L, kFBufPts);
-  const size_t buf = pts + (pts >> 4) + 1;
-  return (2 * buf + L + L / 15 + 16) * 8;
+  const size_t buf = (pts + (pts >> 4) + 2) & ~(size_t)1;
+  size_t lev = 0;
+  const int f0 = (logL & 3) ? (logL & 3) : 4;
+  for (int lm = f0 + 4; lm <= logL; lm += 4) lev += (size_t)level_entries(lm);
+  return (pts + 2 * buf + lev) * 8;
 }
 
 // FFT length for a period T and cut-off K: a power of two >= 2K (no two wanted

@@ -167,61 +167,68 @@ __device__ __forceinline__ void split2h(float v0, float v1, uint32_t& hi, uint32
 //     s_a e^{j k x_a} (2 - (1 - e^{j k w}))   (equal signs), or s_a e^{j k x_a} (alone),
 // so an edge's two corners cancel in the factor D_k = 1 - e^{j k w} before any
 // rounding, and D_k is carried with a relative error of a few ulp however small it
-// is (versine tables; D_{k+1} = D_k + D_1 - D_k D_1 stays free of cancellation).
+// is (versine tables; D_{k+32} = D_k + D_32 - D_k D_32 stays free of cancellation).
 // A lane owns the 8 frequencies k0 + 32 i (the 32 lanes of a warp cover 256
 // consecutive frequencies, so their table reads fall on distinct banks): the
 // anchors at k0 come from two-level tables at the exact integer phase, the
-// next 7 by angle addition (A_{k+32} = A_k e^{j 32 x_a}) and the D recurrence
-// D_{k+32} = D_k + D_32 - D_k D_32.  Rows are summed
-// in FP32 in the sorted order, so repeated calls are bit-identical.  One pass
-// covers 256 frequencies of the item's 64 rows in a shared-memory tile, written
-// out coalesced in the output format:
+// next 7 by angle addition (A_{k+32} = A_k e^{j 32 x_a}) and the D recurrence;
+// the pair's steps e^{j 32 x_a} and D_32 are formed once per item.  Rows are
+// summed in FP32 in the sorted order, so repeated calls are bit-identical.
+// Output formats:
 //   kHRowsFp16: FP16 hi/lo rows 2(k-1) (Re) and 2(k-1)+1 (Im), columns y (the
-//               tensor-core contraction over y);
+//               tensor-core contraction over y); a pass covers 256 frequencies
+//               of the item's 64 rows in a shared-memory tile, written out
+//               coalesced (512 threads, one CTA per SM);
 //   kHPolyF32:  conj(H) as complex FP32 in polyphase order [k-1][a][b],
 //               y = a + P b (the pruned FFT along y), row T folded onto row 0
-//               (e^{-j 2 pi l T / T} = 1).
+//               (e^{-j 2 pi l T / T} = 1); each lane stores its row's values
+//               directly (the item's rows fill whole 32-byte sectors of each
+//               (k, a) run in L2), so work units (row, pass) need no barrier
+//               (256 threads, two CTAs per SM).
 // Items with more corners than the sort holds fall back to exact 64-bit
 // fixed-point sums from the integer quarter-wave table (order-free, exact up to
 // the table's rounding), written in the same formats.
 constexpr int kHY = 64;                 // rows per item
-constexpr int kHThreads = 512;          // 16 warps
-constexpr int kHWarps = kHThreads / 32;
-constexpr int kHPassF = 256;            // frequencies per pass (a run of 8 per lane)
+constexpr int kHPassF = 256;            // frequencies per pass (8 per lane)
 constexpr int kHCap = 4096;             // corners sorted in shared memory (fast path)
+constexpr int kHPairMax = kHCap / 2 + kHY;   // pairs of an item: sum of ceil(n_row / 2)
 constexpr int kHLd = kHPassF + 2;       // tile row stride (float2; rows stay 16-byte aligned)
 constexpr int kHTabMax = 256;           // two-level table entries per level (T <= 2^16)
 constexpr int kHCacheFB = 2048;         // fallback: corners staged in shared memory
 constexpr int kHRowsFp16 = 0, kHPolyF32 = 1;
 
-constexpr size_t kHTileBytes = (size_t)kHY * kHLd * 8;
-constexpr size_t kHPairBytes = (size_t)kHCap * 8;
-constexpr size_t kHTabBytes = (size_t)4 * kHTabMax * 8;
-constexpr size_t kHMainBytes = kHTileBytes + kHPairBytes;   // fast path tile + pairs | fallback levels + cache
+template <int FMT>
+struct HCfg {
+  static constexpr int threads = FMT == kHRowsFp16 ? 512 : 256;
+  static constexpr int min_blocks = FMT == kHRowsFp16 ? 1 : 2;
+  static constexpr size_t tile = FMT == kHRowsFp16 ? (size_t)kHY * kHLd * 8 : (size_t)kHCap * 4;   // tile | keys
+  static constexpr size_t meta = tile;                                  // uint2 [kHPairMax]
+  static constexpr size_t cst = meta + (size_t)kHPairMax * 8;           // float4 [kHPairMax]
+  static constexpr size_t tabs = cst + (size_t)kHPairMax * 16;          // float2 [4][kHTabMax]
+  static constexpr size_t rows = tabs + (size_t)4 * kHTabMax * 8;       // int [2][kHY + 2]
+  static constexpr size_t total = rows + (size_t)2 * (kHY + 2) * 4 + 16;
+};
 
-size_t hyb_h_smem(int T) {
-  (void)T;
-  return kHMainBytes + kHTabBytes + (size_t)2 * (kHY + 2) * 4 + 64;
-}
+size_t hyb_h_smem(int fmt) { return fmt == kHRowsFp16 ? HCfg<kHRowsFp16>::total : HCfg<kHPolyF32>::total; }
 
 // Two-level tables of e^{j 2 pi p / T} (W) and of the versine D(p) = 1 - e^{j 2 pi p / T}:
-// p = u 2^f + v; W(p) = Wc[u] Wf[v]; for D the phase is taken signed, p = i 2^f + b
-// with |b| <= 2^(f-1) <= |i 2^f| / 2, D(p) = Dc[i] + Wc[i] Df[b] (no cancellation).
+// p = u 2^f + v, W(p) = Wc[u] Wf[v].  D uses D(T - q) = conj D(q) to take q <= T/2,
+// then D(q) = Dc[i] + Wc[i] Df[b] (q = i 2^f + b): both terms turn by at most a
+// right angle from each other, so the sum has no cancellation.
 struct HTabs {
   const float2 *Wc, *Wf, *Dc, *Df;
-  uint32_t f, fm, ncm, T, half;
+  uint32_t f, fm, T, half;
 };
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.y, b.x, a.x * b.y));
 }
 __device__ __forceinline__ float2 tab_w(const HTabs& t, uint32_t p) { return cmul(t.Wc[p >> t.f], t.Wf[p & t.fm]); }
 __device__ __forceinline__ float2 tab_d(const HTabs& t, uint32_t p) {
-  const int ps = (int)p - (p >= t.half ? (int)t.T : 0);
-  const int i = (ps + (int)(t.fm + 1) / 2) >> t.f;   // nearest coarse point (floor shift)
-  const int b = ps - (i << t.f);
-  const uint32_t iu = (uint32_t)i & t.ncm, bu = (uint32_t)b & t.fm;
-  const float2 c = t.Dc[iu], w = t.Wc[iu], d = t.Df[bu];
-  return make_float2(c.x + fmaf(w.x, d.x, -(w.y * d.y)), c.y + fmaf(w.y, d.x, w.x * d.y));
+  const bool neg = p > t.half;
+  const uint32_t q = neg ? t.T - p : p;
+  const float2 c = t.Dc[q >> t.f], w = t.Wc[q >> t.f], d = t.Df[q & t.fm];
+  const float im = c.y + fmaf(w.y, d.x, w.x * d.y);
+  return make_float2(c.x + fmaf(w.x, d.x, -(w.y * d.y)), neg ? -im : im);
 }
 // 1 - e^{j theta} from cos and sin: 1 - cos as sin^2 / (1 + cos) where cos >= 0
 __device__ __forceinline__ float2 versine(float2 cs) {
@@ -230,15 +237,21 @@ __device__ __forceinline__ float2 versine(float2 cs) {
 }
 
 // A staged corner of the fallback: the phase k x mod T of every frequency k is
-// read at index k u (mod 4 Q) of the decimated level that starts at lbase
-// (quarter period Q = 2^lq; u odd unless x mod T is a multiple of T/4), which
-// keeps the 32 consecutive frequencies of a warp on distinct banks; sflip = 1 for s = -1.
+// read at index k u (mod 4 Q) of the level that starts at lbase (quarter period
+// Q = 2^lq); sflip = 1 for s = -1.  With decimated levels in shared memory
+// (DEC), x = 2^e u reads level e, which keeps the 32 consecutive frequencies of
+// a warp on distinct banks; without them every corner reads level 0.
+template <bool DEC>
 __device__ __forceinline__ int4 stage_corner(uint32_t xm, int sgn, int logQ) {
-  int e = xm ? __ffs(xm) - 1 : 0;
-  uint32_t u = xm >> e;
-  if (e > logQ - 1) {   // x a multiple of T/4 (or 0): level 0 reads at most 4 entries
-    e = 0;
-    u = xm;
+  int e = 0;
+  uint32_t u = xm;
+  if (DEC) {
+    e = xm ? __ffs(xm) - 1 : 0;
+    u = xm >> e;
+    if (e > logQ - 1) {   // x a multiple of T/4 (or 0): level 0 reads at most 4 entries
+      e = 0;
+      u = xm;
+    }
   }
   const int lq = logQ - e;
   return make_int4((int)u, level_offset(e, logQ), lq | ((sgn < 0 ? 1 : 0) << 8), 1 << lq);
@@ -258,35 +271,62 @@ __device__ __forceinline__ int item_rows(int y0, int T) {
   return FMT == kHRowsFp16 ? min(kHY, T + 1 - y0) : min(kHY, T - y0);
 }
 
-// Fallback for an item with more than kHCap corners: exact fixed-point sums,
-// thread (group q of 4, frequency t of 128) over its y octets q, q + 4.
+// The corner range(s) of an item in the grouping: [a, b) and, for the
+// polyphase item holding row 0, row T's corners [fa, fa + nf) after it.
+struct HRange {
+  int a, b, fa, nf;
+  __device__ __forceinline__ int count() const { return (b - a) + nf; }
+  __device__ __forceinline__ int corner(const int* perm, int i) const {
+    return i < b - a ? perm[a + i] : perm[fa + i - (b - a)];
+  }
+};
 template <int FMT>
-__device__ void h_item_exact(const Plan& pl, const Groups& g, int clip, int y0, int* lv, int4* vc, int* soff,
-                             const HOut& out) {
+__device__ __forceinline__ HRange item_range(const Groups& g, int y0, int T) {
+  HRange r;
+  r.a = g.start[min(y0, T + 1)];
+  r.b = g.start[min(y0 + kHY, T + 1)];
+  r.fa = 0;
+  r.nf = 0;
+  if (FMT == kHPolyF32 && y0 == 0 && T >= kHY) {   // below one item, row T is already in [a, b)
+    r.fa = g.start[T];
+    r.nf = g.start[T + 1] - g.start[T];
+  }
+  return r;
+}
+
+// Fallback for an item with more than kHCap corners: exact fixed-point sums,
+// thread (group q, frequency t of 128) over the item's y octets q, q + G, ...
+// (G = blockDim / 128).  DEC: the decimated levels are in shared memory (lv);
+// otherwise level 0 is read from the workspace's fixed-point table.
+template <int FMT, bool DEC>
+__device__ void h_item_exact(const Plan& pl, const Groups& g, int clip, int y0, const int* lv, int4* vc,
+                             int* soff, const HOut& out) {
   const int T = pl.T, K = pl.K, logQ = pl.logT - 2;
   const uint32_t mask = (uint32_t)T - 1u;
   const float inv_q = ldexpf(1.f, -pl.fixq);
   const int small_group = (1 << (31 - pl.fixq)) - 1;   // |sum| < 2^31 in int32
   const int* perm = g.perm;
   const int nrows = item_rows<FMT>(y0, T);
-  const int a = g.start[min(y0, T + 1)], b = g.start[min(y0 + kHY, T + 1)];
-  // row T folded onto row 0 (polyphase output, the item holding row 0)
-  const bool fold = FMT == kHPolyF32 && y0 == 0;
-  const int fa = fold ? g.start[T] : 0, fb = fold ? g.start[T + 1] : 0;
-  const bool cached = (b - a) + (fb - fa) <= kHCacheFB;
-  for (int i = threadIdx.x; i <= kHY; i += blockDim.x) soff[i] = g.start[min(y0 + i, T + 1)] - a;
-  if (threadIdx.x == 0) soff[kHY + 1] = (b - a) + (fb - fa);
+  const HRange rg = item_range<FMT>(g, y0, T);
+  const int n = rg.count();
+  const bool cached = n <= kHCacheFB;
+  for (int i = threadIdx.x; i <= kHY; i += blockDim.x) soff[i] = g.start[min(y0 + i, T + 1)] - rg.a;
   if (cached)
-    for (int i = threadIdx.x; i < (b - a) + (fb - fa); i += blockDim.x) {
-      const int v = i < b - a ? perm[a + i] : perm[fa + i - (b - a)];
-      vc[i] = stage_corner((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int v = rg.corner(perm, i);
+      vc[i] = stage_corner<DEC>((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
     }
   __syncthreads();
+  // row T onto row 0 (polyphase): staged after the item's range, or inside it below one item
+  const bool fold = FMT == kHPolyF32 && y0 == 0;
+  const int f0 = fold ? (rg.nf ? rg.b - rg.a : soff[min(T, kHY)]) : 0;
+  const int f1 = fold ? (rg.nf ? n : soff[min(T + 1, kHY)]) : 0;
+  const int G = blockDim.x / 128;
   const int q = threadIdx.x / 128, t = threadIdx.x % 128;
   for (int pass = 0; pass < (K + 127) / 128; ++pass) {
     const int k = pass * 128 + 1 + t;
     if (k > K) continue;
-    for (int oc = q; oc < kHY / 8; oc += 4) {
+    for (int oc = q; oc < kHY / 8; oc += G) {
       float fcv[8], fsv[8];
 #pragma unroll
       for (int yy = 0; yy < 8; ++yy) {
@@ -296,8 +336,8 @@ __device__ void h_item_exact(const Plan& pl, const Groups& g, int clip, int y0, 
           if (cached) {
             cn = vc[i];
           } else {
-            const int v = i < b - a ? perm[a + i] : perm[fa + i - (b - a)];
-            cn = stage_corner((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
+            const int v = rg.corner(perm, i);
+            cn = stage_corner<DEC>((uint32_t)__ldg(pl.vx + v) & mask, (int)__ldg(pl.vsg + v), logQ);
           }
           const int lq = cn.z & 0xFF, Q = cn.w;
           const uint32_t sf = (uint32_t)cn.z >> 8;
@@ -305,17 +345,17 @@ __device__ void h_item_exact(const Plan& pl, const Groups& g, int clip, int y0, 
           const uint32_t qd = p >> lq, r = p & (uint32_t)(Q - 1);
           const bool odd = qd & 1u;
           const int* L = lv + cn.y;
-          const int c = L[odd ? Q - r : r], sn = L[odd ? r : Q - r];
+          const int c = DEC ? L[odd ? Q - r : r] : __ldg(L + (odd ? Q - r : r));
+          const int sn = DEC ? L[odd ? r : Q - r] : __ldg(L + (odd ? r : Q - r));
           // cos < 0 in quadrants 1, 2; sin < 0 in quadrants 2, 3; s = -1 flips both
           ac_ += ((((qd + 1u) >> 1) & 1u) ^ sf) ? -c : c;
           as_ += ((qd >> 1) ^ sf) ? -sn : sn;
         };
-        // the corner ranges of row y (and of row T when it is folded onto row 0)
         int i0 = soff[y], i1 = soff[y + 1], j0 = 0, j1 = 0;
         if (y >= nrows) i1 = i0;
         if (fold && y == 0) {
-          j0 = b - a;
-          j1 = soff[kHY + 1];
+          j0 = f0;
+          j1 = f1;
         }
         long long ac = 0, as = 0;
         if ((i1 - i0) + (j1 - j0) <= small_group) {   // warp-uniform
@@ -356,25 +396,21 @@ __device__ void h_item_exact(const Plan& pl, const Groups& g, int clip, int y0, 
   }
 }
 
-// Fast path of one item (see above).  The tile holds 64 rows x 256 frequencies.
+// Fast-path staging of an item: sort keys (row << 17 | x << 1 | sign), the
+// first sorted corner of each row (rowc), the first pair of each row (rowp), and
+// per pair meta {x_a | kind << 20 | sign_a << 22, w} (kind 0: opposite signs, 1:
+// equal, 2: alone) and steps {e^{j 32 x_a}, D_32}.
 template <int FMT>
-__device__ void h_item_pairs(const Plan& pl, const Groups& g, int clip, int y0, int ncorner, float2* tile,
-                             uint2* pairs, int* rowc, int* rowp, int* s_row, const HTabs& tb, const HOut& out) {
-  const int T = pl.T, K = pl.K;
+__device__ void h_stage(const Plan& pl, const Groups& g, int y0, const HRange& rg, uint32_t* keys, uint2* meta,
+                        float4* cst, int* rowc, int* rowp, const HTabs& tb) {
+  const int T = pl.T, n = rg.count(), tid = threadIdx.x, nt = blockDim.x;
   const uint32_t mask = (uint32_t)T - 1u;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int nrows = item_rows<FMT>(y0, T);
-  const int a = g.start[min(y0, T + 1)], b = g.start[min(y0 + kHY, T + 1)];
-  const bool fold = FMT == kHPolyF32 && y0 == 0;
-  const int fa = fold ? g.start[T] : 0;
-  // 1. sort keys (row << 17 | x << 1 | sign), padded to a power of two (in the tile)
-  uint32_t* keys = reinterpret_cast<uint32_t*>(tile);
   int npad = 1;
-  while (npad < ncorner) npad <<= 1;
-  for (int i = tid; i < npad; i += kHThreads) {
+  while (npad < n) npad <<= 1;
+  for (int i = tid; i < npad; i += nt) {
     uint32_t key = 0xFFFFFFFFu;
-    if (i < ncorner) {
-      const int v = i < b - a ? g.perm[a + i] : g.perm[fa + i - (b - a)];
+    if (i < n) {
+      const int v = rg.corner(g.perm, i);
       const int yv = __ldg(pl.vy + v);
       const int yl = (FMT == kHPolyF32 && yv == T) ? 0 : yv - y0;
       const uint32_t xm = (uint32_t)__ldg(pl.vx + v) & mask;
@@ -385,7 +421,7 @@ __device__ void h_item_pairs(const Plan& pl, const Groups& g, int clip, int y0, 
   __syncthreads();
   for (int kk = 2; kk <= npad; kk <<= 1)
     for (int j = kk >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < npad; i += kHThreads) {
+      for (int i = tid; i < npad; i += nt) {
         const int ixj = i ^ j;
         if (ixj > i) {
           const uint32_t u = keys[i], w = keys[ixj];
@@ -397,9 +433,8 @@ __device__ void h_item_pairs(const Plan& pl, const Groups& g, int clip, int y0, 
       }
       __syncthreads();
     }
-  // 2. row starts (first sorted key of each row) and pair starts
-  for (int r = tid; r <= kHY; r += kHThreads) {
-    int lo = 0, hi = ncorner;   // first index whose row is >= r
+  for (int r = tid; r <= kHY; r += nt) {
+    int lo = 0, hi = n;   // first index whose row is >= r
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
       if ((int)(keys[mid] >> 17) < r) lo = mid + 1; else hi = mid;
@@ -407,17 +442,21 @@ __device__ void h_item_pairs(const Plan& pl, const Groups& g, int clip, int y0, 
     rowc[r] = lo;
   }
   __syncthreads();
-  if (tid == 0) {
-    int acc = 0;
-    for (int r = 0; r < kHY; ++r) {
-      rowp[r] = acc;
-      acc += (rowc[r + 1] - rowc[r] + 1) >> 1;
+  if (tid < 32) {   // rowp = exclusive scan of ceil(n_row / 2) over the 64 rows
+    const int c0 = (rowc[2 * tid + 1] - rowc[2 * tid] + 1) >> 1;
+    const int c1 = (rowc[2 * tid + 2] - rowc[2 * tid + 1] + 1) >> 1;
+    int incl = c0 + c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t2 = __shfl_up_sync(0xffffffffu, incl, o);
+      if (tid >= o) incl += t2;
     }
-    rowp[kHY] = acc;
+    rowp[2 * tid] = incl - c0 - c1;
+    rowp[2 * tid + 1] = incl - c1;
+    if (tid == 31) rowp[kHY] = incl;
   }
   __syncthreads();
-  // 3. pairs: {x_a | kind << 20 | sign_a << 22, w}; kind 0 opposite signs, 1 equal, 2 alone
-  for (int i = tid; i < ncorner; i += kHThreads) {
+  for (int i = tid; i < n; i += nt) {
     const uint32_t ka = keys[i];
     const int r = (int)(ka >> 17), pos = i - rowc[r];
     if (pos & 1) continue;
@@ -428,19 +467,62 @@ __device__ void h_item_pairs(const Plan& pl, const Groups& g, int clip, int y0, 
       w = ((kb2 >> 1) & 0xFFFFu) - xa;
       kind = (kb2 & 1u) == sa ? 1u : 0u;
     }
-    pairs[rowp[r] + (pos >> 1)] = make_uint2(xa | (kind << 20) | (sa << 22), w);
+    const int p = rowp[r] + (pos >> 1);
+    meta[p] = make_uint2(xa | (kind << 20) | (sa << 22), w);
+    const float2 S = tab_w(tb, (32u * xa) & mask), D = tab_d(tb, (32u * w) & mask);
+    cst[p] = make_float4(S.x, S.y, D.x, D.y);
   }
-  __syncthreads();   // the keys (in the tile) are dead from here on
+  __syncthreads();   // the keys are dead from here on
+}
 
-  // 4. passes of 256 frequencies
+// The 8 sums of one row for frequencies k0 + 32 i (acc zeroed by the caller).
+__device__ __forceinline__ void row_sums(const uint2* __restrict__ meta, const float4* __restrict__ cst, int p0,
+                                         int p1, uint32_t k0, uint32_t mask, const HTabs& tb, float2 (&acc)[8]) {
+  for (int p = p0; p < p1; ++p) {
+    const uint2 pr = meta[p];
+    const float4 c = cst[p];
+    const uint32_t xa = pr.x & 0xFFFFFu, kind = (pr.x >> 20) & 3u, w = pr.y;
+    const float2 S = make_float2(c.x, c.y);
+    float2 A = tab_w(tb, (k0 * xa) & mask);
+    if (pr.x >> 22) A = make_float2(-A.x, -A.y);
+    if (kind == 2u) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        acc[j].x += A.x;
+        acc[j].y += A.y;
+        A = cmul(A, S);
+      }
+    } else {
+      const float2 D1 = make_float2(c.z, c.w);
+      float2 D = tab_d(tb, (k0 * w) & mask);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float2 E = kind ? make_float2(2.f - D.x, -D.y) : D;
+        acc[j].x = fmaf(A.x, E.x, fmaf(-A.y, E.y, acc[j].x));
+        acc[j].y = fmaf(A.x, E.y, fmaf(A.y, E.x, acc[j].y));
+        A = cmul(A, S);
+        // D_{k+32} = D_k + D_32 - D_k D_32
+        const float dr = fmaf(D.y, D1.y, fmaf(-D.x, D1.x, D.x + D1.x));
+        const float di = fmaf(-D.x, D1.y, fmaf(-D.y, D1.x, D.y + D1.y));
+        D = make_float2(dr, di);
+      }
+    }
+  }
+}
+
+// kHRowsFp16 fast path: passes of 256 frequencies over the item's 64 rows into
+// the tile, written out as FP16 hi/lo row segments.
+__device__ void h_rows_fp16(const Plan& pl, int clip, int y0, float2* tile, const uint2* meta, const float4* cst,
+                            const int* rowp, int* s_row, const HTabs& tb, const HOut& out) {
+  const int T = pl.T, K = pl.K, tid = threadIdx.x, lane = tid & 31;
+  const uint32_t mask = (uint32_t)T - 1u;
+  const int nrows = item_rows<kHRowsFp16>(y0, T);
   const int npass = (K + kHPassF - 1) / kHPassF;
-  const int P = FMT == kHPolyF32 ? 1 << out.logP : 1;
   for (int pass = 0; pass < npass; ++pass) {
     const int kb = pass * kHPassF + 1;
     if (tid == 0) *s_row = 0;
     __syncthreads();
     const uint32_t k0 = (uint32_t)(kb + lane);
-    const bool live = (int)k0 <= K;
     for (;;) {
       int r = 0;
       if (lane == 0) r = atomicAdd(s_row, 1);
@@ -449,93 +531,113 @@ __device__ void h_item_pairs(const Plan& pl, const Groups& g, int clip, int y0, 
       float2 acc[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
-      if (live && r < nrows) {
-        for (int p = rowp[r]; p < rowp[r + 1]; ++p) {
-          const uint2 pr = pairs[p];
-          const uint32_t xa = pr.x & 0xFFFFFu, kind = (pr.x >> 20) & 3u, w = pr.y;
-          const float2 S = tab_w(tb, (32u * xa) & mask);
-          float2 A = tab_w(tb, (k0 * xa) & mask);
-          if (pr.x >> 22) A = make_float2(-A.x, -A.y);
-          if (kind == 2u) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              acc[j].x += A.x;
-              acc[j].y += A.y;
-              A = cmul(A, S);
-            }
-          } else {
-            const float2 D1 = tab_d(tb, (32u * w) & mask);
-            float2 D = tab_d(tb, (k0 * w) & mask);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float2 E = kind ? make_float2(2.f - D.x, -D.y) : D;
-              acc[j].x = fmaf(A.x, E.x, fmaf(-A.y, E.y, acc[j].x));
-              acc[j].y = fmaf(A.x, E.y, fmaf(A.y, E.x, acc[j].y));
-              A = cmul(A, S);
-              // D_{k+32} = D_k + D_32 - D_k D_32
-              const float dr = fmaf(D.y, D1.y, fmaf(-D.x, D1.x, D.x + D1.x));
-              const float di = fmaf(-D.x, D1.y, fmaf(-D.y, D1.x, D.y + D1.y));
-              D = make_float2(dr, di);
-            }
-          }
-        }
-      }
+      if ((int)k0 <= K && r < nrows) row_sums(meta, cst, rowp[r], rowp[r + 1], k0, mask, tb, acc);
       float2* row = tile + (size_t)r * kHLd + lane;
 #pragma unroll
       for (int j = 0; j < 8; ++j) row[32 * j] = acc[j];
     }
     __syncthreads();
-    // write the tile out
-    if (FMT == kHRowsFp16) {
-      for (int e = tid; e < kHPassF * (kHY / 8); e += kHThreads) {
-        const int kl = e % kHPassF, oc = e / kHPassF, k = kb + kl;
-        if (k > K) continue;
-        float fcv[8], fsv[8];
+    for (int e = tid; e < kHPassF * (kHY / 8); e += blockDim.x) {
+      const int kl = e % kHPassF, oc = e / kHPassF, k = kb + kl;
+      if (k > K) continue;
+      float fcv[8], fsv[8];
 #pragma unroll
-        for (int yy = 0; yy < 8; ++yy) {
-          const float2 v = tile[(size_t)(oc * 8 + yy) * kHLd + kl];
-          fcv[yy] = v.x;
-          fsv[yy] = v.y;
-        }
-        uint32_t hc[4], hs[4], lc[4], ls[4];
+      for (int yy = 0; yy < 8; ++yy) {
+        const float2 v = tile[(size_t)(oc * 8 + yy) * kHLd + kl];
+        fcv[yy] = v.x;
+        fsv[yy] = v.y;
+      }
+      uint32_t hc[4], hs[4], lc[4], ls[4];
 #pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-          split2h(fcv[2 * qq], fcv[2 * qq + 1], hc[qq], lc[qq]);
-          split2h(fsv[2 * qq], fsv[2 * qq + 1], hs[qq], ls[qq]);
-        }
-        const size_t rc = ((size_t)clip * pl.M2 + 2 * (k - 1)) * pl.ny_pad + y0 + 8 * oc, rs = rc + pl.ny_pad;
-        *reinterpret_cast<uint4*>(out.hi + rc) = make_uint4(hc[0], hc[1], hc[2], hc[3]);
-        *reinterpret_cast<uint4*>(out.hi + rs) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
-        *reinterpret_cast<uint4*>(out.lo + rc) = make_uint4(lc[0], lc[1], lc[2], lc[3]);
-        *reinterpret_cast<uint4*>(out.lo + rs) = make_uint4(ls[0], ls[1], ls[2], ls[3]);
+      for (int qq = 0; qq < 4; ++qq) {
+        split2h(fcv[2 * qq], fcv[2 * qq + 1], hc[qq], lc[qq]);
+        split2h(fsv[2 * qq], fsv[2 * qq + 1], hs[qq], ls[qq]);
       }
-    } else {
-      const int nb = nrows >> out.logP;   // b values of each residue a in this item
-      const size_t b0 = (size_t)(y0 >> out.logP);
-      for (int e = tid; e < kHPassF * P; e += kHThreads) {
-        const int kl = e % kHPassF, ar = e / kHPassF, k = kb + kl;
-        if (k > K) continue;
-        float2* dst = out.poly + ((size_t)(k - 1) * P + ar) * out.L + b0;
-        for (int bb = 0; bb < nb; ++bb) {
-          const float2 v = tile[(size_t)(ar + bb * P) * kHLd + kl];
-          dst[bb] = make_float2(v.x, -v.y);
-        }
-      }
+      const size_t rc = ((size_t)clip * pl.M2 + 2 * (k - 1)) * pl.ny_pad + y0 + 8 * oc, rs = rc + pl.ny_pad;
+      *reinterpret_cast<uint4*>(out.hi + rc) = make_uint4(hc[0], hc[1], hc[2], hc[3]);
+      *reinterpret_cast<uint4*>(out.hi + rs) = make_uint4(hs[0], hs[1], hs[2], hs[3]);
+      *reinterpret_cast<uint4*>(out.lo + rc) = make_uint4(lc[0], lc[1], lc[2], lc[3]);
+      *reinterpret_cast<uint4*>(out.lo + rs) = make_uint4(ls[0], ls[1], ls[2], ls[3]);
     }
     __syncthreads();
+  }
+}
+
+// kHPolyF32 fast path: work units (residue a, group of 4 b, pass) from a
+// counter.  A warp sums the unit's 4 rows y = a + P b (consecutive b), so each
+// lane ends with 4 consecutive b of each of its 8 frequencies: one 32-byte
+// sector of conj(H)[k-1][a][.] per frequency, stored directly.
+__device__ void h_poly_direct(const Plan& pl, int y0, const uint2* meta, const float4* cst, const int* rowp,
+                              int* s_row, const HTabs& tb, const HOut& out) {
+  const int T = pl.T, K = pl.K, lane = threadIdx.x & 31;
+  const uint32_t mask = (uint32_t)T - 1u;
+  const int nrows = item_rows<kHPolyF32>(y0, T);
+  const int npass = (K + kHPassF - 1) / kHPassF;
+  const int logP = out.logP, P = 1 << logP;
+  const int nb = nrows >> logP;            // b values of each residue in this item
+  const int ngrp = (nb + 3) >> 2;
+  const int nunit = P * ngrp;              // per pass
+  const size_t b0 = (size_t)(y0 >> logP);
+  if (threadIdx.x == 0) *s_row = 0;
+  __syncthreads();
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(s_row, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= nunit * npass) break;
+    const int pass = u / nunit, w = u % nunit, a = w % P, grp = w / P;
+    const uint32_t k0 = (uint32_t)(pass * kHPassF + 1 + lane);
+    if ((int)k0 > K) continue;   // lanes past K (last pass) idle; nothing below is warp-collective
+    float2 acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int bl = 4 * grp + i;
+      if (bl < nb) {
+        const int r = a + (bl << logP);
+        row_sums(meta, cst, rowp[r], rowp[r + 1], k0, mask, tb, acc[i]);
+      }
+    }
+    const size_t kstride = (size_t)32 * T;   // 32 frequencies further on
+    float2* dst = out.poly + ((size_t)(k0 - 1) * P + a) * out.L + b0 + 4 * grp;
+    if (4 * grp + 4 <= nb) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if ((int)k0 + 32 * j > K) break;
+        float4* d4 = reinterpret_cast<float4*>(dst + j * kstride);
+        d4[0] = make_float4(acc[0][j].x, -acc[0][j].y, acc[1][j].x, -acc[1][j].y);
+        d4[1] = make_float4(acc[2][j].x, -acc[2][j].y, acc[3][j].x, -acc[3][j].y);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if ((int)k0 + 32 * j > K) break;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (4 * grp + i < nb) dst[j * kstride + i] = make_float2(acc[i][j].x, -acc[i][j].y);
+      }
+    }
   }
 }
 
 // Items (clip, 64-row chunk) are taken from a work counter (clips differ in
 // size by orders of magnitude, so a static split leaves CTAs idle).
 template <int FMT>
-__global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* ws, HOut out) {
+__global__ void __launch_bounds__(HCfg<FMT>::threads, HCfg<FMT>::min_blocks)
+    hyb_h_kernel(Plan pl, uint8_t* ws, HOut out) {
+  using C = HCfg<FMT>;
   extern __shared__ __align__(16) uint8_t sm[];
   __shared__ int s_item, s_row;
   const int T = pl.T, logT = pl.logT;
-  uint8_t* main = sm;
-  float2* tabs = reinterpret_cast<float2*>(sm + kHMainBytes);
-  int* rowc = reinterpret_cast<int*>(sm + kHMainBytes + kHTabBytes);
+  uint32_t* keys = reinterpret_cast<uint32_t*>(sm);
+  float2* tile = reinterpret_cast<float2*>(sm);
+  uint2* meta = reinterpret_cast<uint2*>(sm + C::meta);
+  float4* cst = reinterpret_cast<float4*>(sm + C::cst);
+  float2* tabs = reinterpret_cast<float2*>(sm + C::tabs);
+  int* rowc = reinterpret_cast<int*>(sm + C::rows);
   int* rowp = rowc + kHY + 2;
   const int nclips = pl.batch ? pl.n_clips : 1;
   unsigned* counter = reinterpret_cast<unsigned*>(ws + kSyncOffset) + 2;   // zeroed by the prep kernel
@@ -549,18 +651,16 @@ __global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* w
     for (uint32_t i = threadIdx.x; i < nc + nf; i += blockDim.x) {
       const bool coarse = i < nc;
       const uint32_t u = coarse ? i : i - nc;
-      const uint32_t pw = coarse ? u << f : u;                               // W phase
-      const uint32_t pd = coarse ? u << f : (u < nf / 2 ? u : (uint32_t)T - (nf - u));   // D phase (signed fine)
-      const float2 w = pl.full ? f32_lookup<true>(gt, pw, logQ) : f32_lookup<false>(gt, pw, logQ);
-      const float2 wd = pl.full ? f32_lookup<true>(gt, pd, logQ) : f32_lookup<false>(gt, pd, logQ);
+      const uint32_t p = coarse ? u << f : u;
+      const float2 w = pl.full ? f32_lookup<true>(gt, p, logQ) : f32_lookup<false>(gt, p, logQ);
       (coarse ? Wc : Wf)[u] = w;
-      (coarse ? Dc : Df)[u] = versine(wd);
+      (coarse ? Dc : Df)[u] = versine(w);
     }
   }
-  const HTabs tb{Wc, Wf, Dc, Df, f, nf - 1u, nc - 1u, (uint32_t)T, (uint32_t)T / 2u};
+  const HTabs tb{Wc, Wf, Dc, Df, f, nf - 1u, (uint32_t)T, (uint32_t)T / 2u};
   const int nchunk = FMT == kHRowsFp16 ? pl.ny_pad / kHY : max(1, T / kHY);
   const long long nitems = (long long)nclips * nchunk;
-  bool levels = false;   // the fallback's fixed-point levels are in shared memory
+  bool levels = false;   // the fallback's decimated levels are in shared memory
   for (;;) {
     __syncthreads();   // the previous item's readers are done (and the tables are built)
     if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
@@ -571,19 +671,19 @@ __global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* w
     const int y0 = chunk * kHY;
     const Groups g = pl.batch ? groups_clip(ws + pl.off_ycnt, T, pl.ny_pad, nclips, clip, pl.V)
                               : groups_at(ws + pl.off_ycnt, T, pl.ny_pad);
-    const int a = g.start[min(y0, T + 1)], b = g.start[min(y0 + kHY, T + 1)];
-    int n = b - a;
-    if (FMT == kHPolyF32 && y0 == 0) n += g.start[T + 1] - g.start[T];
-    if (FMT == kHPolyF32 && T < kHY) n = g.start[T + 1] - g.start[0];   // one item: rows 0..T-1 and T
-    if (n <= kHCap) {
-      levels = false;   // the tile overwrites them
-      h_item_pairs<FMT>(pl, g, clip, y0, n, reinterpret_cast<float2*>(main),
-                        reinterpret_cast<uint2*>(main + kHTileBytes), rowc, rowp, &s_row, tb, out);
-    } else {
-      int* lv = reinterpret_cast<int*>(main);
-      int4* vc = reinterpret_cast<int4*>(main + align_up(axis_levels_ints(T) * 4, 16));
+    const HRange rg = item_range<FMT>(g, y0, T);
+    if (rg.count() <= kHCap) {
+      levels = false;   // the fast path overwrites them
+      h_stage<FMT>(pl, g, y0, rg, keys, meta, cst, rowc, rowp, tb);
+      if (FMT == kHRowsFp16)
+        h_rows_fp16(pl, clip, y0, tile, meta, cst, rowp, &s_row, tb, out);
+      else
+        h_poly_direct(pl, y0, meta, cst, rowp, &s_row, tb, out);
+    } else if (FMT == kHRowsFp16) {
+      // level 0 = the fixed-point quarter-wave table, then the decimated levels
+      int* lv = reinterpret_cast<int*>(sm);
+      int4* vc = reinterpret_cast<int4*>(sm + align_up(axis_levels_ints(T) * 4, 16));
       if (!levels) {
-        // level 0 = the fixed-point quarter-wave table, then the decimated levels
         const int* tq = reinterpret_cast<const int*>(ws + pl.off_tab_fix);
         for (int i = threadIdx.x; i <= T / 4; i += blockDim.x) lv[i] = tq[i];
         __syncthreads();
@@ -591,7 +691,10 @@ __global__ void __launch_bounds__(kHThreads, 1) hyb_h_kernel(Plan pl, uint8_t* w
         __syncthreads();
         levels = true;
       }
-      h_item_exact<FMT>(pl, g, clip, y0, lv, vc, rowc, out);
+      h_item_exact<FMT, true>(pl, g, clip, y0, lv, vc, rowc, out);
+    } else {
+      h_item_exact<FMT, false>(pl, g, clip, y0, reinterpret_cast<const int*>(ws + pl.off_tab_fix),
+                               reinterpret_cast<int4*>(sm), rowc, out);
     }
   }
 }
@@ -942,11 +1045,13 @@ static cudaError_t launch_h(const Plan& pl, uint8_t* ws, int fmt, cudaStream_t s
     out.L = 1 << pl.fft_logL;
     items = std::max(1, pl.T / kHY);
   }
-  const size_t hs = hyb_h_smem(pl.T);
+  const size_t hs = hyb_h_smem(fmt);
   auto kern = fmt == kHRowsFp16 ? hyb_h_kernel<kHRowsFp16> : hyb_h_kernel<kHPolyF32>;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), hs);
   if (e != cudaSuccess) return e;
-  kern<<<(int)std::min<long long>(items, sms), kHThreads, hs, st>>>(pl, ws, out);
+  const int threads = fmt == kHRowsFp16 ? HCfg<kHRowsFp16>::threads : HCfg<kHPolyF32>::threads;
+  const int per_sm = fmt == kHRowsFp16 ? HCfg<kHRowsFp16>::min_blocks : HCfg<kHPolyF32>::min_blocks;
+  kern<<<(int)std::min<long long>(items, (long long)per_sm * sms), threads, hs, st>>>(pl, ws, out);
   count_launch(1);
   return cudaGetLastError();
 }
