@@ -203,20 +203,18 @@ bool pair_enabled() { return g_pair != 0; }
 //   kGroupedFft  corners grouped by y, pruned FFT along y in FP32 (any precision:
 //                its error is below the plain FP32 path's).
 // The automatic choice takes the cheapest estimate (ms) among the forms the call
-// may take; the estimates are fitted to GB300 measurements of each form:
-//   direct, tensor cores   0.04 + 1.5e-11 V K^2        ((2K)^2 tensor MACs per corner)
+// may take; the estimates are fitted to GB300 measurements of each form's stages
+// (T = 2048 .. 65536, K = 128 .. 1024, V / (T + 1) = 0.8 .. 49):
+//   direct, tensor cores   0.028 + 1.5e-11 V K^2          ((2K)^2 tensor MACs per corner)
 //   direct, plain FP32     0.02 + 1.7e-10 V K^2
-//   grouped, tensor cores  0.08 + 4e-6 T + 1.8e-11 (T + 1) K^2 + h
-//   grouped, FFT           0.08 + 4e-6 T + 2e-9 K T + h
-//   h = 3.3e-10 V K (1 + 120 / chunks)   (the H kernel: K terms per corner over
-//                                         the chunks = T / 64 items of 64 rows)
-// (grouping and axis lines in the constant and T terms).
+//   grouped, tensor cores  g + 4.3e-10 V K p1 + 5.4e-9 T K   (H in FP16 rows, one CTA per SM)
+//                          + 1.35e-11 (T + 1) K^2             (contraction over y)
+//                          + 3.6e-9 K T + 3.5e-8 K^2          (axis lines, split-K sum)
+//   grouped, FFT           g + 3.8e-10 V K p2 + 1.24e-8 K T   (H in polyphase order, the FFT
+//                                                             along y and the axis lines)
+//   g = 0.055 + 6e-8 V (prep, grouping, launches); p1, p2 = the H kernel's CTA slots
+//   (one or two per SM) over its T / 64 items of 64 rows, at least 1.
 enum { kDirect = 0, kGroupedTc = 1, kGroupedFft = 2 };
-
-static double cost_h(double v, double t, double k) {
-  const double chunks = std::max(1.0, t / 64.0);
-  return 3.3e-10 * v * k * (1.0 + 120.0 / chunks);
-}
 
 static int forward_form(const Plan& pl, bool validate) {
   if (g_hybrid == 0 || validate || pl.V <= 0 || pl.logT > 16 || pl.cosine) return kDirect;
@@ -225,17 +223,20 @@ static int forward_form(const Plan& pl, bool validate) {
   if (g_hybrid == 2) return tc_ok ? kGroupedTc : kDirect;
   if (g_hybrid == 3) return fft_ok ? kGroupedFft : kDirect;
   const double v = (double)pl.V, k = (double)pl.K, t = (double)pl.T;
-  double best = pl.prec == FCFS_PREC_SPLIT_F16 ? 0.04 + 1.5e-11 * v * k * k : 0.02 + 1.7e-10 * v * k * k;
+  const double items = std::max(1.0, t / 64.0), sms = (double)sm_count();
+  const double g = 0.055 + 6e-8 * v;
+  double best = pl.prec == FCFS_PREC_SPLIT_F16 ? 0.028 + 1.5e-11 * v * k * k : 0.02 + 1.7e-10 * v * k * k;
   int form = kDirect;
   if (tc_ok) {
-    const double c = 0.08 + 4e-6 * t + 1.8e-11 * (t + 1.0) * k * k + cost_h(v, t, k);
+    const double c = g + 4.3e-10 * v * k * std::max(1.0, sms / items) + 5.4e-9 * t * k +
+                     1.35e-11 * (t + 1.0) * k * k + 3.6e-9 * k * t + 3.5e-8 * k * k;
     if (c < best) {
       best = c;
       form = kGroupedTc;
     }
   }
   if (fft_ok) {
-    const double c = 0.08 + 4e-6 * t + 2e-9 * k * t + cost_h(v, t, k);
+    const double c = g + 3.8e-10 * v * k * std::max(1.0, 2.0 * sms / items) + 1.24e-8 * k * t;
     if (c < best) {
       best = c;
       form = kGroupedFft;
