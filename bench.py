@@ -297,6 +297,38 @@ def traffic_per_launch():
     return None
 
 
+# committed ncu summaries that carry per-launch DRAM traffic: stage -> (file,
+# kernel line tag, the sources the kernel is built from)
+STAGE_TRAFFIC = {
+    "adj_tc_grouped": ("step_T65536_K1024.md", "adj_tc_kernel<1>", ("fcfs_adjoint_tc.cu", "fcfs_common.cuh")),
+    "h_poly": ("step_T65536_K1024.md", "hyb_h_kernel<1>", ("fcfs_hybrid.cu", "fcfs_common.cuh")),
+    "fft_y": ("step_T65536_K1024.md", "fft_y_kernel<256>", ("fcfs_fft.cu", "fcfs_common.cuh")),
+}
+
+
+def stage_traffic(stage):
+    """DRAM bytes per launch of a stage's kernel from its committed ncu summary,
+    if the summary was taken on the kernel's current sources, else None."""
+    import re
+    if stage not in STAGE_TRAFFIC:
+        return None
+    fname, tag, srcs = STAGE_TRAFFIC[stage]
+    try:
+        h = hashlib.sha256()
+        for name in srcs:
+            with open(os.path.join(ROOT, "paper_1010_5562_gb300", "csrc", name), "rb") as fh:
+                h.update(fh.read())
+        for line in open(os.path.join(ROOT, "profiles", fname)):
+            if line.startswith("- " + tag + ":"):
+                sh = re.search(r"source_sha256_16: `([0-9a-f]+)`", line)
+                by = re.search(r"dram_bytes_per_launch: `([0-9]+)`", line)
+                if sh and by and sh.group(1) == h.hexdigest()[:16]:
+                    return float(by.group(1))
+    except Exception:
+        pass
+    return None
+
+
 def whole_job_rate(local_ms, units_per_step, steps, world, device="cpu"):
     """Throughput of `world` replicas that each process `units_per_step` units
     in each of `steps` steps: the slowest rank bounds the job, so the time is
@@ -373,7 +405,7 @@ def roofline_of(stages, clip, K):
         psrc = "derived: %d SMs x %d FP32 lanes x 2 flops x %.0f MHz (%s SM max clock)" % (SMS, FP32_LANES, mhz, src)
         achieved = work / (ms * 1e-3) / 1e12
     out.update({"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": None, "work": what, "peak_source": psrc})
+                "traffic": stage_traffic(name), "work": what, "peak_source": psrc})
     return out
 
 
@@ -711,21 +743,18 @@ def run_extras(fcfs, dev, flush, stream, args):
     bx, by, bs, boff = (torch.from_numpy(a).to(dev) for a in concat_clips(clips))
     n = len(clips)
     terms_b = float(sum(c.V for c in clips)) * W * W
-    uc = autotune.tune_batch(bx, by, bs, boff, T, K, prec="split_f16")
-    fcfs.set_batch_unit_chunks(uc)
+    plan = autotune.tune_batch(bx, by, bs, boff, T, K, prec="split_f16")
     Fb = torch.empty((n, W, W), dtype=torch.complex64, device=dev)
     Ab = torch.empty(n, dtype=torch.int64, device=dev)
-    wsb = torch.empty(fcfs._lib.load().fcfs_batch_workspace_size(bx.numel(), n, T, K, 1), dtype=torch.uint8,
-                      device=dev)
+    wsb = torch.empty(plan.workspace_size(), dtype=torch.uint8, device=dev)
     cap = torch.cuda.Stream(dev)   # graphs are captured on a side stream
     with torch.cuda.stream(cap):
-        fcfs.batch(bx, by, bs, boff, T, K, out=Fb, area_out=Ab, workspace=wsb, stream=cap)
+        plan.batch(bx, by, bs, boff, out=Fb, area_out=Ab, workspace=wsb, stream=cap)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=cap):
-        fcfs.batch(bx, by, bs, boff, T, K, out=Fb, area_out=Ab, workspace=wsb, stream=cap)
+        plan.batch(bx, by, bs, boff, out=Fb, area_out=Ab, workspace=wsb, stream=cap)
     ms_b = _timed_ms(torch, g.replay, 5, flush, stream)
-    fcfs.set_batch_unit_chunks(0)
     per = [tuple(torch.from_numpy(a).to(dev) for a in (c.x, c.y, c.s)) for c in clips]
     wsc = torch.empty(max(fcfs.workspace_size(c.V, T, K) for c in clips), dtype=torch.uint8, device=dev)
     Fc = torch.empty((W, W), dtype=torch.complex64, device=dev)
@@ -740,7 +769,7 @@ def run_extras(fcfs, dev, flush, stream, args):
                                 % bx.numel(),
                     "value": terms_b / (ms_b * 1e-3), "unit": UNIT, "ms": ms_b,
                     "per_clip_calls_value": terms_b / (ms_c * 1e-3), "per_clip_calls_ms": ms_c,
-                    "unit_chunks": uc, "launch": "one fcfs_batch call replayed from a CUDA graph",
+                    "plan": plan.knobs(), "launch": "one fcfs_plan_batch call replayed from a CUDA graph",
                     "_check": (clips, K, Fb, Ab)}
 
     # large clip (the step's clip): every forward form, forced

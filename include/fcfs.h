@@ -157,6 +157,55 @@ fcfs_status fcfs_batch(const int32_t* x, const int32_t* y, const int8_t* s,
                        void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * Plans: one workload's sizes and launch-shape choices in an opaque object.
+ * Tiles of a layout are independent (Sec. III-A), so how the work is cut (the
+ * contraction's form, its vertex splits, the tile shape, the batch unit size)
+ * changes nothing in the result beyond FP32 rounding; a plan carries those
+ * choices, fixed by a tuner or left to the library's rules.  A plan's calls
+ * apply its knobs for their own duration on the calling thread; they ignore
+ * the process-wide fcfs_debug_set_* hooks for every knob the plan sets.
+ *   kind       : FCFS_PLAN_FORWARD (n_clips = 1), FCFS_PLAN_BATCH, FCFS_PLAN_ADJOINT
+ *                (n_clips = 1).
+ *   V          : corners (the batch total), as for the entry points.
+ * fcfs_plan_create returns FCFS_EINVAL for bad arguments, FCFS_EUNSUPPORTED
+ * for sizes the entry points reject, and sets *plan (else NULL); the caller
+ * owns the plan and releases it with fcfs_plan_destroy.
+ * Knobs (fcfs_plan_set; -1 where allowed, or 0, means automatic):
+ *   FCFS_KNOB_FORM        forward: 0 over the corners, 1 corners grouped by y
+ *                         with the split-FP16 contraction over y, 2 grouped with
+ *                         the pruned FFT along y; batch and adjoint: 0 per
+ *                         corner / direct units, 1 grouped.
+ *   FCFS_KNOB_SPLITS      forward: vertex splits of the contraction.
+ *   FCFS_KNOB_PAIR        forward and batch: 1 CTA-pair 256 x 256 tiles (2-SM
+ *                         MMA) where eligible, 0 one-CTA tiles.
+ *   FCFS_KNOB_UNIT_CHUNKS batch: pipeline chunks per (clip, tile, split) unit.
+ * fcfs_plan_set returns FCFS_EINVAL for a knob the kind does not have or a
+ * value out of range.  fcfs_plan_get returns the value a call will use (the
+ * automatic ones resolved), -1 on error.  fcfs_plan_workspace_size is the
+ * workspace for the plan's sizes and knobs (0 on error); a plan's calls take
+ * the arguments of fcfs_forward / fcfs_batch / fcfs_adjoint without the sizes
+ * it holds (V may be smaller than the plan's).
+ */
+enum { FCFS_PLAN_FORWARD = 0, FCFS_PLAN_BATCH = 1, FCFS_PLAN_ADJOINT = 2 };
+enum { FCFS_KNOB_FORM = 0, FCFS_KNOB_SPLITS = 1, FCFS_KNOB_PAIR = 2, FCFS_KNOB_UNIT_CHUNKS = 3 };
+typedef struct fcfs_plan_s* fcfs_plan;
+fcfs_status fcfs_plan_create(fcfs_plan* plan, int32_t kind, int64_t V, int32_t n_clips, int32_t T,
+                             int32_t K, int32_t prec);
+void fcfs_plan_destroy(fcfs_plan plan);
+fcfs_status fcfs_plan_set(fcfs_plan plan, int32_t knob, int64_t value);
+int64_t fcfs_plan_get(fcfs_plan plan, int32_t knob);
+size_t fcfs_plan_workspace_size(fcfs_plan plan);
+fcfs_status fcfs_plan_forward(fcfs_plan plan, const int32_t* x, const int32_t* y, const int8_t* s,
+                              int64_t V, uint32_t flags, float* F_out, int64_t* area_out,
+                              void* workspace, size_t ws_bytes, void* stream);
+fcfs_status fcfs_plan_batch(fcfs_plan plan, const int32_t* x, const int32_t* y, const int8_t* s,
+                            const int64_t* offsets, int64_t V_total, float* F_out,
+                            int64_t* area_out, void* workspace, size_t ws_bytes, void* stream);
+fcfs_status fcfs_plan_adjoint(fcfs_plan plan, const int32_t* x, const int32_t* y, const int8_t* s,
+                              int64_t V, const float* dF, float* gx, float* gy,
+                              void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * Continuous cosine series of one clip (the cosine extension of FCFS named in
  * the concluding section; the paper gives no formula, so this keeps the
  * conventions of the Fourier block: the inner product with the basis, no
@@ -290,11 +339,14 @@ const char* fcfs_kernel_timing_name(int32_t i);
 float fcfs_kernel_timing_ms(int32_t i);
 void fcfs_debug_set_splits(int32_t n);
 void fcfs_debug_set_fuse(int32_t on);
-/* Which contraction fcfs_forward (flags 0) will run for these sizes: 1 when it
- * groups the corners by y and contracts over the T + 1 values of y, 0 when it
- * contracts over the V corners, -1 for unsupported sizes.  The automatic choice
- * (fcfs_debug_set_hybrid(1), the default) compares cost estimates of the two
- * forms; fcfs_debug_set_hybrid(0) and (2) force them off and on. */
+/* Which form fcfs_forward (flags 0) will take for these sizes: 0 the
+ * contraction over the V corners, 1 the corners grouped by y and the
+ * split-FP16 contraction over the T + 1 values of y, 2 the corners grouped by
+ * y and the pruned FFT along y (Step 4's sparse-image DFT with its output
+ * limited to |l| <= K, FP32), -1 for unsupported sizes.  The automatic choice
+ * (fcfs_debug_set_hybrid(1), the default) compares cost estimates of the
+ * forms the call may take; fcfs_debug_set_hybrid(0), (2) and (3) force the
+ * first, second and third. */
 int32_t fcfs_forward_grouped(int64_t V, int32_t T, int32_t K, int32_t prec);
 /* The same for fcfs_adjoint: 1 when its tensor-core contraction runs over the
  * values of the grouped coordinate, 0 per corner (and always 0 for FP32), -1
@@ -314,9 +366,11 @@ void fcfs_debug_set_barrier_extra(int32_t n);
 /* Row-binned contraction of single-clip split-FP16 calls on CTA pairs (the
  * corners grouped by y, the off-axis block contracted over the T + 1 values of
  * y instead of the V corners; the binning of Steps 2-3 carried into Step 4):
- * mode 0 never, 1 (the default) when a cost estimate of the two forms
- * favours it (fcfs_forward_grouped tells), 2 whenever the call is eligible
- * (split FP16, 2K >= 256, no device validation).  Batches group when
+ * mode 0 never, 1 (the default) when a cost estimate of the forms favours
+ * it (fcfs_forward_grouped tells), 2 the split-FP16 contraction over y whenever
+ * the call is eligible (split FP16, 2K >= 256, no device validation), 3 the
+ * pruned FFT along y whenever eligible (any precision, K <= 4096, no device
+ * validation).  Batches group when
  * V >= 8 n (T + 1) and K >= 256.  The split-FP16 adjoint groups its corners by
  * the contraction coordinate under the same modes, automatically when a cost
  * estimate of its two forms favours it.  Same results within

@@ -31,6 +31,14 @@ SIGNATURES = {
     "fcfs_get_status": (C.c_int, [_p, _p]),
     "fcfs_forward_noalloc": (C.c_int, [_p, _p, _p, _i64, _i32, _i32, _i32, _u32, _p, _p, _p]),
     "fcfs_noalloc_status": (C.c_int, [_p]),
+    "fcfs_plan_create": (C.c_int, [C.POINTER(_p), _i32, _i64, _i32, _i32, _i32, _i32]),
+    "fcfs_plan_destroy": (None, [_p]),
+    "fcfs_plan_set": (C.c_int, [_p, _i32, _i64]),
+    "fcfs_plan_get": (_i64, [_p, _i32]),
+    "fcfs_plan_workspace_size": (_sz, [_p]),
+    "fcfs_plan_forward": (C.c_int, [_p, _p, _p, _p, _i64, _u32, _p, _p, _p, _sz, _p]),
+    "fcfs_plan_batch": (C.c_int, [_p, _p, _p, _p, _p, _i64, _p, _p, _p, _sz, _p]),
+    "fcfs_plan_adjoint": (C.c_int, [_p, _p, _p, _p, _i64, _p, _p, _p, _p, _sz, _p]),
     "fcfs_debug_set_splits": (None, [_i32]),
     "fcfs_debug_set_fuse": (None, [_i32]),
     "fcfs_debug_set_pair": (None, [_i32]),

@@ -1,16 +1,17 @@
-"""Autotuner for the launch shape of the FCFS kernels.
+"""Autotuner for the launch shape of the FCFS kernels; its choices go into plans.
 
-Two knobs are tuned by timing real calls with CUDA events:
+Knobs are tuned by timing real calls with CUDA events, each candidate run
+through a Plan (fcfs_plan_* of the C ABI), so no process-wide hook changes:
 
-* single clip: the number of vertex splits of the contraction (split-K), which
-  trades parallelism against the size of the partial sums;
-* batch: the number of pipeline chunks per (clip, tile, split) unit, which
-  trades load balance against the number of partial tiles.
+* single clip: the form of the contraction (over the corners, split-FP16 over
+  y, pruned FFT along y), and for the contraction over the corners its vertex
+  splits (split-K) and tile shape (CTA pairs or one-CTA tiles);
+* batch: chunks per (clip, tile, split) unit, tile shape, grouping by y.
 
-Results are cached in a JSON file keyed by GPU name, T, K, precision and the
-power-of-two bucket of the corner count, so a workload is tuned once per
-machine.  The cache lives at $FCFS_AUTOTUNE_CACHE, else
-~/.cache/fcfs_gb300/autotune.json.
+The winning knobs are cached in a JSON file keyed by GPU name, T, K, precision,
+the power-of-two bucket of the corner count and the clip count, so a workload
+is tuned once per machine; tune_* return a Plan carrying them.  The cache lives
+at $FCFS_AUTOTUNE_CACHE, else ~/.cache/fcfs_gb300/autotune.json.
 """
 import json
 import math
@@ -21,7 +22,7 @@ import torch
 
 from . import fcfs
 
-SPLIT_CANDIDATES = (0, 1, 2, 4, 8, 12, 16, 19, 24, 32, 38, 48, 64, 76, 96, 152)
+SPLIT_CANDIDATES = (0, 2, 4, 8, 12, 19, 38, 76, 152)
 UNIT_CANDIDATES = (8, 16, 32, 64, 128)   # longer FP32 accumulation runs lose accuracy
 
 
@@ -50,7 +51,7 @@ def _store(db):
 def _key(kind, T, K, prec, V, n=1):
     gpu = torch.cuda.get_device_name()
     vb = int(math.log2(max(1, V)))
-    return "%s|%s|T%d|K%d|%s|V2^%d|n%d" % (kind, gpu, T, K, prec, vb, n)
+    return "plan|%s|%s|T%d|K%d|%s|V2^%d|n%d" % (kind, gpu, T, K, prec, vb, n)
 
 
 def _time(fn, reps):
@@ -65,58 +66,74 @@ def _time(fn, reps):
     return statistics.median(a.elapsed_time(b) for a, b in ev)
 
 
-def tune_forward(x, y, s, T, K, prec="split_f16", reps=5, force=False):
-    """Best split count for one clip (0 = the library's own choice); cached."""
+def _forward_candidates(prec, K):
+    """Knob sets tried for one clip: each form with the library's own split
+    count, then the contraction over the corners with other split counts and,
+    for split FP16, one-CTA tiles."""
+    cands = [{"form": 0}, {"form": 2}]
+    if prec == "split_f16" and 2 * K >= 256:
+        cands.insert(1, {"form": 1})
+        cands.append({"form": 0, "pair": 0})
+    cands += [{"form": 0, "splits": sp} for sp in SPLIT_CANDIDATES if sp]
+    return cands
+
+
+def _best(kind, key, cands, make, run, reps, force):
     db = _load()
-    key = _key("forward", T, K, prec, x.numel())
     if key in db and not force:
-        return db[key]["splits"]
+        return make(db[key]["knobs"])
+    best, results = None, {}
+    for kn in cands:
+        try:
+            plan = make(kn)
+            ms = _time(run(plan), reps)
+        except fcfs.FCFSError:
+            continue   # a knob set the sizes do not allow
+        results[json.dumps(kn, sort_keys=True)] = ms
+        if best is None or ms < best[0]:
+            best = (ms, kn)
+    db[key] = {"knobs": best[1], "ms": best[0], "tried": results}
+    _store(db)
+    return make(best[1])
+
+
+def tune_forward(x, y, s, T, K, prec="split_f16", reps=5, force=False):
+    """A forward Plan with the fastest knobs for one clip (measured; cached)."""
+    V = x.numel()
     W = 2 * K + 1
     out = torch.empty((W, W), dtype=torch.complex64, device=x.device)
     area = torch.empty(1, dtype=torch.int64, device=x.device)
-    best = (float("inf"), 0)
-    results = {}
-    nchunks = (x.numel() + 63) // 64
-    for sp in SPLIT_CANDIDATES:
-        if sp > nchunks:
-            continue
-        fcfs.set_splits(sp)
-        try:
-            ws = torch.empty(fcfs.workspace_size(x.numel(), T, K, prec), dtype=torch.uint8, device=x.device)
-            ms = _time(lambda: fcfs.forward(x, y, s, T, K, prec=prec, out=out, area_out=area, workspace=ws), reps)
-        finally:
-            fcfs.set_splits(0)
-        results[str(sp)] = ms
-        best = min(best, (ms, sp))
-    db[key] = {"splits": best[1], "ms": best[0], "tried": results}
-    _store(db)
-    return best[1]
+    nchunks = (V + 63) // 64
+    cands = [c for c in _forward_candidates(prec, K) if c.get("splits", 0) <= nchunks]
+
+    def make(kn):
+        return fcfs.Plan("forward", V, T, K, prec, **kn)
+
+    def run(plan):
+        ws = fcfs.alloc_workspace(plan.workspace_size(), x.device)
+        return lambda: plan.forward(x, y, s, out=out, area_out=area, workspace=ws)
+
+    return _best("forward", _key("forward", T, K, prec, V), cands, make, run, reps, force)
 
 
 def tune_batch(x, y, s, offsets, T, K, prec="split_f16", reps=3, force=False):
-    """Best chunks per unit for a batch (0 = default); cached."""
+    """A batch Plan with the fastest knobs (chunks per unit, tile shape, grouping
+    by y) for these clips (measured; cached)."""
     n = offsets.numel() - 1
-    db = _load()
-    key = _key("batch", T, K, prec, x.numel(), n)
-    if key in db and not force:
-        return db[key]["unit_chunks"]
+    V = x.numel()
     W = 2 * K + 1
     out = torch.empty((n, W, W), dtype=torch.complex64, device=x.device)
     area = torch.empty(n, dtype=torch.int64, device=x.device)
-    lib = fcfs._lib.load()
-    best = (float("inf"), 0)
-    results = {}
-    for uc in UNIT_CANDIDATES:
-        fcfs.set_batch_unit_chunks(uc)
-        try:
-            need = lib.fcfs_batch_workspace_size(x.numel(), n, T, K, fcfs.PREC[prec])
-            ws = torch.empty(need, dtype=torch.uint8, device=x.device)
-            ms = _time(lambda: fcfs.batch(x, y, s, offsets, T, K, prec=prec, out=out, area_out=area,
-                                          workspace=ws), reps)
-        finally:
-            fcfs.set_batch_unit_chunks(0)
-        results[str(uc)] = ms
-        best = min(best, (ms, uc))
-    db[key] = {"unit_chunks": best[1], "ms": best[0], "tried": results}
-    _store(db)
-    return best[1]
+    cands = [{"form": 0, "unit_chunks": uc} for uc in UNIT_CANDIDATES]
+    if prec == "split_f16" and 2 * K >= 256:
+        cands += [{"form": 0, "unit_chunks": uc, "pair": 0} for uc in UNIT_CANDIDATES]
+        cands.append({"form": 1})
+
+    def make(kn):
+        return fcfs.Plan("batch", V, T, K, prec, n_clips=n, **kn)
+
+    def run(plan):
+        ws = fcfs.alloc_workspace(plan.workspace_size(), x.device)
+        return lambda: plan.batch(x, y, s, offsets, out=out, area_out=area, workspace=ws)
+
+    return _best("batch", _key("batch", T, K, prec, V, n), cands, make, run, reps, force)

@@ -95,7 +95,15 @@ static int g_split_override = 0;   // testing/autotuning hook, 0 = automatic
 static int g_fuse = 1;             // testing hook: 0 keeps the axis and reduce kernels separate
 static int g_pair = 1;             // testing hook: 0 keeps single clips on one-CTA tiles
 static int g_barrier_extra = 0;    // testing hook: see fcfs_debug_set_barrier_extra
-static int g_hybrid = 1;           // 0: never group by y, 1: automatic, 2: whenever eligible
+static int g_hybrid = 1;           // 0: never group by y, 1: automatic, 2: grouped tc, 3: grouped FFT
+
+static thread_local const Knobs* t_knobs = nullptr;
+const Knobs* current_knobs() { return t_knobs; }
+KnobScope::KnobScope(const Knobs* k) : prev(t_knobs) { t_knobs = k; }
+KnobScope::~KnobScope() { t_knobs = prev; }
+int knob_splits() { return t_knobs && t_knobs->splits > 0 ? t_knobs->splits : g_split_override; }
+static int knob_pair() { return t_knobs && t_knobs->pair >= 0 ? t_knobs->pair : g_pair; }
+static int knob_hybrid() { return t_knobs && t_knobs->hybrid >= 0 ? t_knobs->hybrid : g_hybrid; }
 
 // Tag of the cached tables: their kind, period, fixed-point scale and offsets.
 static uint64_t table_tag(const Plan& pl) {
@@ -140,7 +148,7 @@ static fcfs_status plan_impl(int64_t V, int32_t T, int32_t K, int32_t prec, bool
   }
   pl.tiles_m = (pl.M2 + pl.bm - 1) / pl.bm;
   pl.tiles_n = (pl.M2 + pl.bn - 1) / pl.bn;
-  if (tc && single && (cosine || (g_pair && pl.M2 >= 256))) {
+  if (tc && single && (cosine || (knob_pair() && pl.M2 >= 256))) {
     // 256 x 256 tiles on CTA pairs: tile row pair (2 tm', 2 tm' + 1), one per CTA
     pl.pair = 1;
     pl.bn = 256;
@@ -149,7 +157,7 @@ static fcfs_status plan_impl(int64_t V, int32_t T, int32_t K, int32_t prec, bool
   }
   const long long nchunks = (V + pl.chunk - 1) / pl.chunk;
   const long long slots = (long long)sm_count() * (tc ? 1 : 2);
-  int s = g_split_override > 0 ? (int)std::min<long long>(g_split_override, nchunks)
+  int s = knob_splits() > 0 ? (int)std::min<long long>(knob_splits(), nchunks)
                                : choose_splits((long long)pl.tiles_m * pl.tiles_n, nchunks, slots, 4);
   if (s > 0) {
     const long long per = (nchunks + s - 1) / s;
@@ -193,8 +201,8 @@ fcfs_status make_plan_cosine(int64_t V, int32_t T, int32_t K, int32_t prec, Plan
   return plan_impl(V, 2 * T, K, prec, true, true, pl);
 }
 
-int hybrid_mode() { return g_hybrid == 3 ? 1 : g_hybrid; }
-bool pair_enabled() { return g_pair != 0; }
+int hybrid_mode() { return knob_hybrid() == 3 ? 1 : knob_hybrid(); }
+bool pair_enabled() { return knob_pair() != 0; }
 
 // The contraction of a single-clip call (fcfs_forward_grouped reports it):
 //   kDirect      over the V corners (tensor cores, or the plain FP32 kernel);
@@ -217,11 +225,12 @@ bool pair_enabled() { return g_pair != 0; }
 enum { kDirect = 0, kGroupedTc = 1, kGroupedFft = 2 };
 
 static int forward_form(const Plan& pl, bool validate) {
-  if (g_hybrid == 0 || validate || pl.V <= 0 || pl.logT > 16 || pl.cosine) return kDirect;
+  const int hy = knob_hybrid();
+  if (hy == 0 || validate || pl.V <= 0 || pl.logT > 16 || pl.cosine) return kDirect;
   const bool tc_ok = pl.pair && pl.prec == FCFS_PREC_SPLIT_F16;
   const bool fft_ok = pl.K <= 4096;
-  if (g_hybrid == 2) return tc_ok ? kGroupedTc : kDirect;
-  if (g_hybrid == 3) return fft_ok ? kGroupedFft : kDirect;
+  if (hy == 2) return tc_ok ? kGroupedTc : kDirect;
+  if (hy == 3) return fft_ok ? kGroupedFft : kDirect;
   const double v = (double)pl.V, k = (double)pl.K, t = (double)pl.T;
   const double items = std::max(1.0, t / 64.0), sms = (double)sm_count();
   const double g = 0.055 + 6e-8 * v;
@@ -251,7 +260,7 @@ static void plan_hybrid(Plan& pl) {
   pl.hyb = 1;
   pl.ny_pad = (pl.T + 1 + 63) / 64 * 64;
   const long long nchunks = pl.ny_pad / 64;
-  const int s = g_split_override > 0 ? (int)std::min<long long>(g_split_override, nchunks)
+  const int s = knob_splits() > 0 ? (int)std::min<long long>(knob_splits(), nchunks)
                                      : choose_splits((long long)pl.tiles_m * pl.tiles_n, nchunks, sm_count(), 4);
   const long long per = (nchunks + s - 1) / s;
   pl.split_len = per * 64;
@@ -472,6 +481,20 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
     FCFS_CU(launch_reduce(pl, ws, F, area, validate, st));
   }
   prof_mark(7, st);
+  return FCFS_OK;
+}
+
+// The form, split count and tile shape a single-clip forward call takes under
+// the current knobs.
+fcfs_status forward_plan_info(int64_t V, int32_t T, int32_t K, int32_t prec, int* form, int* splits, int* pair) {
+  Plan pl;
+  const fcfs_status r = make_plan_ex(V, T, K, prec, true, pl);
+  if (r != FCFS_OK) return r;
+  const int f = forward_form(pl, false);
+  plan_form(pl, f);
+  *form = f;
+  *splits = pl.splits;
+  *pair = pl.pair;
   return FCFS_OK;
 }
 

@@ -65,7 +65,9 @@ static fcfs_status make_batch_plan(int64_t V, int32_t n, int32_t T, int32_t K, i
     pl.total = o;
     return FCFS_OK;
   }
-  const int chunks = g_unit_chunks > 0 ? g_unit_chunks : 4096 / pl.chunk;
+  const Knobs* kn = current_knobs();
+  const int uc = kn && kn->unit_chunks > 0 ? kn->unit_chunks : g_unit_chunks;
+  const int chunks = uc > 0 ? uc : 4096 / pl.chunk;
   pl.unit_vertices = (int64_t)chunks * pl.chunk;
   // split FP16 with 2K >= 256: units on CTA pairs (256 x 256 tiles, 2-SM MMA)
   if (prec == FCFS_PREC_SPLIT_F16 && pl.M2 >= 256 && pair_enabled()) {
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(1024) batch_units_kernel(Plan pl, uint8_t* ws)
   if (threadIdx.x == blockDim.x - 1) ustart[n] = scan[threadIdx.x];
 }
 
-static fcfs_status batch_impl(const int32_t* x, const int32_t* y, const int8_t* s, const int64_t* offsets,
+fcfs_status batch_impl(const int32_t* x, const int32_t* y, const int8_t* s, const int64_t* offsets,
                               int32_t n, int64_t V, int32_t T, int32_t K, int32_t prec, uint32_t flags, float* F,
                               int64_t* area, void* ws, size_t ws_bytes, cudaStream_t st) {
   if (!F || !area || !offsets || n < 1) return FCFS_EINVAL;
@@ -149,6 +151,19 @@ static fcfs_status batch_impl(const int32_t* x, const int32_t* y, const int8_t* 
   }
   if (launch_axis(pl, x, y, s, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
   if (launch_reduce(pl, ws, F, area, false, st) != cudaSuccess) return FCFS_ECUDA;
+  return FCFS_OK;
+}
+
+// Whether a batch is grouped by y, its chunks per unit and its tile shape under
+// the current knobs.
+fcfs_status batch_plan_info(int64_t V, int32_t n, int32_t T, int32_t K, int32_t prec, int* grouped,
+                            int* unit_chunks, int* pair) {
+  Plan pl;
+  const fcfs_status r = make_batch_plan(V, n, T, K, prec, nullptr, pl);
+  if (r != FCFS_OK) return r;
+  *grouped = pl.hyb;
+  *unit_chunks = pl.hyb ? 0 : (int)(pl.unit_vertices / pl.chunk);
+  *pair = pl.pair;
   return FCFS_OK;
 }
 

@@ -503,6 +503,22 @@ struct AdjTcArgs {
   int ny_pad;       // grouped: T + 1 rounded up to 64 (the groups' exponent array)
   size_t off_groups;  // grouped: by y (gx), then by x (gy) (fcfs_group.cuh)
 };
+// Launch-shape knobs of a call: a plan's (fcfs_plan_*) while one of its calls
+// runs on this thread, else the process-wide test and tuning hooks.  Negative
+// (or, for splits and unit chunks, zero) values defer to the hooks.
+struct Knobs {
+  int hybrid;        // 0 direct, 1 automatic, 2 grouped tensor-core, 3 grouped FFT
+  int splits;        // vertex splits of a single-clip contraction (0: automatic)
+  int pair;          // 1: CTA-pair tiles where eligible, 0: one-CTA tiles
+  int unit_chunks;   // batch: pipeline chunks per unit (0: default)
+};
+const Knobs* current_knobs();
+struct KnobScope {
+  const Knobs* prev;
+  explicit KnobScope(const Knobs* k);
+  ~KnobScope();
+};
+int knob_splits();
 // Row-binned (grouped) mode of the forward and adjoint calls: 0 never, 1 automatic, 2 forced
 int hybrid_mode();
 // CTA pairs for 2K >= 256 on the split-FP16 path (fcfs_debug_set_pair)

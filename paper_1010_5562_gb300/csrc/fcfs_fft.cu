@@ -29,6 +29,7 @@ namespace {
 
 constexpr int kFBufPts = 4096;   // complex points per buffer (several FFTs when L < 4096)
 constexpr int kFOwnMax = 9;      // outputs per thread (2K + 1 <= 9 blockDim)
+constexpr int kFTab = 256;       // two-level table entries per level (T <= 2^16)
 
 struct FftArgs {
   Plan pl;
@@ -159,7 +160,9 @@ __global__ void __launch_bounds__(NT) fft_y_kernel(FftArgs ar) {
   float2* raw = reinterpret_cast<float2*>(sm);         // bulk-copy target, pts entries
   float2* bufA = raw + pts;
   float2* bufB = bufA + bufpts;
-  float2* lev = bufB + bufpts;                         // twiddle levels of passes 1, 2, ...
+  float2* wc = bufB + bufpts;                          // e^{+j 2 pi p / T} = wc[p >> f] wf[p & fm]
+  float2* wf = wc + kFTab;
+  float2* lev = wf + kFTab;                            // twiddle levels of passes 1, 2, ...
   const int k = blockIdx.x + 1;
   const int f0 = first_log_radix(logL);
   Status* st = reinterpret_cast<Status*>(const_cast<uint8_t*>(ar.ws) + pl.off_status);
@@ -182,6 +185,12 @@ __global__ void __launch_bounds__(NT) fft_y_kernel(FftArgs ar) {
       }
       off += n;
     }
+  }
+  const uint32_t f = ((uint32_t)logT + 1u) / 2u, nf = 1u << f, nc = (uint32_t)T >> f;
+  for (uint32_t i = threadIdx.x; i < nc + nf; i += blockDim.x) {
+    const uint32_t p = i < nc ? i << f : i - nc;
+    const float2 w = pl.full ? f32_lookup<true>(gt, p, logQ) : f32_lookup<false>(gt, p, logQ);
+    (i < nc ? wc[i] : wf[i - nc]) = w;
   }
   if (threadIdx.x == 0) {
     mbar_init(&full_bar, 1);
@@ -227,7 +236,7 @@ __global__ void __launch_bounds__(NT) fft_y_kernel(FftArgs ar) {
       __syncthreads();
     }
     // G(l) += e^{-j 2 pi l a / T} D_a(l mod L) over the residues of this range
-    // (twiddles read from the correctly rounded table at the exact phase)
+    // (twiddles from the two-level table at the exact phase)
 #pragma unroll
     for (int i = 0; i < kFOwnMax; ++i) {
       const int l = -K + (int)threadIdx.x + (int)blockDim.x * i;
@@ -235,7 +244,7 @@ __global__ void __launch_bounds__(NT) fft_y_kernel(FftArgs ar) {
       const int m = l & (L - 1);
       for (int q = 0; q < nfft; ++q) {
         const uint32_t ph = ((uint32_t)l * (uint32_t)(a0 + q)) & mask;
-        const float2 w = pl.full ? f32_lookup<true>(gt, ph, logQ) : f32_lookup<false>(gt, ph, logQ);   // e^{+j ...}
+        const float2 w = c_mul(wc[ph >> f], wf[ph & (nf - 1u)]);   // e^{+j ...}
         const float2 d = X[pad16(q * L + m)];
         // acc += conj(w) d
         acc[i].x = fmaf(w.x, d.x, fmaf(w.y, d.y, acc[i].x));
@@ -282,7 +291,7 @@ size_t fft_y_smem(int logL) {
   size_t lev = 0;
   const int f0 = (logL & 3) ? (logL & 3) : 4;
   for (int lm = f0 + 4; lm <= logL; lm += 4) lev += (size_t)level_entries(lm);
-  return (pts + 2 * buf + lev) * 8;
+  return (pts + 2 * buf + 2 * kFTab + lev) * 8;
 }
 
 // FFT length for a period T and cut-off K: a power of two >= 2K (no two wanted

@@ -11,7 +11,7 @@ from ._lib import FCFSError, PREC, FLAG_VALIDATE
 
 __all__ = ["forward", "adjoint", "edge_chain", "batch", "cosine", "haar", "workspace_size",
            "cosine_workspace_size", "haar_workspace_size", "forward_grouped", "adjoint_grouped",
-           "get_status", "launch_count", "FCFSError"]
+           "get_status", "launch_count", "Plan", "FCFSError"]
 
 
 def _ptr(t):
@@ -117,6 +117,87 @@ def batch(x, y, s, offsets, T, K, prec="split_f16", validate=False, out=None, ar
                           _ptr(workspace), workspace.numel(), _stream(stream))
     _lib.check("fcfs_batch", code)
     return out, area_out
+
+
+PLAN_KINDS = {"forward": 0, "batch": 1, "adjoint": 2}
+KNOBS = {"form": 0, "splits": 1, "pair": 2, "unit_chunks": 3}
+
+
+class Plan:
+    """A workload's sizes and launch-shape choices (fcfs_plan_* of the C ABI).
+
+    Knobs: form (forward: 0 over the corners, 1 split-FP16 contraction over y,
+    2 pruned FFT along y; batch/adjoint: 0 direct, 1 grouped), splits, pair,
+    unit_chunks; -1 or 0 leaves a knob to the library.  get() returns the value
+    a call will use.  The plan is released when the object is."""
+
+    def __init__(self, kind, V, T, K, prec="split_f16", n_clips=1, **knobs):
+        import ctypes as C
+        lib = _lib.load()
+        h = C.c_void_p()
+        code = lib.fcfs_plan_create(C.byref(h), PLAN_KINDS[kind], int(V), int(n_clips), int(T), int(K),
+                                    _prec(prec))
+        _lib.check("fcfs_plan_create", code)
+        self._h, self.kind, self.V, self.T, self.K, self.prec, self.n_clips = h, kind, int(V), int(T), int(K), prec, int(n_clips)
+        for k, v in knobs.items():
+            self.set(k, v)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.load().fcfs_plan_destroy(h)
+            self._h = None
+
+    def set(self, knob, value):
+        _lib.check("fcfs_plan_set", _lib.load().fcfs_plan_set(self._h, KNOBS[knob], int(value)))
+        return self
+
+    def get(self, knob):
+        return int(_lib.load().fcfs_plan_get(self._h, KNOBS[knob]))
+
+    def knobs(self):
+        return {k: self.get(k) for k in KNOBS}
+
+    def workspace_size(self):
+        return int(_lib.load().fcfs_plan_workspace_size(self._h))
+
+    def forward(self, x, y, s, out=None, area_out=None, workspace=None, stream=None):
+        _check_vertices(x, y, s)
+        dev = x.device
+        W = 2 * self.K + 1
+        out = torch.empty((W, W), dtype=torch.complex64, device=dev) if out is None else out
+        area_out = torch.empty((1,), dtype=torch.int64, device=dev) if area_out is None else area_out
+        workspace = alloc_workspace(self.workspace_size(), dev) if workspace is None else workspace
+        code = _lib.load().fcfs_plan_forward(self._h, _ptr(x), _ptr(y), _ptr(s), x.numel(), 0, _ptr(out),
+                                             _ptr(area_out), _ptr(workspace), workspace.numel(), _stream(stream))
+        _lib.check("fcfs_plan_forward", code)
+        return out, area_out
+
+    def batch(self, x, y, s, offsets, out=None, area_out=None, workspace=None, stream=None):
+        _check_vertices(x, y, s)
+        dev = x.device
+        n = offsets.numel() - 1
+        W = 2 * self.K + 1
+        out = torch.empty((n, W, W), dtype=torch.complex64, device=dev) if out is None else out
+        area_out = torch.empty((n,), dtype=torch.int64, device=dev) if area_out is None else area_out
+        workspace = alloc_workspace(self.workspace_size(), dev) if workspace is None else workspace
+        code = _lib.load().fcfs_plan_batch(self._h, _ptr(x), _ptr(y), _ptr(s), _ptr(offsets), x.numel(),
+                                           _ptr(out), _ptr(area_out), _ptr(workspace), workspace.numel(),
+                                           _stream(stream))
+        _lib.check("fcfs_plan_batch", code)
+        return out, area_out
+
+    def adjoint(self, x, y, s, dF, gx=None, gy=None, workspace=None, stream=None):
+        _check_vertices(x, y, s)
+        dev = x.device
+        V = x.numel()
+        gx = torch.empty(V, dtype=torch.float32, device=dev) if gx is None else gx
+        gy = torch.empty(V, dtype=torch.float32, device=dev) if gy is None else gy
+        workspace = alloc_workspace(self.workspace_size(), dev) if workspace is None else workspace
+        code = _lib.load().fcfs_plan_adjoint(self._h, _ptr(x), _ptr(y), _ptr(s), V, _ptr(dF), _ptr(gx), _ptr(gy),
+                                             _ptr(workspace), workspace.numel(), _stream(stream))
+        _lib.check("fcfs_plan_adjoint", code)
+        return gx, gy
 
 
 def cosine_workspace_size(V, T, K, prec="split_f16"):

@@ -222,3 +222,51 @@ def test_python_contraction_queries(lib):
     assert fcfs.adjoint_grouped(31700, 2048, 128) == 0
     assert fcfs.adjoint_grouped(945586, 65536, 1024, prec="fp32") == 0
     assert fcfs.forward_grouped(100, 1000, 8) == -1
+
+
+def test_plans_host(lib):
+    """Plans through the C ABI without device work: creation checks, knob
+    ranges, resolved knobs and workspace sizes, independence from the hooks."""
+    import ctypes as C
+    h = C.c_void_p()
+    assert lib.fcfs_plan_create(C.byref(h), 0, 945450, 1, 65536, 1024, 1) == 0 and h.value
+    try:
+        assert lib.fcfs_plan_get(h, 0) == 2                        # automatic: the pruned FFT along y
+        auto_ws = lib.fcfs_plan_workspace_size(h)
+        assert auto_ws == lib.fcfs_workspace_size(945450, 65536, 1024, 1)
+        assert lib.fcfs_plan_set(h, 0, 1) == 0                     # split-FP16 contraction over y
+        assert lib.fcfs_plan_get(h, 0) == 1
+        assert lib.fcfs_plan_workspace_size(h) >= 2 * 2048 * 65600 * 2
+        assert lib.fcfs_plan_set(h, 0, 0) == 0 and lib.fcfs_plan_get(h, 0) == 0
+        assert lib.fcfs_plan_set(h, 1, 7) == 0 and lib.fcfs_plan_get(h, 1) == 7   # vertex splits
+        assert lib.fcfs_plan_get(h, 2) == 1                        # CTA pairs for 2K >= 256
+        assert lib.fcfs_plan_set(h, 2, 0) == 0 and lib.fcfs_plan_get(h, 2) == 0
+        assert lib.fcfs_plan_set(h, 0, 3) == 1                     # no such form
+        assert lib.fcfs_plan_set(h, 3, 16) == 1                    # unit chunks: batch plans only
+        assert lib.fcfs_plan_set(h, 9, 0) == 1
+        # the process-wide hooks are untouched by the plan
+        assert lib.fcfs_forward_grouped(945450, 65536, 1024, 1) == 2
+    finally:
+        lib.fcfs_plan_destroy(h)
+    b = C.c_void_p()
+    assert lib.fcfs_plan_create(C.byref(b), 1, 100000, 8, 2048, 128, 1) == 0
+    try:
+        assert lib.fcfs_plan_get(b, 3) == 64                       # default: 4096 corners per unit
+        assert lib.fcfs_plan_set(b, 3, 16) == 0 and lib.fcfs_plan_get(b, 3) == 16
+        assert lib.fcfs_plan_workspace_size(b) > 0
+        assert lib.fcfs_plan_set(b, 1, 4) == 1                     # splits: forward plans only
+    finally:
+        lib.fcfs_plan_destroy(b)
+    a = C.c_void_p()
+    assert lib.fcfs_plan_create(C.byref(a), 2, 945586, 1, 65536, 1024, 1) == 0
+    try:
+        assert lib.fcfs_plan_get(a, 0) == 1                        # the grouped adjoint
+        assert lib.fcfs_plan_set(a, 0, 0) == 0 and lib.fcfs_plan_get(a, 0) == 0
+        assert lib.fcfs_plan_workspace_size(a) > 0
+    finally:
+        lib.fcfs_plan_destroy(a)
+    bad = C.c_void_p()
+    assert lib.fcfs_plan_create(C.byref(bad), 0, 100, 1, 1000, 8, 1) == 6 and not bad.value   # T not 2^n
+    assert lib.fcfs_plan_create(C.byref(bad), 0, 100, 2, 1024, 8, 1) == 1                     # clips of a forward plan
+    assert lib.fcfs_plan_create(C.byref(bad), 5, 100, 1, 1024, 8, 1) == 1
+    assert lib.fcfs_plan_create(None, 0, 100, 1, 1024, 8, 1) == 1

@@ -122,17 +122,69 @@ def test_batch_in_cuda_graph(fc):
     assert torch.equal(F, ref)
 
 
-def test_autotune_cache(fc, tmp_path, monkeypatch):
+def test_autotune_plans(fc, tmp_path, monkeypatch):
+    """The autotuner times knob sets through plans and returns a plan carrying
+    the winner (served from its cache the second time); the tuned plan's
+    blocks match the automatic call's, and no process-wide hook was changed."""
     from paper_1010_5562_gb300 import autotune
     monkeypatch.setenv("FCFS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     clips = small_batch()[:4]
+    T, K = clips[0].T, 40
     x, y, s, off = (torch.from_numpy(a).cuda() for a in concat_clips(clips))
-    uc = autotune.tune_batch(x, y, s, off, clips[0].T, 40, reps=1)
-    assert uc in autotune.UNIT_CANDIDATES
+    plan = autotune.tune_batch(x, y, s, off, T, K, reps=1)
+    assert plan.get("unit_chunks") in autotune.UNIT_CANDIDATES or plan.get("form") == 1
     assert (tmp_path / "tune.json").exists()
-    assert autotune.tune_batch(x, y, s, off, clips[0].T, 40) == uc   # served from the cache
-    sp = autotune.tune_forward(x[:clips[0].V], y[:clips[0].V], s[:clips[0].V], clips[0].T, 40, reps=1)
-    assert sp in autotune.SPLIT_CANDIDATES
+    again = autotune.tune_batch(x, y, s, off, T, K)
+    assert again.knobs() == plan.knobs()
+    Fp, ap = plan.batch(x, y, s, off)
+    Fa, aa = fc.batch(x, y, s, off, T, K)
+    assert torch.equal(ap, aa)
+    A = [oracle.area_exact(c.x, c.y, c.s, c.T) for c in clips]
+    for c in range(len(clips)):
+        assert float(torch.max(torch.abs(Fp[c] - Fa[c]))) / max(A[c], 1) <= 2 * TOL["split_f16"]
+    v0 = clips[0].V
+    fplan = autotune.tune_forward(x[:v0], y[:v0], s[:v0], T, K, reps=1)
+    F1, a1 = fplan.forward(x[:v0], y[:v0], s[:v0])
+    F0, a0 = fc.forward(x[:v0], y[:v0], s[:v0], T, K)
+    assert int(a1) == int(a0) == A[0]
+    assert float(torch.max(torch.abs(F1 - F0))) / A[0] <= 2 * TOL["split_f16"]
+    lib = fc._lib.load()
+    assert lib.fcfs_forward_grouped(12576, 4096, 256, 1) == 0   # the hooks still automatic
+
+
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_forward_plans_match_oracle(fc, form):
+    """Each forward form through a plan, against the oracle; the plan reports
+    the form it runs and leaves the process-wide hook alone."""
+    clip = make_clip(1024, 200, 31, smin=6, smax=60)
+    K = 160
+    plan = fc.Plan("forward", clip.V, clip.T, K, "split_f16", form=form, splits=3 if form == 0 else 0)
+    assert plan.get("form") == form
+    x, y, s = (torch.from_numpy(a).cuda() for a in (clip.x, clip.y, clip.s))
+    F, a = plan.forward(x, y, s)
+    torch.cuda.synchronize()
+    A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+    assert int(a) == A
+    Fo = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    assert np.max(np.abs(F.cpu().numpy() - Fo)) / A <= TOL["split_f16"]
+    assert fc.forward_grouped(clip.V, clip.T, K) == fc._lib.load().fcfs_forward_grouped(clip.V, clip.T, K, 1)
+
+
+def test_adjoint_plan_matches_call(fc):
+    clip = make_clip(1024, 100, 32, smin=6, smax=60)
+    K = 130
+    rng = np.random.default_rng(9)
+    W = 2 * K + 1
+    G = torch.from_numpy((rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))).astype(np.complex64)).cuda()
+    x, y, s = (torch.from_numpy(a).cuda() for a in (clip.x, clip.y, clip.s))
+    for form in (0, 1):
+        plan = fc.Plan("adjoint", clip.V, clip.T, K, "split_f16", form=form)
+        assert plan.get("form") == form
+        gx, gy = plan.adjoint(x, y, s, G)
+        rx, ry = oracle.vertex_gradient(clip.x, clip.y, clip.s, clip.T, K, G.cpu().numpy().astype(np.complex128))
+        gx, gy = gx.cpu().numpy(), gy.cpu().numpy()
+        err = max(np.max(np.abs(gx - rx)) / np.max(np.abs(rx)), np.max(np.abs(gy - ry)) / np.max(np.abs(ry)))
+        assert err <= 1e-5, (form, err)
 
 
 def run_batch_mode(fc, clips, K, mode):
