@@ -354,6 +354,18 @@ def peaks():
         return FALLBACK_BF16_TFLOPS, FALLBACK_HBM_GBS, 2070.0, "fallback"
 
 
+ADJOINT_FORMS = {0: "per_corner", 1: "grouped_tc", 2: "grouped_fft"}
+FORM_TEXT = {
+    "forward": {"direct": "contraction over the corners (tcgen05, split FP16)",
+                "grouped_tc": "corners grouped by y, FP32 pair sums, split-FP16 tcgen05 contraction over y",
+                "grouped_fft": "corners grouped by y, FP32 pair sums and pruned FFT along y (FP32 arithmetic)"},
+    "adjoint": {"per_corner": "split-FP16 tcgen05 contraction per corner",
+                "grouped_tc": "split-FP16 tcgen05 contraction grouped by y and by x",
+                "grouped_fft": "corners grouped by y and by x, one input-pruned FFT along the grouped coordinate "
+                               "per frequency and one dot per corner (FP32 arithmetic)"},
+}
+
+
 def stage_work(name, clip, K):
     """Roofline of one library stage on the step's clip: (bound, algorithmic work
     per launch, unit of the rate, what the work counts), or None for stages
@@ -374,6 +386,13 @@ def stage_work(name, clip, K):
                 "2 matrices (gx, gy) x 2 (T+1) (2K)^2: one real MAC per b-value-coefficient term")
     if name == "adj_tc":
         return ("tensor", 4.0 * V * M2 * M2, "TFLOP/s", "2 matrices x 2 V (2K)^2")
+    if name == "adj_fft":
+        return ("hbm", 2.0 * T * (K + 1) * 8.0 + 2.0 * (2 * K + 1) ** 2 * 8.0, "GB/s",
+                "V_k(b) of both matrices written once (2 T (K+1) complex64) + the cotangent read once per matrix")
+    if name == "adj_dot":
+        return ("alu", 10.0 * 2.0 * V * (K + 1), "TFLOP/s",
+                "10 FP32 flops per corner-frequency term, 2 V (K+1) terms (E_k(a) by one complex rotation, "
+                "Re(E_k V_k) accumulated)")
     if name == "axis_lines":
         return ("alu", 4.0 * K * (T + 1), "Tops/s", "4 K (T+1) exact integer MACs (the two axis lines)")
     return None
@@ -513,7 +532,7 @@ def run_ours(args):
     forms = {0: "direct", 1: "grouped_tc", 2: "grouped_fft"}
     parts = {"forward": {"form": forms.get(fcfs.forward_grouped(V, T, K), "?"), "stages_ms": round(fwd_ms, 4),
                          "value": V * W * W / (fwd_ms * 1e-3)},
-             "adjoint": {"form": "grouped" if fcfs.adjoint_grouped(V, T, K) == 1 else "per corner",
+             "adjoint": {"form": ADJOINT_FORMS.get(fcfs.adjoint_grouped(V, T, K), "?"),
                          "stages_ms": round(adj_ms, 4), "value": V * W * W / (adj_ms * 1e-3)}}
 
     # ---- plain FP32 on the same clip (forward and adjoint) ----
@@ -626,8 +645,8 @@ def run_ours(args):
         "data": "synthetic (seeded Manhattan clip; stands in for the paper's proprietary 22 nm layout)",
         "config": {"workload": WORKLOAD,
                    "precision": ("split_f16 class (max|dF|/area <= 1e-5): the library's fastest form per call; "
-                                 "forward: corners grouped by y, FP32 pair sums and pruned FFT along y (FP32 "
-                                 "arithmetic); adjoint: split-FP16 tcgen05 contraction grouped by y and by x"),
+                                 "forward: %s; adjoint: %s" % (FORM_TEXT["forward"].get(parts["forward"]["form"], "?"),
+                                                              FORM_TEXT["adjoint"].get(parts["adjoint"]["form"], "?"))),
                    "T": T, "K": K, "V": V,
                    "l2": "workspaces exceed L2, and L2 is flushed before every timed step (256 MiB write, "
                          "outside the events)",
@@ -636,7 +655,7 @@ def run_ours(args):
         "parts": parts,
         "plain_fp32": {"value": value32, "unit": UNIT, "ms_per_step": statistics.mean(ms32),
                        "forward_form": forms.get(fcfs.forward_grouped(V, T, K, prec="fp32"), "?"),
-                       "adjoint_form": "per corner (FP32 CUDA cores)"},
+                       "adjoint_form": ADJOINT_FORMS.get(fcfs.adjoint_grouped(V, T, K, prec="fp32"), "?")},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -732,7 +751,7 @@ def run_extras(fcfs, dev, flush, stream, args):
     out["adjoint"] = {"workload": "clip T=2048, 5000 polygons, V=%d, K=128, pupil-disc loss vs edges "
                                   "jittered +-2; corner derivatives" % clip.V,
                       "value": clip.V * W * W / (ms16 * 1e-3), "unit": UNIT, "ms": ms16,
-                      "precision": "split_f16 (tcgen05 contraction)",
+                      "precision": "split_f16 class (%s)" % ADJOINT_FORMS.get(fcfs.adjoint_grouped(clip.V, T, K), "?"),
                       "fp32": {"value": clip.V * W * W / (ms * 1e-3), "ms": ms},
                       "_check": (clip, tgt, K, G.cpu().numpy(), gx.cpu().numpy(), gy.cpu().numpy(),
                                  gx16.cpu().numpy(), gy16.cpu().numpy())}
@@ -796,10 +815,35 @@ def run_extras(fcfs, dev, flush, stream, args):
             fcfs.set_hybrid(1)
         forms[key] = {"ms": ms5, "value": clip5.V * W5 * W5 / (ms5 * 1e-3),
                       "stages_ms": {n: round(t, 4) for n, t in kt}, "_F": F5, "_A": A5}
-    out["large"] = {"workload": "clip T=65536, 150000 polygons, V=%d, K=1024 (2049x2049), forward forms "
-                                "forced one by one" % clip5.V, "unit": UNIT,
+    # the same clip's adjoint (the step's cotangent), every form forced
+    G5 = torch.from_numpy(cotangent(K5)).to(dev)
+    aforms = {}
+    for mode, key in ((0, "per_corner_tc"), (2, "grouped_tc"), (3, "grouped_fft")):
+        fcfs.set_hybrid(mode)
+        try:
+            g5x = torch.empty(clip5.V, dtype=torch.float32, device=dev)
+            g5y = torch.empty_like(g5x)
+            wsa5 = torch.empty(fcfs._lib.load().fcfs_adjoint_workspace_size(clip5.V, clip5.T, K5, 1),
+                               dtype=torch.uint8, device=dev)
+            fn = lambda: fcfs.adjoint(x5, y5, s5, clip5.T, K5, G5, prec="split_f16", gx=g5x, gy=g5y, workspace=wsa5,
+                                      stream=stream)
+            ms5 = _timed_ms(torch, fn, 3, flush, stream)
+            flush.fill_(1)
+            fcfs.kernel_timing_enable(True)
+            fn()
+            kt = fcfs.kernel_timing()
+            fcfs.kernel_timing_enable(False)
+            del wsa5
+        finally:
+            fcfs.set_hybrid(1)
+        aforms[key] = {"ms": ms5, "value": clip5.V * W5 * W5 / (ms5 * 1e-3),
+                       "stages_ms": {n: round(t, 4) for n, t in kt}, "_g": (g5x, g5y)}
+    out["large"] = {"workload": "clip T=65536, 150000 polygons, V=%d, K=1024 (2049x2049), forward and adjoint "
+                                "forms forced one by one (split-FP16 class)" % clip5.V, "unit": UNIT,
                     "auto": {0: "direct_tc", 1: "grouped_tc", 2: "grouped_fft"}[fcfs.forward_grouped(clip5.V, clip5.T, K5)],
-                    "forms": forms, "_check": (clip5, K5)}
+                    "forms": forms,
+                    "adjoint_auto": ADJOINT_FORMS.get(fcfs.adjoint_grouped(clip5.V, clip5.T, K5), "?"),
+                    "adjoint_forms": aforms, "_check": (clip5, K5)}
 
     # the T = 4096 clip: one forward block (the contraction over its corners)
     clip2, K2 = config_clip(2)
@@ -1026,6 +1070,15 @@ def extras_accuracy(line, extras):
             F5 = d.pop("_F").cpu().numpy()[np.ix_(pick + K5, pick + K5)]
             d["max_abs_err_over_area_sampled"] = float(np.max(np.abs(F5 - Fo)) / A)
             d["area_exact"] = int(d.pop("_A").item()) == A
+        # adjoint forms: 64 sampled corners against the oracle's derivatives
+        rng = np.random.default_rng(64)
+        idx = np.sort(rng.choice(clip5.V, 64, replace=False))
+        Gq = cotangent(K5).astype(np.complex128)
+        rx, ry = oracle.vertex_gradient(clip5.x[idx], clip5.y[idx], clip5.s[idx], clip5.T, K5, Gq)
+        sc = max(float(np.max(np.abs(rx))), float(np.max(np.abs(ry))))
+        for key, d in line["large"]["adjoint_forms"].items():
+            g5x, g5y = (t.cpu().numpy().astype(np.float64)[idx] for t in d.pop("_g"))
+            d["max_rel_err_sampled"] = max(float(np.max(np.abs(g5x - rx))), float(np.max(np.abs(g5y - ry)))) / sc
     if "clip_T4096" in extras:
         clip2, K2 = extras["clip_T4096"].pop("_check")
         A = oracle.area_exact(clip2.x, clip2.y, clip2.s, clip2.T)

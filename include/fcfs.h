@@ -114,6 +114,11 @@ fcfs_status fcfs_forward(const int32_t* x, const int32_t* y, const int8_t* s, in
  *   gx[v] = -s_v Re sum_{k,l} conj(dF(k,l)) exp(-j 2 pi k x_v/T) X[l](y_v),
  *   gy[v] = -s_v Re sum_{k,l} conj(dF(k,l)) X[k](x_v) exp(-j 2 pi l y_v/T),
  * with the full tail integrals (per corner their constant parts do not cancel).
+ * Three forms (fcfs_adjoint_grouped): per corner, or with the corners grouped
+ * by the contracted coordinate b (y for gx, x for gy) either a split-FP16
+ * contraction over the values of b or, per frequency k, one input-pruned FFT
+ * of length T along b (P = T / L FFTs of length L >= 2K, the pruned FFT of
+ * Sec. III-C run on the adjoint) followed by one (K+1)-term dot per corner.
  *   gx, gy     : V floats each (device), written completely.
  * Workspace as for fcfs_forward, sized by fcfs_adjoint_workspace_size().
  */
@@ -173,8 +178,9 @@ fcfs_status fcfs_batch(const int32_t* x, const int32_t* y, const int8_t* s,
  * Knobs (fcfs_plan_set; -1 where allowed, or 0, means automatic):
  *   FCFS_KNOB_FORM        forward: 0 over the corners, 1 corners grouped by y
  *                         with the split-FP16 contraction over y, 2 grouped with
- *                         the pruned FFT along y; batch and adjoint: 0 per
- *                         corner / direct units, 1 grouped.
+ *                         the pruned FFT along y; adjoint: 0 per corner, 1
+ *                         grouped with the split-FP16 contraction, 2 grouped
+ *                         with the pruned FFT; batch: 0 direct units, 1 grouped.
  *   FCFS_KNOB_SPLITS      forward: vertex splits of the contraction.
  *   FCFS_KNOB_PAIR        forward and batch: 1 CTA-pair 256 x 256 tiles (2-SM
  *                         MMA) where eligible, 0 one-CTA tiles.
@@ -348,9 +354,15 @@ void fcfs_debug_set_fuse(int32_t on);
  * forms the call may take; fcfs_debug_set_hybrid(0), (2) and (3) force the
  * first, second and third. */
 int32_t fcfs_forward_grouped(int64_t V, int32_t T, int32_t K, int32_t prec);
-/* The same for fcfs_adjoint: 1 when its tensor-core contraction runs over the
- * values of the grouped coordinate, 0 per corner (and always 0 for FP32), -1
- * for unsupported sizes or precision. */
+/* The same for fcfs_adjoint: 0 the contraction per corner (tensor cores, or
+ * the plain FP32 kernel), 1 the corners grouped by y (gx) and by x (gy) and
+ * the split-FP16 contraction over the T + 1 values of the grouped coordinate
+ * (split-FP16 calls only), 2 grouped with the pruned FFT along it (the
+ * adjoint's sums over b as input-pruned FFTs, then one dot per corner; FP32,
+ * any precision, 16 <= T, 2K <= min(T, 4096)); -1 for unsupported sizes or
+ * precision.  The automatic choice compares cost estimates of the forms;
+ * fcfs_debug_set_hybrid(0), (2) and (3) force the first, second and third
+ * where they apply. */
 int32_t fcfs_adjoint_grouped(int64_t V, int32_t T, int32_t K, int32_t prec);
 /* fcfs_debug_set_pair(0) keeps single-clip split-FP16 calls on one-CTA
  * 128 x 256 tiles; 1 (the default) runs clips with 2K >= 256 on CTA pairs
@@ -371,9 +383,9 @@ void fcfs_debug_set_barrier_extra(int32_t n);
  * the call is eligible (split FP16, 2K >= 256, no device validation), 3 the
  * pruned FFT along y whenever eligible (any precision, K <= 4096, no device
  * validation).  Batches group when
- * V >= 8 n (T + 1) and K >= 256.  The split-FP16 adjoint groups its corners by
- * the contraction coordinate under the same modes, automatically when a cost
- * estimate of its two forms favours it.  Same results within
+ * V >= 8 n (T + 1) and K >= 256.  The adjoint takes its forms under the same
+ * modes (0 per corner, 2 grouped contraction, 3 grouped pruned FFT, 1 the
+ * cheapest estimate; fcfs_adjoint_grouped tells).  Same results within
  * the split-FP16 error bound.  Must not change between fcfs_workspace_size and
  * the call that uses the workspace. */
 void fcfs_debug_set_hybrid(int32_t mode);

@@ -44,33 +44,108 @@ struct AdjPlan {
   // hi / lo [hi|lo][matrix][nrows_pad][kdim_pad], its row terms and the k = 0 row
   int tc, nrows_pad, kdim_pad;
   size_t off_mp, off_rows, off_m0;
-  // grouped tensor-core contraction: the corners grouped by y and by x
-  int grouped, ny_pad;
+  // form: 0 per corner, 1 grouped tensor-core contraction, 2 grouped pruned FFT;
+  // the grouped forms group the corners by y (gx) and by x (gy)
+  int form, grouped, ny_pad;
   size_t off_groups;
+  // pruned FFT: T = P L, V_k at the polyphase positions, the side terms, the tables
+  int fft_logL;
+  size_t off_z, off_side, off_tabs;
 };
 constexpr int kAdjThreads = 128;
 constexpr size_t kAdjSmemBudget = 200 * 1024;
+
+// Estimated time (ms) of each adjoint form, fitted to GB300 measurements of
+// all of them on 17 clips (T = 1024 .. 65536, K = 64 .. 1024, V = 1.2e3 ..
+// 9.5e5; within 16% of each measured time, 48% for the FP32 contraction):
+//   per corner, tensor cores  0.037 + 1.97e-11 V K^2 + 5.76e-9 V K + 1.84e-7 K^2
+//   per corner, plain FP32    0.045 + 7.5e-10 V K^2 + 1.14e-6 K^2
+//   grouped, tensor cores     0.055 + 2.1e-6 T + 2.66e-11 (T + 1) K^2 + 9.74e-10 V K + 1.42e-7 K^2
+//   grouped, pruned FFT       0.022 + 4.03e-5 2 (K + 1)                  (one CTA per k and matrix)
+//                             + 3.58e-10 2 (K + 1) T log2 L + 3.43e-9 2 T (K + 1)   (FFTs; V_k
+//                             written and read once) + 1.77e-7 V
+// The pruned FFT measured fastest on every one of the 17 clips.
+static double adj_cost(int form, bool tc, double v, double k, double t, double logL) {
+  switch (form) {
+    case 0:
+      return tc ? 0.037 + 1.97e-11 * v * k * k + 5.76e-9 * v * k + 1.84e-7 * k * k
+                : 0.045 + 7.5e-10 * v * k * k + 1.14e-6 * k * k;
+    case 1: return 0.055 + 2.1e-6 * t + 2.66e-11 * (t + 1.0) * k * k + 9.74e-10 * v * k + 1.42e-7 * k * k;
+    default:
+      return 0.022 + 4.03e-5 * 2.0 * (k + 1.0) + 3.58e-10 * 2.0 * (k + 1.0) * t * logL +
+             3.43e-9 * 2.0 * t * (k + 1.0) + 1.77e-7 * v;
+  }
+}
+
+// FFT length of the pruned-FFT adjoint: the smallest power of two >= 2K (0 when
+// the form does not apply: L > T, L > 4096, T < 16 or T > 2^16).
+static int adj_fft_log_len(int T, int K) {
+  int lg = 1;
+  while ((1 << lg) < 2 * K) ++lg;
+  if (T < 16 || T > 65536 || (1 << lg) > T || lg > 12) return 0;
+  return lg;
+}
 
 static fcfs_status make_adj_plan(int64_t V, int32_t T, int32_t K, int32_t prec, AdjPlan& ap) {
   fcfs_status r = make_plan(V, T, K, FCFS_PREC_FP32, ap.p);
   if (r != FCFS_OK) return r;
   ap.tc = prec == FCFS_PREC_SPLIT_F16 ? 1 : 0;
+  ap.form = 0;
   ap.grouped = 0;
-  ap.ny_pad = 0;
+  ap.ny_pad = (T + 1 + 63) / 64 * 64;
   ap.off_groups = 0;
+  ap.fft_logL = adj_fft_log_len(T, K);
+  ap.off_z = ap.off_side = ap.off_tabs = 0;
   ap.rows = 2 * K + 1;
   ap.cols = 2 * K + 2;
   const size_t tab = align_up(tab_f32_bytes(T, ap.p.full), 128);
   ap.R = 0;
   for (int R : {64, 32, 16, 8})
     if (!ap.R && tab + (size_t)ap.cols * R * sizeof(float) <= kAdjSmemBudget) ap.R = R;
-  if (!ap.R) {   // the FP32 contraction needs a row tile in shared memory; the tensor cores do not
-    if (!ap.tc) return FCFS_EUNSUPPORTED;
-    ap.R = 8;
+  // the FP32 per-corner contraction needs a row tile in shared memory; the tensor cores do not
+  const bool per_corner_ok = ap.tc || ap.R > 0;
+  const bool tc_grouped_ok = ap.tc && V > 0;
+  const bool fft_ok = ap.fft_logL > 0 && V > 0;
+  if (!per_corner_ok && !fft_ok) return FCFS_EUNSUPPORTED;
+  {
+    const int mode = hybrid_knob();
+    const double v = (double)V, k = (double)K, t = (double)T, lg = (double)ap.fft_logL;
+    if (mode == 0 && per_corner_ok) ap.form = 0;
+    else if (mode == 2 && tc_grouped_ok) ap.form = 1;
+    else if (mode == 3 && fft_ok) ap.form = 2;
+    else {
+      double best = 1e300;
+      const bool ok[3] = {per_corner_ok, tc_grouped_ok, fft_ok};
+      for (int f = 0; f < 3; ++f) {
+        if (!ok[f]) continue;
+        const double c = adj_cost(f, ap.tc != 0, v, k, t, lg);
+        if (c < best) {
+          best = c;
+          ap.form = f;
+        }
+      }
+    }
   }
+  if (!ap.R) ap.R = 8;
   ap.row_tiles = (ap.rows + ap.R - 1) / ap.R;
   ap.rows_pad = ap.row_tiles * ap.R;
   size_t o = ap.p.off_part;   // the forward's split partials are not needed here
+  if (ap.form == 2) {
+    // corners grouped by the polyphase position of b, V_k for every b < T, side terms
+    ap.grouped = 1;
+    ap.off_groups = o;
+    o = align_up(o + 2 * group_bytes(V, T, ap.ny_pad), kWsAlign);
+    ap.off_side = o;
+    o = align_up(o + (size_t)2 * (K + 1) * sizeof(float4), kWsAlign);
+    ap.off_tabs = o;
+    o = align_up(o + adj_tables_bytes(ap.fft_logL), kWsAlign);
+    ap.off_z = o;
+    o = align_up(o + (size_t)2 * T * (K + 1) * sizeof(float2), kWsAlign);
+    ap.off_m = ap.off_part = 0;
+    ap.total = o;
+    ap.p.total = o;
+    return FCFS_OK;
+  }
   ap.off_m = o;
   o = align_up(o + (size_t)2 * ap.cols * ap.rows_pad * sizeof(float), kWsAlign);
   if (ap.tc) {
@@ -84,18 +159,8 @@ static fcfs_status make_adj_plan(int64_t V, int32_t T, int32_t K, int32_t prec, 
     ap.off_m0 = o;
     o = align_up(o + (size_t)2 * (ap.kdim_pad + 4) * sizeof(float), kWsAlign);
     // grouped form: the MMA runs over the T + 1 values of b and the epilogue
-    // over the corners grouped by b.  The automatic choice compares two cost
-    // estimates (ms) fitted to GB300 measurements of both forms (T = 2048 ..
-    // 65536, K = 128 .. 1024, V / (T + 1) = 1.9 .. 49; the estimate picks the
-    // faster form in all ten cases):
-    //   per corner  0.05 + 2.23e-11 V K^2 + 5.16e-9 V K
-    //   grouped     0.086 + 1.79e-6 T + 3.27e-11 (T + 1) K^2 + 8.5e-10 V K
-    const int mode = hybrid_mode();
-    const double v = (double)V, k = (double)K, t = (double)T;
-    const double per_corner = 0.05 + 2.23e-11 * v * k * k + 5.16e-9 * v * k;
-    const double grouped = 0.086 + 1.79e-6 * t + 3.27e-11 * (t + 1.0) * k * k + 8.5e-10 * v * k;
-    ap.grouped = V > 0 && (mode == 2 || (mode == 1 && grouped < per_corner)) ? 1 : 0;
-    ap.ny_pad = (T + 1 + 63) / 64 * 64;
+    // over the corners grouped by b
+    ap.grouped = ap.form == 1 ? 1 : 0;
     if (ap.grouped) {
       ap.off_groups = o;
       o = align_up(o + 2 * group_bytes(V, T, ap.ny_pad), kWsAlign);
@@ -380,10 +445,42 @@ static fcfs_status adjoint_impl(const int32_t* x, const int32_t* y, const int8_t
   if (r != FCFS_OK) return r;
   if ((r = check_ws(ap.p, ws, ws_bytes)) != FCFS_OK) return r;
   if (V == 0) return FCFS_OK;
-  if (ap.tc && (!aligned16_ptr(x) || !aligned16_ptr(y))) return FCFS_EINVAL;
+  if (ap.tc && ap.form != 2 && (!aligned16_ptr(x) || !aligned16_ptr(y))) return FCFS_EINVAL;
   {
     KtScope ks("adj_prep", st);
     if (launch_prep(ap.p, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
+  }
+  if (ap.form == 2) {
+    // pruned FFT along b for every k, then the per-corner dots
+    AdjFftArgs ar;
+    ar.pl = ap.p;
+    ar.pl.vx = x;
+    ar.pl.vy = y;
+    ar.pl.vsg = s;
+    ar.dF = reinterpret_cast<const float2*>(dF);
+    ar.logL = ap.fft_logL;
+    ar.logP = ap.p.logT - ap.fft_logL;
+    ar.off_z = ap.off_z;
+    ar.off_side = ap.off_side;
+    ar.off_groups = ap.off_groups;
+    ar.off_tabs = ap.off_tabs;
+    ar.ny_pad = ap.ny_pad;
+    ar.gx = gx;
+    ar.gy = gy;
+    {
+      KtScope ks("adj_group", st);
+      if (launch_grouping(y, x, V, T, ap.ny_pad, static_cast<uint8_t*>(ws) + ap.off_groups, st, ar.logP) !=
+          cudaSuccess)
+        return FCFS_ECUDA;
+    }
+    {
+      KtScope ks("adj_fft", st);
+      if (launch_adj_tables(ar, ws, st) != cudaSuccess || launch_adj_fft(ar, ws, st) != cudaSuccess)
+        return FCFS_ECUDA;
+    }
+    KtScope ks("adj_dot", st);
+    if (launch_adj_dot(ar, ws, st) != cudaSuccess) return FCFS_ECUDA;
+    return FCFS_OK;
   }
   {
     KtScope ks("adj_coef", st);
@@ -480,7 +577,7 @@ int32_t fcfs_adjoint_grouped(int64_t V, int32_t T, int32_t K, int32_t prec) {
   if (prec != FCFS_PREC_FP32 && prec != FCFS_PREC_SPLIT_F16) return -1;
   AdjPlan ap;
   if (make_adj_plan(V, T, K, prec, ap) != FCFS_OK) return -1;
-  return ap.grouped ? 1 : 0;
+  return ap.form;
 }
 
 fcfs_status fcfs_adjoint(const int32_t* x, const int32_t* y, const int8_t* s, int64_t V, int32_t T, int32_t K,

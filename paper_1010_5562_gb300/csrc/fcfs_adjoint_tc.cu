@@ -35,6 +35,7 @@
 #include <algorithm>
 
 #include "fcfs_common.cuh"
+#include "fcfs_fft.cuh"
 #include "fcfs_group.cuh"
 
 namespace fcfs {
@@ -78,40 +79,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
       : "memory");
-}
-
-// Packed FP32 pairs (Blackwell f32x2): d = a * b + c and d = a * b elementwise,
-// each element rounded as its scalar counterpart.
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return d;
-}
-__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
-// One angle-addition step (c, s) -> (c w.x - s w.y, s w.x + c w.y) in two packed operations.
-__device__ __forceinline__ float2 rot2(float2 v, float2 w) {
-  return ffma2(make_float2(v.y, v.x), make_float2(-w.y, w.y), fmul2(v, make_float2(w.x, w.x)));
-}
-
-// Two-level sincos table: (cos, sin)(2 pi p / T) = coarse[p >> f] * fine[p mod 2^f],
-// both factors correctly rounded FP32 values copied from the plan's table.
-struct TwoLevel {
-  const float2* t;   // coarse [nc], then fine [2^f]
-  uint32_t f, fmask, nc;
-};
-__device__ __forceinline__ float2 tl_lookup(const TwoLevel& tl, uint32_t p) {
-  const float2 c = tl.t[p >> tl.f], d = tl.t[tl.nc + (p & tl.fmask)];
-  return make_float2(fmaf(c.x, d.x, -(c.y * d.y)), fmaf(c.y, d.x, c.x * d.y));
 }
 
 template <bool GROUPED>

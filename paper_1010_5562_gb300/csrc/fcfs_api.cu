@@ -202,6 +202,7 @@ fcfs_status make_plan_cosine(int64_t V, int32_t T, int32_t K, int32_t prec, Plan
 }
 
 int hybrid_mode() { return knob_hybrid() == 3 ? 1 : knob_hybrid(); }
+int hybrid_knob() { return knob_hybrid(); }
 bool pair_enabled() { return knob_pair() != 0; }
 
 // The contraction of a single-clip call (fcfs_forward_grouped reports it):

@@ -503,6 +503,26 @@ struct AdjTcArgs {
   int ny_pad;       // grouped: T + 1 rounded up to 64 (the groups' exponent array)
   size_t off_groups;  // grouped: by y (gx), then by x (gy) (fcfs_group.cuh)
 };
+// Pruned-FFT adjoint (fcfs_adjoint_fft.cu): V_k(b) by input-pruned FFTs along
+// the grouped coordinate b, then per-corner dots.
+struct AdjFftArgs {
+  Plan pl;              // T, K, tables, status; vx, vy, vsg the corners
+  const float2* dF;     // (2K+1)^2 cotangent
+  int logL, logP;       // T = P L, L = 2^logL >= 2K
+  size_t off_z;         // complex FP32 [2][T/16][K+1][16]: V_k at polyphase positions b'
+  size_t off_side;      // float4 [2][K+1]: const_k (re, im), lin_k (re, im)
+  size_t off_groups;    // corners grouped by the polyphase position of y (gx), then of x (gy)
+  size_t off_tabs;      // float2 tables of the FFTs and dots (adj_tables_bytes)
+  int ny_pad;
+  float* gx;
+  float* gy;
+};
+size_t adj_fft_smem(int K, int logL);
+size_t adj_tables_bytes(int logL);
+cudaError_t launch_adj_tables(const AdjFftArgs& ar, void* ws, cudaStream_t st);
+cudaError_t launch_adj_fft(const AdjFftArgs& ar, void* ws, cudaStream_t st);
+cudaError_t launch_adj_dot(const AdjFftArgs& ar, void* ws, cudaStream_t st);
+
 // Launch-shape knobs of a call: a plan's (fcfs_plan_*) while one of its calls
 // runs on this thread, else the process-wide test and tuning hooks.  Negative
 // (or, for splits and unit chunks, zero) values defer to the hooks.
@@ -521,6 +541,8 @@ struct KnobScope {
 int knob_splits();
 // Row-binned (grouped) mode of the forward and adjoint calls: 0 never, 1 automatic, 2 forced
 int hybrid_mode();
+// the form knob itself: 0 direct / per corner, 1 automatic, 2 grouped tensor-core, 3 grouped FFT
+int hybrid_knob();
 // CTA pairs for 2K >= 256 on the split-FP16 path (fcfs_debug_set_pair)
 bool pair_enabled();
 cudaError_t launch_adj_tc(const AdjTcArgs& ar, const CUtensorMap& mhi, const CUtensorMap& mlo, void* ws,

@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "fcfs_epilogue.cuh"
+#include "fcfs_fft.cuh"
 #include "fcfs_launch.cuh"
 
 namespace fcfs {
@@ -38,111 +39,6 @@ struct FftArgs {
   int logL, logP;
   float2* F;            // (2K+1)^2 block
 };
-
-__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.y, b.x, a.x * b.y));
-}
-// a * e^{-j 2 pi q / R} for the compile-time twiddles of the radix butterflies
-template <int R, int Q>
-__device__ __forceinline__ float2 rot(float2 a) {
-  constexpr int q = Q % R;
-  if constexpr (q == 0) {
-    return a;
-  } else if constexpr (4 * q == R) {   // -j
-    return make_float2(a.y, -a.x);
-  } else if constexpr (2 * q == R) {
-    return make_float2(-a.x, -a.y);
-  } else if constexpr (4 * q == 3 * R) {   // +j
-    return make_float2(-a.y, a.x);
-  } else {
-    // cos and sin of 2 pi q / R for R in {8, 16}
-    constexpr double c8 = 0.70710678118654752440, c16 = 0.92387953251128675613, s16 = 0.38268343236508977173;
-    constexpr int qq = R == 8 ? 2 * q : q;   // in sixteenths of a turn
-    constexpr double cs = (qq == 1 || qq == 15) ? c16 : (qq == 2 || qq == 14) ? c8 : (qq == 3 || qq == 13) ? s16
-                        : (qq == 5 || qq == 11) ? -s16 : (qq == 6 || qq == 10) ? -c8 : -c16;
-    constexpr double sn = (qq == 1 || qq == 7) ? s16 : (qq == 2 || qq == 6) ? c8 : (qq == 3 || qq == 5) ? c16
-                        : (qq == 9 || qq == 15) ? -s16 : (qq == 10 || qq == 14) ? -c8 : -c16;
-    const float c = (float)cs, s = (float)sn;   // e^{-j t} = c - j s
-    return make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -(a.x * s)));
-  }
-}
-
-// In-register DFT of R points, forward sign, by halving (even/odd).
-template <int R>
-struct Dft {
-  template <int S, int O>
-  __device__ __forceinline__ static void sub(const float2* x, float2* y) {
-    // y[q] = sum_r x[O + S r] e^{-j 2 pi q r / R}, q < R
-    if constexpr (R == 1) {
-      y[0] = x[O];
-    } else {
-      float2 e[R / 2], o[R / 2];
-      Dft<R / 2>::template sub<2 * S, O>(x, e);
-      Dft<R / 2>::template sub<2 * S, O + S>(x, o);
-      apply<0>(e, o, y);
-    }
-  }
-  template <int Q>
-  __device__ __forceinline__ static void apply(const float2* e, const float2* o, float2* y) {
-    if constexpr (Q < R / 2) {
-      const float2 t = rot<R, Q>(o[Q]);
-      y[Q] = c_add(e[Q], t);
-      y[Q + R / 2] = c_sub(e[Q], t);
-      apply<Q + 1>(e, o, y);
-    }
-  }
-};
-
-// Shared-memory buffers are padded by one element per 16 (index i at i + i/16),
-// so the strided stores of the first passes fall on distinct banks.
-__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
-
-// Twiddle level of a pass, e^{-j 2 pi i / M} for i < M: a table of M entries
-// for M <= 256, else the product hi[i >> 6] lo[i & 63] of two correctly
-// rounded tables (M / 64 and 64 entries).
-struct TwLevel {
-  const float2* hi;
-  const float2* lo;
-  int two;
-};
-__device__ __forceinline__ float2 tw_at(const TwLevel& t, int i) {
-  return t.two ? c_mul(t.hi[i >> 6], t.lo[i & 63]) : t.hi[i];
-}
-
-// One Stockham pass of radix R over nfft FFTs of L points: X -> Y (Y padded; X
-// padded, or unpadded for the first pass, which reads the buffer the bulk copy
-// filled).
-template <int R, bool RAW_IN>
-__device__ __forceinline__ void stockham_pass(const float2* __restrict__ X, float2* __restrict__ Y,
-                                              const TwLevel& twl, int logL, int nfft, int Ns) {
-  const int L = 1 << logL, per = L / R, M = Ns * R;
-  const int total = nfft * per;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int fo = (t / per) * L, j = t % per;
-    const int kp = j & (Ns - 1);
-    float2 v[R], y[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = RAW_IN ? X[fo + j + r * per] : X[pad16(fo + j + r * per)];
-    if (kp != 0) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], tw_at(twl, (r * kp) & (M - 1)));
-    }
-    Dft<R>::template sub<1, 0>(v, y);
-    const int base = fo + (j - kp) * R + kp;
-#pragma unroll
-    for (int q = 0; q < R; ++q) Y[pad16(base + q * Ns)] = y[q];
-  }
-}
-
-// Pass structure of an L = 2^logL point FFT: a first pass of radix 2^f0 (f0 =
-// logL mod 4, or 4), then radix-16 passes.  Pass i >= 1 runs at Ns = 2^(f0 + 4(i-1))
-// with twiddle level M_i = 2^(f0 + 4 i), stored after the levels before it.
-__device__ __forceinline__ int first_log_radix(int logL) { return (logL & 3) ? (logL & 3) : 4; }
-
-// Entries of the twiddle level of size 2^lm.
-__host__ __device__ __forceinline__ int level_entries(int lm) { return lm <= 8 ? 1 << lm : (1 << (lm - 6)) + 64; }
 
 // blockIdx.x = k - 1; NT threads (256, or 1024 when 2K + 1 > 9 * 256).  The
 // residues' inputs arrive by bulk copy into an unpadded buffer, the next range's

@@ -9,7 +9,9 @@
 //                                         to [0, 15]; 0 for groups of <= 2^14 corners)
 //   int32 perm[V]                         corner indices, group after group
 // start[T + 1] is the number of grouped corners; corners whose coordinate is
-// outside [0, T] are left out.  The order inside a group is whatever the
+// outside [0, T] are left out.  The group of a corner is its coordinate, or,
+// for the adjoint's pruned FFT, the polyphase position of the coordinate
+// (group_key).  The order inside a group is whatever the
 // atomic cursors give: users must not depend on it.
 #pragma once
 
@@ -21,6 +23,15 @@ __host__ __device__ inline int group_stride(int T) { return (T + 2 + 3) & ~3; }
 
 __host__ __device__ inline size_t group_bytes(int64_t V, int T, int ny_pad) {
   return align_up(align_up((size_t)3 * group_stride(T) * 4 + (size_t)ny_pad, 16) + (size_t)(V > 0 ? V : 1) * 4, 256);
+}
+
+// Group of coordinate c in [0, T]: c itself (key_logP < 0), or its position in
+// the polyphase order of a period T = P L, P = 2^key_logP: (c mod P) L + c / P,
+// with c = T on the position of 0 (the periodic functions repeat there).
+__host__ __device__ inline int group_key(int c, int T, int key_logP) {
+  if (key_logP < 0) return c;
+  const int b = c == T ? 0 : c;
+  return (b & ((1 << key_logP) - 1)) * (T >> key_logP) + (b >> key_logP);
 }
 
 struct Groups {
@@ -61,9 +72,9 @@ __host__ __device__ inline Groups groups_clip(uint8_t* base, int T, int ny_pad, 
 }
 
 // Group the V corners by c0 (and, with c1 != nullptr, separately by c1 into
-// the next region, base + group_bytes): a memset and three kernels (count,
-// scan, scatter) whatever the number of coordinates.
+// the next region, base + group_bytes), on group_key(c, T, key_logP): a memset
+// and three kernels (count, scan, scatter) whatever the number of coordinates.
 cudaError_t launch_grouping(const int32_t* c0, const int32_t* c1, int64_t V, int T, int ny_pad, uint8_t* base,
-                            cudaStream_t st);
+                            cudaStream_t st, int key_logP = -1);
 
 }  // namespace fcfs

@@ -32,13 +32,13 @@ namespace {
 // Stage 1: grouping (fcfs_group.cuh); blockIdx.y selects the coordinate
 // ---------------------------------------------------------------------------
 __global__ void group_count_kernel(const int32_t* __restrict__ c0, const int32_t* __restrict__ c1, long long V,
-                                   int T, int ny_pad, uint8_t* base) {
+                                   int T, int ny_pad, uint8_t* base, int key_logP) {
   griddep_wait();   // may be launched behind the previous kernel (programmatic dependent launch)
   const int32_t* c = blockIdx.y ? c1 : c0;
   const Groups g = groups_at(base + blockIdx.y * group_bytes(V, T, ny_pad), T, ny_pad);
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
     const int y = __ldg(c + v);
-    if (y >= 0 && y <= T) atomicAdd(&g.cnt[y], 1);
+    if (y >= 0 && y <= T) atomicAdd(&g.cnt[group_key(y, T, key_logP)], 1);
   }
 }
 
@@ -137,13 +137,13 @@ __global__ void batch_group_scatter_kernel(const int32_t* __restrict__ y, const 
 }
 
 __global__ void group_scatter_kernel(const int32_t* __restrict__ c0, const int32_t* __restrict__ c1, long long V,
-                                     int T, int ny_pad, uint8_t* base) {
+                                     int T, int ny_pad, uint8_t* base, int key_logP) {
   griddep_wait();
   const int32_t* c = blockIdx.y ? c1 : c0;
   const Groups g = groups_at(base + blockIdx.y * group_bytes(V, T, ny_pad), T, ny_pad);
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
     const int y = __ldg(c + v);
-    if (y >= 0 && y <= T) g.perm[atomicAdd(&g.cur[y], 1)] = (int)v;
+    if (y >= 0 && y <= T) g.perm[atomicAdd(&g.cur[group_key(y, T, key_logP)], 1)] = (int)v;
   }
 }
 
@@ -983,7 +983,7 @@ size_t hybrid_extra_bytes(int64_t V, int T, int M2, int ny_pad, size_t& off_ycnt
 }
 
 cudaError_t launch_grouping(const int32_t* c0, const int32_t* c1, int64_t V, int T, int ny_pad, uint8_t* base,
-                            cudaStream_t st) {
+                            cudaStream_t st, int key_logP) {
   const int nc = c1 ? 2 : 1;
   const size_t gb = group_bytes(V, T, ny_pad);
   for (int i = 0; i < nc; ++i) {
@@ -996,13 +996,13 @@ cudaError_t launch_grouping(const int32_t* c0, const int32_t* c1, int64_t V, int
   const int vblocks = (int)std::max<long long>(1, std::min<long long>((V + 255) / 256, 8LL * sms));
   cudaError_t e;
   if ((e = launch_after(group_count_kernel, dim3(vblocks, nc), dim3(256), 0, st, c0, c1, (long long)V, T, ny_pad,
-                        base)) != cudaSuccess)
+                        base, key_logP)) != cudaSuccess)
     return e;
   if ((e = launch_after(group_scan_kernel, dim3(nc), dim3(kScanThreads), 0, st, (long long)V, T, ny_pad, base)) !=
       cudaSuccess)
     return e;
   return launch_after(group_scatter_kernel, dim3(vblocks, nc), dim3(256), 0, st, c0, c1, (long long)V, T, ny_pad,
-                      base);
+                      base, key_logP);
 }
 
 // Group the corners of a single clip or of every clip of a batch by y.

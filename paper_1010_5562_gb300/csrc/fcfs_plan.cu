@@ -33,8 +33,8 @@ namespace {
 // FCFS_KNOB_FORM of a plan -> Knobs::hybrid for its kind
 int hybrid_of(int32_t kind, int64_t form) {
   if (form < 0) return -1;
-  if (kind == FCFS_PLAN_FORWARD) return form == 0 ? 0 : (form == 1 ? 2 : 3);
-  return form == 0 ? 0 : 2;   // batch and adjoint: direct units / per corner, or grouped
+  if (kind == FCFS_PLAN_BATCH) return form == 0 ? 0 : 2;   // direct units, or grouped
+  return form == 0 ? 0 : (form == 1 ? 2 : 3);   // forward and adjoint: direct, grouped tc, grouped FFT
 }
 
 bool valid(const fcfs_plan_s* p) { return p != nullptr && p->kind >= 0 && p->kind <= FCFS_PLAN_ADJOINT; }
@@ -68,7 +68,7 @@ fcfs_status fcfs_plan_set(fcfs_plan p, int32_t knob, int64_t value) {
   if (!valid(p)) return FCFS_EINVAL;
   switch (knob) {
     case FCFS_KNOB_FORM:
-      if (value < -1 || value > (p->kind == FCFS_PLAN_FORWARD ? 2 : 1)) return FCFS_EINVAL;
+      if (value < -1 || value > (p->kind == FCFS_PLAN_BATCH ? 1 : 2)) return FCFS_EINVAL;
       p->form = value;
       p->kn.hybrid = hybrid_of(p->kind, value);
       return FCFS_OK;

@@ -127,7 +127,8 @@ class Plan:
     """A workload's sizes and launch-shape choices (fcfs_plan_* of the C ABI).
 
     Knobs: form (forward: 0 over the corners, 1 split-FP16 contraction over y,
-    2 pruned FFT along y; batch/adjoint: 0 direct, 1 grouped), splits, pair,
+    2 pruned FFT along y; adjoint: 0 per corner, 1 grouped split-FP16
+    contraction, 2 grouped pruned FFT; batch: 0 direct, 1 grouped), splits, pair,
     unit_chunks; -1 or 0 leaves a knob to the library.  get() returns the value
     a call will use.  The plan is released when the object is."""
 
@@ -253,8 +254,10 @@ def forward_grouped(V, T, K, prec="split_f16"):
 
 
 def adjoint_grouped(V, T, K, prec="split_f16"):
-    """1 if adjoint() groups the corners for these sizes, 0 if it works per
-    corner, -1 if the sizes or the precision are unsupported."""
+    """Which form adjoint() takes for these sizes: 0 per corner, 1 corners
+    grouped by the contracted coordinate with the split-FP16 contraction over
+    its values, 2 grouped with one pruned FFT along it per frequency and a dot
+    per corner (FP32); -1 if the sizes or the precision are unsupported."""
     return int(_lib.load().fcfs_adjoint_grouped(int(V), int(T), int(K), _prec(prec)))
 
 
@@ -292,9 +295,10 @@ def set_barrier_extra(n):
 
 
 def set_hybrid(mode):
-    """Grouping of single-clip forward calls by y: 0 never, 1 automatic (cost
-    estimates; see forward_grouped), 2 the split-FP16 contraction over y whenever
-    eligible, 3 the pruned FFT along y whenever eligible."""
+    """Form of single-clip forward and adjoint calls: 0 direct / per corner, 1
+    automatic (cost estimates; see forward_grouped and adjoint_grouped), 2 the
+    grouped split-FP16 contraction whenever eligible, 3 the grouped pruned FFT
+    whenever eligible."""
     _lib.load().fcfs_debug_set_hybrid(int(mode))
 
 

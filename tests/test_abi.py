@@ -187,12 +187,17 @@ FORWARD_SWEEP = [
     (65536, 256, 945586, 1, "tie"), (2048, 128, 31546, 1, "direct"),
     (2048, 128, 31546, 0, "grouped_fft"),
 ]
+# adjoint: (T, K, V, fastest form) from the GB300 measurements of all four
+# (per corner on tensor cores, per corner FP32, grouped tensor cores, pruned FFT)
 ADJOINT_SWEEP = [
-    (2048, 128, 31700, "direct"), (4096, 256, 12622, "tie"), (4096, 256, 50386, "grouped"),
-    (4096, 256, 201294, "grouped"), (4096, 1024, 50386, "grouped"), (16384, 512, 200908, "grouped"),
-    (65536, 1024, 125716, "grouped"), (65536, 512, 377722, "grouped"), (65536, 256, 945586, "grouped"),
-    (65536, 1024, 945586, "grouped"),
+    (2048, 128, 31700, "fft"), (4096, 256, 3144, "fft"), (4096, 256, 12622, "fft"),
+    (4096, 1024, 12622, "fft"), (4096, 256, 50386, "fft"), (4096, 1024, 50386, "fft"),
+    (4096, 256, 201294, "fft"), (16384, 512, 188808, "fft"), (65536, 1024, 125716, "fft"),
+    (65536, 256, 125716, "tie"), (65536, 1024, 945450, "fft"), (65536, 512, 945450, "fft"),
+    (65536, 256, 945450, "fft"), (2048, 128, 1232, "fft"), (2048, 512, 1232, "fft"),
+    (1024, 64, 1836, "fft"), (1024, 256, 1836, "fft"),
 ]
+ADJOINT_FORMS = {0: "per_corner", 1: "grouped_tc", 2: "fft"}
 FORWARD_MISSES = []
 
 
@@ -207,10 +212,22 @@ def test_automatic_choices_against_the_sweeps(lib):
             misses.append((T, K, V, prec))
     assert sorted(misses) == sorted(FORWARD_MISSES), misses
     for T, K, V, best in ADJOINT_SWEEP:
-        got = "grouped" if lib.fcfs_adjoint_grouped(V, T, K, 1) == 1 else "direct"
-        assert best == "tie" or got == best, (T, K, V, got)
-    assert lib.fcfs_adjoint_grouped(945586, 65536, 1024, 0) == 0    # the FP32 adjoint never groups
+        for prec in (1, 0):   # split FP16, plain FP32: the pruned FFT wins in both classes
+            got = ADJOINT_FORMS[lib.fcfs_adjoint_grouped(V, T, K, prec)]
+            assert best == "tie" or got == best, (T, K, V, prec, got)
     assert lib.fcfs_adjoint_grouped(100, 1000, 8, 1) == -1
+    assert lib.fcfs_adjoint_grouped(40, 8, 2, 1) == 0              # T < 16: no pruned FFT
+    assert lib.fcfs_adjoint_grouped(40, 4096, 4096, 1) in (0, 1)   # 2K > 4096: no pruned FFT
+    try:
+        lib.fcfs_debug_set_hybrid(0)
+        assert lib.fcfs_adjoint_grouped(945450, 65536, 1024, 1) == 0
+        lib.fcfs_debug_set_hybrid(2)
+        assert lib.fcfs_adjoint_grouped(945450, 65536, 1024, 1) == 1
+        assert lib.fcfs_adjoint_grouped(945450, 65536, 1024, 0) == 2   # FP32: no tensor-core form
+        lib.fcfs_debug_set_hybrid(3)
+        assert lib.fcfs_adjoint_grouped(31700, 2048, 128, 1) == 2
+    finally:
+        lib.fcfs_debug_set_hybrid(1)
 
 
 def test_python_contraction_queries(lib):
@@ -218,9 +235,9 @@ def test_python_contraction_queries(lib):
     from paper_1010_5562_gb300 import fcfs
     assert fcfs.forward_grouped(945450, 65536, 1024) == 2
     assert fcfs.forward_grouped(12576, 4096, 256) == 0
-    assert fcfs.adjoint_grouped(945586, 65536, 1024) == 1
-    assert fcfs.adjoint_grouped(31700, 2048, 128) == 0
-    assert fcfs.adjoint_grouped(945586, 65536, 1024, prec="fp32") == 0
+    assert fcfs.adjoint_grouped(945586, 65536, 1024) == 2
+    assert fcfs.adjoint_grouped(31700, 2048, 128) == 2
+    assert fcfs.adjoint_grouped(945586, 65536, 1024, prec="fp32") == 2
     assert fcfs.forward_grouped(100, 1000, 8) == -1
 
 
@@ -260,8 +277,12 @@ def test_plans_host(lib):
     a = C.c_void_p()
     assert lib.fcfs_plan_create(C.byref(a), 2, 945586, 1, 65536, 1024, 1) == 0
     try:
-        assert lib.fcfs_plan_get(a, 0) == 1                        # the grouped adjoint
+        assert lib.fcfs_plan_get(a, 0) == 2                        # the pruned-FFT adjoint
+        auto_ws = lib.fcfs_plan_workspace_size(a)
+        assert auto_ws >= 2 * 65536 * 1025 * 8                     # V_k of both matrices
+        assert lib.fcfs_plan_set(a, 0, 1) == 0 and lib.fcfs_plan_get(a, 0) == 1
         assert lib.fcfs_plan_set(a, 0, 0) == 0 and lib.fcfs_plan_get(a, 0) == 0
+        assert lib.fcfs_plan_set(a, 0, 3) == 1                     # no such form
         assert lib.fcfs_plan_workspace_size(a) > 0
     finally:
         lib.fcfs_plan_destroy(a)

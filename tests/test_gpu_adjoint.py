@@ -192,7 +192,7 @@ def test_grouped_adjoint_large_groups(fc):
     rng = np.random.default_rng(9)
     W = 2 * K + 1
     G = rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))
-    gx, gy = grad_mode(fc, clip, K, G, 1)   # automatic: per corner at K = 128 (the cost estimate)
+    gx, gy = grad_mode(fc, clip, K, G, 1)   # automatic
     gx2, gy2 = grad_mode(fc, clip, K, G, 2)
     idx = np.sort(rng.choice(clip.V, 48, replace=False))
     rx, ry = oracle.vertex_gradient(clip.x[idx], clip.y[idx], clip.s[idx], T, K, G)
@@ -201,20 +201,22 @@ def test_grouped_adjoint_large_groups(fc):
 
 
 def test_grouped_adjoint_launches(fc):
-    """Grouped: prep, coefficients, pack, count, scan, scatter, contraction,
-    finalize; per corner: prep, coefficients, pack, contraction, finalize.
-    Workload 4 stays per corner automatically: the cost estimates favour it
-    (measured 0.074 ms per corner against 0.081 grouped)."""
+    """Grouped tensor-core form: prep, coefficients, pack, count, scan, scatter,
+    contraction, finalize; per corner: prep, coefficients, pack, contraction,
+    finalize.  Workload 4 takes the pruned-FFT form automatically (measured
+    0.044 ms against 0.075 for either tensor-core form): prep, count, scan,
+    scatter, tables, FFTs, dots."""
     clip, K = config_clip(4)
     x, y, s = dev(clip.x), dev(clip.y), dev(clip.s)
     dF = torch.zeros((2 * K + 1, 2 * K + 1), dtype=torch.complex64, device="cuda")
     n0 = fc.launch_count()
     fc.adjoint(x, y, s, clip.T, K, dF, prec="split_f16")
-    assert fc.launch_count() - n0 == 5
-    fc.set_hybrid(2)
+    assert fc.launch_count() - n0 == 7
     try:
-        n0 = fc.launch_count()
-        fc.adjoint(x, y, s, clip.T, K, dF, prec="split_f16")
-        assert fc.launch_count() - n0 == 8
+        for mode, n in ((0, 5), (2, 8)):
+            fc.set_hybrid(mode)
+            n0 = fc.launch_count()
+            fc.adjoint(x, y, s, clip.T, K, dF, prec="split_f16")
+            assert fc.launch_count() - n0 == n, mode
     finally:
         fc.set_hybrid(1)

@@ -177,7 +177,7 @@ def test_adjoint_plan_matches_call(fc):
     W = 2 * K + 1
     G = torch.from_numpy((rng.standard_normal((W, W)) + 1j * rng.standard_normal((W, W))).astype(np.complex64)).cuda()
     x, y, s = (torch.from_numpy(a).cuda() for a in (clip.x, clip.y, clip.s))
-    for form in (0, 1):
+    for form in (0, 1, 2):
         plan = fc.Plan("adjoint", clip.V, clip.T, K, "split_f16", form=form)
         assert plan.get("form") == form
         gx, gy = plan.adjoint(x, y, s, G)
