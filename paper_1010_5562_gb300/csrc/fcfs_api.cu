@@ -108,7 +108,7 @@ static int knob_hybrid() { return t_knobs && t_knobs->hybrid >= 0 ? t_knobs->hyb
 // Tag of the cached tables: their kind, period, fixed-point scale and offsets.
 static uint64_t table_tag(const Plan& pl) {
   uint64_t h = 0xCBF29CE484222325ull;   // FNV-1a over the fields that fix the table bytes
-  const uint64_t f[6] = {3u /* layout version */, (uint64_t)pl.T, (uint64_t)pl.fixq, (uint64_t)pl.full,
+  const uint64_t f[6] = {4u /* layout version */, (uint64_t)pl.T, (uint64_t)pl.fixq, (uint64_t)pl.full,
                          (uint64_t)pl.off_tab_f32, (uint64_t)pl.off_tab_fix};
   for (uint64_t v : f)
     for (int b = 0; b < 8; ++b) {
@@ -177,6 +177,12 @@ static fcfs_status plan_impl(int64_t V, int32_t T, int32_t K, int32_t prec, bool
   o = align_up(o + bins_bytes(T), kWsAlign);
   pl.off_hist = o;
   o = align_up(o + (size_t)2 * (T + 1) * sizeof(int), kWsAlign);
+  if (single && !cosine && T >= kAxisFftMinT) {
+    // before the partials: the grouped forms lay their regions out from off_part
+    pl.axfft = 1;
+    pl.off_axfft = o;
+    o = align_up(o + axis_fft_bytes(T, K), kWsAlign);
+  }
   pl.off_part = o;
   o = align_up(o + (size_t)pl.splits * pl.M2 * pl.M2 * sizeof(float), kWsAlign);
   pl.total = o;

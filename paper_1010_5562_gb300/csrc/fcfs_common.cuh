@@ -20,6 +20,8 @@ constexpr int kFullTableMaxT = 8192;   // full-period tables up to this T, quart
 // so their full-period tables stop at T = 4096 (32 KiB)
 constexpr int kTcFullTableMaxT = 4096;
 constexpr int kWsAlign = 256;
+// single clips from this period on take the axis lines by a pruned FFT of the bins
+constexpr int kAxisFftMinT = 16384;
 
 struct Plan {
   int64_t V;
@@ -71,6 +73,10 @@ struct Plan {
   // continuous cosine series: T is twice the clip's period and the M2 = K rows
   // (and columns) of the contraction are sin(2 pi f a / T), f = 1..K, only
   int32_t cosine;
+  // single clips of T >= 16384: the axis lines by a pruned FP64 FFT of the bins
+  // (fcfs_axis_fft.cu) into the same fixed-point sums
+  int32_t axfft;
+  size_t off_axfft;            // complex FP64 [2][P][K] residue sums, then int64 [P] area parts
 };
 
 // Bin one corner for the axis lines (Steps 2-3): bin_x[x] += s y, bin_y[y] += s x
@@ -518,6 +524,9 @@ struct AdjFftArgs {
   float* gy;
 };
 size_t adj_fft_smem(int K, int logL);
+// axis lines of a single large clip by a pruned FFT of the bins
+size_t axis_fft_bytes(int T, int K);
+cudaError_t launch_axis_fft(const Plan& pl, void* ws, cudaStream_t st);
 size_t adj_tables_bytes(int logL);
 cudaError_t launch_adj_tables(const AdjFftArgs& ar, void* ws, cudaStream_t st);
 cudaError_t launch_adj_fft(const AdjFftArgs& ar, void* ws, cudaStream_t st);

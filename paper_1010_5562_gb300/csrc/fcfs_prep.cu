@@ -319,6 +319,7 @@ cudaError_t launch_axis(const Plan& pl, const int32_t* x, const int32_t* y, cons
                                        st, pl, x, y, s, static_cast<uint8_t*>(ws), validate ? 1 : 0);
     if (e != cudaSuccess) return e;
   }
+  if (pl.axfft) return launch_axis_fft(pl, ws, st);   // large single clips: pruned FFT of the bins
   const int kblocks = (pl.K + kAxisThreads - 1) / kAxisThreads;
   const int clips = pl.batch ? pl.n_clips : 1;
   // blocks per SM to aim for: many when the level tables are small (each
