@@ -64,10 +64,6 @@ __device__ __forceinline__ float2 tab_w(const float2* wc, const float2* wf, uint
   return c_mul(wc[p >> f], wf[p & ((1u << f) - 1u)]);
 }
 
-// Twiddle level of a radix-16 pass of size 2^lm: a direct table up to 2^11
-// entries, else 2^(lm-6) coarse and 64 fine entries.
-__host__ __device__ constexpr int adj_level_entries(int lm) { return lm <= 11 ? 1 << lm : (1 << (lm - 6)) + 64; }
-__host__ __device__ constexpr int adj_first_log_radix(int logL) { return (logL & 3) ? (logL & 3) : 4; }
 
 // Shared-memory layout of the FFT kernel: two padded buffers, the
 // coefficients c_{k,l} (l = -K..K), the two-level table, the pass twiddles,
@@ -79,7 +75,7 @@ struct FftSmem {
     s.bufpts = ((kABufPts + (kABufPts >> 4)) + 2) & ~1;   // L <= kABufPts (K <= 2048)
     s.ncoef = (2 * K + 1 + 1) & ~1;
     s.nlev = 0;
-    for (int lm = adj_first_log_radix(logL) + 4; lm <= logL; lm += 4) s.nlev += adj_level_entries(lm);
+    for (int lm = first_log_radix(logL) + 4; lm <= logL; lm += 4) s.nlev += tw_level_entries(lm);
     return s;
   }
   __host__ __device__ size_t bytes() const { return (size_t)(2 * bufpts + ncoef + 2 * kATab + nlev + kAFTab) * 8; }
@@ -96,9 +92,9 @@ struct TabLayout {
   int n2, n3, total;
   __host__ __device__ static TabLayout of(int logL) {
     TabLayout t;
-    const int f0 = adj_first_log_radix(logL);
-    t.n2 = f0 + 4 <= logL ? adj_level_entries(f0 + 4) : 0;
-    t.n3 = f0 + 8 <= logL ? adj_level_entries(f0 + 8) : 0;
+    const int f0 = first_log_radix(logL);
+    t.n2 = f0 + 4 <= logL ? tw_level_entries(f0 + 4) : 0;
+    t.n3 = f0 + 8 <= logL ? tw_level_entries(f0 + 8) : 0;
     t.total = 2 * kATab + t.n2 + t.n3 + kAFTab;
     return t;
   }
@@ -108,7 +104,7 @@ __global__ void adj_tables_kernel(AdjFftArgs ar, uint8_t* ws) {
   const Plan& pl = ar.pl;
   const int T = pl.T, logT = pl.logT, logL = ar.logL;
   const TabLayout lay = TabLayout::of(logL);
-  const int f0 = adj_first_log_radix(logL);
+  const int f0 = first_log_radix(logL);
   const uint32_t logQ = (uint32_t)logT - 2u, mask = (uint32_t)T - 1u;
   const uint32_t f = ((uint32_t)logT + 1u) / 2u, nc = (uint32_t)T >> f;
   const float* gt = reinterpret_cast<const float*>(ws + pl.off_tab_f32);
@@ -143,7 +139,7 @@ __global__ void adj_tables_kernel(AdjFftArgs ar, uint8_t* ws) {
 // One CTA per (k, m): blockIdx.x = k in [0, K], blockIdx.y = m; L = 2^LOGL.
 template <int LOGL>
 __global__ void __launch_bounds__(kAFftThreads, 2) adj_fft_kernel(AdjFftArgs ar, uint8_t* ws) {
-  constexpr int L = 1 << LOGL, F0 = adj_first_log_radix(LOGL), R0 = 1 << F0;
+  constexpr int L = 1 << LOGL, F0 = first_log_radix(LOGL), R0 = 1 << F0;
   constexpr int LM2 = F0 + 4, LM3 = F0 + 8;   // levels of the radix-16 passes (when <= LOGL)
   extern __shared__ __align__(128) uint8_t sm[];
   __shared__ float red[4][kAFftThreads / 32];
@@ -159,7 +155,7 @@ __global__ void __launch_bounds__(kAFftThreads, 2) adj_fft_kernel(AdjFftArgs ar,
   float2* wc = coef + lay.ncoef;      // e^{+j 2 pi p / T} = wc[p >> f] wf[p mod 2^f]
   float2* wf = wc + kATab;
   float2* lev2 = wf + kATab;          // twiddles of the radix-16 passes
-  float2* lev3 = lev2 + (LM2 <= LOGL ? adj_level_entries(LM2) : 0);
+  float2* lev3 = lev2 + (LM2 <= LOGL ? tw_level_entries(LM2) : 0);
   const int k = blockIdx.x, mat = blockIdx.y;
   const uint32_t mask = (uint32_t)T - 1u;
   const uint32_t f = ((uint32_t)logT + 1u) / 2u;
@@ -267,7 +263,7 @@ __global__ void __launch_bounds__(kAFftThreads, 2) adj_fft_kernel(AdjFftArgs ar,
   // F[m] = e^{+j 2 pi m PER1 / T}, when the first pass has a stride and R0 P fits the table
   const int RP = R0 * P;
   const bool fact = PER1 >= 16 && RP <= kAFTab;
-  float2* ft = lev3 + (LM3 <= LOGL ? adj_level_entries(LM3) : 0);
+  float2* ft = lev3 + (LM3 <= LOGL ? tw_level_entries(LM3) : 0);
   const size_t zstride = (size_t)(K + 1) * kDotTile;   // float2 between consecutive tiles of b'
   for (int a0 = 0, round = 0; a0 < P; a0 += nfft, ++round) {
     auto in_u = [&](int e0, int s) -> float2 {

@@ -290,6 +290,8 @@ static void plan_fft(Plan& pl) {
   o = align_up(o + group_bytes(pl.V, pl.T, pl.ny_pad), kWsAlign);
   pl.off_poly = o;
   o = align_up(o + (size_t)pl.K * pl.T * 8, kWsAlign);
+  pl.off_fftab = o;
+  o = align_up(o + fft_tables_bytes(pl.T, pl.fft_logL), kWsAlign);
   pl.total = o;
 }
 

@@ -70,6 +70,7 @@ struct Plan {
   int32_t yfft;
   int32_t fft_logL;            // FFT length L = 2^fft_logL (T = P L)
   size_t off_poly;             // complex FP32 [K][P][L]: conj(H) in polyphase order
+  size_t off_fftab;            // the FFT's tables (fft_tables_bytes; L = 4096 only)
   // continuous cosine series: T is twice the clip's period and the M2 = K rows
   // (and columns) of the contraction are sin(2 pi f a / T), f = 1..K, only
   int32_t cosine;
@@ -524,6 +525,7 @@ struct AdjFftArgs {
   float* gy;
 };
 size_t adj_fft_smem(int K, int logL);
+size_t fft_tables_bytes(int T, int logL);
 // axis lines of a single large clip by a pruned FFT of the bins
 size_t axis_fft_bytes(int T, int K);
 cudaError_t launch_axis_fft(const Plan& pl, void* ws, cudaStream_t st);

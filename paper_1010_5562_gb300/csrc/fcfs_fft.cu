@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(NT) fft_y_kernel(FftArgs ar) {
   uint32_t phase = 0;
   bool ok = true;
   for (int a0 = 0; a0 < P && ok; a0 += nfft) {
-    ok = mbar_wait(&full_bar, phase, st, 90);
+    // bounded wait, its outcome made block-uniform before the barriers below
+    ok = __syncthreads_and(mbar_wait(&full_bar, phase, st, 90) ? 1 : 0) != 0;
     phase ^= 1u;
     if (!ok) break;   // FCFS_ETIMEOUT is recorded; the copy did not land
     float2 *X = bufA, *Y = bufB;
@@ -149,7 +150,10 @@ __global__ void __launch_bounds__(NT) fft_y_kernel(FftArgs ar) {
     }
     __syncthreads();   // the sums have read X before the next range's passes overwrite it
   }
-  if (!ok) return;
+  if (!ok) {
+    if (threadIdx.x == 0) mbar_wait(&full_bar, phase ^ 1u, st, 92);   // a late copy lands before the exit
+    return;
+  }
   // F(k, l) = -T^2 / (4 pi^2 k l) G(k, l) for l != 0 (the axis lines come from the
   // exact integer sums); F(-k, -l) = conj F(k, l)
   const long long W = 2LL * K + 1;
@@ -162,6 +166,181 @@ __global__ void __launch_bounds__(NT) fft_y_kernel(FftArgs ar) {
     const float2 v = make_float2(a * acc[i].x, a * acc[i].y);
     ar.F[(K + k) * W + (K + l)] = v;
     ar.F[(K - k) * W + (K - l)] = make_float2(v.x, -v.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// L = 4096 (the T = 65536 clips, and K = 2048): one residue per round on
+// L / 16 threads, the passes at compile-time sizes, and the last pass summing
+// its outputs straight into each thread's outputs l (thread j owns the l with
+// l mod L = j + q L / 16): no shared-memory round trip for the sums.
+// Tables (float2, fixed slots), written once per call by fft_tables_kernel:
+//   [0, 256) wc, [256, 512) wf      two-level e^{+j 2 pi p / T}
+//   [512, + n2), [.., + n3)         twiddles of the second and third pass
+//   [.., + 17 P)                    per residue a: e^{+j 2 pi q (L/16) a / T}, q < 16,
+//                                   then e^{+j 2 pi L a / T}
+// ---------------------------------------------------------------------------
+constexpr int kFusedLogL = 12;
+
+struct FusedTabs {
+  int n2, n3, ng, total;
+  __host__ __device__ static FusedTabs of(int P) {
+    constexpr int f0 = first_log_radix(kFusedLogL);
+    FusedTabs t;
+    t.n2 = tw_level_entries(f0 + 4);
+    t.n3 = tw_level_entries(f0 + 8);
+    t.ng = 17 * P;
+    t.total = 2 * kFTab + t.n2 + t.n3 + ((t.ng + 1) & ~1);
+    return t;
+  }
+};
+
+__global__ void fft_tables_kernel(Plan pl, uint8_t* ws, float2* out) {
+  constexpr int LOGL = kFusedLogL, L = 1 << LOGL, f0 = first_log_radix(LOGL);
+  const int T = pl.T, logT = pl.logT, P = T >> LOGL;
+  const FusedTabs lay = FusedTabs::of(P);
+  const uint32_t logQ = (uint32_t)logT - 2u, mask = (uint32_t)T - 1u;
+  const uint32_t f = ((uint32_t)logT + 1u) / 2u, nc = (uint32_t)T >> f;
+  const float* gt = reinterpret_cast<const float*>(ws + pl.off_tab_f32);
+  griddep_wait();   // the prep kernel's FP32 table
+  auto W = [&](uint32_t p) { return pl.full ? f32_lookup<true>(gt, p, logQ) : f32_lookup<false>(gt, p, logQ); };
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= lay.total) return;
+  float2 v = make_float2(0.f, 0.f);
+  if (i < kFTab) {
+    if ((uint32_t)i < nc) v = W((uint32_t)i << f);
+  } else if (i < 2 * kFTab) {
+    if ((uint32_t)(i - kFTab) < (1u << f)) v = W((uint32_t)(i - kFTab));
+  } else if (i < 2 * kFTab + lay.n2 + lay.n3) {
+    const bool second = i < 2 * kFTab + lay.n2;
+    const int lm = second ? f0 + 4 : f0 + 8, e0 = second ? i - 2 * kFTab : i - 2 * kFTab - lay.n2;
+    const int e = lm <= 11 ? e0 : (e0 < (1 << (lm - 6)) ? 64 * e0 : e0 - (1 << (lm - 6)));
+    const float2 w = W(((uint32_t)e << (logT - lm)) & mask);   // e^{-j 2 pi e / M} = conj W(e T / M)
+    v = make_float2(w.x, -w.y);
+  } else {
+    const int g = i - (2 * kFTab + lay.n2 + lay.n3);
+    if (g < lay.ng) {
+      const int a = g / 17, q = g % 17;
+      const uint32_t p = q < 16 ? ((uint32_t)(q * (L / 16)) * (uint32_t)a) & mask : ((uint32_t)L * (uint32_t)a) & mask;
+      v = W(p);
+    }
+  }
+  out[i] = v;
+}
+
+__global__ void __launch_bounds__(1 << (kFusedLogL - 4), 2) fft_y_fused_kernel(FftArgs ar, const float2* tabs) {
+  constexpr int LOGL = kFusedLogL, L = 1 << LOGL, NS = L / 16, F0 = first_log_radix(LOGL), R0 = 1 << F0;
+  constexpr int LM2 = F0 + 4, LM3 = F0 + 8;
+  constexpr int BUF = ((L + (L >> 4)) + 2) & ~1;
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ __align__(8) uint64_t full_bar, tab_bar;
+  const Plan& pl = ar.pl;
+  const int T = pl.T, K = pl.K, logT = pl.logT, P = T >> LOGL;
+  const FusedTabs lay = FusedTabs::of(P);
+  float2* raw = reinterpret_cast<float2*>(sm);   // bulk-copy target, L entries
+  float2* bufA = raw + L;
+  float2* bufB = bufA + BUF;
+  float2* wc = bufB + BUF;                       // the tables, one bulk copy
+  float2* wf = wc + kFTab;
+  float2* lev2 = wf + kFTab;
+  float2* lev3 = lev2 + lay.n2;
+  float2* gq = lev3 + lay.n3;                    // [a][17]
+  const int k = blockIdx.x + 1, j = threadIdx.x;
+  const uint32_t mask = (uint32_t)T - 1u, f = ((uint32_t)logT + 1u) / 2u;
+  Status* st = reinterpret_cast<Status*>(const_cast<uint8_t*>(ar.ws) + pl.off_status);
+  const float2* src = ar.poly + (size_t)(k - 1) * P * L;
+  if (threadIdx.x == 0) {
+    mbar_init(&full_bar, 1);
+    mbar_init(&tab_bar, 1);
+    fence_mbar_init();
+  }
+  griddep_wait();   // the H kernel's conj(H), the tables kernel's tables
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&tab_bar, (uint32_t)lay.total * 8u);
+    bulk_load(wc, tabs, (uint32_t)lay.total * 8u, &tab_bar);
+    mbar_arrive_expect_tx(&full_bar, (uint32_t)L * 8u);
+    bulk_load(raw, src, (uint32_t)L * 8u, &full_bar);
+  }
+  // outputs of this thread: m = j + q NS, l = m (m <= K) or m - L (m >= L - K);
+  // with L = 2K, m = K is both l = K and l = -K (the second in accK)
+  float2 acc[16], accK = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = make_float2(0.f, 0.f);
+  // every wait is bounded and its outcome made block-uniform before any barrier
+  bool ok = __syncthreads_and(mbar_wait(&tab_bar, 0, st, 91) ? 1 : 0) != 0;
+  int a = 0;
+  for (; a < P && ok; ++a) {
+    ok = __syncthreads_and(mbar_wait(&full_bar, (uint32_t)a & 1u, st, 90) ? 1 : 0) != 0;
+    if (!ok) break;   // FCFS_ETIMEOUT is recorded; the copy did not land
+    auto in_raw = [&](int e0, int r) -> float2 { return raw[e0 + r * (L / R0)]; };
+    auto out_b = [&](int b0, int q, float2 v) { bufB[pad16_step<1>(b0, q)] = v; };
+    stockham_pass_io<R0, LOGL, 0, false>(in_raw, out_b, lev2, lev2, 1);
+    __syncthreads();   // raw is read: the next residue may land in it
+    if (threadIdx.x == 0 && a + 1 < P) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&full_bar, (uint32_t)L * 8u);
+      bulk_load(raw, src + (size_t)(a + 1) * L, (uint32_t)L * 8u, &full_bar);
+    }
+    auto in_b = [&](int e0, int r) -> float2 { return bufB[pad16_step<NS>(e0, r)]; };
+    auto out_a = [&](int b0, int q, float2 v) { bufA[pad16_step<(1 << F0)>(b0, q)] = v; };
+    stockham_pass_io<16, LOGL, F0, (LM2 > 11)>(in_b, out_a, lev2, lev2 + (LM2 > 11 ? (1 << (LM2 - 6)) : 0), 1);
+    __syncthreads();
+    // last pass of butterfly j: D_a(j + q NS), then the twiddled sums
+    float2 v[16], y[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = bufA[pad16_step<NS>(j, r)];
+#pragma unroll
+    for (int r = 1; r < 16; ++r) {
+      const int i = (r * j) & (L - 1);
+      v[r] = c_mul(v[r], (LM3 > 11) ? c_mul(lev3[i >> 6], lev3[(1 << (LM3 - 6)) + (i & 63)]) : lev3[i]);
+    }
+    Dft<16>::template sub<1, 0>(v, y);
+    // G(k, l) += e^{-j 2 pi l a / T} D_a(l mod L): e^{+j 2 pi m a / T} = w(j a) gq[a][q],
+    // and for l = m - L one more factor conj(gq[a][16])
+    const float2 base = c_mul(wc[(((uint32_t)j * (uint32_t)a) & mask) >> f],
+                              wf[((uint32_t)j * (uint32_t)a) & mask & ((1u << f) - 1u)]);
+    const float2 hl = gq[a * 17 + 16];
+    const float2* ga = gq + a * 17;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int m = j + q * NS;
+      const bool pos = m <= K, neg = m >= L - K;
+      if (pos || neg) {
+        const float2 w = c_mul(base, ga[q]);   // e^{+j 2 pi m a / T}
+        const float2 wn = c_mul(w, make_float2(hl.x, -hl.y));   // e^{+j 2 pi (m - L) a / T}
+        const float2 ww = pos ? w : wn;
+        acc[q].x = fmaf(ww.x, y[q].x, fmaf(ww.y, y[q].y, acc[q].x));   // acc += conj(ww) y
+        acc[q].y = fmaf(ww.x, y[q].y, fmaf(-ww.y, y[q].x, acc[q].y));
+        if (pos && neg) {
+          accK.x = fmaf(wn.x, y[q].x, fmaf(wn.y, y[q].y, accK.x));
+          accK.y = fmaf(wn.x, y[q].y, fmaf(-wn.y, y[q].x, accK.y));
+        }
+      }
+    }
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) {   // let the copies in flight land before the CTA exits
+      mbar_wait(&tab_bar, 0, st, 93);
+      if (a < P) mbar_wait(&full_bar, (uint32_t)a & 1u, st, 92);
+    }
+    return;
+  }
+  // F(k, l) = -T^2 / (4 pi^2 k l) G(k, l) for l != 0; F(-k, -l) = conj F(k, l)
+  const long long W = 2LL * K + 1;
+  auto put = [&](int l, float2 g) {
+    const float sc = -pl.quad_scale / ((float)k * (float)l);
+    const float2 v = make_float2(sc * g.x, sc * g.y);
+    ar.F[(K + k) * W + (K + l)] = v;
+    ar.F[(K - k) * W + (K - l)] = make_float2(v.x, -v.y);
+  };
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int m = j + q * NS;
+    const bool pos = m <= K, neg = m >= L - K;
+    if (pos && m != 0) put(m, acc[q]);
+    else if (neg && !pos) put(m - L, acc[q]);
+    if (pos && neg) put(-K, accK);
   }
 }
 
@@ -202,8 +381,31 @@ int fft_log_len(int T, int K) {
   return std::min(lg, logT);
 }
 
+size_t fft_tables_bytes(int T, int logL) {
+  return logL == kFusedLogL ? (size_t)FusedTabs::of(T >> kFusedLogL).total * 8 : 0;
+}
+
 cudaError_t launch_fft_y(const Plan& pl, void* ws, float* F, cudaStream_t st) {
   const int logL = pl.fft_logL;
+  if (logL == kFusedLogL) {
+    FftArgs ar;
+    ar.pl = pl;
+    ar.ws = static_cast<const uint8_t*>(ws);
+    ar.poly = reinterpret_cast<const float2*>(static_cast<const uint8_t*>(ws) + pl.off_poly);
+    ar.logL = logL;
+    ar.logP = pl.logT - logL;
+    ar.F = reinterpret_cast<float2*>(F);
+    float2* tabs = reinterpret_cast<float2*>(static_cast<uint8_t*>(ws) + pl.off_fftab);
+    const FusedTabs lay = FusedTabs::of(pl.T >> logL);
+    cudaError_t e = launch_after(fft_tables_kernel, dim3((lay.total + 255) / 256), dim3(256), 0, st, pl,
+                                 static_cast<uint8_t*>(ws), tabs);
+    if (e != cudaSuccess) return e;
+    constexpr int L = 1 << kFusedLogL, BUF = ((L + (L >> 4)) + 2) & ~1;
+    const size_t smem = (size_t)(L + 2 * BUF + lay.total) * 8;
+    if ((e = ensure_smem(reinterpret_cast<const void*>(fft_y_fused_kernel), smem)) != cudaSuccess) return e;
+    return launch_after(fft_y_fused_kernel, dim3(pl.K), dim3(L / 16), smem, st, ar,
+                        static_cast<const float2*>(tabs));
+  }
   FftArgs ar;
   ar.pl = pl;
   ar.ws = static_cast<const uint8_t*>(ws);

@@ -161,7 +161,11 @@ __device__ __forceinline__ int pad16_step(int e0, int r) {
 // Pass structure of an L = 2^logL point FFT: a first pass of radix 2^f0 (f0 =
 // logL mod 4, or 4), then radix-16 passes.  Pass i >= 1 runs at Ns = 2^(f0 + 4(i-1))
 // with twiddle level M_i = 2^(f0 + 4 i), stored after the levels before it.
-__device__ __forceinline__ int first_log_radix(int logL) { return (logL & 3) ? (logL & 3) : 4; }
+__host__ __device__ constexpr int first_log_radix(int logL) { return (logL & 3) ? (logL & 3) : 4; }
+
+// Entries of a twiddle level of size 2^lm in the compile-time passes: a direct
+// table up to 2^11 entries, else 2^(lm-6) coarse and 64 fine entries.
+__host__ __device__ constexpr int tw_level_entries(int lm) { return lm <= 11 ? 1 << lm : (1 << (lm - 6)) + 64; }
 
 // Entries of the twiddle level of size 2^lm.
 __host__ __device__ __forceinline__ int level_entries(int lm) { return lm <= 8 ? 1 << lm : (1 << (lm - 6)) + 64; }
