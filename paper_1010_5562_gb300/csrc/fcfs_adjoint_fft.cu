@@ -323,50 +323,50 @@ __global__ void __launch_bounds__(kAFftThreads, 2) adj_fft_kernel(AdjFftArgs ar,
   }
 }
 
-// Two corners of one polyphase position: epilogue coordinates a, steps
-// e^{+j 2 pi a / T} (w) and e^{+j 2 pi 8 a / T} (q), running sums of
-// (cos, sin)(2 pi k a / T) * V_k(b).
+// Two corners of one polyphase position: epilogue coordinates a, the steps
+// z = e^{-j 2 pi a / T} and z^8, and the running sums of Re(z^k V_k(b)).
 struct DotPair {
   uint32_t a0, a1;
-  float2 w0, w1, q0, q1, acc0, acc1;
+  float2 z0, z1, q0, q1;
+  float acc0, acc1;
 };
 
 // Frequencies k0 .. k0 + n - 1 of a streamed chunk (n = kDotRows unless TAIL)
-// for the pair at column j.  E_k = (cos, sin)(2 pi k a / T): one table anchor
-// at k0 (exact phase k0 a mod T), block anchors k0 + 8 m by the exact step q,
-// angle addition by w inside a block (at most 7 steps; the three-term
-// recurrence 2 cos(2 pi a / T) E_k - E_{k-1} would save two FMAs per frequency
-// but its rounding grows with the square of the steps: it measured 9e-7
-// against 3.6e-7 on the T = 2048 clip).  The sums run in three levels (8
-// terms, the chunk's blocks, the chunks), which keeps the FP32 rounding of the
-// K + 1 term dot near that of an 8 + 8 + K / 64 term one.
+// for the pair at column j.  Re(E_k(a) V_k) = Re(z^k V_k) with z = e^{-j 2 pi a / T}:
+// per block of 8 frequencies S = sum_t V_{k0+8m+t} z^t by Horner's rule (four
+// FMAs per frequency), then Re(z^{k0+8m} S) with the block anchor z^{k0+8m}
+// from an exact table value at k0 (phase k0 a mod T) and the exact step z^8.
+// The sums run in three levels (the blocks, the chunk's 8 blocks, the chunks).
+// The angle-addition alternative (E_k by one rotation per frequency, six FMAs
+// with the accumulation) measured 0.59 ms on the T = 65536 clip; the
+// three-term recurrence 2 cos(2 pi a / T) E_k - E_{k-1}, 9e-7 error.
 template <bool TAIL>
 __device__ __forceinline__ void dot_chunk(const float2* __restrict__ zc, int n, int k0, int j, DotPair& d,
                                           const TwoLevel& tl, uint32_t mask) {
   const int rows = TAIL ? n : kDotRows;
   float2 A0 = tl_lookup(tl, ((uint32_t)k0 * d.a0) & mask), A1 = tl_lookup(tl, ((uint32_t)k0 * d.a1) & mask);
-  float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
+  A0.y = -A0.y;   // z^{k0} = conj(e^{+j 2 pi k0 a / T})
+  A1.y = -A1.y;
+  float c0 = 0.f, c1 = 0.f;
 #pragma unroll
   for (int kk = 0; kk < rows; kk += 8) {
-    float2 e0 = A0, e1 = A1;
-    float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+    const int nb = TAIL ? min(8, rows - kk) : 8;
+    float2 S0 = zc[(kk + nb - 1) * kDotTile + j], S1 = S0;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      if (!TAIL || kk + t < rows) {
-        const float2 z = zc[(kk + t) * kDotTile + j];
-        s0 = ffma2(e0, z, s0);
-        s1 = ffma2(e1, z, s1);
-        e0 = rot2(e0, d.w0);
-        e1 = rot2(e1, d.w1);
+    for (int t = 6; t >= 0; --t) {
+      if (!TAIL || t < nb - 1) {
+        const float2 v = zc[(kk + t) * kDotTile + j];
+        S0 = make_float2(fmaf(S0.x, d.z0.x, fmaf(-S0.y, d.z0.y, v.x)), fmaf(S0.x, d.z0.y, fmaf(S0.y, d.z0.x, v.y)));
+        S1 = make_float2(fmaf(S1.x, d.z1.x, fmaf(-S1.y, d.z1.y, v.x)), fmaf(S1.x, d.z1.y, fmaf(S1.y, d.z1.x, v.y)));
       }
     }
-    c0 = make_float2(c0.x + s0.x, c0.y + s0.y);
-    c1 = make_float2(c1.x + s1.x, c1.y + s1.y);
+    c0 += fmaf(A0.x, S0.x, -(A0.y * S0.y));   // Re(A S)
+    c1 += fmaf(A1.x, S1.x, -(A1.y * S1.y));
     A0 = c_mul(A0, d.q0);
     A1 = c_mul(A1, d.q1);
   }
-  d.acc0 = make_float2(d.acc0.x + c0.x, d.acc0.y + c0.y);
-  d.acc1 = make_float2(d.acc1.x + c1.x, d.acc1.y + c1.y);
+  d.acc0 += c0;
+  d.acc1 += c1;
 }
 
 // One CTA per (tile, m): blockIdx.x = tile of 16 polyphase positions, blockIdx.y = m.
@@ -461,11 +461,15 @@ __global__ void __launch_bounds__(kDotThreads, 6) adj_dot_kernel(AdjFftArgs ar, 
     DotPair d;
     d.a0 = (uint32_t)a0;
     d.a1 = (uint32_t)a1;
-    d.w0 = tl_lookup(tl, d.a0 & mask);
-    d.w1 = tl_lookup(tl, d.a1 & mask);
+    d.z0 = tl_lookup(tl, d.a0 & mask);
+    d.z1 = tl_lookup(tl, d.a1 & mask);
     d.q0 = tl_lookup(tl, (8u * d.a0) & mask);
     d.q1 = tl_lookup(tl, (8u * d.a1) & mask);
-    d.acc0 = d.acc1 = make_float2(0.f, 0.f);
+    d.z0.y = -d.z0.y;   // z = e^{-j 2 pi a / T}, z^8
+    d.z1.y = -d.z1.y;
+    d.q0.y = -d.q0.y;
+    d.q1.y = -d.q1.y;
+    d.acc0 = d.acc1 = 0.f;
     for (int ch = 0; ch < nch; ++ch, ++g) {
       const int s = g % kDotStages;
       const uint32_t ph = (uint32_t)(g / kDotStages) & 1u;
@@ -497,12 +501,12 @@ __global__ void __launch_bounds__(kDotThreads, 6) adj_dot_kernel(AdjFftArgs ar, 
       return (float)T * ex;
     };
     if (v0 >= 0) {
-      float tot = d.acc0.x + d.acc0.y;
+      float tot = d.acc0;
       if (t0) tot += border(d.a0);
       gout[v0] = -(float)pl.vsg[v0] * tot;
     }
     if (v1 >= 0) {
-      float tot = d.acc1.x + d.acc1.y;
+      float tot = d.acc1;
       if (t1) tot += border(d.a1);
       gout[v1] = -(float)pl.vsg[v1] * tot;
     }
