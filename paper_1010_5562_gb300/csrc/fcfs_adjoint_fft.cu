@@ -337,6 +337,8 @@ struct DotPair {
 // FMAs per frequency), then Re(z^{k0+8m} S) with the block anchor z^{k0+8m}
 // from an exact table value at k0 (phase k0 a mod T) and the exact step z^8.
 // The sums run in three levels (the blocks, the chunk's 8 blocks, the chunks).
+// The pair's two corners share each V_k load and advance together in packed
+// FP32 pairs.
 // The angle-addition alternative (E_k by one rotation per frequency, six FMAs
 // with the accumulation) measured 0.59 ms on the T = 65536 clip; the
 // three-term recurrence 2 cos(2 pi a / T) E_k - E_{k-1}, 9e-7 error.
@@ -347,21 +349,29 @@ __device__ __forceinline__ void dot_chunk(const float2* __restrict__ zc, int n, 
   float2 A0 = tl_lookup(tl, ((uint32_t)k0 * d.a0) & mask), A1 = tl_lookup(tl, ((uint32_t)k0 * d.a1) & mask);
   A0.y = -A0.y;   // z^{k0} = conj(e^{+j 2 pi k0 a / T})
   A1.y = -A1.y;
+  // the two corners side by side in packed pairs (x of corner 0, x of corner 1), ...:
+  // one f32x2 FMA advances both, each half rounded as its scalar FMA
+  const float2 zx = make_float2(d.z0.x, d.z1.x), zy = make_float2(d.z0.y, d.z1.y);
+  const float2 nzy = make_float2(-d.z0.y, -d.z1.y);
   float c0 = 0.f, c1 = 0.f;
 #pragma unroll
   for (int kk = 0; kk < rows; kk += 8) {
     const int nb = TAIL ? min(8, rows - kk) : 8;
-    float2 S0 = zc[(kk + nb - 1) * kDotTile + j], S1 = S0;
+    const float2 top = zc[(kk + nb - 1) * kDotTile + j];
+    float2 Sx = make_float2(top.x, top.x), Sy = make_float2(top.y, top.y);   // S of corners 0 and 1
 #pragma unroll
     for (int t = 6; t >= 0; --t) {
       if (!TAIL || t < nb - 1) {
         const float2 v = zc[(kk + t) * kDotTile + j];
-        S0 = make_float2(fmaf(S0.x, d.z0.x, fmaf(-S0.y, d.z0.y, v.x)), fmaf(S0.x, d.z0.y, fmaf(S0.y, d.z0.x, v.y)));
-        S1 = make_float2(fmaf(S1.x, d.z1.x, fmaf(-S1.y, d.z1.y, v.x)), fmaf(S1.x, d.z1.y, fmaf(S1.y, d.z1.x, v.y)));
+        // S <- S z + v:  Sx' = Sx zx - Sy zy + vx,  Sy' = Sx zy + Sy zx + vy
+        const float2 nx = ffma2(Sx, zx, ffma2(Sy, nzy, make_float2(v.x, v.x)));
+        const float2 ny = ffma2(Sx, zy, ffma2(Sy, zx, make_float2(v.y, v.y)));
+        Sx = nx;
+        Sy = ny;
       }
     }
-    c0 += fmaf(A0.x, S0.x, -(A0.y * S0.y));   // Re(A S)
-    c1 += fmaf(A1.x, S1.x, -(A1.y * S1.y));
+    c0 += fmaf(A0.x, Sx.x, -(A0.y * Sy.x));   // Re(A S)
+    c1 += fmaf(A1.x, Sx.y, -(A1.y * Sy.y));
     A0 = c_mul(A0, d.q0);
     A1 = c_mul(A1, d.q1);
   }
