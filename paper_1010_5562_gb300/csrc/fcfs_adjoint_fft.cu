@@ -265,6 +265,8 @@ __global__ void __launch_bounds__(kAFftThreads, 2) adj_fft_kernel(AdjFftArgs ar,
   const bool fact = PER1 >= 16 && RP <= kAFTab;
   float2* ft = lev3 + (LM3 <= LOGL ? tw_level_entries(LM3) : 0);
   const size_t zstride = (size_t)(K + 1) * kDotTile;   // float2 between consecutive tiles of b'
+  const size_t zstep = (size_t)(NSL / kDotTile > 0 ? NSL / kDotTile : 0) * zstride;   // output q -> q + 1
+  const float bstep = (float)NSL * (float)P;                                          // b of output q -> q + 1
   for (int a0 = 0, round = 0; a0 < P; a0 += nfft, ++round) {
     auto in_u = [&](int e0, int s) -> float2 {
       const int q = e0 >> LOGL, j = e0 & (L - 1), r = j + s * PER1;
@@ -284,13 +286,14 @@ __global__ void __launch_bounds__(kAFftThreads, 2) adj_fft_kernel(AdjFftArgs ar,
       return u;
     };
     auto out_z = [&](int b0, int qq, float2 v) {
-      // point b0 + qq NSL: residue p = a0 + (b0 >> LOGL), m = (b0 & (L - 1)) + qq NSL
+      // point b0 + qq NSL: residue p = a0 + (b0 >> LOGL), m = (b0 & (L - 1)) + qq NSL;
+      // the parts from b0 are common to the butterfly's outputs, qq adds constant steps
       const int p = a0 + (b0 >> LOGL), m0 = b0 & (L - 1);
-      const float b = (float)(p + (m0 << logP)) + (float)(qq * NSL) * (float)P;
+      const float b = (float)(p + (m0 << logP)) + (float)qq * bstep;
       const int bp0 = (p << LOGL) | m0;
       size_t idx;
       if constexpr (NSL % kDotTile == 0)
-        idx = ((size_t)(bp0 >> 4) + (size_t)(qq * (NSL / kDotTile))) * zstride + (size_t)k * kDotTile + (bp0 & 15);
+        idx = (size_t)(bp0 >> 4) * zstride + (size_t)k * kDotTile + (bp0 & 15) + (size_t)qq * zstep;
       else {
         const int bp = bp0 + qq * NSL;
         idx = (size_t)(bp >> 4) * zstride + (size_t)k * kDotTile + (bp & 15);
