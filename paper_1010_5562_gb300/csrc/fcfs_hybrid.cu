@@ -493,18 +493,27 @@ __device__ __forceinline__ void row_sums(const uint2* __restrict__ meta, const f
         A = cmul(A, S);
       }
     } else {
-      const float2 D1 = make_float2(c.z, c.w);
+      // D_{k+32} = D_k + D_32 - D_k D_32 = D_32 + D_k C, C = 1 - D_32 = e^{j 32 w}
+      // (four FMAs); kind is uniform over the warp (one row, one pair at a time)
+      const float2 D1 = make_float2(c.z, c.w), C = make_float2(1.f - c.z, -c.w);
       float2 D = tab_d(tb, (k0 * w) & mask);
+      if (kind == 0u) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float2 E = kind ? make_float2(2.f - D.x, -D.y) : D;
-        acc[j].x = fmaf(A.x, E.x, fmaf(-A.y, E.y, acc[j].x));
-        acc[j].y = fmaf(A.x, E.y, fmaf(A.y, E.x, acc[j].y));
-        A = cmul(A, S);
-        // D_{k+32} = D_k + D_32 - D_k D_32
-        const float dr = fmaf(D.y, D1.y, fmaf(-D.x, D1.x, D.x + D1.x));
-        const float di = fmaf(-D.x, D1.y, fmaf(-D.y, D1.x, D.y + D1.y));
-        D = make_float2(dr, di);
+        for (int j = 0; j < 8; ++j) {
+          acc[j].x = fmaf(A.x, D.x, fmaf(-A.y, D.y, acc[j].x));
+          acc[j].y = fmaf(A.x, D.y, fmaf(A.y, D.x, acc[j].y));
+          A = cmul(A, S);
+          D = make_float2(fmaf(D.x, C.x, fmaf(-D.y, C.y, D1.x)), fmaf(D.x, C.y, fmaf(D.y, C.x, D1.y)));
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float2 E = make_float2(2.f - D.x, -D.y);
+          acc[j].x = fmaf(A.x, E.x, fmaf(-A.y, E.y, acc[j].x));
+          acc[j].y = fmaf(A.x, E.y, fmaf(A.y, E.x, acc[j].y));
+          A = cmul(A, S);
+          D = make_float2(fmaf(D.x, C.x, fmaf(-D.y, C.y, D1.x)), fmaf(D.x, C.y, fmaf(D.y, C.x, D1.y)));
+        }
       }
     }
   }
