@@ -517,6 +517,7 @@ def run_ours(args):
     reps = 3
     acc = {}
     fwd_ms = adj_ms = 0.0
+    fcfs.set_overlap(False)   # each stage alone on the call's stream
     for _ in range(reps):
         flush.fill_(1)
         fcfs.kernel_timing_enable(True)
@@ -528,6 +529,7 @@ def run_ours(args):
             else:
                 fwd_ms += t / reps
     fcfs.kernel_timing_enable(False)
+    fcfs.set_overlap(True)
     roofline = roofline_of(acc, clip, K)
     forms = {0: "direct", 1: "grouped_tc", 2: "grouped_fft"}
     parts = {"forward": {"form": forms.get(fcfs.forward_grouped(V, T, K), "?"), "stages_ms": round(fwd_ms, 4),
@@ -807,10 +809,12 @@ def run_extras(fcfs, dev, flush, stream, args):
                                       stream=stream)
             ms5 = _timed_ms(torch, fn, 3, flush, stream)
             flush.fill_(1)
+            fcfs.set_overlap(False)   # each stage alone on the call's stream
             fcfs.kernel_timing_enable(True)
             fn()
             kt = fcfs.kernel_timing()
             fcfs.kernel_timing_enable(False)
+            fcfs.set_overlap(True)
         finally:
             fcfs.set_hybrid(1)
         forms[key] = {"ms": ms5, "value": clip5.V * W5 * W5 / (ms5 * 1e-3),
@@ -829,10 +833,12 @@ def run_extras(fcfs, dev, flush, stream, args):
                                       stream=stream)
             ms5 = _timed_ms(torch, fn, 3, flush, stream)
             flush.fill_(1)
+            fcfs.set_overlap(False)   # each stage alone on the call's stream
             fcfs.kernel_timing_enable(True)
             fn()
             kt = fcfs.kernel_timing()
             fcfs.kernel_timing_enable(False)
+            fcfs.set_overlap(True)
             del wsa5
         finally:
             fcfs.set_hybrid(1)
@@ -860,11 +866,13 @@ def run_extras(fcfs, dev, flush, stream, args):
         st = {}
         for _ in range(20):
             flush.fill_(1)
+            fcfs.set_overlap(False)   # each stage alone on the call's stream
             fcfs.kernel_timing_enable(True)
             fn()
             for n, t in fcfs.kernel_timing():
                 st[n] = st.get(n, 0.0) + t / 20
         fcfs.kernel_timing_enable(False)
+        fcfs.set_overlap(True)
         e = {"ms": ms2, "value": clip2.V * W2 * W2 / (ms2 * 1e-3),
              "form": {0: "direct", 1: "grouped_tc", 2: "grouped_fft"}[fcfs.forward_grouped(clip2.V, clip2.T, K2, prec=prec)],
              "_F": F2.cpu()}

@@ -389,6 +389,14 @@ void fcfs_debug_set_barrier_extra(int32_t n);
  * the split-FP16 error bound.  Must not change between fcfs_workspace_size and
  * the call that uses the workspace. */
 void fcfs_debug_set_hybrid(int32_t mode);
+/* Stages of a call that do not depend on its main sequence (the axis lines of
+ * the grouped forward forms, the grouping of the pruned-FFT adjoint) run on a
+ * second stream of the calling thread, forked from and joined back into the
+ * call's stream by events (graph-capturable): on = 1, the default unless the
+ * environment has FCFS_OVERLAP=0.  With 0 every stage runs on the call's
+ * stream, in order, which is what per-stage timing (fcfs_kernel_timing_*)
+ * needs to see each stage alone.  Same results either way. */
+void fcfs_debug_set_overlap(int32_t on);
 
 /* Vertex-split granularity of fcfs_batch: n pipeline chunks (64 corners on the
  * tensor path, 32 on the FP32 path) per unit; 0 restores the default of 4096

@@ -44,6 +44,7 @@ SIGNATURES = {
     "fcfs_debug_set_pair": (None, [_i32]),
     "fcfs_debug_set_barrier_extra": (None, [_i32]),
     "fcfs_debug_set_hybrid": (None, [_i32]),
+    "fcfs_debug_set_overlap": (None, [_i32]),
     "fcfs_forward_grouped": (_i32, [_i64, _i32, _i32, _i32]),
     "fcfs_adjoint_grouped": (_i32, [_i64, _i32, _i32, _i32]),
     "fcfs_profile_enable": (None, [_i32]),

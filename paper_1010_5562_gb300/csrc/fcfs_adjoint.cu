@@ -467,9 +467,13 @@ static fcfs_status adjoint_impl(const int32_t* x, const int32_t* y, const int8_t
     ar.ny_pad = ap.ny_pad;
     ar.gx = gx;
     ar.gy = gy;
+    // the grouping beside the tables and the FFTs (only the dots need it)
+    SideStream* ss = side_stream();
     {
-      KtScope ks("adj_group", st);
-      if (launch_grouping(y, x, V, T, ap.ny_pad, static_cast<uint8_t*>(ws) + ap.off_groups, st, ar.logP) !=
+      const cudaStream_t gs = ss ? ss->s : st;
+      if (ss && side_fork(ss, st) != cudaSuccess) return FCFS_ECUDA;
+      KtScope ks("adj_group", gs);
+      if (launch_grouping(y, x, V, T, ap.ny_pad, static_cast<uint8_t*>(ws) + ap.off_groups, gs, ar.logP) !=
           cudaSuccess)
         return FCFS_ECUDA;
     }
@@ -478,6 +482,7 @@ static fcfs_status adjoint_impl(const int32_t* x, const int32_t* y, const int8_t
       if (launch_adj_tables(ar, ws, st) != cudaSuccess || launch_adj_fft(ar, ws, st) != cudaSuccess)
         return FCFS_ECUDA;
     }
+    if (ss && side_join(ss, st) != cudaSuccess) return FCFS_ECUDA;
     KtScope ks("adj_dot", st);
     if (launch_adj_dot(ar, ws, st) != cudaSuccess) return FCFS_ECUDA;
     return FCFS_OK;

@@ -56,6 +56,44 @@ void kt_end(cudaStream_t st) {
   g_kt_open = -1;
 }
 
+static std::atomic<int> g_overlap{-1};   // -1: not yet read from the environment
+SideStream* side_stream() {
+  int on = g_overlap.load(std::memory_order_relaxed);
+  if (on < 0) {
+    on = (getenv("FCFS_OVERLAP") && atoi(getenv("FCFS_OVERLAP")) == 0) ? 0 : 1;
+    int expect = -1;
+    g_overlap.compare_exchange_strong(expect, on);
+    on = g_overlap.load(std::memory_order_relaxed);
+  }
+  if (!on) return nullptr;
+  constexpr int kDevMax = 64;
+  thread_local SideStream tab[kDevMax] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevMax) return nullptr;
+  SideStream& ss = tab[dev];
+  if (!ss.s) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t f = nullptr, j = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&f, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess) {
+      if (f) cudaEventDestroy(f);
+      cudaStreamDestroy(s);
+      return nullptr;
+    }
+    ss = SideStream{s, f, j};
+  }
+  return &ss;
+}
+cudaError_t side_fork(SideStream* ss, cudaStream_t st) {
+  const cudaError_t e = cudaEventRecord(ss->fork, st);
+  return e != cudaSuccess ? e : cudaStreamWaitEvent(ss->s, ss->fork, 0);
+}
+cudaError_t side_join(SideStream* ss, cudaStream_t st) {
+  const cudaError_t e = cudaEventRecord(ss->join, ss->s);
+  return e != cudaSuccess ? e : cudaStreamWaitEvent(st, ss->join, 0);
+}
+
 static int ceil_log2(long long v) {
   int r = 0;
   while ((1LL << r) < v) ++r;
@@ -445,17 +483,32 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
     pl.area_out = reinterpret_cast<long long*>(area);
   }
   prof_mark(4, st);
-  if (pl.yfft) {
-    // grouping, H, the FFT along y; then the exact axis lines and their output
-    FCFS_CU(launch_grouped_fft(pl, ws, F, st));
+  if (pl.yfft || pl.hyb) {
+    // grouping, H, the contraction or the FFT along y; beside them (they need only
+    // the bins) the exact axis lines on the side stream; then the output
+    SideStream* ss = side_stream();
+    if (ss) {
+      FCFS_CU(side_fork(ss, st));
+      KtScope ks("axis_lines", ss->s);
+      FCFS_CU(launch_axis(pl, x, y, s, ws, false, ss->s));
+    }
+    FCFS_CU(pl.yfft ? launch_grouped_fft(pl, ws, F, st) : launch_hybrid(pl, ws, st));
     prof_mark(5, st);
     prof_mark(2, st);
-    {
+    if (ss) {
+      FCFS_CU(side_join(ss, st));
+    } else {
       KtScope ks("axis_lines", st);
       FCFS_CU(launch_axis(pl, x, y, s, ws, false, st));
     }
     prof_mark(3, st);
     prof_mark(6, st);
+    if (pl.hyb && !pl.yfft) {
+      KtScope ks("reduce", st);
+      FCFS_CU(launch_reduce(pl, ws, F, area, validate, st));
+      prof_mark(7, st);
+      return FCFS_OK;
+    }
     {
       KtScope ks("axis_out", st);
       FCFS_CU(launch_axis_out(pl, ws, F, area, st));
@@ -463,9 +516,7 @@ fcfs_status forward_impl(const int32_t* x, const int32_t* y, const int8_t* s, in
     prof_mark(7, st);
     return FCFS_OK;
   }
-  if (pl.hyb) {
-    FCFS_CU(launch_hybrid(pl, ws, st));
-  } else if (prec == FCFS_PREC_SPLIT_F16) {
+  if (prec == FCFS_PREC_SPLIT_F16) {
     KtScope ks(pl.fused ? "gemm_tc_fused" : "gemm_tc", st);
     FCFS_CU(launch_gemm_tc(pl, mp, ws, st));
   } else {
@@ -559,6 +610,7 @@ void fcfs_debug_set_fuse(int32_t on) { g_fuse = on ? 1 : 0; }
 void fcfs_debug_set_pair(int32_t on) { g_pair = on ? 1 : 0; }
 void fcfs_debug_set_barrier_extra(int32_t n) { g_barrier_extra = n > 0 ? n : 0; }
 void fcfs_debug_set_hybrid(int32_t mode) { g_hybrid = mode < 0 ? 0 : (mode > 3 ? 3 : mode); }
+void fcfs_debug_set_overlap(int32_t on) { g_overlap.store(on ? 1 : 0, std::memory_order_relaxed); }
 
 int32_t fcfs_forward_grouped(int64_t V, int32_t T, int32_t K, int32_t prec) {
   Plan pl;

@@ -590,4 +590,19 @@ struct KtScope {
   ~KtScope() { kt_end(st); }
 };
 
+// A second stream of the calling thread (one per device) for the stages of a
+// call that do not depend on its main sequence: side_fork makes it wait for
+// everything enqueued on the call's stream so far, side_join makes the call's
+// stream wait for everything enqueued on it, so a call stays one event-ordered
+// (and graph-capturable) sequence.  nullptr when the environment has
+// FCFS_OVERLAP=0 or the stream cannot be created: the caller then runs the
+// stage on its own stream.
+struct SideStream {
+  cudaStream_t s;
+  cudaEvent_t fork, join;
+};
+SideStream* side_stream();
+cudaError_t side_fork(SideStream* ss, cudaStream_t st);
+cudaError_t side_join(SideStream* ss, cudaStream_t st);
+
 }  // namespace fcfs

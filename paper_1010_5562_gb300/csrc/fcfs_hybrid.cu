@@ -43,52 +43,61 @@ __global__ void group_count_kernel(const int32_t* __restrict__ c0, const int32_t
 }
 
 // One CTA: exclusive scan of the T + 1 counts of g into start (and the
-// cursors), plus `first`, in tiles of 4 entries per thread; start[T + 1] =
-// first + the number of grouped corners; the exponents e of the large groups.
+// cursors), plus `first`; start[T + 1] = first + the number of grouped corners;
+// the exponents e of the large groups.  Each thread owns one contiguous range
+// of the counts (a multiple of 4 entries, within the padded array): it sums its
+// range, one block-wide scan of the sums gives each range's offset, and a
+// second pass over the range writes the running sums.
 constexpr int kScanThreads = 1024;
 __device__ void scan_groups(const Groups& g, int T, int ny_pad, int first) {
-  const int n = T + 1;
+  const int n = T + 1, S = group_stride(T);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ int wsum[kScanThreads / 32];
-  int carry = first;
-  for (int b0 = 0; b0 < n; b0 += 4 * kScanThreads) {
-    const int i0 = b0 + 4 * (int)threadIdx.x;
-    int4 c = make_int4(0, 0, 0, 0);
-    if (i0 < n) {   // the vector stays inside the padded array
-      c = *reinterpret_cast<const int4*>(g.cnt + i0);
-      if (i0 + 1 >= n) c.y = 0;
-      if (i0 + 2 >= n) c.z = 0;
-      if (i0 + 3 >= n) c.w = 0;
-    }
-    const int tsum = c.x + c.y + c.z + c.w;
-    int incl = tsum;
+  const int per = ((S + kScanThreads - 1) / kScanThreads + 3) & ~3;
+  const int i0 = min(S, (int)threadIdx.x * per), i1 = min(S, i0 + per);
+  auto counts = [&](int i) {   // four counts from i (the vector stays inside the padded array); past n: 0
+    int4 c = *reinterpret_cast<const int4*>(g.cnt + i);
+    if (i >= n) c.x = 0;
+    if (i + 1 >= n) c.y = 0;
+    if (i + 2 >= n) c.z = 0;
+    if (i + 3 >= n) c.w = 0;
+    return c;
+  };
+  int tsum = 0;
+  for (int i = i0; i < i1; i += 4) {
+    const int4 c = counts(i);
+    tsum += c.x + c.y + c.z + c.w;
+  }
+  int incl = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = wsum[lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
+      const int t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
     }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      int w = wsum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += t;
-      }
-      wsum[lane] = w;   // inclusive over warps
-    }
-    __syncthreads();
-    if (i0 < n) {
-      const int e0 = carry + (warp > 0 ? wsum[warp - 1] : 0) + incl - tsum;
-      const int4 st4 = make_int4(e0, e0 + c.x, e0 + c.x + c.y, e0 + c.x + c.y + c.z);
-      *reinterpret_cast<int4*>(g.start + i0) = st4;
-      *reinterpret_cast<int4*>(g.cur + i0) = st4;
-    }
-    carry += wsum[kScanThreads / 32 - 1];
-    __syncthreads();   // wsum is reused by the next tile
+    wsum[lane] = w;   // inclusive over warps
   }
-  if (threadIdx.x == 0) g.start[n] = carry;
+  __syncthreads();
+  int run = first + (warp > 0 ? wsum[warp - 1] : 0) + incl - tsum;
+  for (int i = i0; i < i1; i += 4) {
+    const int4 c = counts(i);
+    const int4 st4 = make_int4(run, run + c.x, run + c.x + c.y, run + c.x + c.y + c.z);
+    run += c.x + c.y + c.z + c.w;
+    if (i < n) {   // start and cursors of the n groups (whole vectors stay inside the padded arrays)
+      *reinterpret_cast<int4*>(g.start + i) = st4;
+      *reinterpret_cast<int4*>(g.cur + i) = st4;
+    }
+  }
+  __syncthreads();   // start[n] after the vector stores that may cover it
+  if (threadIdx.x == 0) g.start[n] = first + wsum[kScanThreads / 32 - 1];
   for (int i = threadIdx.x; i < ny_pad; i += kScanThreads) {
     int ex = 0;
     if (i < n && g.cnt[i] > (1 << 14)) {

@@ -302,6 +302,13 @@ def set_hybrid(mode):
     _lib.load().fcfs_debug_set_hybrid(int(mode))
 
 
+def set_overlap(on):
+    """Run the stages of a call that do not depend on its main sequence on a
+    second stream (True, the default) or every stage in order on the call's
+    stream (False: what per-stage timing needs)."""
+    _lib.load().fcfs_debug_set_overlap(1 if on else 0)
+
+
 def set_batch_unit_chunks(n):
     """Vertex-split granularity of batch(): n pipeline chunks per unit (0: default)."""
     _lib.load().fcfs_set_batch_unit_chunks(int(n))
