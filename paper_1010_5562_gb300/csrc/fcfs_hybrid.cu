@@ -47,8 +47,14 @@ __global__ void group_count_kernel(const int32_t* __restrict__ c0, const int32_t
 // the exponents e of the large groups.  Each thread owns one contiguous range
 // of the counts (a multiple of 4 entries, within the padded array): it sums its
 // range, one block-wide scan of the sums gives each range's offset, and a
-// second pass over the range writes the running sums.
+// second pass over the range writes the running sums and the exponents.  Both
+// passes keep four vector loads in flight.
 constexpr int kScanThreads = 1024;
+__device__ __forceinline__ int8_t group_exponent(int c) {   // ceil(log2 c) - 14, within [0, 15]
+  if (c <= (1 << 14)) return 0;
+  const int l = 32 - __clz(c - 1);
+  return (int8_t)min(15, l - 14);
+}
 __device__ void scan_groups(const Groups& g, int T, int ny_pad, int first) {
   const int n = T + 1, S = group_stride(T);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -56,7 +62,7 @@ __device__ void scan_groups(const Groups& g, int T, int ny_pad, int first) {
   const int per = ((S + kScanThreads - 1) / kScanThreads + 3) & ~3;
   const int i0 = min(S, (int)threadIdx.x * per), i1 = min(S, i0 + per);
   auto counts = [&](int i) {   // four counts from i (the vector stays inside the padded array); past n: 0
-    int4 c = *reinterpret_cast<const int4*>(g.cnt + i);
+    int4 c = i < i1 ? *reinterpret_cast<const int4*>(g.cnt + i) : make_int4(0, 0, 0, 0);
     if (i >= n) c.x = 0;
     if (i + 1 >= n) c.y = 0;
     if (i + 2 >= n) c.z = 0;
@@ -64,9 +70,12 @@ __device__ void scan_groups(const Groups& g, int T, int ny_pad, int first) {
     return c;
   };
   int tsum = 0;
-  for (int i = i0; i < i1; i += 4) {
-    const int4 c = counts(i);
-    tsum += c.x + c.y + c.z + c.w;
+  for (int i = i0; i < i1; i += 16) {
+    int4 c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) c[u] = counts(i + 4 * u);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) tsum += c[u].x + c[u].y + c[u].z + c[u].w;
   }
   int incl = tsum;
 #pragma unroll
@@ -87,26 +96,32 @@ __device__ void scan_groups(const Groups& g, int T, int ny_pad, int first) {
   }
   __syncthreads();
   int run = first + (warp > 0 ? wsum[warp - 1] : 0) + incl - tsum;
-  for (int i = i0; i < i1; i += 4) {
-    const int4 c = counts(i);
-    const int4 st4 = make_int4(run, run + c.x, run + c.x + c.y, run + c.x + c.y + c.z);
-    run += c.x + c.y + c.z + c.w;
-    if (i < n) {   // start and cursors of the n groups (whole vectors stay inside the padded arrays)
-      *reinterpret_cast<int4*>(g.start + i) = st4;
-      *reinterpret_cast<int4*>(g.cur + i) = st4;
+  for (int i = i0; i < i1; i += 16) {
+    int4 c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) c[u] = counts(i + 4 * u);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = i + 4 * u;
+      if (j >= i1) break;
+      const int4 st4 = make_int4(run, run + c[u].x, run + c[u].x + c[u].y, run + c[u].x + c[u].y + c[u].z);
+      run += c[u].x + c[u].y + c[u].z + c[u].w;
+      if (j < n) {   // start and cursors of the n groups (whole vectors stay inside the padded arrays)
+        *reinterpret_cast<int4*>(g.start + j) = st4;
+        *reinterpret_cast<int4*>(g.cur + j) = st4;
+      }
+      if (j < ny_pad) {   // the exponents of these four groups (0 past n), one 4-byte store
+        const uint32_t e = (uint32_t)(uint8_t)group_exponent(c[u].x) | ((uint32_t)(uint8_t)group_exponent(c[u].y) << 8) |
+                           ((uint32_t)(uint8_t)group_exponent(c[u].z) << 16) |
+                           ((uint32_t)(uint8_t)group_exponent(c[u].w) << 24);
+        *reinterpret_cast<uint32_t*>(g.ey + j) = e;
+      }
     }
   }
+  // exponents past the counts array (ny_pad > S): zero
+  for (int i = S + 4 * (int)threadIdx.x; i < ny_pad; i += 4 * kScanThreads) *reinterpret_cast<uint32_t*>(g.ey + i) = 0u;
   __syncthreads();   // start[n] after the vector stores that may cover it
   if (threadIdx.x == 0) g.start[n] = first + wsum[kScanThreads / 32 - 1];
-  for (int i = threadIdx.x; i < ny_pad; i += kScanThreads) {
-    int ex = 0;
-    if (i < n && g.cnt[i] > (1 << 14)) {
-      int l = 0;
-      while ((1 << l) < g.cnt[i] && l < 31) ++l;
-      ex = min(15, l - 14);
-    }
-    g.ey[i] = (int8_t)ex;
-  }
 }
 
 // One CTA per coordinate.
