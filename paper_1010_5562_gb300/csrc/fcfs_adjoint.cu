@@ -48,9 +48,10 @@ struct AdjPlan {
   // the grouped forms group the corners by y (gx) and by x (gy)
   int form, grouped, ny_pad;
   size_t off_groups;
-  // pruned FFT: T = P L, V_k at the polyphase positions, the side terms, the tables
+  // pruned FFT: T = P L, V_k at the polyphase positions, the side terms, the tables,
+  // the transposed cotangent
   int fft_logL;
-  size_t off_z, off_side, off_tabs;
+  size_t off_z, off_side, off_tabs, off_dft;
 };
 constexpr int kAdjThreads = 128;
 constexpr size_t kAdjSmemBudget = 200 * 1024;
@@ -95,7 +96,7 @@ static fcfs_status make_adj_plan(int64_t V, int32_t T, int32_t K, int32_t prec, 
   ap.ny_pad = (T + 1 + 63) / 64 * 64;
   ap.off_groups = 0;
   ap.fft_logL = adj_fft_log_len(T, K);
-  ap.off_z = ap.off_side = ap.off_tabs = 0;
+  ap.off_z = ap.off_side = ap.off_tabs = ap.off_dft = 0;
   ap.rows = 2 * K + 1;
   ap.cols = 2 * K + 2;
   const size_t tab = align_up(tab_f32_bytes(T, ap.p.full), 128);
@@ -139,6 +140,8 @@ static fcfs_status make_adj_plan(int64_t V, int32_t T, int32_t K, int32_t prec, 
     o = align_up(o + (size_t)2 * (K + 1) * sizeof(float4), kWsAlign);
     ap.off_tabs = o;
     o = align_up(o + adj_tables_bytes(ap.fft_logL), kWsAlign);
+    ap.off_dft = o;
+    o = align_up(o + (size_t)(2 * K + 1) * (2 * K + 1) * sizeof(float2), kWsAlign);
     ap.off_z = o;
     o = align_up(o + (size_t)2 * T * (K + 1) * sizeof(float2), kWsAlign);
     ap.off_m = ap.off_part = 0;
@@ -446,10 +449,6 @@ static fcfs_status adjoint_impl(const int32_t* x, const int32_t* y, const int8_t
   if ((r = check_ws(ap.p, ws, ws_bytes)) != FCFS_OK) return r;
   if (V == 0) return FCFS_OK;
   if (ap.tc && ap.form != 2 && (!aligned16_ptr(x) || !aligned16_ptr(y))) return FCFS_EINVAL;
-  {
-    KtScope ks("adj_prep", st);
-    if (launch_prep(ap.p, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
-  }
   if (ap.form == 2) {
     // pruned FFT along b for every k, then the per-corner dots
     AdjFftArgs ar;
@@ -464,10 +463,13 @@ static fcfs_status adjoint_impl(const int32_t* x, const int32_t* y, const int8_t
     ar.off_side = ap.off_side;
     ar.off_groups = ap.off_groups;
     ar.off_tabs = ap.off_tabs;
+    ar.off_dft = ap.off_dft;
     ar.ny_pad = ap.ny_pad;
     ar.gx = gx;
     ar.gy = gy;
-    // the grouping beside the tables and the FFTs (only the dots need it)
+    // the grouping on the side stream beside the prep, tables and FFTs (only the
+    // dots need it; it leaves out coordinates outside [0, T], so it need not
+    // wait for the prep kernel's checks)
     SideStream* ss = side_stream();
     {
       const cudaStream_t gs = ss ? ss->s : st;
@@ -478,6 +480,10 @@ static fcfs_status adjoint_impl(const int32_t* x, const int32_t* y, const int8_t
         return FCFS_ECUDA;
     }
     {
+      KtScope ks("adj_prep", st);
+      if (launch_prep(ap.p, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
+    }
+    {
       KtScope ks("adj_fft", st);
       if (launch_adj_tables(ar, ws, st) != cudaSuccess || launch_adj_fft(ar, ws, st) != cudaSuccess)
         return FCFS_ECUDA;
@@ -486,6 +492,10 @@ static fcfs_status adjoint_impl(const int32_t* x, const int32_t* y, const int8_t
     KtScope ks("adj_dot", st);
     if (launch_adj_dot(ar, ws, st) != cudaSuccess) return FCFS_ECUDA;
     return FCFS_OK;
+  }
+  {
+    KtScope ks("adj_prep", st);
+    if (launch_prep(ap.p, ws, false, st) != cudaSuccess) return FCFS_ECUDA;
   }
   {
     KtScope ks("adj_coef", st);

@@ -20,6 +20,8 @@
 // over b.  l = +-K share the residue K when L = 2K; their terms add, since the
 // kernel e^{-j 2 pi r m / L} depends on l only through r.
 //
+// adj_tables_kernel writes the FFTs' and dots' twiddle tables and the
+// transposed cotangent, so that both matrices read D(k, .) along rows.
 // adj_fft_kernel, one CTA per (k, m): c_{k,.}, const_k and lin_k from the
 // cotangent (the constant's sum compensated, T Dv(k,0) added in FP64), then the
 // residues p two at a time (4096 points per buffer): inputs at exact integer
@@ -100,7 +102,31 @@ struct TabLayout {
   }
 };
 
-__global__ void adj_tables_kernel(AdjFftArgs ar, uint8_t* ws) {
+// The transposed cotangent dFt(l, k) = dF(k, l): 32 x 32 tiles through shared
+// memory, rows read and written whole (blocks past the tables' own).
+constexpr int kTrTile = 32;
+__device__ __forceinline__ void transpose_tile(const float2* __restrict__ dF, float2* __restrict__ dFt, int W, int t) {
+  __shared__ float2 tile[kTrTile][kTrTile + 1];
+  const int nt = (W + kTrTile - 1) / kTrTile;
+  const int c0 = (t % nt) * kTrTile, r0 = (t / nt) * kTrTile;
+  const int tx = threadIdx.x & (kTrTile - 1), ty = threadIdx.x / kTrTile;
+#pragma unroll
+  for (int i = ty; i < kTrTile; i += 8)
+    if (r0 + i < W && c0 + tx < W) tile[i][tx] = __ldg(dF + (size_t)(r0 + i) * W + c0 + tx);
+  __syncthreads();
+#pragma unroll
+  for (int i = ty; i < kTrTile; i += 8)
+    if (c0 + i < W && r0 + tx < W) dFt[(size_t)(c0 + i) * W + r0 + tx] = tile[tx][i];
+}
+
+// 256 threads: blocks [0, ntab) the tables, the next ones a tile of the
+// transposed cotangent each.
+__global__ void __launch_bounds__(256) adj_tables_kernel(AdjFftArgs ar, uint8_t* ws, int ntab) {
+  griddep_wait();   // the prep kernel's FP32 table (and, before it, the caller's cotangent)
+  if ((int)blockIdx.x >= ntab) {
+    transpose_tile(ar.dF, reinterpret_cast<float2*>(ws + ar.off_dft), 2 * ar.pl.K + 1, (int)blockIdx.x - ntab);
+    return;
+  }
   const Plan& pl = ar.pl;
   const int T = pl.T, logT = pl.logT, logL = ar.logL;
   const TabLayout lay = TabLayout::of(logL);
@@ -109,7 +135,6 @@ __global__ void adj_tables_kernel(AdjFftArgs ar, uint8_t* ws) {
   const uint32_t f = ((uint32_t)logT + 1u) / 2u, nc = (uint32_t)T >> f;
   const float* gt = reinterpret_cast<const float*>(ws + pl.off_tab_f32);
   float2* out = reinterpret_cast<float2*>(ws + ar.off_tabs);
-  griddep_wait();   // the prep kernel's FP32 table
   auto W = [&](uint32_t p) { return pl.full ? f32_lookup<true>(gt, p, logQ) : f32_lookup<false>(gt, p, logQ); };
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= lay.total) return;
@@ -172,10 +197,9 @@ __global__ void __launch_bounds__(kAFftThreads, 2) adj_fft_kernel(AdjFftArgs ar,
   }
 
   // c_{k,l} = -j T/(2 pi l) Dv(k,l) and the compensated sum of the c_{k,l}
-  auto D = [&](int kk, int ll) -> float2 {
-    const float2 g = mat == 0 ? __ldg(ar.dF + (size_t)(kk + K) * W + (ll + K)) : __ldg(ar.dF + (size_t)(ll + K) * W + (kk + K));
-    return conj2(g);
-  };
+  // gy reads the rows of the transposed cotangent: both matrices read D(k, .) as a row
+  const float2* Dsrc = mat == 0 ? ar.dF : reinterpret_cast<const float2*>(ws + ar.off_dft);
+  auto D = [&](int kk, int ll) -> float2 { return conj2(__ldg(Dsrc + (size_t)(kk + K) * W + (ll + K))); };
   const float t2pi = (float)((double)T / (2.0 * CUDART_PI));
   CSum sr{0.f, 0.f}, si{0.f, 0.f};
   // four values of l per thread at a time: their loads are issued together
@@ -538,8 +562,10 @@ size_t adj_fft_smem(int K, int logL) { return FftSmem::of(K, logL).bytes(); }
 size_t adj_tables_bytes(int logL) { return (size_t)TabLayout::of(logL).total * 8; }
 
 cudaError_t launch_adj_tables(const AdjFftArgs& ar, void* ws, cudaStream_t st) {
-  const int n = TabLayout::of(ar.logL).total;
-  return launch_after(adj_tables_kernel, dim3((n + 255) / 256), dim3(256), 0, st, ar, static_cast<uint8_t*>(ws));
+  const int ntab = (TabLayout::of(ar.logL).total + 255) / 256;
+  const int nt = (2 * ar.pl.K + 1 + kTrTile - 1) / kTrTile;
+  return launch_after(adj_tables_kernel, dim3(ntab + nt * nt), dim3(256), 0, st, ar, static_cast<uint8_t*>(ws),
+                      ntab);
 }
 
 static size_t adj_dot_smem() { return (size_t)kDotStages * kDotRows * kDotTile * 8 + (size_t)2 * kATab * 8; }

@@ -515,6 +515,7 @@ struct AdjTcArgs {
 struct AdjFftArgs {
   Plan pl;              // T, K, tables, status; vx, vy, vsg the corners
   const float2* dF;     // (2K+1)^2 cotangent
+  size_t off_dft;       // the cotangent transposed (gy reads its rows)
   int logL, logP;       // T = P L, L = 2^logL >= 2K
   size_t off_z;         // complex FP32 [2][T/16][K+1][16]: V_k at polyphase positions b'
   size_t off_side;      // float4 [2][K+1]: const_k (re, im), lin_k (re, im)

@@ -205,7 +205,7 @@ def test_grouped_adjoint_launches(fc):
     contraction, finalize; per corner: prep, coefficients, pack, contraction,
     finalize.  Workload 4 takes the pruned-FFT form automatically (measured
     0.044 ms against 0.075 for either tensor-core form): prep, count, scan,
-    scatter, tables, FFTs, dots."""
+    scatter, tables (with the transposed cotangent), FFTs, dots."""
     clip, K = config_clip(4)
     x, y, s = dev(clip.x), dev(clip.y), dev(clip.s)
     dF = torch.zeros((2 * K + 1, 2 * K + 1), dtype=torch.complex64, device="cuda")

@@ -164,7 +164,8 @@ def test_fft_adjoint_deterministic_and_forms_agree(fc):
 
 
 def test_fft_adjoint_launches(fc):
-    """prep, grouping (count, scan, scatter), the tables, the FFTs, the dots."""
+    """prep, grouping (count, scan, scatter), the tables (with the transposed
+    cotangent), the FFTs, the dots."""
     clip, K = config_clip(4)
     x, y, s = dev(clip.x), dev(clip.y), dev(clip.s)
     dF = torch.zeros((2 * K + 1, 2 * K + 1), dtype=torch.complex64, device="cuda")
