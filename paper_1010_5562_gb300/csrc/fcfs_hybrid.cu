@@ -228,7 +228,8 @@ struct HCfg {
   static constexpr size_t tile = FMT == kHRowsFp16 ? (size_t)kHY * kHLd * 8 : (size_t)kHCap * 4;   // tile | keys
   static constexpr size_t meta = tile;                                  // uint2 [kHPairMax]
   static constexpr size_t cst = meta + (size_t)kHPairMax * 8;           // float4 [kHPairMax]
-  static constexpr size_t tabs = cst + (size_t)kHPairMax * 16;          // float2 [4][kHTabMax]
+  static constexpr size_t cst2 = cst + (size_t)kHPairMax * 16;          // float4 [kHPairMax] (kHPolyF32)
+  static constexpr size_t tabs = cst2 + (FMT == kHPolyF32 ? (size_t)kHPairMax * 16 : 0);   // float2 [4][kHTabMax]
   static constexpr size_t rows = tabs + (size_t)4 * kHTabMax * 8;       // int [2][kHY + 2]
   static constexpr size_t total = rows + (size_t)2 * (kHY + 2) * 4 + 16;
 };
@@ -423,10 +424,11 @@ __device__ void h_item_exact(const Plan& pl, const Groups& g, int clip, int y0, 
 // Fast-path staging of an item: sort keys (row << 17 | x << 1 | sign), the
 // first sorted corner of each row (rowc), the first pair of each row (rowp), and
 // per pair meta {x_a | kind << 20 | sign_a << 22, w} (kind 0: opposite signs, 1:
-// equal, 2: alone) and steps {e^{j 32 x_a}, D_32}.
+// equal, 2: alone) and steps {e^{j 32 x_a}, D_32} (kHPolyF32 also {e^{j 64 x_a},
+// D_64} in cst2).
 template <int FMT>
 __device__ void h_stage(const Plan& pl, const Groups& g, int y0, const HRange& rg, uint32_t* keys, uint2* meta,
-                        float4* cst, int* rowc, int* rowp, const HTabs& tb) {
+                        float4* cst, float4* cst2, int* rowc, int* rowp, const HTabs& tb) {
   const int T = pl.T, n = rg.count(), tid = threadIdx.x, nt = blockDim.x;
   const uint32_t mask = (uint32_t)T - 1u;
   int npad = 1;
@@ -495,6 +497,10 @@ __device__ void h_stage(const Plan& pl, const Groups& g, int y0, const HRange& r
     meta[p] = make_uint2(xa | (kind << 20) | (sa << 22), w);
     const float2 S = tab_w(tb, (32u * xa) & mask), D = tab_d(tb, (32u * w) & mask);
     cst[p] = make_float4(S.x, S.y, D.x, D.y);
+    if (FMT == kHPolyF32) {
+      const float2 S2 = tab_w(tb, (64u * xa) & mask), D2 = tab_d(tb, (64u * w) & mask);
+      cst2[p] = make_float4(S2.x, S2.y, D2.x, D2.y);
+    }
   }
   __syncthreads();   // the keys are dead from here on
 }
@@ -541,6 +547,113 @@ __device__ __forceinline__ void row_sums(const uint2* __restrict__ meta, const f
       }
     }
   }
+}
+
+// Packed FP32 pairs (f32x2): d = a b + c and d = a b elementwise, each element
+// rounded as the scalar fmaf / multiply.
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
+
+// The 8 sums of one row as in row_sums, the lane's frequencies taken two at a
+// time, k0 + 32 j and k0 + 32 (j + 1) for j = 0, 2, 4, 6, in the halves of packed
+// f32x2 operations: re[j / 2] = (Re_j, Re_{j+1}), im[j / 2] likewise (zeroed by
+// the caller).  Both chains start from the table anchor at k0 and its exact-step
+// successor at k0 + 32 (A_{k+32} = A_k e^{j 32 x_a}, D_{k+32} = D_32 + D_k e^{j 32 w})
+// and step by 64 frequencies: A_{k+64} = A_k S^2 and D_{k+64} = D_64 + D_k C^2,
+// with S^2 = e^{j 64 x_a} and D_64 from the tables (staged per pair) and
+// C^2 = e^{j 64 w} = 1 - D_64: half the steps of the scalar chains.  The
+// opposite-sign product Re(A D) = A_x D_x - A_y D_y has its negative part summed
+// on its own (q) and taken off at the end of the row; the rare equal-sign pairs
+// take scalar FMAs on the halves.
+__device__ __forceinline__ void row_sums_x2(const uint2* __restrict__ meta, const float4* __restrict__ cst,
+                                            const float4* __restrict__ cst2, int p0, int p1, uint32_t k0,
+                                            uint32_t mask, const HTabs& tb, float2 (&re)[4], float2 (&im)[4]) {
+  float2 q[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) q[j] = make_float2(0.f, 0.f);
+  for (int p = p0; p < p1; ++p) {
+    const uint2 pr = meta[p];
+    const float4 c = cst[p];
+    const float4 c2 = cst2[p];
+    const uint32_t xa = pr.x & 0xFFFFFu, kind = (pr.x >> 20) & 3u, w = pr.y;
+    const float2 S = make_float2(c.x, c.y);
+    float2 A0 = tab_w(tb, (k0 * xa) & mask);
+    if (pr.x >> 22) A0 = make_float2(-A0.x, -A0.y);
+    const float2 A1 = cmul(A0, S);
+    float2 ax = make_float2(A0.x, A1.x), ay = make_float2(A0.y, A1.y);
+    const float2 s2x = dup(c2.x), s2y = dup(c2.y), ns2y = dup(-c2.y);
+    if (kind == 2u) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        re[j] = pfma(ax, dup(1.f), re[j]);
+        im[j] = pfma(ay, dup(1.f), im[j]);
+        if (j < 3) {
+          const float2 nx = pfma(ay, ns2y, pmul(ax, s2x));
+          ay = pfma(ay, s2x, pmul(ax, s2y));
+          ax = nx;
+        }
+      }
+      continue;
+    }
+    const float2 D32 = make_float2(c.z, c.w), C = make_float2(1.f - c.z, -c.w);
+    const float2 D0 = tab_d(tb, (k0 * w) & mask);
+    const float2 D1 = make_float2(fmaf(D0.x, C.x, fmaf(-D0.y, C.y, D32.x)), fmaf(D0.x, C.y, fmaf(D0.y, C.x, D32.y)));
+    const float2 c2x = dup(1.f - c2.z), c2y = dup(-c2.w), nc2y = dup(c2.w);
+    const float2 d64x = dup(c2.z), d64y = dup(c2.w);
+    float2 dx = make_float2(D0.x, D1.x), dy = make_float2(D0.y, D1.y);
+    // kind is uniform over the warp (one row, one pair at a time)
+    if (kind == 0u) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        re[j] = pfma(ax, dx, re[j]);
+        q[j] = pfma(ay, dy, q[j]);
+        im[j] = pfma(ax, dy, pfma(ay, dx, im[j]));
+        if (j < 3) {
+          const float2 nx = pfma(ay, ns2y, pmul(ax, s2x));
+          ay = pfma(ay, s2x, pmul(ax, s2y));
+          ax = nx;
+          const float2 ex = pfma(dy, nc2y, pfma(dx, c2x, d64x));
+          dy = pfma(dy, c2x, pfma(dx, c2y, d64y));
+          dx = ex;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        // A (2 - D) on each half
+        const float ex0 = 2.f - dx.x, ey0 = -dy.x, ex1 = 2.f - dx.y, ey1 = -dy.y;
+        re[j].x = fmaf(ax.x, ex0, fmaf(-ay.x, ey0, re[j].x));
+        im[j].x = fmaf(ax.x, ey0, fmaf(ay.x, ex0, im[j].x));
+        re[j].y = fmaf(ax.y, ex1, fmaf(-ay.y, ey1, re[j].y));
+        im[j].y = fmaf(ax.y, ey1, fmaf(ay.y, ex1, im[j].y));
+        if (j < 3) {
+          const float2 nx = pfma(ay, ns2y, pmul(ax, s2x));
+          ay = pfma(ay, s2x, pmul(ax, s2y));
+          ax = nx;
+          const float2 ex = pfma(dy, nc2y, pfma(dx, c2x, d64x));
+          dy = pfma(dy, c2x, pfma(dx, c2y, d64y));
+          dx = ex;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) re[j] = pfma(q[j], dup(-1.f), re[j]);
 }
 
 // kHRowsFp16 fast path: passes of 256 frequencies over the item's 64 rows into
@@ -600,8 +713,8 @@ __device__ void h_rows_fp16(const Plan& pl, int clip, int y0, float2* tile, cons
 // counter.  A warp sums the unit's 4 rows y = a + P b (consecutive b), so each
 // lane ends with 4 consecutive b of each of its 8 frequencies: one 32-byte
 // sector of conj(H)[k-1][a][.] per frequency, stored directly.
-__device__ void h_poly_direct(const Plan& pl, int y0, const uint2* meta, const float4* cst, const int* rowp,
-                              int* s_row, const HTabs& tb, const HOut& out) {
+__device__ void h_poly_direct(const Plan& pl, int y0, const uint2* meta, const float4* cst, const float4* cst2,
+                              const int* rowp, int* s_row, const HTabs& tb, const HOut& out) {
   const int T = pl.T, K = pl.K, lane = threadIdx.x & 31;
   const uint32_t mask = (uint32_t)T - 1u;
   const int nrows = item_rows<kHPolyF32>(y0, T);
@@ -621,19 +734,28 @@ __device__ void h_poly_direct(const Plan& pl, int y0, const uint2* meta, const f
     const int pass = u / nunit, w = u % nunit, a = w % P, grp = w / P;
     const uint32_t k0 = (uint32_t)(pass * kHPassF + 1 + lane);
     if ((int)k0 > K) continue;   // lanes past K (last pass) idle; nothing below is warp-collective
-    float2 acc[4][8];
+    float2 re[4][4], im[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
+      for (int j = 0; j < 4; ++j) re[i][j] = im[i][j] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int bl = 4 * grp + i;
       if (bl < nb) {
         const int r = a + (bl << logP);
-        row_sums(meta, cst, rowp[r], rowp[r + 1], k0, mask, tb, acc[i]);
+        row_sums_x2(meta, cst, cst2, rowp[r], rowp[r + 1], k0, mask, tb, re[i], im[i]);
       }
     }
+    // frequency k0 + 32 j of row i: (re, im)[i][j / 2], half j mod 2
+    float2 acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        acc[i][2 * j] = make_float2(re[i][j].x, im[i][j].x);
+        acc[i][2 * j + 1] = make_float2(re[i][j].y, im[i][j].y);
+      }
     const size_t kstride = (size_t)32 * T;   // 32 frequencies further on
     float2* dst = out.poly + ((size_t)(k0 - 1) * P + a) * out.L + b0 + 4 * grp;
     if (4 * grp + 4 <= nb) {
@@ -669,6 +791,7 @@ __global__ void __launch_bounds__(HCfg<FMT>::threads, HCfg<FMT>::min_blocks)
   float2* tile = reinterpret_cast<float2*>(sm);
   uint2* meta = reinterpret_cast<uint2*>(sm + C::meta);
   float4* cst = reinterpret_cast<float4*>(sm + C::cst);
+  float4* cst2 = reinterpret_cast<float4*>(sm + C::cst2);
   float2* tabs = reinterpret_cast<float2*>(sm + C::tabs);
   int* rowc = reinterpret_cast<int*>(sm + C::rows);
   int* rowp = rowc + kHY + 2;
@@ -707,11 +830,11 @@ __global__ void __launch_bounds__(HCfg<FMT>::threads, HCfg<FMT>::min_blocks)
     const HRange rg = item_range<FMT>(g, y0, T);
     if (rg.count() <= kHCap) {
       levels = false;   // the fast path overwrites them
-      h_stage<FMT>(pl, g, y0, rg, keys, meta, cst, rowc, rowp, tb);
+      h_stage<FMT>(pl, g, y0, rg, keys, meta, cst, cst2, rowc, rowp, tb);
       if (FMT == kHRowsFp16)
         h_rows_fp16(pl, clip, y0, tile, meta, cst, rowp, &s_row, tb, out);
       else
-        h_poly_direct(pl, y0, meta, cst, rowp, &s_row, tb, out);
+        h_poly_direct(pl, y0, meta, cst, cst2, rowp, &s_row, tb, out);
     } else if (FMT == kHRowsFp16) {
       // level 0 = the fixed-point quarter-wave table, then the decimated levels
       int* lv = reinterpret_cast<int*>(sm);
