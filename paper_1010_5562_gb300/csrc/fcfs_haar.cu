@@ -54,6 +54,10 @@ constexpr int kHT = 32;          // pyramid tile side (five levels per pass)
 constexpr int kHThreads = 256;
 constexpr int kHaarMaxJ = 14;    // 2^28 cells: 1-2 GiB of cell areas, 2 GiB of FP64 output
 constexpr int kNarrowMaxW = 1024;   // cell side up to which Z is int32
+constexpr int kBand = 32;          // banded path: cell rows per band (one tile row)
+constexpr int kChunk = 256;        // banded path: columns per chunk (eight 32 x 32 tiles)
+constexpr int kBandStage = 4096;   // banded path: splats staged in shared memory per CTA
+constexpr int kBandMaxChunks = 64; // banded path: chunks per CTA (2^14 / kChunk)
 
 struct HaarPlan {
   int J, logN, G, N;
@@ -61,6 +65,8 @@ struct HaarPlan {
   int narrow;                    // 1: Z in int32 (cell side <= kNarrowMaxW)
   int strips, segs, tiles_per_seg;
   int npass;                     // pyramid passes, the fused one first; pass p leaves a grid of coarse_side[p]
+  int banded;                    // 1: bands of 32 rows, the cell grid kept on chip (grids of >= 256 cells a side)
+  int nbands, band_cpc, band_nq; // bands, chunks of 256 columns per CTA, CTAs per band
   int ny_pad;                    // T + 1 rounded up to 64 (the grouping's exponent array)
   size_t off_z, off_colsum, off_coarse[6], off_groups, total;
   int coarse_side[6];
@@ -96,11 +102,21 @@ fcfs_status make_haar_plan(int64_t V, int32_t T, int32_t J, HaarPlan& hp) {
   segs = segs < 1 ? 1 : (segs > tiles ? tiles : segs);
   hp.tiles_per_seg = (tiles + segs - 1) / segs;
   hp.segs = (tiles + hp.tiles_per_seg - 1) / hp.tiles_per_seg;
+  hp.banded = (hp.narrow && hp.G >= kChunk) ? 1 : 0;
+  if (hp.banded) {
+    // CTAs per band: a power of two giving at least 8 per SM over the grid
+    hp.nbands = hp.G / kBand;
+    const int nchunks = hp.G / kChunk;
+    int nq = 1;
+    while (nq < nchunks && (long long)nq * hp.nbands < 8LL * sms) nq <<= 1;
+    hp.band_nq = nq;
+    hp.band_cpc = nchunks / nq;
+  }
   size_t o = 256;   // header: the status word
   hp.off_z = o;
-  o = align_up(o + (size_t)hp.G * hp.G * elem, kWsAlign);
+  if (!hp.banded) o = align_up(o + (size_t)hp.G * hp.G * elem, kWsAlign);
   hp.off_colsum = o;
-  o = align_up(o + (size_t)hp.segs * hp.G * elem, kWsAlign);
+  o = align_up(o + (hp.banded ? (size_t)hp.nbands * hp.G * 4 : (size_t)hp.segs * hp.G * elem), kWsAlign);
   int side = tiles;   // side of the area grid each pass leaves, down to one cell
   for (;;) {
     hp.coarse_side[hp.npass] = side;
@@ -138,34 +154,36 @@ __device__ __forceinline__ E warp_sum(E v) {
 __device__ __forceinline__ int wadd(int a, int b) { return (int)((unsigned)a + (unsigned)b); }
 __device__ __forceinline__ long long wadd(long long a, long long b) { return a + b; }
 
-// Row i of Z, built and scanned along the row in shared memory, written once.
-// Along x the quadrant of a corner in cell row c = floor(x / w) covers row c
-// over r = (c + 1) w - x and every later row over w: after the column scan
-// that is the two-point splat r at c, w - r at c + 1.  So row i receives the
-// corners of rows i (weight r) and i - 1 (weight w - r), found through the
-// grouping of the corners by x, each splatted along y as q at d = floor(y / w)
-// and w - q at d + 1; the inclusive scan along the row follows.  Corners with
-// x or y outside [0, N) or a sign other than +-1 add nothing.  One CTA per
-// row; the scan is done by warps over chunks of 32 (conflict-free reads).
+// Rows [i0, i0 + nb) of Z (i0 = nb blockIdx.x) summed, built and scanned along
+// the row in shared memory, written once as row blockIdx.x.  Along x the
+// quadrant of a corner in cell row c = floor(x / w) covers row c over
+// r = (c + 1) w - x and every later row over w: after the column scan that is
+// the two-point splat r at c, w - r at c + 1.  So row i receives the corners of
+// rows i (weight r) and i - 1 (weight w - r), found through the grouping of the
+// corners by x, each splatted along y as q at d = floor(y / w) and w - q at
+// d + 1; the inclusive scan along the row follows.  Corners with x or y
+// outside [0, N) or a sign other than +-1 add nothing.  One CTA per row (nb = 1:
+// the rows of Z) or per band of rows (their column sums); the scan is done by
+// warps over chunks of 32 (conflict-free reads).
 template <typename E>
 __global__ void __launch_bounds__(kHThreads) haar_row_build_kernel(const int32_t* __restrict__ x,
                                                                    const int32_t* __restrict__ y,
                                                                    const int8_t* __restrict__ s,
                                                                    const int* __restrict__ start,
                                                                    const int* __restrict__ perm, int N, int G,
-                                                                   int lw, E* Z) {
+                                                                   int lw, int nb, E* Z) {
   griddep_wait();   // launched behind the grouping (programmatic dependent launch)
   using U = typename std::conditional<sizeof(E) == 4, unsigned, unsigned long long>::type;
   constexpr int kWarps = kHThreads / 32;
   extern __shared__ __align__(16) unsigned char hraw[];
   U* row = reinterpret_cast<U*>(hraw);
   __shared__ U tot[kWarps];
-  const int i = blockIdx.x;
+  const int i0 = blockIdx.x * nb;
   const long long w = 1LL << lw;
   for (int j = threadIdx.x; j < G; j += blockDim.x) row[j] = 0;
   __syncthreads();
-  const int xlo = (i > 0 ? i - 1 : 0) << lw;
-  const int xhi = min(N, (i + 1) << lw);   // corners with x in [xlo, xhi): rows i - 1 and i
+  const int xlo = (i0 > 0 ? i0 - 1 : 0) << lw;
+  const int xhi = min(N, (i0 + nb) << lw);   // corners with x in [xlo, xhi): rows i0 - 1 .. i0 + nb - 1
   const int b0 = start[xlo], e0 = start[xhi];
   for (int j = b0 + (int)threadIdx.x; j < e0; j += blockDim.x) {
     const int v = perm[j];
@@ -173,7 +191,7 @@ __global__ void __launch_bounds__(kHThreads) haar_row_build_kernel(const int32_t
     if (yv < 0 || yv >= N || (sv != 1 && sv != -1)) continue;
     const int c = xv >> lw;
     const long long r = (long long)(c + 1) * w - xv;   // in (0, w]
-    const long long wx = c == i ? r : w - r;
+    const long long wx = (c >= i0 ? r : 0) + (c + 1 < i0 + nb ? w - r : 0);
     if (wx == 0) continue;
     const int d = yv >> lw;
     const long long q = (long long)(d + 1) * w - yv;
@@ -191,7 +209,7 @@ __global__ void __launch_bounds__(kHThreads) haar_row_build_kernel(const int32_t
   __syncthreads();
   U off = 0;
   for (int w2 = 0; w2 < warp; ++w2) off += tot[w2];
-  U* out = reinterpret_cast<U*>(Z) + (size_t)i * G;
+  U* out = reinterpret_cast<U*>(Z) + (size_t)blockIdx.x * G;
   for (int j0 = b; j0 < e; j0 += 32) {   // warp-uniform
     const int j = j0 + lane;
     U v = j < e ? row[j] : 0;
@@ -389,6 +407,169 @@ __global__ void __launch_bounds__(kStripWarps * 32, sizeof(E) == 4 ? 3 : 2) haar
   }
 }
 
+// Banded path (grids of at least 256 x 256 cells, Z in 32 bits).  The cell
+// areas of band b (cell rows [32 b, 32 b + 32)) at column d are
+//     A(i, d) = C_b(d) + sum_{i' = 32 b}^{i} R(i', d),   R(i', d) = sum_{d' <= d} Z(i', d'),
+// with C_b(d) the sum of R over all rows above the band.  The band sums S_b(d)
+// (the row build with nb = 32: the rows of a band summed, then scanned) and
+// their exclusive scan over the bands give C_b; each band is then built chunk
+// by chunk in shared memory (row scans carried across the chunks), scanned down
+// its columns from C_b and reduced by the tile pyramids, so the 2^2J cell
+// areas never reach global memory.
+
+// C_b(d) = sum over the bands b' < b of S_b'(d), in place (modulo 2^32: only
+// differences matter).  One CTA per strip of 32 columns, each warp a range of
+// bands: the ranges' sums, their prefix across the warps, then the running sums.
+__global__ void __launch_bounds__(kHThreads) haar_band_scan_kernel(unsigned* S, int G, int nbands) {
+  griddep_wait();   // launched behind the band sums
+  constexpr int kWarps = kHThreads / 32;
+  __shared__ unsigned tot[kWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t col = (size_t)blockIdx.x * 32 + lane;
+  const int per = (nbands + kWarps - 1) / kWarps;
+  const int b0 = min(nbands, warp * per), b1 = min(nbands, b0 + per);
+  unsigned sum = 0;
+#pragma unroll 8
+  for (int b = b0; b < b1; ++b) sum += S[(size_t)b * G + col];
+  tot[warp][lane] = sum;
+  __syncthreads();
+  unsigned run = 0;
+  for (int w2 = 0; w2 < warp; ++w2) run += tot[w2][lane];
+#pragma unroll 8
+  for (int b = b0; b < b1; ++b) {
+    const size_t o = (size_t)b * G + col;
+    const unsigned v = S[o];
+    S[o] = run;
+    run += v;
+  }
+}
+
+// f(row - i0, column, weight) for every splat of the corners of cell rows
+// [i0 - 1, i0 + kBand) on the rows of the band [i0, i0 + kBand): the same terms
+// as the row build's (row c with r, row c + 1 with w - r; column d with q,
+// column d + 1 with w - q; empty or out-of-grid terms left out).
+template <typename F>
+__device__ __forceinline__ void band_splats(const int32_t* __restrict__ x, const int32_t* __restrict__ y,
+                                            const int8_t* __restrict__ s, const int* __restrict__ start,
+                                            const int* __restrict__ perm, int N, int G, int lw, int i0, F&& f) {
+  const int w = 1 << lw;
+  const int xlo = (i0 > 0 ? i0 - 1 : 0) << lw;
+  const int xhi = min(N, (i0 + kBand) << lw);
+  const int b0 = start[xlo], e0 = start[xhi];
+  for (int j = b0 + (int)threadIdx.x; j < e0; j += blockDim.x) {
+    const int v = perm[j];
+    const int xv = __ldg(x + v), yv = __ldg(y + v), sv = __ldg(s + v);
+    if (yv < 0 || yv >= N || (sv != 1 && sv != -1)) continue;
+    const int c = xv >> lw, d = yv >> lw;
+    const int r = ((c + 1) << lw) - xv, q = ((d + 1) << lw) - yv;   // in (0, w]
+    const bool two = q < w && d + 1 < G;
+    if (c >= i0) {
+      f(c - i0, d, sv * r * q);
+      if (two) f(c - i0, d + 1, sv * r * (w - q));
+    }
+    if (c + 1 < i0 + kBand && r < w) {
+      f(c + 1 - i0, d, sv * (w - r) * q);
+      if (two) f(c + 1 - i0, d + 1, sv * (w - r) * (w - q));
+    }
+  }
+}
+
+constexpr size_t kBandTiles = (size_t)(kChunk / kHT) * kHT * (kHT + 1) * 4;
+constexpr size_t kBandSmem = kBandTiles + (size_t)kBandStage * 8;
+
+// One CTA per (band, range of cpc chunks of 256 columns), 8 warps.  The band's
+// splats left of the range are summed into the row carries, those in it staged
+// in shared memory by chunk (counting sort; a band with more than kBandStage of
+// them splats each chunk straight from the corners instead).  Per chunk: the
+// splats into eight 32 x 32 tiles, the row scans from the row carries (warp w:
+// rows 4w .. 4w + 3), then per warp its tile's column scan from C_b and the
+// tile pyramid (levels J - 1 .. J - 5), the tile's area to the coarse grid.
+__global__ void __launch_bounds__(kHThreads, 3) haar_band_kernel(
+    const int32_t* __restrict__ x, const int32_t* __restrict__ y, const int8_t* __restrict__ s,
+    const int* __restrict__ start, const int* __restrict__ perm, int N, int G, int lw, int J, int logN,
+    const unsigned* __restrict__ C, int cpc, long long* coarse, double* W) {
+  griddep_wait();   // launched behind the band scan (and the grouping before it)
+  extern __shared__ __align__(16) unsigned char bsm[];
+  unsigned(*tile)[kHT][kHT + 1] = reinterpret_cast<unsigned(*)[kHT][kHT + 1]>(bsm);
+  uint2* stage = reinterpret_cast<uint2*>(bsm + kBandTiles);   // {row << 8 | column in chunk, weight}
+  __shared__ unsigned rowcarry[kBand];
+  __shared__ int off[kBandMaxChunks + 1], cur[kBandMaxChunks];
+  const int b = blockIdx.y, i0 = b * kBand;
+  const int d0 = blockIdx.x * cpc * kChunk, d1 = d0 + cpc * kChunk;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid < kBand) rowcarry[tid] = 0;
+  if (tid <= kBandMaxChunks) off[tid] = 0;
+  __syncthreads();
+  band_splats(x, y, s, start, perm, N, G, lw, i0, [&](int rl, int col, int wt) {
+    if (col < d0) atomicAdd(&rowcarry[rl], (unsigned)wt);
+    else if (col < d1) atomicAdd(&off[(col - d0) / kChunk], 1);
+  });
+  __syncthreads();
+  if (tid == 0) {
+    int o = 0;
+    for (int k = 0; k < cpc; ++k) {
+      const int c = off[k];
+      off[k] = cur[k] = o;
+      o += c;
+    }
+    off[cpc] = o;
+  }
+  __syncthreads();
+  const bool staged = off[cpc] <= kBandStage;   // block-uniform
+  if (staged) {
+    band_splats(x, y, s, start, perm, N, G, lw, i0, [&](int rl, int col, int wt) {
+      if (col >= d0 && col < d1) {
+        const int pos = atomicAdd(&cur[(col - d0) / kChunk], 1);
+        stage[pos] = make_uint2((unsigned)(rl << 8) | (unsigned)((col - d0) % kChunk), (unsigned)wt);
+      }
+    });
+  }
+  for (int k = 0; k < cpc; ++k) {
+    const int c0 = d0 + k * kChunk;
+    __syncthreads();   // the previous chunk's pyramids (and the staging) are done
+    uint4* tz = reinterpret_cast<uint4*>(bsm);
+    for (int e = tid; e < (int)(kBandTiles / 16); e += kHThreads) tz[e] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    if (staged) {
+      for (int e = off[k] + tid; e < off[k + 1]; e += kHThreads) {
+        const uint2 st = stage[e];
+        const int rl = (int)(st.x >> 8), cl = (int)(st.x & 255u);
+        atomicAdd(&tile[cl >> 5][rl][cl & 31], st.y);
+      }
+    } else {
+      band_splats(x, y, s, start, perm, N, G, lw, i0, [&](int rl, int col, int wt) {
+        if (col >= c0 && col < c0 + kChunk) atomicAdd(&tile[(col - c0) >> 5][rl][(col - c0) & 31], (unsigned)wt);
+      });
+    }
+    __syncthreads();
+    // row scans: lane l holds column l of each of the eight tiles
+    for (int rr = 0; rr < kBand / 8; ++rr) {
+      const int rl = warp * (kBand / 8) + rr;
+      unsigned run = rowcarry[rl];
+#pragma unroll
+      for (int t = 0; t < kChunk / kHT; ++t) {
+        const unsigned v = warp_incl_scan(tile[t][rl][lane], lane);
+        tile[t][rl][lane] = v + run;
+        run += __shfl_sync(0xffffffffu, v, 31);
+      }
+      if (lane == 0) rowcarry[rl] = run;
+    }
+    __syncthreads();
+    // the warp's tile: column scan from C_b, then its pyramid
+    int(*a)[kHT + 1] = reinterpret_cast<int(*)[kHT + 1]>(tile[warp]);
+    unsigned carry = C[(size_t)b * G + c0 + warp * kHT + lane];
+#pragma unroll
+    for (int r = 0; r < kHT; ++r) {
+      carry += (unsigned)a[r][lane];
+      a[r][lane] = (int)carry;
+    }
+    __syncwarp();
+    const int tj = c0 / kHT + warp;
+    warp_pyramid(a, kHT, b, tj, J, logN, W, G, lane);
+    if (lane == 0) coarse[(size_t)b * (G / kHT) + tj] = (long long)a[0][0];
+  }
+}
+
 // One CTA per t x t tile of a coarse area grid of side G (cells of level L):
 // the tile's levels L - 1 .. L - log2 t; its area goes to coarse[ti][tj], and
 // the last pass (a single tile) writes W[0][0] = area / N.
@@ -426,21 +607,39 @@ cudaError_t launch_haar_t(const HaarPlan& hp, const int32_t* x, const int32_t* y
   if ((e = launch_grouping(x, nullptr, hp.V, hp.N, hp.ny_pad, gb, st)) != cudaSuccess) return e;
   const Groups g = groups_at(gb, hp.N, hp.ny_pad);
   const size_t row_smem = (size_t)G * sizeof(E);
-  ensure_smem(reinterpret_cast<const void*>(haar_row_build_kernel<E>), row_smem);
-  if ((e = launch_after(haar_row_build_kernel<E>, dim3(G), dim3(kHThreads), row_smem, st, x, y, s,
-                        (const int*)g.start, (const int*)g.perm, hp.N, G, hp.logN - hp.J, Z)) != cudaSuccess)
-    return e;
-  E* colsum = reinterpret_cast<E*>(ws + hp.off_colsum);
-  if ((e = launch_after(haar_colsum_kernel<E>, dim3(hp.strips, hp.segs), dim3(kHThreads), 0, st, Z, G,
-                        hp.tiles_per_seg * t, colsum)) != cudaSuccess)
-    return e;
+  const int lw = hp.logN - hp.J;
   long long* coarse = reinterpret_cast<long long*>(ws + hp.off_coarse[0]);
-  const int warps = hp.strips * hp.segs;
-  ensure_smem(reinterpret_cast<const void*>(haar_strip_kernel<E>), strip_smem_bytes<E>());
-  if ((e = launch_after(haar_strip_kernel<E>, dim3((warps + kStripWarps - 1) / kStripWarps), dim3(kStripWarps * 32),
-                        strip_smem_bytes<E>(), st, (const E*)Z, G, hp.J, hp.logN, (const E*)colsum, hp.strips,
-                        hp.segs, hp.tiles_per_seg, coarse, W)) != cudaSuccess)
-    return e;
+  ensure_smem(reinterpret_cast<const void*>(haar_row_build_kernel<E>), row_smem);
+  if (hp.banded) {
+    // band sums, their scan over the bands, then the bands on chip
+    unsigned* S = reinterpret_cast<unsigned*>(ws + hp.off_colsum);
+    if ((e = launch_after(haar_row_build_kernel<E>, dim3(hp.nbands), dim3(kHThreads), row_smem, st, x, y, s,
+                          (const int*)g.start, (const int*)g.perm, hp.N, G, lw, kBand,
+                          reinterpret_cast<E*>(S))) != cudaSuccess)
+      return e;
+    if ((e = launch_after(haar_band_scan_kernel, dim3(G / 32), dim3(kHThreads), 0, st, S, G, hp.nbands)) !=
+        cudaSuccess)
+      return e;
+    ensure_smem(reinterpret_cast<const void*>(haar_band_kernel), kBandSmem);
+    if ((e = launch_after(haar_band_kernel, dim3(hp.band_nq, hp.nbands), dim3(kHThreads), kBandSmem, st, x, y, s,
+                          (const int*)g.start, (const int*)g.perm, hp.N, G, lw, hp.J, hp.logN, (const unsigned*)S,
+                          hp.band_cpc, coarse, W)) != cudaSuccess)
+      return e;
+  } else {
+    if ((e = launch_after(haar_row_build_kernel<E>, dim3(G), dim3(kHThreads), row_smem, st, x, y, s,
+                          (const int*)g.start, (const int*)g.perm, hp.N, G, lw, 1, Z)) != cudaSuccess)
+      return e;
+    E* colsum = reinterpret_cast<E*>(ws + hp.off_colsum);
+    if ((e = launch_after(haar_colsum_kernel<E>, dim3(hp.strips, hp.segs), dim3(kHThreads), 0, st, Z, G,
+                          hp.tiles_per_seg * t, colsum)) != cudaSuccess)
+      return e;
+    const int warps = hp.strips * hp.segs;
+    ensure_smem(reinterpret_cast<const void*>(haar_strip_kernel<E>), strip_smem_bytes<E>());
+    if ((e = launch_after(haar_strip_kernel<E>, dim3((warps + kStripWarps - 1) / kStripWarps),
+                          dim3(kStripWarps * 32), strip_smem_bytes<E>(), st, (const E*)Z, G, hp.J, hp.logN,
+                          (const E*)colsum, hp.strips, hp.segs, hp.tiles_per_seg, coarse, W)) != cudaSuccess)
+      return e;
+  }
   int L = hp.J - ilog2(t);
   for (int p = 1; p < hp.npass; ++p) {
     const int g = hp.coarse_side[p - 1], tt = g < kHT ? g : kHT;

@@ -131,7 +131,10 @@ def test_haar_host_checks(lib):
     """The Haar-transform entry points: sizes and host-detectable errors."""
     hw = lib.fcfs_haar_workspace_size
     a = hw(12576, 4096, 12)
-    assert a >= 4 * 4 ** 12 and a % 256 == 0             # the level-12 cell grid (int32: cells of side 1)
+    # banded (grids of >= 256 cells a side): the band sums (2^12 / 32 x 2^12 int32),
+    # never the 2^24-cell grid
+    assert 4 * 4 ** 12 // 32 <= a < 4 * 4 ** 12 and a % 256 == 0
+    assert hw(12576, 4096, 7) >= 4 * 4 ** 7               # 128 x 128 cells: the grid (int32: cells of side 32)
     assert hw(100, 65536, 5) >= 8 * 4 ** 5                # cells of side 2048: int64 grid
     assert hw(0, 4096, 0) > 0 and hw(100, 16, 4) > 0
     assert hw(100, 4096, 13) == 0                         # J > log2 T

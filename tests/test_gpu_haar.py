@@ -102,13 +102,40 @@ def test_haar_border_and_empty(fc):
     assert torch.all(W == 0)
 
 
+def test_haar_dense_band(fc):
+    """A band of 32 cell rows holding more splats than the banded kernel stages
+    in shared memory (8192 corners in the first 32 x 256 cells): its chunks are
+    splatted straight from the corners; the other bands are staged."""
+    rings = [rect_ring(2 * i, 2 * j, 2 * i + 1, 2 * j + 1) for i in range(16) for j in range(128)]
+    rings += [rect_ring(100, 40, 900, 1700), rect_ring(1500, 3, 2047, 2048)]
+    c = clip_from_rings(2048, rings)
+    W = gpu_haar(fc, c, 11).cpu().numpy()
+    assert np.array_equal(W, haar.pcht(c.x, c.y, c.poly_offsets, 2048, 11))
+
+
+@pytest.mark.parametrize("J,scale", [(13, 8), (14, 4)])
+def test_haar_banded_chunks_parseval(fc, J, scale):
+    """Grids of 2^13 and 2^14 cells a side on T = 65536 (several 256-column
+    chunks per CTA, row carries across them): with every coordinate a multiple
+    of the cell side each cell is wholly inside or outside, the level-J
+    projection is the image, and Parseval gives the area over all 2^2J
+    coefficients; W[0][0] = area / T."""
+    import dataclasses
+    base = make_clip(65536 // scale, 30000, 70 + J, smin=2, smax=60)
+    clip = dataclasses.replace(base, T=65536, x=base.x * scale, y=base.y * scale)
+    A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+    W = gpu_haar(fc, clip, J)
+    assert abs(float(torch.sum(W * W)) - A) / A < 1e-12
+    assert float(W[0, 0]) == A / 65536
+
+
 def test_haar_deterministic_and_launches(fc):
     clip = make_clip(1024, 300, 64, smin=6, smax=40)
     x, y, s = to_dev(clip)
     ws = fc.alloc_workspace(fc.haar_workspace_size(clip.V, clip.T, 10), x.device)
     n0 = fc.launch_count()
     W1 = fc.haar(x, y, s, clip.T, 10, workspace=ws).clone()
-    assert fc.launch_count() - n0 == 7   # grouping by x (3), row build, column sums, scan + pyramid, 32 x 32 grid
+    assert fc.launch_count() - n0 == 7   # grouping by x (3), band sums, band scan, bands, 32 x 32 grid
     W2 = fc.haar(x, y, s, clip.T, 10, workspace=ws)
     torch.cuda.synchronize()
     assert torch.equal(W1, W2)
