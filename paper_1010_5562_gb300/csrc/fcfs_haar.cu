@@ -474,15 +474,19 @@ __device__ __forceinline__ void band_splats(const int32_t* __restrict__ x, const
   }
 }
 
-constexpr size_t kBandTiles = (size_t)(kChunk / kHT) * kHT * (kHT + 1) * 4;
+// the chunk's eight 32 x 33 tiles, each 4 words further along the banks than
+// the last: the row scans' lanes (8 tiles x 4 rows at one column) hit distinct banks
+constexpr int kBandTileWords = kHT * (kHT + 1) + 4;
+constexpr size_t kBandTiles = (size_t)(kChunk / kHT) * kBandTileWords * 4;
 constexpr size_t kBandSmem = kBandTiles + (size_t)kBandStage * 8;
 
 // One CTA per (band, range of cpc chunks of 256 columns), 8 warps.  The band's
 // splats left of the range are summed into the row carries, those in it staged
 // in shared memory by chunk (counting sort; a band with more than kBandStage of
 // them splats each chunk straight from the corners instead).  Per chunk: the
-// splats into eight 32 x 32 tiles, the row scans from the row carries (warp w:
-// rows 4w .. 4w + 3), then per warp its tile's column scan from C_b and the
+// splats into eight 32 x 32 tiles, the row scans from the row carries (thread
+// (row, tile): its 32 columns in order, the tiles' totals prefixed across the
+// row's eight threads), then per warp its tile's column scan from C_b and the
 // tile pyramid (levels J - 1 .. J - 5), the tile's area to the coarse grid.
 __global__ void __launch_bounds__(kHThreads, 3) haar_band_kernel(
     const int32_t* __restrict__ x, const int32_t* __restrict__ y, const int8_t* __restrict__ s,
@@ -490,7 +494,7 @@ __global__ void __launch_bounds__(kHThreads, 3) haar_band_kernel(
     const unsigned* __restrict__ C, int cpc, long long* coarse, double* W) {
   griddep_wait();   // launched behind the band scan (and the grouping before it)
   extern __shared__ __align__(16) unsigned char bsm[];
-  unsigned(*tile)[kHT][kHT + 1] = reinterpret_cast<unsigned(*)[kHT][kHT + 1]>(bsm);
+  auto tile = [&](int t) { return reinterpret_cast<unsigned(*)[kHT + 1]>(bsm + (size_t)t * kBandTileWords * 4); };
   uint2* stage = reinterpret_cast<uint2*>(bsm + kBandTiles);   // {row << 8 | column in chunk, weight}
   __shared__ unsigned rowcarry[kBand];
   __shared__ int off[kBandMaxChunks + 1], cur[kBandMaxChunks];
@@ -534,29 +538,41 @@ __global__ void __launch_bounds__(kHThreads, 3) haar_band_kernel(
       for (int e = off[k] + tid; e < off[k + 1]; e += kHThreads) {
         const uint2 st = stage[e];
         const int rl = (int)(st.x >> 8), cl = (int)(st.x & 255u);
-        atomicAdd(&tile[cl >> 5][rl][cl & 31], st.y);
+        atomicAdd(&tile(cl >> 5)[rl][cl & 31], st.y);
       }
     } else {
       band_splats(x, y, s, start, perm, N, G, lw, i0, [&](int rl, int col, int wt) {
-        if (col >= c0 && col < c0 + kChunk) atomicAdd(&tile[(col - c0) >> 5][rl][(col - c0) & 31], (unsigned)wt);
+        if (col >= c0 && col < c0 + kChunk) atomicAdd(&tile((col - c0) >> 5)[rl][(col - c0) & 31], (unsigned)wt);
       });
     }
     __syncthreads();
-    // row scans: lane l holds column l of each of the eight tiles
-    for (int rr = 0; rr < kBand / 8; ++rr) {
-      const int rl = warp * (kBand / 8) + rr;
-      unsigned run = rowcarry[rl];
+    {
+      // row scans: thread (row rl, tile t) sums its 32 columns, the totals of the
+      // row's tiles are prefixed over its eight consecutive lanes, then the
+      // running sums are written from the row carry plus that prefix
+      const int rl = tid >> 3, t = tid & 7;
+      unsigned(*row)[kHT + 1] = tile(t);
+      unsigned sum = 0;
+#pragma unroll 8
+      for (int c = 0; c < kHT; ++c) sum += row[rl][c];
+      unsigned incl = sum;
 #pragma unroll
-      for (int t = 0; t < kChunk / kHT; ++t) {
-        const unsigned v = warp_incl_scan(tile[t][rl][lane], lane);
-        tile[t][rl][lane] = v + run;
-        run += __shfl_sync(0xffffffffu, v, 31);
+      for (int d = 1; d < 8; d <<= 1) {
+        const unsigned u = __shfl_up_sync(0xffffffffu, incl, d, 8);
+        if (t >= d) incl += u;
       }
-      if (lane == 0) rowcarry[rl] = run;
+      unsigned run = rowcarry[rl] + (incl - sum);
+#pragma unroll 8
+      for (int c = 0; c < kHT; ++c) {
+        run += row[rl][c];
+        row[rl][c] = run;
+      }
+      __syncthreads();   // every thread has read its row carry
+      if (t == 7) rowcarry[rl] = run;
     }
     __syncthreads();
     // the warp's tile: column scan from C_b, then its pyramid
-    int(*a)[kHT + 1] = reinterpret_cast<int(*)[kHT + 1]>(tile[warp]);
+    int(*a)[kHT + 1] = reinterpret_cast<int(*)[kHT + 1]>(tile(warp));
     unsigned carry = C[(size_t)b * G + c0 + warp * kHT + lane];
 #pragma unroll
     for (int r = 0; r < kHT; ++r) {
