@@ -978,10 +978,12 @@ def haar_extras(fcfs, dev, flush, stream):
     """Continuous Haar transform (all 4^J coefficients up to level J): the bench
     clip at full depth (T = 4096, J = 12) and the T = 65536 clip at J = 14.
     HBM roofline of the whole call: algorithmic bytes = the corners read once
-    (9 B each) plus the FP64 coefficients written once (8 B each); the pipeline
-    moves more per cell: 3 passes over the level-J grid of 4 B per cell (int32
-    grid, cells up to 1024 wide) or 8 B (the row build's write, the column sums'
-    read, the strip kernel's read), plus the 8 B coefficient per cell."""
+    (9 B each) plus the FP64 coefficients written once (8 B each).  What the
+    pipeline moves: on grids of >= 256 cells a side (the banded kernels, 32-bit
+    cells) the coefficients, the band sums (4 B per 32 cells, written, read
+    twice by the band scan, written again, read by the bands: 0.5 B per cell)
+    and the corners twice (band sums, bands); on smaller grids 3 passes over the
+    level-J grid of 4 B (or 8 B) per cell plus the coefficients."""
     import torch
     from synth import config_clip
     peak, src = measured_hbm()
@@ -996,7 +998,10 @@ def haar_extras(fcfs, dev, flush, stream):
                        10 if J <= 12 else 3, flush, stream)
         alg = 9.0 * clip.V + 8.0 * G * G
         elem = 4.0 if (clip.T >> J) <= 1024 else 8.0
-        moved = (3.0 * elem + 8.0) * G * G + 9.0 * clip.V
+        if G >= 256 and elem == 4.0:
+            moved = 8.5 * G * G + 18.0 * clip.V
+        else:
+            moved = (3.0 * elem + 8.0) * G * G + 9.0 * clip.V
         d = {"V": clip.V, "T": clip.T, "J": J, "value": G * G / (ms * 1e-3), "ms": ms,
              "algorithmic_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9,
              "frac_of_hbm_peak": alg / (ms * 1e-3) / 1e9 / peak,
