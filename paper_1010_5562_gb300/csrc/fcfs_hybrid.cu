@@ -220,6 +220,7 @@ constexpr int kHLd = kHPassF + 2;       // tile row stride (float2; rows stay 16
 constexpr int kHTabMax = 256;           // two-level table entries per level (T <= 2^16)
 constexpr int kHCacheFB = 2048;         // fallback: corners staged in shared memory
 constexpr int kHRowsFp16 = 0, kHPolyF32 = 1;
+constexpr int kHRankMax = 128;          // items whose rows hold at most this many corners are sorted by rank
 
 template <int FMT>
 struct HCfg {
@@ -421,51 +422,88 @@ __device__ void h_item_exact(const Plan& pl, const Groups& g, int clip, int y0, 
   }
 }
 
-// Fast-path staging of an item: sort keys (row << 17 | x << 1 | sign), the
-// first sorted corner of each row (rowc), the first pair of each row (rowp), and
+// Fast-path staging of an item: sort keys (row << 17 | x << 1 | sign) (a
+// counting sort by row, then ranks within the rows; a bitonic sort of the item
+// when a row holds more than kHRankMax corners), the first sorted corner of each
+// row (rowc), the first pair of each row (rowp), and
 // per pair meta {x_a | kind << 20 | sign_a << 22, w} (kind 0: opposite signs, 1:
 // equal, 2: alone) and steps {e^{j 32 x_a}, D_32} (kHPolyF32 also {e^{j 64 x_a},
 // D_64} in cst2).
 template <int FMT>
-__device__ void h_stage(const Plan& pl, const Groups& g, int y0, const HRange& rg, uint32_t* keys, uint2* meta,
-                        float4* cst, float4* cst2, int* rowc, int* rowp, const HTabs& tb) {
+__device__ void h_stage(const Plan& pl, const Groups& g, int y0, const HRange& rg, uint32_t* keys, uint32_t* tmp,
+                        uint2* meta, float4* cst, float4* cst2, int* rowc, int* rowp, const HTabs& tb) {
   const int T = pl.T, n = rg.count(), tid = threadIdx.x, nt = blockDim.x;
   const uint32_t mask = (uint32_t)T - 1u;
-  int npad = 1;
-  while (npad < n) npad <<= 1;
-  for (int i = tid; i < npad; i += nt) {
-    uint32_t key = 0xFFFFFFFFu;
-    if (i < n) {
-      const int v = rg.corner(g.perm, i);
-      const int yv = __ldg(pl.vy + v);
-      const int yl = (FMT == kHPolyF32 && yv == T) ? 0 : yv - y0;
-      const uint32_t xm = (uint32_t)__ldg(pl.vx + v) & mask;
-      key = ((uint32_t)yl << 17) | (xm << 1) | (__ldg(pl.vsg + v) < 0 ? 1u : 0u);
-    }
-    keys[i] = key;
+  __shared__ int s_rank;
+  // the keys in item order, and the corners per row
+  for (int r = tid; r < kHY + 2; r += nt) rowc[r] = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {
+    const int v = rg.corner(g.perm, i);
+    const int yv = __ldg(pl.vy + v);
+    const int yl = (FMT == kHPolyF32 && yv == T) ? 0 : yv - y0;
+    const uint32_t xm = (uint32_t)__ldg(pl.vx + v) & mask;
+    const uint32_t key = ((uint32_t)yl << 17) | (xm << 1) | (__ldg(pl.vsg + v) < 0 ? 1u : 0u);
+    tmp[i] = key;
+    atomicAdd(&rowc[yl], 1);
   }
   __syncthreads();
-  for (int kk = 2; kk <= npad; kk <<= 1)
-    for (int j = kk >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < npad; i += nt) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const uint32_t u = keys[i], w = keys[ixj];
-          if ((u > w) == ((i & kk) == 0)) {
-            keys[i] = w;
-            keys[ixj] = u;
+  if (tid < 32) {   // rowc = the rows' first sorted positions (two rows a lane), rowp their cursors
+    const int c0 = rowc[2 * tid], c1 = rowc[2 * tid + 1];
+    int incl = c0 + c1, mx = max(c0, c1);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t2 = __shfl_up_sync(0xffffffffu, incl, o);
+      if (tid >= o) incl += t2;
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const int ex = incl - c0 - c1;
+    rowc[2 * tid] = rowp[2 * tid] = ex;
+    rowc[2 * tid + 1] = rowp[2 * tid + 1] = ex + c0;
+    if (tid == 31) rowc[kHY] = incl;
+    if (tid == 0) s_rank = mx <= kHRankMax ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_rank) {
+    // a counting sort by row, then each corner placed at its rank among its row's
+    // keys (equal keys are equal corners: their order does not matter)
+    for (int i = tid; i < n; i += nt) {
+      const uint32_t key = tmp[i];
+      keys[atomicAdd(&rowp[key >> 17], 1)] = key;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) {
+      const uint32_t key = keys[i];
+      const int r = (int)(key >> 17), b = rowc[r], e = rowc[r + 1];
+      int rank = 0;
+      for (int j = b; j < e; ++j) {
+        const uint32_t kj = keys[j];
+        rank += (kj < key || (kj == key && j < i)) ? 1 : 0;
+      }
+      tmp[b + rank] = key;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) keys[i] = tmp[i];
+  } else {
+    // rows of many corners: a bitonic sort of the whole item
+    int npad = 1;
+    while (npad < n) npad <<= 1;
+    for (int i = tid; i < npad; i += nt) keys[i] = i < n ? tmp[i] : 0xFFFFFFFFu;
+    __syncthreads();
+    for (int kk = 2; kk <= npad; kk <<= 1)
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < npad; i += nt) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const uint32_t u = keys[i], w = keys[ixj];
+            if ((u > w) == ((i & kk) == 0)) {
+              keys[i] = w;
+              keys[ixj] = u;
+            }
           }
         }
+        __syncthreads();
       }
-      __syncthreads();
-    }
-  for (int r = tid; r <= kHY; r += nt) {
-    int lo = 0, hi = n;   // first index whose row is >= r
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if ((int)(keys[mid] >> 17) < r) lo = mid + 1; else hi = mid;
-    }
-    rowc[r] = lo;
   }
   __syncthreads();
   if (tid < 32) {   // rowp = exclusive scan of ceil(n_row / 2) over the 64 rows
@@ -792,6 +830,9 @@ __global__ void __launch_bounds__(HCfg<FMT>::threads, HCfg<FMT>::min_blocks)
   uint2* meta = reinterpret_cast<uint2*>(sm + C::meta);
   float4* cst = reinterpret_cast<float4*>(sm + C::cst);
   float4* cst2 = reinterpret_cast<float4*>(sm + C::cst2);
+  // the staging's second key array: behind the keys in the tile (kHRowsFp16), the
+  // second step array (kHPolyF32); both are written only after the staging
+  uint32_t* tmp = reinterpret_cast<uint32_t*>(sm + (FMT == kHRowsFp16 ? (size_t)kHCap * 4 : C::cst2));
   float2* tabs = reinterpret_cast<float2*>(sm + C::tabs);
   int* rowc = reinterpret_cast<int*>(sm + C::rows);
   int* rowp = rowc + kHY + 2;
@@ -830,7 +871,7 @@ __global__ void __launch_bounds__(HCfg<FMT>::threads, HCfg<FMT>::min_blocks)
     const HRange rg = item_range<FMT>(g, y0, T);
     if (rg.count() <= kHCap) {
       levels = false;   // the fast path overwrites them
-      h_stage<FMT>(pl, g, y0, rg, keys, meta, cst, cst2, rowc, rowp, tb);
+      h_stage<FMT>(pl, g, y0, rg, keys, tmp, meta, cst, cst2, rowc, rowp, tb);
       if (FMT == kHRowsFp16)
         h_rows_fp16(pl, clip, y0, tile, meta, cst, rowp, &s_row, tb, out);
       else
