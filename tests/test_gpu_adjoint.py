@@ -98,7 +98,9 @@ def test_autograd_edge_gradient_and_finite_differences(fc):
     _, G = oracle.pupil_loss(Fo, Fto, K)
     rx, ry = oracle.vertex_gradient(clip.x, clip.y, clip.s, T, K, G)
     rE = oracle.edge_gradient(rx, ry, clip.ev0, clip.ev1, clip.eaxis)
-    assert rel(gE, rE) < 1e-4     # includes the FP32 forward error of F in the cotangent
+    # includes the FP32 forward error of F in the cotangent (measured 1.4e-6; 2.5e-6
+    # with the split-FP16 forward)
+    assert rel(gE, rE) < 1e-5
 
     def loss_at(p):
         with torch.no_grad():

@@ -112,6 +112,28 @@ def test_fft_dense_rows_fallback(fc):
     assert np.max(np.abs(F[np.ix_(pick + K, pick + K)] - Fo)) / A <= 5e-6
 
 
+@pytest.mark.parametrize("mode,tol", [(FFT, TOL), (2, 1e-5)], ids=["grouped_fft", "grouped_tc"])
+def test_wide_rows_sorted_whole(fc, mode, tol):
+    """Rows of more than 128 corners (150 rectangles side by side on y in
+    [100, 164): 300 corners on rows 100 and 164) take the bitonic sort of their
+    whole item; the other items, with rows of a few corners, the sort by rank
+    within the rows.  Both H formats (polyphase FP32, FP16 rows) against the
+    oracle over the whole block."""
+    T, K = 4096, 96
+    rings = [rect_ring(20 + 25 * i, 100, 40 + 25 * i, 164) for i in range(150)]
+    base = make_clip(T, 300, 31, smin=8, smax=60)
+    for m in range(base.n_polys):
+        xs, ys = base.ring(m)
+        if ys.min() > 300:   # keep the random polygons clear of the wide rows
+            rings.append((xs, ys))
+    clip = clip_from_rings(T, rings)
+    F, a = run(fc, clip, K, mode)
+    A = oracle.area_exact(clip.x, clip.y, clip.s, clip.T)
+    assert a == A
+    Fo = oracle.block(clip.x, clip.y, clip.s, clip.T, K)
+    assert np.max(np.abs(F - Fo)) / A <= tol
+
+
 def test_fft_rows_on_the_clip_border(fc):
     """Corners on y = T (folded onto row 0) and on x = T and x = 0."""
     T, K = 512, 60
