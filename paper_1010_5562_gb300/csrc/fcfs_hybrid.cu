@@ -44,84 +44,101 @@ __global__ void group_count_kernel(const int32_t* __restrict__ c0, const int32_t
 
 // One CTA: exclusive scan of the T + 1 counts of g into start (and the
 // cursors), plus `first`; start[T + 1] = first + the number of grouped corners;
-// the exponents e of the large groups.  Each thread owns one contiguous range
-// of the counts (a multiple of 4 entries, within the padded array): it sums its
-// range, one block-wide scan of the sums gives each range's offset, and a
-// second pass over the range writes the running sums and the exponents.  Both
-// passes keep four vector loads in flight.
+// the exponents e of the large groups.  The counts are read as 4-vectors in
+// rounds of one vector per thread (round j, thread t: vector j kScanThreads + t,
+// coalesced), every round's loads in flight together: a first pass sums each
+// vector, scans the sums within the warps and then over the warps and the
+// rounds; a second pass reloads the vectors and writes the running sums and the
+// exponents.
 constexpr int kScanThreads = 1024;
+constexpr int kScanRounds = 17;   // 4 kScanRounds kScanThreads >= group_stride(65536)
 __device__ __forceinline__ int8_t group_exponent(int c) {   // ceil(log2 c) - 14, within [0, 15]
   if (c <= (1 << 14)) return 0;
   const int l = 32 - __clz(c - 1);
   return (int8_t)min(15, l - 14);
 }
 __device__ void scan_groups(const Groups& g, int T, int ny_pad, int first) {
-  const int n = T + 1, S = group_stride(T);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ int wsum[kScanThreads / 32];
-  const int per = ((S + kScanThreads - 1) / kScanThreads + 3) & ~3;
-  const int i0 = min(S, (int)threadIdx.x * per), i1 = min(S, i0 + per);
-  auto counts = [&](int i) {   // four counts from i (the vector stays inside the padded array); past n: 0
-    int4 c = i < i1 ? *reinterpret_cast<const int4*>(g.cnt + i) : make_int4(0, 0, 0, 0);
+  constexpr int kW = kScanThreads / 32;
+  static_assert(kW == 32 && kScanRounds <= 32, "one lane per warp and per round");
+  const int n = T + 1, S = group_stride(T), nvec = S >> 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int wpre[kScanRounds][kW];   // per round: the warps' exclusive prefix
+  __shared__ int rtot[kScanRounds], rpre[kScanRounds], total;
+  auto counts = [&](int v) {   // vector v of the counts (inside the padded array); past n: 0
+    const int i = 4 * v;
+    int4 c = v < nvec ? *reinterpret_cast<const int4*>(g.cnt + i) : make_int4(0, 0, 0, 0);
     if (i >= n) c.x = 0;
     if (i + 1 >= n) c.y = 0;
     if (i + 2 >= n) c.z = 0;
     if (i + 3 >= n) c.w = 0;
     return c;
   };
-  int tsum = 0;
-  for (int i = i0; i < i1; i += 16) {
-    int4 c[4];
+  int pre[kScanRounds];   // first the vectors' sums, then their exclusive prefix within the warp
 #pragma unroll
-    for (int u = 0; u < 4; ++u) c[u] = counts(i + 4 * u);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) tsum += c[u].x + c[u].y + c[u].z + c[u].w;
+  for (int j = 0; j < kScanRounds; ++j) {
+    const int4 c = counts(j * kScanThreads + tid);
+    pre[j] = c.x + c.y + c.z + c.w;
   }
-  int incl = tsum;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    int w = wsum[lane];
+  for (int j = 0; j < kScanRounds; ++j) {
+    int x = pre[j];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += t;
+      const int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
     }
-    wsum[lane] = w;   // inclusive over warps
+    pre[j] = x - pre[j];
+    if (lane == 31) wpre[j][warp] = x;
   }
   __syncthreads();
-  int run = first + (warp > 0 ? wsum[warp - 1] : 0) + incl - tsum;
-  for (int i = i0; i < i1; i += 16) {
-    int4 c[4];
+  if (warp < kScanRounds) {   // warp j: the warps' totals of round j
+    const int w = wpre[warp][lane];
+    int x = w;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) c[u] = counts(i + 4 * u);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    wpre[warp][lane] = x - w;
+    if (lane == 31) rtot[warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {   // the rounds' totals
+    const int r = lane < kScanRounds ? rtot[lane] : 0;
+    int x = r;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = i + 4 * u;
-      if (j >= i1) break;
-      const int4 st4 = make_int4(run, run + c[u].x, run + c[u].x + c[u].y, run + c[u].x + c[u].y + c[u].z);
-      run += c[u].x + c[u].y + c[u].z + c[u].w;
-      if (j < n) {   // start and cursors of the n groups (whole vectors stay inside the padded arrays)
-        *reinterpret_cast<int4*>(g.start + j) = st4;
-        *reinterpret_cast<int4*>(g.cur + j) = st4;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane < kScanRounds) rpre[lane] = x - r;
+    if (lane == 31) total = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kScanRounds; ++j) {
+    const int v = j * kScanThreads + tid;
+    if (v < nvec) {
+      const int4 c = counts(v);
+      const int run = first + rpre[j] + wpre[j][warp] + pre[j];
+      const int i = 4 * v;
+      const int4 st4 = make_int4(run, run + c.x, run + c.x + c.y, run + c.x + c.y + c.z);
+      if (i < n) {   // start and cursors of the n groups (whole vectors stay inside the padded arrays)
+        *reinterpret_cast<int4*>(g.start + i) = st4;
+        *reinterpret_cast<int4*>(g.cur + i) = st4;
       }
-      if (j < ny_pad) {   // the exponents of these four groups (0 past n), one 4-byte store
-        const uint32_t e = (uint32_t)(uint8_t)group_exponent(c[u].x) | ((uint32_t)(uint8_t)group_exponent(c[u].y) << 8) |
-                           ((uint32_t)(uint8_t)group_exponent(c[u].z) << 16) |
-                           ((uint32_t)(uint8_t)group_exponent(c[u].w) << 24);
-        *reinterpret_cast<uint32_t*>(g.ey + j) = e;
+      if (i < ny_pad) {   // the exponents of these four groups (0 past n), one 4-byte store
+        const uint32_t e = (uint32_t)(uint8_t)group_exponent(c.x) | ((uint32_t)(uint8_t)group_exponent(c.y) << 8) |
+                           ((uint32_t)(uint8_t)group_exponent(c.z) << 16) |
+                           ((uint32_t)(uint8_t)group_exponent(c.w) << 24);
+        *reinterpret_cast<uint32_t*>(g.ey + i) = e;
       }
     }
   }
   // exponents past the counts array (ny_pad > S): zero
   for (int i = S + 4 * (int)threadIdx.x; i < ny_pad; i += 4 * kScanThreads) *reinterpret_cast<uint32_t*>(g.ey + i) = 0u;
   __syncthreads();   // start[n] after the vector stores that may cover it
-  if (threadIdx.x == 0) g.start[n] = first + wsum[kScanThreads / 32 - 1];
+  if (threadIdx.x == 0) g.start[n] = first + total;
 }
 
 // One CTA per coordinate.
