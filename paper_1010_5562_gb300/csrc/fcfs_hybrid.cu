@@ -49,7 +49,9 @@ __global__ void group_count_kernel(const int32_t* __restrict__ c0, const int32_t
 // coalesced), every round's loads in flight together: a first pass sums each
 // vector, scans the sums within the warps and then over the warps and the
 // rounds; a second pass reloads the vectors and writes the running sums and the
-// exponents.
+// exponents.  R (a template parameter: the fewest rounds that cover the counts)
+// bounds the registers, so that a small scan's CTA fits beside the kernel before
+// it.
 constexpr int kScanThreads = 1024;
 constexpr int kScanRounds = 17;   // 4 kScanRounds kScanThreads >= group_stride(65536)
 __device__ __forceinline__ int8_t group_exponent(int c) {   // ceil(log2 c) - 14, within [0, 15]
@@ -57,13 +59,18 @@ __device__ __forceinline__ int8_t group_exponent(int c) {   // ceil(log2 c) - 14
   const int l = 32 - __clz(c - 1);
   return (int8_t)min(15, l - 14);
 }
+// Rounds of vectors that cover the counts of coordinates in [0, T].
+__host__ __device__ inline int scan_rounds(int T) { return (group_stride(T) / 4 + kScanThreads - 1) / kScanThreads; }
+
+template <int R>
 __device__ void scan_groups(const Groups& g, int T, int ny_pad, int first) {
   constexpr int kW = kScanThreads / 32;
-  static_assert(kW == 32 && kScanRounds <= 32, "one lane per warp and per round");
+  static_assert(kW == 32 && R <= 32, "one lane per warp and per round");
   const int n = T + 1, S = group_stride(T), nvec = S >> 2;
+  const int rounds = min(R, (nvec + kScanThreads - 1) / kScanThreads);   // rounds that hold counts (block-uniform)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __shared__ int wpre[kScanRounds][kW];   // per round: the warps' exclusive prefix
-  __shared__ int rtot[kScanRounds], rpre[kScanRounds], total;
+  __shared__ int wpre[R][kW];   // per round: the warps' exclusive prefix
+  __shared__ int rtot[R], rpre[R], total;
   auto counts = [&](int v) {   // vector v of the counts (inside the padded array); past n: 0
     const int i = 4 * v;
     int4 c = v < nvec ? *reinterpret_cast<const int4*>(g.cnt + i) : make_int4(0, 0, 0, 0);
@@ -73,14 +80,15 @@ __device__ void scan_groups(const Groups& g, int T, int ny_pad, int first) {
     if (i + 3 >= n) c.w = 0;
     return c;
   };
-  int pre[kScanRounds];   // first the vectors' sums, then their exclusive prefix within the warp
+  int pre[R];   // first the vectors' sums, then their exclusive prefix within the warp
 #pragma unroll
-  for (int j = 0; j < kScanRounds; ++j) {
+  for (int j = 0; j < R; ++j) {
     const int4 c = counts(j * kScanThreads + tid);
     pre[j] = c.x + c.y + c.z + c.w;
   }
 #pragma unroll
-  for (int j = 0; j < kScanRounds; ++j) {
+  for (int j = 0; j < R; ++j) {
+    if (j >= rounds) break;
     int x = pre[j];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -91,7 +99,7 @@ __device__ void scan_groups(const Groups& g, int T, int ny_pad, int first) {
     if (lane == 31) wpre[j][warp] = x;
   }
   __syncthreads();
-  if (warp < kScanRounds) {   // warp j: the warps' totals of round j
+  if (warp < rounds) {   // warp j: the warps' totals of round j
     const int w = wpre[warp][lane];
     int x = w;
 #pragma unroll
@@ -104,19 +112,20 @@ __device__ void scan_groups(const Groups& g, int T, int ny_pad, int first) {
   }
   __syncthreads();
   if (warp == 0) {   // the rounds' totals
-    const int r = lane < kScanRounds ? rtot[lane] : 0;
+    const int r = lane < rounds ? rtot[lane] : 0;
     int x = r;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int t = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += t;
     }
-    if (lane < kScanRounds) rpre[lane] = x - r;
+    if (lane < rounds) rpre[lane] = x - r;
     if (lane == 31) total = x;
   }
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < kScanRounds; ++j) {
+  for (int j = 0; j < R; ++j) {
+    if (j >= rounds) break;
     const int v = j * kScanThreads + tid;
     if (v < nvec) {
       const int4 c = counts(v);
@@ -142,9 +151,10 @@ __device__ void scan_groups(const Groups& g, int T, int ny_pad, int first) {
 }
 
 // One CTA per coordinate.
+template <int R>
 __global__ void __launch_bounds__(kScanThreads) group_scan_kernel(long long V, int T, int ny_pad, uint8_t* base) {
   griddep_wait();
-  scan_groups(groups_at(base + blockIdx.x * group_bytes(V, T, ny_pad), T, ny_pad), T, ny_pad, 0);
+  scan_groups<R>(groups_at(base + blockIdx.x * group_bytes(V, T, ny_pad), T, ny_pad), T, ny_pad, 0);
 }
 
 // Batch: clip c = blockIdx.y groups its corners [offsets[c], offsets[c + 1])
@@ -160,11 +170,12 @@ __global__ void batch_group_count_kernel(const int32_t* __restrict__ y, const in
     if (yv >= 0 && yv <= T) atomicAdd(&g.cnt[yv], 1);
   }
 }
+template <int R>
 __global__ void __launch_bounds__(kScanThreads) batch_group_scan_kernel(const int64_t* __restrict__ offsets, int n,
                                                                         int T, int ny_pad, long long V,
                                                                         uint8_t* base) {
   const int c = blockIdx.x;
-  scan_groups(groups_clip(base, T, ny_pad, n, c, V), T, ny_pad, (int)offsets[c]);
+  scan_groups<R>(groups_clip(base, T, ny_pad, n, c, V), T, ny_pad, (int)offsets[c]);
 }
 __global__ void batch_group_scatter_kernel(const int32_t* __restrict__ y, const int64_t* __restrict__ offsets, int n,
                                            int T, int ny_pad, long long V, uint8_t* base) {
@@ -1212,8 +1223,9 @@ cudaError_t launch_grouping(const int32_t* c0, const int32_t* c1, int64_t V, int
   if ((e = launch_after(group_count_kernel, dim3(vblocks, nc), dim3(256), 0, st, c0, c1, (long long)V, T, ny_pad,
                         base, key_logP)) != cudaSuccess)
     return e;
-  if ((e = launch_after(group_scan_kernel, dim3(nc), dim3(kScanThreads), 0, st, (long long)V, T, ny_pad, base)) !=
-      cudaSuccess)
+  const int rounds = scan_rounds(T);
+  auto scan = rounds <= 1 ? group_scan_kernel<1> : rounds <= 4 ? group_scan_kernel<4> : group_scan_kernel<kScanRounds>;
+  if ((e = launch_after(scan, dim3(nc), dim3(kScanThreads), 0, st, (long long)V, T, ny_pad, base)) != cudaSuccess)
     return e;
   return launch_after(group_scatter_kernel, dim3(vblocks, nc), dim3(256), 0, st, c0, c1, (long long)V, T, ny_pad,
                       base, key_logP);
@@ -1231,8 +1243,11 @@ static cudaError_t group_rows(const Plan& pl, uint8_t* ws, cudaStream_t st) {
     const int bx = (int)std::max<long long>(1, std::min<long long>((per_clip + 255) / 256, 64));
     batch_group_count_kernel<<<dim3(bx, nclips), 256, 0, st>>>(pl.vy, pl.offsets, nclips, pl.T, pl.ny_pad, pl.V,
                                                               ws + pl.off_ycnt);
-    batch_group_scan_kernel<<<nclips, kScanThreads, 0, st>>>(pl.offsets, nclips, pl.T, pl.ny_pad, pl.V,
-                                                            ws + pl.off_ycnt);
+    const int rounds = scan_rounds(pl.T);
+    auto scan = rounds <= 1   ? batch_group_scan_kernel<1>
+                : rounds <= 4 ? batch_group_scan_kernel<4>
+                              : batch_group_scan_kernel<kScanRounds>;
+    scan<<<nclips, kScanThreads, 0, st>>>(pl.offsets, nclips, pl.T, pl.ny_pad, pl.V, ws + pl.off_ycnt);
     batch_group_scatter_kernel<<<dim3(bx, nclips), 256, 0, st>>>(pl.vy, pl.offsets, nclips, pl.T, pl.ny_pad, pl.V,
                                                                 ws + pl.off_ycnt);
     count_launch(3);
