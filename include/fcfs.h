@@ -265,7 +265,11 @@ fcfs_status fcfs_cosine(const int32_t* x, const int32_t* y, const int8_t* s, int
  *   flags      : must be 0.
  *   W_out      : 4^J doubles (device), written completely.
  *   workspace  : >= fcfs_haar_workspace_size(V, T, J) bytes, 256-byte aligned
- *                (an int64 grid of 4^J level-J cell areas and smaller grids).
+ *                (the corners grouped by x, the coarse area grids, and either the
+ *                column sums of bands of 32 cell rows -- grids of >= 256 cells a
+ *                side with cells up to 1024 wide, built band by band on chip --
+ *                or the whole grid of 4^J level-J cell areas, 32-bit for cells up
+ *                to 1024 wide, else 64-bit).
  * Returns FCFS_OK once enqueued.
  */
 size_t fcfs_haar_workspace_size(int64_t V, int32_t T, int32_t J);
