@@ -300,7 +300,7 @@ def traffic_per_launch():
 # committed ncu summaries that carry per-launch DRAM traffic: stage -> (file,
 # kernel line tag, the sources the kernel is built from)
 STAGE_TRAFFIC = {
-    "h_poly": ("step_T65536_K1024.md", "hyb_h_kernel<1>", ("fcfs_hybrid.cu", "fcfs_common.cuh")),
+    "h_poly": ("step_T65536_K1024.md", "hyb_h_kernel<1>", ("fcfs_hybrid.cu", "fcfs_fft.cuh", "fcfs_common.cuh")),
     "fft_y": ("step_T65536_K1024.md", "fft_y_fused_kernel", ("fcfs_fft.cu", "fcfs_fft.cuh", "fcfs_common.cuh")),
     "adj_fft": ("step_T65536_K1024.md", "adj_fft_kernel<11>", ("fcfs_adjoint_fft.cu", "fcfs_fft.cuh", "fcfs_common.cuh")),
     "adj_dot": ("step_T65536_K1024.md", "adj_dot_kernel", ("fcfs_adjoint_fft.cu", "fcfs_fft.cuh", "fcfs_common.cuh")),

@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "fcfs_epilogue.cuh"
+#include "fcfs_fft.cuh"
 #include "fcfs_group.cuh"
 #include "fcfs_launch.cuh"
 
@@ -615,24 +616,7 @@ __device__ __forceinline__ void row_sums(const uint2* __restrict__ meta, const f
   }
 }
 
-// Packed FP32 pairs (f32x2): d = a b + c and d = a b elementwise, each element
-// rounded as the scalar fmaf / multiply.
-__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return d;
-}
-__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
+// Packed FP32 pairs: ffma2 / fmul2 (fcfs_fft.cuh); dup broadcasts a value to both halves.
 __device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 
 // The 8 sums of one row as in row_sums, the lane's frequencies taken two at a
@@ -666,11 +650,11 @@ __device__ __forceinline__ void row_sums_x2(const uint2* __restrict__ meta, cons
     if (kind == 2u) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        re[j] = pfma(ax, dup(1.f), re[j]);
-        im[j] = pfma(ay, dup(1.f), im[j]);
+        re[j] = ffma2(ax, dup(1.f), re[j]);
+        im[j] = ffma2(ay, dup(1.f), im[j]);
         if (j < 3) {
-          const float2 nx = pfma(ay, ns2y, pmul(ax, s2x));
-          ay = pfma(ay, s2x, pmul(ax, s2y));
+          const float2 nx = ffma2(ay, ns2y, fmul2(ax, s2x));
+          ay = ffma2(ay, s2x, fmul2(ax, s2y));
           ax = nx;
         }
       }
@@ -686,15 +670,15 @@ __device__ __forceinline__ void row_sums_x2(const uint2* __restrict__ meta, cons
     if (kind == 0u) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        re[j] = pfma(ax, dx, re[j]);
-        q[j] = pfma(ay, dy, q[j]);
-        im[j] = pfma(ax, dy, pfma(ay, dx, im[j]));
+        re[j] = ffma2(ax, dx, re[j]);
+        q[j] = ffma2(ay, dy, q[j]);
+        im[j] = ffma2(ax, dy, ffma2(ay, dx, im[j]));
         if (j < 3) {
-          const float2 nx = pfma(ay, ns2y, pmul(ax, s2x));
-          ay = pfma(ay, s2x, pmul(ax, s2y));
+          const float2 nx = ffma2(ay, ns2y, fmul2(ax, s2x));
+          ay = ffma2(ay, s2x, fmul2(ax, s2y));
           ax = nx;
-          const float2 ex = pfma(dy, nc2y, pfma(dx, c2x, d64x));
-          dy = pfma(dy, c2x, pfma(dx, c2y, d64y));
+          const float2 ex = ffma2(dy, nc2y, ffma2(dx, c2x, d64x));
+          dy = ffma2(dy, c2x, ffma2(dx, c2y, d64y));
           dx = ex;
         }
       }
@@ -708,18 +692,18 @@ __device__ __forceinline__ void row_sums_x2(const uint2* __restrict__ meta, cons
         re[j].y = fmaf(ax.y, ex1, fmaf(-ay.y, ey1, re[j].y));
         im[j].y = fmaf(ax.y, ey1, fmaf(ay.y, ex1, im[j].y));
         if (j < 3) {
-          const float2 nx = pfma(ay, ns2y, pmul(ax, s2x));
-          ay = pfma(ay, s2x, pmul(ax, s2y));
+          const float2 nx = ffma2(ay, ns2y, fmul2(ax, s2x));
+          ay = ffma2(ay, s2x, fmul2(ax, s2y));
           ax = nx;
-          const float2 ex = pfma(dy, nc2y, pfma(dx, c2x, d64x));
-          dy = pfma(dy, c2x, pfma(dx, c2y, d64y));
+          const float2 ex = ffma2(dy, nc2y, ffma2(dx, c2x, d64x));
+          dy = ffma2(dy, c2x, ffma2(dx, c2y, d64y));
           dx = ex;
         }
       }
     }
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) re[j] = pfma(q[j], dup(-1.f), re[j]);
+  for (int j = 0; j < 4; ++j) re[j] = ffma2(q[j], dup(-1.f), re[j]);
 }
 
 // kHRowsFp16 fast path: passes of 256 frequencies over the item's 64 rows into
